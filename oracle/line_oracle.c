@@ -1,0 +1,401 @@
+/*
+ * FP64 serial CPU oracle for the LINE training step that NOMAD distributes
+ * (arXiv 2604.09419).  TEST INFRASTRUCTURE ONLY: the tests, the smoke check
+ * and the CPU-baseline leg of the benchmark call it; the library never does.
+ * It shares no source with the CUDA path.
+ *
+ * What it computes, in the paper's notation:
+ *   - negative distribution q(v) ∝ d(v)^0.75 with d the (weighted) out-degree
+ *     (Section IV-A, Eq. 1);
+ *   - weight-proportional edge selection (Algorithm 3, the discrete
+ *     distribution over E_p / ||E_p||);
+ *   - both as alias tables over exact integer masses;
+ *   - the per-pair gradient scalars g = eta(1 - sigma(U[u].C[v])) and
+ *     g = -eta alpha_neg sigma(U[u].C[v-]) (Algorithm 1);
+ *   - the LineUpdate of Algorithm 1 / Eq. 2-3 with the per-batch delta
+ *     accumulation of Eq. 4: every row's contributions within a batch are
+ *     summed against the batch-start tables and applied once after the batch.
+ *
+ * Everything is plain loops in the order of the definitions; no blocking, no
+ * fusion.  Build: gcc -O2 -ffp-contract=off -shared -fPIC.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel Random Numbers: As   */
+/* Easy as 1, 2, 3", SC'11): 10 rounds of the 4x32 S-box, key bumped by the  */
+/* Weyl constants between rounds.                                            */
+/* ------------------------------------------------------------------------ */
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+void orc_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4]) {
+    uint32_t c0 = ctr_in[0], c1 = ctr_in[1], c2 = ctr_in[2], c3 = ctr_in[3];
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_W0;
+            k1 += PHILOX_W1;
+        }
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n1 = lo1;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        uint32_t n3 = lo0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* One draw: counter (t_lo, t_hi, call, domain), key (seed_lo, seed_hi). */
+static void draw_words(uint64_t seed, uint32_t domain, uint64_t t, uint32_t call, uint32_t w[4]) {
+    uint32_t ctr[4] = {(uint32_t)t, (uint32_t)(t >> 32), call, domain};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    orc_philox4x32_10(ctr, key, w);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 1 weights.                                                            */
+/* ------------------------------------------------------------------------ */
+
+/* d(v)^0.75 written as sqrt(d) * sqrt(sqrt(d)): both square roots and the
+ * product are correctly rounded, so the value is a function of d alone. */
+static double pow075(double d) {
+    if (d <= 0.0) return 0.0;
+    double r = sqrt(d);
+    return r * sqrt(r);
+}
+
+/* d(v) = sum of the weights of v's out-arcs (arcs in index order, left to
+ * right), then x_v = d(v)^0.75.  Arcs must be grouped by src; only src and w
+ * are read.  w == NULL means unit weights. */
+int orc_neg_weights(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const float* w, double* x_out) {
+    for (int64_t v = 0; v < n_nodes; ++v) x_out[v] = 0.0;
+    for (int64_t e = 0; e < n_arcs; ++e) {
+        int32_t s = src[e];
+        if (s < 0 || s >= n_nodes) return -1;
+        x_out[s] += w ? (double)w[e] : 1.0;
+    }
+    for (int64_t v = 0; v < n_nodes; ++v) x_out[v] = pow075(x_out[v]);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Alias tables over exact integer masses.                                   */
+/* ------------------------------------------------------------------------ */
+#define ALIAS_BLOCK 1024
+#define Q32 4294967296ull
+#define THR_FULL 0xFFFFFFFFu
+
+/* Fixed-order FP64 sum: blocks of 1024 consecutive values (zero padded),
+ * each reduced by halving strides (v[i] += v[i + s] for s = 512..1); the
+ * block sums are reduced the same way, recursively. */
+double orc_fixed_sum(int64_t n, const double* x) {
+    if (n <= 0) return 0.0;
+    int64_t nb = (n + ALIAS_BLOCK - 1) / ALIAS_BLOCK;
+    double* sums = (double*)malloc(sizeof(double) * (size_t)nb);
+    double buf[ALIAS_BLOCK];
+    for (int64_t b = 0; b < nb; ++b) {
+        for (int i = 0; i < ALIAS_BLOCK; ++i) {
+            int64_t j = b * ALIAS_BLOCK + i;
+            buf[i] = j < n ? x[j] : 0.0;
+        }
+        for (int s = ALIAS_BLOCK / 2; s >= 1; s /= 2)
+            for (int i = 0; i < s; ++i) buf[i] = buf[i] + buf[i + s];
+        sums[b] = buf[0];
+    }
+    double r = nb == 1 ? sums[0] : orc_fixed_sum(nb, sums);
+    free(sums);
+    return r;
+}
+
+/* Integer masses m_i with sum exactly n * 2^32:
+ *   W = fixed-order sum of x;  S = (n * 2^32) / W;  m_i = floor(x_i * S);
+ *   D = n * 2^32 - sum(m).
+ *   D > 0: round-robin +1 over the indices with x_i > 0 in increasing order
+ *          (q = D / P added to all P of them, +1 more to the first D % P);
+ *   D < 0: -1 to each of the first |D| indices with m_i >= 1.
+ * Returns 0, or -1 if W is not positive and finite, -2 if |D| cannot be
+ * absorbed. */
+int orc_alias_masses(int64_t n, const double* x, uint64_t* m) {
+    double W = orc_fixed_sum(n, x);
+    if (!(W > 0.0) || !isfinite(W)) return -1;
+    double S = ((double)n * 4294967296.0) / W;
+    uint64_t total = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        double f = floor(x[i] * S);
+        m[i] = (uint64_t)f;
+        total += m[i];
+    }
+    int64_t D = (int64_t)((uint64_t)n * Q32 - total);
+    if (D > 0) {
+        int64_t P = 0;
+        for (int64_t i = 0; i < n; ++i) P += x[i] > 0.0;
+        int64_t q = D / P, r = D % P, rank = 0;
+        for (int64_t i = 0; i < n; ++i) {
+            if (x[i] > 0.0) {
+                m[i] += (uint64_t)(q + (rank < r ? 1 : 0));
+                ++rank;
+            }
+        }
+    } else if (D < 0) {
+        int64_t need = -D;
+        for (int64_t i = 0; i < n && need > 0; ++i) {
+            if (m[i] >= 1) {
+                m[i] -= 1;
+                --need;
+            }
+        }
+        if (need > 0) return -2;
+    }
+    return 0;
+}
+
+/* Sweep pairing of light buckets (m < 2^32) with heavy ones (m > 2^32): the
+ * current heavy item donates to the lights in increasing index order; when
+ * its remaining mass r drops below 2^32 its own bucket becomes a light one
+ * with threshold r, topped up by the next heavy item.  Buckets with
+ * m == 2^32, and the last heavy item, keep all their mass.
+ * Draw: i = mulhi64(w1:w0, n); k = (w2 < thr[i]) ? i : alias[i]. */
+int orc_alias_pair(int64_t n, const uint64_t* m, uint32_t* thr, uint32_t* alias) {
+    int64_t* heavy = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+    int64_t nh = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        if (m[i] == Q32) {
+            thr[i] = THR_FULL;
+            alias[i] = (uint32_t)i;
+        } else if (m[i] > Q32) {
+            heavy[nh++] = i;
+        }
+    }
+    int rc = 0;
+    if (nh > 0) {
+        int64_t k = 0;
+        uint64_t r = m[heavy[0]];
+        for (int64_t l = 0; l < n && rc == 0; ++l) {
+            if (m[l] >= Q32) continue;
+            thr[l] = (uint32_t)m[l];
+            alias[l] = (uint32_t)heavy[k];
+            r -= Q32 - m[l];
+            while (r < Q32) {
+                if (k + 1 >= nh) { rc = -3; break; }
+                thr[heavy[k]] = (uint32_t)r;
+                alias[heavy[k]] = (uint32_t)heavy[k + 1];
+                r = m[heavy[k + 1]] - (Q32 - r);
+                ++k;
+            }
+        }
+        if (rc == 0) {
+            if (k != nh - 1 || r != Q32) rc = -4;
+            thr[heavy[k]] = THR_FULL;
+            alias[heavy[k]] = (uint32_t)heavy[k];
+        }
+    } else {
+        for (int64_t i = 0; i < n; ++i)
+            if (m[i] < Q32) rc = -5; /* lights without heavies: masses do not sum to n*2^32 */
+    }
+    free(heavy);
+    return rc;
+}
+
+int orc_alias_build(int64_t n, const double* x, uint64_t* m_out, uint32_t* thr, uint32_t* alias) {
+    int rc = orc_alias_masses(n, x, m_out);
+    if (rc) return rc;
+    return orc_alias_pair(n, m_out, thr, alias);
+}
+
+static inline uint32_t alias_draw(int64_t n, const uint32_t* thr, const uint32_t* alias,
+                                  uint32_t w0, uint32_t w1, uint32_t w2) {
+    uint64_t r64 = ((uint64_t)w1 << 32) | (uint64_t)w0;
+    uint64_t i = (uint64_t)(((unsigned __int128)r64 * (unsigned __int128)(uint64_t)n) >> 64);
+    return w2 < thr[i] ? (uint32_t)i : alias[i];
+}
+
+uint32_t orc_alias_draw(int64_t n, const uint32_t* thr, const uint32_t* alias,
+                        uint32_t w0, uint32_t w1, uint32_t w2) {
+    return alias_draw(n, thr, alias, w0, w1, w2);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Per-sample draws: sample t, call 0 draws the arc e (u = src[e],           */
+/* v = dst[e]); calls 1..K draw the negatives from q (Algorithm 1, Eq. 1).   */
+/* out[(t - t0) * (K + 2) + {0, 1, 1 + j}] = u, v, n_j.                      */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n_nodes, n_arcs;
+    const int32_t* src;
+    const int32_t* dst;
+    const uint32_t* thr_e;
+    const uint32_t* alias_e;
+    const uint32_t* thr_n;
+    const uint32_t* alias_n;
+} orc_tables;
+
+static void sample_one(const orc_tables* T, uint64_t seed, uint32_t domain, uint64_t t, int K, int32_t* rec) {
+    uint32_t w[4];
+    draw_words(seed, domain, t, 0, w);
+    uint32_t e = alias_draw(T->n_arcs, T->thr_e, T->alias_e, w[0], w[1], w[2]);
+    rec[0] = T->src[e];
+    rec[1] = T->dst[e];
+    for (int j = 1; j <= K; ++j) {
+        draw_words(seed, domain, t, (uint32_t)j, w);
+        rec[1 + j] = (int32_t)alias_draw(T->n_nodes, T->thr_n, T->alias_n, w[0], w[1], w[2]);
+    }
+}
+
+int orc_sample(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t* dst,
+               const uint32_t* thr_e, const uint32_t* alias_e, const uint32_t* thr_n, const uint32_t* alias_n,
+               uint64_t seed, uint32_t domain, uint64_t t0, int64_t count, int K, int32_t* out) {
+    orc_tables T = {n_nodes, n_arcs, src, dst, thr_e, alias_e, thr_n, alias_n};
+    for (int64_t i = 0; i < count; ++i) sample_one(&T, seed, domain, t0 + (uint64_t)i, K, out + i * (K + 2));
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Initialisation: U[i][k] = ((w >> 8) - 2^23) * 2^-24 / dim, w = word       */
+/* (k mod 4) of the draw at counter (i_lo, i_hi, k / 4, 1): uniform on       */
+/* [-0.5/dim, 0.5/dim).  C = 0.                                              */
+/* ------------------------------------------------------------------------ */
+void orc_init_uniform(int64_t n, int dim, uint64_t seed, double* U) {
+    for (int64_t i = 0; i < n; ++i) {
+        for (int k = 0; k < dim; ++k) {
+            uint32_t w[4];
+            draw_words(seed, 1, (uint64_t)i, (uint32_t)(k / 4), w);
+            int32_t q = (int32_t)(w[k % 4] >> 8) - (1 << 23);
+            U[i * dim + k] = ((double)q * (1.0 / 16777216.0)) / (double)dim;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Minibatch-synchronous LINE (Algorithm 1 with Eq. 2-4).                    */
+/* ------------------------------------------------------------------------ */
+static double sigmoid(double s) { return 1.0 / (1.0 + exp(-s)); }
+
+static double dot(const double* a, const double* b, int dim) {
+    double s = 0.0;
+    for (int k = 0; k < dim; ++k) s += a[k] * b[k];
+    return s;
+}
+
+/* eta_b = lr0 (schedule 0) or lr0 * max(1 - t0 / T, floor_frac) (schedule 1),
+ * t0 the first global sample index of the batch. */
+double orc_batch_lr(double lr0, int schedule, double floor_frac, uint64_t T, uint64_t t0) {
+    if (schedule == 0) return lr0;
+    double f = 1.0 - (double)t0 / (double)T;
+    if (f < floor_frac) f = floor_frac;
+    return lr0 * f;
+}
+
+/* Trains n_samples samples starting at global index sample_offset, in batches
+ * of `batch` consecutive samples.  For each pair (x, y, label) of a sample:
+ *   s = U_b[x] . Ctx_b[y],  g = eta_b (1 - sigma(s)) (label 1)
+ *                             g = -eta_b alpha_neg sigma(s) (label 0),
+ *   dU[x]   += g Ctx_b[y] - eta_b lambda U_b[x]
+ *   dCtx[y] += g U_b[x]   - eta_b lambda Ctx_b[y]
+ * where _b is the state at the start of the batch; after the batch X += dX.
+ * order 2: Ctx = C (a separate table); order 1: Ctx = U (C is unused).
+ * lr_total is T of the schedule (0 means sample_offset + n_samples). */
+int orc_train(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t* dst,
+              const uint32_t* thr_e, const uint32_t* alias_e, const uint32_t* thr_n, const uint32_t* alias_n,
+              int order, int dim, int K, double lr0, int schedule, double lr_floor_frac, uint64_t lr_total,
+              uint64_t n_samples, uint64_t seed, int64_t batch, double lambda, double alpha_neg,
+              uint64_t sample_offset, double* U, double* C) {
+    if (batch <= 0 || dim <= 0 || K < 0 || (order != 1 && order != 2)) return -1;
+    orc_tables T = {n_nodes, n_arcs, src, dst, thr_e, alias_e, thr_n, alias_n};
+    double* Ctx = order == 2 ? C : U;
+    double* dU = (double*)calloc((size_t)n_nodes * (size_t)dim, sizeof(double));
+    double* dC = order == 2 ? (double*)calloc((size_t)n_nodes * (size_t)dim, sizeof(double)) : dU;
+    char* touchU = (char*)calloc((size_t)n_nodes, 1);
+    char* touchC = order == 2 ? (char*)calloc((size_t)n_nodes, 1) : touchU;
+    int32_t* rows = (int32_t*)malloc(sizeof(int32_t) * (size_t)(2 * batch * (K + 2)));
+    int32_t* rec = (int32_t*)malloc(sizeof(int32_t) * (size_t)(K + 2));
+    if (!dU || !dC || !touchU || !touchC || !rows || !rec) return -2;
+    uint64_t Ttot = lr_total ? lr_total : sample_offset + n_samples;
+    uint64_t end = sample_offset + n_samples;
+    for (uint64_t t0 = sample_offset; t0 < end; t0 += (uint64_t)batch) {
+        uint64_t t1 = t0 + (uint64_t)batch < end ? t0 + (uint64_t)batch : end;
+        double eta = orc_batch_lr(lr0, schedule, lr_floor_frac, Ttot, t0);
+        int64_t nrows_u = 0, nrows_c = 0;
+        int32_t* rows_u = rows;
+        int32_t* rows_c = rows + batch * (K + 2);
+        for (uint64_t t = t0; t < t1; ++t) {
+            sample_one(&T, seed, 0, t, K, rec);
+            int32_t x = rec[0];
+            for (int j = 0; j <= K; ++j) {
+                int32_t y = rec[1 + j];
+                double label = j == 0 ? 1.0 : 0.0;
+                const double* ux = U + (int64_t)x * dim;
+                const double* cy = Ctx + (int64_t)y * dim;
+                double s = dot(ux, cy, dim);
+                double g = j == 0 ? eta * (label - sigmoid(s)) : -eta * alpha_neg * sigmoid(s);
+                double* dux = dU + (int64_t)x * dim;
+                double* dcy = dC + (int64_t)y * dim;
+                for (int k = 0; k < dim; ++k) {
+                    dux[k] += g * cy[k] - eta * lambda * ux[k];
+                    dcy[k] += g * ux[k] - eta * lambda * cy[k];
+                }
+                if (!touchU[x]) { touchU[x] = 1; rows_u[nrows_u++] = x; }
+                if (!touchC[y]) {
+                    touchC[y] = 1;
+                    if (order == 2) rows_c[nrows_c++] = y;
+                    else rows_u[nrows_u++] = y;
+                }
+            }
+        }
+        for (int64_t r = 0; r < nrows_u; ++r) {
+            int64_t v = rows_u[r];
+            for (int k = 0; k < dim; ++k) { U[v * dim + k] += dU[v * dim + k]; dU[v * dim + k] = 0.0; }
+            touchU[v] = 0;
+        }
+        for (int64_t r = 0; r < nrows_c; ++r) {
+            int64_t v = rows_c[r];
+            for (int k = 0; k < dim; ++k) { C[v * dim + k] += dC[v * dim + k]; dC[v * dim + k] = 0.0; }
+            touchC[v] = 0;
+        }
+    }
+    free(rec);
+    free(rows);
+    if (order == 2) { free(dC); free(touchC); }
+    free(dU);
+    free(touchU);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Negative-sampling LINE loss over m fixed samples (draw domain 3):         */
+/*   L = - sum_t [ log sigma(s+) + sum_j log sigma(-s-_j) ]                  */
+/* with s = U[u] . Ctx[y] (Ctx = C for order 2, U for order 1).              */
+/* ------------------------------------------------------------------------ */
+static double log_sigmoid(double s) {
+    /* log sigma(s) = -(max(-s, 0) + log1p(exp(-|s|))) */
+    double a = s < 0.0 ? -s : 0.0;
+    return -(a + log1p(exp(-fabs(s))));
+}
+
+double orc_eval_loss(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t* dst,
+                     const uint32_t* thr_e, const uint32_t* alias_e, const uint32_t* thr_n, const uint32_t* alias_n,
+                     int order, int dim, int K, uint64_t seed, int64_t m, const double* U, const double* C) {
+    orc_tables T = {n_nodes, n_arcs, src, dst, thr_e, alias_e, thr_n, alias_n};
+    const double* Ctx = order == 2 ? C : U;
+    int32_t* rec = (int32_t*)malloc(sizeof(int32_t) * (size_t)(K + 2));
+    double L = 0.0;
+    for (int64_t t = 0; t < m; ++t) {
+        sample_one(&T, seed, 3, (uint64_t)t, K, rec);
+        const double* ux = U + (int64_t)rec[0] * dim;
+        for (int j = 0; j <= K; ++j) {
+            double s = dot(ux, Ctx + (int64_t)rec[1 + j] * dim, dim);
+            L -= j == 0 ? log_sigmoid(s) : log_sigmoid(-s);
+        }
+    }
+    free(rec);
+    return L;
+}
