@@ -1,0 +1,314 @@
+"""Benchmark: LINE edge-sample updates/s on R-MAT scale 20 (d=128, K=5, FP32).
+
+Workload: R-MAT scale 20 (1,048,576 nodes, edge factor 16, (a,b,c,d) =
+(.57,.19,.19,.05), symmetrised, duplicates merged into integer weights),
+first- and second-order LINE, d=128, K=5 negatives from deg^0.75, FP32
+tables, deterministic minibatch B=4096, lr 0.025 with linear decay over
+20 x |E| samples per order.  One step = |E| = 16 * 2^20 samples of each
+order (one "epoch" of each), so 20 steps are the full run.
+
+Output: one JSON line (rank 0).  `value` is device-timed throughput with the
+graph and tables resident in HBM; `e2e` is the same metric through the C ABI
+from host buffers (graph upload + alias build + training + read-back of the
+order-2 U table, every step).  `--impl reference` times the FP64 oracle on
+the host cores instead (a bounded prefix of the same workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "edge-sample updates/s (d=128,K=5)"
+UNIT = "updates/s"
+DIM, K, B = 128, 5, 4096
+ROW_BYTES_F32 = DIM * 4
+# algorithmic bytes per edge-sample update: 7 rows read + 7 written, plus
+# sampling metadata (edge alias 8 B + arc endpoints 8 B + K neg alias 5 x 8 B)
+ALG_BYTES_PATH = 14 * ROW_BYTES_F32 + 8 + 8 + 8 * K
+# the update kernels alone move the 14 rows
+ALG_BYTES_UPDATE = 14 * ROW_BYTES_F32
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--mode", default="auto", choices=["auto", "batched", "persistent"])
+    p.add_argument("--scale", type=int, default=20)
+    p.add_argument("--samples-per-step", type=int, default=0, help="0: |E| = 16 * 2^scale")
+    p.add_argument("--e2e-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-samples", type=int, default=1 << 21)
+    return p.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.QUERY}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(g, n_samples: int):
+    """The FP64 oracle, single-threaded, on a prefix of the same workload (order 2)."""
+    import numpy as np
+
+    import oracle as O
+    T = O.Tables(g)
+    U = O.init_uniform(g.n_nodes, DIM, 1)
+    C = np.zeros_like(U)
+    t0 = time.perf_counter()
+    O.train(T, U, C, order=2, K=K, n_samples=n_samples, seed=11, batch=B, lr_total=20 * 16 * g.n_nodes)
+    dt = time.perf_counter() - t0
+    return {"value": n_samples / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"order-2 FP64 oracle on the first {n_samples} samples of the workload "
+                      f"(single thread, host has {os.cpu_count()} cores); {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if world > 1 and rank != 0:
+        return
+    from paper_2604_09419_gb300 import inputs as I
+    g = I.rmat(args.scale, seed=0)
+    n = min(args.cpu_samples, 1 << 19)
+    times = []
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        cpu_baseline(g, 4096)
+    for _ in range(args.steps):
+        r = cpu_baseline(g, n)
+        times.append(n / r["value"])
+    value = n / statistics.median(times)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, g),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"{n} samples of order 2 per step (FP64 oracle, single thread)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, g):
+    return {"workload": f"rmat{args.scale}_line_order1+2_d{DIM}_K{K}_B{B}_fp32",
+            "graph": f"R-MAT scale {args.scale}, edge factor 16, (.57,.19,.19,.05), symmetrised",
+            "n_nodes": g.n_nodes, "n_arcs": g.n_arcs, "dim": DIM, "K": K, "batch": B,
+            "samples_per_step": 2 * samples_per_step(args),
+            "lr": "0.025 linear decay over 20*|E| samples per order",
+            "l2": "inputs larger than L2 (FP32 U1, U2, C2 tables: 1.5 GiB; alias tables 258 MB)"}
+
+
+def samples_per_step(args):
+    return args.samples_per_step or 16 * (1 << args.scale)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_2604_09419_gb300 import inputs as I
+    from paper_2604_09419_gb300 import line as L
+
+    g = I.rmat(args.scale, seed=0)
+    S = samples_per_step(args)
+    total_per_order = 20 * 16 * (1 << args.scale)
+    stream = torch.cuda.current_stream()
+    ctx = L.Context(local, stream.cuda_stream)
+    src = torch.from_numpy(g.src).cuda()
+    dst = torch.from_numpy(g.dst).cuda()
+    w = torch.from_numpy(g.w).cuda()
+    ctx.build_alias(g.n_nodes, src, dst, w)
+    mode = {"auto": L.MODE_BATCHED, "batched": L.MODE_BATCHED, "persistent": L.MODE_PERSISTENT}[args.mode]
+    seed = 1000 + rank  # independent replicas per rank
+
+    def opts(offset):
+        o = L.train_opts_default()
+        o.batch = B
+        o.mode = mode
+        o.timing = 1
+        o.sample_offset = offset
+        return o
+
+    ctx.init_embeddings(1, DIM, L.DTYPE_F32, seed=1)
+    ctx.init_embeddings(2, DIM, L.DTYPE_F32, seed=2)
+    state = {"offset": 0}
+
+    def step():
+        off = state["offset"] % total_per_order
+        for order in (1, 2):
+            ctx.train_steps(order, DIM, K, S, seed, total=total_per_order, opts=opts(off))
+        state["offset"] += S
+
+    for _ in range(args.warmup):
+        step()
+    ctx.reset_stats()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    barrier()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step()
+        ev1.record(stream)
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    st = ctx.stats()
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    updates = 2 * S * args.steps * world
+    value = updates / (ms / 1e3)
+
+    # roofline of the update kernels (gather + apply), from their own CUDA events
+    peak, peak_kind = peaks()
+    upd_ms = st.update_ms
+    upd_bytes = st.update_samples * ALG_BYTES_UPDATE
+    achieved = upd_bytes / (upd_ms / 1e3) / 1e9 if upd_ms > 0 else None
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak if achieved else None, "traffic": None,
+                "kernel": "update phase (k_gather + k_apply)" if mode == L.MODE_BATCHED else "k_persistent",
+                "alg_bytes_per_sample": ALG_BYTES_UPDATE, "peak_kind": peak_kind,
+                "path_achieved_gbs": value / world * ALG_BYTES_PATH / 1e9,
+                "path_frac": value / world * ALG_BYTES_PATH / 1e9 / peak}
+    launches = int(st.update_launches + st.prepass_launches)
+
+    # end to end through the C ABI from pinned host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        hs = torch.from_numpy(g.src).pin_memory()
+        hd = torch.from_numpy(g.dst).pin_memory()
+        hw = torch.from_numpy(g.w).pin_memory()
+        out = torch.empty((g.n_nodes, DIM), dtype=torch.float32).pin_memory()
+        ctx2 = L.Context(local, stream.cuda_stream)
+        ctx2.build_alias(g.n_nodes, hs, hd, hw)
+        ctx2.init_embeddings(1, DIM, L.DTYPE_F32, seed=1)
+        ctx2.init_embeddings(2, DIM, L.DTYPE_F32, seed=2)
+        barrier()
+        t0 = time.perf_counter()
+        for i in range(args.e2e_steps):
+            ctx2.build_alias(g.n_nodes, hs, hd, hw)
+            ctx2.init_embeddings(1, DIM, L.DTYPE_F32, seed=1)
+            ctx2.init_embeddings(2, DIM, L.DTYPE_F32, seed=2)
+            for order in (1, 2):
+                ctx2.train_steps(order, DIM, K, S, seed, total=total_per_order, opts=opts(0))
+            ctx2.get_embeddings(2, L.WHICH_U, out)
+        barrier()
+        dt = time.perf_counter() - t0
+        ctx2.close()
+        e2e = {"value": 2 * S * args.e2e_steps * world / dt, "unit": UNIT,
+               "h2d_bytes_per_step": int(g.n_arcs * 12), "d2h_bytes_per_step": int(g.n_nodes * DIM * 4),
+               "includes": "graph upload + alias build + table init + both orders + U2 read-back"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(g, args.cpu_samples)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(args, g), "roofline": roofline, "cpu_baseline": cpu,
+                "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
+                "mode": "batched" if mode == L.MODE_BATCHED else "persistent"}
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

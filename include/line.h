@@ -1,0 +1,211 @@
+/*
+ * line.h - C ABI of the GB300 (sm_103a) LINE training library.
+ *
+ * The library implements, on one GPU, the LINE training step that NOMAD
+ * (arXiv 2604.09419) distributes over CPU clusters:
+ *   - weight-proportional arc (positive pair) selection - Algorithm 3, the
+ *     discrete distribution over E_p / ||E_p||;
+ *   - K negatives per positive from q(v) = d(v)^0.75 / sum_x d(x)^0.75 -
+ *     Section IV-A, Eq. 1 (d = weighted out-degree);
+ *   - per pair the gradient scalar g = eta(1 - sigma(U[u].C[v])) or
+ *     g = -eta alpha_neg sigma(U[u].C[v-]) - Algorithm 1 - and the
+ *     LineUpdate of Eq. 2-3;
+ *   - minibatch-synchronous semantics: all contributions to a row within a
+ *     batch are computed from the batch-start tables and summed before being
+ *     applied once, as the owner applies the summed remote deltas of Eq. 4.
+ *     The sum runs over a sorted segmented reduction in a fixed order, so
+ *     results are bitwise reproducible.
+ *
+ * Every draw is a Philox4x32-10 output (Salmon et al., SC'11) at counter
+ * (t_lo, t_hi, call, domain) under key (seed_lo, seed_hi); t is the global
+ * sample index, call 0 draws the arc and calls 1..K the negatives, domain 0
+ * is training and 3 the loss evaluation.  A draw maps its words (w0, w1, w2)
+ * through an alias table: i = mulhi64(w1:w0, n), k = w2 < thr[i] ? i : alias[i].
+ *
+ * Conventions
+ *   - Every call returns a line_status.  After LINE_ERR_CUDA or
+ *     LINE_ERR_TIMEOUT the context is sticky-errored: later calls return
+ *     LINE_ERR_STATE until line_destroy.  line_last_error() describes the
+ *     first failure.
+ *   - All GPU work is enqueued on the stream given to line_create and is
+ *     stream ordered.  Calls that return a value to the host (train, eval,
+ *     get_alias with host buffers, get_stats) synchronise that stream.
+ *   - Pointers named "buffer" may be device memory or host memory (the
+ *     library copies with unified addressing); the caller owns them and may
+ *     free them when the call returns.
+ *   - The library owns every device allocation it makes (graph copy, alias
+ *     tables, embedding tables, scratch) and frees them in line_destroy.
+ *   - A context is not thread-safe; use one per host thread.
+ */
+#ifndef LINE_H
+#define LINE_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define LINE_API __attribute__((visibility("default")))
+#else
+#define LINE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct line_ctx line_ctx;
+
+typedef enum {
+    LINE_OK = 0,
+    LINE_ERR_ARG = -1,      /* invalid argument; nothing was enqueued */
+    LINE_ERR_OOM = -2,      /* a device allocation failed */
+    LINE_ERR_CUDA = -3,     /* a CUDA call or kernel failed (sticky) */
+    LINE_ERR_TIMEOUT = -4,  /* a device wait exceeded its spin limit (sticky) */
+    LINE_ERR_STATE = -5,    /* call out of order (no graph / no tables) or sticky error */
+    LINE_ERR_VALIDATE = -6  /* input graph or table failed validation */
+} line_status;
+
+enum { LINE_DTYPE_F32 = 0, LINE_DTYPE_BF16 = 1 };
+enum { LINE_TABLE_EDGE = 0, LINE_TABLE_NEG = 1 };
+enum { LINE_WHICH_U = 0, LINE_WHICH_C = 1 };
+enum { LINE_MODE_BATCHED = 0, LINE_MODE_PERSISTENT = 1 };
+
+/* Graph as directed arcs (an undirected edge is two arcs), Section II / V-A.
+ * src, dst: n_arcs int32 node ids in [0, n_nodes); src must be
+ * non-decreasing (CSR order).  w: n_arcs positive finite weights, or NULL
+ * for unit weights.  The three are buffers (device or host); they are read
+ * during line_build_alias only. */
+typedef struct {
+    int64_t n_nodes;
+    int64_t n_arcs;
+    const int32_t* src;
+    const int32_t* dst;
+    const float* w;
+} line_graph_desc;
+
+/* Learning rate per batch (Section V-A: eta = 0.025):
+ * schedule 0: eta_b = lr0;  schedule 1: eta_b = lr0 * max(1 - t0/T, floor_frac)
+ * with t0 the first global sample index of the batch and T = total
+ * (total == 0 means sample_offset + n_samples of the call). */
+typedef struct {
+    double lr0;
+    int schedule;
+    double floor_frac;
+    uint64_t total;
+} line_lr;
+
+/* Options of line_train_steps.  Fill with line_train_opts_default(). */
+typedef struct {
+    int64_t batch;           /* B: samples per minibatch (Algorithm 1), 1..1048576 */
+    double lambda;           /* weight decay lambda of Eq. 2-3 (>= 0) */
+    double alpha_neg;        /* negative weight alpha_neg of Algorithm 1 */
+    uint64_t sample_offset;  /* global index of the first sample; batches start here */
+    int mode;                /* LINE_MODE_BATCHED or LINE_MODE_PERSISTENT */
+    int64_t spin_limit;      /* bound on every device wait loop (iterations); <= 0: default */
+    int chunk_batches;       /* batches per pre-pass chunk; 0: automatic */
+    int warps_per_block;     /* 0: automatic */
+    int timing;              /* 1: time the training kernels with CUDA events (line_get_stats) */
+} line_train_opts;
+
+/* Per-kernel timing collected when opts.timing == 1 (reset by line_reset_stats). */
+typedef struct {
+    int64_t update_launches;   /* launches of the row-update kernel(s) */
+    double update_ms;          /* their summed CUDA-event time */
+    uint64_t update_samples;   /* samples those launches processed */
+    int64_t prepass_launches;  /* sampling + sort + segment launches */
+    double prepass_ms;
+    double total_ms;           /* event time of whole line_train_steps calls */
+    uint64_t total_samples;
+} line_stats;
+
+LINE_API void line_train_opts_default(line_train_opts* opts);
+LINE_API const char* line_status_string(line_status s);
+
+/* Create a context on CUDA device `device`; all work goes to `cuda_stream`
+ * (a cudaStream_t, NULL for the legacy default stream).  *out receives the
+ * context or NULL on failure. */
+LINE_API line_status line_create(line_ctx** out, int device, void* cuda_stream);
+LINE_API void line_destroy(line_ctx* ctx);
+LINE_API const char* line_last_error(const line_ctx* ctx);
+
+/* Copy the graph and build both alias tables on the GPU (Eq. 1 and
+ * Algorithm 3).  Weights x (arc weights for the edge table; d(v)^0.75 for
+ * the negative table, d summed over v's arcs in arc order, d^0.75 computed
+ * as sqrt(d)*sqrt(sqrt(d))) are normalised in FP64: W is the sum of x in a
+ * fixed order (blocks of 1024 reduced by halving strides, recursively),
+ * S = n*2^32/W, m_i = floor(x_i*S), and the remainder D = n*2^32 - sum(m) is
+ * spread round robin over x_i > 0 (D > 0) or taken from the first |D| items
+ * with m_i >= 1 (D < 0).  Light buckets (m < 2^32) are paired with heavy
+ * items (m > 2^32) by the sweep rule: heavy items in index order top up the
+ * lights in index order, a heavy item whose remaining mass r falls below
+ * 2^32 becomes a light bucket with thr = r topped up by the next heavy one.
+ * Replaces any previous graph and drops the embedding tables.
+ * Errors: LINE_ERR_ARG (sizes), LINE_ERR_VALIDATE (unsorted src, ids out of
+ * range, non-positive or non-finite weights, a node set with no positive
+ * weight), LINE_ERR_OOM. */
+LINE_API line_status line_build_alias(line_ctx* ctx, const line_graph_desc* g);
+
+LINE_API line_status line_get_graph_info(line_ctx* ctx, int64_t* n_nodes, int64_t* n_arcs);
+
+/* Export an alias table (LINE_TABLE_EDGE: n_arcs entries; LINE_TABLE_NEG:
+ * n_nodes entries) into two uint32 buffers thr[] and alias[]. */
+LINE_API line_status line_get_alias(line_ctx* ctx, int table, uint32_t* thr, uint32_t* alias);
+
+/* Write the draws of samples t0 .. t0+count-1 in `domain` as int32 records
+ * out[count][K+2] = (u, v, n_1 .. n_K) (a buffer). */
+LINE_API line_status line_sample_debug(line_ctx* ctx, int K, uint64_t seed, uint32_t domain, uint64_t t0,
+                              int64_t count, int32_t* out);
+
+/* (Re)create the tables of one order: order 1 has U only (the context of a
+ * pair is U, first-order proximity), order 2 has U and C (second order).
+ * U[i][k] = ((w >> 8) - 2^23) * 2^-24 / dim with w = word (k mod 4) of the
+ * draw at counter (i_lo, i_hi, k/4, 1): uniform on [-0.5/dim, 0.5/dim);
+ * C = 0.  dim in {16, 32, 64, 128, 256}; dtype LINE_DTYPE_F32 or
+ * LINE_DTYPE_BF16 (storage; arithmetic is FP32, BF16 write-back uses
+ * stochastic rounding). */
+LINE_API line_status line_init_embeddings(line_ctx* ctx, int order, int dim, int dtype, uint64_t seed);
+
+/* Train n_samples samples (global indices sample_offset .. +n_samples-1) of
+ * order 1 or 2 with K negatives (0..32) per positive, minibatch-synchronous
+ * (see the file comment).  Splitting a run at a multiple of opts.batch from
+ * its first offset, with the same lr->total, gives bitwise identical tables.
+ * Synchronises the stream at the end to read the device status word.
+ * Errors: LINE_ERR_ARG, LINE_ERR_STATE (no graph or tables of that order and
+ * dim), LINE_ERR_TIMEOUT (persistent mode: a dependency wait exceeded
+ * opts.spin_limit), LINE_ERR_CUDA. */
+LINE_API line_status line_train_steps(line_ctx* ctx, int order, int dim, int K, const line_lr* lr,
+                             uint64_t n_samples, uint64_t seed, const line_train_opts* opts);
+
+/* Copy a whole table (n_nodes x dim, row-major) into `dst` (a buffer) as
+ * dst_dtype (F32, or BF16 when the table is BF16). */
+LINE_API line_status line_get_embeddings(line_ctx* ctx, int order, int which, void* dst, int dst_dtype);
+
+/* Overwrite rows of a table from `src` (a buffer of n_rows x dim values of
+ * src_dtype).  rows: n_rows int32 row ids (a buffer), or NULL for rows
+ * 0..n_rows-1.  F32 into a BF16 table rounds to nearest even.  Used for
+ * warm starts and checkpoint restore. */
+LINE_API line_status line_set_embeddings(line_ctx* ctx, int order, int which, const void* src, int src_dtype,
+                                const int32_t* rows, int64_t n_rows);
+
+/* Negative-sampling LINE loss over the first m samples of draw domain 3:
+ * L = -sum_t [log sigma(s+) + sum_j log sigma(-s-_j)], s = U[u].Ctx[y]
+ * computed in FP64 from the stored values, summed in a fixed order.
+ * Result in *out_host (host pointer). */
+LINE_API line_status line_eval_loss(line_ctx* ctx, int order, int K, uint64_t seed, int64_t m, double* out_host);
+
+LINE_API line_status line_get_stats(line_ctx* ctx, line_stats* out);
+LINE_API line_status line_reset_stats(line_ctx* ctx);
+
+/* Wait for all work of the context's stream. */
+LINE_API line_status line_synchronize(line_ctx* ctx);
+
+/* Exercise the bounded device wait: launches a kernel that waits on a flag
+ * nothing sets, for at most spin_limit polls, and returns LINE_ERR_TIMEOUT
+ * when the wait runs out (the context stays usable: this timeout is not
+ * sticky).  Used by the failure-handling tests. */
+LINE_API line_status line_debug_wait_timeout(line_ctx* ctx, int64_t spin_limit);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LINE_H */

@@ -1,0 +1,506 @@
+// C ABI of the LINE library (include/line.h): argument checking, ownership of
+// device state, error reporting.  All GPU work is in the other .cu files.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "line_internal.cuh"
+
+using namespace line;
+
+namespace {
+
+struct Tables {
+    void* U = nullptr;
+    void* C = nullptr;
+    int dim = 0;
+    int dtype = 0;
+    bool ready = false;
+};
+
+size_t elem_size(int dtype) { return dtype == LINE_DTYPE_F32 ? 4 : 2; }
+
+}  // namespace
+
+struct line_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    bool sticky = false;
+    // graph
+    bool has_graph = false;
+    int64_t n_nodes = 0, n_arcs = 0;
+    int32_t* src = nullptr;
+    int32_t* dst = nullptr;
+    uint2* edge_tab = nullptr;
+    uint2* neg_tab = nullptr;
+    // tables by order (index 1 and 2)
+    Tables tab[3];
+    // device status word and small scratch
+    uint32_t* status = nullptr;
+    uint32_t* flag = nullptr;
+    double* dscratch = nullptr;
+    TrainWorkspace* ws = nullptr;
+    TrainTimes times;
+    double total_ms = 0;
+    uint64_t total_samples = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace {
+
+line_status fail(line_ctx* c, line_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) {
+        if (c->err.empty() || !c->sticky) c->err = buf;
+        if (s == LINE_ERR_CUDA || s == LINE_ERR_TIMEOUT) c->sticky = true;
+    }
+    return s;
+}
+
+line_status cuda_fail(line_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(c, LINE_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+    }
+    return fail(c, LINE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call, what)                                      \
+    do {                                                    \
+        cudaError_t _e = (call);                            \
+        if (_e != cudaSuccess) return cuda_fail(c, _e, what); \
+    } while (0)
+
+line_status enter(line_ctx* c) {
+    if (!c) return LINE_ERR_ARG;
+    if (c->sticky) return LINE_ERR_STATE;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    return LINE_OK;
+}
+
+// Reads and clears the device status word (synchronises the stream).
+line_status check_status(line_ctx* c, const char* what, bool timeout_sticky = true) {
+    uint32_t st = 0;
+    CK(cudaMemcpyAsync(&st, c->status, sizeof st, cudaMemcpyDeviceToHost, c->stream), "status read");
+    CK(cudaStreamSynchronize(c->stream), what);
+    if (st) CK(cudaMemsetAsync(c->status, 0, sizeof(uint32_t), c->stream), "status reset");
+    if (st & DEV_ERR_GRAPH) return fail(c, LINE_ERR_VALIDATE, "%s: graph validation failed", what);
+    if (st & DEV_ERR_ALIAS) return fail(c, LINE_ERR_VALIDATE, "%s: alias construction invariant failed", what);
+    if (st & DEV_ERR_TIMEOUT) {
+        if (timeout_sticky) return fail(c, LINE_ERR_TIMEOUT, "%s: device wait exceeded the spin limit", what);
+        return LINE_ERR_TIMEOUT;
+    }
+    if (st & DEV_ERR_INDEX) return fail(c, LINE_ERR_ARG, "%s: index out of range", what);
+    return LINE_OK;
+}
+
+void free_tables(Tables& t) {
+    if (t.U) cudaFree(t.U);
+    if (t.C) cudaFree(t.C);
+    t = Tables{};
+}
+
+void free_graph(line_ctx* c) {
+    for (void* p : {(void*)c->src, (void*)c->dst, (void*)c->edge_tab, (void*)c->neg_tab})
+        if (p) cudaFree(p);
+    c->src = c->dst = nullptr;
+    c->edge_tab = c->neg_tab = nullptr;
+    c->has_graph = false;
+    for (auto& t : c->tab) free_tables(t);
+}
+
+bool dim_ok(int dim) { return dim == 16 || dim == 32 || dim == 64 || dim == 128 || dim == 256; }
+
+}  // namespace
+
+extern "C" {
+
+void line_train_opts_default(line_train_opts* o) {
+    if (!o) return;
+    o->batch = 4096;
+    o->lambda = 0.0;
+    o->alpha_neg = 1.0;
+    o->sample_offset = 0;
+    o->mode = LINE_MODE_BATCHED;
+    o->spin_limit = 0;
+    o->chunk_batches = 0;
+    o->warps_per_block = 0;
+    o->timing = 0;
+}
+
+const char* line_status_string(line_status s) {
+    switch (s) {
+        case LINE_OK: return "ok";
+        case LINE_ERR_ARG: return "invalid argument";
+        case LINE_ERR_OOM: return "out of device memory";
+        case LINE_ERR_CUDA: return "CUDA error";
+        case LINE_ERR_TIMEOUT: return "device wait timed out";
+        case LINE_ERR_STATE: return "invalid state";
+        case LINE_ERR_VALIDATE: return "validation failed";
+    }
+    return "unknown status";
+}
+
+line_status line_create(line_ctx** out, int device, void* cuda_stream) {
+    if (!out) return LINE_ERR_ARG;
+    *out = nullptr;
+    int n = 0;
+    if (cudaGetDeviceCount(&n) != cudaSuccess || device < 0 || device >= n) {
+        cudaGetLastError();
+        return LINE_ERR_ARG;
+    }
+    line_ctx* c = new line_ctx();
+    c->device = device;
+    c->stream = (cudaStream_t)cuda_stream;
+    if (cudaSetDevice(device) != cudaSuccess || cudaMalloc(&c->status, 256) != cudaSuccess ||
+        cudaMemset(c->status, 0, 256) != cudaSuccess || cudaMalloc(&c->dscratch, 64) != cudaSuccess ||
+        cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) {
+        cudaGetLastError();
+        line_destroy(c);
+        return LINE_ERR_CUDA;
+    }
+    c->flag = c->status + 32;  // never set: target of line_debug_wait_timeout
+    c->ws = workspace_create();
+    *out = c;
+    return LINE_OK;
+}
+
+void line_destroy(line_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    else cudaDeviceSynchronize();
+    free_graph(c);
+    workspace_destroy(c->ws);
+    if (c->status) cudaFree(c->status);
+    if (c->dscratch) cudaFree(c->dscratch);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    cudaGetLastError();
+    delete c;
+}
+
+const char* line_last_error(const line_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+line_status line_build_alias(line_ctx* c, const line_graph_desc* g) {
+    line_status st = enter(c);
+    if (st) return st;
+    if (!g || !g->src || !g->dst) return fail(c, LINE_ERR_ARG, "line_build_alias: null graph arrays");
+    if (g->n_nodes < 1 || g->n_nodes >= (1ll << 30)) return fail(c, LINE_ERR_ARG, "line_build_alias: n_nodes out of range");
+    if (g->n_arcs < 1 || g->n_arcs >= (1ll << 32) - 1) return fail(c, LINE_ERR_ARG, "line_build_alias: n_arcs out of range");
+    free_graph(c);
+    const int64_t n = g->n_nodes, m = g->n_arcs;
+    cudaStream_t s = c->stream;
+    CK(cudaMalloc(&c->src, sizeof(int32_t) * m), "graph allocation");
+    CK(cudaMalloc(&c->dst, sizeof(int32_t) * m), "graph allocation");
+    CK(cudaMalloc(&c->edge_tab, sizeof(uint2) * m), "alias allocation");
+    CK(cudaMalloc(&c->neg_tab, sizeof(uint2) * n), "alias allocation");
+    CK(cudaMemcpyAsync(c->src, g->src, sizeof(int32_t) * m, cudaMemcpyDefault, s), "graph copy");
+    CK(cudaMemcpyAsync(c->dst, g->dst, sizeof(int32_t) * m, cudaMemcpyDefault, s), "graph copy");
+    float* w = nullptr;
+    void* tmp = nullptr;
+    double* x = nullptr;
+    line_status result = LINE_OK;
+    do {
+        cudaError_t e;
+        if (g->w) {
+            if ((e = cudaMalloc(&w, sizeof(float) * m)) != cudaSuccess) { result = cuda_fail(c, e, "weights"); break; }
+            if ((e = cudaMemcpyAsync(w, g->w, sizeof(float) * m, cudaMemcpyDefault, s)) != cudaSuccess) {
+                result = cuda_fail(c, e, "weights copy");
+                break;
+            }
+        }
+        if ((e = validate_graph(n, m, c->src, c->dst, w, c->status, s)) != cudaSuccess) { result = cuda_fail(c, e, "validate"); break; }
+        if ((result = check_status(c, "line_build_alias"))) break;
+        const int64_t big = n > m ? n : m;
+        if ((e = cudaMalloc(&x, sizeof(double) * big)) != cudaSuccess) { result = cuda_fail(c, e, "alias scratch"); break; }
+        if ((e = cudaMalloc(&tmp, alias_build_tmp_bytes(big))) != cudaSuccess) { result = cuda_fail(c, e, "alias scratch"); break; }
+        // edge table: arc weights (Algorithm 3)
+        if ((e = edge_weights(m, w, x, s)) != cudaSuccess) { result = cuda_fail(c, e, "edge weights"); break; }
+        if ((e = alias_build(x, m, c->edge_tab, tmp, c->status, s)) != cudaSuccess) { result = cuda_fail(c, e, "edge alias"); break; }
+        if ((result = check_status(c, "line_build_alias (edges)"))) break;
+        // negative table: d(v)^0.75 (Eq. 1)
+        if ((e = neg_weights(n, m, c->src, w, x, s)) != cudaSuccess) { result = cuda_fail(c, e, "degree weights"); break; }
+        if ((e = alias_build(x, n, c->neg_tab, tmp, c->status, s)) != cudaSuccess) { result = cuda_fail(c, e, "negative alias"); break; }
+        if ((result = check_status(c, "line_build_alias (negatives)"))) break;
+    } while (false);
+    if (w) cudaFree(w);
+    if (x) cudaFree(x);
+    if (tmp) cudaFree(tmp);
+    if (result != LINE_OK) {
+        cudaStreamSynchronize(s);
+        free_graph(c);
+        return result;
+    }
+    c->n_nodes = n;
+    c->n_arcs = m;
+    c->has_graph = true;
+    return LINE_OK;
+}
+
+line_status line_get_graph_info(line_ctx* c, int64_t* n_nodes, int64_t* n_arcs) {
+    line_status st = enter(c);
+    if (st) return st;
+    if (!c->has_graph) return fail(c, LINE_ERR_STATE, "no graph");
+    if (n_nodes) *n_nodes = c->n_nodes;
+    if (n_arcs) *n_arcs = c->n_arcs;
+    return LINE_OK;
+}
+
+line_status line_get_alias(line_ctx* c, int table, uint32_t* thr, uint32_t* alias) {
+    line_status st = enter(c);
+    if (st) return st;
+    if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_get_alias: no graph");
+    if ((table != LINE_TABLE_EDGE && table != LINE_TABLE_NEG) || !thr || !alias)
+        return fail(c, LINE_ERR_ARG, "line_get_alias: bad arguments");
+    const int64_t n = table == LINE_TABLE_EDGE ? c->n_arcs : c->n_nodes;
+    const uint2* tab = table == LINE_TABLE_EDGE ? c->edge_tab : c->neg_tab;
+    uint32_t* buf = nullptr;
+    CK(cudaMalloc(&buf, sizeof(uint32_t) * 2 * n), "alias export scratch");
+    cudaError_t e = export_alias(tab, n, buf, buf + n, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(thr, buf, sizeof(uint32_t) * n, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(alias, buf + n, sizeof(uint32_t) * n, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(c, e, "line_get_alias");
+    return LINE_OK;
+}
+
+line_status line_sample_debug(line_ctx* c, int K, uint64_t seed, uint32_t domain, uint64_t t0, int64_t count,
+                              int32_t* out) {
+    line_status st = enter(c);
+    if (st) return st;
+    if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_sample_debug: no graph");
+    if (K < 0 || K > kMaxK || count < 0 || (!out && count > 0)) return fail(c, LINE_ERR_ARG, "line_sample_debug: bad arguments");
+    if (count == 0) return LINE_OK;
+    int32_t* buf = nullptr;
+    const size_t bytes = sizeof(int32_t) * (size_t)count * (K + 2);
+    cudaPointerAttributes attr;
+    bool dev_out = cudaPointerGetAttributes(&attr, out) == cudaSuccess && attr.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    if (!dev_out) CK(cudaMalloc(&buf, bytes), "sample scratch");
+    cudaError_t e = sample_records(c->src, c->dst, c->edge_tab, c->n_arcs, c->neg_tab, c->n_nodes, seed, domain, t0,
+                                   count, K, dev_out ? out : buf, c->stream);
+    if (e == cudaSuccess && !dev_out) e = cudaMemcpyAsync(out, buf, bytes, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (buf) cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(c, e, "line_sample_debug");
+    return LINE_OK;
+}
+
+line_status line_init_embeddings(line_ctx* c, int order, int dim, int dtype, uint64_t seed) {
+    line_status st = enter(c);
+    if (st) return st;
+    if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_init_embeddings: no graph");
+    if ((order != 1 && order != 2) || !dim_ok(dim) || (dtype != LINE_DTYPE_F32 && dtype != LINE_DTYPE_BF16))
+        return fail(c, LINE_ERR_ARG, "line_init_embeddings: bad order/dim/dtype");
+    Tables& t = c->tab[order];
+    free_tables(t);
+    const size_t bytes = (size_t)c->n_nodes * dim * elem_size(dtype);
+    CK(cudaMalloc(&t.U, bytes), "table allocation");
+    CK(init_table(t.U, dtype, c->n_nodes, dim, seed, c->stream), "table init");
+    if (order == 2) {
+        CK(cudaMalloc(&t.C, bytes), "table allocation");
+        CK(cudaMemsetAsync(t.C, 0, bytes, c->stream), "table init");
+    }
+    t.dim = dim;
+    t.dtype = dtype;
+    t.ready = true;
+    return LINE_OK;
+}
+
+line_status line_train_steps(line_ctx* c, int order, int dim, int K, const line_lr* lr, uint64_t n_samples,
+                             uint64_t seed, const line_train_opts* opts) {
+    line_status st = enter(c);
+    if (st) return st;
+    if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_train_steps: no graph");
+    if (order != 1 && order != 2) return fail(c, LINE_ERR_ARG, "line_train_steps: order must be 1 or 2");
+    Tables& t = c->tab[order];
+    if (!t.ready || t.dim != dim) return fail(c, LINE_ERR_STATE, "line_train_steps: tables of order %d and dim %d not initialised", order, dim);
+    if (K < 0 || K > kMaxK) return fail(c, LINE_ERR_ARG, "line_train_steps: K out of range");
+    if (!lr || !(lr->lr0 >= 0.0) || (lr->schedule != 0 && lr->schedule != 1) || !(lr->floor_frac >= 0.0))
+        return fail(c, LINE_ERR_ARG, "line_train_steps: bad learning rate");
+    line_train_opts o;
+    line_train_opts_default(&o);
+    if (opts) o = *opts;
+    if (o.batch < 1 || o.batch > (1 << 20)) return fail(c, LINE_ERR_ARG, "line_train_steps: batch out of range");
+    if (!(o.lambda >= 0.0) || !(o.alpha_neg >= 0.0)) return fail(c, LINE_ERR_ARG, "line_train_steps: bad lambda/alpha_neg");
+    if (o.mode != LINE_MODE_BATCHED && o.mode != LINE_MODE_PERSISTENT) return fail(c, LINE_ERR_ARG, "line_train_steps: bad mode");
+    if (o.warps_per_block < 0 || o.warps_per_block > 32) return fail(c, LINE_ERR_ARG, "line_train_steps: bad warps_per_block");
+    if (n_samples == 0) return LINE_OK;
+    if (o.sample_offset + n_samples < o.sample_offset) return fail(c, LINE_ERR_ARG, "line_train_steps: sample range overflows");
+    TrainArgs a{};
+    a.order = order;
+    a.dim = dim;
+    a.K = K;
+    a.dtype = t.dtype;
+    a.n_nodes = c->n_nodes;
+    a.n_arcs = c->n_arcs;
+    a.src = c->src;
+    a.dst = c->dst;
+    a.edge_tab = c->edge_tab;
+    a.neg_tab = c->neg_tab;
+    a.U = t.U;
+    a.C = t.C;
+    a.seed = seed;
+    a.t_begin = o.sample_offset;
+    a.t_end = o.sample_offset + n_samples;
+    a.batch = o.batch;
+    a.lr0 = lr->lr0;
+    a.lr_floor = lr->floor_frac;
+    a.lr_schedule = lr->schedule;
+    a.lr_total = lr->total ? lr->total : o.sample_offset + n_samples;
+    a.lambda = o.lambda;
+    a.alpha_neg = o.alpha_neg;
+    a.mode = o.mode;
+    a.spin_limit = o.spin_limit > 0 ? o.spin_limit : (int64_t)1 << 26;
+    a.chunk_batches = o.chunk_batches;
+    a.warps_per_block = o.warps_per_block;
+    a.timing = o.timing;
+    std::string err;
+    if (o.timing) CK(cudaEventRecord(c->ev0, c->stream), "event");
+    cudaError_t e = train_run(a, c->ws, c->status, &c->times, c->stream, &err);
+    if (e != cudaSuccess) {
+        if (!err.empty()) return fail(c, e == cudaErrorMemoryAllocation ? LINE_ERR_OOM : LINE_ERR_ARG, "line_train_steps: %s", err.c_str());
+        return cuda_fail(c, e, "line_train_steps");
+    }
+    if (o.timing) CK(cudaEventRecord(c->ev1, c->stream), "event");
+    st = check_status(c, "line_train_steps");
+    if (st) return st;
+    if (o.timing) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        c->total_ms += ms;
+        c->total_samples += n_samples;
+    }
+    return LINE_OK;
+}
+
+line_status line_get_embeddings(line_ctx* c, int order, int which, void* dst, int dst_dtype) {
+    line_status st = enter(c);
+    if (st) return st;
+    if (order != 1 && order != 2) return fail(c, LINE_ERR_ARG, "line_get_embeddings: bad order");
+    Tables& t = c->tab[order];
+    if (!t.ready) return fail(c, LINE_ERR_STATE, "line_get_embeddings: no tables of order %d", order);
+    if (!dst || (which != LINE_WHICH_U && which != LINE_WHICH_C) || (which == LINE_WHICH_C && order != 2))
+        return fail(c, LINE_ERR_ARG, "line_get_embeddings: bad arguments");
+    if (dst_dtype != LINE_DTYPE_F32 && !(dst_dtype == LINE_DTYPE_BF16 && t.dtype == LINE_DTYPE_BF16))
+        return fail(c, LINE_ERR_ARG, "line_get_embeddings: unsupported dtype conversion");
+    const void* srcp = which == LINE_WHICH_U ? t.U : t.C;
+    const size_t elems = (size_t)c->n_nodes * t.dim;
+    if (dst_dtype == t.dtype) {
+        CK(cudaMemcpyAsync(dst, srcp, elems * elem_size(t.dtype), cudaMemcpyDefault, c->stream), "embedding copy");
+    } else {
+        void* buf = nullptr;
+        CK(cudaMalloc(&buf, elems * 4), "conversion scratch");
+        cudaError_t e = convert_rows(srcp, t.dtype, buf, LINE_DTYPE_F32, nullptr, c->n_nodes, t.dim, c->n_nodes,
+                                     c->status, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dst, buf, elems * 4, cudaMemcpyDefault, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        cudaFree(buf);
+        if (e != cudaSuccess) return cuda_fail(c, e, "line_get_embeddings");
+    }
+    CK(cudaStreamSynchronize(c->stream), "line_get_embeddings");
+    return LINE_OK;
+}
+
+line_status line_set_embeddings(line_ctx* c, int order, int which, const void* src, int src_dtype,
+                                const int32_t* rows, int64_t n_rows) {
+    line_status st = enter(c);
+    if (st) return st;
+    if (order != 1 && order != 2) return fail(c, LINE_ERR_ARG, "line_set_embeddings: bad order");
+    Tables& t = c->tab[order];
+    if (!t.ready) return fail(c, LINE_ERR_STATE, "line_set_embeddings: no tables of order %d", order);
+    if ((which != LINE_WHICH_U && which != LINE_WHICH_C) || (which == LINE_WHICH_C && order != 2) ||
+        (src_dtype != LINE_DTYPE_F32 && src_dtype != LINE_DTYPE_BF16) || n_rows < 0 || (n_rows > 0 && !src) ||
+        (!rows && n_rows > c->n_nodes))
+        return fail(c, LINE_ERR_ARG, "line_set_embeddings: bad arguments");
+    if (n_rows == 0) return LINE_OK;
+    void* dstp = which == LINE_WHICH_U ? t.U : t.C;
+    const size_t in_bytes = (size_t)n_rows * t.dim * elem_size(src_dtype);
+    void* sbuf = nullptr;
+    int32_t* rbuf = nullptr;
+    cudaError_t e = cudaMalloc(&sbuf, in_bytes);
+    if (e == cudaSuccess && rows) e = cudaMalloc(&rbuf, sizeof(int32_t) * n_rows);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(sbuf, src, in_bytes, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && rows) e = cudaMemcpyAsync(rbuf, rows, sizeof(int32_t) * n_rows, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess)
+        e = convert_rows(sbuf, src_dtype, dstp, t.dtype, rbuf, n_rows, t.dim, c->n_nodes, c->status, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (sbuf) cudaFree(sbuf);
+    if (rbuf) cudaFree(rbuf);
+    if (e != cudaSuccess) return cuda_fail(c, e, "line_set_embeddings");
+    return check_status(c, "line_set_embeddings");
+}
+
+line_status line_eval_loss(line_ctx* c, int order, int K, uint64_t seed, int64_t m, double* out_host) {
+    line_status st = enter(c);
+    if (st) return st;
+    if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_eval_loss: no graph");
+    if (order != 1 && order != 2) return fail(c, LINE_ERR_ARG, "line_eval_loss: bad order");
+    Tables& t = c->tab[order];
+    if (!t.ready) return fail(c, LINE_ERR_STATE, "line_eval_loss: no tables of order %d", order);
+    if (K < 0 || K > kMaxK || m < 0 || !out_host) return fail(c, LINE_ERR_ARG, "line_eval_loss: bad arguments");
+    if (m == 0) {
+        *out_host = 0.0;
+        return LINE_OK;
+    }
+    double* terms = nullptr;
+    void* tmp = nullptr;
+    cudaError_t e = cudaMalloc(&terms, sizeof(double) * m);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, fixed_sum_tmp_bytes(m));
+    if (e == cudaSuccess)
+        e = eval_loss_terms(t.U, order == 2 ? t.C : t.U, t.dtype, t.dim, K, c->src, c->dst, c->edge_tab, c->n_arcs,
+                            c->neg_tab, c->n_nodes, seed, m, terms, c->stream);
+    if (e == cudaSuccess) e = fixed_sum_f64(terms, m, (double*)tmp, c->dscratch, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out_host, c->dscratch, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (terms) cudaFree(terms);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "line_eval_loss");
+    return LINE_OK;
+}
+
+line_status line_get_stats(line_ctx* c, line_stats* out) {
+    if (!c || !out) return LINE_ERR_ARG;
+    out->update_launches = c->times.update_launches;
+    out->update_ms = c->times.update_ms;
+    out->update_samples = c->times.update_samples;
+    out->prepass_launches = c->times.prepass_launches;
+    out->prepass_ms = c->times.prepass_ms;
+    out->total_ms = c->total_ms;
+    out->total_samples = c->total_samples;
+    return LINE_OK;
+}
+
+line_status line_reset_stats(line_ctx* c) {
+    if (!c) return LINE_ERR_ARG;
+    c->times = TrainTimes{};
+    c->total_ms = 0;
+    c->total_samples = 0;
+    return LINE_OK;
+}
+
+line_status line_synchronize(line_ctx* c) {
+    line_status st = enter(c);
+    if (st) return st;
+    CK(cudaStreamSynchronize(c->stream), "line_synchronize");
+    return LINE_OK;
+}
+
+line_status line_debug_wait_timeout(line_ctx* c, int64_t spin_limit) {
+    line_status st = enter(c);
+    if (st) return st;
+    if (spin_limit < 1 || spin_limit > (1ll << 24)) return fail(c, LINE_ERR_ARG, "line_debug_wait_timeout: spin_limit out of range");
+    CK(debug_wait(c->flag, spin_limit, c->status, c->stream), "debug wait");
+    return check_status(c, "line_debug_wait_timeout", /*timeout_sticky=*/false);
+}
+
+}  // extern "C"

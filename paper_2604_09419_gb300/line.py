@@ -1,0 +1,201 @@
+"""Python binding of the LINE C ABI (``include/line.h``).
+
+Argument marshalling only: every function here forwards to the entry point of
+the same name in ``_build/libline.so``.  Buffers may be CUDA tensors (device
+pointers) or NumPy arrays / CPU tensors (host pointers); the library copies
+with unified addressing.  There is no fallback: if the shared library is
+missing or cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libline.so")
+
+LINE_OK, LINE_ERR_ARG, LINE_ERR_OOM, LINE_ERR_CUDA, LINE_ERR_TIMEOUT, LINE_ERR_STATE, LINE_ERR_VALIDATE = (
+    0, -1, -2, -3, -4, -5, -6)
+DTYPE_F32, DTYPE_BF16 = 0, 1
+TABLE_EDGE, TABLE_NEG = 0, 1
+WHICH_U, WHICH_C = 0, 1
+MODE_BATCHED, MODE_PERSISTENT = 0, 1
+
+
+class GraphDesc(ctypes.Structure):
+    _fields_ = [("n_nodes", ctypes.c_int64), ("n_arcs", ctypes.c_int64), ("src", ctypes.c_void_p),
+                ("dst", ctypes.c_void_p), ("w", ctypes.c_void_p)]
+
+
+class LR(ctypes.Structure):
+    _fields_ = [("lr0", ctypes.c_double), ("schedule", ctypes.c_int), ("floor_frac", ctypes.c_double),
+                ("total", ctypes.c_uint64)]
+
+
+class TrainOpts(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_int64), ("lambda_", ctypes.c_double), ("alpha_neg", ctypes.c_double),
+                ("sample_offset", ctypes.c_uint64), ("mode", ctypes.c_int), ("spin_limit", ctypes.c_int64),
+                ("chunk_batches", ctypes.c_int), ("warps_per_block", ctypes.c_int), ("timing", ctypes.c_int)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("update_launches", ctypes.c_int64), ("update_ms", ctypes.c_double),
+                ("update_samples", ctypes.c_uint64), ("prepass_launches", ctypes.c_int64),
+                ("prepass_ms", ctypes.c_double), ("total_ms", ctypes.c_double), ("total_samples", ctypes.c_uint64)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libline.so not built ({LIB_PATH}); run __graft_entry__.build()")
+    L = ctypes.CDLL(LIB_PATH)
+    vp, i64, u64, u32, i32, dbl = (ctypes.c_void_p, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint32,
+                                   ctypes.c_int, ctypes.c_double)
+    sigs = {
+        "line_train_opts_default": (None, [ctypes.POINTER(TrainOpts)]),
+        "line_status_string": (ctypes.c_char_p, [i32]),
+        "line_create": (i32, [ctypes.POINTER(vp), i32, vp]),
+        "line_destroy": (None, [vp]),
+        "line_last_error": (ctypes.c_char_p, [vp]),
+        "line_build_alias": (i32, [vp, ctypes.POINTER(GraphDesc)]),
+        "line_get_graph_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+        "line_get_alias": (i32, [vp, i32, vp, vp]),
+        "line_sample_debug": (i32, [vp, i32, u64, u32, u64, i64, vp]),
+        "line_init_embeddings": (i32, [vp, i32, i32, i32, u64]),
+        "line_train_steps": (i32, [vp, i32, i32, i32, ctypes.POINTER(LR), u64, u64, ctypes.POINTER(TrainOpts)]),
+        "line_get_embeddings": (i32, [vp, i32, i32, vp, i32]),
+        "line_set_embeddings": (i32, [vp, i32, i32, vp, i32, vp, i64]),
+        "line_eval_loss": (i32, [vp, i32, i32, u64, i64, ctypes.POINTER(dbl)]),
+        "line_get_stats": (i32, [vp, ctypes.POINTER(Stats)]),
+        "line_reset_stats": (i32, [vp]),
+        "line_synchronize": (i32, [vp]),
+        "line_debug_wait_timeout": (i32, [vp, i64]),
+    }
+    for name, (res, args) in sigs.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+EXPORTED = ("line_train_opts_default", "line_status_string", "line_create", "line_destroy", "line_last_error",
+            "line_build_alias", "line_get_graph_info", "line_get_alias", "line_sample_debug",
+            "line_init_embeddings", "line_train_steps", "line_get_embeddings", "line_set_embeddings",
+            "line_eval_loss", "line_get_stats", "line_reset_stats", "line_synchronize", "line_debug_wait_timeout")
+
+
+class LineError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{lib.line_status_string(status).decode()} ({status}): {msg}")
+        self.status = status
+
+
+def ptr(x) -> int | None:
+    """Address of a CUDA tensor, CPU tensor or NumPy array (None for None)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags.c_contiguous
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        assert x.is_contiguous()
+        return x.data_ptr()
+    raise TypeError(type(x))
+
+
+def train_opts_default() -> TrainOpts:
+    o = TrainOpts()
+    lib.line_train_opts_default(ctypes.byref(o))
+    return o
+
+
+class Context:
+    """Owns one ``line_ctx``; methods mirror the C entry points."""
+
+    def __init__(self, device: int = 0, stream: int | None = None):
+        h = ctypes.c_void_p()
+        st = lib.line_create(ctypes.byref(h), device, stream)
+        if st != LINE_OK:
+            raise LineError(st, "line_create failed")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib.line_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _ck(self, st):
+        if st != LINE_OK:
+            raise LineError(st, lib.line_last_error(self.h).decode())
+        return st
+
+    def last_error(self) -> str:
+        return lib.line_last_error(self.h).decode()
+
+    def build_alias(self, n_nodes, src, dst, w=None):
+        g = GraphDesc(n_nodes, int(src.shape[0]), ptr(src), ptr(dst), ptr(w))
+        return self._ck(lib.line_build_alias(self.h, ctypes.byref(g)))
+
+    def graph_info(self):
+        n, m = ctypes.c_int64(), ctypes.c_int64()
+        self._ck(lib.line_get_graph_info(self.h, ctypes.byref(n), ctypes.byref(m)))
+        return n.value, m.value
+
+    def get_alias(self, table, thr, alias):
+        return self._ck(lib.line_get_alias(self.h, table, ptr(thr), ptr(alias)))
+
+    def sample_debug(self, K, seed, domain, t0, count, out):
+        return self._ck(lib.line_sample_debug(self.h, K, seed, domain, t0, count, ptr(out)))
+
+    def init_embeddings(self, order, dim, dtype=DTYPE_F32, seed=0):
+        return self._ck(lib.line_init_embeddings(self.h, order, dim, dtype, seed))
+
+    def train_steps(self, order, dim, K, n_samples, seed, *, lr0=0.025, schedule=1, floor_frac=1e-4, total=0,
+                    opts: TrainOpts | None = None, check=True, **kw):
+        lr = LR(lr0, schedule, floor_frac, total)
+        o = opts if opts is not None else train_opts_default()
+        for k, v in kw.items():
+            setattr(o, "lambda_" if k == "lam" else k, v)
+        st = lib.line_train_steps(self.h, order, dim, K, ctypes.byref(lr), n_samples, seed, ctypes.byref(o))
+        return self._ck(st) if check else st
+
+    def get_embeddings(self, order, which, dst, dtype=DTYPE_F32):
+        return self._ck(lib.line_get_embeddings(self.h, order, which, ptr(dst), dtype))
+
+    def set_embeddings(self, order, which, src, dtype=DTYPE_F32, rows=None):
+        n = int(src.shape[0]) if rows is None else int(rows.shape[0])
+        return self._ck(lib.line_set_embeddings(self.h, order, which, ptr(src), dtype, ptr(rows), n))
+
+    def eval_loss(self, order, K, seed, m) -> float:
+        out = ctypes.c_double()
+        self._ck(lib.line_eval_loss(self.h, order, K, seed, m, ctypes.byref(out)))
+        return out.value
+
+    def stats(self) -> Stats:
+        s = Stats()
+        self._ck(lib.line_get_stats(self.h, ctypes.byref(s)))
+        return s
+
+    def reset_stats(self):
+        return self._ck(lib.line_reset_stats(self.h))
+
+    def synchronize(self):
+        return self._ck(lib.line_synchronize(self.h))
+
+    def debug_wait_timeout(self, spin_limit) -> int:
+        return lib.line_debug_wait_timeout(self.h, spin_limit)
+
+
+def table_numpy(ctx: Context, n_nodes: int, dim: int, order: int, which: int) -> np.ndarray:
+    """Copy a table into a new host FP32 array (through the C ABI)."""
+    out = np.empty((n_nodes, dim), np.float32)
+    ctx.get_embeddings(order, which, out, DTYPE_F32)
+    return out

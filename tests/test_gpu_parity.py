@@ -1,0 +1,177 @@
+"""GPU path vs the FP64 oracle, through the C ABI.
+
+* alias tables bit-exact (Eq. 1 and Algorithm 3's weight-proportional pick);
+* sampled indices bit-exact (Algorithm 1's positive + K negatives per sample);
+* FP32 embeddings within 1e-5 max-abs of the FP64 oracle (minibatch LINE,
+  Eq. 2-4), across dims, orders, batch sizes, K, lambda and alpha_neg;
+* bitwise determinism, resume equivalence, schedule equivalence;
+* the loss of the GPU tables against the oracle's loss of the same tables.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from tests import gpu_util as G
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5  # FP32 GPU vs FP64 oracle, max abs (the target's stated bound)
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = G.context()
+    yield c
+    c.close()
+
+
+@pytest.mark.parametrize("name", ["tiny", "rmat14", "dchung", "two", "isolated"])
+def test_alias_tables_bit_exact(ctx, name):
+    from paper_2604_09419_gb300 import line as L
+    g = G.graph(name)
+    T = G.oracle_tables(name)
+    G.upload(ctx, g)
+    thr, alias = G.gpu_alias(ctx, g, L.TABLE_EDGE)
+    assert np.array_equal(thr, T.thr_e) and np.array_equal(alias, T.alias_e)
+    thr, alias = G.gpu_alias(ctx, g, L.TABLE_NEG)
+    assert np.array_equal(thr, T.thr_n) and np.array_equal(alias, T.alias_n)
+
+
+def test_alias_host_buffers(ctx):
+    from paper_2604_09419_gb300 import line as L
+    g = G.graph("rmat14")
+    T = G.oracle_tables("rmat14")
+    G.upload(ctx, g, host=True)
+    thr, alias = G.gpu_alias(ctx, g, L.TABLE_NEG)
+    assert np.array_equal(thr, T.thr_n) and np.array_equal(alias, T.alias_n)
+
+
+@pytest.mark.parametrize("name", ["tiny", "dchung"])
+def test_samples_bit_exact(ctx, name):
+    g = G.graph(name)
+    T = G.oracle_tables(name)
+    G.upload(ctx, g)
+    # a whole tiny run (100,000 samples, K = 5), and windows with t_hi != 0
+    for t0, count, K, domain in [(0, 100_000, 5, 0), ((3 << 32) - 17, 5000, 5, 0), (12345, 3000, 0, 3),
+                                 (99, 2000, 32, 0)]:
+        got = G.gpu_samples(ctx, K, 0xABCDEF12345, t0, count, domain)
+        want = O.sample(T, 0xABCDEF12345, t0, count, K, domain)
+        assert np.array_equal(got, want), (t0, count, K)
+
+
+def _train_both(ctx, name, order, dim, K, n, B, seed=5, init_seed=1, check_tol=True, **kw):
+    from paper_2604_09419_gb300 import line as L
+    g = G.graph(name)
+    G.upload(ctx, g)
+    ctx.init_embeddings(order, dim, L.DTYPE_F32, seed=init_seed)
+    okw = {k: v for k, v in kw.items() if k in ("mode", "chunk_batches", "warps_per_block")}
+    lam = kw.get("lam", 0.0)
+    alpha = kw.get("alpha_neg", 1.0)
+    ctx.train_steps(order, dim, K, n, seed, batch=B, lam=lam, alpha_neg=alpha, **okw)
+    U, C = G.tables(ctx, g, order, dim)
+    Uo, Co = G.oracle_run(name, order, dim, K, n, seed, B, init_seed, lam=lam, alpha_neg=alpha)
+    err = np.abs(U - Uo).max()
+    if order == 2:
+        err = max(err, np.abs(C - Co).max())
+    if check_tol:
+        assert err <= TOL, err
+    return U, C, err
+
+
+@pytest.mark.parametrize("order", [2, 1])
+def test_tiny_config_parity(ctx, order):
+    """Tiny Chung-Lu, d=16, K=5, 100,000 samples, B=256 (390 full batches + 160), lr 0.025 linear."""
+    _, _, err = _train_both(ctx, "tiny", order, 16, 5, 100_000, 256)
+    print(f"tiny order {order}: max |GPU - oracle| = {err:.3e}")
+
+
+@pytest.mark.parametrize("dim", [32, 64, 128, 256])
+def test_dims(ctx, dim):
+    _train_both(ctx, "tiny", 2, dim, 5, 20_000, 128)
+
+
+@pytest.mark.parametrize("B,n,K", [(1, 300, 5), (7, 1000, 3), (5000, 3000, 5), (256, 10_000, 0), (64, 5000, 1),
+                                   (100, 4000, 32)])
+def test_batch_and_k_edge_cases(ctx, B, n, K):
+    _train_both(ctx, "tiny", 2, 16, K, n, B)
+
+
+def test_decay_and_alpha(ctx):
+    _train_both(ctx, "tiny", 2, 32, 5, 30_000, 256, lam=1e-3, alpha_neg=0.5)
+    _train_both(ctx, "tiny", 1, 32, 5, 30_000, 256, lam=1e-3, alpha_neg=0.5)
+
+
+def test_weighted_directed_graph(ctx):
+    _train_both(ctx, "dchung", 2, 64, 5, 50_000, 512)
+
+
+def test_ragged_rmat(ctx):
+    """R-MAT scale 14: hub rows appear many times per batch (long segments)."""
+    _train_both(ctx, "rmat14", 2, 128, 5, 40_000, 4096)
+    _train_both(ctx, "rmat14", 1, 128, 5, 40_000, 4096)
+
+
+def _run(ctx, g, order, dim, K, n, B, seed=5, **kw):
+    from paper_2604_09419_gb300 import line as L
+    ctx.init_embeddings(order, dim, L.DTYPE_F32, seed=1)
+    ctx.train_steps(order, dim, K, n, seed, batch=B, **kw)
+    return G.tables(ctx, g, order, dim)
+
+
+def test_determinism_and_schedules(ctx):
+    g = G.graph("rmat14")
+    G.upload(ctx, g)
+    a = _run(ctx, g, 2, 64, 5, 60_000, 1024)
+    b = _run(ctx, g, 2, 64, 5, 60_000, 1024)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    for cb in (1, 3, 7):
+        c = _run(ctx, g, 2, 64, 5, 60_000, 1024, chunk_batches=cb)
+        assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1]), cb
+    for wpb in (1, 4, 16):
+        c = _run(ctx, g, 2, 64, 5, 60_000, 1024, warps_per_block=wpb)
+        assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1]), wpb
+
+
+def test_resume_split_is_bitwise(ctx):
+    from paper_2604_09419_gb300 import line as L
+    g = G.graph("tiny")
+    G.upload(ctx, g)
+    n, B = 50_000, 256
+    full = _run(ctx, g, 2, 32, 5, n, B)
+    ctx.init_embeddings(2, 32, L.DTYPE_F32, seed=1)
+    split = 256 * 77
+    ctx.train_steps(2, 32, 5, split, 5, batch=B, total=n)
+    ctx.train_steps(2, 32, 5, n - split, 5, batch=B, total=n, sample_offset=split)
+    U, C = G.tables(ctx, g, 2, 32)
+    assert np.array_equal(U, full[0]) and np.array_equal(C, full[1])
+
+
+def test_loss_matches_oracle_on_gpu_tables(ctx):
+    g = G.graph("tiny")
+    G.upload(ctx, g)
+    U, C = _run(ctx, g, 2, 16, 5, 50_000, 256)
+    T = G.oracle_tables("tiny")
+    for m in (1, 1000, 65_537):
+        got = ctx.eval_loss(2, 5, 9, m)
+        want = O.eval_loss(T, U.astype(np.float64), C.astype(np.float64), order=2, K=5, seed=9, m=m)
+        assert abs(got - want) <= 1e-9 * abs(want), (m, got, want)
+    U1, _ = _run(ctx, g, 1, 16, 5, 20_000, 256)
+    got = ctx.eval_loss(1, 5, 9, 4000)
+    want = O.eval_loss(T, U1.astype(np.float64), None, order=1, K=5, seed=9, m=4000)
+    assert abs(got - want) <= 1e-9 * abs(want)
+
+
+def test_untouched_rows_and_zero_lr(ctx):
+    g = G.graph("isolated")
+    G.upload(ctx, g)
+    from paper_2604_09419_gb300 import line as L
+    ctx.init_embeddings(2, 16, L.DTYPE_F32, seed=3)
+    U0, C0 = G.tables(ctx, g, 2, 16)
+    ctx.train_steps(2, 16, 5, 5000, 1, batch=64, lr0=0.0)
+    U1, C1 = G.tables(ctx, g, 2, 16)
+    assert np.array_equal(U0, U1) and np.array_equal(C0, C1)
+    ctx.train_steps(2, 16, 5, 5000, 1, batch=64)
+    U2, C2 = G.tables(ctx, g, 2, 16)
+    # nodes 41.. have degree 0: never drawn, rows unchanged
+    assert np.array_equal(U2[41:], U0[41:]) and not C2[41:].any()
+    assert not np.array_equal(U2[:41], U0[:41])
