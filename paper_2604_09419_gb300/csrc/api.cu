@@ -360,7 +360,7 @@ line_status line_train_steps(line_ctx* c, int order, int dim, int K, const line_
     a.lambda = o.lambda;
     a.alpha_neg = o.alpha_neg;
     a.mode = o.mode;
-    a.spin_limit = o.spin_limit > 0 ? o.spin_limit : (int64_t)1 << 26;
+    a.spin_limit = o.spin_limit > 0 ? o.spin_limit : (int64_t)1 << 22;  // ~1 s of polling
     a.chunk_batches = o.chunk_batches;
     a.warps_per_block = o.warps_per_block;
     a.timing = o.timing;

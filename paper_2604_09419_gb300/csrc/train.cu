@@ -122,6 +122,10 @@ __device__ __forceinline__ float group_sum(float v) {
     return v;
 }
 
+// Sort item value: (sample within the chunk) << kSlotBits | slot.
+constexpr uint32_t kSlotBits = 6;
+constexpr uint32_t kSlotMask = (1u << kSlotBits) - 1u;
+
 // ---------------------------------------------------------------------------
 // Kernel parameters shared by the data-phase kernels.
 // ---------------------------------------------------------------------------
@@ -141,9 +145,7 @@ struct DataParams {
     int64_t batch;
     int n_batches;
     uint64_t seed;
-    double lr0, lr_floor;
-    uint64_t lr_total;
-    int lr_schedule;
+    const float* eta;  // [n_batches] learning rate of each batch (FP32)
     float lambda, alpha_neg;
     uint32_t* status;
     // persistent schedule
@@ -157,37 +159,52 @@ struct DataParams {
     uint32_t* abort_word;
 };
 
-__device__ __forceinline__ float batch_eta(const DataParams& p, uint64_t t0) {
-    double f = 1.0;
-    if (p.lr_schedule == 1) {
-        f = 1.0 - (double)t0 / (double)p.lr_total;
-        if (f < p.lr_floor) f = p.lr_floor;
-    }
-    return (float)(p.lr0 * f);
-}
-
 // ---------------------------------------------------------------------------
 // Per-sample work: gather, dots, gradient scalars, slab contributions.
-// ctx_stage: this lane group's shared staging area, (K+1) x 32 lanes x E.
+// ctx_stage: this warp's shared staging area, (K+1) x 32 lanes x E.
+// The record's ids are read by the group's lanes in one go and broadcast, and
+// the context rows are loaded CH at a time so their loads are in flight
+// together.
 // ---------------------------------------------------------------------------
+template <int L>
+__device__ __forceinline__ uint32_t group_mask(int grp) {
+    return L == 32 ? 0xFFFFFFFFu : (((1u << L) - 1u) << (grp * L));
+}
+
 template <int D, int DT>
 __device__ __forceinline__ void sample_item(const DataParams& p, int64_t s_local, int lig, int lane, bool active,
                                             float eta, float* ctx_stage) {
     using G = Geom<D, DT>;
+    constexpr int CH = G::E <= 4 ? 4 : 2;  // context rows in flight per lane
     const int R = p.K + 2;
     const int32_t* rec = p.rec + (active ? s_local : 0) * R;
-    const int32_t u = active ? rec[0] : 0;
+    const uint32_t gm = group_mask<G::L>(lane / G::L);
+    // lane l of the group holds rec[l] (and rec[l + L], ... for small groups)
+    const int32_t r0 = (active && lig < R) ? rec[lig] : 0;
+    const int32_t u = __shfl_sync(gm, r0, 0, G::L);
     float xu[G::E];
     load_row<D, DT>(p.U, u, lig, xu);
-    // stage the K+1 context rows (positive first) in shared memory
-#pragma unroll 4
-    for (int j = 0; j <= p.K; ++j) {
-        const int32_t y = active ? rec[1 + j] : 0;
-        float c[G::E];
-        load_row<D, DT>(p.C, y, lig, c);
-        float4* st = reinterpret_cast<float4*>(ctx_stage + (j * 32 + lane) * G::E);
+    for (int j0 = 0; j0 <= p.K; j0 += CH) {
+        float c[CH][G::E];
 #pragma unroll
-        for (int q = 0; q < G::E / 4; ++q) st[q] = make_float4(c[4 * q], c[4 * q + 1], c[4 * q + 2], c[4 * q + 3]);
+        for (int jj = 0; jj < CH; ++jj) {
+            const int j = j0 + jj;
+            const int idx = 1 + j;  // record entry of context row j
+            int32_t y = __shfl_sync(gm, r0, idx % G::L, G::L);
+            if (idx >= G::L) y = (active && j <= p.K) ? rec[idx] : 0;
+            if (j > p.K) y = 0;
+            if (j <= p.K) load_row<D, DT>(p.C, y, lig, c[jj]);
+        }
+#pragma unroll
+        for (int jj = 0; jj < CH; ++jj) {
+            const int j = j0 + jj;
+            if (j <= p.K) {
+                float4* st = reinterpret_cast<float4*>(ctx_stage + (j * 32 + lane) * G::E);
+#pragma unroll
+                for (int q = 0; q < G::E / 4; ++q)
+                    st[q] = make_float4(c[jj][4 * q], c[jj][4 * q + 1], c[jj][4 * q + 2], c[jj][4 * q + 3]);
+            }
+        }
     }
     float du[G::E];
 #pragma unroll
@@ -228,50 +245,76 @@ __device__ __forceinline__ void sample_item(const DataParams& p, int64_t s_local
 
 // ---------------------------------------------------------------------------
 // Per-segment work: fixed-order sum of the slab entries of one (batch, row)
-// and the write-back.
+// and the write-back.  The group's lanes read the entries' values (and, in
+// the persistent schedule, wait on their samples) in parallel, L at a time;
+// the slab loads of PF entries are then in flight together and are added in
+// sorted order.  Returns false when a bounded wait ran out.
 // ---------------------------------------------------------------------------
 template <int D, int DT>
-__device__ __forceinline__ void segment_item(const DataParams& p, uint32_t seg, int lig, float eta, uint64_t t0,
-                                             bool wait_samples) {
+__device__ __forceinline__ bool segment_item(const DataParams& p, uint32_t seg, int lig, int lane, bool active,
+                                             float eta, uint64_t t0, bool wait_samples) {
     using G = Geom<D, DT>;
-    const uint32_t begin = p.seg_start[seg], end = p.seg_start[seg + 1];
-    const uint32_t key = (uint32_t)(p.items[begin] >> 32);
-    const uint32_t rowid = key & ((1u << p.row_bits) - 1u);
-    const bool is_c = p.order == 2 && rowid >= (uint32_t)p.n_nodes;
-    void* table = is_c ? p.C : p.U;
-    const int64_t row = is_c ? (int64_t)rowid - p.n_nodes : (int64_t)rowid;
+    constexpr int PF = G::E <= 4 ? 4 : 2;
+    const uint32_t gm = group_mask<G::L>(lane / G::L);
+    const uint32_t begin = active ? p.seg_start[seg] : 0u, end = active ? p.seg_start[seg + 1] : 0u;
     const int R = p.K + 2;
     float acc[G::E];
 #pragma unroll
     for (int e = 0; e < G::E; ++e) acc[e] = 0.0f;
     int cnt = 0;
-    for (uint32_t i = begin; i < end; ++i) {
-        const uint32_t v = (uint32_t)p.items[i];
-        const uint32_t slot = v % (uint32_t)R;
-        if (wait_samples) {
-            if (!wait_geq(p.sample_done + v / (uint32_t)R, p.gen, p.spin_limit, p.abort_word)) {
-                atomicOr(p.status, DEV_ERR_TIMEOUT);
-                atomicExch(p.abort_word, 1u);
-                return;
+    uint32_t key = 0;
+    bool ok = true;
+    for (uint32_t base = begin; base < end; base += G::L) {
+        const uint32_t i = base + (uint32_t)lig;
+        const bool have = i < end;
+        const uint64_t item = have ? p.items[i] : 0ull;
+        if (base == begin) key = __shfl_sync(gm, (uint32_t)(item >> 32), 0, G::L);
+        const uint32_t v = (uint32_t)item;
+        if (wait_samples && have && ok)
+            ok = wait_geq(p.sample_done + (v >> kSlotBits), p.gen, p.spin_limit, p.abort_word);
+        const int m = (int)min((uint32_t)G::L, end - base);
+        __syncwarp(gm);
+        for (int k0 = 0; k0 < m; k0 += PF) {
+            float4 buf[PF][G::E / 4];
+#pragma unroll
+            for (int kk = 0; kk < PF; ++kk) {
+                const uint32_t vk = __shfl_sync(gm, v, (k0 + kk) % G::L, G::L);
+                if (k0 + kk < m) {
+                    const uint32_t slot = vk & kSlotMask;
+                    const int64_t entry = (int64_t)(vk >> kSlotBits) * R + slot;
+                    const float4* src = reinterpret_cast<const float4*>(p.slab + entry * D + lig * G::E);
+#pragma unroll
+                    for (int q = 0; q < G::E / 4; ++q) buf[kk][q] = ld_cg(src + q);
+                    cnt += slot == 0 ? p.K + 1 : 1;
+                }
+            }
+#pragma unroll
+            for (int kk = 0; kk < PF; ++kk) {
+                if (k0 + kk < m) {
+#pragma unroll
+                    for (int q = 0; q < G::E / 4; ++q) {
+                        acc[4 * q] += buf[kk][q].x;
+                        acc[4 * q + 1] += buf[kk][q].y;
+                        acc[4 * q + 2] += buf[kk][q].z;
+                        acc[4 * q + 3] += buf[kk][q].w;
+                    }
+                }
             }
         }
-        cnt += slot == 0 ? p.K + 1 : 1;
-        const float4* src = reinterpret_cast<const float4*>(p.slab + (int64_t)v * D + lig * G::E);
-#pragma unroll
-        for (int q = 0; q < G::E / 4; ++q) {
-            const float4 a = ld_cg(src + q);
-            acc[4 * q] += a.x;
-            acc[4 * q + 1] += a.y;
-            acc[4 * q + 2] += a.z;
-            acc[4 * q + 3] += a.w;
-        }
     }
+    if (wait_samples && !__all_sync(gm, ok)) return false;
+    if (!active) return true;
+    const uint32_t rowid = key & ((1u << p.row_bits) - 1u);
+    const bool is_c = p.order == 2 && rowid >= (uint32_t)p.n_nodes;
+    void* table = is_c ? p.C : p.U;
+    const int64_t row = is_c ? (int64_t)rowid - p.n_nodes : (int64_t)rowid;
     float x[G::E];
     load_row<D, DT>(table, row, lig, x);
     const float decay = (float)cnt * (eta * p.lambda);
 #pragma unroll
     for (int e = 0; e < G::E; ++e) x[e] = fmaf(-decay, x[e], x[e]) + acc[e];
     store_row<D, DT>(table, row, lig, x, p.seed, t0, is_c ? 1u : 0u);
+    return true;
 }
 
 // ---------------------------------------------------------------------------
@@ -290,7 +333,7 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_gather(DataParams p, int b) 
     const int64_t s_begin = (int64_t)b * p.batch;
     const int64_t s_end = min(s_begin + p.batch, p.chunk_samples);
     const int64_t s_local = s_begin + ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * G::GPW + grp;
-    const float eta = batch_eta(p, p.t_chunk + (uint64_t)s_begin);
+    const float eta = p.eta[b];
     float* stage = smem + (size_t)warp * (p.K + 1) * 32 * G::E;
     sample_item<D, DT>(p, s_local, lig, lane, s_local < s_end, eta, stage);
 }
@@ -303,11 +346,167 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_apply(DataParams p, int b) {
     const uint32_t seg_begin = p.batch_seg[b], seg_end = p.batch_seg[b + 1];
     const int64_t s_begin = (int64_t)b * p.batch;
     const uint64_t t0 = p.t_chunk + (uint64_t)s_begin;
-    const float eta = batch_eta(p, t0);
+    const float eta = p.eta[b];
     const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 5) * G::GPW;
-    for (int64_t sg = seg_begin + ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * G::GPW + grp; sg < seg_end;
-         sg += groups)
-        segment_item<D, DT>(p, (uint32_t)sg, lig, eta, t0, false);
+    // every group of the warp runs the same number of iterations (shuffles)
+    const int64_t first = seg_begin + ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * G::GPW;
+    for (int64_t sg0 = first; sg0 < seg_end; sg0 += groups) {
+        const int64_t sg = sg0 + grp;
+        segment_item<D, DT>(p, (uint32_t)sg, lig, lane, sg < seg_end, eta, t0, false);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Persistent schedule: one cooperative launch per chunk.  Work items in a
+// fixed order - batch 0's sample items, batch 0's segment items, batch 1's
+// sample items, ... - are dealt round robin to the warps; every warp walks
+// its items in increasing order.  An item waits only on items earlier in that
+// order, so the earliest unfinished item can always run (all warps are
+// resident): the schedule cannot deadlock, and every wait is bounded anyway.
+//   sample item (batch b): rows it reads must hold their values after the
+//     last batch that touched them: for a row of batch b-1 it waits on that
+//     segment's flag; batches b-2 and b-3 must be fully applied (by
+//     induction this covers every earlier batch).
+//   segment item (batch b): waits for the sample items of its entries (they
+//     wrote the slab entries and are the only readers of the row's
+//     batch-start value).
+// ---------------------------------------------------------------------------
+constexpr int kPersistThreads = 256;   // 8 warps per block
+constexpr int kPersistMinBlocks = 3;   // <= 85 registers: 24 warps per SM
+
+__device__ __forceinline__ bool batch_applied_ok(const DataParams& p, int bb) {
+    if (bb < 0) return true;
+    const uint32_t need = p.batch_seg[bb + 1] - p.batch_seg[bb];
+    return wait_geq(p.batch_applied + bb, need, p.spin_limit, p.abort_word);
+}
+
+__device__ __forceinline__ void fail_abort(const DataParams& p) {
+    atomicOr(p.status, DEV_ERR_TIMEOUT);
+    atomicExch(p.abort_word, 1u);
+}
+
+template <int D, int DT>
+__global__ void __launch_bounds__(kPersistThreads, kPersistMinBlocks) k_persistent(DataParams p) {
+    using G = Geom<D, DT>;
+    extern __shared__ float4 smem4[];
+    float* smem = reinterpret_cast<float*>(smem4);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane / G::L, lig = lane % G::L;
+    const int wpb = blockDim.x >> 5;
+    const int R = p.K + 2;
+    float* stage = smem + (size_t)warp * (p.K + 1) * 32 * G::E;
+    const uint64_t W = (uint64_t)gridDim.x * wpb;
+    const uint64_t total = p.item_base[p.n_batches];
+    int b = 0;
+    int checked_b = -1;
+    for (uint64_t t = (uint64_t)blockIdx.x * wpb + warp; t < total; t += W) {
+        while (t >= p.item_base[b + 1]) ++b;
+        if (*(volatile uint32_t*)p.abort_word) return;
+        const uint64_t local = t - p.item_base[b];
+        const int64_t s_begin = (int64_t)b * p.batch;
+        const int64_t nb = min((int64_t)p.batch, p.chunk_samples - s_begin);
+        const uint64_t nA = (uint64_t)((nb + G::GPW - 1) / G::GPW);
+        const uint64_t t0 = p.t_chunk + (uint64_t)s_begin;
+        const float eta = p.eta[b];
+        if (local < nA) {
+            if (checked_b != b) {
+                if (!batch_applied_ok(p, b - 2) || !batch_applied_ok(p, b - 3)) {
+                    fail_abort(p);
+                    return;
+                }
+                checked_b = b;
+            }
+            const int64_t s_local = s_begin + (int64_t)local * G::GPW + grp;
+            const bool active = s_local < s_begin + nb;
+            bool ok = true;
+            if (active) {
+                for (int k = lig; k < R; k += G::L) {
+                    const int32_t ps = p.prev_seg[s_local * R + k];
+                    if (ps >= 0 && !wait_geq(p.seg_done + ps, p.gen, p.spin_limit, p.abort_word)) ok = false;
+                }
+            }
+            if (!__all_sync(0xFFFFFFFFu, ok)) {
+                fail_abort(p);
+                return;
+            }
+            sample_item<D, DT>(p, s_local, lig, lane, active, eta, stage);
+            __syncwarp();
+            if (active && lig == 0) st_release(p.sample_done + s_local, p.gen);
+        } else {
+            const uint32_t seg = p.batch_seg[b] + (uint32_t)((local - nA) * G::GPW) + grp;
+            const bool active = seg < p.batch_seg[b + 1];
+            const bool ok = segment_item<D, DT>(p, seg, lig, lane, active, eta, t0, true);
+            if (!__all_sync(0xFFFFFFFFu, ok)) {
+                fail_abort(p);
+                return;
+            }
+            // the group's row stores are ordered before the flag by the warp
+            // barrier; the release store publishes them
+            __syncwarp();
+            if (active && lig == 0) {
+                st_release(p.seg_done + seg, p.gen);
+                red_release_add(p.batch_applied + b, 1u);
+            }
+        }
+    }
+}
+
+// eta[b] = lr0 (schedule 0) or lr0 * max(1 - t0/T, floor) (schedule 1) for
+// the batch starting at global sample t0 = t_chunk + b * batch; FP64 once per
+// batch, used as FP32.
+__global__ void k_batch_eta(int n_batches, uint64_t t_chunk, int64_t batch, double lr0, int schedule, double floor_frac,
+                            uint64_t total, float* __restrict__ eta) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_batches) return;
+    double f = 1.0;
+    if (schedule == 1) {
+        f = 1.0 - (double)(t_chunk + (uint64_t)b * (uint64_t)batch) / (double)total;
+        if (f < floor_frac) f = floor_frac;
+    }
+    eta[b] = (float)(lr0 * f);
+}
+
+// item_base[b] = first work item of batch b (sample items then segment items).
+__global__ void k_item_base(const uint32_t* __restrict__ batch_seg, int n_batches, int64_t batch,
+                            int64_t chunk_samples, int gpw, uint64_t* __restrict__ item_base) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    uint64_t acc = 0;
+    for (int b = 0; b < n_batches; ++b) {
+        item_base[b] = acc;
+        const int64_t nb = min(batch, chunk_samples - (int64_t)b * batch);
+        acc += (uint64_t)((nb + gpw - 1) / gpw);
+        acc += (uint64_t)((batch_seg[b + 1] - batch_seg[b] + gpw - 1) / gpw);
+    }
+    item_base[n_batches] = acc;
+}
+
+// prev_seg[(sample, slot)] = segment of the same row in the previous batch of
+// the chunk, or -1.  One thread per segment: binary search among the previous
+// batch's segment keys, then written for every entry of the segment.
+__global__ void k_prev_seg(const uint64_t* __restrict__ items, const uint32_t* __restrict__ seg_start,
+                           const uint32_t* n_segs_p, const uint32_t* __restrict__ batch_seg, uint32_t row_bits,
+                           uint32_t R, int32_t* __restrict__ prev_seg) {
+    const uint32_t n_segs = *n_segs_p;
+    const uint32_t mask = (1u << row_bits) - 1u;
+    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n_segs; j += gridDim.x * blockDim.x) {
+        const uint32_t key = (uint32_t)(items[seg_start[j]] >> 32);
+        const uint32_t b = key >> row_bits;
+        int32_t ps = -1;
+        if (b > 0) {
+            const uint32_t want = ((b - 1) << row_bits) | (key & mask);
+            uint32_t lo = batch_seg[b - 1], hi = batch_seg[b];
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if ((uint32_t)(items[seg_start[mid]] >> 32) < want) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < batch_seg[b] && (uint32_t)(items[seg_start[lo]] >> 32) == want) ps = (int32_t)lo;
+        }
+        for (uint32_t i = seg_start[j]; i < seg_start[j + 1]; ++i) {
+            const uint32_t v = (uint32_t)items[i];
+            prev_seg[(v >> kSlotBits) * R + (v & kSlotMask)] = ps;
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -329,31 +528,32 @@ struct PrepassParams {
     uint64_t* items;
 };
 
-__device__ __forceinline__ uint64_t make_item(uint32_t batch, uint32_t row_bits, uint32_t rowid, uint32_t value) {
-    return ((uint64_t)((batch << row_bits) | rowid) << 32) | value;
+__device__ __forceinline__ uint64_t make_item(uint32_t batch, uint32_t row_bits, uint32_t rowid, uint32_t s_local,
+                                              uint32_t slot) {
+    return ((uint64_t)((batch << row_bits) | rowid) << 32) | ((s_local << kSlotBits) | slot);
 }
 
 __global__ void k_chunk_draws(PrepassParams p) {
-    const int C1 = p.K + 1, R = p.K + 2;
-    const int64_t total = p.chunk_samples * C1;
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t s = q / C1;
-        const int c = (int)(q - s * C1);
-        const uint32_t b = (uint32_t)(s / p.batch);
-        const uint4 w = draw_words(p.seed, 0u, p.t_chunk + (uint64_t)s, (uint32_t)c);
+    const uint32_t C1 = (uint32_t)p.K + 1u, R = (uint32_t)p.K + 2u;
+    const uint32_t total = (uint32_t)p.chunk_samples * C1;
+    for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
+        const uint32_t s = q / C1;
+        const uint32_t c = q - s * C1;
+        const uint32_t b = s / (uint32_t)p.batch;
+        const uint4 w = draw_words(p.seed, 0u, p.t_chunk + (uint64_t)s, c);
         const uint32_t ctx_off = p.order == 2 ? (uint32_t)p.n_nodes : 0u;
-        const uint32_t base = (uint32_t)(s * R);
+        const uint32_t base = s * R;
         if (c == 0) {
             const uint32_t e = alias_pick(p.edge_tab, (uint64_t)p.n_arcs, w);
             const int32_t u = __ldg(p.src + e), v = __ldg(p.dst + e);
             p.rec[base] = u;
             p.rec[base + 1] = v;
-            p.items[base] = make_item(b, p.row_bits, (uint32_t)u, base);
-            p.items[base + 1] = make_item(b, p.row_bits, (uint32_t)v + ctx_off, base + 1);
+            p.items[base] = make_item(b, p.row_bits, (uint32_t)u, s, 0u);
+            p.items[base + 1] = make_item(b, p.row_bits, (uint32_t)v + ctx_off, s, 1u);
         } else {
             const uint32_t y = alias_pick(p.neg_tab, (uint64_t)p.n_nodes, w);
             p.rec[base + 1 + c] = (int32_t)y;
-            p.items[base + 1 + c] = make_item(b, p.row_bits, y + ctx_off, base + 1 + c);
+            p.items[base + 1 + c] = make_item(b, p.row_bits, y + ctx_off, s, 1u + c);
         }
     }
 }
@@ -494,7 +694,7 @@ struct Buf {
 
 struct TrainWorkspace {
     Buf rec, items0, items1, hist, scan_tiles, seg_start, batch_seg, counters, slab;
-    Buf sample_done, seg_done, batch_applied, prev_seg, item_base;
+    Buf sample_done, seg_done, batch_applied, prev_seg, item_base, eta;
     std::vector<cudaEvent_t> events;  // timing events, three per chunk
     uint32_t gen = 0;
     cudaError_t event(size_t i, cudaEvent_t* out) {
@@ -549,7 +749,51 @@ static cudaError_t launch_data_batched(const DataParams& p, int warps_per_block,
     return cudaGetLastError();
 }
 
+template <int D, int DT>
+static cudaError_t launch_data_persistent(const DataParams& p, int warps_per_block, cudaStream_t s) {
+    using G = Geom<D, DT>;
+    const size_t per_warp = (size_t)(p.K + 1) * 32 * G::E * sizeof(float);
+    int wpb = warps_per_block > 0 ? warps_per_block : 8;
+    wpb = std::min<int>(wpb, kPersistThreads / 32);
+    wpb = std::max<int>(1, std::min<int>(wpb, (int)(kMaxSmem / per_warp)));
+    const size_t smem = (size_t)wpb * per_warp;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_persistent<D, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        attr_set = true;
+    }
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<D, DT>, wpb * 32, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    DataParams pc = p;
+    void* args[] = {&pc};
+    return cudaLaunchCooperativeKernel((const void*)k_persistent<D, DT>, dim3((unsigned)(per_sm * sms)),
+                                       dim3((unsigned)(wpb * 32)), args, smem, s);
+}
+
 using LaunchFn = cudaError_t (*)(const DataParams&, int, cudaStream_t);
+
+static LaunchFn pick_persistent(int dim, int dtype) {
+#define LINE_PICK(DD)                                                                          \
+    if (dim == DD) return dtype == LINE_DTYPE_F32 ? launch_data_persistent<DD, LINE_DTYPE_F32> \
+                                                  : launch_data_persistent<DD, LINE_DTYPE_BF16>;
+    LINE_PICK(16)
+    LINE_PICK(32)
+    LINE_PICK(64)
+    LINE_PICK(128)
+    LINE_PICK(256)
+#undef LINE_PICK
+    return nullptr;
+}
+
+static int groups_per_warp(int dim, int dtype) {
+    const int vec = dtype == LINE_DTYPE_F32 ? 4 : 8;
+    const int L = std::min(32, dim / vec);
+    return 32 / L;
+}
 
 static LaunchFn pick_batched(int dim, int dtype) {
 #define LINE_PICK(DD)                                                                       \
@@ -580,7 +824,10 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     int64_t nb_max = (int64_t)1 << (32 - row_bits);
     int64_t nb = a.chunk_batches > 0 ? a.chunk_batches : std::max<int64_t>(1, (int64_t(1) << 18) / a.batch);
     nb = std::min(nb, nb_max);
-    while (nb > 1 && (uint64_t)nb * (uint64_t)a.batch * (uint64_t)R >= (1ull << 31)) nb >>= 1;
+    // item values hold the chunk sample in 32 - kSlotBits bits
+    while (nb > 1 && ((uint64_t)nb * (uint64_t)a.batch * (uint64_t)R >= (1ull << 31) ||
+                      (uint64_t)nb * (uint64_t)a.batch > (1ull << (32 - kSlotBits))))
+        nb >>= 1;
     const uint64_t total_batches = (n_samples + a.batch - 1) / a.batch;
     nb = (int64_t)std::min<uint64_t>((uint64_t)nb, total_batches);
     const uint32_t batch_bits = bits_for((uint64_t)nb);
@@ -603,9 +850,30 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         !ensure(ws->scan_tiles, sizeof(uint32_t) * (scan_tiles((int64_t)kRsBins * ntiles + max_items) + 2)) ||
         !ensure(ws->seg_start, sizeof(uint32_t) * (max_items + 1)) ||
         !ensure(ws->batch_seg, sizeof(uint32_t) * (nb + 1)) || !ensure(ws->counters, 256) ||
+        !ensure(ws->eta, sizeof(float) * (nb + 1)) ||
         !ensure(ws->slab, sizeof(float) * (size_t)max_items * a.dim))
         return e;
-    LaunchFn data = pick_batched(a.dim, a.dtype);
+    const bool persistent = a.mode == LINE_MODE_PERSISTENT;
+    if (persistent) {
+        if (!ensure(ws->prev_seg, sizeof(int32_t) * max_items) || !ensure(ws->item_base, sizeof(uint64_t) * (nb + 1)) ||
+            !ensure(ws->batch_applied, sizeof(uint32_t) * (nb + 1)))
+            return e;
+        // generation flags start at zero and are never reset: a chunk's
+        // flags are "done" when they equal its generation number
+        const size_t need_s = sizeof(uint32_t) * max_chunk, need_g = sizeof(uint32_t) * (max_items + 1);
+        if (ws->sample_done.cap < need_s) {
+            if (!ensure(ws->sample_done, need_s)) return e;
+            if ((e = cudaMemsetAsync(ws->sample_done.p, 0, need_s, s)) != cudaSuccess) return e;
+            ws->gen = 0;
+        }
+        if (ws->seg_done.cap < need_g) {
+            if (!ensure(ws->seg_done, need_g)) return e;
+            if ((e = cudaMemsetAsync(ws->seg_done.p, 0, need_g, s)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(ws->sample_done.p, 0, ws->sample_done.cap, s)) != cudaSuccess) return e;
+            ws->gen = 0;
+        }
+    }
+    LaunchFn data = persistent ? pick_persistent(a.dim, a.dtype) : pick_batched(a.dim, a.dtype);
     if (!data) {
         *err = "unsupported dim";
         return cudaErrorInvalidValue;
@@ -637,10 +905,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     dp.slab = (float*)ws->slab.p;
     dp.batch = a.batch;
     dp.seed = a.seed;
-    dp.lr0 = a.lr0;
-    dp.lr_floor = a.lr_floor;
-    dp.lr_total = a.lr_total;
-    dp.lr_schedule = a.lr_schedule;
+    dp.eta = (const float*)ws->eta.p;
     dp.lambda = (float)a.lambda;
     dp.alpha_neg = (float)a.alpha_neg;
     dp.status = status;
@@ -648,6 +913,14 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     dp.C = a.order == 2 ? a.C : a.U;
 
     uint32_t* n_segs_dev = (uint32_t*)ws->counters.p;
+    uint32_t* abort_word = (uint32_t*)ws->counters.p + 16;
+    dp.sample_done = (uint32_t*)ws->sample_done.p;
+    dp.seg_done = (uint32_t*)ws->seg_done.p;
+    dp.batch_applied = (uint32_t*)ws->batch_applied.p;
+    dp.prev_seg = (const int32_t*)ws->prev_seg.p;
+    dp.item_base = (const uint64_t*)ws->item_base.p;
+    dp.spin_limit = a.spin_limit;
+    dp.abort_word = abort_word;
     size_t n_ev = 0;
     struct ChunkRec {
         int64_t samples;
@@ -690,9 +963,22 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
                                        OutSegStart{in, (uint32_t*)ws->seg_start.p, n_items, n_segs_dev},
                                        (uint32_t*)ws->scan_tiles.p, s)) != cudaSuccess)
             return e;
+        k_batch_eta<<<(unsigned)((cb + 127) / 128), 128, 0, s>>>(cb, t, a.batch, a.lr0, a.lr_schedule, a.lr_floor,
+                                                                 a.lr_total, (float*)ws->eta.p);
         k_batch_seg<<<(unsigned)std::min<int64_t>((n_items + 255) / 256, 152 * 16), 256, 0, s>>>(
             in, (const uint32_t*)ws->seg_start.p, n_segs_dev, row_bits, cb, (uint32_t*)ws->batch_seg.p);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        if (persistent) {
+            const unsigned gs = (unsigned)std::min<int64_t>((n_items + 255) / 256, 152 * 16);
+            k_prev_seg<<<gs, 256, 0, s>>>(in, (const uint32_t*)ws->seg_start.p, n_segs_dev, (const uint32_t*)ws->batch_seg.p,
+                                          row_bits, (uint32_t)R, (int32_t*)ws->prev_seg.p);
+            k_item_base<<<1, 32, 0, s>>>((const uint32_t*)ws->batch_seg.p, cb, a.batch, cs,
+                                         groups_per_warp(a.dim, a.dtype), (uint64_t*)ws->item_base.p);
+            if ((e = cudaMemsetAsync(ws->batch_applied.p, 0, sizeof(uint32_t) * (cb + 1), s)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(abort_word, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            dp.gen = ++ws->gen;
+        }
         if (a.timing) {
             if ((e = ws->event(n_ev + 1, &ev_b)) != cudaSuccess) return e;
             cudaEventRecord(ev_b, s);
@@ -721,8 +1007,8 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
             times->prepass_ms += ms1;
             times->update_ms += ms2;
             // draws + per pass (hist, 3 scan launches, scatter) + segment scan (3) + batch_seg
-            times->prepass_launches += 1 + 5 * passes + 4;
-            times->update_launches += 2 * (int64_t)chunk_log[i].batches;
+            times->prepass_launches += 1 + 5 * passes + 5 + (persistent ? 2 : 0);
+            times->update_launches += persistent ? 1 : 2 * (int64_t)chunk_log[i].batches;
             times->update_samples += (uint64_t)chunk_log[i].samples;
         }
     }

@@ -175,3 +175,89 @@ def test_untouched_rows_and_zero_lr(ctx):
     # nodes 41.. have degree 0: never drawn, rows unchanged
     assert np.array_equal(U2[41:], U0[41:]) and not C2[41:].any()
     assert not np.array_equal(U2[:41], U0[:41])
+
+
+@pytest.mark.parametrize("name,order,dim,B,n", [("tiny", 2, 16, 256, 100_000), ("tiny", 1, 16, 256, 50_000),
+                                               ("rmat14", 2, 128, 4096, 200_000), ("rmat14", 1, 128, 4096, 100_000),
+                                               ("dchung", 2, 64, 1000, 50_000), ("tiny", 2, 256, 64, 20_000)])
+def test_persistent_matches_batched_bitwise(ctx, name, order, dim, B, n):
+    from paper_2604_09419_gb300 import line as L
+    g = G.graph(name)
+    G.upload(ctx, g)
+    a = _run(ctx, g, order, dim, 5, n, B, mode=L.MODE_BATCHED)
+    for cb in (0, 1, 5):
+        b = _run(ctx, g, order, dim, 5, n, B, mode=L.MODE_PERSISTENT, chunk_batches=cb)
+        assert np.array_equal(a[0], b[0]), cb
+        if order == 2:
+            assert np.array_equal(a[1], b[1]), cb
+
+
+def test_persistent_parity_with_oracle(ctx):
+    from paper_2604_09419_gb300 import line as L
+    _train_both(ctx, "tiny", 2, 16, 5, 100_000, 256, mode=L.MODE_PERSISTENT)
+    _train_both(ctx, "rmat14", 1, 128, 5, 40_000, 4096, mode=L.MODE_PERSISTENT)
+
+
+def test_full_size_rmat20_prefix(ctx):
+    """The benchmark's workload (R-MAT 20, d=128, K=5, B=4096) in the benchmark's
+    launch configuration, on a prefix the oracle finishes in seconds."""
+    from paper_2604_09419_gb300 import line as L
+    g = G.graph("rmat20")
+    G.upload(ctx, g)
+    T = G.oracle_tables("rmat20")
+    # alias tables and windows of draws at full size
+    thr, alias = G.gpu_alias(ctx, g, L.TABLE_NEG)
+    assert np.array_equal(thr, T.thr_n) and np.array_equal(alias, T.alias_n)
+    thr, alias = G.gpu_alias(ctx, g, L.TABLE_EDGE)
+    assert np.array_equal(thr, T.thr_e) and np.array_equal(alias, T.alias_e)
+    for t0 in (0, 335_544_320 - 1_000_000):
+        assert np.array_equal(G.gpu_samples(ctx, 5, 1000, t0, 1_000_000), O.sample(T, 1000, t0, 1_000_000, 5))
+    n, total = 4096 * 48, 335_544_320
+    for order, mode in ((2, L.MODE_PERSISTENT), (1, L.MODE_PERSISTENT), (2, L.MODE_BATCHED)):
+        ctx.init_embeddings(order, 128, L.DTYPE_F32, seed=order)
+        ctx.train_steps(order, 128, 5, n, 1000, batch=4096, total=total, mode=mode)
+        U, C = G.tables(ctx, g, order, 128)
+        Uo = O.init_uniform(g.n_nodes, 128, order)
+        Co = np.zeros_like(Uo) if order == 2 else None
+        O.train(T, Uo, Co, order=order, K=5, n_samples=n, seed=1000, batch=4096, lr_total=total)
+        err = np.abs(U - Uo).max()
+        if order == 2:
+            err = max(err, np.abs(C - Co).max())
+        print(f"rmat20 order {order} mode {mode}: max |GPU - oracle| = {err:.3e}")
+        assert err <= TOL
+
+
+def test_bf16_tables(ctx):
+    """BF16 storage with FP32 arithmetic and stochastic rounding: error vs the
+    FP64 oracle is stated (printed), lr 0 leaves the tables bit-identical, both
+    schedules agree bitwise, and the rounding is unbiased."""
+    from paper_2604_09419_gb300 import line as L
+    g = G.graph("tiny")
+    G.upload(ctx, g)
+    dim, n, B = 64, 100_000, 256
+    ctx.init_embeddings(2, dim, L.DTYPE_BF16, seed=1)
+    U0, C0 = G.tables(ctx, g, 2, dim)
+    ctx.train_steps(2, dim, 5, 5000, 3, batch=B, lr0=0.0)
+    U1, C1 = G.tables(ctx, g, 2, dim)
+    assert np.array_equal(U0, U1) and np.array_equal(C0, C1)
+    runs = []
+    for mode in (L.MODE_BATCHED, L.MODE_PERSISTENT):
+        ctx.init_embeddings(2, dim, L.DTYPE_BF16, seed=1)
+        ctx.train_steps(2, dim, 5, n, 3, batch=B, mode=mode)
+        runs.append(G.tables(ctx, g, 2, dim))
+    assert np.array_equal(runs[0][0], runs[1][0]) and np.array_equal(runs[0][1], runs[1][1])
+    Ub, Cb = runs[0]
+    # the oracle starts from the BF16-rounded initial table
+    T = G.oracle_tables("tiny")
+    Uo = U0.astype(np.float64)
+    Co = np.zeros_like(Uo)
+    O.train(T, Uo, Co, order=2, K=5, n_samples=n, seed=3, batch=B)
+    err_u, err_c = np.abs(Ub - Uo).max(), np.abs(Cb - Co).max()
+    rms = np.sqrt(np.mean(np.concatenate([(Ub - Uo).ravel(), (Cb - Co).ravel()]) ** 2))
+    scale = max(np.abs(Uo).max(), np.abs(Co).max())
+    print(f"bf16 tiny d={dim}: max |GPU - FP64| U {err_u:.3e} C {err_c:.3e}, rms {rms:.3e}, max |x| {scale:.3f}")
+    assert max(err_u, err_c) < 0.15 * scale  # a sanity bound; the error itself is reported
+    # unbiased rounding: the mean signed error is small against its spread
+    diff = np.concatenate([(Ub - Uo).ravel(), (Cb - Co).ravel()])
+    diff = diff[diff != 0]
+    assert abs(diff.mean()) < 5 * diff.std() / np.sqrt(diff.size)
