@@ -2,7 +2,7 @@
 //
 // A call processes its samples in chunks of whole batches.  Per chunk:
 //
-//   pre-pass (index work only, independent of the tables):
+//   pre-pass (index work only; it does not read the tables):
 //     1. draws: for every sample its arc (u, v) and K negatives, kept as a
 //        record (u, v, n_1..n_K), and K+2 sort items, one per row the sample
 //        touches: key = (batch, row), value = (sample, slot).  Slot 0 is
@@ -10,28 +10,35 @@
 //        for second order, U for first order; C rows get ids offset by n).
 //     2. a stable LSD radix sort of the items by key; equal keys keep the
 //        (sample, slot) order.
-//     3. segments: one per distinct key = one per (batch, row).
+//     3. segments: one per distinct key = one per (batch, row).  A segment
+//        with one entry is a singleton: its row is read and written by one
+//        sample only.  Every (sample, slot) learns its segment and its
+//        position in the sorted order; segments with two or more entries get
+//        a descriptor (first position, length, key, pair count).
 //
 //   data phase, batch after batch:
-//     gather  one lane group per sample loads U_b[u] and the K+1 context rows
-//             (staged in shared memory), forms s_j = U_b[u].Ctx_b[y_j],
+//     gather  one lane group per sample loads U_b[u] and the K+1 context
+//             rows (staged in shared memory), forms s_j = U_b[u].Ctx_b[y_j],
 //             g_j = eta_b (1 - sigma(s_j)) for the positive and
-//             -eta_b alpha_neg sigma(s_j) for the negatives (Algorithm 1), and
-//             writes the per-row gradient contributions to a delta slab:
-//             slot 0: sum_j g_j Ctx_b[y_j]; slot 1+j: g_j U_b[u].
-//     apply   one lane group per segment sums its slab entries in sorted
-//             order and writes X <- X_b - cnt eta_b lambda X_b + sum, with
-//             cnt the number of pair occurrences of the row (Eq. 2-3 summed
-//             over the batch as in Eq. 4).  BF16 tables are written back with
-//             stochastic rounding.
+//             -eta_b alpha_neg sigma(s_j) for the negatives (Algorithm 1).
+//             Its contributions are slot 0: sum_j g_j Ctx_b[y_j] for U[u],
+//             slot 1+j: g_j U_b[u] for Ctx[y_j].  A singleton row is written
+//             back at once (Eq. 2-3); a shared row's contribution goes to the
+//             delta slab at its sorted position.
+//     apply   one lane group per shared segment sums its (contiguous) slab
+//             entries in sorted order and writes X <- X_b - cnt eta_b lambda
+//             X_b + sum, cnt the number of pair occurrences of the row (the
+//             batch-summed update of Eq. 4).
+//   BF16 tables are written back with stochastic rounding.
 //
 // The order of every floating-point sum is fixed, so results are bitwise
-// reproducible.  Two schedules run the same per-sample and per-segment code:
+// reproducible, and a singleton row gets exactly the value the apply step
+// would give it.  Two schedules run the same per-sample and per-segment code:
 //   LINE_MODE_BATCHED     two launches per batch;
-//   LINE_MODE_PERSISTENT  one launch per chunk: every warp walks a fixed
-//                         list of work items (batch b's samples, then b's
-//                         segments, then b+1's ...) and waits, with bounded
-//                         spins, only on the items it depends on.
+//   LINE_MODE_PERSISTENT  one cooperative launch per chunk: every warp walks
+//                         a fixed list of work items (batch b's samples, then
+//                         b's shared segments, then b+1's ...) and waits,
+//                         with bounded spins, only on the items it depends on.
 #include <algorithm>
 #include <cstdio>
 #include <vector>
@@ -122,9 +129,16 @@ __device__ __forceinline__ float group_sum(float v) {
     return v;
 }
 
+template <int L>
+__device__ __forceinline__ uint32_t group_mask(int grp) {
+    return L == 32 ? 0xFFFFFFFFu : (((1u << L) - 1u) << (grp * L));
+}
+
 // Sort item value: (sample within the chunk) << kSlotBits | slot.
 constexpr uint32_t kSlotBits = 6;
 constexpr uint32_t kSlotMask = (1u << kSlotBits) - 1u;
+// slot_info.x: sorted position, bit 31 set for a singleton segment.
+constexpr uint32_t kSingleBit = 1u << 31;
 
 // ---------------------------------------------------------------------------
 // Kernel parameters shared by the data-phase kernels.
@@ -135,12 +149,12 @@ struct DataParams {
     int order, K;  // records have K+2 entries
     int64_t n_nodes;
     uint32_t row_bits;
-    const int32_t* rec;        // [chunk samples][K+2]
-    const uint64_t* items;     // sorted (key << 32 | value)
-    const uint32_t* seg_start; // [n_segs + 1]
-    const uint32_t* batch_seg; // [n_batches + 1]
-    float* slab;               // [chunk samples][K+2][D]
-    uint64_t t_chunk;          // global index of the chunk's first sample
+    const int32_t* rec;          // [chunk samples][K+2]
+    const uint2* slot_info;      // [chunk samples][K+2]: {position | singleton bit, segment}
+    const uint4* mdesc;          // shared segments: {first position, length, key, pair count}
+    const uint32_t* batch_mseg;  // [n_batches + 1] first shared segment of each batch
+    float* slab;                 // [chunk samples * (K+2)][D], by sorted position
+    uint64_t t_chunk;            // global index of the chunk's first sample
     int64_t chunk_samples;
     int64_t batch;
     int n_batches;
@@ -149,38 +163,58 @@ struct DataParams {
     float lambda, alpha_neg;
     uint32_t* status;
     // persistent schedule
-    uint32_t* sample_done;  // [chunk samples] generation flags
-    uint32_t* seg_done;     // [chunk segments] generation flags
-    uint32_t* batch_applied;  // [n_batches] count of applied segments
-    const int32_t* prev_seg;  // [chunk samples][K+2]: segment of the same row in the previous batch, or -1
+    const int32_t* slot_prev;   // [chunk samples][K+2]: latest earlier segment of the same row, or -1
+    const uint32_t* mseg_id;    // [shared segments] segment number
+    uint32_t* seg_done;         // [segments] generation flags: the row of the segment is written
+    uint32_t* arrive;           // [segments] contributions written to the slab
     const uint64_t* item_base;  // [n_batches + 1] first work item of each batch
     uint32_t gen;
     int64_t spin_limit;
     uint32_t* abort_word;
 };
 
-// ---------------------------------------------------------------------------
-// Per-sample work: gather, dots, gradient scalars, slab contributions.
-// ctx_stage: this warp's shared staging area, (K+1) x 32 lanes x E.
-// The record's ids are read by the group's lanes in one go and broadcast, and
-// the context rows are loaded CH at a time so their loads are in flight
-// together.
-// ---------------------------------------------------------------------------
-template <int L>
-__device__ __forceinline__ uint32_t group_mask(int grp) {
-    return L == 32 ? 0xFFFFFFFFu : (((1u << L) - 1u) << (grp * L));
+// Record entry idx of the group's sample: lane idx % L holds entries
+// idx < L in `held`; later ones are read from memory.
+__device__ __forceinline__ int32_t shfl_w(uint32_t gm, int32_t v, int src, int w) { return __shfl_sync(gm, v, src, w); }
+__device__ __forceinline__ uint2 shfl_w(uint32_t gm, uint2 v, int src, int w) {
+    return make_uint2(__shfl_sync(gm, v.x, src, w), __shfl_sync(gm, v.y, src, w));
 }
 
-template <int D, int DT>
-__device__ __forceinline__ void sample_item(const DataParams& p, int64_t s_local, int lig, int lane, bool active,
-                                            float eta, float* ctx_stage) {
+template <int L, typename T>
+__device__ __forceinline__ T rec_entry(uint32_t gm, T held, const T* row, int idx, bool active) {
+    T v = shfl_w(gm, held, idx % L, L);
+    if (idx >= L) v = active ? row[idx] : T{};
+    return v;
+}
+
+// ---------------------------------------------------------------------------
+// Per-sample work.  Returns false when a bounded wait ran out (persistent).
+// ctx_stage: this warp's shared staging area, (K+1) x 32 lanes x E floats.
+// ---------------------------------------------------------------------------
+template <int D, int DT, bool PERSIST>
+__device__ __forceinline__ bool sample_item(const DataParams& p, int64_t s_local, int lig, int lane, bool active,
+                                            float eta, uint64_t t0, float* ctx_stage) {
     using G = Geom<D, DT>;
     constexpr int CH = G::E <= 4 ? 4 : 2;  // context rows in flight per lane
     const int R = p.K + 2;
-    const int32_t* rec = p.rec + (active ? s_local : 0) * R;
+    const int64_t sbase = (active ? s_local : 0) * R;
+    const int32_t* rec = p.rec + sbase;
+    const uint2* info = p.slot_info + sbase;
     const uint32_t gm = group_mask<G::L>(lane / G::L);
-    // lane l of the group holds rec[l] (and rec[l + L], ... for small groups)
     const int32_t r0 = (active && lig < R) ? rec[lig] : 0;
+    const uint2 i0 = (active && lig < R) ? info[lig] : make_uint2(0u, 0u);
+    bool ok = true;
+    if constexpr (PERSIST) {
+        // rows written by an earlier segment of this chunk: wait for it
+        if (active) {
+            for (int k = lig; k < R; k += G::L) {
+                const int32_t pv = p.slot_prev[sbase + k];
+                if (pv >= 0 && ok) ok = wait_geq(p.seg_done + pv, p.gen, p.spin_limit, p.abort_word);
+            }
+        }
+        __syncwarp(gm);
+        if (!__all_sync(gm, ok)) return false;
+    }
     const int32_t u = __shfl_sync(gm, r0, 0, G::L);
     float xu[G::E];
     load_row<D, DT>(p.U, u, lig, xu);
@@ -189,10 +223,7 @@ __device__ __forceinline__ void sample_item(const DataParams& p, int64_t s_local
 #pragma unroll
         for (int jj = 0; jj < CH; ++jj) {
             const int j = j0 + jj;
-            const int idx = 1 + j;  // record entry of context row j
-            int32_t y = __shfl_sync(gm, r0, idx % G::L, G::L);
-            if (idx >= G::L) y = (active && j <= p.K) ? rec[idx] : 0;
-            if (j > p.K) y = 0;
+            int32_t y = rec_entry<G::L>(gm, r0, rec, 1 + j, active && j <= p.K);
             if (j <= p.K) load_row<D, DT>(p.C, y, lig, c[jj]);
         }
 #pragma unroll
@@ -206,10 +237,11 @@ __device__ __forceinline__ void sample_item(const DataParams& p, int64_t s_local
             }
         }
     }
+    const uint32_t ctx_table = p.order == 2 ? 1u : 0u;
+    const float etalam = eta * p.lambda;
     float du[G::E];
 #pragma unroll
     for (int e = 0; e < G::E; ++e) du[e] = 0.0f;
-    float* slab = p.slab + (active ? s_local : 0) * (int64_t)R * D + lig * G::E;
     for (int j = 0; j <= p.K; ++j) {
         float c[G::E];
         const float4* ld = reinterpret_cast<const float4*>(ctx_stage + (j * 32 + lane) * G::E);
@@ -229,88 +261,102 @@ __device__ __forceinline__ void sample_item(const DataParams& p, int64_t s_local
         const float g = j == 0 ? eta * (1.0f - sig) : -eta * p.alpha_neg * sig;
 #pragma unroll
         for (int e = 0; e < G::E; ++e) du[e] = fmaf(g, c[e], du[e]);
+        const uint2 inf = rec_entry<G::L>(gm, i0, info, 1 + j, active);
+        const int32_t y = rec_entry<G::L>(gm, r0, rec, 1 + j, active);
         if (active) {
-            float4* dst = reinterpret_cast<float4*>(slab + (int64_t)(1 + j) * D);
+            if (inf.x & kSingleBit) {
+                // the only reader of row y in this batch: write it now
+                const float decay = 1.0f * etalam;
+                float x[G::E];
 #pragma unroll
-            for (int q = 0; q < G::E / 4; ++q)
-                st_cg(dst + q, make_float4(g * xu[4 * q], g * xu[4 * q + 1], g * xu[4 * q + 2], g * xu[4 * q + 3]));
+                for (int e = 0; e < G::E; ++e) x[e] = fmaf(-decay, c[e], c[e]) + g * xu[e];
+                store_row<D, DT>(p.C, y, lig, x, p.seed, t0, ctx_table);
+            } else {
+                float4* dst = reinterpret_cast<float4*>(p.slab + (int64_t)inf.x * D + lig * G::E);
+#pragma unroll
+                for (int q = 0; q < G::E / 4; ++q)
+                    st_cg(dst + q, make_float4(g * xu[4 * q], g * xu[4 * q + 1], g * xu[4 * q + 2], g * xu[4 * q + 3]));
+            }
         }
     }
+    const uint2 inf0 = shfl_w(gm, i0, 0, G::L);
     if (active) {
-        float4* dst = reinterpret_cast<float4*>(slab);
+        if (inf0.x & kSingleBit) {
+            const float decay = (float)(p.K + 1) * etalam;
 #pragma unroll
-        for (int q = 0; q < G::E / 4; ++q) st_cg(dst + q, make_float4(du[4 * q], du[4 * q + 1], du[4 * q + 2], du[4 * q + 3]));
+            for (int e = 0; e < G::E; ++e) xu[e] = fmaf(-decay, xu[e], xu[e]) + du[e];
+            store_row<D, DT>(p.U, u, lig, xu, p.seed, t0, 0u);
+        } else {
+            float4* dst = reinterpret_cast<float4*>(p.slab + (int64_t)inf0.x * D + lig * G::E);
+#pragma unroll
+            for (int q = 0; q < G::E / 4; ++q) st_cg(dst + q, make_float4(du[4 * q], du[4 * q + 1], du[4 * q + 2], du[4 * q + 3]));
+        }
     }
+    if constexpr (PERSIST) {
+        // publish: the group's stores are ordered before the release stores
+        // by the warp barrier; lane k signals slot k
+        __syncwarp(gm);
+        if (active) {
+            for (int k = lig; k < R; k += G::L) {
+                const uint2 inf = info[k];
+                if (inf.x & kSingleBit) st_release(p.seg_done + inf.y, p.gen);
+                else red_release_add(p.arrive + inf.y, 1u);
+            }
+        }
+    }
+    return ok;
 }
 
 // ---------------------------------------------------------------------------
-// Per-segment work: fixed-order sum of the slab entries of one (batch, row)
-// and the write-back.  The group's lanes read the entries' values (and, in
-// the persistent schedule, wait on their samples) in parallel, L at a time;
-// the slab loads of PF entries are then in flight together and are added in
-// sorted order.  Returns false when a bounded wait ran out.
+// Per shared segment: fixed-order sum of its contiguous slab entries and the
+// write-back.  Returns false when a bounded wait ran out (persistent).
 // ---------------------------------------------------------------------------
-template <int D, int DT>
-__device__ __forceinline__ bool segment_item(const DataParams& p, uint32_t seg, int lig, int lane, bool active,
-                                             float eta, uint64_t t0, bool wait_samples) {
+template <int D, int DT, bool PERSIST>
+__device__ __forceinline__ bool segment_item(const DataParams& p, uint32_t m, int lig, bool active, float eta,
+                                             uint64_t t0) {
     using G = Geom<D, DT>;
-    constexpr int PF = G::E <= 4 ? 4 : 2;
-    const uint32_t gm = group_mask<G::L>(lane / G::L);
-    const uint32_t begin = active ? p.seg_start[seg] : 0u, end = active ? p.seg_start[seg + 1] : 0u;
-    const int R = p.K + 2;
-    float acc[G::E];
-#pragma unroll
-    for (int e = 0; e < G::E; ++e) acc[e] = 0.0f;
-    int cnt = 0;
-    uint32_t key = 0;
-    bool ok = true;
-    for (uint32_t base = begin; base < end; base += G::L) {
-        const uint32_t i = base + (uint32_t)lig;
-        const bool have = i < end;
-        const uint64_t item = have ? p.items[i] : 0ull;
-        if (base == begin) key = __shfl_sync(gm, (uint32_t)(item >> 32), 0, G::L);
-        const uint32_t v = (uint32_t)item;
-        if (wait_samples && have && ok)
-            ok = wait_geq(p.sample_done + (v >> kSlotBits), p.gen, p.spin_limit, p.abort_word);
-        const int m = (int)min((uint32_t)G::L, end - base);
-        __syncwarp(gm);
-        for (int k0 = 0; k0 < m; k0 += PF) {
-            float4 buf[PF][G::E / 4];
-#pragma unroll
-            for (int kk = 0; kk < PF; ++kk) {
-                const uint32_t vk = __shfl_sync(gm, v, (k0 + kk) % G::L, G::L);
-                if (k0 + kk < m) {
-                    const uint32_t slot = vk & kSlotMask;
-                    const int64_t entry = (int64_t)(vk >> kSlotBits) * R + slot;
-                    const float4* src = reinterpret_cast<const float4*>(p.slab + entry * D + lig * G::E);
-#pragma unroll
-                    for (int q = 0; q < G::E / 4; ++q) buf[kk][q] = ld_cg(src + q);
-                    cnt += slot == 0 ? p.K + 1 : 1;
-                }
-            }
-#pragma unroll
-            for (int kk = 0; kk < PF; ++kk) {
-                if (k0 + kk < m) {
-#pragma unroll
-                    for (int q = 0; q < G::E / 4; ++q) {
-                        acc[4 * q] += buf[kk][q].x;
-                        acc[4 * q + 1] += buf[kk][q].y;
-                        acc[4 * q + 2] += buf[kk][q].z;
-                        acc[4 * q + 3] += buf[kk][q].w;
-                    }
-                }
-            }
-        }
-    }
-    if (wait_samples && !__all_sync(gm, ok)) return false;
+    constexpr int PF = G::E <= 4 ? 8 : 4;  // slab entries in flight per lane
     if (!active) return true;
-    const uint32_t rowid = key & ((1u << p.row_bits) - 1u);
+    const uint4 d = p.mdesc[m];  // {first position, length, key, pair count}
+    if constexpr (PERSIST) {
+        // all contributions written (and, through them, every read of the
+        // row's batch-start value and the row's previous write done)
+        if (!wait_geq(p.arrive + p.mseg_id[m], d.y, p.spin_limit, p.abort_word)) return false;
+    }
+    const uint32_t rowid = d.z & ((1u << p.row_bits) - 1u);
     const bool is_c = p.order == 2 && rowid >= (uint32_t)p.n_nodes;
     void* table = is_c ? p.C : p.U;
     const int64_t row = is_c ? (int64_t)rowid - p.n_nodes : (int64_t)rowid;
     float x[G::E];
     load_row<D, DT>(table, row, lig, x);
-    const float decay = (float)cnt * (eta * p.lambda);
+    float acc[G::E];
+#pragma unroll
+    for (int e = 0; e < G::E; ++e) acc[e] = 0.0f;
+    const float* base = p.slab + (int64_t)d.x * D + lig * G::E;
+    for (uint32_t k0 = 0; k0 < d.y; k0 += PF) {
+        float4 buf[PF][G::E / 4];
+#pragma unroll
+        for (int kk = 0; kk < PF; ++kk) {
+            if (k0 + kk < d.y) {
+                const float4* src = reinterpret_cast<const float4*>(base + (int64_t)(k0 + kk) * D);
+#pragma unroll
+                for (int q = 0; q < G::E / 4; ++q) buf[kk][q] = ld_cg(src + q);
+            }
+        }
+#pragma unroll
+        for (int kk = 0; kk < PF; ++kk) {
+            if (k0 + kk < d.y) {
+#pragma unroll
+                for (int q = 0; q < G::E / 4; ++q) {
+                    acc[4 * q] += buf[kk][q].x;
+                    acc[4 * q + 1] += buf[kk][q].y;
+                    acc[4 * q + 2] += buf[kk][q].z;
+                    acc[4 * q + 3] += buf[kk][q].w;
+                }
+            }
+        }
+    }
+    const float decay = (float)d.w * (eta * p.lambda);
 #pragma unroll
     for (int e = 0; e < G::E; ++e) x[e] = fmaf(-decay, x[e], x[e]) + acc[e];
     store_row<D, DT>(table, row, lig, x, p.seed, t0, is_c ? 1u : 0u);
@@ -333,9 +379,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_gather(DataParams p, int b) 
     const int64_t s_begin = (int64_t)b * p.batch;
     const int64_t s_end = min(s_begin + p.batch, p.chunk_samples);
     const int64_t s_local = s_begin + ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * G::GPW + grp;
-    const float eta = p.eta[b];
     float* stage = smem + (size_t)warp * (p.K + 1) * 32 * G::E;
-    sample_item<D, DT>(p, s_local, lig, lane, s_local < s_end, eta, stage);
+    sample_item<D, DT, false>(p, s_local, lig, lane, s_local < s_end, p.eta[b], p.t_chunk + (uint64_t)s_begin, stage);
 }
 
 template <int D, int DT>
@@ -343,42 +388,30 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_apply(DataParams p, int b) {
     using G = Geom<D, DT>;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane / G::L, lig = lane % G::L;
-    const uint32_t seg_begin = p.batch_seg[b], seg_end = p.batch_seg[b + 1];
-    const int64_t s_begin = (int64_t)b * p.batch;
-    const uint64_t t0 = p.t_chunk + (uint64_t)s_begin;
+    const uint32_t m_begin = p.batch_mseg[b], m_end = p.batch_mseg[b + 1];
+    const uint64_t t0 = p.t_chunk + (uint64_t)b * (uint64_t)p.batch;
     const float eta = p.eta[b];
     const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 5) * G::GPW;
-    // every group of the warp runs the same number of iterations (shuffles)
-    const int64_t first = seg_begin + ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * G::GPW;
-    for (int64_t sg0 = first; sg0 < seg_end; sg0 += groups) {
-        const int64_t sg = sg0 + grp;
-        segment_item<D, DT>(p, (uint32_t)sg, lig, lane, sg < seg_end, eta, t0, false);
-    }
+    for (int64_t m = m_begin + ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * G::GPW + grp; m < m_end; m += groups)
+        segment_item<D, DT, false>(p, (uint32_t)m, lig, true, eta, t0);
 }
 
 // ---------------------------------------------------------------------------
 // Persistent schedule: one cooperative launch per chunk.  Work items in a
-// fixed order - batch 0's sample items, batch 0's segment items, batch 1's
-// sample items, ... - are dealt round robin to the warps; every warp walks
+// fixed order - batch 0's sample items, batch 0's shared-segment items, batch
+// 1's sample items, ... - are dealt round robin to the warps; every warp walks
 // its items in increasing order.  An item waits only on items earlier in that
 // order, so the earliest unfinished item can always run (all warps are
 // resident): the schedule cannot deadlock, and every wait is bounded anyway.
-//   sample item (batch b): rows it reads must hold their values after the
-//     last batch that touched them: for a row of batch b-1 it waits on that
-//     segment's flag; batches b-2 and b-3 must be fully applied (by
-//     induction this covers every earlier batch).
-//   segment item (batch b): waits for the sample items of its entries (they
-//     wrote the slab entries and are the only readers of the row's
-//     batch-start value).
+//   sample item: before reading a row it waits for the latest earlier
+//     segment of that row in the chunk (written by a sample item when it was
+//     a singleton, by a segment item otherwise); it then writes its singleton
+//     rows and publishes them, and counts its shared contributions in.
+//   segment item: waits until all contributions of its segment are in, sums
+//     them, writes the row and publishes it.
 // ---------------------------------------------------------------------------
-constexpr int kPersistThreads = 256;   // 8 warps per block
-constexpr int kPersistMinBlocks = 3;   // <= 85 registers: 24 warps per SM
-
-__device__ __forceinline__ bool batch_applied_ok(const DataParams& p, int bb) {
-    if (bb < 0) return true;
-    const uint32_t need = p.batch_seg[bb + 1] - p.batch_seg[bb];
-    return wait_geq(p.batch_applied + bb, need, p.spin_limit, p.abort_word);
-}
+constexpr int kPersistThreads = 256;  // 8 warps per block
+constexpr int kPersistMinBlocks = 3;
 
 __device__ __forceinline__ void fail_abort(const DataParams& p) {
     atomicOr(p.status, DEV_ERR_TIMEOUT);
@@ -393,12 +426,10 @@ __global__ void __launch_bounds__(kPersistThreads, kPersistMinBlocks) k_persiste
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane / G::L, lig = lane % G::L;
     const int wpb = blockDim.x >> 5;
-    const int R = p.K + 2;
     float* stage = smem + (size_t)warp * (p.K + 1) * 32 * G::E;
     const uint64_t W = (uint64_t)gridDim.x * wpb;
     const uint64_t total = p.item_base[p.n_batches];
     int b = 0;
-    int checked_b = -1;
     for (uint64_t t = (uint64_t)blockIdx.x * wpb + warp; t < total; t += W) {
         while (t >= p.item_base[b + 1]) ++b;
         if (*(volatile uint32_t*)p.abort_word) return;
@@ -408,103 +439,20 @@ __global__ void __launch_bounds__(kPersistThreads, kPersistMinBlocks) k_persiste
         const uint64_t nA = (uint64_t)((nb + G::GPW - 1) / G::GPW);
         const uint64_t t0 = p.t_chunk + (uint64_t)s_begin;
         const float eta = p.eta[b];
+        bool ok;
         if (local < nA) {
-            if (checked_b != b) {
-                if (!batch_applied_ok(p, b - 2) || !batch_applied_ok(p, b - 3)) {
-                    fail_abort(p);
-                    return;
-                }
-                checked_b = b;
-            }
             const int64_t s_local = s_begin + (int64_t)local * G::GPW + grp;
-            const bool active = s_local < s_begin + nb;
-            bool ok = true;
-            if (active) {
-                for (int k = lig; k < R; k += G::L) {
-                    const int32_t ps = p.prev_seg[s_local * R + k];
-                    if (ps >= 0 && !wait_geq(p.seg_done + ps, p.gen, p.spin_limit, p.abort_word)) ok = false;
-                }
-            }
-            if (!__all_sync(0xFFFFFFFFu, ok)) {
-                fail_abort(p);
-                return;
-            }
-            sample_item<D, DT>(p, s_local, lig, lane, active, eta, stage);
-            __syncwarp();
-            if (active && lig == 0) st_release(p.sample_done + s_local, p.gen);
+            ok = sample_item<D, DT, true>(p, s_local, lig, lane, s_local < s_begin + nb, eta, t0, stage);
         } else {
-            const uint32_t seg = p.batch_seg[b] + (uint32_t)((local - nA) * G::GPW) + grp;
-            const bool active = seg < p.batch_seg[b + 1];
-            const bool ok = segment_item<D, DT>(p, seg, lig, lane, active, eta, t0, true);
-            if (!__all_sync(0xFFFFFFFFu, ok)) {
-                fail_abort(p);
-                return;
-            }
-            // the group's row stores are ordered before the flag by the warp
-            // barrier; the release store publishes them
+            const uint32_t m = p.batch_mseg[b] + (uint32_t)((local - nA) * G::GPW) + grp;
+            const bool active = m < p.batch_mseg[b + 1];
+            ok = segment_item<D, DT, true>(p, m, lig, active, eta, t0);
             __syncwarp();
-            if (active && lig == 0) {
-                st_release(p.seg_done + seg, p.gen);
-                red_release_add(p.batch_applied + b, 1u);
-            }
+            if (ok && active && lig == 0) st_release(p.seg_done + p.mseg_id[m], p.gen);
         }
-    }
-}
-
-// eta[b] = lr0 (schedule 0) or lr0 * max(1 - t0/T, floor) (schedule 1) for
-// the batch starting at global sample t0 = t_chunk + b * batch; FP64 once per
-// batch, used as FP32.
-__global__ void k_batch_eta(int n_batches, uint64_t t_chunk, int64_t batch, double lr0, int schedule, double floor_frac,
-                            uint64_t total, float* __restrict__ eta) {
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= n_batches) return;
-    double f = 1.0;
-    if (schedule == 1) {
-        f = 1.0 - (double)(t_chunk + (uint64_t)b * (uint64_t)batch) / (double)total;
-        if (f < floor_frac) f = floor_frac;
-    }
-    eta[b] = (float)(lr0 * f);
-}
-
-// item_base[b] = first work item of batch b (sample items then segment items).
-__global__ void k_item_base(const uint32_t* __restrict__ batch_seg, int n_batches, int64_t batch,
-                            int64_t chunk_samples, int gpw, uint64_t* __restrict__ item_base) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    uint64_t acc = 0;
-    for (int b = 0; b < n_batches; ++b) {
-        item_base[b] = acc;
-        const int64_t nb = min(batch, chunk_samples - (int64_t)b * batch);
-        acc += (uint64_t)((nb + gpw - 1) / gpw);
-        acc += (uint64_t)((batch_seg[b + 1] - batch_seg[b] + gpw - 1) / gpw);
-    }
-    item_base[n_batches] = acc;
-}
-
-// prev_seg[(sample, slot)] = segment of the same row in the previous batch of
-// the chunk, or -1.  One thread per segment: binary search among the previous
-// batch's segment keys, then written for every entry of the segment.
-__global__ void k_prev_seg(const uint64_t* __restrict__ items, const uint32_t* __restrict__ seg_start,
-                           const uint32_t* n_segs_p, const uint32_t* __restrict__ batch_seg, uint32_t row_bits,
-                           uint32_t R, int32_t* __restrict__ prev_seg) {
-    const uint32_t n_segs = *n_segs_p;
-    const uint32_t mask = (1u << row_bits) - 1u;
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n_segs; j += gridDim.x * blockDim.x) {
-        const uint32_t key = (uint32_t)(items[seg_start[j]] >> 32);
-        const uint32_t b = key >> row_bits;
-        int32_t ps = -1;
-        if (b > 0) {
-            const uint32_t want = ((b - 1) << row_bits) | (key & mask);
-            uint32_t lo = batch_seg[b - 1], hi = batch_seg[b];
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if ((uint32_t)(items[seg_start[mid]] >> 32) < want) lo = mid + 1;
-                else hi = mid;
-            }
-            if (lo < batch_seg[b] && (uint32_t)(items[seg_start[lo]] >> 32) == want) ps = (int32_t)lo;
-        }
-        for (uint32_t i = seg_start[j]; i < seg_start[j + 1]; ++i) {
-            const uint32_t v = (uint32_t)items[i];
-            prev_seg[(v >> kSlotBits) * R + (v & kSlotMask)] = ps;
+        if (!__all_sync(0xFFFFFFFFu, ok)) {
+            if (lane == 0) fail_abort(p);
+            return;
         }
     }
 }
@@ -659,17 +607,124 @@ struct OutSegStart {
     }
 };
 
-// batch_seg[b] = first segment of batch b; batch_seg[n_batches] = n_segs.
-__global__ void k_batch_seg(const uint64_t* __restrict__ items, const uint32_t* __restrict__ seg_start,
-                            const uint32_t* n_segs_p, uint32_t row_bits, int n_batches, uint32_t* __restrict__ batch_seg) {
+// Per segment j: slot_info of every entry = {sorted position | singleton
+// bit, j}; for the persistent schedule, rowitems[j] = (row << 32) | j.
+__global__ void k_seg_meta(const uint64_t* __restrict__ items, const uint32_t* __restrict__ seg_start,
+                           const uint32_t* n_segs_p, uint32_t row_bits, uint32_t R, uint2* __restrict__ slot_info,
+                           uint64_t* __restrict__ rowitems) {
     const uint32_t n_segs = *n_segs_p;
+    const uint32_t mask = (1u << row_bits) - 1u;
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n_segs; j += gridDim.x * blockDim.x) {
-        const int bj = (int)((uint32_t)(items[seg_start[j]] >> 32) >> row_bits);
-        const int bp = j ? (int)((uint32_t)(items[seg_start[j - 1]] >> 32) >> row_bits) : -1;
-        for (int b = bp + 1; b <= bj; ++b) batch_seg[b] = j;
-        if (j + 1 == n_segs)
-            for (int b = bj + 1; b <= n_batches; ++b) batch_seg[b] = n_segs;
+        const uint32_t begin = seg_start[j], end = seg_start[j + 1];
+        const uint32_t single = end - begin == 1 ? kSingleBit : 0u;
+        for (uint32_t i = begin; i < end; ++i) {
+            const uint32_t v = (uint32_t)items[i];
+            slot_info[(v >> kSlotBits) * R + (v & kSlotMask)] = make_uint2(i | single, j);
+        }
+        if (rowitems) rowitems[j] = ((uint64_t)((uint32_t)(items[begin] >> 32) & mask) << 32) | j;
     }
+}
+
+// Shared segments (two or more entries) get a descriptor.
+struct GenMulti {
+    const uint32_t* seg_start;
+    const uint32_t* n_segs;
+    __device__ uint32_t operator()(int64_t j) const {
+        return (j < (int64_t)*n_segs && seg_start[j + 1] - seg_start[j] > 1) ? 1u : 0u;
+    }
+};
+struct OutMulti {
+    const uint64_t* items;
+    const uint32_t* seg_start;
+    const uint32_t* n_segs;
+    int64_t n;
+    int K;
+    uint4* mdesc;
+    uint32_t* mseg_id;
+    uint32_t* n_mseg;
+    __device__ void operator()(int64_t j, uint32_t excl, uint32_t incl) const {
+        if (j < (int64_t)*n_segs) {
+            const uint32_t begin = seg_start[j], end = seg_start[j + 1];
+            if (end - begin > 1) {
+                uint32_t cnt = 0;
+                for (uint32_t i = begin; i < end; ++i) cnt += ((uint32_t)items[i] & kSlotMask) == 0 ? (uint32_t)K + 1 : 1u;
+                mdesc[excl] = make_uint4(begin, end - begin, (uint32_t)(items[begin] >> 32), cnt);
+                mseg_id[excl] = (uint32_t)j;
+            }
+        }
+        if (j == n - 1) *n_mseg = incl;
+    }
+};
+
+// batch_mseg[b] = first shared segment of batch b; batch_mseg[n_batches] = count.
+__global__ void k_batch_mseg(const uint4* __restrict__ mdesc, const uint32_t* n_mseg_p, uint32_t row_bits,
+                             int n_batches, uint32_t* __restrict__ batch_mseg) {
+    const uint32_t nm = *n_mseg_p;
+    if (nm == 0) {
+        for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= n_batches; b += gridDim.x * blockDim.x) batch_mseg[b] = 0;
+        return;
+    }
+    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < nm; m += gridDim.x * blockDim.x) {
+        const int bm = (int)(mdesc[m].z >> row_bits);
+        const int bp = m ? (int)(mdesc[m - 1].z >> row_bits) : -1;
+        for (int b = bp + 1; b <= bm; ++b) batch_mseg[b] = m;
+        if (m + 1 == nm)
+            for (int b = bm + 1; b <= n_batches; ++b) batch_mseg[b] = nm;
+    }
+}
+
+// rowitems sorted by row (stable, so batches ascend within a row): the latest
+// earlier segment of the same row precedes each segment.
+__global__ void k_prev_seg(const uint64_t* __restrict__ sorted, const uint32_t* n_segs_p, int32_t* __restrict__ prev) {
+    const uint32_t n_segs = *n_segs_p;
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n_segs; k += gridDim.x * blockDim.x) {
+        const uint64_t cur = sorted[k];
+        int32_t pv = -1;
+        if (k > 0 && (sorted[k - 1] >> 32) == (cur >> 32)) pv = (int32_t)(uint32_t)sorted[k - 1];
+        prev[(uint32_t)cur] = pv;
+    }
+}
+
+__global__ void k_slot_prev(const uint2* __restrict__ slot_info, const int32_t* __restrict__ prev, int64_t n_items,
+                            int32_t* __restrict__ slot_prev) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_items; i += (int64_t)gridDim.x * blockDim.x)
+        slot_prev[i] = prev[slot_info[i].y];
+}
+
+// Padding for the row sort: ids past n_segs sort after every real row.
+__global__ void k_pad_rowitems(uint64_t* __restrict__ rowitems, const uint32_t* n_segs_p, int64_t n, uint32_t pad) {
+    const int64_t n_segs = *n_segs_p;
+    for (int64_t j = n_segs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
+        rowitems[j] = ((uint64_t)pad << 32) | (uint64_t)j;
+}
+
+// eta[b] = lr0 (schedule 0) or lr0 * max(1 - t0/T, floor) (schedule 1) for
+// the batch starting at global sample t0 = t_chunk + b * batch; FP64 once per
+// batch, used as FP32.
+__global__ void k_batch_eta(int n_batches, uint64_t t_chunk, int64_t batch, double lr0, int schedule, double floor_frac,
+                            uint64_t total, float* __restrict__ eta) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= n_batches) return;
+    double f = 1.0;
+    if (schedule == 1) {
+        f = 1.0 - (double)(t_chunk + (uint64_t)b * (uint64_t)batch) / (double)total;
+        if (f < floor_frac) f = floor_frac;
+    }
+    eta[b] = (float)(lr0 * f);
+}
+
+// item_base[b] = first work item of batch b (sample items, then shared-segment items).
+__global__ void k_item_base(const uint32_t* __restrict__ batch_mseg, int n_batches, int64_t batch,
+                            int64_t chunk_samples, int gpw, uint64_t* __restrict__ item_base) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    uint64_t acc = 0;
+    for (int b = 0; b < n_batches; ++b) {
+        item_base[b] = acc;
+        const int64_t nb = min(batch, chunk_samples - (int64_t)b * batch);
+        acc += (uint64_t)((nb + gpw - 1) / gpw);
+        acc += (uint64_t)((batch_mseg[b + 1] - batch_mseg[b] + gpw - 1) / gpw);
+    }
+    item_base[n_batches] = acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -693,8 +748,8 @@ struct Buf {
 };
 
 struct TrainWorkspace {
-    Buf rec, items0, items1, hist, scan_tiles, seg_start, batch_seg, counters, slab;
-    Buf sample_done, seg_done, batch_applied, prev_seg, item_base, eta;
+    Buf rec, items0, items1, hist, scan_tiles, seg_start, counters, eta, slab, slot_info, mdesc, mseg_id, batch_mseg;
+    Buf rowitems0, rowitems1, prev, slot_prev, seg_done, arrive, item_base;
     std::vector<cudaEvent_t> events;  // timing events, three per chunk
     uint32_t gen = 0;
     cudaError_t event(size_t i, cudaEvent_t* out) {
@@ -722,16 +777,42 @@ static uint32_t bits_for(uint64_t v) {  // bits to hold values 0..v-1
     return b;
 }
 
+// Stable LSD radix sort of n items by key bits [32, 32 + bits); the result is
+// left in *result (a or b).
+static cudaError_t radix_sort(uint64_t* a, uint64_t* b, int64_t n, uint32_t bits, uint32_t* hist, uint32_t* scan_buf,
+                              cudaStream_t s, uint64_t** result, int* launches) {
+    const int tiles = (int)((n + kRsTile - 1) / kRsTile);
+    uint64_t* in = a;
+    uint64_t* out = b;
+    for (uint32_t sh = 0; sh < bits; sh += kRsBits) {
+        k_radix_hist<<<tiles, kRsThreads, 0, s>>>(in, n, 32 + (int)sh, hist, tiles);
+        cudaError_t e = device_scan<uint32_t>((int64_t)kRsBins * tiles, GenU32{hist}, OutExcl32{hist}, scan_buf, s);
+        if (e != cudaSuccess) return e;
+        k_radix_scatter<<<tiles, kRsThreads, 0, s>>>(in, out, n, 32 + (int)sh, hist, tiles);
+        std::swap(in, out);
+        *launches += 5;
+    }
+    *result = in;
+    return cudaGetLastError();
+}
+
+template <int D, int DT>
+static int gather_warps(const DataParams& p, int requested, int cap, size_t* smem_out) {
+    using G = Geom<D, DT>;
+    // staging: (K+1) context rows x 32 lanes x E floats per warp
+    const size_t per_warp = (size_t)(p.K + 1) * 32 * G::E * sizeof(float);
+    int wpb = requested > 0 ? requested : 8;
+    wpb = std::min<int>(wpb, cap);
+    wpb = std::max<int>(1, std::min<int>(wpb, (int)(kMaxSmem / per_warp)));
+    *smem_out = (size_t)wpb * per_warp;
+    return wpb;
+}
+
 template <int D, int DT>
 static cudaError_t launch_data_batched(const DataParams& p, int warps_per_block, cudaStream_t s) {
     using G = Geom<D, DT>;
-    // staging: (K+1) context rows x 32 lanes x E floats per warp; at most
-    // kMaxSmem per block, at most kMaxWarps warps
-    const size_t per_warp = (size_t)(p.K + 1) * 32 * G::E * sizeof(float);
-    int wpb = warps_per_block > 0 ? warps_per_block : 8;
-    wpb = std::min<int>(wpb, kMaxWarps);
-    wpb = std::max<int>(1, std::min<int>(wpb, (int)(kMaxSmem / per_warp)));
-    const size_t smem = (size_t)wpb * per_warp;
+    size_t smem = 0;
+    const int wpb = gather_warps<D, DT>(p, warps_per_block, kMaxWarps, &smem);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_gather<D, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
@@ -742,8 +823,9 @@ static cudaError_t launch_data_batched(const DataParams& p, int warps_per_block,
         const int64_t nb = std::min<int64_t>(p.batch, p.chunk_samples - (int64_t)b * p.batch);
         const unsigned g1 = (unsigned)((nb + per_block - 1) / per_block);
         k_gather<D, DT><<<g1, wpb * 32, smem, s>>>(p, b);
-        const int64_t max_segs = nb * (p.K + 2);
-        const unsigned g2 = (unsigned)std::min<int64_t>((max_segs + per_block - 1) / per_block, 152 * 16);
+        // a shared segment has two or more of the batch's nb * (K+2) entries
+        const int64_t max_m = nb * (p.K + 2) / 2 + 1;
+        const unsigned g2 = (unsigned)std::min<int64_t>((max_m + per_block - 1) / per_block, 152 * 8);
         k_apply<D, DT><<<g2, wpb * 32, 0, s>>>(p, b);
     }
     return cudaGetLastError();
@@ -751,12 +833,8 @@ static cudaError_t launch_data_batched(const DataParams& p, int warps_per_block,
 
 template <int D, int DT>
 static cudaError_t launch_data_persistent(const DataParams& p, int warps_per_block, cudaStream_t s) {
-    using G = Geom<D, DT>;
-    const size_t per_warp = (size_t)(p.K + 1) * 32 * G::E * sizeof(float);
-    int wpb = warps_per_block > 0 ? warps_per_block : 8;
-    wpb = std::min<int>(wpb, kPersistThreads / 32);
-    wpb = std::max<int>(1, std::min<int>(wpb, (int)(kMaxSmem / per_warp)));
-    const size_t smem = (size_t)wpb * per_warp;
+    size_t smem = 0;
+    const int wpb = gather_warps<D, DT>(p, warps_per_block, kPersistThreads / 32, &smem);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_persistent<D, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
@@ -776,10 +854,15 @@ static cudaError_t launch_data_persistent(const DataParams& p, int warps_per_blo
 
 using LaunchFn = cudaError_t (*)(const DataParams&, int, cudaStream_t);
 
-static LaunchFn pick_persistent(int dim, int dtype) {
-#define LINE_PICK(DD)                                                                          \
-    if (dim == DD) return dtype == LINE_DTYPE_F32 ? launch_data_persistent<DD, LINE_DTYPE_F32> \
-                                                  : launch_data_persistent<DD, LINE_DTYPE_BF16>;
+static LaunchFn pick_launcher(int dim, int dtype, bool persistent) {
+#define LINE_PICK(DD)                                                                                   \
+    if (dim == DD) {                                                                                    \
+        if (persistent)                                                                                 \
+            return dtype == LINE_DTYPE_F32 ? launch_data_persistent<DD, LINE_DTYPE_F32>                 \
+                                           : launch_data_persistent<DD, LINE_DTYPE_BF16>;               \
+        return dtype == LINE_DTYPE_F32 ? launch_data_batched<DD, LINE_DTYPE_F32>                        \
+                                       : launch_data_batched<DD, LINE_DTYPE_BF16>;                      \
+    }
     LINE_PICK(16)
     LINE_PICK(32)
     LINE_PICK(64)
@@ -795,19 +878,6 @@ static int groups_per_warp(int dim, int dtype) {
     return 32 / L;
 }
 
-static LaunchFn pick_batched(int dim, int dtype) {
-#define LINE_PICK(DD)                                                                       \
-    if (dim == DD) return dtype == LINE_DTYPE_F32 ? launch_data_batched<DD, LINE_DTYPE_F32> \
-                                                  : launch_data_batched<DD, LINE_DTYPE_BF16>;
-    LINE_PICK(16)
-    LINE_PICK(32)
-    LINE_PICK(64)
-    LINE_PICK(128)
-    LINE_PICK(256)
-#undef LINE_PICK
-    return nullptr;
-}
-
 cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, TrainTimes* times, cudaStream_t s,
                       std::string* err) {
     const int R = a.K + 2;
@@ -815,16 +885,15 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     if (n_samples == 0) return cudaSuccess;
     const uint64_t rows_space = a.order == 2 ? 2ull * (uint64_t)a.n_nodes : (uint64_t)a.n_nodes;
     const uint32_t row_bits = bits_for(rows_space);
-    if (row_bits > 31) {
+    if (row_bits > 30) {
         *err = "too many nodes for 32-bit sort keys";
         return cudaErrorInvalidValue;
     }
-    // batches per chunk: about 2^18 samples, limited by the key bits and by
-    // 32-bit item values (chunk samples * (K+2) < 2^32)
+    // batches per chunk: about 2^18 samples, limited by the key bits, by
+    // 31-bit sorted positions and by the chunk-sample field of item values
     int64_t nb_max = (int64_t)1 << (32 - row_bits);
     int64_t nb = a.chunk_batches > 0 ? a.chunk_batches : std::max<int64_t>(1, (int64_t(1) << 18) / a.batch);
     nb = std::min(nb, nb_max);
-    // item values hold the chunk sample in 32 - kSlotBits bits
     while (nb > 1 && ((uint64_t)nb * (uint64_t)a.batch * (uint64_t)R >= (1ull << 31) ||
                       (uint64_t)nb * (uint64_t)a.batch > (1ull << (32 - kSlotBits))))
         nb >>= 1;
@@ -835,6 +904,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     const int64_t max_chunk = nb * a.batch;
     const int64_t max_items = max_chunk * R;
     const int ntiles = (int)((max_items + kRsTile - 1) / kRsTile);
+    const bool persistent = a.mode == LINE_MODE_PERSISTENT;
 
     cudaError_t e;
     auto ensure = [&](Buf& b, size_t bytes) -> bool {
@@ -848,38 +918,33 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         !ensure(ws->items1, sizeof(uint64_t) * max_items) ||
         !ensure(ws->hist, sizeof(uint32_t) * (size_t)kRsBins * ntiles) ||
         !ensure(ws->scan_tiles, sizeof(uint32_t) * (scan_tiles((int64_t)kRsBins * ntiles + max_items) + 2)) ||
-        !ensure(ws->seg_start, sizeof(uint32_t) * (max_items + 1)) ||
-        !ensure(ws->batch_seg, sizeof(uint32_t) * (nb + 1)) || !ensure(ws->counters, 256) ||
-        !ensure(ws->eta, sizeof(float) * (nb + 1)) ||
+        !ensure(ws->seg_start, sizeof(uint32_t) * (max_items + 1)) || !ensure(ws->counters, 256) ||
+        !ensure(ws->eta, sizeof(float) * (nb + 1)) || !ensure(ws->slot_info, sizeof(uint2) * max_items) ||
+        !ensure(ws->mdesc, sizeof(uint4) * max_items) || !ensure(ws->mseg_id, sizeof(uint32_t) * max_items) ||
+        !ensure(ws->batch_mseg, sizeof(uint32_t) * (nb + 1)) ||
         !ensure(ws->slab, sizeof(float) * (size_t)max_items * a.dim))
         return e;
-    const bool persistent = a.mode == LINE_MODE_PERSISTENT;
     if (persistent) {
-        if (!ensure(ws->prev_seg, sizeof(int32_t) * max_items) || !ensure(ws->item_base, sizeof(uint64_t) * (nb + 1)) ||
-            !ensure(ws->batch_applied, sizeof(uint32_t) * (nb + 1)))
+        if (!ensure(ws->rowitems0, sizeof(uint64_t) * max_items) || !ensure(ws->rowitems1, sizeof(uint64_t) * max_items) ||
+            !ensure(ws->prev, sizeof(int32_t) * max_items) || !ensure(ws->slot_prev, sizeof(int32_t) * max_items) ||
+            !ensure(ws->arrive, sizeof(uint32_t) * max_items) || !ensure(ws->item_base, sizeof(uint64_t) * (nb + 1)))
             return e;
         // generation flags start at zero and are never reset: a chunk's
         // flags are "done" when they equal its generation number
-        const size_t need_s = sizeof(uint32_t) * max_chunk, need_g = sizeof(uint32_t) * (max_items + 1);
-        if (ws->sample_done.cap < need_s) {
-            if (!ensure(ws->sample_done, need_s)) return e;
-            if ((e = cudaMemsetAsync(ws->sample_done.p, 0, need_s, s)) != cudaSuccess) return e;
-            ws->gen = 0;
-        }
-        if (ws->seg_done.cap < need_g) {
-            if (!ensure(ws->seg_done, need_g)) return e;
-            if ((e = cudaMemsetAsync(ws->seg_done.p, 0, need_g, s)) != cudaSuccess) return e;
-            if ((e = cudaMemsetAsync(ws->sample_done.p, 0, ws->sample_done.cap, s)) != cudaSuccess) return e;
+        const size_t need = sizeof(uint32_t) * max_items;
+        if (ws->seg_done.cap < need) {
+            if (!ensure(ws->seg_done, need)) return e;
+            if ((e = cudaMemsetAsync(ws->seg_done.p, 0, need, s)) != cudaSuccess) return e;
             ws->gen = 0;
         }
     }
-    LaunchFn data = persistent ? pick_persistent(a.dim, a.dtype) : pick_batched(a.dim, a.dtype);
+    LaunchFn data = pick_launcher(a.dim, a.dtype, persistent);
     if (!data) {
         *err = "unsupported dim";
         return cudaErrorInvalidValue;
     }
 
-    PrepassParams pp;
+    PrepassParams pp{};
     pp.src = a.src;
     pp.dst = a.dst;
     pp.edge_tab = a.edge_tab;
@@ -893,15 +958,21 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     pp.row_bits = row_bits;
     pp.rec = (int32_t*)ws->rec.p;
 
+    uint32_t* n_segs_dev = (uint32_t*)ws->counters.p;
+    uint32_t* n_mseg_dev = (uint32_t*)ws->counters.p + 1;
+    uint32_t* abort_word = (uint32_t*)ws->counters.p + 16;
+
     DataParams dp{};
-    dp.U = nullptr;
+    dp.U = a.U;
+    dp.C = a.order == 2 ? a.C : a.U;
     dp.order = a.order;
     dp.K = a.K;
     dp.n_nodes = a.n_nodes;
     dp.row_bits = row_bits;
     dp.rec = (const int32_t*)ws->rec.p;
-    dp.seg_start = (const uint32_t*)ws->seg_start.p;
-    dp.batch_seg = (const uint32_t*)ws->batch_seg.p;
+    dp.slot_info = (const uint2*)ws->slot_info.p;
+    dp.mdesc = (const uint4*)ws->mdesc.p;
+    dp.batch_mseg = (const uint32_t*)ws->batch_mseg.p;
     dp.slab = (float*)ws->slab.p;
     dp.batch = a.batch;
     dp.seed = a.seed;
@@ -909,32 +980,31 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     dp.lambda = (float)a.lambda;
     dp.alpha_neg = (float)a.alpha_neg;
     dp.status = status;
-    dp.U = a.U;
-    dp.C = a.order == 2 ? a.C : a.U;
-
-    uint32_t* n_segs_dev = (uint32_t*)ws->counters.p;
-    uint32_t* abort_word = (uint32_t*)ws->counters.p + 16;
-    dp.sample_done = (uint32_t*)ws->sample_done.p;
+    dp.slot_prev = (const int32_t*)ws->slot_prev.p;
+    dp.mseg_id = (const uint32_t*)ws->mseg_id.p;
     dp.seg_done = (uint32_t*)ws->seg_done.p;
-    dp.batch_applied = (uint32_t*)ws->batch_applied.p;
-    dp.prev_seg = (const int32_t*)ws->prev_seg.p;
+    dp.arrive = (uint32_t*)ws->arrive.p;
     dp.item_base = (const uint64_t*)ws->item_base.p;
     dp.spin_limit = a.spin_limit;
     dp.abort_word = abort_word;
+
     size_t n_ev = 0;
     struct ChunkRec {
         int64_t samples;
         int batches;
+        int prepass_launches;
     };
     std::vector<ChunkRec> chunk_log;
-    cudaEvent_t ev_a = nullptr, ev_b = nullptr, ev_c = nullptr;
+    cudaEvent_t ev = nullptr;
+    const unsigned seg_grid = (unsigned)std::min<int64_t>((max_items + 255) / 256, 152 * 16);
     for (uint64_t t = a.t_begin; t < a.t_end; t += (uint64_t)max_chunk) {
         const int64_t cs = (int64_t)std::min<uint64_t>((uint64_t)max_chunk, a.t_end - t);
         const int cb = (int)((cs + a.batch - 1) / a.batch);
         const int64_t n_items = cs * R;
+        int launches = 0;
         if (a.timing) {
-            if ((e = ws->event(n_ev, &ev_a)) != cudaSuccess) return e;
-            cudaEventRecord(ev_a, s);
+            if ((e = ws->event(n_ev, &ev)) != cudaSuccess) return e;
+            cudaEventRecord(ev, s);
         }
         // 1. draws
         pp.t_chunk = t;
@@ -944,70 +1014,74 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
             const int64_t work = cs * (a.K + 1);
             const unsigned g = (unsigned)std::min<int64_t>((work + 255) / 256, 152 * 64);
             k_chunk_draws<<<g, 256, 0, s>>>(pp);
+            k_batch_eta<<<(unsigned)((cb + 127) / 128), 128, 0, s>>>(cb, t, a.batch, a.lr0, a.lr_schedule, a.lr_floor,
+                                                                     a.lr_total, (float*)ws->eta.p);
+            launches += 2;
         }
-        // 2. stable LSD radix sort by key bits [32, 32 + key_bits)
-        uint64_t* in = (uint64_t*)ws->items0.p;
-        uint64_t* out = (uint64_t*)ws->items1.p;
-        const int tiles = (int)((n_items + kRsTile - 1) / kRsTile);
-        uint32_t* hist = (uint32_t*)ws->hist.p;
-        for (uint32_t sh = 0; sh < key_bits; sh += kRsBits) {
-            k_radix_hist<<<tiles, kRsThreads, 0, s>>>(in, n_items, 32 + (int)sh, hist, tiles);
-            if ((e = device_scan<uint32_t>((int64_t)kRsBins * tiles, GenU32{hist}, OutExcl32{hist},
-                                           (uint32_t*)ws->scan_tiles.p, s)) != cudaSuccess)
-                return e;
-            k_radix_scatter<<<tiles, kRsThreads, 0, s>>>(in, out, n_items, 32 + (int)sh, hist, tiles);
-            std::swap(in, out);
-        }
-        // 3. segments
-        if ((e = device_scan<uint32_t>(n_items, GenHead{in},
-                                       OutSegStart{in, (uint32_t*)ws->seg_start.p, n_items, n_segs_dev},
+        // 2. stable sort by (batch, row)
+        uint64_t* sorted = nullptr;
+        if ((e = radix_sort((uint64_t*)ws->items0.p, (uint64_t*)ws->items1.p, n_items, key_bits, (uint32_t*)ws->hist.p,
+                            (uint32_t*)ws->scan_tiles.p, s, &sorted, &launches)) != cudaSuccess)
+            return e;
+        // 3. segments, slot positions, shared-segment descriptors
+        if ((e = device_scan<uint32_t>(n_items, GenHead{sorted},
+                                       OutSegStart{sorted, (uint32_t*)ws->seg_start.p, n_items, n_segs_dev},
                                        (uint32_t*)ws->scan_tiles.p, s)) != cudaSuccess)
             return e;
-        k_batch_eta<<<(unsigned)((cb + 127) / 128), 128, 0, s>>>(cb, t, a.batch, a.lr0, a.lr_schedule, a.lr_floor,
-                                                                 a.lr_total, (float*)ws->eta.p);
-        k_batch_seg<<<(unsigned)std::min<int64_t>((n_items + 255) / 256, 152 * 16), 256, 0, s>>>(
-            in, (const uint32_t*)ws->seg_start.p, n_segs_dev, row_bits, cb, (uint32_t*)ws->batch_seg.p);
-        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        k_seg_meta<<<seg_grid, 256, 0, s>>>(sorted, (const uint32_t*)ws->seg_start.p, n_segs_dev, row_bits, (uint32_t)R,
+                                            (uint2*)ws->slot_info.p, persistent ? (uint64_t*)ws->rowitems0.p : nullptr);
+        OutMulti om{sorted, (const uint32_t*)ws->seg_start.p, n_segs_dev, n_items, a.K,
+                    (uint4*)ws->mdesc.p, (uint32_t*)ws->mseg_id.p, n_mseg_dev};
+        if ((e = device_scan<uint32_t>(n_items, GenMulti{(const uint32_t*)ws->seg_start.p, n_segs_dev}, om,
+                                       (uint32_t*)ws->scan_tiles.p, s)) != cudaSuccess)
+            return e;
+        k_batch_mseg<<<seg_grid, 256, 0, s>>>((const uint4*)ws->mdesc.p, n_mseg_dev, row_bits, cb,
+                                              (uint32_t*)ws->batch_mseg.p);
+        launches += 3 + 1 + 3 + 1;
         if (persistent) {
-            const unsigned gs = (unsigned)std::min<int64_t>((n_items + 255) / 256, 152 * 16);
-            k_prev_seg<<<gs, 256, 0, s>>>(in, (const uint32_t*)ws->seg_start.p, n_segs_dev, (const uint32_t*)ws->batch_seg.p,
-                                          row_bits, (uint32_t)R, (int32_t*)ws->prev_seg.p);
-            k_item_base<<<1, 32, 0, s>>>((const uint32_t*)ws->batch_seg.p, cb, a.batch, cs,
+            // latest earlier segment of each row: sort segments by row
+            k_pad_rowitems<<<seg_grid, 256, 0, s>>>((uint64_t*)ws->rowitems0.p, n_segs_dev, n_items, 1u << row_bits);
+            uint64_t* rsorted = nullptr;
+            if ((e = radix_sort((uint64_t*)ws->rowitems0.p, (uint64_t*)ws->rowitems1.p, n_items, row_bits + 1,
+                                (uint32_t*)ws->hist.p, (uint32_t*)ws->scan_tiles.p, s, &rsorted, &launches)) != cudaSuccess)
+                return e;
+            k_prev_seg<<<seg_grid, 256, 0, s>>>(rsorted, n_segs_dev, (int32_t*)ws->prev.p);
+            k_slot_prev<<<seg_grid, 256, 0, s>>>((const uint2*)ws->slot_info.p, (const int32_t*)ws->prev.p, n_items,
+                                                 (int32_t*)ws->slot_prev.p);
+            k_item_base<<<1, 32, 0, s>>>((const uint32_t*)ws->batch_mseg.p, cb, a.batch, cs,
                                          groups_per_warp(a.dim, a.dtype), (uint64_t*)ws->item_base.p);
-            if ((e = cudaMemsetAsync(ws->batch_applied.p, 0, sizeof(uint32_t) * (cb + 1), s)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(ws->arrive.p, 0, sizeof(uint32_t) * n_items, s)) != cudaSuccess) return e;
             if ((e = cudaMemsetAsync(abort_word, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-            if ((e = cudaGetLastError()) != cudaSuccess) return e;
+            launches += 4;
             dp.gen = ++ws->gen;
         }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (a.timing) {
-            if ((e = ws->event(n_ev + 1, &ev_b)) != cudaSuccess) return e;
-            cudaEventRecord(ev_b, s);
+            if ((e = ws->event(n_ev + 1, &ev)) != cudaSuccess) return e;
+            cudaEventRecord(ev, s);
         }
         // data phase
-        dp.items = in;
         dp.t_chunk = t;
         dp.chunk_samples = cs;
         dp.n_batches = cb;
         if ((e = data(dp, a.warps_per_block, s)) != cudaSuccess) return e;
         if (a.timing) {
-            if ((e = ws->event(n_ev + 2, &ev_c)) != cudaSuccess) return e;
-            cudaEventRecord(ev_c, s);
+            if ((e = ws->event(n_ev + 2, &ev)) != cudaSuccess) return e;
+            cudaEventRecord(ev, s);
             n_ev += 3;
-            chunk_log.push_back({cs, cb});
+            chunk_log.push_back({cs, cb, launches});
         }
     }
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (a.timing && n_ev) {
         if ((e = cudaEventSynchronize(ws->events[n_ev - 1])) != cudaSuccess) return e;
-        const int64_t passes = (key_bits + kRsBits - 1) / kRsBits;
         for (size_t i = 0; i < chunk_log.size(); ++i) {
             float ms1 = 0, ms2 = 0;
             cudaEventElapsedTime(&ms1, ws->events[3 * i], ws->events[3 * i + 1]);
             cudaEventElapsedTime(&ms2, ws->events[3 * i + 1], ws->events[3 * i + 2]);
             times->prepass_ms += ms1;
             times->update_ms += ms2;
-            // draws + per pass (hist, 3 scan launches, scatter) + segment scan (3) + batch_seg
-            times->prepass_launches += 1 + 5 * passes + 5 + (persistent ? 2 : 0);
+            times->prepass_launches += chunk_log[i].prepass_launches;
             times->update_launches += persistent ? 1 : 2 * (int64_t)chunk_log[i].batches;
             times->update_samples += (uint64_t)chunk_log[i].samples;
         }
