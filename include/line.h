@@ -192,6 +192,28 @@ LINE_API line_status line_set_embeddings(line_ctx* ctx, int order, int which, co
  * Result in *out_host (host pointer). */
 LINE_API line_status line_eval_loss(line_ctx* ctx, int order, int K, uint64_t seed, int64_t m, double* out_host);
 
+/* Largest m accepted by line_eval_loss_noalloc. */
+#define LINE_NOALLOC_MAX_SAMPLES (1 << 20)
+
+/* line_eval_loss without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot call
+ * cudaMalloc while they run - for instance a service that reserved all device
+ * memory for its tables up front and must not grow its footprint, or a
+ * latency-bound loop in which cudaMalloc/cudaFree would synchronise the
+ * device.  The per-sample terms and the partial sums live in one fixed
+ * array of LINE_NOALLOC_MAX_SAMPLES + 1024 doubles (8 MiB + 8 KiB) that every
+ * GPU loading this library holds until the process exits; the result is the
+ * same as line_eval_loss.  m must be 1..LINE_NOALLOC_MAX_SAMPLES, otherwise
+ * LINE_ERR_ARG and nothing runs.  The first call on a device looks up the
+ * array's device address (once per device, that device current); make that
+ * first call before any stream capture.  All calls, from every context, share
+ * the one array: calls whose GPU work overlaps (different streams or
+ * contexts on the same device) race and give wrong results; calls ordered on
+ * one stream are safe, and no state carries over from one call to the next.
+ * Result in *out_host (host pointer). */
+LINE_API line_status line_eval_loss_noalloc(line_ctx* ctx, int order, int K, uint64_t seed, int64_t m,
+                                            double* out_host);
+
 LINE_API line_status line_get_stats(line_ctx* ctx, line_stats* out);
 LINE_API line_status line_reset_stats(line_ctx* ctx);
 

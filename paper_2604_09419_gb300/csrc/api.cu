@@ -468,6 +468,26 @@ line_status line_eval_loss(line_ctx* c, int order, int K, uint64_t seed, int64_t
     return LINE_OK;
 }
 
+line_status line_eval_loss_noalloc(line_ctx* c, int order, int K, uint64_t seed, int64_t m, double* out_host) {
+    line_status st = enter(c);
+    if (st) return st;
+    if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_eval_loss_noalloc: no graph");
+    if (order != 1 && order != 2) return fail(c, LINE_ERR_ARG, "line_eval_loss_noalloc: bad order");
+    Tables& t = c->tab[order];
+    if (!t.ready) return fail(c, LINE_ERR_STATE, "line_eval_loss_noalloc: no tables of order %d", order);
+    if (K < 0 || K > kMaxK || !out_host) return fail(c, LINE_ERR_ARG, "line_eval_loss_noalloc: bad arguments");
+    if (m < 1 || m > LINE_NOALLOC_MAX_SAMPLES)
+        return fail(c, LINE_ERR_ARG, "line_eval_loss_noalloc: m = %lld outside 1..%d (the fixed scratch size)",
+                    (long long)m, LINE_NOALLOC_MAX_SAMPLES);
+    CK(eval_loss_noalloc(c->device, t.U, order == 2 ? t.C : t.U, t.dtype, t.dim, K, c->src, c->dst, c->edge_tab,
+                         c->n_arcs, c->neg_tab, c->n_nodes, seed, m, c->dscratch, c->stream),
+       "line_eval_loss_noalloc");
+    CK(cudaMemcpyAsync(out_host, c->dscratch, sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+       "line_eval_loss_noalloc");
+    CK(cudaStreamSynchronize(c->stream), "line_eval_loss_noalloc");
+    return LINE_OK;
+}
+
 line_status line_get_stats(line_ctx* c, line_stats* out) {
     if (!c || !out) return LINE_ERR_ARG;
     out->update_launches = c->times.update_launches;

@@ -137,7 +137,14 @@ cudaError_t eval_loss_terms(const void* U, const void* Ctx, int dtype, int dim, 
                             const int32_t* dst, const uint2* edge_tab, int64_t n_arcs, const uint2* neg_tab,
                             int64_t n_nodes, uint64_t seed, int64_t m, double* terms, cudaStream_t s);
 
-// train.cu: see TrainPlan there.
+// noalloc.cu: the loss evaluation with its scratch in a fixed device array
+cudaError_t noalloc_scratch_address(int device, double** out);
+cudaError_t eval_loss_noalloc(int device, const void* U, const void* Ctx, int dtype, int dim, int K,
+                              const int32_t* src, const int32_t* dst, const uint2* edge_tab, int64_t n_arcs,
+                              const uint2* neg_tab, int64_t n_nodes, uint64_t seed, int64_t m, double* out_dev,
+                              cudaStream_t s);
+
+// train.cu
 struct TrainArgs {
     int order, dim, K, dtype;
     int64_t n_nodes, n_arcs;

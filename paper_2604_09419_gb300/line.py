@@ -16,6 +16,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libline.so")
 
+NOALLOC_MAX_SAMPLES = 1 << 20
 LINE_OK, LINE_ERR_ARG, LINE_ERR_OOM, LINE_ERR_CUDA, LINE_ERR_TIMEOUT, LINE_ERR_STATE, LINE_ERR_VALIDATE = (
     0, -1, -2, -3, -4, -5, -6)
 DTYPE_F32, DTYPE_BF16 = 0, 1
@@ -67,6 +68,7 @@ def _load():
         "line_get_embeddings": (i32, [vp, i32, i32, vp, i32]),
         "line_set_embeddings": (i32, [vp, i32, i32, vp, i32, vp, i64]),
         "line_eval_loss": (i32, [vp, i32, i32, u64, i64, ctypes.POINTER(dbl)]),
+        "line_eval_loss_noalloc": (i32, [vp, i32, i32, u64, i64, ctypes.POINTER(dbl)]),
         "line_get_stats": (i32, [vp, ctypes.POINTER(Stats)]),
         "line_reset_stats": (i32, [vp]),
         "line_synchronize": (i32, [vp]),
@@ -83,7 +85,7 @@ lib = _load()
 EXPORTED = ("line_train_opts_default", "line_status_string", "line_create", "line_destroy", "line_last_error",
             "line_build_alias", "line_get_graph_info", "line_get_alias", "line_sample_debug",
             "line_init_embeddings", "line_train_steps", "line_get_embeddings", "line_set_embeddings",
-            "line_eval_loss", "line_get_stats", "line_reset_stats", "line_synchronize", "line_debug_wait_timeout")
+            "line_eval_loss", "line_eval_loss_noalloc", "line_get_stats", "line_reset_stats", "line_synchronize", "line_debug_wait_timeout")
 
 
 class LineError(RuntimeError):
@@ -177,6 +179,12 @@ class Context:
     def eval_loss(self, order, K, seed, m) -> float:
         out = ctypes.c_double()
         self._ck(lib.line_eval_loss(self.h, order, K, seed, m, ctypes.byref(out)))
+        return out.value
+
+    def eval_loss_noalloc(self, order, K, seed, m) -> float:
+        """line_eval_loss with no device allocation (scratch in a fixed array)."""
+        out = ctypes.c_double()
+        self._ck(lib.line_eval_loss_noalloc(self.h, order, K, seed, m, ctypes.byref(out)))
         return out.value
 
     def stats(self) -> Stats:
