@@ -134,6 +134,17 @@ __device__ __forceinline__ uint32_t group_mask(int grp) {
     return L == 32 ? 0xFFFFFFFFu : (((1u << L) - 1u) << (grp * L));
 }
 
+// Programmatic dependent launch: let the next kernel of the stream start its
+// prologue, and wait until the previous kernel's writes are visible.
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+// A shared segment's entries are summed in chunks of kChunk: partial sums in
+// entry order, then the partials in chunk order.  Segments longer than one
+// chunk (the hub rows) are summed by a whole CTA in the batched schedule.
+constexpr uint32_t kChunk = 8;
+constexpr uint32_t kLongBit = 1u << 31;  // in mdesc.y: summed by a CTA
+
 // Sort item value: (sample within the chunk) << kSlotBits | slot.
 constexpr uint32_t kSlotBits = 6;
 constexpr uint32_t kSlotMask = (1u << kSlotBits) - 1u;
@@ -153,6 +164,9 @@ struct DataParams {
     const uint2* slot_info;      // [chunk samples][K+2]: {position | singleton bit, segment}
     const uint4* mdesc;          // shared segments: {first position, length, key, pair count}
     const uint32_t* batch_mseg;  // [n_batches + 1] first shared segment of each batch
+    const uint4* ldesc;          // [n_batches][lcap] long shared segments of each batch
+    const uint32_t* lcount;      // [n_batches] number of long shared segments
+    uint32_t lcap;
     float* slab;                 // [chunk samples * (K+2)][D], by sorted position
     uint64_t t_chunk;            // global index of the chunk's first sample
     int64_t chunk_samples;
@@ -191,11 +205,11 @@ __device__ __forceinline__ T rec_entry(uint32_t gm, T held, const T* row, int id
 // Per-sample work.  Returns false when a bounded wait ran out (persistent).
 // ctx_stage: this warp's shared staging area, (K+1) x 32 lanes x E floats.
 // ---------------------------------------------------------------------------
-template <int D, int DT, bool PERSIST>
+template <int D, int DT, bool PERSIST, bool PDL = false>
 __device__ __forceinline__ bool sample_item(const DataParams& p, int64_t s_local, int lig, int lane, bool active,
                                             float eta, uint64_t t0, float* ctx_stage) {
     using G = Geom<D, DT>;
-    constexpr int CH = G::E <= 4 ? 4 : 2;  // context rows in flight per lane
+    constexpr int CH = G::E <= 4 ? 8 : 4;  // context rows in flight per lane
     const int R = p.K + 2;
     const int64_t sbase = (active ? s_local : 0) * R;
     const int32_t* rec = p.rec + sbase;
@@ -203,6 +217,7 @@ __device__ __forceinline__ bool sample_item(const DataParams& p, int64_t s_local
     const uint32_t gm = group_mask<G::L>(lane / G::L);
     const int32_t r0 = (active && lig < R) ? rec[lig] : 0;
     const uint2 i0 = (active && lig < R) ? info[lig] : make_uint2(0u, 0u);
+    if constexpr (PDL) pdl_wait();  // the tables' rows: written by the previous kernel
     bool ok = true;
     if constexpr (PERSIST) {
         // rows written by an earlier segment of this chunk: wait for it
@@ -317,11 +332,12 @@ __device__ __forceinline__ bool segment_item(const DataParams& p, uint32_t m, in
     using G = Geom<D, DT>;
     constexpr int PF = G::E <= 4 ? 8 : 4;  // slab entries in flight per lane
     if (!active) return true;
-    const uint4 d = p.mdesc[m];  // {first position, length, key, pair count}
+    const uint4 d = p.mdesc[m];  // {first position, length | long bit, key, pair count}
+    const uint32_t len = d.y & ~kLongBit;
     if constexpr (PERSIST) {
         // all contributions written (and, through them, every read of the
         // row's batch-start value and the row's previous write done)
-        if (!wait_geq(p.arrive + p.mseg_id[m], d.y, p.spin_limit, p.abort_word)) return false;
+        if (!wait_geq(p.arrive + p.mseg_id[m], len, p.spin_limit, p.abort_word)) return false;
     }
     const uint32_t rowid = d.z & ((1u << p.row_bits) - 1u);
     const bool is_c = p.order == 2 && rowid >= (uint32_t)p.n_nodes;
@@ -333,28 +349,36 @@ __device__ __forceinline__ bool segment_item(const DataParams& p, uint32_t m, in
 #pragma unroll
     for (int e = 0; e < G::E; ++e) acc[e] = 0.0f;
     const float* base = p.slab + (int64_t)d.x * D + lig * G::E;
-    for (uint32_t k0 = 0; k0 < d.y; k0 += PF) {
-        float4 buf[PF][G::E / 4];
+    for (uint32_t c0 = 0; c0 < len; c0 += kChunk) {
+        float part[G::E];
 #pragma unroll
-        for (int kk = 0; kk < PF; ++kk) {
-            if (k0 + kk < d.y) {
-                const float4* src = reinterpret_cast<const float4*>(base + (int64_t)(k0 + kk) * D);
+        for (int e = 0; e < G::E; ++e) part[e] = 0.0f;
 #pragma unroll
-                for (int q = 0; q < G::E / 4; ++q) buf[kk][q] = ld_cg(src + q);
+        for (uint32_t k0 = 0; k0 < kChunk; k0 += PF) {
+            float4 buf[PF][G::E / 4];
+#pragma unroll
+            for (int kk = 0; kk < PF; ++kk) {
+                if (c0 + k0 + kk < len) {
+                    const float4* src = reinterpret_cast<const float4*>(base + (int64_t)(c0 + k0 + kk) * D);
+#pragma unroll
+                    for (int q = 0; q < G::E / 4; ++q) buf[kk][q] = ld_cg(src + q);
+                }
             }
-        }
 #pragma unroll
-        for (int kk = 0; kk < PF; ++kk) {
-            if (k0 + kk < d.y) {
+            for (int kk = 0; kk < PF; ++kk) {
+                if (c0 + k0 + kk < len) {
 #pragma unroll
-                for (int q = 0; q < G::E / 4; ++q) {
-                    acc[4 * q] += buf[kk][q].x;
-                    acc[4 * q + 1] += buf[kk][q].y;
-                    acc[4 * q + 2] += buf[kk][q].z;
-                    acc[4 * q + 3] += buf[kk][q].w;
+                    for (int q = 0; q < G::E / 4; ++q) {
+                        part[4 * q] += buf[kk][q].x;
+                        part[4 * q + 1] += buf[kk][q].y;
+                        part[4 * q + 2] += buf[kk][q].z;
+                        part[4 * q + 3] += buf[kk][q].w;
+                    }
                 }
             }
         }
+#pragma unroll
+        for (int e = 0; e < G::E; ++e) acc[e] += part[e];
     }
     const float decay = (float)d.w * (eta * p.lambda);
 #pragma unroll
@@ -363,37 +387,129 @@ __device__ __forceinline__ bool segment_item(const DataParams& p, uint32_t m, in
     return true;
 }
 
+// A long shared segment summed by the 8 warps of a CTA: warp w sums chunks
+// w, w+8, ... (entry order within a chunk); warp 0 adds the chunk partials in
+// chunk order - the same order as segment_item.  Uses lane group 0 of each
+// warp.  part: shared, 8 x D floats.
+template <int D, int DT>
+__device__ __forceinline__ void long_segment_cta(const DataParams& p, uint4 d, float eta, uint64_t t0, float* part) {
+    using G = Geom<D, DT>;
+    constexpr int PF = G::E <= 4 ? 8 : 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool mine = lane < G::L;  // group 0 of the warp
+    const int lig = lane;
+    const uint32_t len = d.y & ~kLongBit;
+    const uint32_t n_chunks = (len + kChunk - 1) / kChunk;
+    float acc[G::E];
+#pragma unroll
+    for (int e = 0; e < G::E; ++e) acc[e] = 0.0f;
+    const float* base = p.slab + (int64_t)d.x * D + (mine ? lig : 0) * G::E;
+    for (uint32_t r0 = 0; r0 < n_chunks; r0 += 8) {
+        const uint32_t c = r0 + (uint32_t)warp;
+        if (mine && c < n_chunks) {
+            float pt[G::E];
+#pragma unroll
+            for (int e = 0; e < G::E; ++e) pt[e] = 0.0f;
+            const uint32_t c0 = c * kChunk;
+#pragma unroll
+            for (uint32_t k0 = 0; k0 < kChunk; k0 += PF) {
+                float4 buf[PF][G::E / 4];
+#pragma unroll
+                for (int kk = 0; kk < PF; ++kk) {
+                    if (c0 + k0 + kk < len) {
+                        const float4* src = reinterpret_cast<const float4*>(base + (int64_t)(c0 + k0 + kk) * D);
+#pragma unroll
+                        for (int q = 0; q < G::E / 4; ++q) buf[kk][q] = ld_cg(src + q);
+                    }
+                }
+#pragma unroll
+                for (int kk = 0; kk < PF; ++kk) {
+                    if (c0 + k0 + kk < len) {
+#pragma unroll
+                        for (int q = 0; q < G::E / 4; ++q) {
+                            pt[4 * q] += buf[kk][q].x;
+                            pt[4 * q + 1] += buf[kk][q].y;
+                            pt[4 * q + 2] += buf[kk][q].z;
+                            pt[4 * q + 3] += buf[kk][q].w;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int e = 0; e < G::E; ++e) part[warp * D + lig * G::E + e] = pt[e];
+        }
+        __syncthreads();
+        if (warp == 0 && mine) {
+            const uint32_t nr = min(8u, n_chunks - r0);
+            for (uint32_t w = 0; w < nr; ++w)
+#pragma unroll
+                for (int e = 0; e < G::E; ++e) acc[e] += part[w * D + lig * G::E + e];
+        }
+        __syncthreads();
+    }
+    if (warp == 0 && mine) {
+        const uint32_t rowid = d.z & ((1u << p.row_bits) - 1u);
+        const bool is_c = p.order == 2 && rowid >= (uint32_t)p.n_nodes;
+        void* table = is_c ? p.C : p.U;
+        const int64_t row = is_c ? (int64_t)rowid - p.n_nodes : (int64_t)rowid;
+        float x[G::E];
+        load_row<D, DT>(table, row, lig, x);
+        const float decay = (float)d.w * (eta * p.lambda);
+#pragma unroll
+        for (int e = 0; e < G::E; ++e) x[e] = fmaf(-decay, x[e], x[e]) + acc[e];
+        store_row<D, DT>(table, row, lig, x, p.seed, t0, is_c ? 1u : 0u);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Batched schedule: one launch per phase per batch.
 // ---------------------------------------------------------------------------
 constexpr int kMaxWarps = 16;
 constexpr size_t kMaxSmem = 200 * 1024;
 
-template <int D, int DT>
+template <int D, int DT, bool PDL>
 __global__ void __launch_bounds__(kMaxWarps * 32) k_gather(DataParams p, int b) {
     using G = Geom<D, DT>;
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
+    if constexpr (PDL) pdl_launch_dependents();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane / G::L, lig = lane % G::L;
     const int64_t s_begin = (int64_t)b * p.batch;
     const int64_t s_end = min(s_begin + p.batch, p.chunk_samples);
     const int64_t s_local = s_begin + ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * G::GPW + grp;
     float* stage = smem + (size_t)warp * (p.K + 1) * 32 * G::E;
-    sample_item<D, DT, false>(p, s_local, lig, lane, s_local < s_end, p.eta[b], p.t_chunk + (uint64_t)s_begin, stage);
+    sample_item<D, DT, false, PDL>(p, s_local, lig, lane, s_local < s_end, p.eta[b], p.t_chunk + (uint64_t)s_begin,
+                                   stage);
 }
 
+// Blocks [0, g_long) take the batch's long shared segments, one per CTA; the
+// other blocks take the short ones, one per lane group.  8 warps per block.
+constexpr int kApplyThreads = 256;
+
 template <int D, int DT>
-__global__ void __launch_bounds__(kMaxWarps * 32) k_apply(DataParams p, int b) {
+__global__ void __launch_bounds__(kApplyThreads) k_apply(DataParams p, int b, int g_long) {
     using G = Geom<D, DT>;
+    __shared__ float part[8 * D];
+    pdl_launch_dependents();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane / G::L, lig = lane % G::L;
     const uint32_t m_begin = p.batch_mseg[b], m_end = p.batch_mseg[b + 1];
+    const uint32_t n_long = p.lcount[b];
     const uint64_t t0 = p.t_chunk + (uint64_t)b * (uint64_t)p.batch;
     const float eta = p.eta[b];
-    const int64_t groups = (int64_t)gridDim.x * (blockDim.x >> 5) * G::GPW;
-    for (int64_t m = m_begin + ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * G::GPW + grp; m < m_end; m += groups)
+    pdl_wait();  // the slab and the rows: written by the gather
+    if ((int)blockIdx.x < g_long) {
+        for (uint32_t l = blockIdx.x; l < n_long; l += (uint32_t)g_long)
+            long_segment_cta<D, DT>(p, p.ldesc[(size_t)b * p.lcap + l], eta, t0, part);
+        return;
+    }
+    const int64_t groups = (int64_t)(gridDim.x - g_long) * (blockDim.x >> 5) * G::GPW;
+    for (int64_t m = m_begin + ((int64_t)(blockIdx.x - g_long) * (blockDim.x >> 5) + warp) * G::GPW + grp; m < m_end;
+         m += groups) {
+        if (p.mdesc[m].y & kLongBit) continue;
         segment_item<D, DT, false>(p, (uint32_t)m, lig, true, eta, t0);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -642,13 +758,27 @@ struct OutMulti {
     uint4* mdesc;
     uint32_t* mseg_id;
     uint32_t* n_mseg;
+    uint32_t row_bits;
+    uint4* ldesc;
+    uint32_t* lcount;
+    uint32_t lcap;
     __device__ void operator()(int64_t j, uint32_t excl, uint32_t incl) const {
         if (j < (int64_t)*n_segs) {
             const uint32_t begin = seg_start[j], end = seg_start[j + 1];
             if (end - begin > 1) {
                 uint32_t cnt = 0;
                 for (uint32_t i = begin; i < end; ++i) cnt += ((uint32_t)items[i] & kSlotMask) == 0 ? (uint32_t)K + 1 : 1u;
-                mdesc[excl] = make_uint4(begin, end - begin, (uint32_t)(items[begin] >> 32), cnt);
+                const uint32_t key = (uint32_t)(items[begin] >> 32);
+                uint32_t len = end - begin;
+                if (len > kChunk) {
+                    // the batch's long list (its order does not matter: each
+                    // long segment is summed by one CTA)
+                    const uint32_t b = key >> row_bits;
+                    const uint32_t l = atomicAdd(lcount + b, 1u);
+                    ldesc[(size_t)b * lcap + l] = make_uint4(begin, len, key, cnt);
+                    len |= kLongBit;
+                }
+                mdesc[excl] = make_uint4(begin, len, key, cnt);
                 mseg_id[excl] = (uint32_t)j;
             }
         }
@@ -749,6 +879,7 @@ struct Buf {
 
 struct TrainWorkspace {
     Buf rec, items0, items1, hist, scan_tiles, seg_start, counters, eta, slab, slot_info, mdesc, mseg_id, batch_mseg;
+    Buf ldesc, lcount;
     Buf rowitems0, rowitems1, prev, slot_prev, seg_done, arrive, item_base;
     std::vector<cudaEvent_t> events;  // timing events, three per chunk
     uint32_t gen = 0;
@@ -808,6 +939,22 @@ static int gather_warps(const DataParams& p, int requested, int cap, size_t* sme
     return wpb;
 }
 
+template <typename... Args, typename... Vals>
+static cudaError_t launch_pdl(void (*kern)(Args...), unsigned grid, unsigned block, size_t smem, cudaStream_t s,
+                              bool pdl, Vals... vals) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, vals...);
+}
+
 template <int D, int DT>
 static cudaError_t launch_data_batched(const DataParams& p, int warps_per_block, cudaStream_t s) {
     using G = Geom<D, DT>;
@@ -815,19 +962,28 @@ static cudaError_t launch_data_batched(const DataParams& p, int warps_per_block,
     const int wpb = gather_warps<D, DT>(p, warps_per_block, kMaxWarps, &smem);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_gather<D, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        cudaFuncSetAttribute(k_gather<D, DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
+        cudaFuncSetAttribute(k_gather<D, DT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
         attr_set = true;
     }
     const int64_t per_block = (int64_t)wpb * G::GPW;
-    for (int b = 0; b < p.n_batches; ++b) {
+    const int64_t apply_per_block = (int64_t)(kApplyThreads / 32) * G::GPW;
+    const int g_long = 16;
+    cudaError_t e = cudaSuccess;
+    for (int b = 0; b < p.n_batches && e == cudaSuccess; ++b) {
         const int64_t nb = std::min<int64_t>(p.batch, p.chunk_samples - (int64_t)b * p.batch);
         const unsigned g1 = (unsigned)((nb + per_block - 1) / per_block);
-        k_gather<D, DT><<<g1, wpb * 32, smem, s>>>(p, b);
+        // the chunk's first gather follows the pre-pass with a full dependency;
+        // later launches overlap their start with the previous kernel's tail
+        if (b == 0) e = launch_pdl(k_gather<D, DT, false>, g1, wpb * 32, smem, s, false, p, b);
+        else e = launch_pdl(k_gather<D, DT, true>, g1, wpb * 32, smem, s, true, p, b);
+        if (e != cudaSuccess) break;
         // a shared segment has two or more of the batch's nb * (K+2) entries
         const int64_t max_m = nb * (p.K + 2) / 2 + 1;
-        const unsigned g2 = (unsigned)std::min<int64_t>((max_m + per_block - 1) / per_block, 152 * 8);
-        k_apply<D, DT><<<g2, wpb * 32, 0, s>>>(p, b);
+        const unsigned g2 = (unsigned)std::min<int64_t>((max_m + apply_per_block - 1) / apply_per_block, 152 * 4);
+        e = launch_pdl(k_apply<D, DT>, (unsigned)g_long + g2, kApplyThreads, 0, s, true, p, b, g_long);
     }
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 
@@ -905,6 +1061,8 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     const int64_t max_items = max_chunk * R;
     const int ntiles = (int)((max_items + kRsTile - 1) / kRsTile);
     const bool persistent = a.mode == LINE_MODE_PERSISTENT;
+    // long shared segments (more than kChunk entries) per batch, at most
+    const uint32_t lcap = (uint32_t)(a.batch * R / (kChunk + 1) + 1);
 
     cudaError_t e;
     auto ensure = [&](Buf& b, size_t bytes) -> bool {
@@ -922,6 +1080,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         !ensure(ws->eta, sizeof(float) * (nb + 1)) || !ensure(ws->slot_info, sizeof(uint2) * max_items) ||
         !ensure(ws->mdesc, sizeof(uint4) * max_items) || !ensure(ws->mseg_id, sizeof(uint32_t) * max_items) ||
         !ensure(ws->batch_mseg, sizeof(uint32_t) * (nb + 1)) ||
+        !ensure(ws->ldesc, sizeof(uint4) * (size_t)nb * lcap) || !ensure(ws->lcount, sizeof(uint32_t) * (nb + 1)) ||
         !ensure(ws->slab, sizeof(float) * (size_t)max_items * a.dim))
         return e;
     if (persistent) {
@@ -973,6 +1132,9 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     dp.slot_info = (const uint2*)ws->slot_info.p;
     dp.mdesc = (const uint4*)ws->mdesc.p;
     dp.batch_mseg = (const uint32_t*)ws->batch_mseg.p;
+    dp.ldesc = (const uint4*)ws->ldesc.p;
+    dp.lcount = (const uint32_t*)ws->lcount.p;
+    dp.lcap = lcap;
     dp.slab = (float*)ws->slab.p;
     dp.batch = a.batch;
     dp.seed = a.seed;
@@ -1030,8 +1192,10 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
             return e;
         k_seg_meta<<<seg_grid, 256, 0, s>>>(sorted, (const uint32_t*)ws->seg_start.p, n_segs_dev, row_bits, (uint32_t)R,
                                             (uint2*)ws->slot_info.p, persistent ? (uint64_t*)ws->rowitems0.p : nullptr);
+        if ((e = cudaMemsetAsync(ws->lcount.p, 0, sizeof(uint32_t) * (cb + 1), s)) != cudaSuccess) return e;
         OutMulti om{sorted, (const uint32_t*)ws->seg_start.p, n_segs_dev, n_items, a.K,
-                    (uint4*)ws->mdesc.p, (uint32_t*)ws->mseg_id.p, n_mseg_dev};
+                    (uint4*)ws->mdesc.p, (uint32_t*)ws->mseg_id.p, n_mseg_dev, row_bits,
+                    (uint4*)ws->ldesc.p, (uint32_t*)ws->lcount.p, lcap};
         if ((e = device_scan<uint32_t>(n_items, GenMulti{(const uint32_t*)ws->seg_start.p, n_segs_dev}, om,
                                        (uint32_t*)ws->scan_tiles.p, s)) != cudaSuccess)
             return e;
