@@ -877,11 +877,23 @@ struct Buf {
     }
 };
 
+// Per-chunk outputs of the pre-pass, read by the data phase.  Two sets: the
+// pre-pass of chunk c+1 (on its own low-priority stream) fills one while the
+// data phase of chunk c reads the other.
+struct ChunkSet {
+    Buf rec, slot_info, mdesc, mseg_id, batch_mseg, ldesc, lcount, eta, slot_prev, arrive, item_base;
+    cudaEvent_t prep_done = nullptr;  // pre-pass of the set's current chunk finished
+    cudaEvent_t data_done = nullptr;  // data phase of the set's previous chunk finished
+    bool data_pending = false;
+};
+
 struct TrainWorkspace {
-    Buf rec, items0, items1, hist, scan_tiles, seg_start, counters, eta, slab, slot_info, mdesc, mseg_id, batch_mseg;
-    Buf ldesc, lcount;
-    Buf rowitems0, rowitems1, prev, slot_prev, seg_done, arrive, item_base;
-    std::vector<cudaEvent_t> events;  // timing events, three per chunk
+    Buf items0, items1, hist, scan_tiles, seg_start, counters, slab, rowitems0, rowitems1, prev, seg_done;
+    ChunkSet set[2];
+    cudaStream_t prep = nullptr;    // pre-pass stream
+    cudaEvent_t start = nullptr;    // caller-stream work before the call
+    cudaEvent_t prep_end = nullptr; // last pre-pass of the call
+    std::vector<cudaEvent_t> events;  // timing events
     uint32_t gen = 0;
     cudaError_t event(size_t i, cudaEvent_t* out) {
         while (events.size() <= i) {
@@ -893,14 +905,37 @@ struct TrainWorkspace {
         *out = events[i];
         return cudaSuccess;
     }
+    cudaError_t init(int device) {
+        if (prep) return cudaSuccess;
+        int lo = 0, hi = 0;
+        cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
+        if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&prep, cudaStreamNonBlocking, lo);
+        for (auto& cs : set) {
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&cs.prep_done, cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&cs.data_done, cudaEventDisableTiming);
+        }
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&start, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&prep_end, cudaEventDisableTiming);
+        (void)device;
+        return e;
+    }
+    ~TrainWorkspace() {
+        if (prep) {
+            cudaStreamSynchronize(prep);
+            cudaStreamDestroy(prep);
+        }
+        for (auto& cs : set) {
+            if (cs.prep_done) cudaEventDestroy(cs.prep_done);
+            if (cs.data_done) cudaEventDestroy(cs.data_done);
+        }
+        if (start) cudaEventDestroy(start);
+        if (prep_end) cudaEventDestroy(prep_end);
+        for (auto e : events) cudaEventDestroy(e);
+    }
 };
 
 TrainWorkspace* workspace_create() { return new TrainWorkspace(); }
-void workspace_destroy(TrainWorkspace* ws) {
-    if (!ws) return;
-    for (auto e : ws->events) cudaEventDestroy(e);
-    delete ws;
-}
+void workspace_destroy(TrainWorkspace* ws) { delete ws; }
 
 static uint32_t bits_for(uint64_t v) {  // bits to hold values 0..v-1
     uint32_t b = 1;
@@ -1072,21 +1107,33 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         }
         return true;
     };
-    if (!ensure(ws->rec, sizeof(int32_t) * max_items) || !ensure(ws->items0, sizeof(uint64_t) * max_items) ||
-        !ensure(ws->items1, sizeof(uint64_t) * max_items) ||
+    int device = 0;
+    if ((e = cudaGetDevice(&device)) != cudaSuccess) return e;
+    if ((e = ws->init(device)) != cudaSuccess) return e;
+    // a set still in use by an earlier call's data phase is not reallocated
+    // before that phase is done
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+    if (!ensure(ws->items0, sizeof(uint64_t) * max_items) || !ensure(ws->items1, sizeof(uint64_t) * max_items) ||
         !ensure(ws->hist, sizeof(uint32_t) * (size_t)kRsBins * ntiles) ||
         !ensure(ws->scan_tiles, sizeof(uint32_t) * (scan_tiles((int64_t)kRsBins * ntiles + max_items) + 2)) ||
         !ensure(ws->seg_start, sizeof(uint32_t) * (max_items + 1)) || !ensure(ws->counters, 256) ||
-        !ensure(ws->eta, sizeof(float) * (nb + 1)) || !ensure(ws->slot_info, sizeof(uint2) * max_items) ||
-        !ensure(ws->mdesc, sizeof(uint4) * max_items) || !ensure(ws->mseg_id, sizeof(uint32_t) * max_items) ||
-        !ensure(ws->batch_mseg, sizeof(uint32_t) * (nb + 1)) ||
-        !ensure(ws->ldesc, sizeof(uint4) * (size_t)nb * lcap) || !ensure(ws->lcount, sizeof(uint32_t) * (nb + 1)) ||
         !ensure(ws->slab, sizeof(float) * (size_t)max_items * a.dim))
         return e;
+    for (auto& cs : ws->set) {
+        if (!ensure(cs.rec, sizeof(int32_t) * max_items) || !ensure(cs.eta, sizeof(float) * (nb + 1)) ||
+            !ensure(cs.slot_info, sizeof(uint2) * max_items) || !ensure(cs.mdesc, sizeof(uint4) * max_items) ||
+            !ensure(cs.mseg_id, sizeof(uint32_t) * max_items) || !ensure(cs.batch_mseg, sizeof(uint32_t) * (nb + 1)) ||
+            !ensure(cs.ldesc, sizeof(uint4) * (size_t)nb * lcap) || !ensure(cs.lcount, sizeof(uint32_t) * (nb + 1)))
+            return e;
+        if (persistent && (!ensure(cs.slot_prev, sizeof(int32_t) * max_items) ||
+                           !ensure(cs.arrive, sizeof(uint32_t) * max_items) ||
+                           !ensure(cs.item_base, sizeof(uint64_t) * (nb + 1))))
+            return e;
+        cs.data_pending = false;
+    }
     if (persistent) {
         if (!ensure(ws->rowitems0, sizeof(uint64_t) * max_items) || !ensure(ws->rowitems1, sizeof(uint64_t) * max_items) ||
-            !ensure(ws->prev, sizeof(int32_t) * max_items) || !ensure(ws->slot_prev, sizeof(int32_t) * max_items) ||
-            !ensure(ws->arrive, sizeof(uint32_t) * max_items) || !ensure(ws->item_base, sizeof(uint64_t) * (nb + 1)))
+            !ensure(ws->prev, sizeof(int32_t) * max_items))
             return e;
         // generation flags start at zero and are never reset: a chunk's
         // flags are "done" when they equal its generation number
@@ -1102,6 +1149,10 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         *err = "unsupported dim";
         return cudaErrorInvalidValue;
     }
+    cudaStream_t ps = ws->prep;
+    // the pre-pass reads the graph and alias tables made on the caller's stream
+    if ((e = cudaEventRecord(ws->start, s)) != cudaSuccess) return e;
+    if ((e = cudaStreamWaitEvent(ps, ws->start, 0)) != cudaSuccess) return e;
 
     PrepassParams pp{};
     pp.src = a.src;
@@ -1115,7 +1166,6 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     pp.K = a.K;
     pp.order = a.order;
     pp.row_bits = row_bits;
-    pp.rec = (int32_t*)ws->rec.p;
 
     uint32_t* n_segs_dev = (uint32_t*)ws->counters.p;
     uint32_t* n_mseg_dev = (uint32_t*)ws->counters.p + 1;
@@ -1128,126 +1178,145 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     dp.K = a.K;
     dp.n_nodes = a.n_nodes;
     dp.row_bits = row_bits;
-    dp.rec = (const int32_t*)ws->rec.p;
-    dp.slot_info = (const uint2*)ws->slot_info.p;
-    dp.mdesc = (const uint4*)ws->mdesc.p;
-    dp.batch_mseg = (const uint32_t*)ws->batch_mseg.p;
-    dp.ldesc = (const uint4*)ws->ldesc.p;
-    dp.lcount = (const uint32_t*)ws->lcount.p;
     dp.lcap = lcap;
     dp.slab = (float*)ws->slab.p;
     dp.batch = a.batch;
     dp.seed = a.seed;
-    dp.eta = (const float*)ws->eta.p;
     dp.lambda = (float)a.lambda;
     dp.alpha_neg = (float)a.alpha_neg;
     dp.status = status;
-    dp.slot_prev = (const int32_t*)ws->slot_prev.p;
-    dp.mseg_id = (const uint32_t*)ws->mseg_id.p;
     dp.seg_done = (uint32_t*)ws->seg_done.p;
-    dp.arrive = (uint32_t*)ws->arrive.p;
-    dp.item_base = (const uint64_t*)ws->item_base.p;
     dp.spin_limit = a.spin_limit;
     dp.abort_word = abort_word;
 
-    size_t n_ev = 0;
     struct ChunkRec {
         int64_t samples;
         int batches;
         int prepass_launches;
+        size_t ev;  // events ev, ev+1 (pre-pass stream), ev+2, ev+3 (data stream)
     };
     std::vector<ChunkRec> chunk_log;
+    size_t n_ev = 0;
     cudaEvent_t ev = nullptr;
     const unsigned seg_grid = (unsigned)std::min<int64_t>((max_items + 255) / 256, 152 * 16);
-    for (uint64_t t = a.t_begin; t < a.t_end; t += (uint64_t)max_chunk) {
+    int c = 0;
+    for (uint64_t t = a.t_begin; t < a.t_end; t += (uint64_t)max_chunk, ++c) {
+        ChunkSet& cset = ws->set[c & 1];
         const int64_t cs = (int64_t)std::min<uint64_t>((uint64_t)max_chunk, a.t_end - t);
         const int cb = (int)((cs + a.batch - 1) / a.batch);
         const int64_t n_items = cs * R;
         int launches = 0;
+        // ---- pre-pass of chunk c on the pre-pass stream, into set c % 2,
+        // once the data phase of chunk c-2 (the set's last reader) is done
+        if (cset.data_pending && (e = cudaStreamWaitEvent(ps, cset.data_done, 0)) != cudaSuccess) return e;
         if (a.timing) {
             if ((e = ws->event(n_ev, &ev)) != cudaSuccess) return e;
-            cudaEventRecord(ev, s);
+            cudaEventRecord(ev, ps);
         }
-        // 1. draws
         pp.t_chunk = t;
         pp.chunk_samples = cs;
+        pp.rec = (int32_t*)cset.rec.p;
         pp.items = (uint64_t*)ws->items0.p;
         {
             const int64_t work = cs * (a.K + 1);
             const unsigned g = (unsigned)std::min<int64_t>((work + 255) / 256, 152 * 64);
-            k_chunk_draws<<<g, 256, 0, s>>>(pp);
-            k_batch_eta<<<(unsigned)((cb + 127) / 128), 128, 0, s>>>(cb, t, a.batch, a.lr0, a.lr_schedule, a.lr_floor,
-                                                                     a.lr_total, (float*)ws->eta.p);
+            k_chunk_draws<<<g, 256, 0, ps>>>(pp);
+            k_batch_eta<<<(unsigned)((cb + 127) / 128), 128, 0, ps>>>(cb, t, a.batch, a.lr0, a.lr_schedule, a.lr_floor,
+                                                                      a.lr_total, (float*)cset.eta.p);
             launches += 2;
         }
-        // 2. stable sort by (batch, row)
+        // stable sort by (batch, row)
         uint64_t* sorted = nullptr;
         if ((e = radix_sort((uint64_t*)ws->items0.p, (uint64_t*)ws->items1.p, n_items, key_bits, (uint32_t*)ws->hist.p,
-                            (uint32_t*)ws->scan_tiles.p, s, &sorted, &launches)) != cudaSuccess)
+                            (uint32_t*)ws->scan_tiles.p, ps, &sorted, &launches)) != cudaSuccess)
             return e;
-        // 3. segments, slot positions, shared-segment descriptors
+        // segments, slot positions, shared-segment descriptors
         if ((e = device_scan<uint32_t>(n_items, GenHead{sorted},
                                        OutSegStart{sorted, (uint32_t*)ws->seg_start.p, n_items, n_segs_dev},
-                                       (uint32_t*)ws->scan_tiles.p, s)) != cudaSuccess)
+                                       (uint32_t*)ws->scan_tiles.p, ps)) != cudaSuccess)
             return e;
-        k_seg_meta<<<seg_grid, 256, 0, s>>>(sorted, (const uint32_t*)ws->seg_start.p, n_segs_dev, row_bits, (uint32_t)R,
-                                            (uint2*)ws->slot_info.p, persistent ? (uint64_t*)ws->rowitems0.p : nullptr);
-        if ((e = cudaMemsetAsync(ws->lcount.p, 0, sizeof(uint32_t) * (cb + 1), s)) != cudaSuccess) return e;
+        k_seg_meta<<<seg_grid, 256, 0, ps>>>(sorted, (const uint32_t*)ws->seg_start.p, n_segs_dev, row_bits,
+                                             (uint32_t)R, (uint2*)cset.slot_info.p,
+                                             persistent ? (uint64_t*)ws->rowitems0.p : nullptr);
+        if ((e = cudaMemsetAsync(cset.lcount.p, 0, sizeof(uint32_t) * (cb + 1), ps)) != cudaSuccess) return e;
         OutMulti om{sorted, (const uint32_t*)ws->seg_start.p, n_segs_dev, n_items, a.K,
-                    (uint4*)ws->mdesc.p, (uint32_t*)ws->mseg_id.p, n_mseg_dev, row_bits,
-                    (uint4*)ws->ldesc.p, (uint32_t*)ws->lcount.p, lcap};
+                    (uint4*)cset.mdesc.p, (uint32_t*)cset.mseg_id.p, n_mseg_dev, row_bits,
+                    (uint4*)cset.ldesc.p, (uint32_t*)cset.lcount.p, lcap};
         if ((e = device_scan<uint32_t>(n_items, GenMulti{(const uint32_t*)ws->seg_start.p, n_segs_dev}, om,
-                                       (uint32_t*)ws->scan_tiles.p, s)) != cudaSuccess)
+                                       (uint32_t*)ws->scan_tiles.p, ps)) != cudaSuccess)
             return e;
-        k_batch_mseg<<<seg_grid, 256, 0, s>>>((const uint4*)ws->mdesc.p, n_mseg_dev, row_bits, cb,
-                                              (uint32_t*)ws->batch_mseg.p);
+        k_batch_mseg<<<seg_grid, 256, 0, ps>>>((const uint4*)cset.mdesc.p, n_mseg_dev, row_bits, cb,
+                                               (uint32_t*)cset.batch_mseg.p);
         launches += 3 + 1 + 3 + 1;
         if (persistent) {
             // latest earlier segment of each row: sort segments by row
-            k_pad_rowitems<<<seg_grid, 256, 0, s>>>((uint64_t*)ws->rowitems0.p, n_segs_dev, n_items, 1u << row_bits);
+            k_pad_rowitems<<<seg_grid, 256, 0, ps>>>((uint64_t*)ws->rowitems0.p, n_segs_dev, n_items, 1u << row_bits);
             uint64_t* rsorted = nullptr;
             if ((e = radix_sort((uint64_t*)ws->rowitems0.p, (uint64_t*)ws->rowitems1.p, n_items, row_bits + 1,
-                                (uint32_t*)ws->hist.p, (uint32_t*)ws->scan_tiles.p, s, &rsorted, &launches)) != cudaSuccess)
+                                (uint32_t*)ws->hist.p, (uint32_t*)ws->scan_tiles.p, ps, &rsorted, &launches)) !=
+                cudaSuccess)
                 return e;
-            k_prev_seg<<<seg_grid, 256, 0, s>>>(rsorted, n_segs_dev, (int32_t*)ws->prev.p);
-            k_slot_prev<<<seg_grid, 256, 0, s>>>((const uint2*)ws->slot_info.p, (const int32_t*)ws->prev.p, n_items,
-                                                 (int32_t*)ws->slot_prev.p);
-            k_item_base<<<1, 32, 0, s>>>((const uint32_t*)ws->batch_mseg.p, cb, a.batch, cs,
-                                         groups_per_warp(a.dim, a.dtype), (uint64_t*)ws->item_base.p);
-            if ((e = cudaMemsetAsync(ws->arrive.p, 0, sizeof(uint32_t) * n_items, s)) != cudaSuccess) return e;
-            if ((e = cudaMemsetAsync(abort_word, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+            k_prev_seg<<<seg_grid, 256, 0, ps>>>(rsorted, n_segs_dev, (int32_t*)ws->prev.p);
+            k_slot_prev<<<seg_grid, 256, 0, ps>>>((const uint2*)cset.slot_info.p, (const int32_t*)ws->prev.p, n_items,
+                                                  (int32_t*)cset.slot_prev.p);
+            k_item_base<<<1, 32, 0, ps>>>((const uint32_t*)cset.batch_mseg.p, cb, a.batch, cs,
+                                          groups_per_warp(a.dim, a.dtype), (uint64_t*)cset.item_base.p);
+            if ((e = cudaMemsetAsync(cset.arrive.p, 0, sizeof(uint32_t) * n_items, ps)) != cudaSuccess) return e;
             launches += 4;
-            dp.gen = ++ws->gen;
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (a.timing) {
             if ((e = ws->event(n_ev + 1, &ev)) != cudaSuccess) return e;
-            cudaEventRecord(ev, s);
+            cudaEventRecord(ev, ps);
         }
-        // data phase
-        dp.t_chunk = t;
-        dp.chunk_samples = cs;
-        dp.n_batches = cb;
-        if ((e = data(dp, a.warps_per_block, s)) != cudaSuccess) return e;
+        if ((e = cudaEventRecord(cset.prep_done, ps)) != cudaSuccess) return e;
+        // ---- data phase of chunk c on the caller's stream
+        if ((e = cudaStreamWaitEvent(s, cset.prep_done, 0)) != cudaSuccess) return e;
         if (a.timing) {
             if ((e = ws->event(n_ev + 2, &ev)) != cudaSuccess) return e;
             cudaEventRecord(ev, s);
-            n_ev += 3;
-            chunk_log.push_back({cs, cb, launches});
         }
+        dp.rec = (const int32_t*)cset.rec.p;
+        dp.slot_info = (const uint2*)cset.slot_info.p;
+        dp.mdesc = (const uint4*)cset.mdesc.p;
+        dp.batch_mseg = (const uint32_t*)cset.batch_mseg.p;
+        dp.ldesc = (const uint4*)cset.ldesc.p;
+        dp.lcount = (const uint32_t*)cset.lcount.p;
+        dp.eta = (const float*)cset.eta.p;
+        dp.slot_prev = (const int32_t*)cset.slot_prev.p;
+        dp.mseg_id = (const uint32_t*)cset.mseg_id.p;
+        dp.arrive = (uint32_t*)cset.arrive.p;
+        dp.item_base = (const uint64_t*)cset.item_base.p;
+        dp.t_chunk = t;
+        dp.chunk_samples = cs;
+        dp.n_batches = cb;
+        if (persistent) {
+            if ((e = cudaMemsetAsync(abort_word, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+            dp.gen = ++ws->gen;
+        }
+        if ((e = data(dp, a.warps_per_block, s)) != cudaSuccess) return e;
+        if (a.timing) {
+            if ((e = ws->event(n_ev + 3, &ev)) != cudaSuccess) return e;
+            cudaEventRecord(ev, s);
+            chunk_log.push_back({cs, cb, launches, n_ev});
+            n_ev += 4;
+        }
+        if ((e = cudaEventRecord(cset.data_done, s)) != cudaSuccess) return e;
+        cset.data_pending = true;
     }
+    // the pre-pass stream's work is all ordered before the last data phase
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     if (a.timing && n_ev) {
         if ((e = cudaEventSynchronize(ws->events[n_ev - 1])) != cudaSuccess) return e;
-        for (size_t i = 0; i < chunk_log.size(); ++i) {
+        for (const ChunkRec& r : chunk_log) {
             float ms1 = 0, ms2 = 0;
-            cudaEventElapsedTime(&ms1, ws->events[3 * i], ws->events[3 * i + 1]);
-            cudaEventElapsedTime(&ms2, ws->events[3 * i + 1], ws->events[3 * i + 2]);
+            cudaEventElapsedTime(&ms1, ws->events[r.ev], ws->events[r.ev + 1]);
+            cudaEventElapsedTime(&ms2, ws->events[r.ev + 2], ws->events[r.ev + 3]);
             times->prepass_ms += ms1;
             times->update_ms += ms2;
-            times->prepass_launches += chunk_log[i].prepass_launches;
-            times->update_launches += persistent ? 1 : 2 * (int64_t)chunk_log[i].batches;
-            times->update_samples += (uint64_t)chunk_log[i].samples;
+            times->prepass_launches += r.prepass_launches;
+            times->update_launches += persistent ? 1 : 2 * (int64_t)r.batches;
+            times->update_samples += (uint64_t)r.samples;
         }
     }
     return cudaSuccess;
