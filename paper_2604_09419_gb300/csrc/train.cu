@@ -2,19 +2,21 @@
 //
 // A call processes its samples in chunks of whole batches.  Per chunk:
 //
-//   pre-pass (index work only; it does not read the tables):
+//   pre-pass (index work only; it does not read the tables), on its own
+//   low-priority stream so that it overlaps the previous chunk's data phase:
 //     1. draws: for every sample its arc (u, v) and K negatives, kept as a
-//        record (u, v, n_1..n_K), and K+2 sort items, one per row the sample
-//        touches: key = (batch, row), value = (sample, slot).  Slot 0 is
-//        U[u]; slots 1..K+1 are the context rows Ctx[v], Ctx[n_j] (Ctx = C
-//        for second order, U for first order; C rows get ids offset by n).
-//     2. a stable LSD radix sort of the items by key; equal keys keep the
-//        (sample, slot) order.
-//     3. segments: one per distinct key = one per (batch, row).  A segment
-//        with one entry is a singleton: its row is read and written by one
-//        sample only.  Every (sample, slot) learns its segment and its
-//        position in the sorted order; segments with two or more entries get
-//        a descriptor (first position, length, key, pair count).
+//        record (u, v, n_1..n_K), and K+2 items, one per row the sample
+//        touches: key = row id, value = (sample, slot).  Slot 0 is U[u];
+//        slots 1..K+1 are the context rows Ctx[v], Ctx[n_j] (Ctx = C for
+//        second order, U for first order; C rows get ids offset by n).
+//     2. per batch, a stable counting sort of the batch's items into 256
+//        buckets by a hash of the row id;
+//     3. per (batch, bucket), a stable sort by row id, then the segments: runs of equal row = the rows the batch touches,
+//        entries in (sample, slot) order.  A segment with one entry is a
+//        singleton: its row is read and written by one sample only.  Every
+//        (sample, slot) learns its position and its segment; segments with
+//        two or more entries ("shared") are listed per batch with their first
+//        position, length, row and pair count.
 //
 //   data phase, batch after batch:
 //     gather  one lane group per sample loads U_b[u] and the K+1 context
@@ -24,17 +26,18 @@
 //             Its contributions are slot 0: sum_j g_j Ctx_b[y_j] for U[u],
 //             slot 1+j: g_j U_b[u] for Ctx[y_j].  A singleton row is written
 //             back at once (Eq. 2-3); a shared row's contribution goes to the
-//             delta slab at its sorted position.
-//     apply   one lane group per shared segment sums its (contiguous) slab
-//             entries in sorted order and writes X <- X_b - cnt eta_b lambda
-//             X_b + sum, cnt the number of pair occurrences of the row (the
-//             batch-summed update of Eq. 4).
+//             delta slab at its position, so a segment's entries are
+//             contiguous.
+//     apply   per shared segment: the entries summed in a fixed chunked
+//             order, X <- X_b - cnt eta_b lambda X_b + sum, cnt the number of
+//             pair occurrences of the row (the batch-summed update of Eq. 4).
 //   BF16 tables are written back with stochastic rounding.
 //
 // The order of every floating-point sum is fixed, so results are bitwise
 // reproducible, and a singleton row gets exactly the value the apply step
 // would give it.  Two schedules run the same per-sample and per-segment code:
-//   LINE_MODE_BATCHED     two launches per batch;
+//   LINE_MODE_BATCHED     two launches per batch, chained with programmatic
+//                         dependent launch;
 //   LINE_MODE_PERSISTENT  one cooperative launch per chunk: every warp walks
 //                         a fixed list of work items (batch b's samples, then
 //                         b's shared segments, then b+1's ...) and waits,
@@ -160,15 +163,16 @@ struct DataParams {
     int order, K;  // records have K+2 entries
     int64_t n_nodes;
     uint32_t row_bits;
-    const int32_t* rec;          // [chunk samples][K+2]
-    const uint2* slot_info;      // [chunk samples][K+2]: {position | singleton bit, segment}
-    const uint4* mdesc;          // shared segments: {first position, length, key, pair count}
-    const uint32_t* batch_mseg;  // [n_batches + 1] first shared segment of each batch
-    const uint4* ldesc;          // [n_batches][lcap] long shared segments of each batch
-    const uint32_t* lcount;      // [n_batches] number of long shared segments
+    const int32_t* rec;      // [chunk samples][K+2]
+    const uint2* slot_info;  // [chunk samples][K+2]: {position | singleton bit, segment (first position)}
+    const uint4* mdesc;      // [n_batches][mcap] shared segments: {first position, length | long bit, row, pair count}
+    const uint32_t* mcount;  // [n_batches]
+    uint32_t mcap;
+    const uint4* ldesc;      // [n_batches][lcap] long shared segments (also in mdesc, flagged)
+    const uint32_t* lcount;  // [n_batches]
     uint32_t lcap;
-    float* slab;                 // [chunk samples * (K+2)][D], by sorted position
-    uint64_t t_chunk;            // global index of the chunk's first sample
+    float* slab;             // [chunk samples * (K+2)][D], by position
+    uint64_t t_chunk;        // global index of the chunk's first sample
     int64_t chunk_samples;
     int64_t batch;
     int n_batches;
@@ -177,10 +181,11 @@ struct DataParams {
     float lambda, alpha_neg;
     uint32_t* status;
     // persistent schedule
-    const int32_t* slot_prev;   // [chunk samples][K+2]: latest earlier segment of the same row, or -1
-    const uint32_t* mseg_id;    // [shared segments] segment number
-    uint32_t* seg_done;         // [segments] generation flags: the row of the segment is written
-    uint32_t* arrive;           // [segments] contributions written to the slab
+    const int32_t* slot_prev;   // [chunk samples][K+2]: segment of the same row in the previous batch, or -1
+    const uint32_t* nseg;       // [n_batches] segments of each batch
+    uint32_t* batch_applied;    // [n_batches] segments of each batch whose row is written
+    uint32_t* seg_done;         // [positions] generation flags: the segment's row is written
+    uint32_t* arrive;           // [positions] contributions of a shared segment in the slab
     const uint64_t* item_base;  // [n_batches + 1] first work item of each batch
     uint32_t gen;
     int64_t spin_limit;
@@ -206,8 +211,8 @@ __device__ __forceinline__ T rec_entry(uint32_t gm, T held, const T* row, int id
 // ctx_stage: this warp's shared staging area, (K+1) x 32 lanes x E floats.
 // ---------------------------------------------------------------------------
 template <int D, int DT, bool PERSIST, bool PDL = false>
-__device__ __forceinline__ bool sample_item(const DataParams& p, int64_t s_local, int lig, int lane, bool active,
-                                            float eta, uint64_t t0, float* ctx_stage) {
+__device__ __forceinline__ bool sample_item(const DataParams& p, int b, int64_t s_local, int lig, int lane,
+                                            bool active, float eta, uint64_t t0, float* ctx_stage) {
     using G = Geom<D, DT>;
     constexpr int CH = G::E <= 4 ? 8 : 4;  // context rows in flight per lane
     const int R = p.K + 2;
@@ -257,40 +262,62 @@ __device__ __forceinline__ bool sample_item(const DataParams& p, int64_t s_local
     float du[G::E];
 #pragma unroll
     for (int e = 0; e < G::E; ++e) du[e] = 0.0f;
-    for (int j = 0; j <= p.K; ++j) {
-        float c[G::E];
-        const float4* ld = reinterpret_cast<const float4*>(ctx_stage + (j * 32 + lane) * G::E);
+    constexpr int JB = 8;  // dot products reduced together (independent shuffles)
+    for (int j0 = 0; j0 <= p.K; j0 += JB) {
+        float sj[JB];
 #pragma unroll
-        for (int q = 0; q < G::E / 4; ++q) {
-            const float4 a = ld[q];
-            c[4 * q] = a.x;
-            c[4 * q + 1] = a.y;
-            c[4 * q + 2] = a.z;
-            c[4 * q + 3] = a.w;
+        for (int jj = 0; jj < JB; ++jj) {
+            sj[jj] = 0.0f;
+            if (j0 + jj <= p.K) {
+                const float4* ld = reinterpret_cast<const float4*>(ctx_stage + ((j0 + jj) * 32 + lane) * G::E);
+#pragma unroll
+                for (int q = 0; q < G::E / 4; ++q) {
+                    const float4 a = ld[q];
+                    sj[jj] = fmaf(xu[4 * q], a.x, sj[jj]);
+                    sj[jj] = fmaf(xu[4 * q + 1], a.y, sj[jj]);
+                    sj[jj] = fmaf(xu[4 * q + 2], a.z, sj[jj]);
+                    sj[jj] = fmaf(xu[4 * q + 3], a.w, sj[jj]);
+                }
+            }
         }
-        float part = 0.0f;
 #pragma unroll
-        for (int e = 0; e < G::E; ++e) part = fmaf(xu[e], c[e], part);
-        const float s = group_sum<G::L>(part);
-        const float sig = 1.0f / (1.0f + expf(-s));
-        const float g = j == 0 ? eta * (1.0f - sig) : -eta * p.alpha_neg * sig;
+        for (int o = G::L / 2; o >= 1; o >>= 1)
 #pragma unroll
-        for (int e = 0; e < G::E; ++e) du[e] = fmaf(g, c[e], du[e]);
-        const uint2 inf = rec_entry<G::L>(gm, i0, info, 1 + j, active);
-        const int32_t y = rec_entry<G::L>(gm, r0, rec, 1 + j, active);
-        if (active) {
-            if (inf.x & kSingleBit) {
-                // the only reader of row y in this batch: write it now
-                const float decay = 1.0f * etalam;
-                float x[G::E];
+            for (int jj = 0; jj < JB; ++jj) sj[jj] += __shfl_xor_sync(0xFFFFFFFFu, sj[jj], o);
 #pragma unroll
-                for (int e = 0; e < G::E; ++e) x[e] = fmaf(-decay, c[e], c[e]) + g * xu[e];
-                store_row<D, DT>(p.C, y, lig, x, p.seed, t0, ctx_table);
-            } else {
-                float4* dst = reinterpret_cast<float4*>(p.slab + (int64_t)inf.x * D + lig * G::E);
+        for (int jj = 0; jj < JB; ++jj) {
+            const int j = j0 + jj;
+            if (j > p.K) break;
+            float c[G::E];
+            const float4* ld = reinterpret_cast<const float4*>(ctx_stage + (j * 32 + lane) * G::E);
 #pragma unroll
-                for (int q = 0; q < G::E / 4; ++q)
-                    st_cg(dst + q, make_float4(g * xu[4 * q], g * xu[4 * q + 1], g * xu[4 * q + 2], g * xu[4 * q + 3]));
+            for (int q = 0; q < G::E / 4; ++q) {
+                const float4 a = ld[q];
+                c[4 * q] = a.x;
+                c[4 * q + 1] = a.y;
+                c[4 * q + 2] = a.z;
+                c[4 * q + 3] = a.w;
+            }
+            const float sig = 1.0f / (1.0f + expf(-sj[jj]));
+            const float g = j == 0 ? eta * (1.0f - sig) : -eta * p.alpha_neg * sig;
+#pragma unroll
+            for (int e = 0; e < G::E; ++e) du[e] = fmaf(g, c[e], du[e]);
+            const uint2 inf = rec_entry<G::L>(gm, i0, info, 1 + j, active);
+            const int32_t y = rec_entry<G::L>(gm, r0, rec, 1 + j, active);
+            if (active) {
+                if (inf.x & kSingleBit) {
+                    // the only reader of row y in this batch: write it now
+                    const float decay = 1.0f * etalam;
+                    float x[G::E];
+#pragma unroll
+                    for (int e = 0; e < G::E; ++e) x[e] = fmaf(-decay, c[e], c[e]) + g * xu[e];
+                    store_row<D, DT>(p.C, y, lig, x, p.seed, t0, ctx_table);
+                } else {
+                    float4* dst = reinterpret_cast<float4*>(p.slab + (int64_t)inf.x * D + lig * G::E);
+#pragma unroll
+                    for (int q = 0; q < G::E / 4; ++q)
+                        st_cg(dst + q, make_float4(g * xu[4 * q], g * xu[4 * q + 1], g * xu[4 * q + 2], g * xu[4 * q + 3]));
+                }
             }
         }
     }
@@ -308,16 +335,25 @@ __device__ __forceinline__ bool sample_item(const DataParams& p, int64_t s_local
         }
     }
     if constexpr (PERSIST) {
-        // publish: the group's stores are ordered before the release stores
-        // by the warp barrier; lane k signals slot k
+        // publish: the group's stores are ordered before the release
+        // operations by the warp barrier; lane k signals slot k, and the
+        // batch's applied-segment count grows by the singletons written
         __syncwarp(gm);
+        uint32_t singles = 0;
         if (active) {
             for (int k = lig; k < R; k += G::L) {
                 const uint2 inf = info[k];
-                if (inf.x & kSingleBit) st_release(p.seg_done + inf.y, p.gen);
-                else red_release_add(p.arrive + inf.y, 1u);
+                if (inf.x & kSingleBit) {
+                    st_release(p.seg_done + inf.y, p.gen);
+                    ++singles;
+                } else {
+                    red_release_add(p.arrive + inf.y, 1u);
+                }
             }
         }
+#pragma unroll
+        for (int o = G::L / 2; o >= 1; o >>= 1) singles += __shfl_xor_sync(gm, singles, o, G::L);
+        if (active && lig == 0 && singles) red_release_add(p.batch_applied + b, singles);
     }
     return ok;
 }
@@ -327,17 +363,17 @@ __device__ __forceinline__ bool sample_item(const DataParams& p, int64_t s_local
 // write-back.  Returns false when a bounded wait ran out (persistent).
 // ---------------------------------------------------------------------------
 template <int D, int DT, bool PERSIST>
-__device__ __forceinline__ bool segment_item(const DataParams& p, uint32_t m, int lig, bool active, float eta,
+__device__ __forceinline__ bool segment_item(const DataParams& p, uint4 d, int lig, bool active, float eta,
                                              uint64_t t0) {
     using G = Geom<D, DT>;
     constexpr int PF = G::E <= 4 ? 8 : 4;  // slab entries in flight per lane
     if (!active) return true;
-    const uint4 d = p.mdesc[m];  // {first position, length | long bit, key, pair count}
+    // d = {first position, length | long bit, row, pair count}
     const uint32_t len = d.y & ~kLongBit;
     if constexpr (PERSIST) {
         // all contributions written (and, through them, every read of the
         // row's batch-start value and the row's previous write done)
-        if (!wait_geq(p.arrive + p.mseg_id[m], len, p.spin_limit, p.abort_word)) return false;
+        if (!wait_geq(p.arrive + d.x, len, p.spin_limit, p.abort_word)) return false;
     }
     const uint32_t rowid = d.z & ((1u << p.row_bits) - 1u);
     const bool is_c = p.order == 2 && rowid >= (uint32_t)p.n_nodes;
@@ -400,6 +436,12 @@ __device__ __forceinline__ void long_segment_cta(const DataParams& p, uint4 d, f
     const int lig = lane;
     const uint32_t len = d.y & ~kLongBit;
     const uint32_t n_chunks = (len + kChunk - 1) / kChunk;
+    const uint32_t rowid = d.z & ((1u << p.row_bits) - 1u);
+    const bool is_c = p.order == 2 && rowid >= (uint32_t)p.n_nodes;
+    void* table = is_c ? p.C : p.U;
+    const int64_t row = is_c ? (int64_t)rowid - p.n_nodes : (int64_t)rowid;
+    float x[G::E];
+    if (warp == 0 && mine) load_row<D, DT>(table, row, lig, x);  // in flight during the sums
     float acc[G::E];
 #pragma unroll
     for (int e = 0; e < G::E; ++e) acc[e] = 0.0f;
@@ -448,12 +490,6 @@ __device__ __forceinline__ void long_segment_cta(const DataParams& p, uint4 d, f
         __syncthreads();
     }
     if (warp == 0 && mine) {
-        const uint32_t rowid = d.z & ((1u << p.row_bits) - 1u);
-        const bool is_c = p.order == 2 && rowid >= (uint32_t)p.n_nodes;
-        void* table = is_c ? p.C : p.U;
-        const int64_t row = is_c ? (int64_t)rowid - p.n_nodes : (int64_t)rowid;
-        float x[G::E];
-        load_row<D, DT>(table, row, lig, x);
         const float decay = (float)d.w * (eta * p.lambda);
 #pragma unroll
         for (int e = 0; e < G::E; ++e) x[e] = fmaf(-decay, x[e], x[e]) + acc[e];
@@ -479,8 +515,8 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_gather(DataParams p, int b) 
     const int64_t s_end = min(s_begin + p.batch, p.chunk_samples);
     const int64_t s_local = s_begin + ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * G::GPW + grp;
     float* stage = smem + (size_t)warp * (p.K + 1) * 32 * G::E;
-    sample_item<D, DT, false, PDL>(p, s_local, lig, lane, s_local < s_end, p.eta[b], p.t_chunk + (uint64_t)s_begin,
-                                   stage);
+    sample_item<D, DT, false, PDL>(p, b, s_local, lig, lane, s_local < s_end, p.eta[b],
+                                   p.t_chunk + (uint64_t)s_begin, stage);
 }
 
 // Blocks [0, g_long) take the batch's long shared segments, one per CTA; the
@@ -494,8 +530,9 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(DataParams p, int b, in
     pdl_launch_dependents();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane / G::L, lig = lane % G::L;
-    const uint32_t m_begin = p.batch_mseg[b], m_end = p.batch_mseg[b + 1];
+    const uint32_t n_m = p.mcount[b];
     const uint32_t n_long = p.lcount[b];
+    const uint4* md = p.mdesc + (size_t)b * p.mcap;
     const uint64_t t0 = p.t_chunk + (uint64_t)b * (uint64_t)p.batch;
     const float eta = p.eta[b];
     pdl_wait();  // the slab and the rows: written by the gather
@@ -505,10 +542,11 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(DataParams p, int b, in
         return;
     }
     const int64_t groups = (int64_t)(gridDim.x - g_long) * (blockDim.x >> 5) * G::GPW;
-    for (int64_t m = m_begin + ((int64_t)(blockIdx.x - g_long) * (blockDim.x >> 5) + warp) * G::GPW + grp; m < m_end;
+    for (int64_t m = ((int64_t)(blockIdx.x - g_long) * (blockDim.x >> 5) + warp) * G::GPW + grp; m < n_m;
          m += groups) {
-        if (p.mdesc[m].y & kLongBit) continue;
-        segment_item<D, DT, false>(p, (uint32_t)m, lig, true, eta, t0);
+        const uint4 d = md[m];
+        if (d.y & kLongBit) continue;
+        segment_item<D, DT, false>(p, d, lig, true, eta, t0);
     }
 }
 
@@ -519,10 +557,11 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(DataParams p, int b, in
 // its items in increasing order.  An item waits only on items earlier in that
 // order, so the earliest unfinished item can always run (all warps are
 // resident): the schedule cannot deadlock, and every wait is bounded anyway.
-//   sample item: before reading a row it waits for the latest earlier
-//     segment of that row in the chunk (written by a sample item when it was
-//     a singleton, by a segment item otherwise); it then writes its singleton
-//     rows and publishes them, and counts its shared contributions in.
+//   sample item of batch b: for a row also touched by batch b-1 it waits for
+//     that segment (written by a sample item when it was a singleton, by a
+//     segment item otherwise); batches b-2 and b-3 must be fully written.  It
+//     then writes its singleton rows and publishes them, and counts its
+//     shared contributions in.
 //   segment item: waits until all contributions of its segment are in, sums
 //     them, writes the row and publishes it.
 // ---------------------------------------------------------------------------
@@ -532,6 +571,11 @@ constexpr int kPersistMinBlocks = 3;
 __device__ __forceinline__ void fail_abort(const DataParams& p) {
     atomicOr(p.status, DEV_ERR_TIMEOUT);
     atomicExch(p.abort_word, 1u);
+}
+
+__device__ __forceinline__ bool batch_applied_ok(const DataParams& p, int bb) {
+    if (bb < 0) return true;
+    return wait_geq(p.batch_applied + bb, p.nseg[bb], p.spin_limit, p.abort_word);
 }
 
 template <int D, int DT>
@@ -545,7 +589,7 @@ __global__ void __launch_bounds__(kPersistThreads, kPersistMinBlocks) k_persiste
     float* stage = smem + (size_t)warp * (p.K + 1) * 32 * G::E;
     const uint64_t W = (uint64_t)gridDim.x * wpb;
     const uint64_t total = p.item_base[p.n_batches];
-    int b = 0;
+    int b = 0, checked_b = -1;
     for (uint64_t t = (uint64_t)blockIdx.x * wpb + warp; t < total; t += W) {
         while (t >= p.item_base[b + 1]) ++b;
         if (*(volatile uint32_t*)p.abort_word) return;
@@ -555,16 +599,29 @@ __global__ void __launch_bounds__(kPersistThreads, kPersistMinBlocks) k_persiste
         const uint64_t nA = (uint64_t)((nb + G::GPW - 1) / G::GPW);
         const uint64_t t0 = p.t_chunk + (uint64_t)s_begin;
         const float eta = p.eta[b];
-        bool ok;
+        bool ok = true;
         if (local < nA) {
-            const int64_t s_local = s_begin + (int64_t)local * G::GPW + grp;
-            ok = sample_item<D, DT, true>(p, s_local, lig, lane, s_local < s_begin + nb, eta, t0, stage);
+            // rows last written in batch b-1 are awaited per row; batches
+            // b-2 and b-3 must be complete (by induction, so is every earlier
+            // batch of the chunk)
+            if (checked_b != b) {
+                ok = batch_applied_ok(p, b - 2) && batch_applied_ok(p, b - 3);
+                checked_b = b;
+            }
+            if (__all_sync(0xFFFFFFFFu, ok)) {
+                const int64_t s_local = s_begin + (int64_t)local * G::GPW + grp;
+                ok = sample_item<D, DT, true>(p, b, s_local, lig, lane, s_local < s_begin + nb, eta, t0, stage);
+            }
         } else {
-            const uint32_t m = p.batch_mseg[b] + (uint32_t)((local - nA) * G::GPW) + grp;
-            const bool active = m < p.batch_mseg[b + 1];
-            ok = segment_item<D, DT, true>(p, m, lig, active, eta, t0);
+            const uint32_t m = (uint32_t)((local - nA) * G::GPW) + grp;
+            const bool active = m < p.mcount[b];
+            const uint4 d = active ? p.mdesc[(size_t)b * p.mcap + m] : make_uint4(0u, 0u, 0u, 0u);
+            ok = segment_item<D, DT, true>(p, d, lig, active, eta, t0);
             __syncwarp();
-            if (ok && active && lig == 0) st_release(p.seg_done + p.mseg_id[m], p.gen);
+            if (ok && active && lig == 0) {
+                st_release(p.seg_done + d.x, p.gen);
+                red_release_add(p.batch_applied + b, 1u);
+            }
         }
         if (!__all_sync(0xFFFFFFFFu, ok)) {
             if (lane == 0) fail_abort(p);
@@ -587,14 +644,12 @@ struct PrepassParams {
     int64_t chunk_samples;
     int64_t batch;
     int K, order;
-    uint32_t row_bits;
     int32_t* rec;
     uint64_t* items;
 };
 
-__device__ __forceinline__ uint64_t make_item(uint32_t batch, uint32_t row_bits, uint32_t rowid, uint32_t s_local,
-                                              uint32_t slot) {
-    return ((uint64_t)((batch << row_bits) | rowid) << 32) | ((s_local << kSlotBits) | slot);
+__device__ __forceinline__ uint64_t make_item(uint32_t rowid, uint32_t s_local, uint32_t slot) {
+    return ((uint64_t)rowid << 32) | ((s_local << kSlotBits) | slot);
 }
 
 __global__ void k_chunk_draws(PrepassParams p) {
@@ -603,7 +658,6 @@ __global__ void k_chunk_draws(PrepassParams p) {
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
         const uint32_t s = q / C1;
         const uint32_t c = q - s * C1;
-        const uint32_t b = s / (uint32_t)p.batch;
         const uint4 w = draw_words(p.seed, 0u, p.t_chunk + (uint64_t)s, c);
         const uint32_t ctx_off = p.order == 2 ? (uint32_t)p.n_nodes : 0u;
         const uint32_t base = s * R;
@@ -612,220 +666,297 @@ __global__ void k_chunk_draws(PrepassParams p) {
             const int32_t u = __ldg(p.src + e), v = __ldg(p.dst + e);
             p.rec[base] = u;
             p.rec[base + 1] = v;
-            p.items[base] = make_item(b, p.row_bits, (uint32_t)u, s, 0u);
-            p.items[base + 1] = make_item(b, p.row_bits, (uint32_t)v + ctx_off, s, 1u);
+            p.items[base] = make_item((uint32_t)u, s, 0u);
+            p.items[base + 1] = make_item((uint32_t)v + ctx_off, s, 1u);
         } else {
             const uint32_t y = alias_pick(p.neg_tab, (uint64_t)p.n_nodes, w);
             p.rec[base + 1 + c] = (int32_t)y;
-            p.items[base + 1 + c] = make_item(b, p.row_bits, y + ctx_off, s, 1u + c);
+            p.items[base + 1 + c] = make_item(y + ctx_off, s, 1u + c);
         }
     }
 }
 
-constexpr int kRsThreads = 256;
-constexpr int kRsWarps = kRsThreads / 32;
-constexpr int kRsRounds = 16;
-constexpr int kRsTile = kRsThreads * kRsRounds;  // 4096 items
-constexpr int kRsBits = 8;
-constexpr int kRsBins = 1 << kRsBits;
+// ---------------------------------------------------------------------------
+// Grouping of each batch's items by row.  Items of batch b occupy positions
+// [b B (K+2), b B (K+2) + nb (K+2)) of the chunk, in (sample, slot) order.
+// ---------------------------------------------------------------------------
+constexpr int kBuckets = 256;            // bucket = 8-bit multiplicative hash of the row id
 
-__global__ void __launch_bounds__(kRsThreads) k_radix_hist(const uint64_t* __restrict__ in, int64_t n, int shift,
-                                                           uint32_t* __restrict__ hist, int ntiles) {
-    __shared__ uint32_t cnt[kRsBins];
-    cnt[threadIdx.x] = 0;
-    __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kRsTile;
-#pragma unroll 4
-    for (int r = 0; r < kRsRounds; ++r) {
-        const int64_t i = base + r * kRsThreads + threadIdx.x;
-        if (i < n) atomicAdd(&cnt[(uint32_t)(in[i] >> shift) & (kRsBins - 1)], 1u);
-    }
-    __syncthreads();
-    hist[(int64_t)threadIdx.x * ntiles + blockIdx.x] = cnt[threadIdx.x];
+// Fibonacci hashing: spreads the hot (low) row ids of skewed graphs.
+__device__ __forceinline__ uint32_t bucket_of(uint32_t row) { return (row * 0x9E3779B1u) >> 24; }
+constexpr int kBucketThreads = 1024;
+constexpr int kBucketWarps = kBucketThreads / 32;
+constexpr uint32_t kPartItems = 16384;   // items of a batch per bucketing CTA
+constexpr int kSortThreads = 256;        // one warp per bucket
+
+struct GroupParams {
+    int n_batches;
+    int64_t batch;
+    int64_t chunk_samples;
+    uint32_t R, K, parts;  // parts: bucketing CTAs per batch
+    uint32_t row_bits;
+    const uint64_t* items;  // draws, (sample, slot) order
+    uint64_t* bucketed;     // items grouped by bucket within each batch
+    uint64_t* tmp;          // scratch of the same size
+    uint32_t* gcnt;         // [n_batches][parts][256] bucket counts of each part
+    uint32_t* boff;         // [n_batches][257] bucket starts within the batch
+    // outputs
+    uint2* slot_info;
+    uint4* mdesc;
+    uint32_t* mcount;
+    uint32_t mcap;
+    uint4* ldesc;
+    uint32_t* lcount;
+    uint32_t lcap;
+    uint32_t* nseg;       // persistent only (nullptr otherwise)
+    uint32_t* sorted_row; // persistent only: row id by position
+    uint32_t* seghead;    // persistent only: first position of the position's segment
+};
+
+__device__ __forceinline__ void batch_range(const GroupParams& q, int b, uint64_t* base, uint32_t* n) {
+    const int64_t nb = min(q.batch, q.chunk_samples - (int64_t)b * q.batch);
+    *base = (uint64_t)b * (uint64_t)q.batch * q.R;
+    *n = (uint32_t)nb * q.R;
 }
 
-struct GenU32 {
-    const uint32_t* a;
-    __device__ uint32_t operator()(int64_t i) const { return a[i]; }
-};
-struct OutExcl32 {
-    uint32_t* a;
-    __device__ void operator()(int64_t i, uint32_t excl, uint32_t) const { a[i] = excl; }
-};
-
-// Stable scatter: warp w owns items [tile + 512 w, +512) and ranks them in 16
-// rounds of 32 (index order); per-digit warp counts then give every item its
-// position among equal digits of the tile.
-__global__ void __launch_bounds__(kRsThreads) k_radix_scatter(const uint64_t* __restrict__ in,
-                                                              uint64_t* __restrict__ out, int64_t n, int shift,
-                                                              const uint32_t* __restrict__ offs, int ntiles) {
-    __shared__ uint32_t wcnt[kRsWarps][kRsBins];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int w = 0; w < kRsWarps; ++w) wcnt[w][threadIdx.x] = 0;
+__global__ void __launch_bounds__(kBucketThreads) k_bucket_count(GroupParams q) {
+    __shared__ uint32_t cnt[kBuckets];
+    const int part = blockIdx.x, b = blockIdx.y;
+    if (threadIdx.x < kBuckets) cnt[threadIdx.x] = 0;
     __syncthreads();
-    const int64_t base = (int64_t)blockIdx.x * kRsTile + (int64_t)warp * (kRsRounds * 32);
+    uint64_t base;
+    uint32_t n;
+    batch_range(q, b, &base, &n);
+    const uint32_t lo = min(n, (uint32_t)part * kPartItems), hi = min(n, lo + kPartItems);
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
+        atomicAdd(&cnt[bucket_of((uint32_t)(q.items[base + i] >> 32))], 1u);
+    __syncthreads();
+    if (threadIdx.x < kBuckets) q.gcnt[((size_t)b * q.parts + part) * kBuckets + threadIdx.x] = cnt[threadIdx.x];
+}
+
+// Stable scatter of one part: bucket start + the earlier parts' counts + the
+// earlier warps' counts + the rank within the warp's rounds.
+__global__ void __launch_bounds__(kBucketThreads) k_bucket_scatter(GroupParams q) {
+    __shared__ uint32_t bstart[kBuckets], poff[kBuckets];
+    __shared__ uint32_t wcnt[kBucketWarps][kBuckets];
+    const int part = blockIdx.x, b = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t base;
+    uint32_t n;
+    batch_range(q, b, &base, &n);
+    for (int i = threadIdx.x; i < kBucketWarps * kBuckets; i += blockDim.x) (&wcnt[0][0])[i] = 0;
+    if (threadIdx.x < kBuckets) {
+        const uint32_t d = threadIdx.x;
+        uint32_t tot = 0, before = 0;
+        for (uint32_t pp = 0; pp < q.parts; ++pp) {
+            const uint32_t c = q.gcnt[((size_t)b * q.parts + pp) * kBuckets + d];
+            if (pp < (uint32_t)part) before += c;
+            tot += c;
+        }
+        bstart[d] = tot;
+        poff[d] = before;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        uint32_t run = 0;
+        for (int d = 0; d < kBuckets; ++d) {
+            const uint32_t c = bstart[d];
+            bstart[d] = run;
+            run += c;
+        }
+    }
+    __syncthreads();
+    if (part == 0 && threadIdx.x <= kBuckets) q.boff[(size_t)b * (kBuckets + 1) + threadIdx.x] = threadIdx.x < kBuckets ? bstart[threadIdx.x] : n;
+    const uint32_t lo = min(n, (uint32_t)part * kPartItems), hi = min(n, lo + kPartItems);
+    const uint32_t per = (hi - lo + kBucketWarps - 1) / kBucketWarps;
+    const uint32_t wlo = min(hi, lo + warp * per), whi = min(hi, wlo + per);
     const uint32_t lt = (1u << lane) - 1u;
-    uint64_t key[kRsRounds];
-    uint32_t dig[kRsRounds], rank[kRsRounds];
-#pragma unroll
-    for (int r = 0; r < kRsRounds; ++r) {
-        const int64_t i = base + r * 32 + lane;
-        const bool valid = i < n;
-        key[r] = valid ? in[i] : 0ull;
-        const uint32_t d = valid ? (uint32_t)(key[r] >> shift) & (kRsBins - 1) : 0xFFFFu;
-        dig[r] = d;
+    for (uint32_t r = wlo; r < whi; r += 32) {
+        const uint32_t i = r + lane;
+        const bool valid = i < whi;
+        const uint32_t d = valid ? bucket_of((uint32_t)(q.items[base + i] >> 32)) : 0xFFFFu;
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
-        const uint32_t before = valid ? wcnt[warp][d] : 0u;
-        rank[r] = before + __popc(peers & lt);
-        __syncwarp();
-        if (valid && (peers & lt) == 0) wcnt[warp][d] = before + __popc(peers);
+        if (valid && (peers & lt) == 0) wcnt[warp][d] += __popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    {
+    if (threadIdx.x < kBuckets) {
         uint32_t run = 0;
-#pragma unroll
-        for (int w = 0; w < kRsWarps; ++w) {
+        for (int w = 0; w < kBucketWarps; ++w) {
             const uint32_t c = wcnt[w][threadIdx.x];
             wcnt[w][threadIdx.x] = run;
             run += c;
         }
     }
     __syncthreads();
+    for (uint32_t r = wlo; r < whi; r += 32) {
+        const uint32_t i = r + lane;
+        const bool valid = i < whi;
+        const uint64_t it = valid ? q.items[base + i] : 0ull;
+        const uint32_t d = valid ? bucket_of((uint32_t)(it >> 32)) : 0xFFFFu;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        const uint32_t before = valid ? wcnt[warp][d] : 0u;
+        if (valid) q.bucketed[base + bstart[d] + poff[d] + before + __popc(peers & lt)] = it;
+        __syncwarp();
+        if (valid && (peers & lt) == 0) wcnt[warp][d] = before + __popc(peers);
+        __syncwarp();
+    }
+}
+
+// One stable 8-bit LSD pass of a warp over n items (global memory), by bits
+// [shift, shift + 8) of the row id.  cnt: the warp's 256 shared counters.
+__device__ void warp_radix_pass(const uint64_t* src, uint64_t* dst, uint32_t n, uint32_t shift, uint32_t* cnt) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t lt = (1u << lane) - 1u;
+    for (int i = lane; i < kBuckets; i += 32) cnt[i] = 0;
+    __syncwarp();
+    for (uint32_t r = 0; r < n; r += 32) {
+        const uint32_t i = r + lane;
+        const bool valid = i < n;
+        const uint32_t d = valid ? (uint32_t)(src[i] >> (32 + shift)) & 255u : 0xFFFFu;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        if (valid && (peers & lt) == 0) cnt[d] += __popc(peers);
+        __syncwarp();
+    }
+    // exclusive scan of the 256 counters: lane l owns counters 8l .. 8l+7
+    uint32_t own = 0;
 #pragma unroll
-    for (int r = 0; r < kRsRounds; ++r) {
-        const int64_t i = base + r * 32 + lane;
-        if (i < n) {
-            const uint32_t d = dig[r];
-            out[offs[(int64_t)d * ntiles + blockIdx.x] + wcnt[warp][d] + rank[r]] = key[r];
-        }
+    for (int k = 0; k < 8; ++k) own += cnt[lane * 8 + k];
+    uint32_t incl = own;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    uint32_t run = incl - own;
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const uint32_t c = cnt[lane * 8 + k];
+        cnt[lane * 8 + k] = run;
+        run += c;
+    }
+    __syncwarp();
+    for (uint32_t r = 0; r < n; r += 32) {
+        const uint32_t i = r + lane;
+        const bool valid = i < n;
+        const uint64_t it = valid ? src[i] : 0ull;
+        const uint32_t d = valid ? (uint32_t)(it >> (32 + shift)) & 255u : 0xFFFFu;
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
+        const uint32_t before = valid ? cnt[d] : 0u;
+        if (valid) dst[before + __popc(peers & lt)] = it;
+        __syncwarp();
+        if (valid && (peers & lt) == 0) cnt[d] = before + __popc(peers);
+        __syncwarp();
     }
 }
 
-struct GenHead {
-    const uint64_t* items;
-    __device__ uint32_t operator()(int64_t i) const {
-        return (i == 0 || (items[i] >> 32) != (items[i - 1] >> 32)) ? 1u : 0u;
-    }
-};
-struct OutSegStart {
-    const uint64_t* items;
-    uint32_t* seg_start;
-    int64_t n;
-    uint32_t* n_segs;
-    __device__ void operator()(int64_t i, uint32_t excl, uint32_t incl) const {
-        if (i == 0 || (items[i] >> 32) != (items[i - 1] >> 32)) seg_start[excl] = (uint32_t)i;
-        if (i == n - 1) {
-            seg_start[incl] = (uint32_t)n;
-            *n_segs = incl;
-        }
-    }
-};
+constexpr uint32_t kWarpSortCap = 512;  // bucket sizes ranked directly in shared memory
+constexpr int kSortBucketsPerCta = kSortThreads / 32;
 
-// Per segment j: slot_info of every entry = {sorted position | singleton
-// bit, j}; for the persistent schedule, rowitems[j] = (row << 32) | j.
-__global__ void k_seg_meta(const uint64_t* __restrict__ items, const uint32_t* __restrict__ seg_start,
-                           const uint32_t* n_segs_p, uint32_t row_bits, uint32_t R, uint2* __restrict__ slot_info,
-                           uint64_t* __restrict__ rowitems) {
-    const uint32_t n_segs = *n_segs_p;
-    const uint32_t mask = (1u << row_bits) - 1u;
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < n_segs; j += gridDim.x * blockDim.x) {
-        const uint32_t begin = seg_start[j], end = seg_start[j + 1];
-        const uint32_t single = end - begin == 1 ? kSingleBit : 0u;
-        for (uint32_t i = begin; i < end; ++i) {
-            const uint32_t v = (uint32_t)items[i];
-            slot_info[(v >> kSlotBits) * R + (v & kSlotMask)] = make_uint2(i | single, j);
+// One warp per (bucket, batch): sort the bucket's items by row (stable), then
+// find its segments.  Small buckets: every item's rank is the number of items
+// with a smaller (row, index); large ones: LSD radix passes in global memory.
+__global__ void __launch_bounds__(kSortThreads) k_bucket_sort(GroupParams q) {
+    extern __shared__ uint64_t sbuf[];  // per warp: 2 x kWarpSortCap items
+    __shared__ uint32_t wcnt[kSortBucketsPerCta][kBuckets];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int d = blockIdx.x * kSortBucketsPerCta + warp, b = blockIdx.y;
+    if (b >= q.n_batches || d >= kBuckets) return;
+    uint64_t base;
+    uint32_t n;
+    batch_range(q, b, &base, &n);
+    const uint32_t lo = q.boff[(size_t)b * (kBuckets + 1) + d], hi = q.boff[(size_t)b * (kBuckets + 1) + d + 1];
+    const uint32_t c = hi - lo;
+    if (c == 0) return;
+    const uint64_t* a;
+    if (c <= kWarpSortCap) {
+        uint64_t* in = sbuf + (size_t)warp * 2 * kWarpSortCap;
+        uint64_t* out = in + kWarpSortCap;
+        for (uint32_t i = lane; i < c; i += 32) in[i] = q.bucketed[base + lo + i];
+        __syncwarp();
+        for (uint32_t i = lane; i < c; i += 32) {
+            const uint64_t it = in[i];
+            const uint32_t key = (uint32_t)(it >> 32);
+            uint32_t rank = 0;
+            for (uint32_t j = 0; j < c; ++j) {
+                const uint32_t kj = (uint32_t)(in[j] >> 32);
+                rank += (kj < key) || (kj == key && j < i);
+            }
+            out[rank] = it;
         }
-        if (rowitems) rowitems[j] = ((uint64_t)((uint32_t)(items[begin] >> 32) & mask) << 32) | j;
+        __syncwarp();
+        a = out;
+    } else {  // a large bucket (a very skewed draw): radix passes over all row bits
+        uint64_t* x = q.bucketed + base + lo;
+        uint64_t* y = q.tmp + base + lo;
+        for (uint32_t sh = 0; sh < q.row_bits; sh += 8) {
+            warp_radix_pass(x, y, c, sh, wcnt[warp]);
+            uint64_t* t = x;
+            x = y;
+            y = t;
+        }
+        __syncwarp();
+        a = x;
     }
-}
-
-// Shared segments (two or more entries) get a descriptor.
-struct GenMulti {
-    const uint32_t* seg_start;
-    const uint32_t* n_segs;
-    __device__ uint32_t operator()(int64_t j) const {
-        return (j < (int64_t)*n_segs && seg_start[j + 1] - seg_start[j] > 1) ? 1u : 0u;
-    }
-};
-struct OutMulti {
-    const uint64_t* items;
-    const uint32_t* seg_start;
-    const uint32_t* n_segs;
-    int64_t n;
-    int K;
-    uint4* mdesc;
-    uint32_t* mseg_id;
-    uint32_t* n_mseg;
-    uint32_t row_bits;
-    uint4* ldesc;
-    uint32_t* lcount;
-    uint32_t lcap;
-    __device__ void operator()(int64_t j, uint32_t excl, uint32_t incl) const {
-        if (j < (int64_t)*n_segs) {
-            const uint32_t begin = seg_start[j], end = seg_start[j + 1];
-            if (end - begin > 1) {
-                uint32_t cnt = 0;
-                for (uint32_t i = begin; i < end; ++i) cnt += ((uint32_t)items[i] & kSlotMask) == 0 ? (uint32_t)K + 1 : 1u;
-                const uint32_t key = (uint32_t)(items[begin] >> 32);
-                uint32_t len = end - begin;
-                if (len > kChunk) {
-                    // the batch's long list (its order does not matter: each
-                    // long segment is summed by one CTA)
-                    const uint32_t b = key >> row_bits;
-                    const uint32_t l = atomicAdd(lcount + b, 1u);
-                    ldesc[(size_t)b * lcap + l] = make_uint4(begin, len, key, cnt);
-                    len |= kLongBit;
-                }
-                mdesc[excl] = make_uint4(begin, len, key, cnt);
-                mseg_id[excl] = (uint32_t)j;
+    const uint64_t gpos = base + lo;  // position of the bucket's first item in the chunk
+    for (uint32_t i = lane; i < c; i += 32) {
+        const uint32_t key = (uint32_t)(a[i] >> 32);
+        if (i > 0 && (uint32_t)(a[i - 1] >> 32) == key) continue;
+        uint32_t j = i + 1;
+        while (j < c && (uint32_t)(a[j] >> 32) == key) ++j;
+        const uint32_t len = j - i;
+        const uint32_t head = (uint32_t)(gpos + i);
+        uint32_t cnt = 0;
+        for (uint32_t k = i; k < j; ++k) {
+            const uint32_t v = (uint32_t)a[k];
+            const uint32_t slot = v & kSlotMask;
+            cnt += slot == 0 ? q.K + 1 : 1u;
+            const uint32_t pos = (uint32_t)(gpos + k);
+            q.slot_info[(v >> kSlotBits) * q.R + slot] = make_uint2(pos | (len == 1 ? kSingleBit : 0u), head);
+            if (q.sorted_row) {
+                q.sorted_row[pos] = key;
+                q.seghead[pos] = head;
             }
         }
-        if (j == n - 1) *n_mseg = incl;
-    }
-};
-
-// batch_mseg[b] = first shared segment of batch b; batch_mseg[n_batches] = count.
-__global__ void k_batch_mseg(const uint4* __restrict__ mdesc, const uint32_t* n_mseg_p, uint32_t row_bits,
-                             int n_batches, uint32_t* __restrict__ batch_mseg) {
-    const uint32_t nm = *n_mseg_p;
-    if (nm == 0) {
-        for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= n_batches; b += gridDim.x * blockDim.x) batch_mseg[b] = 0;
-        return;
-    }
-    for (uint32_t m = blockIdx.x * blockDim.x + threadIdx.x; m < nm; m += gridDim.x * blockDim.x) {
-        const int bm = (int)(mdesc[m].z >> row_bits);
-        const int bp = m ? (int)(mdesc[m - 1].z >> row_bits) : -1;
-        for (int b = bp + 1; b <= bm; ++b) batch_mseg[b] = m;
-        if (m + 1 == nm)
-            for (int b = bm + 1; b <= n_batches; ++b) batch_mseg[b] = nm;
+        if (q.nseg) atomicAdd(q.nseg + b, 1u);
+        if (len > 1) {
+            uint32_t flagged = len;
+            if (len > kChunk) {
+                const uint32_t l = atomicAdd(q.lcount + b, 1u);
+                q.ldesc[(size_t)b * q.lcap + l] = make_uint4(head, len, key, cnt);
+                flagged |= kLongBit;
+            }
+            const uint32_t m = atomicAdd(q.mcount + b, 1u);
+            q.mdesc[(size_t)b * q.mcap + m] = make_uint4(head, flagged, key, cnt);
+        }
     }
 }
 
-// rowitems sorted by row (stable, so batches ascend within a row): the latest
-// earlier segment of the same row precedes each segment.
-__global__ void k_prev_seg(const uint64_t* __restrict__ sorted, const uint32_t* n_segs_p, int32_t* __restrict__ prev) {
-    const uint32_t n_segs = *n_segs_p;
-    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < n_segs; k += gridDim.x * blockDim.x) {
-        const uint64_t cur = sorted[k];
+// slot_prev[(s, slot)] = segment of the same row in the previous batch of the
+// chunk, or -1: binary search in that batch's bucket (sorted by row).
+__global__ void k_prev_lookup(GroupParams q, const int32_t* __restrict__ rec, uint32_t ctx_off,
+                              int32_t* __restrict__ slot_prev) {
+    const uint64_t total = (uint64_t)q.chunk_samples * q.R;
+    for (uint64_t it = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; it < total; it += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t s = (uint32_t)(it / q.R), slot = (uint32_t)(it - (uint64_t)s * q.R);
+        const int b = (int)(s / (uint32_t)q.batch);
         int32_t pv = -1;
-        if (k > 0 && (sorted[k - 1] >> 32) == (cur >> 32)) pv = (int32_t)(uint32_t)sorted[k - 1];
-        prev[(uint32_t)cur] = pv;
+        if (b > 0) {
+            const uint32_t row = slot == 0 ? (uint32_t)rec[(uint64_t)s * q.R] : (uint32_t)rec[it] + ctx_off;
+            const uint32_t d = bucket_of(row);
+            const uint64_t pbase = (uint64_t)(b - 1) * (uint64_t)q.batch * q.R;
+            uint32_t lo = q.boff[(size_t)(b - 1) * (kBuckets + 1) + d], hi = q.boff[(size_t)(b - 1) * (kBuckets + 1) + d + 1];
+            const uint32_t end = hi;
+            while (lo < hi) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (q.sorted_row[pbase + mid] < row) lo = mid + 1;
+                else hi = mid;
+            }
+            if (lo < end && q.sorted_row[pbase + lo] == row) pv = (int32_t)q.seghead[pbase + lo];
+        }
+        slot_prev[it] = pv;
     }
-}
-
-__global__ void k_slot_prev(const uint2* __restrict__ slot_info, const int32_t* __restrict__ prev, int64_t n_items,
-                            int32_t* __restrict__ slot_prev) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_items; i += (int64_t)gridDim.x * blockDim.x)
-        slot_prev[i] = prev[slot_info[i].y];
-}
-
-// Padding for the row sort: ids past n_segs sort after every real row.
-__global__ void k_pad_rowitems(uint64_t* __restrict__ rowitems, const uint32_t* n_segs_p, int64_t n, uint32_t pad) {
-    const int64_t n_segs = *n_segs_p;
-    for (int64_t j = n_segs + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x)
-        rowitems[j] = ((uint64_t)pad << 32) | (uint64_t)j;
 }
 
 // eta[b] = lr0 (schedule 0) or lr0 * max(1 - t0/T, floor) (schedule 1) for
@@ -844,15 +975,15 @@ __global__ void k_batch_eta(int n_batches, uint64_t t_chunk, int64_t batch, doub
 }
 
 // item_base[b] = first work item of batch b (sample items, then shared-segment items).
-__global__ void k_item_base(const uint32_t* __restrict__ batch_mseg, int n_batches, int64_t batch,
-                            int64_t chunk_samples, int gpw, uint64_t* __restrict__ item_base) {
+__global__ void k_item_base(const uint32_t* __restrict__ mcount, int n_batches, int64_t batch, int64_t chunk_samples,
+                            int gpw, uint64_t* __restrict__ item_base) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
     uint64_t acc = 0;
     for (int b = 0; b < n_batches; ++b) {
         item_base[b] = acc;
         const int64_t nb = min(batch, chunk_samples - (int64_t)b * batch);
         acc += (uint64_t)((nb + gpw - 1) / gpw);
-        acc += (uint64_t)((batch_mseg[b + 1] - batch_mseg[b] + gpw - 1) / gpw);
+        acc += (uint64_t)((mcount[b] + gpw - 1) / gpw);
     }
     item_base[n_batches] = acc;
 }
@@ -881,14 +1012,14 @@ struct Buf {
 // pre-pass of chunk c+1 (on its own low-priority stream) fills one while the
 // data phase of chunk c reads the other.
 struct ChunkSet {
-    Buf rec, slot_info, mdesc, mseg_id, batch_mseg, ldesc, lcount, eta, slot_prev, arrive, item_base;
+    Buf rec, slot_info, mdesc, mcount, ldesc, lcount, eta, slot_prev, arrive, item_base, nseg;
     cudaEvent_t prep_done = nullptr;  // pre-pass of the set's current chunk finished
     cudaEvent_t data_done = nullptr;  // data phase of the set's previous chunk finished
     bool data_pending = false;
 };
 
 struct TrainWorkspace {
-    Buf items0, items1, hist, scan_tiles, seg_start, counters, slab, rowitems0, rowitems1, prev, seg_done;
+    Buf items0, items1, gcnt, boff, counters, slab, sorted_row, seghead, seg_done, batch_applied;
     ChunkSet set[2];
     cudaStream_t prep = nullptr;    // pre-pass stream
     cudaEvent_t start = nullptr;    // caller-stream work before the call
@@ -941,25 +1072,6 @@ static uint32_t bits_for(uint64_t v) {  // bits to hold values 0..v-1
     uint32_t b = 1;
     while ((1ull << b) < v) ++b;
     return b;
-}
-
-// Stable LSD radix sort of n items by key bits [32, 32 + bits); the result is
-// left in *result (a or b).
-static cudaError_t radix_sort(uint64_t* a, uint64_t* b, int64_t n, uint32_t bits, uint32_t* hist, uint32_t* scan_buf,
-                              cudaStream_t s, uint64_t** result, int* launches) {
-    const int tiles = (int)((n + kRsTile - 1) / kRsTile);
-    uint64_t* in = a;
-    uint64_t* out = b;
-    for (uint32_t sh = 0; sh < bits; sh += kRsBits) {
-        k_radix_hist<<<tiles, kRsThreads, 0, s>>>(in, n, 32 + (int)sh, hist, tiles);
-        cudaError_t e = device_scan<uint32_t>((int64_t)kRsBins * tiles, GenU32{hist}, OutExcl32{hist}, scan_buf, s);
-        if (e != cudaSuccess) return e;
-        k_radix_scatter<<<tiles, kRsThreads, 0, s>>>(in, out, n, 32 + (int)sh, hist, tiles);
-        std::swap(in, out);
-        *launches += 5;
-    }
-    *result = in;
-    return cudaGetLastError();
 }
 
 template <int D, int DT>
@@ -1015,7 +1127,9 @@ static cudaError_t launch_data_batched(const DataParams& p, int warps_per_block,
         if (e != cudaSuccess) break;
         // a shared segment has two or more of the batch's nb * (K+2) entries
         const int64_t max_m = nb * (p.K + 2) / 2 + 1;
-        const unsigned g2 = (unsigned)std::min<int64_t>((max_m + apply_per_block - 1) / apply_per_block, 152 * 4);
+        // short shared segments run about 10% of the batch's entries (R-MAT
+        // 20: ~2.9K of 28.7K); 2 blocks per SM leave room for the next kernel
+        const unsigned g2 = (unsigned)std::min<int64_t>((max_m + apply_per_block - 1) / apply_per_block, 152 * 2);
         e = launch_pdl(k_apply<D, DT>, (unsigned)g_long + g2, kApplyThreads, 0, s, true, p, b, g_long);
     }
     if (e != cudaSuccess) return e;
@@ -1076,27 +1190,25 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     if (n_samples == 0) return cudaSuccess;
     const uint64_t rows_space = a.order == 2 ? 2ull * (uint64_t)a.n_nodes : (uint64_t)a.n_nodes;
     const uint32_t row_bits = bits_for(rows_space);
-    if (row_bits > 30) {
-        *err = "too many nodes for 32-bit sort keys";
+    if (row_bits > 31) {
+        *err = "too many nodes for 32-bit row ids";
         return cudaErrorInvalidValue;
     }
-    // batches per chunk: about 2^18 samples, limited by the key bits, by
-    // 31-bit sorted positions and by the chunk-sample field of item values
-    int64_t nb_max = (int64_t)1 << (32 - row_bits);
+    // batches per chunk: about 2^18 samples, limited by 31-bit positions and
+    // by the chunk-sample field of item values
     int64_t nb = a.chunk_batches > 0 ? a.chunk_batches : std::max<int64_t>(1, (int64_t(1) << 18) / a.batch);
-    nb = std::min(nb, nb_max);
     while (nb > 1 && ((uint64_t)nb * (uint64_t)a.batch * (uint64_t)R >= (1ull << 31) ||
                       (uint64_t)nb * (uint64_t)a.batch > (1ull << (32 - kSlotBits))))
         nb >>= 1;
     const uint64_t total_batches = (n_samples + a.batch - 1) / a.batch;
     nb = (int64_t)std::min<uint64_t>((uint64_t)nb, total_batches);
-    const uint32_t batch_bits = bits_for((uint64_t)nb);
-    const uint32_t key_bits = batch_bits + row_bits;
     const int64_t max_chunk = nb * a.batch;
     const int64_t max_items = max_chunk * R;
-    const int ntiles = (int)((max_items + kRsTile - 1) / kRsTile);
+    const uint32_t parts = (uint32_t)((a.batch * R + kPartItems - 1) / kPartItems);
     const bool persistent = a.mode == LINE_MODE_PERSISTENT;
-    // long shared segments (more than kChunk entries) per batch, at most
+    // shared segments (two or more entries) and long ones (more than kChunk)
+    // per batch, at most
+    const uint32_t mcap = (uint32_t)(a.batch * R / 2 + 1);
     const uint32_t lcap = (uint32_t)(a.batch * R / (kChunk + 1) + 1);
 
     cudaError_t e;
@@ -1114,26 +1226,26 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     // before that phase is done
     if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
     if (!ensure(ws->items0, sizeof(uint64_t) * max_items) || !ensure(ws->items1, sizeof(uint64_t) * max_items) ||
-        !ensure(ws->hist, sizeof(uint32_t) * (size_t)kRsBins * ntiles) ||
-        !ensure(ws->scan_tiles, sizeof(uint32_t) * (scan_tiles((int64_t)kRsBins * ntiles + max_items) + 2)) ||
-        !ensure(ws->seg_start, sizeof(uint32_t) * (max_items + 1)) || !ensure(ws->counters, 256) ||
+        !ensure(ws->gcnt, sizeof(uint32_t) * (size_t)nb * parts * kBuckets) ||
+        !ensure(ws->boff, sizeof(uint32_t) * (size_t)nb * (kBuckets + 1)) || !ensure(ws->counters, 256) ||
         !ensure(ws->slab, sizeof(float) * (size_t)max_items * a.dim))
         return e;
     for (auto& cs : ws->set) {
         if (!ensure(cs.rec, sizeof(int32_t) * max_items) || !ensure(cs.eta, sizeof(float) * (nb + 1)) ||
-            !ensure(cs.slot_info, sizeof(uint2) * max_items) || !ensure(cs.mdesc, sizeof(uint4) * max_items) ||
-            !ensure(cs.mseg_id, sizeof(uint32_t) * max_items) || !ensure(cs.batch_mseg, sizeof(uint32_t) * (nb + 1)) ||
-            !ensure(cs.ldesc, sizeof(uint4) * (size_t)nb * lcap) || !ensure(cs.lcount, sizeof(uint32_t) * (nb + 1)))
+            !ensure(cs.slot_info, sizeof(uint2) * max_items) || !ensure(cs.mdesc, sizeof(uint4) * (size_t)nb * mcap) ||
+            !ensure(cs.mcount, sizeof(uint32_t) * (nb + 1)) || !ensure(cs.ldesc, sizeof(uint4) * (size_t)nb * lcap) ||
+            !ensure(cs.lcount, sizeof(uint32_t) * (nb + 1)))
             return e;
         if (persistent && (!ensure(cs.slot_prev, sizeof(int32_t) * max_items) ||
                            !ensure(cs.arrive, sizeof(uint32_t) * max_items) ||
-                           !ensure(cs.item_base, sizeof(uint64_t) * (nb + 1))))
+                           !ensure(cs.item_base, sizeof(uint64_t) * (nb + 1)) ||
+                           !ensure(cs.nseg, sizeof(uint32_t) * (nb + 1))))
             return e;
         cs.data_pending = false;
     }
     if (persistent) {
-        if (!ensure(ws->rowitems0, sizeof(uint64_t) * max_items) || !ensure(ws->rowitems1, sizeof(uint64_t) * max_items) ||
-            !ensure(ws->prev, sizeof(int32_t) * max_items))
+        if (!ensure(ws->sorted_row, sizeof(uint32_t) * max_items) || !ensure(ws->seghead, sizeof(uint32_t) * max_items) ||
+            !ensure(ws->batch_applied, sizeof(uint32_t) * (nb + 1)))
             return e;
         // generation flags start at zero and are never reset: a chunk's
         // flags are "done" when they equal its generation number
@@ -1148,6 +1260,12 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     if (!data) {
         *err = "unsupported dim";
         return cudaErrorInvalidValue;
+    }
+    const size_t sort_smem = (size_t)kSortBucketsPerCta * 2 * kWarpSortCap * sizeof(uint64_t);
+    static bool sort_attr = false;
+    if (!sort_attr) {
+        cudaFuncSetAttribute(k_bucket_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem);
+        sort_attr = true;
     }
     cudaStream_t ps = ws->prep;
     // the pre-pass reads the graph and alias tables made on the caller's stream
@@ -1165,10 +1283,24 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     pp.batch = a.batch;
     pp.K = a.K;
     pp.order = a.order;
-    pp.row_bits = row_bits;
+    pp.items = (uint64_t*)ws->items0.p;
 
-    uint32_t* n_segs_dev = (uint32_t*)ws->counters.p;
-    uint32_t* n_mseg_dev = (uint32_t*)ws->counters.p + 1;
+    GroupParams gq{};
+    gq.batch = a.batch;
+    gq.R = (uint32_t)R;
+    gq.K = (uint32_t)a.K;
+    gq.parts = parts;
+    gq.row_bits = row_bits;
+    gq.items = (const uint64_t*)ws->items0.p;
+    gq.bucketed = (uint64_t*)ws->items1.p;
+    gq.tmp = (uint64_t*)ws->items0.p;  // the draws are consumed by the bucketing before the sort
+    gq.gcnt = (uint32_t*)ws->gcnt.p;
+    gq.boff = (uint32_t*)ws->boff.p;
+    gq.mcap = mcap;
+    gq.lcap = lcap;
+    gq.sorted_row = persistent ? (uint32_t*)ws->sorted_row.p : nullptr;
+    gq.seghead = persistent ? (uint32_t*)ws->seghead.p : nullptr;
+
     uint32_t* abort_word = (uint32_t*)ws->counters.p + 16;
 
     DataParams dp{};
@@ -1178,6 +1310,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     dp.K = a.K;
     dp.n_nodes = a.n_nodes;
     dp.row_bits = row_bits;
+    dp.mcap = mcap;
     dp.lcap = lcap;
     dp.slab = (float*)ws->slab.p;
     dp.batch = a.batch;
@@ -1186,6 +1319,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     dp.alpha_neg = (float)a.alpha_neg;
     dp.status = status;
     dp.seg_done = (uint32_t*)ws->seg_done.p;
+    dp.batch_applied = (uint32_t*)ws->batch_applied.p;
     dp.spin_limit = a.spin_limit;
     dp.abort_word = abort_word;
 
@@ -1198,7 +1332,6 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     std::vector<ChunkRec> chunk_log;
     size_t n_ev = 0;
     cudaEvent_t ev = nullptr;
-    const unsigned seg_grid = (unsigned)std::min<int64_t>((max_items + 255) / 256, 152 * 16);
     int c = 0;
     for (uint64_t t = a.t_begin; t < a.t_end; t += (uint64_t)max_chunk, ++c) {
         ChunkSet& cset = ws->set[c & 1];
@@ -1216,53 +1349,36 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         pp.t_chunk = t;
         pp.chunk_samples = cs;
         pp.rec = (int32_t*)cset.rec.p;
-        pp.items = (uint64_t*)ws->items0.p;
         {
             const int64_t work = cs * (a.K + 1);
             const unsigned g = (unsigned)std::min<int64_t>((work + 255) / 256, 152 * 64);
             k_chunk_draws<<<g, 256, 0, ps>>>(pp);
             k_batch_eta<<<(unsigned)((cb + 127) / 128), 128, 0, ps>>>(cb, t, a.batch, a.lr0, a.lr_schedule, a.lr_floor,
                                                                       a.lr_total, (float*)cset.eta.p);
-            launches += 2;
         }
-        // stable sort by (batch, row)
-        uint64_t* sorted = nullptr;
-        if ((e = radix_sort((uint64_t*)ws->items0.p, (uint64_t*)ws->items1.p, n_items, key_bits, (uint32_t*)ws->hist.p,
-                            (uint32_t*)ws->scan_tiles.p, ps, &sorted, &launches)) != cudaSuccess)
-            return e;
-        // segments, slot positions, shared-segment descriptors
-        if ((e = device_scan<uint32_t>(n_items, GenHead{sorted},
-                                       OutSegStart{sorted, (uint32_t*)ws->seg_start.p, n_items, n_segs_dev},
-                                       (uint32_t*)ws->scan_tiles.p, ps)) != cudaSuccess)
-            return e;
-        k_seg_meta<<<seg_grid, 256, 0, ps>>>(sorted, (const uint32_t*)ws->seg_start.p, n_segs_dev, row_bits,
-                                             (uint32_t)R, (uint2*)cset.slot_info.p,
-                                             persistent ? (uint64_t*)ws->rowitems0.p : nullptr);
+        gq.n_batches = cb;
+        gq.chunk_samples = cs;
+        gq.slot_info = (uint2*)cset.slot_info.p;
+        gq.mdesc = (uint4*)cset.mdesc.p;
+        gq.mcount = (uint32_t*)cset.mcount.p;
+        gq.ldesc = (uint4*)cset.ldesc.p;
+        gq.lcount = (uint32_t*)cset.lcount.p;
+        gq.nseg = persistent ? (uint32_t*)cset.nseg.p : nullptr;
+        if ((e = cudaMemsetAsync(cset.mcount.p, 0, sizeof(uint32_t) * (cb + 1), ps)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(cset.lcount.p, 0, sizeof(uint32_t) * (cb + 1), ps)) != cudaSuccess) return e;
-        OutMulti om{sorted, (const uint32_t*)ws->seg_start.p, n_segs_dev, n_items, a.K,
-                    (uint4*)cset.mdesc.p, (uint32_t*)cset.mseg_id.p, n_mseg_dev, row_bits,
-                    (uint4*)cset.ldesc.p, (uint32_t*)cset.lcount.p, lcap};
-        if ((e = device_scan<uint32_t>(n_items, GenMulti{(const uint32_t*)ws->seg_start.p, n_segs_dev}, om,
-                                       (uint32_t*)ws->scan_tiles.p, ps)) != cudaSuccess)
-            return e;
-        k_batch_mseg<<<seg_grid, 256, 0, ps>>>((const uint4*)cset.mdesc.p, n_mseg_dev, row_bits, cb,
-                                               (uint32_t*)cset.batch_mseg.p);
-        launches += 3 + 1 + 3 + 1;
+        if (persistent && (e = cudaMemsetAsync(cset.nseg.p, 0, sizeof(uint32_t) * (cb + 1), ps)) != cudaSuccess) return e;
+        k_bucket_count<<<dim3(parts, cb), kBucketThreads, 0, ps>>>(gq);
+        k_bucket_scatter<<<dim3(parts, cb), kBucketThreads, 0, ps>>>(gq);
+        k_bucket_sort<<<dim3(kBuckets / kSortBucketsPerCta, cb), kSortThreads, sort_smem, ps>>>(gq);
+        launches += 5;
         if (persistent) {
-            // latest earlier segment of each row: sort segments by row
-            k_pad_rowitems<<<seg_grid, 256, 0, ps>>>((uint64_t*)ws->rowitems0.p, n_segs_dev, n_items, 1u << row_bits);
-            uint64_t* rsorted = nullptr;
-            if ((e = radix_sort((uint64_t*)ws->rowitems0.p, (uint64_t*)ws->rowitems1.p, n_items, row_bits + 1,
-                                (uint32_t*)ws->hist.p, (uint32_t*)ws->scan_tiles.p, ps, &rsorted, &launches)) !=
-                cudaSuccess)
-                return e;
-            k_prev_seg<<<seg_grid, 256, 0, ps>>>(rsorted, n_segs_dev, (int32_t*)ws->prev.p);
-            k_slot_prev<<<seg_grid, 256, 0, ps>>>((const uint2*)cset.slot_info.p, (const int32_t*)ws->prev.p, n_items,
-                                                  (int32_t*)cset.slot_prev.p);
-            k_item_base<<<1, 32, 0, ps>>>((const uint32_t*)cset.batch_mseg.p, cb, a.batch, cs,
+            const unsigned g = (unsigned)std::min<int64_t>((n_items + 255) / 256, 152 * 16);
+            k_prev_lookup<<<g, 256, 0, ps>>>(gq, (const int32_t*)cset.rec.p, a.order == 2 ? (uint32_t)a.n_nodes : 0u,
+                                             (int32_t*)cset.slot_prev.p);
+            k_item_base<<<1, 32, 0, ps>>>((const uint32_t*)cset.mcount.p, cb, a.batch, cs,
                                           groups_per_warp(a.dim, a.dtype), (uint64_t*)cset.item_base.p);
             if ((e = cudaMemsetAsync(cset.arrive.p, 0, sizeof(uint32_t) * n_items, ps)) != cudaSuccess) return e;
-            launches += 4;
+            launches += 2;
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (a.timing) {
@@ -1279,12 +1395,12 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         dp.rec = (const int32_t*)cset.rec.p;
         dp.slot_info = (const uint2*)cset.slot_info.p;
         dp.mdesc = (const uint4*)cset.mdesc.p;
-        dp.batch_mseg = (const uint32_t*)cset.batch_mseg.p;
+        dp.mcount = (const uint32_t*)cset.mcount.p;
         dp.ldesc = (const uint4*)cset.ldesc.p;
         dp.lcount = (const uint32_t*)cset.lcount.p;
         dp.eta = (const float*)cset.eta.p;
         dp.slot_prev = (const int32_t*)cset.slot_prev.p;
-        dp.mseg_id = (const uint32_t*)cset.mseg_id.p;
+        dp.nseg = (const uint32_t*)cset.nseg.p;
         dp.arrive = (uint32_t*)cset.arrive.p;
         dp.item_base = (const uint64_t*)cset.item_base.p;
         dp.t_chunk = t;
@@ -1292,6 +1408,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         dp.n_batches = cb;
         if (persistent) {
             if ((e = cudaMemsetAsync(abort_word, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(ws->batch_applied.p, 0, sizeof(uint32_t) * (cb + 1), s)) != cudaSuccess) return e;
             dp.gen = ++ws->gen;
         }
         if ((e = data(dp, a.warps_per_block, s)) != cudaSuccess) return e;
