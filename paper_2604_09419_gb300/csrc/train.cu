@@ -210,6 +210,84 @@ __device__ __forceinline__ T rec_entry(uint32_t gm, T held, const T* row, int id
 // Per-sample work.  Returns false when a bounded wait ran out (persistent).
 // ctx_stage: this warp's shared staging area, (K+1) x 32 lanes x E floats.
 // ---------------------------------------------------------------------------
+// Register-resident gather body for K + 1 <= 8: the K+1 context rows stay in
+// registers; the dots, their reductions and the K+1 sigmoids are independent
+// chains.  Same arithmetic, in the same order, as the staged body below.
+template <int D, int DT>
+__device__ __forceinline__ void sample_body_reg(const DataParams& p, int lig, bool active, float eta, uint64_t t0,
+                                                uint32_t gm, int32_t r0, uint2 i0, const int32_t* rec,
+                                                const uint2* info) {
+    using G = Geom<D, DT>;
+    constexpr int JB = 8;
+    const int32_t u = __shfl_sync(gm, r0, 0, G::L);
+    float xu[G::E];
+    float c[JB][G::E];
+    load_row<D, DT>(p.U, u, lig, xu);
+#pragma unroll
+    for (int j = 0; j < JB; ++j) {
+        const int32_t y = rec_entry<G::L>(gm, r0, rec, 1 + j, active && j <= p.K);
+        if (j <= p.K) load_row<D, DT>(p.C, y, lig, c[j]);
+    }
+    float sj[JB];
+#pragma unroll
+    for (int j = 0; j < JB; ++j) {
+        sj[j] = 0.0f;
+#pragma unroll
+        for (int e = 0; e < G::E; ++e) sj[j] = fmaf(xu[e], c[j][e], sj[j]);
+    }
+#pragma unroll
+    for (int o = G::L / 2; o >= 1; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < JB; ++j) sj[j] += __shfl_xor_sync(0xFFFFFFFFu, sj[j], o);
+    float g[JB];
+#pragma unroll
+    for (int j = 0; j < JB; ++j) {
+        const float sig = 1.0f / (1.0f + expf(-sj[j]));
+        g[j] = j == 0 ? eta * (1.0f - sig) : -eta * p.alpha_neg * sig;
+    }
+    const uint32_t ctx_table = p.order == 2 ? 1u : 0u;
+    const float etalam = eta * p.lambda;
+    float du[G::E];
+#pragma unroll
+    for (int e = 0; e < G::E; ++e) du[e] = 0.0f;
+#pragma unroll
+    for (int j = 0; j < JB; ++j) {
+        if (j > p.K) continue;
+#pragma unroll
+        for (int e = 0; e < G::E; ++e) du[e] = fmaf(g[j], c[j][e], du[e]);
+        const uint2 inf = rec_entry<G::L>(gm, i0, info, 1 + j, active);
+        const int32_t y = rec_entry<G::L>(gm, r0, rec, 1 + j, active);
+        if (active) {
+            if (inf.x & kSingleBit) {
+                const float decay = 1.0f * etalam;
+                float x[G::E];
+#pragma unroll
+                for (int e = 0; e < G::E; ++e) x[e] = fmaf(-decay, c[j][e], c[j][e]) + g[j] * xu[e];
+                store_row<D, DT>(p.C, y, lig, x, p.seed, t0, ctx_table);
+            } else {
+                float4* dst = reinterpret_cast<float4*>(p.slab + (int64_t)inf.x * D + lig * G::E);
+#pragma unroll
+                for (int q = 0; q < G::E / 4; ++q)
+                    st_cg(dst + q, make_float4(g[j] * xu[4 * q], g[j] * xu[4 * q + 1], g[j] * xu[4 * q + 2],
+                                               g[j] * xu[4 * q + 3]));
+            }
+        }
+    }
+    const uint2 inf0 = shfl_w(gm, i0, 0, G::L);
+    if (active) {
+        if (inf0.x & kSingleBit) {
+            const float decay = (float)(p.K + 1) * etalam;
+#pragma unroll
+            for (int e = 0; e < G::E; ++e) xu[e] = fmaf(-decay, xu[e], xu[e]) + du[e];
+            store_row<D, DT>(p.U, u, lig, xu, p.seed, t0, 0u);
+        } else {
+            float4* dst = reinterpret_cast<float4*>(p.slab + (int64_t)inf0.x * D + lig * G::E);
+#pragma unroll
+            for (int q = 0; q < G::E / 4; ++q) st_cg(dst + q, make_float4(du[4 * q], du[4 * q + 1], du[4 * q + 2], du[4 * q + 3]));
+        }
+    }
+}
+
 template <int D, int DT, bool PERSIST, bool PDL = false>
 __device__ __forceinline__ bool sample_item(const DataParams& p, int b, int64_t s_local, int lig, int lane,
                                             bool active, float eta, uint64_t t0, float* ctx_stage) {
@@ -234,6 +312,12 @@ __device__ __forceinline__ bool sample_item(const DataParams& p, int b, int64_t 
         }
         __syncwarp(gm);
         if (!__all_sync(gm, ok)) return false;
+    }
+    if constexpr (!PERSIST && G::E <= 4) {
+        if (p.K < 8) {
+            sample_body_reg<D, DT>(p, lig, active, eta, t0, gm, r0, i0, rec, info);
+            return true;
+        }
     }
     const int32_t u = __shfl_sync(gm, r0, 0, G::L);
     float xu[G::E];
@@ -1075,11 +1159,11 @@ static uint32_t bits_for(uint64_t v) {  // bits to hold values 0..v-1
 }
 
 template <int D, int DT>
-static int gather_warps(const DataParams& p, int requested, int cap, size_t* smem_out) {
+static int gather_warps(const DataParams& p, int requested, int cap, size_t* smem_out, int dflt = 8) {
     using G = Geom<D, DT>;
     // staging: (K+1) context rows x 32 lanes x E floats per warp
     const size_t per_warp = (size_t)(p.K + 1) * 32 * G::E * sizeof(float);
-    int wpb = requested > 0 ? requested : 8;
+    int wpb = requested > 0 ? requested : dflt;
     wpb = std::min<int>(wpb, cap);
     wpb = std::max<int>(1, std::min<int>(wpb, (int)(kMaxSmem / per_warp)));
     *smem_out = (size_t)wpb * per_warp;
@@ -1106,7 +1190,8 @@ template <int D, int DT>
 static cudaError_t launch_data_batched(const DataParams& p, int warps_per_block, cudaStream_t s) {
     using G = Geom<D, DT>;
     size_t smem = 0;
-    const int wpb = gather_warps<D, DT>(p, warps_per_block, kMaxWarps, &smem);
+    // 4 warps per block: at ~70 registers a 4096-sample batch is one wave
+    const int wpb = gather_warps<D, DT>(p, warps_per_block, kMaxWarps, &smem, 4);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_gather<D, DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
@@ -1115,7 +1200,9 @@ static cudaError_t launch_data_batched(const DataParams& p, int warps_per_block,
     }
     const int64_t per_block = (int64_t)wpb * G::GPW;
     const int64_t apply_per_block = (int64_t)(kApplyThreads / 32) * G::GPW;
-    const int g_long = 16;
+    // long shared segments (more than kChunk entries, ~34 per batch on R-MAT 20)
+    // each get a CTA of their own
+    const int g_long = 64;
     cudaError_t e = cudaSuccess;
     for (int b = 0; b < p.n_batches && e == cudaSuccess; ++b) {
         const int64_t nb = std::min<int64_t>(p.batch, p.chunk_samples - (int64_t)b * p.batch);
