@@ -41,7 +41,7 @@ ALG_BYTES_UPDATE = 14 * ROW_BYTES_F32
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--mode", default="auto", choices=["auto", "batched", "persistent"])
@@ -49,7 +49,7 @@ def parse():
     p.add_argument("--samples-per-step", type=int, default=0, help="0: |E| = 16 * 2^scale")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-samples", type=int, default=1 << 21)
+    p.add_argument("--cpu-samples", type=int, default=1 << 20)
     return p.parse_args()
 
 
