@@ -619,16 +619,22 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(DataParams p, int b, in
     const uint4* md = p.mdesc + (size_t)b * p.mcap;
     const uint64_t t0 = p.t_chunk + (uint64_t)b * (uint64_t)p.batch;
     const float eta = p.eta[b];
-    pdl_wait();  // the slab and the rows: written by the gather
     if ((int)blockIdx.x < g_long) {
-        for (uint32_t l = blockIdx.x; l < n_long; l += (uint32_t)g_long)
-            long_segment_cta<D, DT>(p, p.ldesc[(size_t)b * p.lcap + l], eta, t0, part);
+        // descriptors come from the pre-pass: read before the wait
+        uint4 d = blockIdx.x < n_long ? p.ldesc[(size_t)b * p.lcap + blockIdx.x] : make_uint4(0u, 0u, 0u, 0u);
+        pdl_wait();  // the slab and the rows: written by the gather
+        for (uint32_t l = blockIdx.x; l < n_long; l += (uint32_t)g_long) {
+            if (l != blockIdx.x) d = p.ldesc[(size_t)b * p.lcap + l];
+            long_segment_cta<D, DT>(p, d, eta, t0, part);
+        }
         return;
     }
     const int64_t groups = (int64_t)(gridDim.x - g_long) * (blockDim.x >> 5) * G::GPW;
-    for (int64_t m = ((int64_t)(blockIdx.x - g_long) * (blockDim.x >> 5) + warp) * G::GPW + grp; m < n_m;
-         m += groups) {
-        const uint4 d = md[m];
+    const int64_t m0 = ((int64_t)(blockIdx.x - g_long) * (blockDim.x >> 5) + warp) * G::GPW + grp;
+    uint4 d = m0 < n_m ? md[m0] : make_uint4(0u, 0u, 0u, 0u);
+    pdl_wait();  // the slab and the rows: written by the gather
+    for (int64_t m = m0; m < n_m; m += groups) {
+        if (m != m0) d = md[m];
         if (d.y & kLongBit) continue;
         segment_item<D, DT, false>(p, d, lig, true, eta, t0);
     }
@@ -939,8 +945,8 @@ constexpr uint32_t kWarpSortCap = 512;  // bucket sizes ranked directly in share
 constexpr int kSortBucketsPerCta = kSortThreads / 32;
 
 // One warp per (bucket, batch): sort the bucket's items by row (stable), then
-// find its segments.  Small buckets: every item's rank is the number of items
-// with a smaller (row, index); large ones: LSD radix passes in global memory.
+// find its segments.  Small buckets: a bitonic sort of (row, index) in shared
+// memory; large ones: LSD radix passes in global memory.
 __global__ void __launch_bounds__(kSortThreads) k_bucket_sort(GroupParams q) {
     extern __shared__ uint64_t sbuf[];  // per warp: 2 x kWarpSortCap items
     __shared__ uint32_t wcnt[kSortBucketsPerCta][kBuckets];
@@ -955,22 +961,43 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort(GroupParams q) {
     if (c == 0) return;
     const uint64_t* a;
     if (c <= kWarpSortCap) {
+        // bitonic sort of the unique keys (row << 32 | index) over the next
+        // power of two, padded with the largest key; then items by rank
         uint64_t* in = sbuf + (size_t)warp * 2 * kWarpSortCap;
-        uint64_t* out = in + kWarpSortCap;
-        for (uint32_t i = lane; i < c; i += 32) in[i] = q.bucketed[base + lo + i];
-        __syncwarp();
-        for (uint32_t i = lane; i < c; i += 32) {
-            const uint64_t it = in[i];
-            const uint32_t key = (uint32_t)(it >> 32);
-            uint32_t rank = 0;
-            for (uint32_t j = 0; j < c; ++j) {
-                const uint32_t kj = (uint32_t)(in[j] >> 32);
-                rank += (kj < key) || (kj == key && j < i);
+        uint64_t* key = in + kWarpSortCap;
+        uint32_t P = 32;
+        while (P < c) P <<= 1;
+        for (uint32_t i = lane; i < P; i += 32) {
+            if (i < c) {
+                const uint64_t it = q.bucketed[base + lo + i];
+                in[i] = it;
+                key[i] = (it & 0xFFFFFFFF00000000ull) | i;
+            } else {
+                key[i] = ~0ull;
             }
-            out[rank] = it;
         }
         __syncwarp();
-        a = out;
+        for (uint32_t kk = 2; kk <= P; kk <<= 1) {
+            for (uint32_t jj = kk >> 1; jj > 0; jj >>= 1) {
+                for (uint32_t t = lane; t < P / 2; t += 32) {
+                    const uint32_t i = ((t & ~(jj - 1)) << 1) | (t & (jj - 1));
+                    const uint32_t l = i + jj;
+                    const uint64_t x = key[i], y = key[l];
+                    if ((x > y) == ((i & kk) == 0)) {
+                        key[i] = y;
+                        key[l] = x;
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        // sorted items replace the keys in place (each lane reads, then writes, its own slots)
+        for (uint32_t r = lane; r < c; r += 32) {
+            const uint64_t it = in[(uint32_t)key[r]];
+            key[r] = it;
+        }
+        __syncwarp();
+        a = key;
     } else {  // a large bucket (a very skewed draw): radix passes over all row bits
         uint64_t* x = q.bucketed + base + lo;
         uint64_t* y = q.tmp + base + lo;
