@@ -192,6 +192,28 @@ LINE_API line_status line_set_embeddings(line_ctx* ctx, int order, int which, co
  * Result in *out_host (host pointer). */
 LINE_API line_status line_eval_loss(line_ctx* ctx, int order, int K, uint64_t seed, int64_t m, double* out_host);
 
+/* Link-prediction AUC (Section VI judges embeddings by link prediction on
+ * held-out edges).  orders: bit mask of the tables to use - 1 the order-1 U
+ * table, 2 the order-2 U table, 3 both.  A pair (u, v) scores the cosine of
+ * the concatenation over those orders of U_o[u] / |U_o[u]| and
+ * U_o[v] / |U_o[v]| (an all-zero row gives a zero block; a zero
+ * concatenation scores 0), in FP32.  AUC = (#(neg < pos) + #(neg == pos) / 2)
+ * / (n_pos n_neg) over all (positive, negative) pairs of scores, counted
+ * exactly in integers.
+ *   pos_src/pos_dst: n_pos >= 1 node ids of the positive pairs (held-out
+ *     edges); neg_src/neg_dst: n_neg >= 1 node ids of the negative pairs;
+ *     buffers (host or device), read during the call only.
+ *   scores_out: NULL, or a buffer of n_pos + n_neg floats (positives first).
+ *   counts_out: NULL, or a host array of 2: {#(neg < pos), #(neg == pos)}.
+ *   auc_out: host pointer.
+ * Errors: LINE_ERR_ARG (bad mask, counts, null pointers, or a node id out of
+ * range), LINE_ERR_STATE (a requested order has no tables), LINE_ERR_VALIDATE
+ * (a score is NaN: non-finite table values), LINE_ERR_OOM, LINE_ERR_CUDA.
+ * Allocates n_pos + n_neg pairs' worth of scratch per call; synchronises. */
+LINE_API line_status line_eval_auc(line_ctx* ctx, int orders, const int32_t* pos_src, const int32_t* pos_dst,
+                                   int64_t n_pos, const int32_t* neg_src, const int32_t* neg_dst, int64_t n_neg,
+                                   float* scores_out, uint64_t* counts_out, double* auc_out);
+
 /* Largest m accepted by line_eval_loss_noalloc. */
 #define LINE_NOALLOC_MAX_SAMPLES (1 << 20)
 

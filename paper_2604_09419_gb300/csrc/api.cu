@@ -98,6 +98,7 @@ line_status check_status(line_ctx* c, const char* what, bool timeout_sticky = tr
         return LINE_ERR_TIMEOUT;
     }
     if (st & DEV_ERR_INDEX) return fail(c, LINE_ERR_ARG, "%s: index out of range", what);
+    if (st & DEV_ERR_VALUE) return fail(c, LINE_ERR_VALIDATE, "%s: non-finite value", what);
     return LINE_OK;
 }
 
@@ -465,6 +466,57 @@ line_status line_eval_loss(line_ctx* c, int order, int K, uint64_t seed, int64_t
     if (terms) cudaFree(terms);
     if (tmp) cudaFree(tmp);
     if (e != cudaSuccess) return cuda_fail(c, e, "line_eval_loss");
+    return LINE_OK;
+}
+
+line_status line_eval_auc(line_ctx* c, int orders, const int32_t* pos_src, const int32_t* pos_dst, int64_t n_pos,
+                          const int32_t* neg_src, const int32_t* neg_dst, int64_t n_neg, float* scores_out,
+                          uint64_t* counts_out, double* auc_out) {
+    line_status st = enter(c);
+    if (st) return st;
+    if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_eval_auc: no graph");
+    if (orders < 1 || orders > 3 || n_pos < 1 || n_neg < 1 || n_pos + n_neg >= (1ll << 31) || !pos_src || !pos_dst ||
+        !neg_src || !neg_dst || !auc_out)
+        return fail(c, LINE_ERR_ARG, "line_eval_auc: bad arguments");
+    ScoreTables t{};
+    for (int o = 1; o <= 2; ++o) {
+        if (!(orders & o)) continue;
+        if (!c->tab[o].ready) return fail(c, LINE_ERR_STATE, "line_eval_auc: no tables of order %d", o);
+        t.U[t.n] = c->tab[o].U;
+        t.dim[t.n] = c->tab[o].dim;
+        t.dtype[t.n] = c->tab[o].dtype;
+        ++t.n;
+    }
+    const int64_t n = n_pos + n_neg;
+    int32_t* pairs = nullptr;
+    float* scores = nullptr;
+    void* tmp = nullptr;
+    unsigned long long counts[2] = {0, 0};
+    cudaStream_t s = c->stream;
+    cudaError_t e = cudaMalloc(&pairs, sizeof(int32_t) * 2 * n);
+    if (e == cudaSuccess) e = cudaMalloc(&scores, sizeof(float) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&tmp, auc_tmp_bytes(n_pos, n_neg));
+    int32_t* src = pairs;
+    int32_t* dst = pairs + n;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(src, pos_src, sizeof(int32_t) * n_pos, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(src + n_pos, neg_src, sizeof(int32_t) * n_neg, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst, pos_dst, sizeof(int32_t) * n_pos, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dst + n_pos, neg_dst, sizeof(int32_t) * n_neg, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = eval_auc(t, src, dst, n_pos, n_neg, c->n_nodes, scores, tmp, c->status, s);
+    if (e == cudaSuccess && scores_out)
+        e = cudaMemcpyAsync(scores_out, scores, sizeof(float) * n, cudaMemcpyDefault, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(counts, tmp, sizeof counts, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (pairs) cudaFree(pairs);
+    if (scores) cudaFree(scores);
+    if (tmp) cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(c, e, "line_eval_auc");
+    if ((st = check_status(c, "line_eval_auc"))) return st;
+    if (counts_out) {
+        counts_out[0] = counts[0];
+        counts_out[1] = counts[1];
+    }
+    *auc_out = (double)(2 * counts[0] + counts[1]) / (2.0 * (double)n_pos * (double)n_neg);
     return LINE_OK;
 }
 

@@ -21,6 +21,7 @@ enum : uint32_t {
     DEV_ERR_TIMEOUT = 1u << 1,  // a bounded wait ran out
     DEV_ERR_GRAPH = 1u << 2,    // graph validation failed
     DEV_ERR_ALIAS = 1u << 3,    // alias construction invariant failed
+    DEV_ERR_VALUE = 1u << 4,    // a computed value was not finite
 };
 
 constexpr uint64_t kQ = 1ull << 32;
@@ -141,6 +142,20 @@ cudaError_t debug_wait(uint32_t* flag, int64_t limit, uint32_t* status, cudaStre
 cudaError_t eval_loss_terms(const void* U, const void* Ctx, int dtype, int dim, int K, const int32_t* src,
                             const int32_t* dst, const uint2* edge_tab, int64_t n_arcs, const uint2* neg_tab,
                             int64_t n_nodes, uint64_t seed, int64_t m, double* terms, cudaStream_t s);
+
+// auc.cu: link-prediction scores and AUC
+struct ScoreTables {
+    int n;  // number of tables (orders) concatenated, 1 or 2
+    const void* U[2];
+    int dim[2];
+    int dtype[2];
+};
+size_t auc_tmp_bytes(int64_t n_pos, int64_t n_neg);
+// src/dst: n_pos positive pairs then n_neg negative pairs (device).  scores:
+// [n_pos + n_neg] FP32 out.  tmp: auc_tmp_bytes(n_pos, n_neg) bytes, 256-byte
+// aligned; on return its first two u64 are {#(neg < pos), #(neg == pos)}.
+cudaError_t eval_auc(const ScoreTables& t, const int32_t* src, const int32_t* dst, int64_t n_pos, int64_t n_neg,
+                     int64_t n_nodes, float* scores, void* tmp, uint32_t* status, cudaStream_t s);
 
 // noalloc.cu: the loss evaluation with its scratch in a fixed device array
 cudaError_t noalloc_scratch_address(int device, double** out);

@@ -43,6 +43,7 @@ __all__ = [
     "tiny_chung_lu",
     "rmat20",
     "split_edges",
+    "non_edges",
 ]
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -54,6 +55,7 @@ STREAM_CHUNG_LU = 5
 STREAM_RMAT = 6
 STREAM_DIRECTED = 7
 STREAM_SPLIT = 8
+STREAM_NON_EDGE = 9
 
 
 @dataclasses.dataclass
@@ -266,3 +268,34 @@ def split_edges(g: Graph, frac: float = 0.1, seed: int = 0):
     train = Graph(g.n_nodes, g.src[keep], g.dst[keep], g.w[keep], g.directed, g.name + "_train")
     once = held & (g.src < g.dst)
     return train, g.src[once].copy(), g.dst[once].copy()
+
+
+def non_edges(g: Graph, count: int, seed: int = 0) -> tuple[np.ndarray, np.ndarray]:
+    """``count`` uniform node pairs ``u != v`` that are not arcs of ``g``.
+
+    Pairs are drawn in counter order from one SplitMix64 stream and rejected
+    when ``u == v`` or ``(u, v)`` is an arc of ``g`` (for a symmetric graph that
+    also excludes ``(v, u)``); the first ``count`` accepted pairs are returned,
+    so the result is a pure function of ``(g, count, seed)``.  These are the
+    negative pairs of a link-prediction AUC.
+    """
+    n = np.uint64(g.n_nodes)
+    arcs = np.sort(g.src.astype(np.uint64) * n + g.dst.astype(np.uint64))
+    out_u, out_v = [], []
+    have, ctr = 0, 0
+    while have < count:
+        m = max(2 * (count - have), 1024)
+        c = np.arange(ctr, ctr + m, dtype=np.uint64)
+        ctr += m
+        u = (_hash(seed, STREAM_NON_EDGE, 2 * c) % n).astype(np.int64)
+        v = (_hash(seed, STREAM_NON_EDGE, 2 * c + np.uint64(1)) % n).astype(np.int64)
+        key = u.astype(np.uint64) * n + v.astype(np.uint64)
+        pos = np.searchsorted(arcs, key)
+        hit = (pos < arcs.size) & (arcs[np.minimum(pos, max(arcs.size - 1, 0))] == key) if arcs.size else np.zeros(m, bool)
+        ok = (u != v) & ~hit
+        take = min(count - have, int(ok.sum()))
+        out_u.append(u[ok][:take])
+        out_v.append(v[ok][:take])
+        have += take
+    return (np.concatenate(out_u).astype(np.int32) if out_u else np.zeros(0, np.int32),
+            np.concatenate(out_v).astype(np.int32) if out_v else np.zeros(0, np.int32))

@@ -69,6 +69,7 @@ def _load():
         "line_set_embeddings": (i32, [vp, i32, i32, vp, i32, vp, i64]),
         "line_eval_loss": (i32, [vp, i32, i32, u64, i64, ctypes.POINTER(dbl)]),
         "line_eval_loss_noalloc": (i32, [vp, i32, i32, u64, i64, ctypes.POINTER(dbl)]),
+        "line_eval_auc": (i32, [vp, i32, vp, vp, i64, vp, vp, i64, vp, vp, ctypes.POINTER(dbl)]),
         "line_get_stats": (i32, [vp, ctypes.POINTER(Stats)]),
         "line_reset_stats": (i32, [vp]),
         "line_synchronize": (i32, [vp]),
@@ -85,7 +86,7 @@ lib = _load()
 EXPORTED = ("line_train_opts_default", "line_status_string", "line_create", "line_destroy", "line_last_error",
             "line_build_alias", "line_get_graph_info", "line_get_alias", "line_sample_debug",
             "line_init_embeddings", "line_train_steps", "line_get_embeddings", "line_set_embeddings",
-            "line_eval_loss", "line_eval_loss_noalloc", "line_get_stats", "line_reset_stats", "line_synchronize", "line_debug_wait_timeout")
+            "line_eval_loss", "line_eval_loss_noalloc", "line_eval_auc", "line_get_stats", "line_reset_stats", "line_synchronize", "line_debug_wait_timeout")
 
 
 class LineError(RuntimeError):
@@ -186,6 +187,15 @@ class Context:
         out = ctypes.c_double()
         self._ck(lib.line_eval_loss_noalloc(self.h, order, K, seed, m, ctypes.byref(out)))
         return out.value
+
+    def eval_auc(self, orders, pos_src, pos_dst, neg_src, neg_dst, scores=None):
+        """Link-prediction AUC; returns (auc, (#(neg < pos), #(neg == pos)))."""
+        out = ctypes.c_double()
+        counts = np.zeros(2, np.uint64)
+        self._ck(lib.line_eval_auc(self.h, orders, ptr(pos_src), ptr(pos_dst), int(pos_src.shape[0]), ptr(neg_src),
+                                   ptr(neg_dst), int(neg_src.shape[0]), ptr(scores), counts.ctypes.data,
+                                   ctypes.byref(out)))
+        return out.value, (int(counts[0]), int(counts[1]))
 
     def stats(self) -> Stats:
         s = Stats()

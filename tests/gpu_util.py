@@ -78,3 +78,29 @@ def oracle_run(name, order, dim, K, n, seed, B, init_seed, **kw):
     C = np.zeros_like(U) if order == 2 else None
     O.train(T, U, C, order=order, K=K, n_samples=n, seed=seed, batch=B, **kw)
     return U, C
+
+
+def bf16_round(x) -> np.ndarray:
+    """Round to the nearest BF16 value (ties to even), returned as float32."""
+    b = np.ascontiguousarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) >> 16 << 16
+    return b.astype(np.uint32).view(np.float32)
+
+
+def upload_tables(ctx, order, U, C=None, dtype=0):
+    """Install host tables (e.g. the oracle's) as the context's tables of
+    `order`; returns the FP64 copies of the values actually stored (FP32, or
+    BF16-rounded when dtype is BF16)."""
+    from paper_2604_09419_gb300 import line as L
+    dim = U.shape[1]
+    ctx.init_embeddings(order, dim, dtype, seed=0)
+    out = []
+    for which, X in ((L.WHICH_U, U), (L.WHICH_C, C)):
+        if X is None:
+            continue
+        X32 = np.ascontiguousarray(X, np.float32)
+        if dtype == L.DTYPE_BF16:
+            X32 = bf16_round(X32)
+        ctx.set_embeddings(order, which, X32, L.DTYPE_F32)
+        out.append(X32.astype(np.float64))
+    return out if len(out) > 1 else out[0]

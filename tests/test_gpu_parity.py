@@ -146,18 +146,22 @@ def test_resume_split_is_bitwise(ctx):
     assert np.array_equal(U, full[0]) and np.array_equal(C, full[1])
 
 
-def test_loss_matches_oracle_on_gpu_tables(ctx):
+def test_loss_matches_oracle_on_the_same_tables(ctx):
+    """The GPU loss of oracle-trained tables, installed through the ABI,
+    against the oracle's loss of the same (FP32-rounded) tables."""
     g = G.graph("tiny")
     G.upload(ctx, g)
-    U, C = _run(ctx, g, 2, 16, 5, 50_000, 256)
     T = G.oracle_tables("tiny")
+    U, C = G.oracle_run("tiny", 2, 16, 5, 50_000, 7, 256, 3)
+    U, C = G.upload_tables(ctx, 2, U, C)
     for m in (1, 1000, 65_537):
         got = ctx.eval_loss(2, 5, 9, m)
-        want = O.eval_loss(T, U.astype(np.float64), C.astype(np.float64), order=2, K=5, seed=9, m=m)
+        want = O.eval_loss(T, U, C, order=2, K=5, seed=9, m=m)
         assert abs(got - want) <= 1e-9 * abs(want), (m, got, want)
-    U1, _ = _run(ctx, g, 1, 16, 5, 20_000, 256)
+    U1, _ = G.oracle_run("tiny", 1, 16, 5, 20_000, 8, 256, 4)
+    U1 = G.upload_tables(ctx, 1, U1)
     got = ctx.eval_loss(1, 5, 9, 4000)
-    want = O.eval_loss(T, U1.astype(np.float64), None, order=1, K=5, seed=9, m=4000)
+    want = O.eval_loss(T, U1, None, order=1, K=5, seed=9, m=4000)
     assert abs(got - want) <= 1e-9 * abs(want)
 
 
