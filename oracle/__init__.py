@@ -71,6 +71,8 @@ def lib():
             L = ctypes.CDLL(path)
             L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
             L.orc_philox4x32_10.restype = None
+            L.orc_draw_words.argtypes = [_u64, _u32, _u32, _u64, _i64, _u32p]
+            L.orc_draw_words.restype = None
             L.orc_neg_weights.argtypes = [_i64, _i64, _i32p, ctypes.c_void_p, _f64p]
             L.orc_neg_weights.restype = _int
             L.orc_fixed_sum.argtypes = [_i64, _f64p]
@@ -102,6 +104,13 @@ def philox(ctr, key) -> np.ndarray:
     """Philox4x32-10 of one 128-bit counter under one 64-bit key (SC'11)."""
     out = np.zeros(4, np.uint32)
     lib().orc_philox4x32_10(np.asarray(ctr, np.uint32), np.asarray(key, np.uint32), out)
+    return out
+
+
+def draw_words(seed: int, domain: int, call: int, t0: int, count: int) -> np.ndarray:
+    """[count][4] Philox words of draws t0.. of one (domain, call)."""
+    out = np.zeros((count, 4), np.uint32)
+    lib().orc_draw_words(seed, domain, call, t0, count, out.reshape(-1))
     return out
 
 

@@ -62,6 +62,12 @@ static void draw_words(uint64_t seed, uint32_t domain, uint64_t t, uint32_t call
     orc_philox4x32_10(ctr, key, w);
 }
 
+/* Words of `count` consecutive draws t0 .. t0+count-1 of one (domain, call):
+ * out[4 t + i] = word i of draw t. */
+void orc_draw_words(uint64_t seed, uint32_t domain, uint32_t call, uint64_t t0, int64_t count, uint32_t* out) {
+    for (int64_t t = 0; t < count; ++t) draw_words(seed, domain, t0 + (uint64_t)t, call, out + 4 * t);
+}
+
 /* ------------------------------------------------------------------------ */
 /* Eq. 1 weights.                                                            */
 /* ------------------------------------------------------------------------ */
