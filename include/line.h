@@ -68,6 +68,7 @@ enum { LINE_DTYPE_F32 = 0, LINE_DTYPE_BF16 = 1 };
 enum { LINE_TABLE_EDGE = 0, LINE_TABLE_NEG = 1 };
 enum { LINE_WHICH_U = 0, LINE_WHICH_C = 1 };
 enum { LINE_MODE_BATCHED = 0, LINE_MODE_PERSISTENT = 1 };
+enum { LINE_SCORE_DOT = 0, LINE_SCORE_COSINE = 1 };
 
 /* Graph as directed arcs (an undirected edge is two arcs), Section II / V-A.
  * src, dst: n_arcs int32 node ids in [0, n_nodes); src must be
@@ -138,7 +139,9 @@ LINE_API const char* line_last_error(const line_ctx* ctx);
  * items (m > 2^32) by the sweep rule: heavy items in index order top up the
  * lights in index order, a heavy item whose remaining mass r falls below
  * 2^32 becomes a light bucket with thr = r topped up by the next heavy one.
- * Replaces any previous graph and drops the embedding tables.
+ * Replaces any previous graph.  Embedding tables (and the warm-start MLP)
+ * are kept when the new graph has the same n_nodes - so training can
+ * continue on a changed edge set - and dropped otherwise.
  * Errors: LINE_ERR_ARG (sizes), LINE_ERR_VALIDATE (unsorted src, ids out of
  * range, non-positive or non-finite weights, a node set with no positive
  * weight), LINE_ERR_OOM. */
@@ -194,25 +197,94 @@ LINE_API line_status line_eval_loss(line_ctx* ctx, int order, int K, uint64_t se
 
 /* Link-prediction AUC (Section VI judges embeddings by link prediction on
  * held-out edges).  orders: bit mask of the tables to use - 1 the order-1 U
- * table, 2 the order-2 U table, 3 both.  A pair (u, v) scores the cosine of
- * the concatenation over those orders of U_o[u] / |U_o[u]| and
- * U_o[v] / |U_o[v]| (an all-zero row gives a zero block; a zero
- * concatenation scores 0), in FP32.  AUC = (#(neg < pos) + #(neg == pos) / 2)
- * / (n_pos n_neg) over all (positive, negative) pairs of scores, counted
- * exactly in integers.
+ * table, 2 the order-2 U table, 3 both.  With z(x) the concatenation over
+ * those orders of U_o[x], a pair (u, v) scores, in FP32,
+ *   LINE_SCORE_DOT:    z(u).z(v);
+ *   LINE_SCORE_COSINE: the cosine of the concatenations of U_o[u] / |U_o[u]|
+ *     and U_o[v] / |U_o[v]| (an all-zero row gives a zero block; a zero
+ *     concatenation scores 0).
+ * AUC = (#(neg < pos) + #(neg == pos) / 2) / (n_pos n_neg) over all
+ * (positive, negative) pairs of scores, counted exactly in integers.
  *   pos_src/pos_dst: n_pos >= 1 node ids of the positive pairs (held-out
  *     edges); neg_src/neg_dst: n_neg >= 1 node ids of the negative pairs;
  *     buffers (host or device), read during the call only.
  *   scores_out: NULL, or a buffer of n_pos + n_neg floats (positives first).
  *   counts_out: NULL, or a host array of 2: {#(neg < pos), #(neg == pos)}.
  *   auc_out: host pointer.
- * Errors: LINE_ERR_ARG (bad mask, counts, null pointers, or a node id out of
- * range), LINE_ERR_STATE (a requested order has no tables), LINE_ERR_VALIDATE
- * (a score is NaN: non-finite table values), LINE_ERR_OOM, LINE_ERR_CUDA.
- * Allocates n_pos + n_neg pairs' worth of scratch per call; synchronises. */
-LINE_API line_status line_eval_auc(line_ctx* ctx, int orders, const int32_t* pos_src, const int32_t* pos_dst,
+ * Errors: LINE_ERR_ARG (bad mask or score, counts, null pointers, or a node
+ * id out of range), LINE_ERR_STATE (a requested order has no tables),
+ * LINE_ERR_VALIDATE (a score is NaN: non-finite table values), LINE_ERR_OOM,
+ * LINE_ERR_CUDA.  Allocates scratch for the pairs per call; synchronises. */
+LINE_API line_status line_eval_auc(line_ctx* ctx, int orders, int score, const int32_t* pos_src, const int32_t* pos_dst,
                                    int64_t n_pos, const int32_t* neg_src, const int32_t* neg_dst, int64_t n_neg,
                                    float* scores_out, uint64_t* counts_out, double* auc_out);
+
+/* ------------------------------------------------------------------------
+ * Warm start of new or held-out nodes.  Not in the paper, whose rows all
+ * start from a random draw (Algorithm 1): a two-layer MLP regresses trained U
+ * rows of one order on inputs every node has, and its predictions initialise
+ * the rows of nodes LINE has not trained; plain LINE refinement follows.
+ * For the table dimension d and hidden width H, P = d + 1 rounded up to a
+ * multiple of 16:
+ *   x = [log(1 + d_w(v)), mean of U[w] over arcs v -> w with known[w],
+ *        0 ... ]                                     (d_w: weighted out-degree)
+ *   a = W1 x + b1, h = GELU(a) = a/2 (1 + erf(a / sqrt 2)), y = W2 h + b2
+ *   L = sum over a minibatch of B nodes of |y - U[v]|^2 / (B d)
+ * Parameters, flat FP32 in this order: W1 (H x P, row-major), b1 (H),
+ * W2 (d x H), b2 (d).  Optimiser: Adam with bias correction (beta1 0.9,
+ * beta2 0.999, eps 1e-8).  The activations x and h are stored as
+ * act_dtype (F32, or BF16 rounded to nearest even); sums are FP32 in a fixed
+ * order, so results are bitwise reproducible.  Initial weights: Philox
+ * domain 7, call 1, counter = flat index: u = ((w0 >> 8) - 2^23) 2^-23,
+ * W1 = u / sqrt(d + 1) on the d + 1 used columns (0 on padding), W2 =
+ * u / sqrt(H), biases 0.  Minibatch sample j of global step s is
+ * nodes[mulhi64(w1:w0, n)] of the Philox draw of domain 7, call 0, counter
+ * s B + j.  One MLP per context; line_build_alias with a different n_nodes
+ * discards it.
+ * ------------------------------------------------------------------------ */
+
+/* Create (or replace) the MLP for the U table of `order` (which must exist),
+ * hidden width 1..4096, activations act_dtype, initial weights from `seed`.
+ * Errors: LINE_ERR_ARG, LINE_ERR_STATE (no graph or tables), LINE_ERR_OOM. */
+LINE_API line_status line_mlp_create(line_ctx* ctx, int order, int hidden, int act_dtype, uint64_t seed);
+
+/* Compute the inputs x of every node from the current U table.  known: a
+ * buffer of n_nodes bytes, non-zero where the node's row is a trained
+ * embedding (neighbours that are not known are left out of the mean). */
+LINE_API line_status line_mlp_features(line_ctx* ctx, const uint8_t* known);
+
+/* Copy the inputs (n_nodes x P) as FP32 into `out` (a buffer). */
+LINE_API line_status line_mlp_get_features(line_ctx* ctx, float* out);
+
+/* Number of parameters in *n_params (if not NULL) and, if `out` is not
+ * NULL, a copy of them (a buffer of n_params floats). */
+LINE_API line_status line_mlp_get_params(line_ctx* ctx, float* out, int64_t* n_params);
+
+/* Overwrite the parameters from `in` (a buffer of n_params floats) and
+ * restart the optimiser state (moments zero, step count 0). */
+LINE_API line_status line_mlp_set_params(line_ctx* ctx, const float* in);
+
+/* Loss and gradient of the minibatch rows[0 .. n_rows) (a buffer of node
+ * ids, 1 <= n_rows <= 65536) at the current parameters, targets the current
+ * U rows; no update.  grads_out: NULL or a buffer of n_params floats;
+ * loss_out: NULL or a host pointer.  Needs line_mlp_features. */
+LINE_API line_status line_mlp_grad(line_ctx* ctx, const int32_t* rows, int64_t n_rows, float* grads_out,
+                                   double* loss_out);
+
+/* `steps` Adam steps with learning rate lr on minibatches of `batch` nodes
+ * (1..65536) drawn from nodes[0 .. n) (a buffer), global steps
+ * step_offset .. step_offset + steps - 1; targets the current U rows.
+ * losses_out: NULL or a host array of `steps` doubles, each step's loss
+ * before its update.  Needs line_mlp_features.  Node ids out of range:
+ * LINE_ERR_ARG (the step uses row 0 instead). */
+LINE_API line_status line_mlp_train(line_ctx* ctx, const int32_t* nodes, int64_t n, int64_t steps, int64_t batch,
+                                    double lr, uint64_t seed, uint64_t step_offset, double* losses_out);
+
+/* Predictions y for the nodes rows[0 .. n_rows) (a buffer).  y_out NULL:
+ * written into those rows of the U table (BF16 tables round to nearest
+ * even) - the warm start; otherwise a buffer of n_rows x d floats and the
+ * table is untouched.  Needs line_mlp_features. */
+LINE_API line_status line_mlp_predict(line_ctx* ctx, const int32_t* rows, int64_t n_rows, float* y_out);
 
 /* Largest m accepted by line_eval_loss_noalloc. */
 #define LINE_NOALLOC_MAX_SAMPLES (1 << 20)

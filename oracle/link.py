@@ -7,10 +7,11 @@ The paper judges embeddings by how well they separate linked from unlinked
 vertex pairs (Section VI, link prediction on held-out edges).  The score and
 the statistic are the plain textbook definitions, written out:
 
-* ``pair_scores`` - cosine similarity of the concatenated embedding of each
-  endpoint, where the embedding of a node is its U row of each requested
-  order, each row first scaled to unit L2 norm (an all-zero row stays zero,
-  and a pair with a zero concatenated vector scores 0);
+* ``pair_scores`` - the inner product of the endpoints' concatenated U
+  rows of the requested orders (``score="dot"``), or their cosine similarity
+  after scaling each order's row to unit L2 norm (``score="cosine"``; an
+  all-zero row stays zero, and a pair with a zero concatenated vector scores
+  0);
 * ``mann_whitney`` - the area under the ROC curve as the Mann-Whitney
   statistic: the fraction of (positive, negative) pairs in which the positive
   scores higher, ties counted one half.
@@ -34,8 +35,16 @@ def normalised_rows(tables, nodes) -> np.ndarray:
     return np.concatenate(parts, axis=1)
 
 
-def pair_scores(tables, src, dst) -> np.ndarray:
-    """Cosine of the concatenated, per-order normalised rows of each pair (FP64)."""
+def pair_scores(tables, src, dst, score: str = "dot") -> np.ndarray:
+    """Inner product (or cosine of the per-order normalised rows) of the
+    concatenated U rows of each pair (FP64)."""
+    if score == "dot":
+        out = np.zeros(len(src))
+        for U in tables:
+            U = np.asarray(U, np.float64)
+            out += (U[np.asarray(src, np.int64)] * U[np.asarray(dst, np.int64)]).sum(axis=1)
+        return out
+    assert score == "cosine", score
     a = normalised_rows(tables, src)
     b = normalised_rows(tables, dst)
     na = np.sqrt((a * a).sum(axis=1))
@@ -64,6 +73,6 @@ def mann_whitney(pos, neg) -> float:
     return (2 * less + equal) / (2.0 * len(pos) * len(neg))
 
 
-def auc(tables, pos_src, pos_dst, neg_src, neg_dst) -> float:
-    """Link-prediction AUC of FP64 cosine scores."""
-    return mann_whitney(pair_scores(tables, pos_src, pos_dst), pair_scores(tables, neg_src, neg_dst))
+def auc(tables, pos_src, pos_dst, neg_src, neg_dst, score: str = "dot") -> float:
+    """Link-prediction AUC of FP64 scores."""
+    return mann_whitney(pair_scores(tables, pos_src, pos_dst, score), pair_scores(tables, neg_src, neg_dst, score))

@@ -80,7 +80,7 @@ __device__ __forceinline__ int64_t lower_bound_i32(const int32_t* a, int64_t n, 
 // x_v = d(v)^0.75 = sqrt(d) * sqrt(sqrt(d)), d = weights of v's arcs summed in
 // arc order (src is sorted, so v's arcs are one contiguous range).
 __global__ void k_neg_weights(int64_t n_nodes, int64_t n_arcs, const int32_t* __restrict__ src,
-                              const float* __restrict__ w, double* __restrict__ x) {
+                              const float* __restrict__ w, double* __restrict__ x, float* __restrict__ deg) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n_nodes;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t lo = lower_bound_i32(src, n_arcs, (int32_t)v);
@@ -93,6 +93,7 @@ __global__ void k_neg_weights(int64_t n_nodes, int64_t n_arcs, const int32_t* __
             r = __dmul_rn(s, __dsqrt_rn(s));
         }
         x[v] = r;
+        if (deg) deg[v] = (float)d;
     }
 }
 
@@ -293,9 +294,9 @@ cudaError_t edge_weights(int64_t n_arcs, const float* w, double* x, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t neg_weights(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const float* w, double* x,
+cudaError_t neg_weights(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const float* w, double* x, float* deg,
                         cudaStream_t s) {
-    k_neg_weights<<<grid_for(n_nodes, 128, 1 << 20), 128, 0, s>>>(n_nodes, n_arcs, src, w, x);
+    k_neg_weights<<<grid_for(n_nodes, 128, 1 << 20), 128, 0, s>>>(n_nodes, n_arcs, src, w, x, deg);
     return cudaGetLastError();
 }
 

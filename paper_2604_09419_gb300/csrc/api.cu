@@ -5,50 +5,11 @@
 #include <cstring>
 #include <string>
 
-#include "line_internal.cuh"
+#include "context.cuh"
 
 using namespace line;
 
-namespace {
-
-struct Tables {
-    void* U = nullptr;
-    void* C = nullptr;
-    int dim = 0;
-    int dtype = 0;
-    bool ready = false;
-};
-
-size_t elem_size(int dtype) { return dtype == LINE_DTYPE_F32 ? 4 : 2; }
-
-}  // namespace
-
-struct line_ctx {
-    int device = 0;
-    cudaStream_t stream = nullptr;
-    std::string err;
-    bool sticky = false;
-    // graph
-    bool has_graph = false;
-    int64_t n_nodes = 0, n_arcs = 0;
-    int32_t* src = nullptr;
-    int32_t* dst = nullptr;
-    uint2* edge_tab = nullptr;
-    uint2* neg_tab = nullptr;
-    // tables by order (index 1 and 2)
-    Tables tab[3];
-    // device status word and small scratch
-    uint32_t* status = nullptr;
-    uint32_t* flag = nullptr;
-    double* dscratch = nullptr;
-    TrainWorkspace* ws = nullptr;
-    TrainTimes times;
-    double total_ms = 0;
-    uint64_t total_samples = 0;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-};
-
-namespace {
+namespace line {
 
 line_status fail(line_ctx* c, line_status s, const char* fmt, ...) {
     char buf[512];
@@ -71,12 +32,6 @@ line_status cuda_fail(line_ctx* c, cudaError_t e, const char* what) {
     return fail(c, LINE_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
-#define CK(call, what)                                      \
-    do {                                                    \
-        cudaError_t _e = (call);                            \
-        if (_e != cudaSuccess) return cuda_fail(c, _e, what); \
-    } while (0)
-
 line_status enter(line_ctx* c) {
     if (!c) return LINE_ERR_ARG;
     if (c->sticky) return LINE_ERR_STATE;
@@ -85,8 +40,7 @@ line_status enter(line_ctx* c) {
     return LINE_OK;
 }
 
-// Reads and clears the device status word (synchronises the stream).
-line_status check_status(line_ctx* c, const char* what, bool timeout_sticky = true) {
+line_status check_status(line_ctx* c, const char* what, bool timeout_sticky) {
     uint32_t st = 0;
     CK(cudaMemcpyAsync(&st, c->status, sizeof st, cudaMemcpyDeviceToHost, c->stream), "status read");
     CK(cudaStreamSynchronize(c->stream), what);
@@ -102,18 +56,27 @@ line_status check_status(line_ctx* c, const char* what, bool timeout_sticky = tr
     return LINE_OK;
 }
 
+
+}  // namespace line
+
+namespace {
+
 void free_tables(Tables& t) {
     if (t.U) cudaFree(t.U);
     if (t.C) cudaFree(t.C);
     t = Tables{};
 }
 
-void free_graph(line_ctx* c) {
-    for (void* p : {(void*)c->src, (void*)c->dst, (void*)c->edge_tab, (void*)c->neg_tab})
+void free_graph(line_ctx* c, bool keep_tables = false) {
+    for (void* p : {(void*)c->src, (void*)c->dst, (void*)c->deg, (void*)c->edge_tab, (void*)c->neg_tab})
         if (p) cudaFree(p);
     c->src = c->dst = nullptr;
+    c->deg = nullptr;
     c->edge_tab = c->neg_tab = nullptr;
     c->has_graph = false;
+    if (keep_tables) return;
+    mlp_destroy(c->mlp);
+    c->mlp = nullptr;
     for (auto& t : c->tab) free_tables(t);
 }
 
@@ -196,13 +159,16 @@ line_status line_build_alias(line_ctx* c, const line_graph_desc* g) {
     if (!g || !g->src || !g->dst) return fail(c, LINE_ERR_ARG, "line_build_alias: null graph arrays");
     if (g->n_nodes < 1 || g->n_nodes >= (1ll << 30)) return fail(c, LINE_ERR_ARG, "line_build_alias: n_nodes out of range");
     if (g->n_arcs < 1 || g->n_arcs >= (1ll << 32) - 1) return fail(c, LINE_ERR_ARG, "line_build_alias: n_arcs out of range");
-    free_graph(c);
+    // tables (and the MLP) survive a graph of the same node count
+    const bool keep = c->has_graph && c->n_nodes == g->n_nodes;
+    free_graph(c, keep);
     const int64_t n = g->n_nodes, m = g->n_arcs;
     cudaStream_t s = c->stream;
     CK(cudaMalloc(&c->src, sizeof(int32_t) * m), "graph allocation");
     CK(cudaMalloc(&c->dst, sizeof(int32_t) * m), "graph allocation");
     CK(cudaMalloc(&c->edge_tab, sizeof(uint2) * m), "alias allocation");
     CK(cudaMalloc(&c->neg_tab, sizeof(uint2) * n), "alias allocation");
+    CK(cudaMalloc(&c->deg, sizeof(float) * n), "degree allocation");
     CK(cudaMemcpyAsync(c->src, g->src, sizeof(int32_t) * m, cudaMemcpyDefault, s), "graph copy");
     CK(cudaMemcpyAsync(c->dst, g->dst, sizeof(int32_t) * m, cudaMemcpyDefault, s), "graph copy");
     float* w = nullptr;
@@ -228,7 +194,7 @@ line_status line_build_alias(line_ctx* c, const line_graph_desc* g) {
         if ((e = alias_build(x, m, c->edge_tab, tmp, c->status, s)) != cudaSuccess) { result = cuda_fail(c, e, "edge alias"); break; }
         if ((result = check_status(c, "line_build_alias (edges)"))) break;
         // negative table: d(v)^0.75 (Eq. 1)
-        if ((e = neg_weights(n, m, c->src, w, x, s)) != cudaSuccess) { result = cuda_fail(c, e, "degree weights"); break; }
+        if ((e = neg_weights(n, m, c->src, w, x, c->deg, s)) != cudaSuccess) { result = cuda_fail(c, e, "degree weights"); break; }
         if ((e = alias_build(x, n, c->neg_tab, tmp, c->status, s)) != cudaSuccess) { result = cuda_fail(c, e, "negative alias"); break; }
         if ((result = check_status(c, "line_build_alias (negatives)"))) break;
     } while (false);
@@ -469,13 +435,13 @@ line_status line_eval_loss(line_ctx* c, int order, int K, uint64_t seed, int64_t
     return LINE_OK;
 }
 
-line_status line_eval_auc(line_ctx* c, int orders, const int32_t* pos_src, const int32_t* pos_dst, int64_t n_pos,
+line_status line_eval_auc(line_ctx* c, int orders, int score, const int32_t* pos_src, const int32_t* pos_dst, int64_t n_pos,
                           const int32_t* neg_src, const int32_t* neg_dst, int64_t n_neg, float* scores_out,
                           uint64_t* counts_out, double* auc_out) {
     line_status st = enter(c);
     if (st) return st;
     if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_eval_auc: no graph");
-    if (orders < 1 || orders > 3 || n_pos < 1 || n_neg < 1 || n_pos + n_neg >= (1ll << 31) || !pos_src || !pos_dst ||
+    if (orders < 1 || orders > 3 || (score != LINE_SCORE_DOT && score != LINE_SCORE_COSINE) || n_pos < 1 || n_neg < 1 || n_pos + n_neg >= (1ll << 31) || !pos_src || !pos_dst ||
         !neg_src || !neg_dst || !auc_out)
         return fail(c, LINE_ERR_ARG, "line_eval_auc: bad arguments");
     ScoreTables t{};
@@ -502,7 +468,7 @@ line_status line_eval_auc(line_ctx* c, int orders, const int32_t* pos_src, const
     if (e == cudaSuccess) e = cudaMemcpyAsync(src + n_pos, neg_src, sizeof(int32_t) * n_neg, cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dst, pos_dst, sizeof(int32_t) * n_pos, cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(dst + n_pos, neg_dst, sizeof(int32_t) * n_neg, cudaMemcpyDefault, s);
-    if (e == cudaSuccess) e = eval_auc(t, src, dst, n_pos, n_neg, c->n_nodes, scores, tmp, c->status, s);
+    if (e == cudaSuccess) e = eval_auc(t, score, src, dst, n_pos, n_neg, c->n_nodes, scores, tmp, c->status, s);
     if (e == cudaSuccess && scores_out)
         e = cudaMemcpyAsync(scores_out, scores, sizeof(float) * n, cudaMemcpyDefault, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(counts, tmp, sizeof counts, cudaMemcpyDeviceToHost, s);

@@ -1,13 +1,15 @@
-// Link-prediction evaluation (reporting): cosine scores of node pairs and the
-// exact Mann-Whitney AUC of positive against negative pairs (the paper's
-// link-prediction judgement of embeddings, Section VI).
+// Link-prediction evaluation (reporting): scores of node pairs and the exact
+// Mann-Whitney AUC of positive against negative pairs (the paper's
+// link-prediction judgement of embeddings, Section VI).  Over the requested
+// orders o, with z(x) = [U_o[x]]_o the concatenated rows:
 //
-//   score(u, v) = z(u).z(v) / (|z(u)| |z(v)|),  z(x) = [U_o[x] / |U_o[x]|]_o
+//   dot:     score(u, v) = z(u).z(v) = sum_o U_o[u].U_o[v]
+//   cosine:  score(u, v) = n(u).n(v) / (|n(u)| |n(v)|),  n(x) = [U_o[x] / |U_o[x]|]_o
 //
-// over the requested orders o, an all-zero row contributing a zero block, a
-// zero concatenated vector giving score 0.  Scores are FP32: per order the
-// dot and the two squared norms are FP32 FMA chains over a lane's dimensions,
-// reduced by a butterfly (every lane ends with the same bits).  The AUC then
+// (cosine: an all-zero row contributes a zero block, a zero concatenated
+// vector scores 0).  Scores are FP32: per order the dot and the two squared
+// norms are FP32 FMA chains over a lane's dimensions, reduced by a butterfly
+// (every lane ends with the same bits).  The AUC then
 // counts, in integers, the (positive, negative) pairs with neg < pos and with
 // neg == pos: the negatives' order-preserving 32-bit keys are radix sorted and
 // every positive key is located by binary search.
@@ -35,7 +37,7 @@ __device__ __forceinline__ uint32_t order_key(float f) {
 }
 
 // One warp per pair.
-__global__ void k_pair_scores(ScoreTables t, const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
+__global__ void k_pair_scores(ScoreTables t, int score, const int32_t* __restrict__ src, const int32_t* __restrict__ dst,
                               int64_t n, int64_t n_nodes, float* __restrict__ scores, uint32_t* __restrict__ keys,
                               uint32_t* status) {
     const int lane = threadIdx.x & 31;
@@ -50,7 +52,7 @@ __global__ void k_pair_scores(ScoreTables t, const int32_t* __restrict__ src, co
             }
             continue;
         }
-        float zz = 0.0f, cu = 0.0f, cv = 0.0f;
+        float zz = 0.0f, cu = 0.0f, cv = 0.0f, dd = 0.0f;
         for (int o = 0; o < t.n; ++o) {
             const void* U = t.U[o];
             const int dim = t.dim[o], dt = t.dtype[o];
@@ -64,11 +66,12 @@ __global__ void k_pair_scores(ScoreTables t, const int32_t* __restrict__ src, co
             dot = warp_sum(dot);
             nu = warp_sum(nu);
             nv = warp_sum(nv);
+            dd += dot;
             if (nu > 0.0f && nv > 0.0f) zz += dot / (sqrtf(nu) * sqrtf(nv));
             if (nu > 0.0f) cu += 1.0f;
             if (nv > 0.0f) cv += 1.0f;
         }
-        const float sc = (cu > 0.0f && cv > 0.0f) ? zz / sqrtf(cu * cv) : 0.0f;
+        const float sc = score == LINE_SCORE_DOT ? dd : (cu > 0.0f && cv > 0.0f) ? zz / sqrtf(cu * cv) : 0.0f;
         if (lane == 0) {
             if (!(sc == sc)) atomicOr(status, DEV_ERR_VALUE);
             scores[i] = sc;
@@ -198,7 +201,7 @@ size_t auc_tmp_bytes(int64_t n_pos, int64_t n_neg) {
     return 256 + sizeof(uint32_t) * (size_t)(n + n_neg + 256 * tiles(n_neg));
 }
 
-cudaError_t eval_auc(const ScoreTables& t, const int32_t* src, const int32_t* dst, int64_t n_pos, int64_t n_neg,
+cudaError_t eval_auc(const ScoreTables& t, int score, const int32_t* src, const int32_t* dst, int64_t n_pos, int64_t n_neg,
                      int64_t n_nodes, float* scores, void* tmp, uint32_t* status, cudaStream_t s) {
     const int64_t n = n_pos + n_neg;
     unsigned long long* counts_dev = reinterpret_cast<unsigned long long*>(tmp);
@@ -210,7 +213,7 @@ cudaError_t eval_auc(const ScoreTables& t, const int32_t* src, const int32_t* ds
     {
         int64_t blocks = (n + 7) / 8;
         if (blocks > 152 * 32) blocks = 152 * 32;
-        k_pair_scores<<<(unsigned)blocks, 256, 0, s>>>(t, src, dst, n, n_nodes, scores, keys, status);
+        k_pair_scores<<<(unsigned)blocks, 256, 0, s>>>(t, score, src, dst, n, n_nodes, scores, keys, status);
     }
     // sort the negatives' keys (keys[n_pos ..]); four passes leave them in place
     uint32_t* a = keys + n_pos;

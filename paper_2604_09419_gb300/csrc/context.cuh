@@ -1,0 +1,70 @@
+// The library context (line_ctx) and the argument/error helpers shared by the
+// C entry points (api.cu, mlp.cu).  Internal: not part of include/line.h.
+#pragma once
+
+#include <string>
+
+#include "line_internal.cuh"
+
+namespace line {
+
+struct Tables {
+    void* U = nullptr;
+    void* C = nullptr;
+    int dim = 0;
+    int dtype = 0;
+    bool ready = false;
+};
+
+inline size_t elem_size(int dtype) { return dtype == LINE_DTYPE_F32 ? 4 : 2; }
+
+struct MlpState;  // warm-start network (mlp.cu)
+void mlp_destroy(MlpState*);
+
+}  // namespace line
+
+struct line_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string err;
+    bool sticky = false;
+    // graph
+    bool has_graph = false;
+    int64_t n_nodes = 0, n_arcs = 0;
+    int32_t* src = nullptr;
+    int32_t* dst = nullptr;
+    float* deg = nullptr;  // weighted out-degree of each node (FP64 sum, stored FP32)
+    uint2* edge_tab = nullptr;
+    uint2* neg_tab = nullptr;
+    // tables by order (index 1 and 2)
+    line::Tables tab[3];
+    // device status word and small scratch
+    uint32_t* status = nullptr;
+    uint32_t* flag = nullptr;
+    double* dscratch = nullptr;
+    line::TrainWorkspace* ws = nullptr;
+    line::TrainTimes times;
+    double total_ms = 0;
+    uint64_t total_samples = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    line::MlpState* mlp = nullptr;
+};
+
+namespace line {
+
+// Records the message (unless an earlier sticky error is kept) and returns s;
+// CUDA and timeout errors make the context sticky.
+line_status fail(line_ctx* c, line_status s, const char* fmt, ...);
+line_status cuda_fail(line_ctx* c, cudaError_t e, const char* what);
+// Entry check: context valid and not sticky, its device current.
+line_status enter(line_ctx* c);
+// Reads and clears the device status word (synchronises the stream).
+line_status check_status(line_ctx* c, const char* what, bool timeout_sticky = true);
+
+}  // namespace line
+
+#define CK(call, what)                                                   \
+    do {                                                                 \
+        cudaError_t _e = (call);                                         \
+        if (_e != cudaSuccess) return ::line::cuda_fail(c, _e, what);    \
+    } while (0)

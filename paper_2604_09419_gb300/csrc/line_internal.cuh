@@ -122,7 +122,8 @@ size_t fixed_sum_tmp_bytes(int64_t n);
 cudaError_t validate_graph(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t* dst,
                            const float* w, uint32_t* status, cudaStream_t s);
 cudaError_t edge_weights(int64_t n_arcs, const float* w, double* x, cudaStream_t s);
-cudaError_t neg_weights(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const float* w, double* x,
+// x[v] = d(v)^0.75; deg (nullable): d(v) rounded to FP32.
+cudaError_t neg_weights(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const float* w, double* x, float* deg,
                         cudaStream_t s);
 size_t alias_build_tmp_bytes(int64_t n);
 // Builds tab[n] = {thr, alias} from weights x[n] (FP64).  tmp: alias_build_tmp_bytes(n).
@@ -154,7 +155,7 @@ size_t auc_tmp_bytes(int64_t n_pos, int64_t n_neg);
 // src/dst: n_pos positive pairs then n_neg negative pairs (device).  scores:
 // [n_pos + n_neg] FP32 out.  tmp: auc_tmp_bytes(n_pos, n_neg) bytes, 256-byte
 // aligned; on return its first two u64 are {#(neg < pos), #(neg == pos)}.
-cudaError_t eval_auc(const ScoreTables& t, const int32_t* src, const int32_t* dst, int64_t n_pos, int64_t n_neg,
+cudaError_t eval_auc(const ScoreTables& t, int score, const int32_t* src, const int32_t* dst, int64_t n_pos, int64_t n_neg,
                      int64_t n_nodes, float* scores, void* tmp, uint32_t* status, cudaStream_t s);
 
 // noalloc.cu: the loss evaluation with its scratch in a fixed device array

@@ -1,0 +1,727 @@
+// Warm start of new or held-out nodes: a two-layer MLP regresses a node's
+// trained U row on its log weighted degree and the mean trained U row of its
+// neighbours; its predictions initialise the rows of nodes LINE never
+// trained (Algorithm 1 starts every row from a random draw), after which
+// plain LINE refinement continues.
+//
+//   x = [log(1 + d_w(v)), mean_{v->w, w known} U[w], 0 pad]   (P = round16(d+1))
+//   a = W1 x + b1,  h = GELU(a) = a/2 (1 + erf(a/sqrt 2)),  y = W2 h + b2
+//   L = sum (y - U[v])^2 / (B d) over a minibatch,  Adam (beta 0.9/0.999, eps 1e-8)
+//
+// Weights, gradients and optimiser state are FP32; the activations x and h
+// are stored as FP32 or BF16 (round to nearest even).  Every contraction is
+// one tiled kernel with FP32 FMA accumulation in index order (split over the
+// batch into slices summed in slice order for the weight gradients), so
+// training is bitwise reproducible.  Random numbers: Philox domain 7, call 0
+// for minibatch picks (counter s*B + j), call 1 for the initial weights
+// (counter = the parameter's flat index).
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "context.cuh"
+
+namespace line {
+
+constexpr uint32_t kMlpDomain = 7;
+constexpr int64_t kMlpMaxBatch = 1 << 16;
+
+struct MlpState {
+    int order = 0, dim = 0, hidden = 0, P = 0, act = 0;
+    int64_t n_params = 0;
+    float* params = nullptr;  // [W1 (hidden x P) | b1 (hidden) | W2 (dim x hidden) | b2 (dim)]
+    float* grads = nullptr;
+    float* m = nullptr;
+    float* v = nullptr;
+    int64_t t = 0;  // Adam steps taken
+    void* X = nullptr;  // [n_nodes][P] features (act dtype)
+    int64_t n_nodes = 0;
+    bool has_features = false;
+    // minibatch scratch (cap rows)
+    int64_t cap = 0;
+    int32_t* rows = nullptr;
+    void* Xb = nullptr;      // [cap][P]
+    float* Tb = nullptr;     // [cap][dim]
+    float* A1 = nullptr;     // [cap][hidden] pre-activations
+    void* Hb = nullptr;      // [cap][hidden] activations
+    float* Yb = nullptr;     // [cap][dim] outputs, then dL/dy
+    float* dH = nullptr;     // [cap][hidden] dL/dh, then dL/da
+    float* part = nullptr;   // split partials
+    size_t part_elems = 0;
+    double* rowloss = nullptr;  // [cap]
+    void* sum_tmp = nullptr;
+    double* losses = nullptr;   // [loss_cap] per-step losses
+    int64_t loss_cap = 0;
+    int32_t* nodes = nullptr;   // training node list (device copy)
+    int64_t nodes_cap = 0;
+};
+
+void mlp_destroy(MlpState* s) {
+    if (!s) return;
+    for (void* p : {(void*)s->params, (void*)s->grads, (void*)s->m, (void*)s->v, s->X, (void*)s->rows, s->Xb,
+                    (void*)s->Tb, (void*)s->A1, s->Hb, (void*)s->Yb, (void*)s->dH, (void*)s->part,
+                    (void*)s->rowloss, s->sum_tmp, (void*)s->losses, (void*)s->nodes})
+        if (p) cudaFree(p);
+    delete s;
+}
+
+namespace {
+
+// ---- element helpers -------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ float to_f(T x);
+template <>
+__device__ __forceinline__ float to_f<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ float to_f<__nv_bfloat16>(__nv_bfloat16 x) { return __bfloat162float(x); }
+
+template <typename T>
+__device__ __forceinline__ T from_f(float x);
+template <>
+__device__ __forceinline__ float from_f<float>(float x) { return x; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
+
+__device__ __forceinline__ float gelu(float a) { return 0.5f * a * (1.0f + erff(a * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float a) {
+    return 0.5f * (1.0f + erff(a * 0.70710678118654752f)) + a * expf(-0.5f * a * a) * 0.39894228040143268f;
+}
+
+__device__ __forceinline__ float load_row_elem(const void* U, int dtype, int64_t idx) {
+    return dtype == LINE_DTYPE_F32 ? reinterpret_cast<const float*>(U)[idx]
+                                   : __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(U)[idx]);
+}
+
+__device__ __forceinline__ int64_t lower_bound_src(const int32_t* src, int64_t n, int32_t v) {
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (src[mid] < v) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// ---- initialisation --------------------------------------------------------
+__global__ void k_mlp_init(float* __restrict__ p, int H, int P, int D, uint64_t seed, float s1, float s2) {
+    const int64_t n1 = (int64_t)H * P, n2 = (int64_t)D * H;
+    const int64_t total = n1 + H + n2 + D;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 w = draw_words(seed, kMlpDomain, (uint64_t)t, 1u);
+        const float u = (float)((int32_t)(w.x >> 8) - (1 << 23)) * (1.0f / 8388608.0f);
+        float val = 0.0f;
+        if (t < n1) {
+            if ((int)(t % P) <= D) val = u * s1;
+        } else if (t >= n1 + H && t < n1 + H + n2) {
+            val = u * s2;
+        }
+        p[t] = val;
+    }
+}
+
+// ---- features: one warp per node -------------------------------------------
+template <typename TX>
+__global__ void k_mlp_features(int64_t n_nodes, int64_t n_arcs, const int32_t* __restrict__ src,
+                               const int32_t* __restrict__ dst, const float* __restrict__ deg, const void* U, int udt,
+                               int D, const uint8_t* __restrict__ known, int P, TX* __restrict__ X) {
+    constexpr int kMaxE = 8;  // D <= 256
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t v = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); v < n_nodes; v += warps) {
+        const int64_t lo = lower_bound_src(src, n_arcs, (int32_t)v);
+        const int64_t hi = lower_bound_src(src, n_arcs, (int32_t)(v + 1));
+        float acc[kMaxE];
+#pragma unroll
+        for (int i = 0; i < kMaxE; ++i) acc[i] = 0.0f;
+        int cnt = 0;
+        for (int64_t e0 = lo; e0 < hi; e0 += 32) {
+            // 32 arcs at a time: lane l reads arc e0 + l; known neighbours
+            // are then added in arc order
+            const int64_t e = e0 + lane;
+            const int32_t w = e < hi ? dst[e] : 0;
+            const bool ok = e < hi && known[w];
+            uint32_t mask = __ballot_sync(0xFFFFFFFFu, ok);
+            cnt += __popc(mask);
+            while (mask) {
+                const int l = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int64_t row = __shfl_sync(0xFFFFFFFFu, w, l);
+#pragma unroll
+                for (int i = 0; i < kMaxE; ++i) {
+                    const int k = lane + 32 * i;
+                    if (k < D) acc[i] += load_row_elem(U, udt, row * D + k);
+                }
+            }
+        }
+        TX* x = X + v * (int64_t)P;
+        if (lane == 0) x[0] = from_f<TX>(log1pf(deg[v]));
+#pragma unroll
+        for (int i = 0; i < kMaxE; ++i) {
+            const int k = lane + 32 * i;
+            if (k < D) x[1 + k] = from_f<TX>(cnt ? acc[i] / (float)cnt : 0.0f);
+        }
+        for (int k = D + 1 + lane; k < P; k += 32) x[k] = from_f<TX>(0.0f);
+    }
+}
+
+// ---- minibatch: rows[j] = nodes[mulhi64(w1:w0, n)], draw s*B + j ------------
+__global__ void k_mlp_batch(const int32_t* __restrict__ nodes, int64_t n, uint64_t seed, uint64_t t0, int64_t B,
+                            int32_t* __restrict__ rows) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < B; j += (int64_t)gridDim.x * blockDim.x) {
+        const uint4 w = draw_words(seed, kMlpDomain, t0 + (uint64_t)j, 0u);
+        const uint64_t r = ((uint64_t)w.y << 32) | (uint64_t)w.x;
+        rows[j] = nodes[__umul64hi(r, (uint64_t)n)];
+    }
+}
+
+// Xb[j] = X[rows[j]]; Tb[j] = U[rows[j]] (FP32) when Tb is given.
+template <typename TX>
+__global__ void k_mlp_gather(const int32_t* __restrict__ rows, int64_t B, int64_t n_nodes,
+                             const TX* __restrict__ X, int P, TX* __restrict__ Xb, const void* U, int udt, int D,
+                             float* __restrict__ Tb, uint32_t* status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t j = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); j < B; j += warps) {
+        int64_t r = rows[j];
+        if (r < 0 || r >= n_nodes) {
+            if (lane == 0) atomicOr(status, DEV_ERR_INDEX);
+            r = 0;
+        }
+        for (int k = lane; k < P; k += 32) Xb[j * P + k] = X[r * P + k];
+        if (Tb)
+            for (int k = lane; k < D; k += 32) Tb[j * D + k] = load_row_elem(U, udt, r * D + k);
+    }
+}
+
+// ---- the contraction -------------------------------------------------------
+// C_z[m][n] = sum over k in slice z of A(m, k) B(k, n), k ascending;
+// A(m, k) = AK ? A[m lda + k] : A[k lda + m], B(k, n) = BK ? B[n ldb + k] : B[k ldb + n].
+constexpr int kBM = 64, kBN = 64, kBK = 16;
+
+template <typename TA, typename TB, bool AK, bool BK>
+__global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, int kslice, const TA* __restrict__ A, int lda,
+                                              const TB* __restrict__ B, int ldb, float* __restrict__ C) {
+    __shared__ float As[kBK][kBM + 4];
+    __shared__ float Bs[kBK][kBN + 4];
+    const int tid = threadIdx.x;
+    const int m0 = blockIdx.y * kBM, n0 = blockIdx.x * kBN;
+    const int kb = blockIdx.z * kslice, ke = min(K, kb + kslice);
+    const int ty = tid / 16, tx = tid % 16;
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.0f;
+    for (int k0 = kb; k0 < ke; k0 += kBK) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int mm = AK ? tid / 4 : (tid % 16) * 4 + q;
+            const int ka = AK ? (tid % 4) * 4 + q : tid / 16;
+            const int gm = m0 + mm, gk = k0 + ka;
+            float a = 0.0f;
+            if (gm < M && gk < ke) a = to_f(AK ? A[(size_t)gm * lda + gk] : A[(size_t)gk * lda + gm]);
+            As[ka][mm] = a;
+            const int nn = BK ? tid / 4 : (tid % 16) * 4 + q;
+            const int kb2 = BK ? (tid % 4) * 4 + q : tid / 16;
+            const int gn = n0 + nn, gk2 = k0 + kb2;
+            float b = 0.0f;
+            if (gn < N && gk2 < ke) b = to_f(BK ? B[(size_t)gn * ldb + gk2] : B[(size_t)gk2 * ldb + gn]);
+            Bs[kb2][nn] = b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kBK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    float* Cz = C + (size_t)blockIdx.z * M * N;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int gm = m0 + ty + 16 * i, gn = n0 + tx + 16 * j;
+            if (gm < M && gn < N) Cz[(size_t)gm * N + gn] = acc[i][j];
+        }
+}
+
+template <typename TA, typename TB, bool AK, bool BK>
+cudaError_t gemm(int M, int N, int K, int slices, const TA* A, int lda, const TB* B, int ldb, float* C,
+                 cudaStream_t s) {
+    const int kslice = ((K + slices - 1) / slices + kBK - 1) / kBK * kBK;
+    const dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, slices);
+    k_gemm<TA, TB, AK, BK><<<grid, 256, 0, s>>>(M, N, K, kslice, A, lda, B, ldb, C);
+    return cudaGetLastError();
+}
+
+// ---- epilogues -------------------------------------------------------------
+// A1 = A1 + b1 (in place), H = GELU(A1) in the activation type.
+template <typename TH>
+__global__ void k_ep_hidden(float* __restrict__ A1, const float* __restrict__ b1, int64_t M, int H, TH* __restrict__ Hb) {
+    const int64_t n = M * H;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float a = A1[i] + b1[i % H];
+        A1[i] = a;
+        Hb[i] = from_f<TH>(gelu(a));
+    }
+}
+
+// Training: y = Y + b2, r = y - t, dY = 2 r / (B D), rowloss[m] = sum r^2
+// (FP64 over the row's lanes in butterfly order).  One warp per row.
+__global__ void k_ep_loss(float* __restrict__ Y, const float* __restrict__ b2, const float* __restrict__ Tb, int64_t M,
+                          int D, float scale, double* __restrict__ rowloss) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t m = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); m < M; m += warps) {
+        double acc = 0.0;
+        for (int n = lane; n < D; n += 32) {
+            const float r = (Y[m * D + n] + b2[n]) - Tb[m * D + n];
+            acc += (double)r * (double)r;
+            Y[m * D + n] = scale * r;
+        }
+#pragma unroll
+        for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
+        if (lane == 0) rowloss[m] = acc;
+    }
+}
+
+// Inference: y = Y + b2 into out[m] (FP32 rows) or, with rows, into table
+// rows[m] of type `odt`.
+__global__ void k_ep_predict(const float* __restrict__ Y, const float* __restrict__ b2, int64_t M, int D,
+                             const int32_t* __restrict__ rows, int64_t n_nodes, void* out, int odt) {
+    const int64_t n = M * D;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t m = i / D, k = i - m * D;
+        const float y = Y[i] + b2[k];
+        if (rows && (rows[m] < 0 || rows[m] >= n_nodes)) continue;  // reported by the gather
+        const int64_t dst = rows ? (int64_t)rows[m] * D + k : i;
+        if (odt == LINE_DTYPE_F32) reinterpret_cast<float*>(out)[dst] = y;
+        else reinterpret_cast<__nv_bfloat16*>(out)[dst] = __float2bfloat16_rn(y);
+    }
+}
+
+// dA = dH * GELU'(A1), in place.
+__global__ void k_ep_dact(float* __restrict__ dH, const float* __restrict__ A1, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dH[i] *= gelu_grad(A1[i]);
+}
+
+// out[i] = sum_z part[z][i], z ascending.
+__global__ void k_sum_slices(const float* __restrict__ part, int S, int64_t count, float* __restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int z = 0; z < S; ++z) s += part[(size_t)z * count + i];
+        out[i] = s;
+    }
+}
+
+// part[z][n] = sum of X[m][n] over the rows m of slice z, m ascending.
+__global__ void k_colsum_slices(const float* __restrict__ X, int64_t M, int N, int64_t rows_per,
+                                float* __restrict__ part) {
+    const int n = blockIdx.x * blockDim.x + threadIdx.x;
+    if (n >= N) return;
+    const int64_t m0 = (int64_t)blockIdx.y * rows_per, m1 = min(M, m0 + rows_per);
+    float s = 0.0f;
+    for (int64_t m = m0; m < m1; ++m) s += X[m * N + n];
+    part[(size_t)blockIdx.y * N + n] = s;
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                       float* __restrict__ v, int64_t n, float lr, float c1, float c2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = 0.9f * m[i] + 0.1f * gi;
+        const float vi = 0.999f * v[i] + 0.001f * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + 1e-8f);
+    }
+}
+
+unsigned grid_of(int64_t n, int threads, int64_t cap = 152 * 16) {
+    int64_t b = (n + threads - 1) / threads;
+    return (unsigned)std::max<int64_t>(1, std::min(b, cap));
+}
+
+// Offsets of the parameter blocks.
+struct Layout {
+    int64_t W1, b1, W2, b2, n;
+    explicit Layout(const MlpState& s) {
+        W1 = 0;
+        b1 = (int64_t)s.hidden * s.P;
+        W2 = b1 + s.hidden;
+        b2 = W2 + (int64_t)s.dim * s.hidden;
+        n = b2 + s.dim;
+    }
+};
+
+int slices_for(int64_t B) { return (int)std::max<int64_t>(1, std::min<int64_t>(32, (B + 127) / 128)); }
+
+cudaError_t ensure_cap(MlpState& s, int64_t rows) {
+    if (rows <= s.cap) return cudaSuccess;
+    const int64_t cap = std::max<int64_t>(rows, 1024);
+    for (void** p : {(void**)&s.rows, &s.Xb, (void**)&s.Tb, (void**)&s.A1, &s.Hb, (void**)&s.Yb, (void**)&s.dH,
+                     (void**)&s.part, (void**)&s.rowloss, &s.sum_tmp}) {
+        if (*p) cudaFree(*p);
+        *p = nullptr;
+    }
+    s.cap = 0;
+    const size_t act = s.act == LINE_DTYPE_F32 ? 4 : 2;
+    const int S = 32;
+    s.part_elems = (size_t)S * std::max<int64_t>((int64_t)s.hidden * s.P, (int64_t)s.dim * s.hidden);
+    cudaError_t e;
+    if ((e = cudaMalloc(&s.rows, sizeof(int32_t) * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&s.Xb, act * cap * s.P)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&s.Tb, sizeof(float) * cap * s.dim)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&s.A1, sizeof(float) * cap * s.hidden)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&s.Hb, act * cap * s.hidden)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&s.Yb, sizeof(float) * cap * s.dim)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&s.dH, sizeof(float) * cap * s.hidden)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&s.part, sizeof(float) * s.part_elems)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&s.rowloss, sizeof(double) * cap)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&s.sum_tmp, fixed_sum_tmp_bytes(cap))) != cudaSuccess) return e;
+    s.cap = cap;
+    return cudaSuccess;
+}
+
+// Forward pass of rows s.rows[0..B): Xb, A1, Hb, Yb (= W2 h, before b2).
+template <typename TX>
+cudaError_t forward(MlpState& s, int64_t B, const Tables& t, bool targets, uint32_t* status, int64_t n_nodes,
+                    cudaStream_t st) {
+    const Layout L(s);
+    const float* W1 = s.params + L.W1;
+    const float* b1 = s.params + L.b1;
+    const float* W2 = s.params + L.W2;
+    TX* Xb = reinterpret_cast<TX*>(s.Xb);
+    TX* Hb = reinterpret_cast<TX*>(s.Hb);
+    k_mlp_gather<TX><<<grid_of(B * 32, 256), 256, 0, st>>>(s.rows, B, n_nodes, reinterpret_cast<const TX*>(s.X), s.P,
+                                                            Xb, t.U, t.dtype, s.dim, targets ? s.Tb : nullptr, status);
+    cudaError_t e;
+    if ((e = gemm<TX, float, true, true>((int)B, s.hidden, s.P, 1, Xb, s.P, W1, s.P, s.A1, st)) != cudaSuccess) return e;
+    k_ep_hidden<TX><<<grid_of(B * s.hidden, 256), 256, 0, st>>>(s.A1, b1, B, s.hidden, Hb);
+    return gemm<TX, float, true, true>((int)B, s.dim, s.hidden, 1, Hb, s.hidden, W2, s.hidden, s.Yb, st);
+}
+
+// Loss and gradients of the batch s.rows[0..B) into s.grads; the batch loss
+// (fixed-order FP64 sum / (B D)) into *loss_dev.
+template <typename TX>
+cudaError_t loss_grad(MlpState& s, int64_t B, const Tables& t, uint32_t* status, int64_t n_nodes, double* loss_dev,
+                      cudaStream_t st) {
+    const Layout L(s);
+    cudaError_t e;
+    if ((e = forward<TX>(s, B, t, true, status, n_nodes, st)) != cudaSuccess) return e;
+    const float* W2 = s.params + L.W2;
+    const float* b2 = s.params + L.b2;
+    const float scale = (float)(2.0 / ((double)B * s.dim));
+    k_ep_loss<<<grid_of(B * 32, 256), 256, 0, st>>>(s.Yb, b2, s.Tb, B, s.dim, scale, s.rowloss);
+    // dH = dY W2, then dA = dH GELU'(a)
+    if ((e = gemm<float, float, true, false>((int)B, s.hidden, s.dim, 1, s.Yb, s.dim, W2, s.hidden, s.dH, st)) !=
+        cudaSuccess)
+        return e;
+    k_ep_dact<<<grid_of(B * s.hidden, 256), 256, 0, st>>>(s.dH, s.A1, B * s.hidden);
+    const TX* Xb = reinterpret_cast<const TX*>(s.Xb);
+    const TX* Hb = reinterpret_cast<const TX*>(s.Hb);
+    const int S = slices_for(B);
+    // gW2 = dY^T H
+    if ((e = gemm<float, TX, false, false>(s.dim, s.hidden, (int)B, S, s.Yb, s.dim, Hb, s.hidden, s.part, st)) !=
+        cudaSuccess)
+        return e;
+    k_sum_slices<<<grid_of((int64_t)s.dim * s.hidden, 256), 256, 0, st>>>(s.part, S, (int64_t)s.dim * s.hidden,
+                                                                          s.grads + L.W2);
+    // gW1 = dA^T X
+    if ((e = gemm<float, TX, false, false>(s.hidden, s.P, (int)B, S, s.dH, s.hidden, Xb, s.P, s.part, st)) !=
+        cudaSuccess)
+        return e;
+    k_sum_slices<<<grid_of((int64_t)s.hidden * s.P, 256), 256, 0, st>>>(s.part, S, (int64_t)s.hidden * s.P,
+                                                                       s.grads + L.W1);
+    // bias gradients: column sums in slices of rows, slices summed in order
+    const int64_t rows_per = (B + S - 1) / S;
+    k_colsum_slices<<<dim3((s.hidden + 255) / 256, S), 256, 0, st>>>(s.dH, B, s.hidden, rows_per, s.part);
+    k_sum_slices<<<grid_of(s.hidden, 256), 256, 0, st>>>(s.part, S, s.hidden, s.grads + L.b1);
+    k_colsum_slices<<<dim3((s.dim + 255) / 256, S), 256, 0, st>>>(s.Yb, B, s.dim, rows_per, s.part);
+    k_sum_slices<<<grid_of(s.dim, 256), 256, 0, st>>>(s.part, S, s.dim, s.grads + L.b2);
+    if ((e = fixed_sum_f64(s.rowloss, B, reinterpret_cast<double*>(s.sum_tmp), loss_dev, st)) != cudaSuccess) return e;
+    return cudaGetLastError();
+}
+
+__global__ void k_scale_loss(double* loss, double inv) { *loss *= inv; }
+
+}  // namespace
+
+}  // namespace line
+
+using namespace line;
+
+namespace {
+
+line_status mlp_ready(line_ctx* c, const char* what, bool need_features) {
+    if (!c->mlp) return fail(c, LINE_ERR_STATE, "%s: no MLP (call line_mlp_create)", what);
+    if (!c->tab[c->mlp->order].ready || c->tab[c->mlp->order].dim != c->mlp->dim)
+        return fail(c, LINE_ERR_STATE, "%s: the tables of order %d (dim %d) are gone", what, c->mlp->order,
+                    c->mlp->dim);
+    if (need_features && !c->mlp->has_features) return fail(c, LINE_ERR_STATE, "%s: no features (call line_mlp_features)", what);
+    return LINE_OK;
+}
+
+// Device copy of a node list (host or device buffer), into s.nodes.
+cudaError_t upload_nodes(MlpState& s, const int32_t* nodes, int64_t n, cudaStream_t st) {
+    if (n > s.nodes_cap) {
+        if (s.nodes) cudaFree(s.nodes);
+        s.nodes = nullptr;
+        s.nodes_cap = 0;
+        cudaError_t e = cudaMalloc(&s.nodes, sizeof(int32_t) * n);
+        if (e != cudaSuccess) return e;
+        s.nodes_cap = n;
+    }
+    return cudaMemcpyAsync(s.nodes, nodes, sizeof(int32_t) * n, cudaMemcpyDefault, st);
+}
+
+}  // namespace
+
+extern "C" {
+
+line_status line_mlp_create(line_ctx* c, int order, int hidden, int act_dtype, uint64_t seed) {
+    line_status st = enter(c);
+    if (st) return st;
+    if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_mlp_create: no graph");
+    if ((order != 1 && order != 2) || hidden < 1 || hidden > 4096 ||
+        (act_dtype != LINE_DTYPE_F32 && act_dtype != LINE_DTYPE_BF16))
+        return fail(c, LINE_ERR_ARG, "line_mlp_create: bad order, hidden width or activation type");
+    const Tables& t = c->tab[order];
+    if (!t.ready) return fail(c, LINE_ERR_STATE, "line_mlp_create: no tables of order %d", order);
+    mlp_destroy(c->mlp);
+    c->mlp = nullptr;
+    MlpState* s = new MlpState();
+    s->order = order;
+    s->dim = t.dim;
+    s->hidden = hidden;
+    s->P = (t.dim + 1 + 15) / 16 * 16;
+    s->act = act_dtype;
+    s->n_nodes = c->n_nodes;
+    const Layout L(*s);
+    s->n_params = L.n;
+    const size_t pb = sizeof(float) * L.n;
+    cudaError_t e = cudaMalloc(&s->params, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&s->grads, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&s->m, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&s->v, pb);
+    if (e == cudaSuccess) e = cudaMalloc(&s->X, (size_t)c->n_nodes * s->P * elem_size(act_dtype));
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->m, 0, pb, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->v, 0, pb, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->grads, 0, pb, c->stream);
+    if (e == cudaSuccess) {
+        const float s1 = (float)(1.0 / sqrt((double)(t.dim + 1)));
+        const float s2 = (float)(1.0 / sqrt((double)hidden));
+        k_mlp_init<<<grid_of(L.n, 256), 256, 0, c->stream>>>(s->params, hidden, s->P, t.dim, seed, s1, s2);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) {
+        mlp_destroy(s);
+        return cuda_fail(c, e, "line_mlp_create");
+    }
+    c->mlp = s;
+    return LINE_OK;
+}
+
+line_status line_mlp_features(line_ctx* c, const uint8_t* known) {
+    line_status st = enter(c);
+    if (st) return st;
+    if ((st = mlp_ready(c, "line_mlp_features", false))) return st;
+    if (!known) return fail(c, LINE_ERR_ARG, "line_mlp_features: null mask");
+    MlpState& s = *c->mlp;
+    const Tables& t = c->tab[s.order];
+    uint8_t* kd = nullptr;
+    cudaError_t e = cudaMalloc(&kd, c->n_nodes);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(kd, known, c->n_nodes, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) {
+        const unsigned g = grid_of(c->n_nodes * 32, 256, 152 * 64);
+        if (s.act == LINE_DTYPE_F32)
+            k_mlp_features<float><<<g, 256, 0, c->stream>>>(c->n_nodes, c->n_arcs, c->src, c->dst, c->deg, t.U,
+                                                            t.dtype, s.dim, kd, s.P, reinterpret_cast<float*>(s.X));
+        else
+            k_mlp_features<__nv_bfloat16><<<g, 256, 0, c->stream>>>(c->n_nodes, c->n_arcs, c->src, c->dst, c->deg,
+                                                                    t.U, t.dtype, s.dim, kd, s.P,
+                                                                    reinterpret_cast<__nv_bfloat16*>(s.X));
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (kd) cudaFree(kd);
+    if (e != cudaSuccess) return cuda_fail(c, e, "line_mlp_features");
+    s.has_features = true;
+    return LINE_OK;
+}
+
+line_status line_mlp_get_features(line_ctx* c, float* out) {
+    line_status st = enter(c);
+    if (st) return st;
+    if ((st = mlp_ready(c, "line_mlp_get_features", true))) return st;
+    if (!out) return fail(c, LINE_ERR_ARG, "line_mlp_get_features: null output");
+    MlpState& s = *c->mlp;
+    const size_t n = (size_t)c->n_nodes * s.P;
+    if (s.act == LINE_DTYPE_F32) {
+        CK(cudaMemcpyAsync(out, s.X, n * 4, cudaMemcpyDefault, c->stream), "line_mlp_get_features");
+        CK(cudaStreamSynchronize(c->stream), "line_mlp_get_features");
+        return LINE_OK;
+    }
+    void* buf = nullptr;
+    CK(cudaMalloc(&buf, n * 4), "line_mlp_get_features");
+    cudaError_t e = convert_rows(s.X, LINE_DTYPE_BF16, buf, LINE_DTYPE_F32, nullptr, c->n_nodes, s.P, c->n_nodes,
+                                 c->status, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, buf, n * 4, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(c, e, "line_mlp_get_features");
+    return LINE_OK;
+}
+
+line_status line_mlp_get_params(line_ctx* c, float* out, int64_t* n_params) {
+    line_status st = enter(c);
+    if (st) return st;
+    if (!c->mlp) return fail(c, LINE_ERR_STATE, "line_mlp_get_params: no MLP");
+    if (n_params) *n_params = c->mlp->n_params;
+    if (out) {
+        CK(cudaMemcpyAsync(out, c->mlp->params, sizeof(float) * c->mlp->n_params, cudaMemcpyDefault, c->stream),
+           "line_mlp_get_params");
+        CK(cudaStreamSynchronize(c->stream), "line_mlp_get_params");
+    }
+    return LINE_OK;
+}
+
+line_status line_mlp_set_params(line_ctx* c, const float* in) {
+    line_status st = enter(c);
+    if (st) return st;
+    if (!c->mlp) return fail(c, LINE_ERR_STATE, "line_mlp_set_params: no MLP");
+    if (!in) return fail(c, LINE_ERR_ARG, "line_mlp_set_params: null input");
+    MlpState& s = *c->mlp;
+    const size_t pb = sizeof(float) * s.n_params;
+    CK(cudaMemcpyAsync(s.params, in, pb, cudaMemcpyDefault, c->stream), "line_mlp_set_params");
+    // a new starting point: the optimiser state restarts
+    CK(cudaMemsetAsync(s.m, 0, pb, c->stream), "line_mlp_set_params");
+    CK(cudaMemsetAsync(s.v, 0, pb, c->stream), "line_mlp_set_params");
+    CK(cudaStreamSynchronize(c->stream), "line_mlp_set_params");
+    s.t = 0;
+    return LINE_OK;
+}
+
+line_status line_mlp_grad(line_ctx* c, const int32_t* rows, int64_t n_rows, float* grads_out, double* loss_out) {
+    line_status st = enter(c);
+    if (st) return st;
+    if ((st = mlp_ready(c, "line_mlp_grad", true))) return st;
+    if (!rows || n_rows < 1 || n_rows > kMlpMaxBatch)
+        return fail(c, LINE_ERR_ARG, "line_mlp_grad: n_rows must be 1..%lld", (long long)kMlpMaxBatch);
+    MlpState& s = *c->mlp;
+    const Tables& t = c->tab[s.order];
+    CK(ensure_cap(s, n_rows), "line_mlp_grad");
+    CK(cudaMemcpyAsync(s.rows, rows, sizeof(int32_t) * n_rows, cudaMemcpyDefault, c->stream), "line_mlp_grad");
+    cudaError_t e = s.act == LINE_DTYPE_F32
+                        ? loss_grad<float>(s, n_rows, t, c->status, c->n_nodes, c->dscratch, c->stream)
+                        : loss_grad<__nv_bfloat16>(s, n_rows, t, c->status, c->n_nodes, c->dscratch, c->stream);
+    if (e == cudaSuccess) {
+        k_scale_loss<<<1, 1, 0, c->stream>>>(c->dscratch, 1.0 / ((double)n_rows * s.dim));
+        e = cudaGetLastError();
+    }
+    double loss = 0.0;
+    if (e == cudaSuccess && grads_out)
+        e = cudaMemcpyAsync(grads_out, s.grads, sizeof(float) * s.n_params, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&loss, c->dscratch, sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "line_mlp_grad");
+    if ((st = check_status(c, "line_mlp_grad"))) return st;
+    if (loss_out) *loss_out = loss;
+    return LINE_OK;
+}
+
+line_status line_mlp_train(line_ctx* c, const int32_t* nodes, int64_t n_nodes, int64_t steps, int64_t batch,
+                           double lr, uint64_t seed, uint64_t step_offset, double* losses_out) {
+    line_status st = enter(c);
+    if (st) return st;
+    if ((st = mlp_ready(c, "line_mlp_train", true))) return st;
+    if (!nodes || n_nodes < 1 || steps < 0 || batch < 1 || batch > kMlpMaxBatch || !(lr >= 0.0))
+        return fail(c, LINE_ERR_ARG, "line_mlp_train: bad arguments");
+    if (steps == 0) return LINE_OK;
+    MlpState& s = *c->mlp;
+    const Tables& t = c->tab[s.order];
+    cudaStream_t str = c->stream;
+    CK(ensure_cap(s, batch), "line_mlp_train");
+    CK(upload_nodes(s, nodes, n_nodes, str), "line_mlp_train");
+    if (steps > s.loss_cap) {
+        if (s.losses) cudaFree(s.losses);
+        s.losses = nullptr;
+        s.loss_cap = 0;
+        CK(cudaMalloc(&s.losses, sizeof(double) * steps), "line_mlp_train");
+        s.loss_cap = steps;
+    }
+    // node ids out of range are reported by the gather (status word)
+    for (int64_t k = 0; k < steps; ++k) {
+        const uint64_t gstep = step_offset + (uint64_t)k;
+        k_mlp_batch<<<grid_of(batch, 256), 256, 0, str>>>(s.nodes, n_nodes, seed, gstep * (uint64_t)batch, batch,
+                                                          s.rows);
+        cudaError_t e = s.act == LINE_DTYPE_F32
+                            ? loss_grad<float>(s, batch, t, c->status, c->n_nodes, s.losses + k, str)
+                            : loss_grad<__nv_bfloat16>(s, batch, t, c->status, c->n_nodes, s.losses + k, str);
+        if (e != cudaSuccess) return cuda_fail(c, e, "line_mlp_train");
+        ++s.t;
+        const float c1 = (float)(1.0 / (1.0 - pow(0.9, (double)s.t)));
+        const float c2 = (float)(1.0 / (1.0 - pow(0.999, (double)s.t)));
+        k_adam<<<grid_of(s.n_params, 256), 256, 0, str>>>(s.params, s.grads, s.m, s.v, s.n_params, (float)lr, c1, c2);
+        CK(cudaGetLastError(), "line_mlp_train");
+    }
+    if (losses_out) {
+        std::vector<double> tmp(steps);
+        CK(cudaMemcpyAsync(tmp.data(), s.losses, sizeof(double) * steps, cudaMemcpyDeviceToHost, str), "line_mlp_train");
+        CK(cudaStreamSynchronize(str), "line_mlp_train");
+        const double inv = 1.0 / ((double)batch * s.dim);
+        for (int64_t k = 0; k < steps; ++k) losses_out[k] = tmp[k] * inv;
+    }
+    return check_status(c, "line_mlp_train");
+}
+
+line_status line_mlp_predict(line_ctx* c, const int32_t* rows, int64_t n_rows, float* y_out) {
+    line_status st = enter(c);
+    if (st) return st;
+    if ((st = mlp_ready(c, "line_mlp_predict", true))) return st;
+    if (!rows || n_rows < 0) return fail(c, LINE_ERR_ARG, "line_mlp_predict: bad arguments");
+    if (n_rows == 0) return LINE_OK;
+    MlpState& s = *c->mlp;
+    const Tables& t = c->tab[s.order];
+    cudaStream_t str = c->stream;
+    const int64_t chunk = std::min<int64_t>(n_rows, kMlpMaxBatch);
+    CK(ensure_cap(s, chunk), "line_mlp_predict");
+    float* ybuf = nullptr;
+    if (y_out) CK(cudaMalloc(&ybuf, sizeof(float) * n_rows * s.dim), "line_mlp_predict");
+    const Layout L(s);
+    cudaError_t e = cudaSuccess;
+    for (int64_t r0 = 0; r0 < n_rows && e == cudaSuccess; r0 += chunk) {
+        const int64_t B = std::min(chunk, n_rows - r0);
+        e = cudaMemcpyAsync(s.rows, rows + r0, sizeof(int32_t) * B, cudaMemcpyDefault, str);
+        if (e == cudaSuccess)
+            e = s.act == LINE_DTYPE_F32 ? forward<float>(s, B, t, false, c->status, c->n_nodes, str)
+                                        : forward<__nv_bfloat16>(s, B, t, false, c->status, c->n_nodes, str);
+        if (e == cudaSuccess) {
+            if (ybuf)
+                k_ep_predict<<<grid_of(B * s.dim, 256), 256, 0, str>>>(s.Yb, s.params + L.b2, B, s.dim, nullptr, 0,
+                                                                       ybuf + r0 * s.dim, LINE_DTYPE_F32);
+            else
+                k_ep_predict<<<grid_of(B * s.dim, 256), 256, 0, str>>>(s.Yb, s.params + L.b2, B, s.dim, s.rows,
+                                                                       c->n_nodes, t.U, t.dtype);
+            e = cudaGetLastError();
+        }
+    }
+    if (e == cudaSuccess && ybuf) e = cudaMemcpyAsync(y_out, ybuf, sizeof(float) * n_rows * s.dim, cudaMemcpyDefault, str);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(str);
+    if (ybuf) cudaFree(ybuf);
+    if (e != cudaSuccess) return cuda_fail(c, e, "line_mlp_predict");
+    return check_status(c, "line_mlp_predict");
+}
+
+}  // extern "C"

@@ -44,6 +44,7 @@ __all__ = [
     "rmat20",
     "split_edges",
     "non_edges",
+    "hold_out_nodes",
 ]
 
 _GOLDEN = np.uint64(0x9E3779B97F4A7C15)
@@ -56,6 +57,7 @@ STREAM_RMAT = 6
 STREAM_DIRECTED = 7
 STREAM_SPLIT = 8
 STREAM_NON_EDGE = 9
+STREAM_NODE_SPLIT = 10
 
 
 @dataclasses.dataclass
@@ -299,3 +301,12 @@ def non_edges(g: Graph, count: int, seed: int = 0) -> tuple[np.ndarray, np.ndarr
         have += take
     return (np.concatenate(out_u).astype(np.int32) if out_u else np.zeros(0, np.int32),
             np.concatenate(out_v).astype(np.int32) if out_v else np.zeros(0, np.int32))
+
+
+def hold_out_nodes(g: Graph, frac: float = 0.1, seed: int = 0) -> tuple[np.ndarray, Graph]:
+    """Hold out ``frac`` of the nodes: returns ``(held, graph)``, ``held`` a
+    boolean mask over nodes and ``graph`` the arcs of ``g`` with neither
+    endpoint held (same node count, so the held nodes are isolated)."""
+    held = uniform01(seed, STREAM_NODE_SPLIT, np.arange(g.n_nodes, dtype=np.uint64)) < frac
+    keep = ~held[g.src] & ~held[g.dst]
+    return held, Graph(g.n_nodes, g.src[keep], g.dst[keep], g.w[keep], g.directed, g.name + "_kept")

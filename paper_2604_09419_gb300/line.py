@@ -23,6 +23,7 @@ DTYPE_F32, DTYPE_BF16 = 0, 1
 TABLE_EDGE, TABLE_NEG = 0, 1
 WHICH_U, WHICH_C = 0, 1
 MODE_BATCHED, MODE_PERSISTENT = 0, 1
+SCORE_DOT, SCORE_COSINE = 0, 1
 
 
 class GraphDesc(ctypes.Structure):
@@ -69,7 +70,15 @@ def _load():
         "line_set_embeddings": (i32, [vp, i32, i32, vp, i32, vp, i64]),
         "line_eval_loss": (i32, [vp, i32, i32, u64, i64, ctypes.POINTER(dbl)]),
         "line_eval_loss_noalloc": (i32, [vp, i32, i32, u64, i64, ctypes.POINTER(dbl)]),
-        "line_eval_auc": (i32, [vp, i32, vp, vp, i64, vp, vp, i64, vp, vp, ctypes.POINTER(dbl)]),
+        "line_eval_auc": (i32, [vp, i32, i32, vp, vp, i64, vp, vp, i64, vp, vp, ctypes.POINTER(dbl)]),
+        "line_mlp_create": (i32, [vp, i32, i32, i32, u64]),
+        "line_mlp_features": (i32, [vp, vp]),
+        "line_mlp_get_features": (i32, [vp, vp]),
+        "line_mlp_get_params": (i32, [vp, vp, ctypes.POINTER(i64)]),
+        "line_mlp_set_params": (i32, [vp, vp]),
+        "line_mlp_grad": (i32, [vp, vp, i64, vp, ctypes.POINTER(dbl)]),
+        "line_mlp_train": (i32, [vp, vp, i64, i64, i64, dbl, u64, u64, vp]),
+        "line_mlp_predict": (i32, [vp, vp, i64, vp]),
         "line_get_stats": (i32, [vp, ctypes.POINTER(Stats)]),
         "line_reset_stats": (i32, [vp]),
         "line_synchronize": (i32, [vp]),
@@ -86,7 +95,9 @@ lib = _load()
 EXPORTED = ("line_train_opts_default", "line_status_string", "line_create", "line_destroy", "line_last_error",
             "line_build_alias", "line_get_graph_info", "line_get_alias", "line_sample_debug",
             "line_init_embeddings", "line_train_steps", "line_get_embeddings", "line_set_embeddings",
-            "line_eval_loss", "line_eval_loss_noalloc", "line_eval_auc", "line_get_stats", "line_reset_stats", "line_synchronize", "line_debug_wait_timeout")
+            "line_eval_loss", "line_eval_loss_noalloc", "line_eval_auc", "line_mlp_create", "line_mlp_features",
+            "line_mlp_get_features", "line_mlp_get_params", "line_mlp_set_params", "line_mlp_grad", "line_mlp_train",
+            "line_mlp_predict", "line_get_stats", "line_reset_stats", "line_synchronize", "line_debug_wait_timeout")
 
 
 class LineError(RuntimeError):
@@ -188,14 +199,51 @@ class Context:
         self._ck(lib.line_eval_loss_noalloc(self.h, order, K, seed, m, ctypes.byref(out)))
         return out.value
 
-    def eval_auc(self, orders, pos_src, pos_dst, neg_src, neg_dst, scores=None):
+    def eval_auc(self, orders, pos_src, pos_dst, neg_src, neg_dst, scores=None, score=SCORE_DOT):
         """Link-prediction AUC; returns (auc, (#(neg < pos), #(neg == pos)))."""
         out = ctypes.c_double()
         counts = np.zeros(2, np.uint64)
-        self._ck(lib.line_eval_auc(self.h, orders, ptr(pos_src), ptr(pos_dst), int(pos_src.shape[0]), ptr(neg_src),
+        self._ck(lib.line_eval_auc(self.h, orders, score, ptr(pos_src), ptr(pos_dst), int(pos_src.shape[0]), ptr(neg_src),
                                    ptr(neg_dst), int(neg_src.shape[0]), ptr(scores), counts.ctypes.data,
                                    ctypes.byref(out)))
         return out.value, (int(counts[0]), int(counts[1]))
+
+    # ---- warm-start MLP
+    def mlp_create(self, order, hidden=256, act_dtype=DTYPE_BF16, seed=0):
+        return self._ck(lib.line_mlp_create(self.h, order, hidden, act_dtype, seed))
+
+    def mlp_features(self, known):
+        return self._ck(lib.line_mlp_features(self.h, ptr(known)))
+
+    def mlp_get_features(self, out):
+        return self._ck(lib.line_mlp_get_features(self.h, ptr(out)))
+
+    def mlp_n_params(self) -> int:
+        n = ctypes.c_int64()
+        self._ck(lib.line_mlp_get_params(self.h, None, ctypes.byref(n)))
+        return n.value
+
+    def mlp_get_params(self) -> np.ndarray:
+        out = np.empty(self.mlp_n_params(), np.float32)
+        self._ck(lib.line_mlp_get_params(self.h, out.ctypes.data, None))
+        return out
+
+    def mlp_set_params(self, params):
+        return self._ck(lib.line_mlp_set_params(self.h, ptr(params)))
+
+    def mlp_grad(self, rows, grads_out=None) -> float:
+        loss = ctypes.c_double()
+        self._ck(lib.line_mlp_grad(self.h, ptr(rows), int(rows.shape[0]), ptr(grads_out), ctypes.byref(loss)))
+        return loss.value
+
+    def mlp_train(self, nodes, steps, batch, lr=1e-3, seed=0, step_offset=0, losses=True):
+        out = np.empty(steps, np.float64) if losses else None
+        self._ck(lib.line_mlp_train(self.h, ptr(nodes), int(nodes.shape[0]), steps, batch, lr, seed, step_offset,
+                                    None if out is None else out.ctypes.data))
+        return out
+
+    def mlp_predict(self, rows, y_out=None):
+        return self._ck(lib.line_mlp_predict(self.h, ptr(rows), int(rows.shape[0]), ptr(y_out)))
 
     def stats(self) -> Stats:
         s = Stats()

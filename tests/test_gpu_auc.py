@@ -1,7 +1,7 @@
 """Link-prediction AUC through the C ABI against the FP64 oracle.
 
-* FP32 cosine scores against the oracle's FP64 scores of the same tables,
-  within a bound derived from FP32 dot products of d terms;
+* FP32 scores (inner product or cosine) against the oracle's FP64 scores of
+  the same tables, within bounds derived from FP32 dot products of d terms;
 * the AUC counts (#(neg < pos), #(neg == pos)) equal to the oracle's
   Mann-Whitney counts over the GPU's own scores, exactly (the comparison
   decisions are taken in the kernel's precision on both sides);
@@ -18,10 +18,14 @@ from tests import gpu_util as G
 pytestmark = pytest.mark.gpu
 
 
-def score_tol(dims):
-    # |fl(cos) - cos| for FP32 FMA dots of d terms: about d unit roundoffs in
-    # the dot and norms, a few more in the sqrt/div/combination
-    return (2 * max(dims) + 16) * 2.0 ** -24
+def score_tol(dims, tabs, src, dst, score):
+    if score == "cosine":
+        # |fl(cos) - cos|: about d unit roundoffs in the dot and the norms, a
+        # few more in the sqrt/div/combination
+        return (2 * max(dims) + 16) * 2.0 ** -24
+    # FP32 FMA dot of d terms: |error| <= d u sum |a_k b_k| (plus the sum of orders)
+    absdot = OL.pair_scores([np.abs(t) for t in tabs], src, dst, "dot")
+    return (max(dims) + 4) * 2.0 ** -24 * absdot + 1e-30
 
 
 @pytest.fixture(scope="module")
@@ -37,13 +41,16 @@ def split_pairs(g, seed=0, frac=0.1):
     return tr, hs, hd, ns, nd
 
 
-def check(ctx, orders, tabs, hs, hd, ns, nd, dims):
+def check(ctx, orders, tabs, hs, hd, ns, nd, dims, score="dot"):
+    from paper_2604_09419_gb300 import line as L
     n = len(hs) + len(ns)
     scores = np.empty(n, np.float32)
-    auc, (less, eq) = ctx.eval_auc(orders, hs, hd, ns, nd, scores)
-    want = np.concatenate([OL.pair_scores(tabs, hs, hd), OL.pair_scores(tabs, ns, nd)])
-    err = np.abs(scores.astype(np.float64) - want).max()
-    assert err <= score_tol(dims), err
+    code = L.SCORE_DOT if score == "dot" else L.SCORE_COSINE
+    auc, (less, eq) = ctx.eval_auc(orders, hs, hd, ns, nd, scores, score=code)
+    src, dst = np.concatenate([hs, ns]), np.concatenate([hd, nd])
+    want = OL.pair_scores(tabs, src, dst, score)
+    err = np.abs(scores.astype(np.float64) - want)
+    assert (err <= score_tol(dims, tabs, src, dst, score)).all(), err.max()
     # exact counts over the GPU's scores
     l2, e2 = OL.mann_whitney_counts(scores[:len(hs)], scores[len(hs):])
     assert (less, eq) == (l2, e2)
@@ -68,11 +75,13 @@ def test_auc_tiny_both_orders(ctx):
     U2, C2 = oracle_trained(tr, 2, 16, 100_000, 4)
     U1 = G.upload_tables(ctx, 1, U1)
     U2, _ = G.upload_tables(ctx, 2, U2, C2)
-    a1, w1 = check(ctx, 1, [U1], hs, hd, ns, nd, [16])
-    a2, w2 = check(ctx, 2, [U2], hs, hd, ns, nd, [16])
-    a3, w3 = check(ctx, 3, [U1, U2], hs, hd, ns, nd, [16, 16])
+    res = []
+    for score in ("dot", "cosine"):
+        res.append(check(ctx, 1, [U1], hs, hd, ns, nd, [16], score))
+        res.append(check(ctx, 2, [U2], hs, hd, ns, nd, [16], score))
+        res.append(check(ctx, 3, [U1, U2], hs, hd, ns, nd, [16, 16], score))
     # FP32 against FP64 scores: the AUCs agree to a few flipped near-ties
-    for a, w in ((a1, w1), (a2, w2), (a3, w3)):
+    for a, w in res:
         assert abs(a - w) < 1e-3
 
 
@@ -89,6 +98,7 @@ def test_auc_ties_many_tiles_and_bf16(ctx):
     U[::3] = 0.0
     U2, _ = G.upload_tables(ctx, 2, U, C, dtype=L.DTYPE_BF16)
     auc, want = check(ctx, 2, [U2], hs, hd, ns, nd, [128])
+    check(ctx, 2, [U2], hs, hd, ns, nd, [128], "cosine")
     scores = np.empty(len(hs) + len(ns), np.float32)
     ctx.eval_auc(2, hs, hd, ns, nd, scores)
     assert (scores == 0).sum() > len(scores) // 4
@@ -107,6 +117,9 @@ def test_auc_errors(ctx):
     assert ei.value.status == L.LINE_ERR_STATE
     with pytest.raises(L.LineError) as ei:
         ctx.eval_auc(4, hs, hd, hs, hd)
+    assert ei.value.status == L.LINE_ERR_ARG
+    with pytest.raises(L.LineError) as ei:
+        ctx.eval_auc(1, hs, hd, hs, hd, score=2)
     assert ei.value.status == L.LINE_ERR_ARG
     bad = np.array([0, g.n_nodes], np.int32)
     with pytest.raises(L.LineError) as ei:
