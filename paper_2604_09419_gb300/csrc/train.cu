@@ -46,10 +46,14 @@
 #include <cstdio>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "line_internal.cuh"
 #include "scan.cuh"
 
 namespace line {
+
+namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------------------
 // Row geometry: a row of D values is handled by L lanes, E values per lane,
@@ -772,8 +776,14 @@ __global__ void k_chunk_draws(PrepassParams p) {
 // ---------------------------------------------------------------------------
 constexpr int kBuckets = 256;            // bucket = 8-bit multiplicative hash of the row id
 
-// Fibonacci hashing: spreads the hot (low) row ids of skewed graphs.
-__device__ __forceinline__ uint32_t bucket_of(uint32_t row) { return (row * 0x9E3779B1u) >> 24; }
+// Fibonacci hashing: spreads the hot (low) row ids of skewed graphs.  The
+// multiplier is odd, so hrow is a bijection of 32-bit words (inverse
+// 0x0E8B2F51); within a batch items are ordered by (hrow(row), index), which
+// puts them bucket by bucket (bucket = top 8 bits) and each row's entries
+// together in index order.
+__device__ __forceinline__ uint32_t hrow(uint32_t row) { return row * 0x9E3779B1u; }
+__device__ __forceinline__ uint32_t unhrow(uint32_t h) { return h * 0x0E8B2F51u; }
+__device__ __forceinline__ uint32_t bucket_of(uint32_t row) { return hrow(row) >> 24; }
 constexpr int kBucketThreads = 1024;
 constexpr int kBucketWarps = kBucketThreads / 32;
 constexpr uint32_t kPartItems = 16384;   // items of a batch per bucketing CTA
@@ -799,7 +809,7 @@ struct GroupParams {
     uint32_t* lcount;
     uint32_t lcap;
     uint32_t* nseg;       // persistent only (nullptr otherwise)
-    uint32_t* sorted_row; // persistent only: row id by position
+    uint32_t* sorted_row; // persistent only: hrow(row id) by position
     uint32_t* seghead;    // persistent only: first position of the position's segment
 };
 
@@ -894,7 +904,7 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket_scatter(GroupParams q
 }
 
 // One stable 8-bit LSD pass of a warp over n items (global memory), by bits
-// [shift, shift + 8) of the row id.  cnt: the warp's 256 shared counters.
+// [shift, shift + 8) of the hashed row id.  cnt: the warp's 256 shared counters.
 __device__ void warp_radix_pass(const uint64_t* src, uint64_t* dst, uint32_t n, uint32_t shift, uint32_t* cnt) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt = (1u << lane) - 1u;
@@ -903,7 +913,7 @@ __device__ void warp_radix_pass(const uint64_t* src, uint64_t* dst, uint32_t n, 
     for (uint32_t r = 0; r < n; r += 32) {
         const uint32_t i = r + lane;
         const bool valid = i < n;
-        const uint32_t d = valid ? (uint32_t)(src[i] >> (32 + shift)) & 255u : 0xFFFFu;
+        const uint32_t d = valid ? (hrow((uint32_t)(src[i] >> 32)) >> shift) & 255u : 0xFFFFu;
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
         if (valid && (peers & lt) == 0) cnt[d] += __popc(peers);
         __syncwarp();
@@ -931,7 +941,7 @@ __device__ void warp_radix_pass(const uint64_t* src, uint64_t* dst, uint32_t n, 
         const uint32_t i = r + lane;
         const bool valid = i < n;
         const uint64_t it = valid ? src[i] : 0ull;
-        const uint32_t d = valid ? (uint32_t)(it >> (32 + shift)) & 255u : 0xFFFFu;
+        const uint32_t d = valid ? (hrow((uint32_t)(it >> 32)) >> shift) & 255u : 0xFFFFu;
         const uint32_t peers = __match_any_sync(0xFFFFFFFFu, d);
         const uint32_t before = valid ? cnt[d] : 0u;
         if (valid) dst[before + __popc(peers & lt)] = it;
@@ -961,8 +971,8 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort(GroupParams q) {
     if (c == 0) return;
     const uint64_t* a;
     if (c <= kWarpSortCap) {
-        // bitonic sort of the unique keys (row << 32 | index) over the next
-        // power of two, padded with the largest key; then items by rank
+        // bitonic sort of the unique keys (hrow(row) << 32 | index) over the
+        // next power of two, padded with the largest key; then items by rank
         uint64_t* in = sbuf + (size_t)warp * 2 * kWarpSortCap;
         uint64_t* key = in + kWarpSortCap;
         uint32_t P = 32;
@@ -971,7 +981,7 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort(GroupParams q) {
             if (i < c) {
                 const uint64_t it = q.bucketed[base + lo + i];
                 in[i] = it;
-                key[i] = (it & 0xFFFFFFFF00000000ull) | i;
+                key[i] = ((uint64_t)hrow((uint32_t)(it >> 32)) << 32) | i;
             } else {
                 key[i] = ~0ull;
             }
@@ -998,10 +1008,10 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort(GroupParams q) {
         }
         __syncwarp();
         a = key;
-    } else {  // a large bucket (a very skewed draw): radix passes over all row bits
+    } else {  // a large bucket (a very skewed draw): radix passes over the hashed row
         uint64_t* x = q.bucketed + base + lo;
         uint64_t* y = q.tmp + base + lo;
-        for (uint32_t sh = 0; sh < q.row_bits; sh += 8) {
+        for (uint32_t sh = 0; sh < 32; sh += 8) {
             warp_radix_pass(x, y, c, sh, wcnt[warp]);
             uint64_t* t = x;
             x = y;
@@ -1026,7 +1036,7 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort(GroupParams q) {
             const uint32_t pos = (uint32_t)(gpos + k);
             q.slot_info[(v >> kSlotBits) * q.R + slot] = make_uint2(pos | (len == 1 ? kSingleBit : 0u), head);
             if (q.sorted_row) {
-                q.sorted_row[pos] = key;
+                q.sorted_row[pos] = hrow(key);
                 q.seghead[pos] = head;
             }
         }
@@ -1044,6 +1054,322 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort(GroupParams q) {
     }
 }
 
+// ---- Grouping of a batch by one thread-block cluster (batches of up to 8 x
+// 3,584 items).  The items are split into P = 2^log_parts parts by the top
+// bits of hrow(row) (a part is a contiguous range of buckets) and each part
+// into 256 sub-buckets by the next 8 bits.  CTA rank r of batch b's cluster
+// counts the (part, sub-bucket) sizes of the r-th slice of the batch's draws;
+// after an exchange of counts every CTA knows where each of its keys
+// (hrow(row) << 32 | index) goes in the owner's shared memory (distributed
+// shared memory) and sends it there.  Each owner then sorts its sub-buckets
+// (about 14 keys each: one thread; larger ones: one warp) and emits its
+// segments.  The order, hence every position, is the same as the bucketed
+// path's: (hrow(row), index).
+constexpr int kGroupThreads = 512;
+constexpr uint32_t kGroupCap = 4096;  // keys of a part held in shared memory
+constexpr int kGroupMaxLog = 3;       // clusters of up to 8 CTAs (portable size)
+constexpr int kSub = 256;             // sub-buckets of a part
+constexpr int kGroupPerThread = 8;    // slice items per thread loaded at once
+
+// In-place ascending sort of a[0 .. n) by one warp: a bitonic network whose
+// comparators all put the minimum first (per merge size k the mirror
+// comparator (i, k-1-i) within each k-block, then half-cleaners of strides
+// k/4 .. 1); positions >= n act as +infinity, so comparators reaching past n
+// are skipped.
+__device__ __forceinline__ void warp_sort_keys(uint64_t* a, uint32_t n) {
+    const int lane = threadIdx.x & 31;
+    uint32_t N = 1;
+    while (N < n) N <<= 1;
+    for (uint32_t k = 2; k <= N; k <<= 1) {
+        const uint32_t lh = 31 - __clz(k >> 1);
+        for (uint32_t t = lane; t < N / 2; t += 32) {
+            const uint32_t blk = t >> lh, off = t & ((k >> 1) - 1);
+            const uint32_t i = blk * k + off, j = blk * k + k - 1 - off;
+            if (j < n) {
+                const uint64_t x = a[i], y = a[j];
+                if (x > y) {
+                    a[i] = y;
+                    a[j] = x;
+                }
+            }
+        }
+        __syncwarp();
+        for (uint32_t jj = k >> 2; jj > 0; jj >>= 1) {
+            for (uint32_t t = lane; t < N / 2; t += 32) {
+                const uint32_t i = ((t & ~(jj - 1)) << 1) | (t & (jj - 1)), j = i + jj;
+                if (j < n) {
+                    const uint64_t x = a[i], y = a[j];
+                    if (x > y) {
+                        a[i] = y;
+                        a[j] = x;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+// The second half of the grouping of one part: sort its sub-buckets, write
+// its bucket starts and emit its segments.  `a` holds the part's nq keys
+// grouped by sub-bucket (s_start); inlined once for shared memory and once
+// for the global scratch, so that the common case uses shared-memory accesses.
+struct GroupShared {
+    uint32_t* start;  // [kSub + 1] sub-bucket starts
+    uint32_t* big;    // [kSub]
+    uint32_t* nbig;
+    uint32_t* mcnt;
+    uint32_t* lcnt;
+    uint32_t* mbase;
+    uint32_t* lbase;
+};
+
+__device__ __forceinline__ void group_tail(const GroupParams& q, uint64_t* a, uint32_t nq, uint64_t base, uint32_t n,
+                                           uint32_t qbase, int b, uint32_t me, uint32_t P, int log_parts,
+                                           const GroupShared& sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int kWarps = kGroupThreads / 32;
+    const uint32_t* s_start = sh.start;
+    const uint64_t gpos = base + qbase;  // position of the part's first key in the chunk
+    // sort each sub-bucket by (hrow(row), index): up to 32 keys by ranks
+    // within a warp, larger ones (a hot row) by a warp bitonic sort
+    for (int sb = warp; sb < kSub; sb += kWarps) {
+        const uint32_t s0 = s_start[sb], c = s_start[sb + 1] - s0;
+        if (c <= 1) continue;
+        if (c <= 32) {
+            const uint64_t key = lane < (int)c ? a[s0 + lane] : ~0ull;
+            uint32_t rank = 0;
+            for (uint32_t l = 0; l < c; ++l) rank += __shfl_sync(0xFFFFFFFFu, key, l) < key;
+            __syncwarp();
+            if (lane < (int)c) a[s0 + rank] = key;
+            __syncwarp();
+        } else {
+            warp_sort_keys(a + s0, c);
+        }
+    }
+    __syncthreads();
+    // bucket starts of the part's buckets: bucket (me, j) begins at
+    // sub-bucket j << log_parts
+    const uint32_t nbk = (uint32_t)kBuckets >> log_parts, d0 = me * nbk;
+    for (uint32_t j = threadIdx.x; j < nbk; j += blockDim.x)
+        q.boff[(size_t)b * (kBuckets + 1) + d0 + j] = qbase + s_start[j << log_parts];
+    if (me == P - 1u && threadIdx.x == 0) q.boff[(size_t)b * (kBuckets + 1) + kBuckets] = n;
+    // segments (a segment never crosses a sub-bucket).  Per sub-bucket, in
+    // rounds of 32 keys: lane l holds key s0 + r + l; starts come from a
+    // ballot, the carry is the open segment of the previous round.
+    // Pass 0 counts the shared and long segments, pass 1 writes.
+    for (int pass = 0; pass < 2; ++pass) {
+        uint32_t n_m = 0, n_l = 0;
+        for (int sb = warp; sb < kSub; sb += kWarps) {
+            const uint32_t s0 = s_start[sb], c = s_start[sb + 1] - s0;
+            for (uint32_t r = 0; r < c; r += 32) {
+                const uint32_t i = s0 + r + lane;
+                const bool valid = r + lane < c;
+                const uint64_t key = valid ? a[i] : ~0ull;
+                const uint32_t hk = (uint32_t)(key >> 32);
+                const uint32_t prev = (valid && i > s0) ? (uint32_t)(a[i - 1] >> 32) : ~hk;
+                const bool start = valid && prev != hk;
+                const uint32_t smask = __ballot_sync(0xFFFFFFFFu, start);
+                // each key's segment: first start at or below it (or the
+                // round's carry), next start above it (or the sub-bucket end)
+                const uint32_t below = smask & (0xFFFFFFFFu >> (31 - lane));
+                uint32_t head = below ? s0 + r + (31 - __clz(below)) : 0u;
+                uint32_t len = 0;
+                if (valid) {
+                    if (!below) {  // continues a segment of an earlier round (a hot row)
+                        uint32_t h0 = i;
+                        while (h0 > s0 && (uint32_t)(a[h0 - 1] >> 32) == hk) --h0;
+                        head = h0;
+                    }
+                    const uint32_t above = smask & ~(0xFFFFFFFFu >> (31 - lane));
+                    uint32_t end = above ? s0 + r + (__ffs(above) - 1) : 0u;
+                    if (!above) {
+                        end = s0 + min(c, r + 32);
+                        while (end < s0 + c && (uint32_t)(a[end] >> 32) == hk) ++end;
+                    }
+                    len = end - head;
+                }
+                const bool is_head = valid && i == head;
+                if (pass == 0) {
+                    n_m += is_head && len > 1;
+                    n_l += is_head && len > kChunk;
+                    continue;
+                }
+                const uint32_t hpos = (uint32_t)(gpos + head);
+                if (valid) {
+                    const uint32_t v = (uint32_t)key;
+                    const uint32_t slot = v & kSlotMask;
+                    const uint32_t pos = (uint32_t)(gpos + i);
+                    q.slot_info[(v >> kSlotBits) * q.R + slot] = make_uint2(pos | (len == 1 ? kSingleBit : 0u), hpos);
+                    if (q.sorted_row) {
+                        q.sorted_row[pos] = hk;
+                        q.seghead[pos] = hpos;
+                    }
+                }
+                if (is_head) {
+                    if (q.nseg) atomicAdd(q.nseg + b, 1u);
+                    if (len > 1) {
+                        // pair count of the segment: K + 1 for a source entry, 1 otherwise
+                        uint32_t cnt = 0;
+                        for (uint32_t k = head; k < head + len; ++k)
+                            cnt += ((uint32_t)a[k] & kSlotMask) == 0 ? q.K + 1 : 1u;
+                        const uint32_t key_row = unhrow(hk);
+                        uint32_t flagged = len;
+                        if (len > kChunk) {
+                            const uint32_t l = *sh.lbase + atomicAdd(sh.lcnt, 1u);
+                            q.ldesc[(size_t)b * q.lcap + l] = make_uint4(hpos, len, key_row, cnt);
+                            flagged |= kLongBit;
+                        }
+                        const uint32_t m = *sh.mbase + atomicAdd(sh.mcnt, 1u);
+                        q.mdesc[(size_t)b * q.mcap + m] = make_uint4(hpos, flagged, key_row, cnt);
+                    }
+                }
+            }
+        }
+        if (pass == 0) {
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) {
+                n_m += __shfl_xor_sync(0xFFFFFFFFu, n_m, o);
+                n_l += __shfl_xor_sync(0xFFFFFFFFu, n_l, o);
+            }
+            if (threadIdx.x == 0) {
+                *sh.mcnt = 0;
+                *sh.lcnt = 0;
+            }
+            __syncthreads();
+            if (lane == 0 && n_m) atomicAdd(sh.mcnt, n_m);
+            if (lane == 0 && n_l) atomicAdd(sh.lcnt, n_l);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                *sh.mbase = *sh.mcnt ? atomicAdd(q.mcount + b, *sh.mcnt) : 0u;
+                *sh.lbase = *sh.lcnt ? atomicAdd(q.lcount + b, *sh.lcnt) : 0u;
+                *sh.mcnt = 0;
+                *sh.lcnt = 0;
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kGroupThreads) k_group_cluster(GroupParams q, int log_parts) {
+    extern __shared__ uint64_t gkeys[];                      // kGroupCap keys
+    __shared__ uint32_t s_cnt[1 << kGroupMaxLog][kSub];      // this slice: keys per (part, sub-bucket)
+    __shared__ uint32_t s_pre[1 << kGroupMaxLog][kSub];      // keys of (part, sub) in lower ranks' slices
+    __shared__ uint32_t s_off[1 << kGroupMaxLog][kSub];      // where this slice's next key of (part, sub) goes
+    __shared__ uint32_t s_start[kSub + 1];                   // my part's sub-bucket starts
+    __shared__ uint32_t s_tot[1 << kGroupMaxLog];            // keys per part
+    __shared__ uint32_t s_big[kSub];                         // sub-buckets too large for one thread
+    __shared__ uint32_t s_nbig, s_mcnt, s_lcnt, s_mbase, s_lbase;
+    cg::cluster_group cl = cg::this_cluster();
+    const uint32_t P = 1u << log_parts, me = cl.block_rank();
+    const int b = blockIdx.y;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint64_t base;
+    uint32_t n;
+    batch_range(q, b, &base, &n);
+    for (uint32_t i = threadIdx.x; i < P * kSub; i += blockDim.x) (&s_cnt[0][0])[i] = 0;
+    if (threadIdx.x == 0) s_nbig = 0;
+    __syncthreads();
+    const uint32_t per = (n + P - 1) / P;
+    const uint32_t lo = min(n, me * per), hi = min(n, lo + per);
+    const int sub_shift = 24 - log_parts;
+    // pass 1: counts of this slice
+    for (uint32_t r = lo; r < hi; r += kGroupThreads * kGroupPerThread) {
+        uint64_t it[kGroupPerThread];
+#pragma unroll
+        for (int k = 0; k < kGroupPerThread; ++k) {
+            const uint32_t i = r + k * kGroupThreads + threadIdx.x;
+            it[k] = i < hi ? q.items[base + i] : 0ull;
+        }
+#pragma unroll
+        for (int k = 0; k < kGroupPerThread; ++k) {
+            const uint32_t i = r + k * kGroupThreads + threadIdx.x;
+            if (i < hi) {
+                const uint32_t hv = hrow((uint32_t)(it[k] >> 32));
+                const uint32_t pt = log_parts ? hv >> (32 - log_parts) : 0u;
+                atomicAdd(&s_cnt[pt][(hv >> sub_shift) & (kSub - 1)], 1u);
+            }
+        }
+    }
+    cl.sync();
+    // every (part, sub-bucket): total over the cluster, and the keys of lower
+    // ranks (which go first); then per part the sub-bucket starts
+    for (uint32_t e = threadIdx.x; e < P * kSub; e += blockDim.x) {
+        uint32_t c[1 << kGroupMaxLog];
+#pragma unroll
+        for (uint32_t rk = 0; rk < (1u << kGroupMaxLog); ++rk)  // all loads in flight at once
+            c[rk] = rk < P ? cl.map_shared_rank(&s_cnt[0][0], rk)[e] : 0u;
+        uint32_t tot = 0, before = 0;
+#pragma unroll
+        for (uint32_t rk = 0; rk < (1u << kGroupMaxLog); ++rk) {
+            if (rk < me) before += c[rk];
+            tot += c[rk];
+        }
+        (&s_off[0][0])[e] = tot;  // totals for now
+        (&s_pre[0][0])[e] = before;
+    }
+    __syncthreads();
+    if (warp < (int)P) {
+        // exclusive scan of part `warp`'s sub-bucket totals: lane l owns 8
+        uint32_t v[kSub / 32], own = 0;
+#pragma unroll
+        for (int k = 0; k < kSub / 32; ++k) own += (v[k] = s_off[warp][lane * (kSub / 32) + k]);
+        uint32_t incl = own;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+            if (lane >= o) incl += x;
+        }
+        uint32_t run = incl - own;
+#pragma unroll
+        for (int k = 0; k < kSub / 32; ++k) {
+            const int sb = lane * (kSub / 32) + k;
+            if (warp == (int)me) s_start[sb] = run;
+            s_off[warp][sb] = run + s_pre[warp][sb];
+            run += v[k];
+        }
+        if (lane == 31) {
+            s_tot[warp] = run;
+            if (warp == (int)me) s_start[kSub] = run;
+        }
+    }
+    __syncthreads();
+    uint32_t qbase = 0, pbase[1 << kGroupMaxLog];
+    bool fits[1 << kGroupMaxLog];
+    for (uint32_t p2 = 0, run = 0; p2 < P; ++p2) {
+        pbase[p2] = run;
+        if (p2 == me) qbase = run;
+        fits[p2] = s_tot[p2] <= kGroupCap;
+        run += s_tot[p2];
+    }
+    const uint32_t nq = s_tot[me];
+    // pass 2: send every key to its place (a part too large for shared memory
+    // - a very skewed draw - uses its own range of the scratch array)
+    for (uint32_t r = lo; r < hi; r += kGroupThreads * kGroupPerThread) {
+        uint64_t it[kGroupPerThread];
+#pragma unroll
+        for (int k = 0; k < kGroupPerThread; ++k) {
+            const uint32_t i = r + k * kGroupThreads + threadIdx.x;
+            it[k] = i < hi ? q.items[base + i] : 0ull;
+        }
+#pragma unroll
+        for (int k = 0; k < kGroupPerThread; ++k) {
+            const uint32_t i = r + k * kGroupThreads + threadIdx.x;
+            if (i < hi) {
+                const uint32_t hv = hrow((uint32_t)(it[k] >> 32));
+                const uint32_t pt = log_parts ? hv >> (32 - log_parts) : 0u;
+                const uint32_t at = atomicAdd(&s_off[pt][(hv >> sub_shift) & (kSub - 1)], 1u);
+                uint64_t* dst = fits[pt] ? cl.map_shared_rank(gkeys, pt) : q.bucketed + base + pbase[pt];
+                dst[at] = ((uint64_t)hv << 32) | (uint32_t)it[k];
+            }
+        }
+    }
+    cl.sync();
+    const GroupShared sh{s_start, s_big, &s_nbig, &s_mcnt, &s_lcnt, &s_mbase, &s_lbase};
+    if (fits[me]) group_tail(q, gkeys, nq, base, n, qbase, b, me, P, log_parts, sh);
+    else group_tail(q, q.bucketed + base + qbase, nq, base, n, qbase, b, me, P, log_parts, sh);
+}
+
 // slot_prev[(s, slot)] = segment of the same row in the previous batch of the
 // chunk, or -1: binary search in that batch's bucket (sorted by row).
 __global__ void k_prev_lookup(GroupParams q, const int32_t* __restrict__ rec, uint32_t ctx_off,
@@ -1055,16 +1381,16 @@ __global__ void k_prev_lookup(GroupParams q, const int32_t* __restrict__ rec, ui
         int32_t pv = -1;
         if (b > 0) {
             const uint32_t row = slot == 0 ? (uint32_t)rec[(uint64_t)s * q.R] : (uint32_t)rec[it] + ctx_off;
-            const uint32_t d = bucket_of(row);
+            const uint32_t d = bucket_of(row), hr = hrow(row);
             const uint64_t pbase = (uint64_t)(b - 1) * (uint64_t)q.batch * q.R;
             uint32_t lo = q.boff[(size_t)(b - 1) * (kBuckets + 1) + d], hi = q.boff[(size_t)(b - 1) * (kBuckets + 1) + d + 1];
             const uint32_t end = hi;
             while (lo < hi) {
                 const uint32_t mid = (lo + hi) >> 1;
-                if (q.sorted_row[pbase + mid] < row) lo = mid + 1;
+                if (q.sorted_row[pbase + mid] < hr) lo = mid + 1;
                 else hi = mid;
             }
-            if (lo < end && q.sorted_row[pbase + lo] == row) pv = (int32_t)q.seghead[pbase + lo];
+            if (lo < end && q.sorted_row[pbase + lo] == hr) pv = (int32_t)q.seghead[pbase + lo];
         }
         slot_prev[it] = pv;
     }
@@ -1319,6 +1645,12 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     const int64_t max_chunk = nb * a.batch;
     const int64_t max_items = max_chunk * R;
     const uint32_t parts = (uint32_t)((a.batch * R + kPartItems - 1) / kPartItems);
+    // batches of up to 8 parts of ~3.5K items are grouped by one cluster in
+    // distributed shared memory; larger ones are bucketed through global
+    // memory first
+    int log_parts = 0;
+    while (a.batch * R > ((int64_t)3584 << log_parts)) ++log_parts;
+    const bool direct = log_parts <= kGroupMaxLog;
     const bool persistent = a.mode == LINE_MODE_PERSISTENT;
     // shared segments (two or more entries) and long ones (more than kChunk)
     // per batch, at most
@@ -1376,11 +1708,12 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         return cudaErrorInvalidValue;
     }
     const size_t sort_smem = (size_t)kSortBucketsPerCta * 2 * kWarpSortCap * sizeof(uint64_t);
-    static bool sort_attr = false;
-    if (!sort_attr) {
-        cudaFuncSetAttribute(k_bucket_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem);
-        sort_attr = true;
-    }
+    const size_t group_smem = (size_t)kGroupCap * sizeof(uint64_t);
+    if ((e = cudaFuncSetAttribute(k_bucket_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sort_smem)) !=
+            cudaSuccess ||
+        (e = cudaFuncSetAttribute(k_group_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)group_smem)) !=
+            cudaSuccess)
+        return e;
     cudaStream_t ps = ws->prep;
     // the pre-pass reads the graph and alias tables made on the caller's stream
     if ((e = cudaEventRecord(ws->start, s)) != cudaSuccess) return e;
@@ -1481,10 +1814,27 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         if ((e = cudaMemsetAsync(cset.mcount.p, 0, sizeof(uint32_t) * (cb + 1), ps)) != cudaSuccess) return e;
         if ((e = cudaMemsetAsync(cset.lcount.p, 0, sizeof(uint32_t) * (cb + 1), ps)) != cudaSuccess) return e;
         if (persistent && (e = cudaMemsetAsync(cset.nseg.p, 0, sizeof(uint32_t) * (cb + 1), ps)) != cudaSuccess) return e;
-        k_bucket_count<<<dim3(parts, cb), kBucketThreads, 0, ps>>>(gq);
-        k_bucket_scatter<<<dim3(parts, cb), kBucketThreads, 0, ps>>>(gq);
-        k_bucket_sort<<<dim3(kBuckets / kSortBucketsPerCta, cb), kSortThreads, sort_smem, ps>>>(gq);
-        launches += 5;
+        if (direct) {
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(1u << log_parts, cb);
+            cfg.blockDim = dim3(kGroupThreads);
+            cfg.dynamicSmemBytes = group_smem;
+            cfg.stream = ps;
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 1u << log_parts;
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            cfg.attrs = attr;
+            cfg.numAttrs = 1;
+            if ((e = cudaLaunchKernelEx(&cfg, k_group_cluster, gq, log_parts)) != cudaSuccess) return e;
+            launches += 3;
+        } else {
+            k_bucket_count<<<dim3(parts, cb), kBucketThreads, 0, ps>>>(gq);
+            k_bucket_scatter<<<dim3(parts, cb), kBucketThreads, 0, ps>>>(gq);
+            k_bucket_sort<<<dim3(kBuckets / kSortBucketsPerCta, cb), kSortThreads, sort_smem, ps>>>(gq);
+            launches += 5;
+        }
         if (persistent) {
             const unsigned g = (unsigned)std::min<int64_t>((n_items + 255) / 256, 152 * 16);
             k_prev_lookup<<<g, 256, 0, ps>>>(gq, (const int32_t*)cset.rec.p, a.order == 2 ? (uint32_t)a.n_nodes : 0u,
