@@ -105,6 +105,8 @@ typedef struct {
     int chunk_batches;       /* batches per pre-pass chunk; 0: automatic */
     int warps_per_block;     /* 0: automatic */
     int timing;              /* 1: time the training kernels with CUDA events (line_get_stats) */
+    int graph;               /* 1: batched mode replays each full chunk's launches from a
+                                captured CUDA graph (same results); 0: direct launches */
 } line_train_opts;
 
 /* Per-kernel timing collected when opts.timing == 1 (reset by line_reset_stats). */

@@ -97,6 +97,7 @@ void line_train_opts_default(line_train_opts* o) {
     o->chunk_batches = 0;
     o->warps_per_block = 0;
     o->timing = 0;
+    o->graph = 1;
 }
 
 const char* line_status_string(line_status s) {
@@ -331,6 +332,7 @@ line_status line_train_steps(line_ctx* c, int order, int dim, int K, const line_
     a.chunk_batches = o.chunk_batches;
     a.warps_per_block = o.warps_per_block;
     a.timing = o.timing;
+    a.graph = o.graph;
     std::string err;
     if (o.timing) CK(cudaEventRecord(c->ev0, c->stream), "event");
     cudaError_t e = train_run(a, c->ws, c->status, &c->times, c->stream, &err);

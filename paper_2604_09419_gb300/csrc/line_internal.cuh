@@ -187,6 +187,7 @@ struct TrainArgs {
     int chunk_batches;
     int warps_per_block;
     int timing;
+    int graph;
 };
 
 struct TrainTimes {

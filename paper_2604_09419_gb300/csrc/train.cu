@@ -44,6 +44,7 @@
 //                         with bounded spins, only on the items it depends on.
 #include <algorithm>
 #include <cstdio>
+#include <cstring>
 #include <vector>
 
 #include <cooperative_groups.h>
@@ -177,6 +178,7 @@ struct DataParams {
     uint32_t lcap;
     float* slab;             // [chunk samples * (K+2)][D], by position
     uint64_t t_chunk;        // global index of the chunk's first sample
+    const uint64_t* t_chunk_dev;  // when set, the same read from device memory (graph replays)
     int64_t chunk_samples;
     int64_t batch;
     int n_batches;
@@ -603,8 +605,9 @@ __global__ void __launch_bounds__(kMaxWarps * 32) k_gather(DataParams p, int b) 
     const int64_t s_end = min(s_begin + p.batch, p.chunk_samples);
     const int64_t s_local = s_begin + ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * G::GPW + grp;
     float* stage = smem + (size_t)warp * (p.K + 1) * 32 * G::E;
-    sample_item<D, DT, false, PDL>(p, b, s_local, lig, lane, s_local < s_end, p.eta[b],
-                                   p.t_chunk + (uint64_t)s_begin, stage);
+    const uint64_t tc = p.t_chunk_dev ? *p.t_chunk_dev : p.t_chunk;
+    sample_item<D, DT, false, PDL>(p, b, s_local, lig, lane, s_local < s_end, p.eta[b], tc + (uint64_t)s_begin,
+                                   stage);
 }
 
 // Blocks [0, g_long) take the batch's long shared segments, one per CTA; the
@@ -621,7 +624,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(DataParams p, int b, in
     const uint32_t n_m = p.mcount[b];
     const uint32_t n_long = p.lcount[b];
     const uint4* md = p.mdesc + (size_t)b * p.mcap;
-    const uint64_t t0 = p.t_chunk + (uint64_t)b * (uint64_t)p.batch;
+    const uint64_t t0 = (p.t_chunk_dev ? *p.t_chunk_dev : p.t_chunk) + (uint64_t)b * (uint64_t)p.batch;
     const float eta = p.eta[b];
     if ((int)blockIdx.x < g_long) {
         // descriptors come from the pre-pass: read before the wait
@@ -740,6 +743,7 @@ struct PrepassParams {
     int K, order;
     int32_t* rec;
     uint64_t* items;
+    uint64_t* t_out;  // receives t_chunk (read by graph replays of the data phase)
 };
 
 __device__ __forceinline__ uint64_t make_item(uint32_t rowid, uint32_t s_local, uint32_t slot) {
@@ -747,6 +751,7 @@ __device__ __forceinline__ uint64_t make_item(uint32_t rowid, uint32_t s_local, 
 }
 
 __global__ void k_chunk_draws(PrepassParams p) {
+    if (blockIdx.x == 0 && threadIdx.x == 0 && p.t_out) *p.t_out = p.t_chunk;
     const uint32_t C1 = (uint32_t)p.K + 1u, R = (uint32_t)p.K + 2u;
     const uint32_t total = (uint32_t)p.chunk_samples * C1;
     for (uint32_t q = blockIdx.x * blockDim.x + threadIdx.x; q < total; q += gridDim.x * blockDim.x) {
@@ -1449,7 +1454,11 @@ struct Buf {
 // pre-pass of chunk c+1 (on its own low-priority stream) fills one while the
 // data phase of chunk c reads the other.
 struct ChunkSet {
-    Buf rec, slot_info, mdesc, mcount, ldesc, lcount, eta, slot_prev, arrive, item_base, nseg;
+    Buf rec, slot_info, mdesc, mcount, ldesc, lcount, eta, slot_prev, arrive, item_base, nseg, tchunk;
+    // captured data phase of a full chunk of this set, and what it was captured for
+    cudaGraphExec_t graph = nullptr;
+    DataParams graph_key{};
+    int graph_wpb = -1;
     cudaEvent_t prep_done = nullptr;  // pre-pass of the set's current chunk finished
     cudaEvent_t data_done = nullptr;  // data phase of the set's previous chunk finished
     bool data_pending = false;
@@ -1459,6 +1468,8 @@ struct TrainWorkspace {
     Buf items0, items1, gcnt, boff, counters, slab, sorted_row, seghead, seg_done, batch_applied;
     ChunkSet set[2];
     cudaStream_t prep = nullptr;    // pre-pass stream
+    cudaStream_t cap = nullptr;     // stream the data-phase graphs are captured on
+    bool graph_failed = false;      // a capture failed: direct launches from then on
     cudaEvent_t start = nullptr;    // caller-stream work before the call
     cudaEvent_t prep_end = nullptr; // last pre-pass of the call
     std::vector<cudaEvent_t> events;  // timing events
@@ -1478,6 +1489,7 @@ struct TrainWorkspace {
         int lo = 0, hi = 0;
         cudaError_t e = cudaDeviceGetStreamPriorityRange(&lo, &hi);
         if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&prep, cudaStreamNonBlocking, lo);
+        if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
         for (auto& cs : set) {
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&cs.prep_done, cudaEventDisableTiming);
             if (e == cudaSuccess) e = cudaEventCreateWithFlags(&cs.data_done, cudaEventDisableTiming);
@@ -1492,9 +1504,11 @@ struct TrainWorkspace {
             cudaStreamSynchronize(prep);
             cudaStreamDestroy(prep);
         }
+        if (cap) cudaStreamDestroy(cap);
         for (auto& cs : set) {
             if (cs.prep_done) cudaEventDestroy(cs.prep_done);
             if (cs.data_done) cudaEventDestroy(cs.data_done);
+            if (cs.graph) cudaGraphExecDestroy(cs.graph);
         }
         if (start) cudaEventDestroy(start);
         if (prep_end) cudaEventDestroy(prep_end);
@@ -1680,7 +1694,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         if (!ensure(cs.rec, sizeof(int32_t) * max_items) || !ensure(cs.eta, sizeof(float) * (nb + 1)) ||
             !ensure(cs.slot_info, sizeof(uint2) * max_items) || !ensure(cs.mdesc, sizeof(uint4) * (size_t)nb * mcap) ||
             !ensure(cs.mcount, sizeof(uint32_t) * (nb + 1)) || !ensure(cs.ldesc, sizeof(uint4) * (size_t)nb * lcap) ||
-            !ensure(cs.lcount, sizeof(uint32_t) * (nb + 1)))
+            !ensure(cs.lcount, sizeof(uint32_t) * (nb + 1)) || !ensure(cs.tchunk, 256))
             return e;
         if (persistent && (!ensure(cs.slot_prev, sizeof(int32_t) * max_items) ||
                            !ensure(cs.arrive, sizeof(uint32_t) * max_items) ||
@@ -1796,6 +1810,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         pp.t_chunk = t;
         pp.chunk_samples = cs;
         pp.rec = (int32_t*)cset.rec.p;
+        pp.t_out = (uint64_t*)cset.tchunk.p;
         {
             const int64_t work = cs * (a.K + 1);
             const unsigned g = (unsigned)std::min<int64_t>((work + 255) / 256, 152 * 64);
@@ -1875,7 +1890,44 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
             if ((e = cudaMemsetAsync(ws->batch_applied.p, 0, sizeof(uint32_t) * (cb + 1), s)) != cudaSuccess) return e;
             dp.gen = ++ws->gen;
         }
-        if ((e = data(dp, a.warps_per_block, s)) != cudaSuccess) return e;
+        if (!persistent && a.graph && !ws->graph_failed && cs == max_chunk && c > 0) {
+            // a full chunk: replay this set's captured data phase (the chunk's
+            // first sample index comes from the set's device copy)
+            dp.t_chunk_dev = (const uint64_t*)cset.tchunk.p;
+            DataParams key = dp;
+            key.t_chunk = 0;
+            if (!cset.graph || cset.graph_wpb != a.warps_per_block ||
+                memcmp(&key, &cset.graph_key, sizeof key) != 0) {
+                if (cset.graph) cudaGraphExecDestroy(cset.graph);
+                cset.graph = nullptr;
+                cudaGraph_t g = nullptr;
+                cudaError_t ce = cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal);
+                if (ce == cudaSuccess) {
+                    const cudaError_t le = data(dp, a.warps_per_block, ws->cap);
+                    ce = cudaStreamEndCapture(ws->cap, &g);
+                    if (ce == cudaSuccess) ce = le;
+                }
+                if (ce == cudaSuccess) ce = cudaGraphInstantiate(&cset.graph, g, 0);
+                if (g) cudaGraphDestroy(g);
+                if (ce != cudaSuccess) {
+                    cudaGetLastError();
+                    cset.graph = nullptr;
+                    ws->graph_failed = true;
+                } else {
+                    cset.graph_key = key;
+                    cset.graph_wpb = a.warps_per_block;
+                }
+            }
+            if (cset.graph) {
+                if ((e = cudaGraphLaunch(cset.graph, s)) != cudaSuccess) return e;
+            } else {
+                dp.t_chunk_dev = nullptr;
+                if ((e = data(dp, a.warps_per_block, s)) != cudaSuccess) return e;
+            }
+        } else {
+            dp.t_chunk_dev = nullptr;
+            if ((e = data(dp, a.warps_per_block, s)) != cudaSuccess) return e;
+        }
         if (a.timing) {
             if ((e = ws->event(n_ev + 3, &ev)) != cudaSuccess) return e;
             cudaEventRecord(ev, s);

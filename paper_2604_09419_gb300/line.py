@@ -39,7 +39,8 @@ class LR(ctypes.Structure):
 class TrainOpts(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int64), ("lambda_", ctypes.c_double), ("alpha_neg", ctypes.c_double),
                 ("sample_offset", ctypes.c_uint64), ("mode", ctypes.c_int), ("spin_limit", ctypes.c_int64),
-                ("chunk_batches", ctypes.c_int), ("warps_per_block", ctypes.c_int), ("timing", ctypes.c_int)]
+                ("chunk_batches", ctypes.c_int), ("warps_per_block", ctypes.c_int), ("timing", ctypes.c_int),
+                ("graph", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -132,6 +132,25 @@ def test_determinism_and_schedules(ctx):
         assert np.array_equal(a[0], c[0]) and np.array_equal(a[1], c[1]), wpb
 
 
+def test_graph_replay_matches_direct_launches_and_oracle(ctx):
+    """Full chunks replayed from captured CUDA graphs (several chunks per
+    set, a partial last chunk) give the same bits as direct launches, and the
+    oracle's tables within the FP32 bound."""
+    g = G.graph("tiny")
+    G.upload(ctx, g)
+    n, B = 100_000, 256
+    direct = _run(ctx, g, 2, 16, 5, n, B, chunk_batches=16, graph=0)
+    for cb in (16, 5):
+        replay = _run(ctx, g, 2, 16, 5, n, B, chunk_batches=cb, graph=1)
+        assert np.array_equal(direct[0], replay[0]) and np.array_equal(direct[1], replay[1]), cb
+    U, C = G.oracle_run("tiny", 2, 16, 5, n, 5, B, 1)
+    assert np.abs(replay[0] - U).max() <= TOL and np.abs(replay[1] - C).max() <= TOL
+    # first order and BF16 tables through the same path
+    d1 = _run(ctx, g, 1, 32, 5, 60_000, B, chunk_batches=8, graph=0)
+    r1 = _run(ctx, g, 1, 32, 5, 60_000, B, chunk_batches=8, graph=1)
+    assert np.array_equal(d1[0], r1[0])
+
+
 def test_resume_split_is_bitwise(ctx):
     from paper_2604_09419_gb300 import line as L
     g = G.graph("tiny")
