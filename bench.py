@@ -7,6 +7,14 @@ tables, deterministic minibatch B=4096, lr 0.025 with linear decay over
 20 x |E| samples per order.  One step = |E| = 16 * 2^20 samples of each
 order (one "epoch" of each), so 20 steps are the full run.
 
+Other workloads (``--workload``; not the default line):
+
+* ``dchung22`` - weighted directed Chung-Lu graph, 4,194,304 nodes, 2^26 arc
+  draws (out-weights power law 2.2, lognormal(0,1) weights); order 2, d=128,
+  K=5: the FP32 path at B=4096 against BF16 tables with stochastic rounding
+  in the launch configuration the autotuner picks (batch 4K-64K, schedule,
+  graph replay), throughput and loss at equal samples.
+
 Output: one JSON line (rank 0).  `value` is device-timed throughput with the
 graph and tables resident in HBM; `e2e` is the same metric through the C ABI
 from host buffers (graph upload + alias build + training + read-back of the
@@ -50,6 +58,7 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-samples", type=int, default=1 << 20)
+    p.add_argument("--workload", default="rmat20", choices=["rmat20", "dchung22"])
     return p.parse_args()
 
 
@@ -178,10 +187,80 @@ def samples_per_step(args):
     return args.samples_per_step or 16 * (1 << args.scale)
 
 
+def run_dchung22(args):
+    """Directed Chung-Lu, order 2: FP32 at B=4096 vs autotuned BF16."""
+    import torch
+
+    from paper_2604_09419_gb300 import inputs as I
+    from paper_2604_09419_gb300 import line as L
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    g = I.chung_lu_directed()
+    stream = torch.cuda.current_stream()
+    ctx = L.Context(local, stream.cuda_stream)
+    ctx.build_alias(g.n_nodes, torch.from_numpy(g.src).cuda(), torch.from_numpy(g.dst).cuda(),
+                    torch.from_numpy(g.w).cuda())
+    E = g.n_arcs
+    total = 10 * E
+    S = args.samples_per_step or E
+    peak, peak_kind = peaks()
+    res = {}
+    for name, dtype in (("fp32", L.DTYPE_F32), ("bf16", L.DTYPE_BF16)):
+        ctx.init_embeddings(2, DIM, dtype, seed=2)
+        o = L.train_opts_default()
+        o.batch = B
+        rate_tuned = None
+        if dtype == L.DTYPE_BF16:
+            o, rate_tuned = ctx.autotune(2, DIM, K, batches=[4096, 8192, 16384, 32768, 65536], try_persistent=True,
+                                         total=total, opts=o)
+        o.timing = 1
+        for i in range(args.warmup):
+            o.sample_offset = i * S
+            ctx.train_steps(2, DIM, K, S, 7, total=total, opts=o)
+        ctx.reset_stats()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            ev0.record(stream)
+            for i in range(args.steps):
+                o.sample_offset = (args.warmup + i) * S
+                ctx.train_steps(2, DIM, K, S, 7, total=total, opts=o)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        st = ctx.stats()
+        row = DIM * (4 if dtype == L.DTYPE_F32 else 2)
+        rate = S * args.steps / (ms / 1e3)
+        upd = st.update_samples * 14 * row / (st.update_ms / 1e3) / 1e9 if st.update_ms > 0 else None
+        res[name] = {"value": rate, "ms_per_step": ms / args.steps, "batch": int(o.batch),
+                     "mode": "batched" if o.mode == L.MODE_BATCHED else "persistent",
+                     "warps_per_block": int(o.warps_per_block), "chunk_batches": int(o.chunk_batches),
+                     "autotuned_rate": rate_tuned,
+                     "roofline": {"bound": "hbm", "achieved": upd, "peak": peak, "unit": "GB/s",
+                                  "frac": upd / peak if upd else None, "alg_bytes_per_sample": 14 * row,
+                                  "peak_kind": peak_kind,
+                                  "path_frac": rate * (14 * row + 8 + 8 + 8 * K) / 1e9 / peak},
+                     "loss_after": ctx.eval_loss(2, K, 99, 1 << 20),
+                     "samples_trained": S * (args.warmup + args.steps), "clocks": clk.summary()}
+    line = {"metric": METRIC, "value": res["bf16"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "dchung22_line_order2_d128_K5_bf16_vs_fp32",
+                       "graph": "directed Chung-Lu, 4,194,304 nodes, 2^26 arc draws, out-weight power law 2.2, "
+                                "lognormal(0,1) arc weights", "n_nodes": g.n_nodes, "n_arcs": E,
+                       "samples_per_step": S, "lr": "0.025 linear decay over 10*|E|"},
+            "fp32": res["fp32"], "bf16": res["bf16"],
+            "loss_rel_diff": (res["bf16"]["loss_after"] - res["fp32"]["loss_after"]) / res["fp32"]["loss_after"]}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "dchung22":
+        run_dchung22(args)
         return
     import numpy as np
     import torch

@@ -166,7 +166,10 @@ LINE_API line_status line_sample_debug(line_ctx* ctx, int K, uint64_t seed, uint
  * draw at counter (i_lo, i_hi, k/4, 1): uniform on [-0.5/dim, 0.5/dim);
  * C = 0.  dim in {16, 32, 64, 128, 256}; dtype LINE_DTYPE_F32 or
  * LINE_DTYPE_BF16 (storage; arithmetic is FP32, BF16 write-back uses
- * stochastic rounding). */
+ * stochastic rounding: 16 random bits added below the BF16 mantissa, then
+ * truncation; the bits of values 4k..4k+3 of a row written by the batch
+ * starting at sample t0 are the SplitMix64 output function of a key of
+ * (seed, table, row, t0, k)). */
 LINE_API line_status line_init_embeddings(line_ctx* ctx, int order, int dim, int dtype, uint64_t seed);
 
 /* Train n_samples samples (global indices sample_offset .. +n_samples-1) of
@@ -179,6 +182,29 @@ LINE_API line_status line_init_embeddings(line_ctx* ctx, int order, int dim, int
  * opts.spin_limit), LINE_ERR_CUDA. */
 LINE_API line_status line_train_steps(line_ctx* ctx, int order, int dim, int K, const line_lr* lr,
                              uint64_t n_samples, uint64_t seed, const line_train_opts* opts);
+
+/* Search space of line_autotune. */
+typedef struct {
+    const int64_t* batches;  /* candidate batch sizes (a host array), or NULL: keep io->batch */
+    int n_batches;           /* 0..16 */
+    uint64_t trial_samples;  /* samples per timed trial; 0: four pre-pass chunks */
+    int try_persistent;      /* 1: also time the persistent schedule */
+} line_tune_opts;
+
+/* Autotuner of the launch configuration (not in the paper, whose CPU code
+ * has no such knobs): for every candidate - gather warps per block (1, 2,
+ * 4), batches per pre-pass chunk (about 2^18 samples, and half that), the
+ * batched schedule with graph replay (and the persistent one if asked), each
+ * listed batch size - it runs an untimed and a timed training run of
+ * trial_samples on scratch copies of the order's tables, and writes the
+ * fastest into *io (batch, warps_per_block, chunk_batches, mode, graph; the
+ * other fields of *io are used as given).  The tables, the statistics and
+ * the learning-rate state of the caller are unchanged.  Changing the batch
+ * size changes the results (minibatch semantics): list batch sizes only when
+ * that is acceptable.  *best_rate (if not NULL): the winner's samples/s.
+ * Errors: as line_train_steps; LINE_ERR_OOM if the scratch tables do not fit. */
+LINE_API line_status line_autotune(line_ctx* ctx, int order, int dim, int K, const line_lr* lr,
+                                   const line_tune_opts* topts, line_train_opts* io, double* best_rate);
 
 /* Copy a whole table (n_nodes x dim, row-major) into `dst` (a buffer) as
  * dst_dtype (F32, or BF16 when the table is BF16). */

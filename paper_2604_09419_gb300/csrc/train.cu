@@ -31,7 +31,8 @@
 //     apply   per shared segment: the entries summed in a fixed chunked
 //             order, X <- X_b - cnt eta_b lambda X_b + sum, cnt the number of
 //             pair occurrences of the row (the batch-summed update of Eq. 4).
-//   BF16 tables are written back with stochastic rounding.
+//   BF16 tables are written back with stochastic rounding (random bits from
+//   a counter hash of seed, table, row, batch and column group).
 //
 // The order of every floating-point sum is fixed, so results are bitwise
 // reproducible, and a singleton row gets exactly the value the apply step
@@ -58,12 +59,17 @@ namespace cg = cooperative_groups;
 
 // ---------------------------------------------------------------------------
 // Row geometry: a row of D values is handled by L lanes, E values per lane,
-// moved as 16-byte vectors (4 FP32 or 8 BF16 values).
+// moved as vectors of 4 values (16 bytes of FP32, 8 bytes of BF16).
 // ---------------------------------------------------------------------------
+// (host and device share these two: the work-item map of the persistent
+// schedule is laid out on the host)
+constexpr int geom_vec(int /*dtype*/) { return 4; }
+constexpr int geom_lanes(int dim, int dtype) { return dim / geom_vec(dtype) < 32 ? dim / geom_vec(dtype) : 32; }
+
 template <int D, int DT>
 struct Geom {
-    static constexpr int VEC = DT == LINE_DTYPE_F32 ? 4 : 8;
-    static constexpr int L = (D / VEC) < 32 ? (D / VEC) : 32;
+    static constexpr int VEC = geom_vec(DT);
+    static constexpr int L = geom_lanes(D, DT);
     static constexpr int E = D / L;
     static constexpr int NV = E / VEC;
     static constexpr int GPW = 32 / L;  // lane groups per warp
@@ -84,23 +90,33 @@ __device__ __forceinline__ void load_row(const void* table, int64_t row, int lig
             v[4 * q + 3] = a.w;
         }
     } else {
-        const uint4* p = reinterpret_cast<const uint4*>(reinterpret_cast<const __nv_bfloat16*>(table) + row * D + lig * G::E);
+        const uint2* p = reinterpret_cast<const uint2*>(reinterpret_cast<const __nv_bfloat16*>(table) + row * D + lig * G::E);
 #pragma unroll
         for (int q = 0; q < G::NV; ++q) {
-            const uint4 a = ld_cg(p + q);
-            const uint32_t w[4] = {a.x, a.y, a.z, a.w};
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                v[8 * q + 2 * h] = __uint_as_float(w[h] << 16);
-                v[8 * q + 2 * h + 1] = __uint_as_float(w[h] & 0xFFFF0000u);
-            }
+            const uint2 a = __ldcg(p + q);
+            v[4 * q] = __uint_as_float(a.x << 16);
+            v[4 * q + 1] = __uint_as_float(a.x & 0xFFFF0000u);
+            v[4 * q + 2] = __uint_as_float(a.y << 16);
+            v[4 * q + 3] = __uint_as_float(a.y & 0xFFFF0000u);
         }
     }
 }
 
-// Store a row part; BF16 uses stochastic rounding with bits from the draw at
-// counter (row, t0_lo, t0_hi, 2 | table << 4 | (k / 8) << 8), k the first
-// column of the 8-value vector (domain 2, one draw per 8 values).
+// 64 random bits for the stochastic rounding of the 4 values at columns
+// 4 k4 .. 4 k4 + 3 of `row` of table `table_id`, written by the batch that
+// starts at sample t0: the SplitMix64 output function (Steele, Lea, Flood,
+// OOPSLA 2014) of a key built from the seed, the batch, the row and k4.
+__device__ __forceinline__ uint64_t sr_bits(uint64_t seed, uint32_t table_id, uint64_t row, uint64_t t0, uint32_t k4) {
+    uint64_t z = seed ^ (t0 * 0x9E3779B97F4A7C15ull) ^
+                 (((row << 16) | ((uint64_t)table_id << 15) | (uint64_t)k4) * 0xD1B54A32D192ED03ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// Store a row part; BF16 rounds stochastically: value i of a 4-value vector
+// adds bits [16 i, 16 i + 16) of sr_bits(...) below the BF16 mantissa, then
+// truncates.
 template <int D, int DT>
 __device__ __forceinline__ void store_row(void* table, int64_t row, int lig, const float (&v)[Geom<D, DT>::E],
                                           uint64_t seed, uint64_t t0, uint32_t table_id) {
@@ -110,22 +126,15 @@ __device__ __forceinline__ void store_row(void* table, int64_t row, int lig, con
 #pragma unroll
         for (int q = 0; q < G::NV; ++q) st_cg(p + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
     } else {
-        uint4* p = reinterpret_cast<uint4*>(reinterpret_cast<__nv_bfloat16*>(table) + row * D + lig * G::E);
+        uint2* p = reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(table) + row * D + lig * G::E);
 #pragma unroll
         for (int q = 0; q < G::NV; ++q) {
-            const uint32_t k8 = (uint32_t)((lig * G::E + 8 * q) >> 3);
-            const uint4 r = philox4x32_10(make_uint4((uint32_t)row, (uint32_t)t0, (uint32_t)(t0 >> 32),
-                                                     2u | (table_id << 4) | (k8 << 8)),
-                                          make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
-            const uint32_t rw[4] = {r.x, r.y, r.z, r.w};
-            uint32_t out[4];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const uint32_t lo = bf16_sr(v[8 * q + 2 * h], rw[h]);
-                const uint32_t hi = bf16_sr(v[8 * q + 2 * h + 1], rw[h] >> 16);
-                out[h] = lo | (hi << 16);
-            }
-            st_cg(p + q, make_uint4(out[0], out[1], out[2], out[3]));
+            const uint32_t k4 = (uint32_t)((lig * G::E + 4 * q) >> 2);
+            const uint64_t r = sr_bits(seed, table_id, (uint64_t)row, t0, k4);
+            const uint32_t r0 = (uint32_t)r, r1 = (uint32_t)(r >> 32);
+            const uint32_t x = (uint32_t)bf16_sr(v[4 * q], r0) | ((uint32_t)bf16_sr(v[4 * q + 1], r0 >> 16) << 16);
+            const uint32_t y = (uint32_t)bf16_sr(v[4 * q + 2], r1) | ((uint32_t)bf16_sr(v[4 * q + 3], r1 >> 16) << 16);
+            __stcg(p + q, make_uint2(x, y));
         }
     }
 }
@@ -590,11 +599,15 @@ __device__ __forceinline__ void long_segment_cta(const DataParams& p, uint4 d, f
 // ---------------------------------------------------------------------------
 // Batched schedule: one launch per phase per batch.
 // ---------------------------------------------------------------------------
-constexpr int kMaxWarps = 16;
 constexpr size_t kMaxSmem = 200 * 1024;
 
+// Gathers run in blocks of at most 4 warps at 7 blocks per SM (at most 73
+// registers), so that a 4,096-sample batch (4,096 warps at d = 128) is
+// resident in one wave.
+constexpr int kGatherWarps = 4;
+
 template <int D, int DT, bool PDL>
-__global__ void __launch_bounds__(kMaxWarps * 32) k_gather(DataParams p, int b) {
+__global__ void __launch_bounds__(kGatherWarps * 32, 7) k_gather(DataParams p, int b) {
     using G = Geom<D, DT>;
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
@@ -1558,7 +1571,7 @@ static cudaError_t launch_data_batched(const DataParams& p, int warps_per_block,
     using G = Geom<D, DT>;
     size_t smem = 0;
     // 4 warps per block: at ~70 registers a 4096-sample batch is one wave
-    const int wpb = gather_warps<D, DT>(p, warps_per_block, kMaxWarps, &smem, 4);
+    const int wpb = gather_warps<D, DT>(p, warps_per_block, kGatherWarps, &smem, kGatherWarps);
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_gather<D, DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
@@ -1631,11 +1644,7 @@ static LaunchFn pick_launcher(int dim, int dtype, bool persistent) {
     return nullptr;
 }
 
-static int groups_per_warp(int dim, int dtype) {
-    const int vec = dtype == LINE_DTYPE_F32 ? 4 : 8;
-    const int L = std::min(32, dim / vec);
-    return 32 / L;
-}
+static int groups_per_warp(int dim, int dtype) { return 32 / geom_lanes(dim, dtype); }
 
 cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, TrainTimes* times, cudaStream_t s,
                       std::string* err) {

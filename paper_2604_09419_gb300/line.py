@@ -43,6 +43,11 @@ class TrainOpts(ctypes.Structure):
                 ("graph", ctypes.c_int)]
 
 
+class TuneOpts(ctypes.Structure):
+    _fields_ = [("batches", ctypes.c_void_p), ("n_batches", ctypes.c_int), ("trial_samples", ctypes.c_uint64),
+                ("try_persistent", ctypes.c_int)]
+
+
 class Stats(ctypes.Structure):
     _fields_ = [("update_launches", ctypes.c_int64), ("update_ms", ctypes.c_double),
                 ("update_samples", ctypes.c_uint64), ("prepass_launches", ctypes.c_int64),
@@ -80,6 +85,8 @@ def _load():
         "line_mlp_grad": (i32, [vp, vp, i64, vp, ctypes.POINTER(dbl)]),
         "line_mlp_train": (i32, [vp, vp, i64, i64, i64, dbl, u64, u64, vp]),
         "line_mlp_predict": (i32, [vp, vp, i64, vp]),
+        "line_autotune": (i32, [vp, i32, i32, i32, ctypes.POINTER(LR), ctypes.POINTER(TuneOpts),
+                                ctypes.POINTER(TrainOpts), ctypes.POINTER(dbl)]),
         "line_get_stats": (i32, [vp, ctypes.POINTER(Stats)]),
         "line_reset_stats": (i32, [vp]),
         "line_synchronize": (i32, [vp]),
@@ -98,7 +105,7 @@ EXPORTED = ("line_train_opts_default", "line_status_string", "line_create", "lin
             "line_init_embeddings", "line_train_steps", "line_get_embeddings", "line_set_embeddings",
             "line_eval_loss", "line_eval_loss_noalloc", "line_eval_auc", "line_mlp_create", "line_mlp_features",
             "line_mlp_get_features", "line_mlp_get_params", "line_mlp_set_params", "line_mlp_grad", "line_mlp_train",
-            "line_mlp_predict", "line_get_stats", "line_reset_stats", "line_synchronize", "line_debug_wait_timeout")
+            "line_mlp_predict", "line_autotune", "line_get_stats", "line_reset_stats", "line_synchronize", "line_debug_wait_timeout")
 
 
 class LineError(RuntimeError):
@@ -208,6 +215,20 @@ class Context:
                                    ptr(neg_dst), int(neg_src.shape[0]), ptr(scores), counts.ctypes.data,
                                    ctypes.byref(out)))
         return out.value, (int(counts[0]), int(counts[1]))
+
+    def autotune(self, order, dim, K, *, batches=None, trial_samples=0, try_persistent=False, lr0=0.025,
+                 schedule=1, floor_frac=1e-4, total=0, opts: TrainOpts | None = None):
+        """Fastest launch configuration on scratch copies of the tables;
+        returns (TrainOpts, samples/s)."""
+        lr = LR(lr0, schedule, floor_frac, total)
+        o = opts if opts is not None else train_opts_default()
+        arr = None if not batches else np.asarray(batches, np.int64)
+        t = TuneOpts(None if arr is None else arr.ctypes.data, 0 if arr is None else len(arr), trial_samples,
+                     1 if try_persistent else 0)
+        rate = ctypes.c_double()
+        self._ck(lib.line_autotune(self.h, order, dim, K, ctypes.byref(lr), ctypes.byref(t), ctypes.byref(o),
+                                   ctypes.byref(rate)))
+        return o, rate.value
 
     # ---- warm-start MLP
     def mlp_create(self, order, hidden=256, act_dtype=DTYPE_BF16, seed=0):

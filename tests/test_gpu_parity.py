@@ -151,6 +151,25 @@ def test_graph_replay_matches_direct_launches_and_oracle(ctx):
     assert np.array_equal(d1[0], r1[0])
 
 
+def test_autotune_keeps_tables_and_returns_a_valid_configuration(ctx):
+    from paper_2604_09419_gb300 import line as L
+    g = G.graph("rmat14")
+    G.upload(ctx, g)
+    ctx.init_embeddings(2, 64, L.DTYPE_F32, seed=1)
+    U0, C0 = G.tables(ctx, g, 2, 64)
+    ctx.reset_stats()
+    o, rate = ctx.autotune(2, 64, 5, batches=[1024, 4096], trial_samples=65_536, try_persistent=True)
+    assert rate > 0 and o.batch in (1024, 4096) and o.chunk_batches >= 1 and o.graph == 1
+    assert o.mode in (L.MODE_BATCHED, L.MODE_PERSISTENT)
+    U1, C1 = G.tables(ctx, g, 2, 64)
+    assert np.array_equal(U0, U1) and np.array_equal(C0, C1)
+    assert ctx.stats().total_samples == 0
+    # the tuned configuration trains to the same bits as the defaults at its batch size
+    a = _run(ctx, g, 2, 64, 5, 50_000, o.batch)
+    b = _run(ctx, g, 2, 64, 5, 50_000, o.batch, opts=o)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+
+
 def test_resume_split_is_bitwise(ctx):
     from paper_2604_09419_gb300 import line as L
     g = G.graph("tiny")
