@@ -14,6 +14,14 @@ Other workloads (``--workload``; not the default line):
   K=5: the FP32 path at B=4096 against BF16 tables with stochastic rounding
   in the launch configuration the autotuner picks (batch 4K-64K, schedule,
   graph replay), throughput and loss at equal samples.
+* ``warm22`` - R-MAT scale 22 with 10% of the edges (AUC positives) and 10% of
+  the nodes held out.  Order-2 LINE (FP32) trains on the kept nodes; then the
+  held-out nodes join and two arms refine on the graph without the held-out
+  edges: plain FP32 LINE from random rows for the new nodes, and BF16 tables
+  with the new rows warm-started by the MLP (trained on the kept nodes'
+  rows).  At every checkpoint: link-prediction AUC (inner products of U rows;
+  held-out edges against as many non-edges) and device time; reports when the
+  BF16 + warm-start arm reaches the FP32 arm's final AUC within 0.005.
 
 Output: one JSON line (rank 0).  `value` is device-timed throughput with the
 graph and tables resident in HBM; `e2e` is the same metric through the C ABI
@@ -58,7 +66,8 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-samples", type=int, default=1 << 20)
-    p.add_argument("--workload", default="rmat20", choices=["rmat20", "dchung22"])
+    p.add_argument("--workload", default="rmat20", choices=["rmat20", "dchung22", "warm22"])
+    p.add_argument("--checkpoints", type=int, default=10, help="warm22: refinement epochs (checkpoints)")
     return p.parse_args()
 
 
@@ -254,6 +263,130 @@ def run_dchung22(args):
     ctx.close()
 
 
+def run_warm22(args):
+    """Warm start of held-out nodes on R-MAT 22: BF16 + MLP vs plain FP32."""
+    import numpy as np
+    import torch
+
+    from paper_2604_09419_gb300 import inputs as I
+    from paper_2604_09419_gb300 import line as L
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    t_gen = time.perf_counter()
+    g = I.rmat(22, seed=0)
+    tr, hs, hd = I.split_edges(g, 0.1, seed=4)
+    ans, ad = I.non_edges(g, len(hs), seed=7)
+    held, kept = I.hold_out_nodes(tr, 0.1, seed=5)
+    inc = held[hs] | held[hd]
+    ps, pd = hs[inc], hd[inc]
+    cs, cd = I.non_edges(g, 8 * len(ps) + 1000, seed=6)
+    m = held[cs] | held[cd]
+    ns, nd = cs[m][:len(ps)], cd[m][:len(ps)]
+    t_gen = time.perf_counter() - t_gen
+    ctx = L.Context(local, stream.cuda_stream)
+
+    def upload(h):
+        ctx.build_alias(h.n_nodes, torch.from_numpy(h.src).cuda(), torch.from_numpy(h.dst).cuda(),
+                        torch.from_numpy(h.w).cuda())
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / 1e3
+
+    # phase 0 (all arms): FP32 order-2 LINE on the kept nodes
+    upload(kept)
+    ctx.init_embeddings(2, DIM, L.DTYPE_F32, seed=2)
+    n0 = 10 * kept.n_arcs
+    t0 = timed(lambda: ctx.train_steps(2, DIM, K, n0, 3, batch=B, total=n0))
+    upload(tr)  # the held-out nodes join (same node count: tables kept)
+    U0 = torch.empty((g.n_nodes, DIM), dtype=torch.float32, device="cuda")
+    C0 = torch.empty_like(U0)
+    ctx.get_embeddings(2, L.WHICH_U, U0)
+    ctx.get_embeddings(2, L.WHICH_C, C0)
+    E = tr.n_arcs
+    # refinement checkpoints, in epochs of the training graph (|E| samples)
+    marks = [0.05, 0.1, 0.2, 0.35, 0.5, 0.75, 1, 1.5, 2, 3, 5, args.checkpoints]
+    marks = [x for x in marks if x <= args.checkpoints]
+    total = int(marks[-1] * E) // B * B
+
+    def evaluate():
+        return {"auc_all": ctx.eval_auc(2, hs, hd, ans, ad)[0], "auc_new_nodes": ctx.eval_auc(2, ps, pd, ns, nd)[0],
+                "loss": ctx.eval_loss(2, K, 99, 1 << 20)}
+
+    def refine(arm):
+        curve, t_acc, done = [], arm.get("setup_s", 0.0), 0
+        curve.append({"samples": 0, "time_s": t_acc, **evaluate()})
+        o = L.train_opts_default()
+        o.batch = B
+        for x in marks:
+            upto = int(x * E) // B * B
+            o.sample_offset = done
+            n = upto - done
+            t_acc += timed(lambda: ctx.train_steps(2, DIM, K, n, 11, total=total, opts=o))
+            done = upto
+            curve.append({"samples": done, "time_s": t_acc, **evaluate()})
+        arm["curve"] = curve
+        return arm
+
+    def start_tables(dtype):
+        ctx.init_embeddings(2, DIM, dtype, seed=0)
+        ctx.set_embeddings(2, L.WHICH_U, U0, L.DTYPE_F32)
+        ctx.set_embeddings(2, L.WHICH_C, C0, L.DTYPE_F32)
+
+    arms = {}
+    # plain FP32 and plain BF16: random rows for the new nodes
+    start_tables(L.DTYPE_F32)
+    arms["fp32"] = refine({"name": "fp32, random rows for new nodes"})
+    t_conv = timed(lambda: start_tables(L.DTYPE_BF16))
+    arms["bf16"] = refine({"name": "bf16, random rows for new nodes", "setup_s": t_conv})
+    # BF16 + MLP warm start of the new rows (setup timed phase by phase)
+    rows = np.flatnonzero(held).astype(np.int32)
+    train_nodes = np.flatnonzero(~held & (np.bincount(kept.src, minlength=g.n_nodes) > 0)).astype(np.int32)
+    mlp_batch = 16384
+    mlp_steps = max(64, len(train_nodes) // mlp_batch)  # about one epoch of the kept nodes
+    known = (~held).astype(np.uint8)
+    setup = {"convert_s": timed(lambda: start_tables(L.DTYPE_BF16))}
+    setup["mlp_create_s"] = timed(lambda: ctx.mlp_create(2, hidden=256, act_dtype=L.DTYPE_BF16, seed=9))
+    setup["features_s"] = timed(lambda: ctx.mlp_features(known))
+    box = {}
+    setup["mlp_train_s"] = timed(lambda: box.update(
+        losses=ctx.mlp_train(train_nodes, steps=mlp_steps, batch=mlp_batch, lr=1e-3, seed=10)))
+    setup["predict_s"] = timed(lambda: ctx.mlp_predict(rows))
+    arms["bf16_warm"] = refine({"name": "bf16 + MLP warm start of the new rows", "setup_s": sum(setup.values()),
+                                "setup": setup, "mlp_steps": mlp_steps, "mlp_batch": mlp_batch,
+                                "mlp_first_loss": float(box["losses"][0]),
+                                "mlp_last_loss": float(np.mean(box["losses"][-8:]))})
+
+    def first_at(arm, target):
+        return next((c for c in arm["curve"] if c["auc_all"] >= target), None)
+
+    fp32_final = arms["fp32"]["curve"][-1]["auc_all"]
+    fp32_best = max(c["auc_all"] for c in arms["fp32"]["curve"])
+    result = {}
+    for tname, tval in (("fp32_final", fp32_final - 0.005), ("fp32_best", fp32_best - 0.005)):
+        result[tname] = {"target_auc": tval, **{k: (first_at(a, tval) or {}).get("time_s") for k, a in arms.items()}}
+    hit = result["fp32_final"]["bf16_warm"]
+    line = {"metric": "wall time of BF16 + warm start to the FP32 path's link-prediction AUC (within 0.005)",
+            "value": hit, "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "bf16",
+            "data": "synthetic",
+            "config": {"workload": "warm22_rmat22_order2_d128_K5_B4096",
+                       "graph": "R-MAT scale 22 (4,194,304 nodes), 10% of edges held out for AUC, 10% of nodes "
+                                "held out and joining after phase 0", "n_arcs_train": E,
+                       "phase0_samples": n0, "phase0_s": t0, "checkpoints_epochs": marks,
+                       "auc_pairs_all": len(hs), "auc_pairs_new_nodes": len(ps), "generation_s": t_gen,
+                       "time": "device time of training, table conversion and MLP steps; evaluation excluded"},
+            "time_to_target_s": result, "fp32_final_auc": fp32_final, "fp32_best_auc": fp32_best, "arms": arms}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -261,6 +394,9 @@ def main():
         return
     if args.workload == "dchung22":
         run_dchung22(args)
+        return
+    if args.workload == "warm22":
+        run_warm22(args)
         return
     import numpy as np
     import torch

@@ -121,47 +121,133 @@ __global__ void k_mlp_init(float* __restrict__ p, int H, int P, int D, uint64_t 
 }
 
 // ---- features: one warp per node -------------------------------------------
+constexpr int kMaxE = 8;            // D <= 256: values of a row per lane
+constexpr int64_t kHubArcs = 2048;   // nodes with more arcs are summed by a whole CTA
+constexpr int kHubWarps = 16;
+
+// Adds the rows U[dst[e]] of the known neighbours among arcs [lo, hi) to acc
+// (lane: values lane, lane + 32, ...), in arc order; returns their number.
+__device__ __forceinline__ int sum_known_rows(int64_t lo, int64_t hi, const int32_t* __restrict__ dst, const void* U,
+                                             int udt, int D, const uint8_t* __restrict__ known, float (&acc)[kMaxE]) {
+    const int lane = threadIdx.x & 31;
+    int cnt = 0;
+    for (int64_t e0 = lo; e0 < hi; e0 += 32) {
+        // 32 arcs at a time: lane l reads arc e0 + l; known neighbours
+        // are then added in arc order
+        const int64_t e = e0 + lane;
+        const int32_t w = e < hi ? dst[e] : 0;
+        const bool ok = e < hi && known[w];
+        uint32_t mask = __ballot_sync(0xFFFFFFFFu, ok);
+        cnt += __popc(mask);
+        while (mask) {
+            // up to kGroup known neighbours: all their loads in flight,
+            // then added in arc order
+            constexpr int kGroup = 8;
+            int64_t rows[kGroup];
+            int m = 0;
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j) {
+                rows[j] = -1;
+                if (mask) {
+                    const int l = __ffs(mask) - 1;
+                    mask &= mask - 1;
+                    rows[j] = __shfl_sync(0xFFFFFFFFu, w, l);
+                    m = j + 1;
+                }
+            }
+            float val[kGroup][kMaxE];
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j)
+#pragma unroll
+                for (int i = 0; i < kMaxE; ++i) {
+                    const int k = lane + 32 * i;
+                    val[j][i] = (j < m && k < D) ? load_row_elem(U, udt, rows[j] * D + k) : 0.0f;
+                }
+#pragma unroll
+            for (int j = 0; j < kGroup; ++j)
+                if (j < m)
+#pragma unroll
+                    for (int i = 0; i < kMaxE; ++i) acc[i] += val[j][i];
+        }
+    }
+    return cnt;
+}
+
+template <typename TX>
+__device__ __forceinline__ void write_features(TX* x, float deg, const float (&acc)[kMaxE], int cnt, int D, int P) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) x[0] = from_f<TX>(log1pf(deg));
+#pragma unroll
+    for (int i = 0; i < kMaxE; ++i) {
+        const int k = lane + 32 * i;
+        if (k < D) x[1 + k] = from_f<TX>(cnt ? acc[i] / (float)cnt : 0.0f);
+    }
+    for (int k = D + 1 + lane; k < P; k += 32) x[k] = from_f<TX>(0.0f);
+}
+
+// One warp per node; nodes with more than kHubArcs arcs are listed in hubs
+// (order irrelevant) and left to k_mlp_features_hub.
 template <typename TX>
 __global__ void k_mlp_features(int64_t n_nodes, int64_t n_arcs, const int32_t* __restrict__ src,
                                const int32_t* __restrict__ dst, const float* __restrict__ deg, const void* U, int udt,
-                               int D, const uint8_t* __restrict__ known, int P, TX* __restrict__ X) {
-    constexpr int kMaxE = 8;  // D <= 256
+                               int D, const uint8_t* __restrict__ known, int P, TX* __restrict__ X,
+                               uint32_t* __restrict__ hubs, uint32_t* __restrict__ n_hubs) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t v = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); v < n_nodes; v += warps) {
         const int64_t lo = lower_bound_src(src, n_arcs, (int32_t)v);
         const int64_t hi = lower_bound_src(src, n_arcs, (int32_t)(v + 1));
+        if (hi - lo > kHubArcs) {
+            if (lane == 0) hubs[atomicAdd(n_hubs, 1u)] = (uint32_t)v;
+            continue;
+        }
         float acc[kMaxE];
 #pragma unroll
         for (int i = 0; i < kMaxE; ++i) acc[i] = 0.0f;
-        int cnt = 0;
-        for (int64_t e0 = lo; e0 < hi; e0 += 32) {
-            // 32 arcs at a time: lane l reads arc e0 + l; known neighbours
-            // are then added in arc order
-            const int64_t e = e0 + lane;
-            const int32_t w = e < hi ? dst[e] : 0;
-            const bool ok = e < hi && known[w];
-            uint32_t mask = __ballot_sync(0xFFFFFFFFu, ok);
-            cnt += __popc(mask);
-            while (mask) {
-                const int l = __ffs(mask) - 1;
-                mask &= mask - 1;
-                const int64_t row = __shfl_sync(0xFFFFFFFFu, w, l);
+        const int cnt = sum_known_rows(lo, hi, dst, U, udt, D, known, acc);
+        write_features<TX>(X + v * (int64_t)P, deg[v], acc, cnt, D, P);
+    }
+}
+
+// One CTA per listed hub: warp w sums the w-th of kHubWarps contiguous arc
+// slices, the partial sums are added in warp order.
+template <typename TX>
+__global__ void __launch_bounds__(kHubWarps * 32) k_mlp_features_hub(
+    int64_t n_arcs, const int32_t* __restrict__ src, const int32_t* __restrict__ dst, const float* __restrict__ deg,
+    const void* U, int udt, int D, const uint8_t* __restrict__ known, int P, TX* __restrict__ X,
+    const uint32_t* __restrict__ hubs, const uint32_t* __restrict__ n_hubs) {
+    __shared__ float part[kHubWarps][256];
+    __shared__ int pcnt[kHubWarps];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nh = *n_hubs;
+    for (uint32_t h = blockIdx.x; h < nh; h += gridDim.x) {
+        const int64_t v = hubs[h];
+        const int64_t lo = lower_bound_src(src, n_arcs, (int32_t)v);
+        const int64_t hi = lower_bound_src(src, n_arcs, (int32_t)(v + 1));
+        const int64_t per = (hi - lo + kHubWarps - 1) / kHubWarps;
+        const int64_t a = min(hi, lo + warp * per), b = min(hi, a + per);
+        float acc[kMaxE];
 #pragma unroll
-                for (int i = 0; i < kMaxE; ++i) {
-                    const int k = lane + 32 * i;
-                    if (k < D) acc[i] += load_row_elem(U, udt, row * D + k);
-                }
+        for (int i = 0; i < kMaxE; ++i) acc[i] = 0.0f;
+        const int c = sum_known_rows(a, b, dst, U, udt, D, known, acc);
+#pragma unroll
+        for (int i = 0; i < kMaxE; ++i)
+            if (lane + 32 * i < D) part[warp][lane + 32 * i] = acc[i];
+        if (lane == 0) pcnt[warp] = c;
+        __syncthreads();
+        if (warp == 0) {
+            int cnt = 0;
+#pragma unroll
+            for (int i = 0; i < kMaxE; ++i) acc[i] = 0.0f;
+            for (int w = 0; w < kHubWarps; ++w) {
+                cnt += pcnt[w];
+#pragma unroll
+                for (int i = 0; i < kMaxE; ++i)
+                    if (lane + 32 * i < D) acc[i] += part[w][lane + 32 * i];
             }
+            write_features<TX>(X + v * (int64_t)P, deg[v], acc, cnt, D, P);
         }
-        TX* x = X + v * (int64_t)P;
-        if (lane == 0) x[0] = from_f<TX>(log1pf(deg[v]));
-#pragma unroll
-        for (int i = 0; i < kMaxE; ++i) {
-            const int k = lane + 32 * i;
-            if (k < D) x[1 + k] = from_f<TX>(cnt ? acc[i] / (float)cnt : 0.0f);
-        }
-        for (int k = D + 1 + lane; k < P; k += 32) x[k] = from_f<TX>(0.0f);
+        __syncthreads();
     }
 }
 
@@ -541,21 +627,34 @@ line_status line_mlp_features(line_ctx* c, const uint8_t* known) {
     MlpState& s = *c->mlp;
     const Tables& t = c->tab[s.order];
     uint8_t* kd = nullptr;
+    uint32_t* hubs = nullptr;  // [count] then the listed hub nodes
+    const int64_t max_hubs = c->n_arcs / kHubArcs + 1;
     cudaError_t e = cudaMalloc(&kd, c->n_nodes);
+    if (e == cudaSuccess) e = cudaMalloc(&hubs, sizeof(uint32_t) * (max_hubs + 1));
     if (e == cudaSuccess) e = cudaMemcpyAsync(kd, known, c->n_nodes, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hubs, 0, sizeof(uint32_t), c->stream);
     if (e == cudaSuccess) {
         const unsigned g = grid_of(c->n_nodes * 32, 256, 152 * 64);
-        if (s.act == LINE_DTYPE_F32)
+        const unsigned gh = (unsigned)std::min<int64_t>(max_hubs, 152 * 4);
+        if (s.act == LINE_DTYPE_F32) {
+            float* X = reinterpret_cast<float*>(s.X);
             k_mlp_features<float><<<g, 256, 0, c->stream>>>(c->n_nodes, c->n_arcs, c->src, c->dst, c->deg, t.U,
-                                                            t.dtype, s.dim, kd, s.P, reinterpret_cast<float*>(s.X));
-        else
+                                                            t.dtype, s.dim, kd, s.P, X, hubs + 1, hubs);
+            k_mlp_features_hub<float><<<gh, kHubWarps * 32, 0, c->stream>>>(c->n_arcs, c->src, c->dst, c->deg, t.U,
+                                                                             t.dtype, s.dim, kd, s.P, X, hubs + 1,
+                                                                             hubs);
+        } else {
+            __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(s.X);
             k_mlp_features<__nv_bfloat16><<<g, 256, 0, c->stream>>>(c->n_nodes, c->n_arcs, c->src, c->dst, c->deg,
-                                                                    t.U, t.dtype, s.dim, kd, s.P,
-                                                                    reinterpret_cast<__nv_bfloat16*>(s.X));
+                                                                    t.U, t.dtype, s.dim, kd, s.P, X, hubs + 1, hubs);
+            k_mlp_features_hub<__nv_bfloat16><<<gh, kHubWarps * 32, 0, c->stream>>>(
+                c->n_arcs, c->src, c->dst, c->deg, t.U, t.dtype, s.dim, kd, s.P, X, hubs + 1, hubs);
+        }
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (kd) cudaFree(kd);
+    if (hubs) cudaFree(hubs);
     if (e != cudaSuccess) return cuda_fail(c, e, "line_mlp_features");
     s.has_features = true;
     return LINE_OK;
