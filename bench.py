@@ -71,6 +71,24 @@ def parse():
     return p.parse_args()
 
 
+def replica_seed(rank: int) -> int:
+    """Replicas (one per rank, no collectives on the data path) train with
+    different seeds."""
+    return 1000 + rank
+
+
+def max_over_ranks(value: float, world: int) -> float:
+    """The job's time is the slowest rank's (max-reduce over the process group)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([value], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -141,6 +159,25 @@ def peaks():
         return float(p["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def measured_traffic():
+    """DRAM bytes per batch of the update kernels from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    import hashlib
+    import re
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_gather_k_apply_rmat20_d128_K5_B4096.md")) as f:
+            text = f.read()
+        with open(os.path.join(ROOT, "paper_2604_09419_gb300", "csrc", "train.cu"), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        m = re.search(r"sha256 prefix ([0-9a-f]{16})", text)
+        t = re.search(r"traffic_bytes_per_batch: (\d+)", text)
+        if m and t and m.group(1) == sha:
+            return int(t.group(1))
+    except OSError:
+        pass
+    return None
 
 
 def cpu_baseline(g, n_samples: int):
@@ -419,7 +456,7 @@ def main():
     w = torch.from_numpy(g.w).cuda()
     ctx.build_alias(g.n_nodes, src, dst, w)
     mode = {"auto": L.MODE_BATCHED, "batched": L.MODE_BATCHED, "persistent": L.MODE_PERSISTENT}[args.mode]
-    seed = 1000 + rank  # independent replicas per rank
+    seed = replica_seed(rank)
 
     def opts(offset):
         o = L.train_opts_default()
@@ -459,11 +496,7 @@ def main():
         barrier()
     ms = ev0.elapsed_time(ev1)
     st = ctx.stats()
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, world)
     updates = 2 * S * args.steps * world
     value = updates / (ms / 1e3)
 
@@ -472,8 +505,11 @@ def main():
     upd_ms = st.update_ms
     upd_bytes = st.update_samples * ALG_BYTES_UPDATE
     achieved = upd_bytes / (upd_ms / 1e3) / 1e9 if upd_ms > 0 else None
+    traffic = measured_traffic() if mode == L.MODE_BATCHED and args.scale == 20 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak if achieved else None, "traffic": None,
+                "frac": achieved / peak if achieved else None, "traffic": traffic,
+                "traffic_unit": "DRAM bytes per 4,096-sample batch (k_gather + k_apply, warm L2, ncu)",
+                "alg_bytes_per_batch": B * ALG_BYTES_UPDATE,
                 "kernel": "update phase (k_gather + k_apply)" if mode == L.MODE_BATCHED else "k_persistent",
                 "alg_bytes_per_sample": ALG_BYTES_UPDATE, "peak_kind": peak_kind,
                 "path_achieved_gbs": value / world * ALG_BYTES_PATH / 1e9,
