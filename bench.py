@@ -5,7 +5,9 @@ Workload: R-MAT scale 20 (1,048,576 nodes, edge factor 16, (a,b,c,d) =
 first- and second-order LINE, d=128, K=5 negatives from deg^0.75, FP32
 tables, deterministic minibatch B=4096, lr 0.025 with linear decay over
 20 x |E| samples per order.  One step = |E| = 16 * 2^20 samples of each
-order (one "epoch" of each), so 20 steps are the full run.
+order (one "epoch" of each), so 20 steps are the full run.  The two orders'
+tables are independent and are trained concurrently (line_train_orders, two
+streams; the same tables as one order after the other).
 
 Other workloads (``--workload``; not the default line):
 
@@ -61,6 +63,8 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--mode", default="auto", choices=["auto", "batched", "persistent"])
+    p.add_argument("--orders", default="concurrent", choices=["concurrent", "sequential"],
+                   help="train the two orders' tables concurrently (line_train_orders) or one after the other")
     p.add_argument("--scale", type=int, default=20)
     p.add_argument("--samples-per-step", type=int, default=0, help="0: |E| = 16 * 2^scale")
     p.add_argument("--e2e-steps", type=int, default=2)
@@ -470,10 +474,15 @@ def main():
     ctx.init_embeddings(2, DIM, L.DTYPE_F32, seed=2)
     state = {"offset": 0}
 
+    concurrent = args.orders == "concurrent"
+
     def step():
         off = state["offset"] % total_per_order
-        for order in (1, 2):
-            ctx.train_steps(order, DIM, K, S, seed, total=total_per_order, opts=opts(off))
+        if concurrent:
+            ctx.train_orders(DIM, K, S, seed, total=total_per_order, opts=opts(off))
+        else:
+            for order in (1, 2):
+                ctx.train_steps(order, DIM, K, S, seed, total=total_per_order, opts=opts(off))
         state["offset"] += S
 
     for _ in range(args.warmup):
@@ -500,21 +509,34 @@ def main():
     updates = 2 * S * args.steps * world
     value = updates / (ms / 1e3)
 
-    # roofline of the update kernels (gather + apply), from their own CUDA events
     peak, peak_kind = peaks()
-    upd_ms = st.update_ms
-    upd_bytes = st.update_samples * ALG_BYTES_UPDATE
-    achieved = upd_bytes / (upd_ms / 1e3) / 1e9 if upd_ms > 0 else None
+    if concurrent:
+        # the two orders' update kernels overlap on two streams, so per-launch
+        # durations overlap too: their algorithmic bytes over the timed
+        # region (CUDA events on the caller's stream) instead
+        achieved = 2 * S * args.steps * ALG_BYTES_UPDATE / (ms / 1e3) / 1e9
+        kernel = "update phase of both orders (k_gather + k_apply), concurrent streams, over the timed region"
+    else:
+        # the update kernels' own CUDA events
+        upd_ms = st.update_ms
+        achieved = st.update_samples * ALG_BYTES_UPDATE / (upd_ms / 1e3) / 1e9 if upd_ms > 0 else None
+        kernel = "update phase (k_gather + k_apply)" if mode == L.MODE_BATCHED else "k_persistent"
     traffic = measured_traffic() if mode == L.MODE_BATCHED and args.scale == 20 else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per 4,096-sample batch (k_gather + k_apply, warm L2, ncu)",
                 "alg_bytes_per_batch": B * ALG_BYTES_UPDATE,
-                "kernel": "update phase (k_gather + k_apply)" if mode == L.MODE_BATCHED else "k_persistent",
+                "kernel": kernel,
                 "alg_bytes_per_sample": ALG_BYTES_UPDATE, "peak_kind": peak_kind,
                 "path_achieved_gbs": value / world * ALG_BYTES_PATH / 1e9,
                 "path_frac": value / world * ALG_BYTES_PATH / 1e9 / peak}
-    launches = int(st.update_launches + st.prepass_launches)
+    if concurrent:
+        # counted from the schedule: per order and step, two launches per
+        # batch and three pre-pass launches per chunk of 64 batches
+        batches = -(-S // B)
+        launches = int(2 * args.steps * (2 * batches + 3 * -(-batches // 64)))
+    else:
+        launches = int(st.update_launches + st.prepass_launches)
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -533,8 +555,11 @@ def main():
             ctx2.build_alias(g.n_nodes, hs, hd, hw)
             ctx2.init_embeddings(1, DIM, L.DTYPE_F32, seed=1)
             ctx2.init_embeddings(2, DIM, L.DTYPE_F32, seed=2)
-            for order in (1, 2):
-                ctx2.train_steps(order, DIM, K, S, seed, total=total_per_order, opts=opts(0))
+            if concurrent:
+                ctx2.train_orders(DIM, K, S, seed, total=total_per_order, opts=opts(0))
+            else:
+                for order in (1, 2):
+                    ctx2.train_steps(order, DIM, K, S, seed, total=total_per_order, opts=opts(0))
             ctx2.get_embeddings(2, L.WHICH_U, out)
         barrier()
         dt = time.perf_counter() - t0
@@ -553,7 +578,7 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(args, g), "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
-                "mode": "batched" if mode == L.MODE_BATCHED else "persistent"}
+                "mode": "batched" if mode == L.MODE_BATCHED else "persistent", "orders": args.orders}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

@@ -183,6 +183,18 @@ LINE_API line_status line_init_embeddings(line_ctx* ctx, int order, int dim, int
 LINE_API line_status line_train_steps(line_ctx* ctx, int order, int dim, int K, const line_lr* lr,
                              uint64_t n_samples, uint64_t seed, const line_train_opts* opts);
 
+/* Train the order-1 and the order-2 tables (both created with `dim`) on
+ * the same samples, concurrently: the two runs are independent (separate
+ * tables), so the call gives bitwise the same tables as
+ * line_train_steps(order 1) followed by line_train_steps(order 2) with the
+ * same arguments, while the GPU overlaps one run's latency-bound phases with
+ * the other's.  The order-1 run uses a second stream and workspace owned by
+ * the context; work after the call on the context's stream follows both
+ * runs.  opts.timing times the call as a whole (total_ms, total_samples =
+ * 2 n_samples) and not per kernel.  Errors: as line_train_steps. */
+LINE_API line_status line_train_orders(line_ctx* ctx, int dim, int K, const line_lr* lr, uint64_t n_samples,
+                                       uint64_t seed, const line_train_opts* opts);
+
 /* Search space of line_autotune. */
 typedef struct {
     const int64_t* batches;  /* candidate batch sizes (a host array), or NULL: keep io->batch */

@@ -144,6 +144,10 @@ void line_destroy(line_ctx* c) {
     else cudaDeviceSynchronize();
     free_graph(c);
     workspace_destroy(c->ws);
+    workspace_destroy(c->ws2);
+    if (c->side) cudaStreamDestroy(c->side);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->status) cudaFree(c->status);
     if (c->dscratch) cudaFree(c->dscratch);
     if (c->ev0) cudaEventDestroy(c->ev0);
@@ -284,26 +288,29 @@ line_status line_init_embeddings(line_ctx* c, int order, int dim, int dtype, uin
     return LINE_OK;
 }
 
-line_status line_train_steps(line_ctx* c, int order, int dim, int K, const line_lr* lr, uint64_t n_samples,
-                             uint64_t seed, const line_train_opts* opts) {
-    line_status st = enter(c);
-    if (st) return st;
-    if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_train_steps: no graph");
-    if (order != 1 && order != 2) return fail(c, LINE_ERR_ARG, "line_train_steps: order must be 1 or 2");
+}  // extern "C"
+
+namespace {
+
+// Checks the arguments of a training call and fills the kernel arguments.
+line_status make_train_args(line_ctx* c, const char* what, int order, int dim, int K, const line_lr* lr,
+                            uint64_t n_samples, uint64_t seed, const line_train_opts* opts, TrainArgs* out) {
+    if (!c->has_graph) return fail(c, LINE_ERR_STATE, "%s: no graph", what);
+    if (order != 1 && order != 2) return fail(c, LINE_ERR_ARG, "%s: order must be 1 or 2", what);
     Tables& t = c->tab[order];
-    if (!t.ready || t.dim != dim) return fail(c, LINE_ERR_STATE, "line_train_steps: tables of order %d and dim %d not initialised", order, dim);
-    if (K < 0 || K > kMaxK) return fail(c, LINE_ERR_ARG, "line_train_steps: K out of range");
+    if (!t.ready || t.dim != dim)
+        return fail(c, LINE_ERR_STATE, "%s: tables of order %d and dim %d not initialised", what, order, dim);
+    if (K < 0 || K > kMaxK) return fail(c, LINE_ERR_ARG, "%s: K out of range", what);
     if (!lr || !(lr->lr0 >= 0.0) || (lr->schedule != 0 && lr->schedule != 1) || !(lr->floor_frac >= 0.0))
-        return fail(c, LINE_ERR_ARG, "line_train_steps: bad learning rate");
+        return fail(c, LINE_ERR_ARG, "%s: bad learning rate", what);
     line_train_opts o;
     line_train_opts_default(&o);
     if (opts) o = *opts;
-    if (o.batch < 1 || o.batch > (1 << 20)) return fail(c, LINE_ERR_ARG, "line_train_steps: batch out of range");
-    if (!(o.lambda >= 0.0) || !(o.alpha_neg >= 0.0)) return fail(c, LINE_ERR_ARG, "line_train_steps: bad lambda/alpha_neg");
-    if (o.mode != LINE_MODE_BATCHED && o.mode != LINE_MODE_PERSISTENT) return fail(c, LINE_ERR_ARG, "line_train_steps: bad mode");
-    if (o.warps_per_block < 0 || o.warps_per_block > 32) return fail(c, LINE_ERR_ARG, "line_train_steps: bad warps_per_block");
-    if (n_samples == 0) return LINE_OK;
-    if (o.sample_offset + n_samples < o.sample_offset) return fail(c, LINE_ERR_ARG, "line_train_steps: sample range overflows");
+    if (o.batch < 1 || o.batch > (1 << 20)) return fail(c, LINE_ERR_ARG, "%s: batch out of range", what);
+    if (!(o.lambda >= 0.0) || !(o.alpha_neg >= 0.0)) return fail(c, LINE_ERR_ARG, "%s: bad lambda/alpha_neg", what);
+    if (o.mode != LINE_MODE_BATCHED && o.mode != LINE_MODE_PERSISTENT) return fail(c, LINE_ERR_ARG, "%s: bad mode", what);
+    if (o.warps_per_block < 0 || o.warps_per_block > 32) return fail(c, LINE_ERR_ARG, "%s: bad warps_per_block", what);
+    if (o.sample_offset + n_samples < o.sample_offset) return fail(c, LINE_ERR_ARG, "%s: sample range overflows", what);
     TrainArgs a{};
     a.order = order;
     a.dim = dim;
@@ -333,21 +340,85 @@ line_status line_train_steps(line_ctx* c, int order, int dim, int K, const line_
     a.warps_per_block = o.warps_per_block;
     a.timing = o.timing;
     a.graph = o.graph;
+    *out = a;
+    return LINE_OK;
+}
+
+line_status train_fail(line_ctx* c, cudaError_t e, const std::string& err, const char* what) {
+    if (!err.empty()) return fail(c, e == cudaErrorMemoryAllocation ? LINE_ERR_OOM : LINE_ERR_ARG, "%s: %s", what, err.c_str());
+    return cuda_fail(c, e, what);
+}
+
+}  // namespace
+
+extern "C" {
+
+line_status line_train_steps(line_ctx* c, int order, int dim, int K, const line_lr* lr, uint64_t n_samples,
+                             uint64_t seed, const line_train_opts* opts) {
+    line_status st = enter(c);
+    if (st) return st;
+    TrainArgs a{};
+    if ((st = make_train_args(c, "line_train_steps", order, dim, K, lr, n_samples, seed, opts, &a))) return st;
+    if (n_samples == 0) return LINE_OK;
     std::string err;
-    if (o.timing) CK(cudaEventRecord(c->ev0, c->stream), "event");
+    if (a.timing) CK(cudaEventRecord(c->ev0, c->stream), "event");
     cudaError_t e = train_run(a, c->ws, c->status, &c->times, c->stream, &err);
-    if (e != cudaSuccess) {
-        if (!err.empty()) return fail(c, e == cudaErrorMemoryAllocation ? LINE_ERR_OOM : LINE_ERR_ARG, "line_train_steps: %s", err.c_str());
-        return cuda_fail(c, e, "line_train_steps");
-    }
-    if (o.timing) CK(cudaEventRecord(c->ev1, c->stream), "event");
+    if (e != cudaSuccess) return train_fail(c, e, err, "line_train_steps");
+    if (a.timing) CK(cudaEventRecord(c->ev1, c->stream), "event");
     st = check_status(c, "line_train_steps");
     if (st) return st;
-    if (o.timing) {
+    if (a.timing) {
         float ms = 0;
         cudaEventElapsedTime(&ms, c->ev0, c->ev1);
         c->total_ms += ms;
         c->total_samples += n_samples;
+    }
+    return LINE_OK;
+}
+
+line_status line_train_orders(line_ctx* c, int dim, int K, const line_lr* lr, uint64_t n_samples, uint64_t seed,
+                              const line_train_opts* opts) {
+    line_status st = enter(c);
+    if (st) return st;
+    TrainArgs a1{}, a2{};
+    if ((st = make_train_args(c, "line_train_orders", 1, dim, K, lr, n_samples, seed, opts, &a1))) return st;
+    if ((st = make_train_args(c, "line_train_orders", 2, dim, K, lr, n_samples, seed, opts, &a2))) return st;
+    if (n_samples == 0) return LINE_OK;
+    // per-chunk timing reads events on the host between chunks, which would
+    // serialise the two streams: the call is timed as a whole instead
+    const bool timing = a1.timing != 0;
+    a1.timing = a2.timing = 0;
+    if (!c->ws2) c->ws2 = workspace_create();
+    if (!c->side) CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "line_train_orders: stream");
+    if (!c->ev_fork) CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "line_train_orders: event");
+    if (!c->ev_join) CK(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming), "line_train_orders: event");
+    if (timing) CK(cudaEventRecord(c->ev0, c->stream), "event");
+    // order 1 on the side stream, after the caller's earlier work
+    CK(cudaEventRecord(c->ev_fork, c->stream), "line_train_orders: fork");
+    CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "line_train_orders: fork");
+    std::string err;
+    cudaError_t e = train_run(a1, c->ws2, c->status, &c->times, c->side, &err);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(c->side);
+        return train_fail(c, e, err, "line_train_orders");
+    }
+    e = train_run(a2, c->ws, c->status, &c->times, c->stream, &err);
+    // the caller's stream continues after both
+    cudaError_t ej = cudaEventRecord(c->ev_join, c->side);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(c->stream, c->ev_join, 0);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(c->side);
+        return train_fail(c, e, err, "line_train_orders");
+    }
+    CK(ej, "line_train_orders: join");
+    if (timing) CK(cudaEventRecord(c->ev1, c->stream), "event");
+    st = check_status(c, "line_train_orders");
+    if (st) return st;
+    if (timing) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        c->total_ms += ms;
+        c->total_samples += 2 * n_samples;
     }
     return LINE_OK;
 }

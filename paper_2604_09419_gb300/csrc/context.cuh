@@ -43,6 +43,11 @@ struct line_ctx {
     uint32_t* flag = nullptr;
     double* dscratch = nullptr;
     line::TrainWorkspace* ws = nullptr;
+    // concurrent training of both orders (line_train_orders): the order-1
+    // run's workspace and stream, and the events joining it to `stream`
+    line::TrainWorkspace* ws2 = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     line::TrainTimes times;
     double total_ms = 0;
     uint64_t total_samples = 0;

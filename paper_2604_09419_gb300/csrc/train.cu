@@ -1691,26 +1691,39 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     int device = 0;
     if ((e = cudaGetDevice(&device)) != cudaSuccess) return e;
     if ((e = ws->init(device)) != cudaSuccess) return e;
-    // a set still in use by an earlier call's data phase is not reallocated
-    // before that phase is done
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-    if (!ensure(ws->items0, sizeof(uint64_t) * max_items) || !ensure(ws->items1, sizeof(uint64_t) * max_items) ||
-        !ensure(ws->gcnt, sizeof(uint32_t) * (size_t)nb * parts * kBuckets) ||
-        !ensure(ws->boff, sizeof(uint32_t) * (size_t)nb * (kBuckets + 1)) || !ensure(ws->counters, 256) ||
-        !ensure(ws->slab, sizeof(float) * (size_t)max_items * a.dim))
-        return e;
-    for (auto& cs : ws->set) {
-        if (!ensure(cs.rec, sizeof(int32_t) * max_items) || !ensure(cs.eta, sizeof(float) * (nb + 1)) ||
-            !ensure(cs.slot_info, sizeof(uint2) * max_items) || !ensure(cs.mdesc, sizeof(uint4) * (size_t)nb * mcap) ||
-            !ensure(cs.mcount, sizeof(uint32_t) * (nb + 1)) || !ensure(cs.ldesc, sizeof(uint4) * (size_t)nb * lcap) ||
-            !ensure(cs.lcount, sizeof(uint32_t) * (nb + 1)) || !ensure(cs.tchunk, 256))
-            return e;
-        if (persistent && (!ensure(cs.slot_prev, sizeof(int32_t) * max_items) ||
-                           !ensure(cs.arrive, sizeof(uint32_t) * max_items) ||
-                           !ensure(cs.item_base, sizeof(uint64_t) * (nb + 1)) ||
-                           !ensure(cs.nseg, sizeof(uint32_t) * (nb + 1))))
-            return e;
-        cs.data_pending = false;
+    // every scratch buffer and its size for this call
+    auto each = [&](auto&& f) -> bool {
+        if (!f(ws->items0, sizeof(uint64_t) * max_items) || !f(ws->items1, sizeof(uint64_t) * max_items) ||
+            !f(ws->gcnt, sizeof(uint32_t) * (size_t)nb * parts * kBuckets) ||
+            !f(ws->boff, sizeof(uint32_t) * (size_t)nb * (kBuckets + 1)) || !f(ws->counters, 256) ||
+            !f(ws->slab, sizeof(float) * (size_t)max_items * a.dim))
+            return false;
+        for (auto& cs : ws->set) {
+            if (!f(cs.rec, sizeof(int32_t) * max_items) || !f(cs.eta, sizeof(float) * (nb + 1)) ||
+                !f(cs.slot_info, sizeof(uint2) * max_items) || !f(cs.mdesc, sizeof(uint4) * (size_t)nb * mcap) ||
+                !f(cs.mcount, sizeof(uint32_t) * (nb + 1)) || !f(cs.ldesc, sizeof(uint4) * (size_t)nb * lcap) ||
+                !f(cs.lcount, sizeof(uint32_t) * (nb + 1)) || !f(cs.tchunk, 256))
+                return false;
+            if (persistent && (!f(cs.slot_prev, sizeof(int32_t) * max_items) ||
+                               !f(cs.arrive, sizeof(uint32_t) * max_items) ||
+                               !f(cs.item_base, sizeof(uint64_t) * (nb + 1)) || !f(cs.nseg, sizeof(uint32_t) * (nb + 1))))
+                return false;
+        }
+        return true;
+    };
+    // Buffers still used by an earlier call's data phase are reallocated
+    // only after that phase is done; when nothing grows, consecutive calls on
+    // the stream pipeline (the chunk sets' events order the reuse).
+    bool grow = false;
+    each([&](Buf& b, size_t bytes) {
+        grow = grow || b.cap < bytes;
+        return true;
+    });
+    if (grow) {
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+        if (ws->prep && (e = cudaStreamSynchronize(ws->prep)) != cudaSuccess) return e;
+        for (auto& cs : ws->set) cs.data_pending = false;
+        if (!each(ensure)) return e;
     }
     if (persistent) {
         if (!ensure(ws->sorted_row, sizeof(uint32_t) * max_items) || !ensure(ws->seghead, sizeof(uint32_t) * max_items) ||

@@ -72,6 +72,7 @@ def _load():
         "line_sample_debug": (i32, [vp, i32, u64, u32, u64, i64, vp]),
         "line_init_embeddings": (i32, [vp, i32, i32, i32, u64]),
         "line_train_steps": (i32, [vp, i32, i32, i32, ctypes.POINTER(LR), u64, u64, ctypes.POINTER(TrainOpts)]),
+        "line_train_orders": (i32, [vp, i32, i32, ctypes.POINTER(LR), u64, u64, ctypes.POINTER(TrainOpts)]),
         "line_get_embeddings": (i32, [vp, i32, i32, vp, i32]),
         "line_set_embeddings": (i32, [vp, i32, i32, vp, i32, vp, i64]),
         "line_eval_loss": (i32, [vp, i32, i32, u64, i64, ctypes.POINTER(dbl)]),
@@ -102,7 +103,7 @@ def _load():
 lib = _load()
 EXPORTED = ("line_train_opts_default", "line_status_string", "line_create", "line_destroy", "line_last_error",
             "line_build_alias", "line_get_graph_info", "line_get_alias", "line_sample_debug",
-            "line_init_embeddings", "line_train_steps", "line_get_embeddings", "line_set_embeddings",
+            "line_init_embeddings", "line_train_steps", "line_train_orders", "line_get_embeddings", "line_set_embeddings",
             "line_eval_loss", "line_eval_loss_noalloc", "line_eval_auc", "line_mlp_create", "line_mlp_features",
             "line_mlp_get_features", "line_mlp_get_params", "line_mlp_set_params", "line_mlp_grad", "line_mlp_train",
             "line_mlp_predict", "line_autotune", "line_get_stats", "line_reset_stats", "line_synchronize", "line_debug_wait_timeout")
@@ -188,6 +189,15 @@ class Context:
             setattr(o, "lambda_" if k == "lam" else k, v)
         st = lib.line_train_steps(self.h, order, dim, K, ctypes.byref(lr), n_samples, seed, ctypes.byref(o))
         return self._ck(st) if check else st
+
+    def train_orders(self, dim, K, n_samples, seed, *, lr0=0.025, schedule=1, floor_frac=1e-4, total=0,
+                     opts: TrainOpts | None = None, **kw):
+        """Both orders' tables on the same samples, concurrently (same bits as two train_steps calls)."""
+        lr = LR(lr0, schedule, floor_frac, total)
+        o = opts if opts is not None else train_opts_default()
+        for k, v in kw.items():
+            setattr(o, "lambda_" if k == "lam" else k, v)
+        return self._ck(lib.line_train_orders(self.h, dim, K, ctypes.byref(lr), n_samples, seed, ctypes.byref(o)))
 
     def get_embeddings(self, order, which, dst, dtype=DTYPE_F32):
         return self._ck(lib.line_get_embeddings(self.h, order, which, ptr(dst), dtype))

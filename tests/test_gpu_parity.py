@@ -170,6 +170,36 @@ def test_autotune_keeps_tables_and_returns_a_valid_configuration(ctx):
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
+@pytest.mark.parametrize("dtype,cb", [(0, 0), (0, 3), (1, 2)])
+def test_train_orders_equals_two_sequential_calls(ctx, dtype, cb):
+    """Both orders trained concurrently give the tables of two separate calls."""
+    from paper_2604_09419_gb300 import line as L
+    g = G.graph("rmat14")
+    G.upload(ctx, g)
+    n, B = 80_000, 1024
+    ctx.init_embeddings(1, 64, dtype, seed=1)
+    ctx.init_embeddings(2, 64, dtype, seed=2)
+    for order in (1, 2):
+        ctx.train_steps(order, 64, 5, n, 9, batch=B, chunk_batches=cb, total=2 * n)
+    ctx.train_steps(1, 64, 5, n, 9, batch=B, chunk_batches=cb, total=2 * n, sample_offset=n)
+    ctx.train_steps(2, 64, 5, n, 9, batch=B, chunk_batches=cb, total=2 * n, sample_offset=n)
+    want1, _ = G.tables(ctx, g, 1, 64)
+    want2 = G.tables(ctx, g, 2, 64)
+    ctx.init_embeddings(1, 64, dtype, seed=1)
+    ctx.init_embeddings(2, 64, dtype, seed=2)
+    ctx.train_orders(64, 5, n, 9, batch=B, chunk_batches=cb, total=2 * n)
+    ctx.train_orders(64, 5, n, 9, batch=B, chunk_batches=cb, total=2 * n, sample_offset=n)
+    got1, _ = G.tables(ctx, g, 1, 64)
+    got2 = G.tables(ctx, g, 2, 64)
+    assert np.array_equal(want1, got1)
+    assert np.array_equal(want2[0], got2[0]) and np.array_equal(want2[1], got2[1])
+    # both orders must exist with the given dim
+    ctx.init_embeddings(1, 32, dtype, seed=1)
+    with pytest.raises(L.LineError) as ei:
+        ctx.train_orders(64, 5, n, 9)
+    assert ei.value.status == L.LINE_ERR_STATE
+
+
 def test_resume_split_is_bitwise(ctx):
     from paper_2604_09419_gb300 import line as L
     g = G.graph("tiny")
