@@ -77,23 +77,64 @@ __device__ __forceinline__ int64_t lower_bound_i32(const int32_t* a, int64_t n, 
     return lo;
 }
 
+__device__ __forceinline__ void store_neg_weight(double d, int64_t v, double* __restrict__ x, float* __restrict__ deg) {
+    double r = 0.0;
+    if (d > 0.0) {
+        const double s = __dsqrt_rn(d);
+        r = __dmul_rn(s, __dsqrt_rn(s));
+    }
+    x[v] = r;
+    if (deg) deg[v] = (float)d;
+}
+
+// flag != 0 when some arc weight is not an integer in [1, 2^24].
+__global__ void k_weights_integral(int64_t n, const float* __restrict__ w, uint32_t* flag) {
+    bool bad = false;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const float v = w[e];
+        bad |= !(v >= 1.0f && v <= 16777216.0f && v == truncf(v));
+    }
+    if (__any_sync(0xFFFFFFFFu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1u);
+}
+
 // x_v = d(v)^0.75 = sqrt(d) * sqrt(sqrt(d)), d = weights of v's arcs summed in
-// arc order (src is sorted, so v's arcs are one contiguous range).
+// arc order (src is sorted, so v's arcs are one contiguous range).  Integer
+// weights (flag == 0): a warp per node sums them in 64-bit integers - exact,
+// so equal to the FP64 sum in arc order (partial sums stay below 2^53).
+__global__ void k_neg_weights_int(int64_t n_nodes, int64_t n_arcs, const int32_t* __restrict__ src,
+                                  const float* __restrict__ w, const uint32_t* flag, double* __restrict__ x,
+                                  float* __restrict__ deg) {
+    if (flag && *flag) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t v = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); v < n_nodes; v += warps) {
+        const int64_t lo = lower_bound_i32(src, n_arcs, (int32_t)v);
+        const int64_t hi = lower_bound_i32(src, n_arcs, (int32_t)(v + 1));
+        unsigned long long sum = 0;
+        if (w) {
+            for (int64_t e = lo + lane; e < hi; e += 32) sum += (unsigned long long)w[e];
+#pragma unroll
+            for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+        } else {
+            sum = (unsigned long long)(hi - lo);
+        }
+        if (lane == 0) store_neg_weight((double)sum, v, x, deg);
+    }
+}
+
+// Any other weights (flag != 0): one thread per node adds them in FP64 in arc
+// order.
 __global__ void k_neg_weights(int64_t n_nodes, int64_t n_arcs, const int32_t* __restrict__ src,
-                              const float* __restrict__ w, double* __restrict__ x, float* __restrict__ deg) {
+                              const float* __restrict__ w, const uint32_t* flag, double* __restrict__ x,
+                              float* __restrict__ deg) {
+    if (!*flag) return;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n_nodes;
          v += (int64_t)gridDim.x * blockDim.x) {
         const int64_t lo = lower_bound_i32(src, n_arcs, (int32_t)v);
         const int64_t hi = lower_bound_i32(src, n_arcs, (int32_t)(v + 1));
         double d = 0.0;
-        for (int64_t e = lo; e < hi; ++e) d = __dadd_rn(d, w ? (double)w[e] : 1.0);
-        double r = 0.0;
-        if (d > 0.0) {
-            const double s = __dsqrt_rn(d);
-            r = __dmul_rn(s, __dsqrt_rn(s));
-        }
-        x[v] = r;
-        if (deg) deg[v] = (float)d;
+        for (int64_t e = lo; e < hi; ++e) d = __dadd_rn(d, (double)w[e]);
+        store_neg_weight(d, v, x, deg);
     }
 }
 
@@ -295,8 +336,17 @@ cudaError_t edge_weights(int64_t n_arcs, const float* w, double* x, cudaStream_t
 }
 
 cudaError_t neg_weights(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const float* w, double* x, float* deg,
-                        cudaStream_t s) {
-    k_neg_weights<<<grid_for(n_nodes, 128, 1 << 20), 128, 0, s>>>(n_nodes, n_arcs, src, w, x, deg);
+                        uint32_t* flag, cudaStream_t s) {
+    if (!w) {  // unit weights: the arc counts
+        k_neg_weights_int<<<grid_for(n_nodes * 32, 256, 152 * 64), 256, 0, s>>>(n_nodes, n_arcs, src, w, nullptr, x,
+                                                                              deg);
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    k_weights_integral<<<grid_for(n_arcs, 256, 152 * 32), 256, 0, s>>>(n_arcs, w, flag);
+    k_neg_weights_int<<<grid_for(n_nodes * 32, 256, 152 * 64), 256, 0, s>>>(n_nodes, n_arcs, src, w, flag, x, deg);
+    k_neg_weights<<<grid_for(n_nodes, 128, 1 << 20), 128, 0, s>>>(n_nodes, n_arcs, src, w, flag, x, deg);
     return cudaGetLastError();
 }
 

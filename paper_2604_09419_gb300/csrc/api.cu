@@ -199,7 +199,7 @@ line_status line_build_alias(line_ctx* c, const line_graph_desc* g) {
         if ((e = alias_build(x, m, c->edge_tab, tmp, c->status, s)) != cudaSuccess) { result = cuda_fail(c, e, "edge alias"); break; }
         if ((result = check_status(c, "line_build_alias (edges)"))) break;
         // negative table: d(v)^0.75 (Eq. 1)
-        if ((e = neg_weights(n, m, c->src, w, x, c->deg, s)) != cudaSuccess) { result = cuda_fail(c, e, "degree weights"); break; }
+        if ((e = neg_weights(n, m, c->src, w, x, c->deg, c->flag + 1, s)) != cudaSuccess) { result = cuda_fail(c, e, "degree weights"); break; }
         if ((e = alias_build(x, n, c->neg_tab, tmp, c->status, s)) != cudaSuccess) { result = cuda_fail(c, e, "negative alias"); break; }
         if ((result = check_status(c, "line_build_alias (negatives)"))) break;
     } while (false);

@@ -56,7 +56,8 @@ __global__ void k_init_uniform(void* __restrict__ U, int dtype, int64_t n, int d
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int32_t qv = (int32_t)(ws[j] >> 8) - (1 << 23);
-            v[j] = (float)(((double)qv * (1.0 / 16777216.0)) / (double)dim);
+            // exact in FP32: |qv| < 2^23, and 2^-24 and dim are powers of two
+            v[j] = ((float)qv * (1.0f / 16777216.0f)) / (float)dim;
         }
         if (dtype == LINE_DTYPE_F32) {
             reinterpret_cast<float4*>(U)[q] = make_float4(v[0], v[1], v[2], v[3]);
