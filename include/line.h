@@ -293,6 +293,14 @@ LINE_API line_status line_mlp_create(line_ctx* ctx, int order, int hidden, int a
  * embedding (neighbours that are not known are left out of the mean). */
 LINE_API line_status line_mlp_features(line_ctx* ctx, const uint8_t* known);
 
+/* Recompute the inputs of the nodes rows[0 .. n_rows) only (a buffer of
+ * node ids), from the current graph and U table - for nodes that joined
+ * after line_mlp_features; the other nodes' inputs are unchanged.  Needs a
+ * line_mlp_features call first.  Errors: LINE_ERR_ARG (an id out of range;
+ * nothing is computed), LINE_ERR_STATE. */
+LINE_API line_status line_mlp_features_rows(line_ctx* ctx, const uint8_t* known, const int32_t* rows,
+                                            int64_t n_rows);
+
 /* Copy the inputs (n_nodes x P) as FP32 into `out` (a buffer). */
 LINE_API line_status line_mlp_get_features(line_ctx* ctx, float* out);
 

@@ -191,10 +191,14 @@ template <typename TX>
 __global__ void k_mlp_features(int64_t n_nodes, int64_t n_arcs, const int32_t* __restrict__ src,
                                const int32_t* __restrict__ dst, const float* __restrict__ deg, const void* U, int udt,
                                int D, const uint8_t* __restrict__ known, int P, TX* __restrict__ X,
-                               uint32_t* __restrict__ hubs, uint32_t* __restrict__ n_hubs) {
+                               uint32_t* __restrict__ hubs, uint32_t* __restrict__ n_hubs,
+                               const int32_t* __restrict__ rows, int64_t n_rows) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t v = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); v < n_nodes; v += warps) {
+    const int64_t count = rows ? n_rows : n_nodes;
+    for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < count; r += warps) {
+        const int64_t v = rows ? (int64_t)rows[r] : r;
+        if (v < 0 || v >= n_nodes) continue;  // rows are checked on the host
         const int64_t lo = lower_bound_src(src, n_arcs, (int32_t)v);
         const int64_t hi = lower_bound_src(src, n_arcs, (int32_t)(v + 1));
         if (hi - lo > kHubArcs) {
@@ -619,34 +623,57 @@ line_status line_mlp_create(line_ctx* c, int order, int hidden, int act_dtype, u
     return LINE_OK;
 }
 
-line_status line_mlp_features(line_ctx* c, const uint8_t* known) {
+// Inputs of the nodes rows[0 .. n_rows) (all nodes when rows is null).
+static line_status mlp_features_impl(line_ctx* c, const char* what, const uint8_t* known, const int32_t* rows,
+                                     int64_t n_rows) {
     line_status st = enter(c);
     if (st) return st;
-    if ((st = mlp_ready(c, "line_mlp_features", false))) return st;
-    if (!known) return fail(c, LINE_ERR_ARG, "line_mlp_features: null mask");
+    if ((st = mlp_ready(c, what, false))) return st;
+    if (!known) return fail(c, LINE_ERR_ARG, "%s: null mask", what);
+    if (rows && n_rows < 0) return fail(c, LINE_ERR_ARG, "%s: bad row count", what);
     MlpState& s = *c->mlp;
+    if (rows && !s.has_features) return fail(c, LINE_ERR_STATE, "%s: compute every node's inputs first", what);
+    if (rows && n_rows == 0) return LINE_OK;
     const Tables& t = c->tab[s.order];
     uint8_t* kd = nullptr;
     uint32_t* hubs = nullptr;  // [count] then the listed hub nodes
+    int32_t* rd = nullptr;
     const int64_t max_hubs = c->n_arcs / kHubArcs + 1;
     cudaError_t e = cudaMalloc(&kd, c->n_nodes);
     if (e == cudaSuccess) e = cudaMalloc(&hubs, sizeof(uint32_t) * (max_hubs + 1));
+    if (e == cudaSuccess && rows) e = cudaMalloc(&rd, sizeof(int32_t) * n_rows);
     if (e == cudaSuccess) e = cudaMemcpyAsync(kd, known, c->n_nodes, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess && rows) e = cudaMemcpyAsync(rd, rows, sizeof(int32_t) * n_rows, cudaMemcpyDefault, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(hubs, 0, sizeof(uint32_t), c->stream);
+    if (e == cudaSuccess && rows) {
+        // ids out of range are refused before any work
+        std::vector<int32_t> h(n_rows);
+        e = cudaMemcpyAsync(h.data(), rd, sizeof(int32_t) * n_rows, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+        for (int64_t i = 0; e == cudaSuccess && i < n_rows; ++i)
+            if (h[i] < 0 || h[i] >= c->n_nodes) {
+                cudaFree(kd);
+                cudaFree(hubs);
+                cudaFree(rd);
+                return fail(c, LINE_ERR_ARG, "%s: row id %d out of range", what, h[i]);
+            }
+    }
     if (e == cudaSuccess) {
-        const unsigned g = grid_of(c->n_nodes * 32, 256, 152 * 64);
+        const int64_t count = rows ? n_rows : c->n_nodes;
+        const unsigned g = grid_of(count * 32, 256, 152 * 64);
         const unsigned gh = (unsigned)std::min<int64_t>(max_hubs, 152 * 4);
         if (s.act == LINE_DTYPE_F32) {
             float* X = reinterpret_cast<float*>(s.X);
             k_mlp_features<float><<<g, 256, 0, c->stream>>>(c->n_nodes, c->n_arcs, c->src, c->dst, c->deg, t.U,
-                                                            t.dtype, s.dim, kd, s.P, X, hubs + 1, hubs);
+                                                            t.dtype, s.dim, kd, s.P, X, hubs + 1, hubs, rd, n_rows);
             k_mlp_features_hub<float><<<gh, kHubWarps * 32, 0, c->stream>>>(c->n_arcs, c->src, c->dst, c->deg, t.U,
                                                                              t.dtype, s.dim, kd, s.P, X, hubs + 1,
                                                                              hubs);
         } else {
             __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(s.X);
             k_mlp_features<__nv_bfloat16><<<g, 256, 0, c->stream>>>(c->n_nodes, c->n_arcs, c->src, c->dst, c->deg,
-                                                                    t.U, t.dtype, s.dim, kd, s.P, X, hubs + 1, hubs);
+                                                                    t.U, t.dtype, s.dim, kd, s.P, X, hubs + 1, hubs,
+                                                                    rd, n_rows);
             k_mlp_features_hub<__nv_bfloat16><<<gh, kHubWarps * 32, 0, c->stream>>>(
                 c->n_arcs, c->src, c->dst, c->deg, t.U, t.dtype, s.dim, kd, s.P, X, hubs + 1, hubs);
         }
@@ -655,9 +682,19 @@ line_status line_mlp_features(line_ctx* c, const uint8_t* known) {
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     if (kd) cudaFree(kd);
     if (hubs) cudaFree(hubs);
-    if (e != cudaSuccess) return cuda_fail(c, e, "line_mlp_features");
+    if (rd) cudaFree(rd);
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
     s.has_features = true;
     return LINE_OK;
+}
+
+line_status line_mlp_features(line_ctx* c, const uint8_t* known) {
+    return mlp_features_impl(c, "line_mlp_features", known, nullptr, 0);
+}
+
+line_status line_mlp_features_rows(line_ctx* c, const uint8_t* known, const int32_t* rows, int64_t n_rows) {
+    if (!rows) return c ? fail(c, LINE_ERR_ARG, "line_mlp_features_rows: null rows") : LINE_ERR_ARG;
+    return mlp_features_impl(c, "line_mlp_features_rows", known, rows, n_rows);
 }
 
 line_status line_mlp_get_features(line_ctx* c, float* out) {

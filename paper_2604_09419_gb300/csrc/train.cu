@@ -1415,18 +1415,19 @@ __global__ void k_prev_lookup(GroupParams q, const int32_t* __restrict__ rec, ui
 }
 
 // eta[b] = lr0 (schedule 0) or lr0 * max(1 - t0/T, floor) (schedule 1) for
-// the batch starting at global sample t0 = t_chunk + b * batch; FP64 once per
-// batch, used as FP32.
-__global__ void k_batch_eta(int n_batches, uint64_t t_chunk, int64_t batch, double lr0, int schedule, double floor_frac,
+// the batch starting at global sample t0 = t_chunk + b * batch, in FP32:
+// 1 - t0/T as (T - t0) / T from the exact integer difference.
+__global__ void k_batch_eta(int n_batches, uint64_t t_chunk, int64_t batch, float lr0, int schedule, float floor_frac,
                             uint64_t total, float* __restrict__ eta) {
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= n_batches) return;
-    double f = 1.0;
+    float f = 1.0f;
     if (schedule == 1) {
-        f = 1.0 - (double)(t_chunk + (uint64_t)b * (uint64_t)batch) / (double)total;
+        const uint64_t t0 = t_chunk + (uint64_t)b * (uint64_t)batch;
+        f = t0 >= total ? 0.0f : (float)(total - t0) / (float)total;
         if (f < floor_frac) f = floor_frac;
     }
-    eta[b] = (float)(lr0 * f);
+    eta[b] = lr0 * f;
 }
 
 // item_base[b] = first work item of batch b (sample items, then shared-segment items).
@@ -1837,8 +1838,9 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
             const int64_t work = cs * (a.K + 1);
             const unsigned g = (unsigned)std::min<int64_t>((work + 255) / 256, 152 * 64);
             k_chunk_draws<<<g, 256, 0, ps>>>(pp);
-            k_batch_eta<<<(unsigned)((cb + 127) / 128), 128, 0, ps>>>(cb, t, a.batch, a.lr0, a.lr_schedule, a.lr_floor,
-                                                                      a.lr_total, (float*)cset.eta.p);
+            k_batch_eta<<<(unsigned)((cb + 127) / 128), 128, 0, ps>>>(cb, t, a.batch, (float)a.lr0, a.lr_schedule,
+                                                                      (float)a.lr_floor, a.lr_total,
+                                                                      (float*)cset.eta.p);
         }
         gq.n_batches = cb;
         gq.chunk_samples = cs;

@@ -80,6 +80,7 @@ def _load():
         "line_eval_auc": (i32, [vp, i32, i32, vp, vp, i64, vp, vp, i64, vp, vp, ctypes.POINTER(dbl)]),
         "line_mlp_create": (i32, [vp, i32, i32, i32, u64]),
         "line_mlp_features": (i32, [vp, vp]),
+        "line_mlp_features_rows": (i32, [vp, vp, vp, i64]),
         "line_mlp_get_features": (i32, [vp, vp]),
         "line_mlp_get_params": (i32, [vp, vp, ctypes.POINTER(i64)]),
         "line_mlp_set_params": (i32, [vp, vp]),
@@ -104,7 +105,7 @@ lib = _load()
 EXPORTED = ("line_train_opts_default", "line_status_string", "line_create", "line_destroy", "line_last_error",
             "line_build_alias", "line_get_graph_info", "line_get_alias", "line_sample_debug",
             "line_init_embeddings", "line_train_steps", "line_train_orders", "line_get_embeddings", "line_set_embeddings",
-            "line_eval_loss", "line_eval_loss_noalloc", "line_eval_auc", "line_mlp_create", "line_mlp_features",
+            "line_eval_loss", "line_eval_loss_noalloc", "line_eval_auc", "line_mlp_create", "line_mlp_features", "line_mlp_features_rows",
             "line_mlp_get_features", "line_mlp_get_params", "line_mlp_set_params", "line_mlp_grad", "line_mlp_train",
             "line_mlp_predict", "line_autotune", "line_get_stats", "line_reset_stats", "line_synchronize", "line_debug_wait_timeout")
 
@@ -246,6 +247,9 @@ class Context:
 
     def mlp_features(self, known):
         return self._ck(lib.line_mlp_features(self.h, ptr(known)))
+
+    def mlp_features_rows(self, known, rows):
+        return self._ck(lib.line_mlp_features_rows(self.h, ptr(known), ptr(rows), int(rows.shape[0])))
 
     def mlp_get_features(self, out):
         return self._ck(lib.line_mlp_get_features(self.h, ptr(out)))

@@ -87,6 +87,37 @@ def test_features_match_oracle(ctx, name, dim, act):
     assert (err <= bound).all(), float((err - bound).max())
 
 
+def test_features_of_a_row_subset(ctx):
+    """Inputs recomputed for some rows after the graph changed equal a full
+    recomputation for those rows (same bits); the other rows keep theirs."""
+    from paper_2604_09419_gb300 import line as L
+    g = G.graph("rmat14")
+    held, kept = I.hold_out_nodes(g, 0.1, seed=3)
+    G.upload(ctx, kept)
+    U, C = trained_tables("rmat14", 64, 40_000, 6)
+    G.upload_tables(ctx, 2, U, C)
+    known = (~held).astype(np.uint8)
+    ctx.mlp_create(2, hidden=32, act_dtype=L.DTYPE_BF16, seed=1)
+    ctx.mlp_features(known)
+    before = np.empty((g.n_nodes, 80), np.float32)
+    ctx.mlp_get_features(before)
+    G.upload(ctx, g)  # the held-out nodes' arcs arrive; tables and MLP are kept
+    rows = np.flatnonzero(held).astype(np.int32)
+    ctx.mlp_features_rows(known, rows)
+    part = np.empty_like(before)
+    ctx.mlp_get_features(part)
+    ctx.mlp_features(known)
+    full = np.empty_like(before)
+    ctx.mlp_get_features(full)
+    assert np.array_equal(part[rows], full[rows])
+    rest = np.flatnonzero(~held)
+    assert np.array_equal(part[rest], before[rest])
+    assert not np.array_equal(before[rows], full[rows])  # their inputs did change
+    with pytest.raises(L.LineError) as ei:
+        ctx.mlp_features_rows(known, np.array([0, g.n_nodes], np.int32))
+    assert ei.value.status == L.LINE_ERR_ARG
+
+
 def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
