@@ -344,9 +344,160 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, int kslice, c
         }
 }
 
+// ---- the same contraction on the 5th-generation tensor cores (tcgen05) ----
+// One CTA (4 warps) per 128 x 64 tile of C and slice of K.  Per K step of 32
+// the threads stage A (128 x 32) and B (64 x 32) into shared memory as TF32
+// (rounded to nearest) in the no-swizzle K-major layout of 8-row x 16-byte
+// core matrices (byte (r, k) = (r/8) 1024 + (k/4) 128 + (r%8) 16 + (k%4) 4);
+// one thread issues four tcgen05.mma kind::tf32 (K = 8 each) accumulating
+// into a 128 x 64 FP32 tile in tensor memory and commits them to an
+// mbarrier; after the K loop each warp reads its 32 rows back with
+// tcgen05.ld.  Every wait is bounded: on a timeout the tile is not written
+// and the status word records it.
+constexpr int kTcM = 128, kTcN = 64, kTcK = 32;
+constexpr uint32_t kTcLbo = 128;                // next core matrix along K
+constexpr uint32_t kTcSbo = (kTcK / 4) * 128;  // next group of 8 rows
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: start >> 4, leading (K) byte offset >> 4,
+// stride (8-row) byte offset >> 4, the fixed 0b001 at bits 46-48, no swizzle.
+__device__ __forceinline__ uint64_t tc_smem_desc(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(kTcLbo >> 4) << 16) | ((uint64_t)(kTcSbo >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major,
+// N >> 3 at bits 17-22, M >> 4 at bits 24-28.
+constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
+                              ((uint32_t)(kTcM >> 4) << 24);
+
+__device__ __forceinline__ float to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+
 template <typename TA, typename TB, bool AK, bool BK>
-cudaError_t gemm(int M, int N, int K, int slices, const TA* A, int lda, const TB* B, int ldb, float* C,
-                 cudaStream_t s) {
+__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int kslice, const TA* __restrict__ A, int lda,
+                                                 const TB* __restrict__ B, int ldb, float* __restrict__ C,
+                                                 uint32_t* status) {
+    __shared__ __align__(1024) float sA[kTcM * kTcK];
+    __shared__ __align__(1024) float sB[kTcN * kTcK];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_base;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * kTcN;
+    const int kb = blockIdx.z * kslice, ke = min(K, kb + kslice);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(kTcN));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    uint32_t phase = 0;
+    bool ok = true;
+    bool first = true;
+    for (int k0 = kb; k0 < ke; k0 += kTcK) {
+        for (int i = tid; i < kTcM * kTcK; i += 128) {
+            const int r = AK ? i / kTcK : i % kTcM, k = AK ? i % kTcK : i / kTcM;
+            const int gm = m0 + r, gk = k0 + k;
+            float a = 0.0f;
+            if (gm < M && gk < ke) a = to_f(AK ? A[(size_t)gm * lda + gk] : A[(size_t)gk * lda + gm]);
+            sA[(r >> 3) * (kTcSbo / 4) + (k >> 2) * (kTcLbo / 4) + (r & 7) * 4 + (k & 3)] = to_tf32(a);
+        }
+        for (int i = tid; i < kTcN * kTcK; i += 128) {
+            const int r = BK ? i / kTcK : i % kTcN, k = BK ? i % kTcK : i / kTcN;
+            const int gn = n0 + r, gk = k0 + k;
+            float b = 0.0f;
+            if (gn < N && gk < ke) b = to_f(BK ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn]);
+            sB[(r >> 3) * (kTcSbo / 4) + (k >> 2) * (kTcLbo / 4) + (r & 7) * 4 + (k & 3)] = to_tf32(b);
+        }
+        asm volatile("fence.proxy.async.shared::cta;");  // the tensor core reads through the async proxy
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int kk = 0; kk < kTcK / 8; ++kk) {
+                const uint64_t da = tc_smem_desc(smem_addr(sA) + kk * 2 * kTcLbo);
+                const uint64_t db = tc_smem_desc(smem_addr(sB) + kk * 2 * kTcLbo);
+                const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                    "l"(da), "l"(db), "r"(kTcIdesc), "r"(acc));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_addr(&mbar)));
+        }
+        first = false;
+        // the tiles are restaged only after the MMAs that read them are done
+        uint32_t done = 0;
+        for (int it = 0; it < (1 << 22) && !done; ++it) {
+            asm volatile(
+                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+                : "=r"(done)
+                : "r"(smem_addr(&mbar)), "r"(phase));
+        }
+        phase ^= 1;
+        ok = ok && done;
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (!__syncthreads_and(ok)) break;
+    }
+    if (ok && !first) {
+        float* Cz = C + (size_t)blockIdx.z * M * N;
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll
+        for (int c0 = 0; c0 < kTcN; c0 += 16) {
+            uint32_t r[16];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                "[%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                  "=r"(r[15])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (row < M) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (n0 + c0 + j < N) Cz[(size_t)row * N + n0 + c0 + j] = __uint_as_float(r[j]);
+            }
+        }
+    } else if (!first) {
+        if (tid == 0) atomicOr(status, DEV_ERR_TIMEOUT);
+    } else {
+        // an empty K slice: the partial sum is zero
+        float* Cz = C + (size_t)blockIdx.z * M * N;
+        for (int i = tid; i < kTcM * kTcN; i += 128) {
+            const int r = m0 + i / kTcN, cc = n0 + i % kTcN;
+            if (r < M && cc < N) Cz[(size_t)r * N + cc] = 0.0f;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcN));
+}
+
+// C_z = A B over K slice z: on the tensor cores (TF32 operands) when tc is
+// set - the BF16-activation mode - else in FP32 on the CUDA cores.
+template <typename TA, typename TB, bool AK, bool BK>
+cudaError_t gemm(bool tc, int M, int N, int K, int slices, const TA* A, int lda, const TB* B, int ldb, float* C,
+                 uint32_t* status, cudaStream_t s) {
+    if (tc) {
+        const int kslice = ((K + slices - 1) / slices + kTcK - 1) / kTcK * kTcK;
+        const dim3 grid((N + kTcN - 1) / kTcN, (M + kTcM - 1) / kTcM, slices);
+        k_gemm_tc<TA, TB, AK, BK><<<grid, 128, 0, s>>>(M, N, K, kslice, A, lda, B, ldb, C, status);
+        return cudaGetLastError();
+    }
     const int kslice = ((K + slices - 1) / slices + kBK - 1) / kBK * kBK;
     const dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, slices);
     k_gemm<TA, TB, AK, BK><<<grid, 256, 0, s>>>(M, N, K, kslice, A, lda, B, ldb, C);
@@ -496,9 +647,12 @@ cudaError_t forward(MlpState& s, int64_t B, const Tables& t, bool targets, uint3
     k_mlp_gather<TX><<<grid_of(B * 32, 256), 256, 0, st>>>(s.rows, B, n_nodes, reinterpret_cast<const TX*>(s.X), s.P,
                                                             Xb, t.U, t.dtype, s.dim, targets ? s.Tb : nullptr, status);
     cudaError_t e;
-    if ((e = gemm<TX, float, true, true>((int)B, s.hidden, s.P, 1, Xb, s.P, W1, s.P, s.A1, st)) != cudaSuccess) return e;
+    const bool tc = s.act == LINE_DTYPE_BF16;
+    if ((e = gemm<TX, float, true, true>(tc, (int)B, s.hidden, s.P, 1, Xb, s.P, W1, s.P, s.A1, status, st)) !=
+        cudaSuccess)
+        return e;
     k_ep_hidden<TX><<<grid_of(B * s.hidden, 256), 256, 0, st>>>(s.A1, b1, B, s.hidden, Hb);
-    return gemm<TX, float, true, true>((int)B, s.dim, s.hidden, 1, Hb, s.hidden, W2, s.hidden, s.Yb, st);
+    return gemm<TX, float, true, true>(tc, (int)B, s.dim, s.hidden, 1, Hb, s.hidden, W2, s.hidden, s.Yb, status, st);
 }
 
 // Loss and gradients of the batch s.rows[0..B) into s.grads; the batch loss
@@ -514,22 +668,23 @@ cudaError_t loss_grad(MlpState& s, int64_t B, const Tables& t, uint32_t* status,
     const float scale = (float)(2.0 / ((double)B * s.dim));
     k_ep_loss<<<grid_of(B * 32, 256), 256, 0, st>>>(s.Yb, b2, s.Tb, B, s.dim, scale, s.rowloss);
     // dH = dY W2, then dA = dH GELU'(a)
-    if ((e = gemm<float, float, true, false>((int)B, s.hidden, s.dim, 1, s.Yb, s.dim, W2, s.hidden, s.dH, st)) !=
-        cudaSuccess)
+    const bool tc = s.act == LINE_DTYPE_BF16;
+    if ((e = gemm<float, float, true, false>(tc, (int)B, s.hidden, s.dim, 1, s.Yb, s.dim, W2, s.hidden, s.dH, status,
+                                             st)) != cudaSuccess)
         return e;
     k_ep_dact<<<grid_of(B * s.hidden, 256), 256, 0, st>>>(s.dH, s.A1, B * s.hidden);
     const TX* Xb = reinterpret_cast<const TX*>(s.Xb);
     const TX* Hb = reinterpret_cast<const TX*>(s.Hb);
     const int S = slices_for(B);
     // gW2 = dY^T H
-    if ((e = gemm<float, TX, false, false>(s.dim, s.hidden, (int)B, S, s.Yb, s.dim, Hb, s.hidden, s.part, st)) !=
-        cudaSuccess)
+    if ((e = gemm<float, TX, false, false>(tc, s.dim, s.hidden, (int)B, S, s.Yb, s.dim, Hb, s.hidden, s.part, status,
+                                           st)) != cudaSuccess)
         return e;
     k_sum_slices<<<grid_of((int64_t)s.dim * s.hidden, 256), 256, 0, st>>>(s.part, S, (int64_t)s.dim * s.hidden,
                                                                           s.grads + L.W2);
     // gW1 = dA^T X
-    if ((e = gemm<float, TX, false, false>(s.hidden, s.P, (int)B, S, s.dH, s.hidden, Xb, s.P, s.part, st)) !=
-        cudaSuccess)
+    if ((e = gemm<float, TX, false, false>(tc, s.hidden, s.P, (int)B, S, s.dH, s.hidden, Xb, s.P, s.part, status,
+                                           st)) != cudaSuccess)
         return e;
     k_sum_slices<<<grid_of((int64_t)s.hidden * s.P, 256), 256, 0, st>>>(s.part, S, (int64_t)s.hidden * s.P,
                                                                        s.grads + L.W1);
