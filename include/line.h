@@ -201,6 +201,7 @@ typedef struct {
     int n_batches;           /* 0..16 */
     uint64_t trial_samples;  /* samples per timed trial; 0: four pre-pass chunks */
     int try_persistent;      /* 1: also time the persistent schedule */
+    int both_orders;         /* 1: time line_train_orders on both orders' tables (order ignored) */
 } line_tune_opts;
 
 /* Autotuner of the launch configuration (not in the paper, whose CPU code
@@ -210,7 +211,8 @@ typedef struct {
  * listed batch size - it runs an untimed and a timed training run of
  * trial_samples on scratch copies of the order's tables, and writes the
  * fastest into *io (batch, warps_per_block, chunk_batches, mode, graph; the
- * other fields of *io are used as given).  The tables, the statistics and
+ * other fields of *io are used as given).  With topts->both_orders the trials
+ * train both orders concurrently (line_train_orders) and the rate counts both.  The tables, the statistics and
  * the learning-rate state of the caller are unchanged.  Changing the batch
  * size changes the results (minibatch semantics): list batch sizes only when
  * that is acceptable.  *best_rate (if not NULL): the winner's samples/s.

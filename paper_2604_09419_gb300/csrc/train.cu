@@ -44,6 +44,7 @@
 //                         b's shared segments, then b+1's ...) and waits,
 //                         with bounded spins, only on the items it depends on.
 #include <algorithm>
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -1539,6 +1540,17 @@ static uint32_t bits_for(uint64_t v) {  // bits to hold values 0..v-1
     return b;
 }
 
+// Runs f once per device (function attributes are per device); thread-safe.
+template <typename F>
+static void once_per_device(std::atomic<uint64_t>& done, F f) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (done.load(std::memory_order_acquire) & bit) return;
+    f();
+    done.fetch_or(bit, std::memory_order_acq_rel);
+}
+
 template <int D, int DT>
 static int gather_warps(const DataParams& p, int requested, int cap, size_t* smem_out, int dflt = 8) {
     using G = Geom<D, DT>;
@@ -1573,12 +1585,11 @@ static cudaError_t launch_data_batched(const DataParams& p, int warps_per_block,
     size_t smem = 0;
     // 4 warps per block: at ~70 registers a 4096-sample batch is one wave
     const int wpb = gather_warps<D, DT>(p, warps_per_block, kGatherWarps, &smem, kGatherWarps);
-    static bool attr_set = false;
-    if (!attr_set) {
+    static std::atomic<uint64_t> attr_set{0};
+    once_per_device(attr_set, [] {
         cudaFuncSetAttribute(k_gather<D, DT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
         cudaFuncSetAttribute(k_gather<D, DT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-        attr_set = true;
-    }
+    });
     const int64_t per_block = (int64_t)wpb * G::GPW;
     const int64_t apply_per_block = (int64_t)(kApplyThreads / 32) * G::GPW;
     // long shared segments (more than kChunk entries, ~34 per batch on R-MAT 20)
@@ -1608,11 +1619,9 @@ template <int D, int DT>
 static cudaError_t launch_data_persistent(const DataParams& p, int warps_per_block, cudaStream_t s) {
     size_t smem = 0;
     const int wpb = gather_warps<D, DT>(p, warps_per_block, kPersistThreads / 32, &smem);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_persistent<D, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
-        attr_set = true;
-    }
+    static std::atomic<uint64_t> attr_set{0};
+    once_per_device(attr_set,
+                    [] { cudaFuncSetAttribute(k_persistent<D, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem); });
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

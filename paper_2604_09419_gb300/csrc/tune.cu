@@ -18,11 +18,13 @@ line_status line_autotune(line_ctx* c, int order, int dim, int K, const line_lr*
     if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_autotune: no graph");
     if (order != 1 && order != 2) return fail(c, LINE_ERR_ARG, "line_autotune: order must be 1 or 2");
     if (!io || !lr) return fail(c, LINE_ERR_ARG, "line_autotune: null options");
-    Tables& t = c->tab[order];
-    if (!t.ready || t.dim != dim)
-        return fail(c, LINE_ERR_STATE, "line_autotune: tables of order %d and dim %d not initialised", order, dim);
     line_tune_opts to{};
     if (topts) to = *topts;
+    // the tables the trials train: order `order`, or both orders
+    std::vector<int> orders = to.both_orders ? std::vector<int>{1, 2} : std::vector<int>{order};
+    for (int o : orders)
+        if (!c->tab[o].ready || c->tab[o].dim != dim)
+            return fail(c, LINE_ERR_STATE, "line_autotune: tables of order %d and dim %d not initialised", o, dim);
     if (to.n_batches < 0 || to.n_batches > 16 || (to.n_batches > 0 && !to.batches))
         return fail(c, LINE_ERR_ARG, "line_autotune: bad batch list");
     std::vector<int64_t> batches;
@@ -46,22 +48,42 @@ line_status line_autotune(line_ctx* c, int order, int dim, int K, const line_lr*
         }
     }
     // scratch copies of the tables: the trials train on them
-    const size_t bytes = (size_t)c->n_nodes * dim * elem_size(t.dtype);
-    void* sU = nullptr;
-    void* sC = nullptr;
-    CK(cudaMalloc(&sU, bytes), "line_autotune: scratch tables");
-    cudaError_t e = cudaMemcpyAsync(sU, t.U, bytes, cudaMemcpyDeviceToDevice, c->stream);
-    if (e == cudaSuccess && t.C) e = cudaMalloc(&sC, bytes);
-    if (e == cudaSuccess && t.C) e = cudaMemcpyAsync(sC, t.C, bytes, cudaMemcpyDeviceToDevice, c->stream);
+    struct Saved {
+        int order;
+        void* U;
+        void* C;
+    };
+    std::vector<Saved> saved;
+    std::vector<void*> scratch;
+    cudaError_t e = cudaSuccess;
+    for (int o : orders) {
+        Tables& t = c->tab[o];
+        const size_t bytes = (size_t)c->n_nodes * dim * elem_size(t.dtype);
+        void* sU = nullptr;
+        void* sC = nullptr;
+        if (e == cudaSuccess) e = cudaMalloc(&sU, bytes);
+        if (sU) scratch.push_back(sU);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(sU, t.U, bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e == cudaSuccess && t.C) e = cudaMalloc(&sC, bytes);
+        if (sC) scratch.push_back(sC);
+        if (e == cudaSuccess && t.C) e = cudaMemcpyAsync(sC, t.C, bytes, cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) break;
+        saved.push_back({o, t.U, t.C});
+        t.U = sU;
+        t.C = sC;
+    }
+    auto restore = [&] {
+        cudaStreamSynchronize(c->stream);
+        for (const Saved& sv : saved) {
+            c->tab[sv.order].U = sv.U;
+            c->tab[sv.order].C = sv.C;
+        }
+        for (void* p : scratch) cudaFree(p);
+    };
     if (e != cudaSuccess) {
-        if (sU) cudaFree(sU);
-        if (sC) cudaFree(sC);
+        restore();
         return cuda_fail(c, e, "line_autotune: scratch tables");
     }
-    void* realU = t.U;
-    void* realC = t.C;
-    t.U = sU;
-    t.C = sC;
     const TrainTimes saved_times = c->times;
     const double saved_ms = c->total_ms;
     const uint64_t saved_samples = c->total_samples;
@@ -83,16 +105,20 @@ line_status line_autotune(line_ctx* c, int order, int dim, int K, const line_lr*
         uint64_t n = to.trial_samples ? to.trial_samples : (uint64_t)4 * cd.cb * cd.batch;
         n = (n + cd.batch - 1) / cd.batch * cd.batch;
         // one untimed run (allocations, graph capture), then the timed one
-        st = line_train_steps(c, order, dim, K, lr, n, 0x5EED, &o);
+        auto trial = [&] {
+            return to.both_orders ? line_train_orders(c, dim, K, lr, n, 0x5EED, &o)
+                                  : line_train_steps(c, order, dim, K, lr, n, 0x5EED, &o);
+        };
+        st = trial();
         if (st) break;
         if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) break;
-        st = line_train_steps(c, order, dim, K, lr, n, 0x5EED, &o);
+        st = trial();
         if (st) break;
         if ((e = cudaEventRecord(e1, c->stream)) != cudaSuccess) break;
         if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
         float ms = 0.0f;
         cudaEventElapsedTime(&ms, e0, e1);
-        const double rate = ms > 0.0f ? (double)n / (ms * 1e-3) : 0.0;
+        const double rate = ms > 0.0f ? (double)n * orders.size() / (ms * 1e-3) : 0.0;
         if (rate > best) {
             best = rate;
             win = cd;
@@ -100,11 +126,7 @@ line_status line_autotune(line_ctx* c, int order, int dim, int K, const line_lr*
     }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    cudaStreamSynchronize(c->stream);
-    t.U = realU;
-    t.C = realC;
-    cudaFree(sU);
-    if (sC) cudaFree(sC);
+    restore();
     c->times = saved_times;
     c->total_ms = saved_ms;
     c->total_samples = saved_samples;

@@ -45,7 +45,7 @@ class TrainOpts(ctypes.Structure):
 
 class TuneOpts(ctypes.Structure):
     _fields_ = [("batches", ctypes.c_void_p), ("n_batches", ctypes.c_int), ("trial_samples", ctypes.c_uint64),
-                ("try_persistent", ctypes.c_int)]
+                ("try_persistent", ctypes.c_int), ("both_orders", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -227,15 +227,15 @@ class Context:
                                    ctypes.byref(out)))
         return out.value, (int(counts[0]), int(counts[1]))
 
-    def autotune(self, order, dim, K, *, batches=None, trial_samples=0, try_persistent=False, lr0=0.025,
-                 schedule=1, floor_frac=1e-4, total=0, opts: TrainOpts | None = None):
+    def autotune(self, order, dim, K, *, batches=None, trial_samples=0, try_persistent=False, both_orders=False,
+                 lr0=0.025, schedule=1, floor_frac=1e-4, total=0, opts: TrainOpts | None = None):
         """Fastest launch configuration on scratch copies of the tables;
         returns (TrainOpts, samples/s)."""
         lr = LR(lr0, schedule, floor_frac, total)
         o = opts if opts is not None else train_opts_default()
         arr = None if not batches else np.asarray(batches, np.int64)
         t = TuneOpts(None if arr is None else arr.ctypes.data, 0 if arr is None else len(arr), trial_samples,
-                     1 if try_persistent else 0)
+                     1 if try_persistent else 0, 1 if both_orders else 0)
         rate = ctypes.c_double()
         self._ck(lib.line_autotune(self.h, order, dim, K, ctypes.byref(lr), ctypes.byref(t), ctypes.byref(o),
                                    ctypes.byref(rate)))

@@ -168,6 +168,16 @@ def test_autotune_keeps_tables_and_returns_a_valid_configuration(ctx):
     a = _run(ctx, g, 2, 64, 5, 50_000, o.batch)
     b = _run(ctx, g, 2, 64, 5, 50_000, o.batch, opts=o)
     assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    # both orders at once: both tables untouched
+    ctx.init_embeddings(1, 64, L.DTYPE_F32, seed=3)
+    ctx.init_embeddings(2, 64, L.DTYPE_F32, seed=4)
+    V1, _ = G.tables(ctx, g, 1, 64)
+    V2, W2 = G.tables(ctx, g, 2, 64)
+    o2, rate2 = ctx.autotune(1, 64, 5, batches=[2048, 4096], trial_samples=65_536, both_orders=True)
+    assert rate2 > 0 and o2.batch in (2048, 4096)
+    X1, _ = G.tables(ctx, g, 1, 64)
+    X2, Y2 = G.tables(ctx, g, 2, 64)
+    assert np.array_equal(V1, X1) and np.array_equal(V2, X2) and np.array_equal(W2, Y2)
 
 
 @pytest.mark.parametrize("dtype,cb", [(0, 0), (0, 3), (1, 2)])
