@@ -92,7 +92,14 @@ def lib():
             L.orc_batch_lr.argtypes = [_dbl, _int, _dbl, _u64, _u64]
             L.orc_batch_lr.restype = _dbl
             L.orc_train.argtypes = TABLE_ARGS + [_int, _int, _int, _dbl, _int, _dbl, _u64, _u64, _u64,
-                                                 _i64, _dbl, _dbl, _u64, _f64p, ctypes.c_void_p]
+                                                 _i64, _dbl, _dbl, _u64, _f64p, ctypes.c_void_p, ctypes.c_void_p,
+                                                 _int, _int]
+            L.orc_walk_cumw.argtypes = [_i64, _i32p, ctypes.c_void_p, _f64p]
+            L.orc_walk_cumw.restype = None
+            L.orc_walk_pairs_per_walk.argtypes = [_int, _int]
+            L.orc_walk_pairs_per_walk.restype = _i64
+            L.orc_sample_walk.argtypes = TABLE_ARGS + [_f64p, _u64, _u64, _i64, _int, _int, _int, _i32p]
+            L.orc_sample_walk.restype = _int
             L.orc_train.restype = _int
             L.orc_eval_loss.argtypes = TABLE_ARGS + [_int, _int, _int, _u64, _i64, _f64p, ctypes.c_void_p]
             L.orc_eval_loss.restype = _dbl
@@ -202,18 +209,42 @@ def batch_lr(lr0, schedule, floor_frac, total, t0) -> float:
     return lib().orc_batch_lr(lr0, schedule, floor_frac, total, t0)
 
 
+def walk_cumw(g) -> np.ndarray:
+    """Cumulative arc weights per node, FP64 in arc order (the walk sampler's table)."""
+    cw = np.zeros(g.n_arcs, np.float64)
+    w = None if g.w is None else np.ascontiguousarray(g.w, np.float32)
+    lib().orc_walk_cumw(g.n_arcs, np.ascontiguousarray(g.src, np.int32), None if w is None else w.ctypes.data, cw)
+    return cw
+
+
+def walk_pairs_per_walk(L: int, W: int) -> int:
+    return lib().orc_walk_pairs_per_walk(L, W)
+
+
+def sample_walk(T: Tables, cw: np.ndarray, seed: int, t0: int, count: int, K: int, L: int, W: int) -> np.ndarray:
+    """[count][K+2] records of the walk sampler (Algorithms 2-3, local walk)."""
+    out = np.zeros((count, K + 2), np.int32)
+    rc = lib().orc_sample_walk(*T.args(), cw, seed, t0, count, K, L, W, out.reshape(-1))
+    if rc:
+        raise ValueError(f"orc_sample_walk failed ({rc})")
+    return out
+
+
 def train(T: Tables, U: np.ndarray, C, *, order: int, K: int, lr0: float = 0.025, schedule: int = 1,
           lr_floor_frac: float = 1e-4, lr_total: int = 0, n_samples: int, seed: int, batch: int,
-          lam: float = 0.0, alpha_neg: float = 1.0, sample_offset: int = 0):
-    """Minibatch-synchronous LINE in place on FP64 tables U (and C for order 2)."""
+          lam: float = 0.0, alpha_neg: float = 1.0, sample_offset: int = 0, walk=None):
+    """Minibatch-synchronous LINE in place on FP64 tables U (and C for order 2).
+    walk: None (arcs drawn by weight) or (cw, L, W) for the walk sampler."""
     assert U.dtype == np.float64 and U.flags.c_contiguous
     dim = U.shape[1]
     cptr = None
     if order == 2:
         assert C is not None and C.dtype == np.float64 and C.flags.c_contiguous and C.shape == U.shape
         cptr = C.ctypes.data
+    cw, L, W = walk if walk is not None else (None, 0, 0)
     rc = lib().orc_train(*T.args(), order, dim, K, lr0, schedule, lr_floor_frac, lr_total, n_samples,
-                         seed, batch, lam, alpha_neg, sample_offset, U, cptr)
+                         seed, batch, lam, alpha_neg, sample_offset, U, cptr,
+                         None if cw is None else cw.ctypes.data, L, W)
     if rc:
         raise ValueError(f"orc_train failed ({rc})")
 

@@ -266,6 +266,116 @@ int orc_sample(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_
 }
 
 /* ------------------------------------------------------------------------ */
+/* Walk sampler: the positive pairs of a random walk (Algorithms 2-3, the    */
+/* local walk of one partition).  Walk wk starts at an arc drawn by weight   */
+/* (draw wk of domain 8, call 0): nodes[0] = src, nodes[1] = dst.  Step i    */
+/* (i = 1 .. L-1) moves from x = nodes[i] to an out-neighbour drawn by arc   */
+/* weight: with words (w0, w1) of draw wk, call i, domain 8,                 */
+/* u = ((w1:w0) >> 11) 2^-53 and target = u * d(x), the first arc e of x     */
+/* whose cumulative weight cw[e] > target (the last arc if none); a node     */
+/* without out-arcs steps back to nodes[i-1].  The pairs of a walk are       */
+/* (nodes[i], nodes[i+k]) for i = 0 .. L-1, k = 1 .. W, i + k <= L, in       */
+/* (i, k) order: P = L W - W (W - 1) / 2 of them.  Sample t takes pair       */
+/* t mod P of walk t / P; its negatives are the edge sampler's (domain 0,    */
+/* calls 1..K at counter t).                                                 */
+/* ------------------------------------------------------------------------ */
+#define WALK_DOMAIN 8u
+
+/* cw[e] = sum of the weights of src[e]'s arcs up to and including e, FP64 in
+ * arc order (src sorted). */
+void orc_walk_cumw(int64_t n_arcs, const int32_t* src, const float* w, double* cw) {
+    double run = 0.0;
+    for (int64_t e = 0; e < n_arcs; ++e) {
+        if (e == 0 || src[e] != src[e - 1]) run = 0.0;
+        run += w ? (double)w[e] : 1.0;
+        cw[e] = run;
+    }
+}
+
+typedef struct {
+    orc_tables T;
+    const double* cw;
+} orc_walker;
+
+static int64_t first_arc_of(const orc_tables* T, int32_t v) {
+    int64_t lo = 0, hi = T->n_arcs;
+    while (lo < hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (T->src[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+static int32_t walk_step(const orc_walker* W, int32_t x, int32_t prev, const uint32_t w[4]) {
+    int64_t lo = first_arc_of(&W->T, x), hi = first_arc_of(&W->T, x + 1);
+    if (lo == hi) return prev;  /* a dead end steps back */
+    uint64_t r = (((uint64_t)w[1] << 32) | (uint64_t)w[0]) >> 11;
+    double u = (double)r * (1.0 / 9007199254740992.0);
+    double target = u * W->cw[hi - 1];
+    /* the first arc whose cumulative weight exceeds the target, by scanning */
+    for (int64_t e = lo; e < hi; ++e)
+        if (W->cw[e] > target) return W->T.dst[e];
+    return W->T.dst[hi - 1];
+}
+
+/* nodes[0 .. L] of walk wk */
+static void walk_nodes(const orc_walker* W, uint64_t seed, uint64_t wk, int L, int32_t* nodes) {
+    uint32_t w[4];
+    draw_words(seed, WALK_DOMAIN, wk, 0, w);
+    uint32_t e = alias_draw(W->T.n_arcs, W->T.thr_e, W->T.alias_e, w[0], w[1], w[2]);
+    nodes[0] = W->T.src[e];
+    nodes[1] = W->T.dst[e];
+    for (int i = 1; i < L; ++i) {
+        draw_words(seed, WALK_DOMAIN, wk, (uint32_t)i, w);
+        nodes[i + 1] = walk_step(W, nodes[i], nodes[i - 1], w);
+    }
+}
+
+int64_t orc_walk_pairs_per_walk(int L, int Wn) { return (int64_t)L * Wn - (int64_t)Wn * (Wn - 1) / 2; }
+
+/* pair p of a walk as (i, k), by counting the pairs of each node in order */
+static void walk_pair(int L, int Wn, int64_t p, int* i_out, int* k_out) {
+    for (int i = 0; i < L; ++i) {
+        int n = Wn < L - i ? Wn : L - i;
+        if (p < n) { *i_out = i; *k_out = (int)p + 1; return; }
+        p -= n;
+    }
+    *i_out = 0;
+    *k_out = 1;
+}
+
+static void sample_walk_one(const orc_walker* W, uint64_t seed, uint64_t t, int K, int L, int Wn, int32_t* nodes,
+                            int64_t* cached, int32_t* rec) {
+    int64_t P = orc_walk_pairs_per_walk(L, Wn);
+    uint64_t wk = t / (uint64_t)P;
+    if (*cached != (int64_t)wk) { walk_nodes(W, seed, wk, L, nodes); *cached = (int64_t)wk; }
+    int i, k;
+    walk_pair(L, Wn, (int64_t)(t % (uint64_t)P), &i, &k);
+    rec[0] = nodes[i];
+    rec[1] = nodes[i + k];
+    uint32_t w[4];
+    for (int j = 1; j <= K; ++j) {
+        draw_words(seed, 0, t, (uint32_t)j, w);
+        rec[1 + j] = (int32_t)alias_draw(W->T.n_nodes, W->T.thr_n, W->T.alias_n, w[0], w[1], w[2]);
+    }
+}
+
+int orc_sample_walk(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t* dst,
+                    const uint32_t* thr_e, const uint32_t* alias_e, const uint32_t* thr_n, const uint32_t* alias_n,
+                    const double* cw, uint64_t seed, uint64_t t0, int64_t count, int K, int L, int Wn,
+                    int32_t* out) {
+    if (L < 1 || Wn < 1 || Wn > L) return -1;
+    orc_walker W = {{n_nodes, n_arcs, src, dst, thr_e, alias_e, thr_n, alias_n}, cw};
+    int32_t* nodes = (int32_t*)malloc(sizeof(int32_t) * (size_t)(L + 1));
+    if (!nodes) return -2;
+    int64_t cached = -1;
+    for (int64_t i = 0; i < count; ++i)
+        sample_walk_one(&W, seed, t0 + (uint64_t)i, K, L, Wn, nodes, &cached, out + i * (K + 2));
+    free(nodes);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Initialisation: U[i][k] = ((w >> 8) - 2^23) * 2^-24 / dim, w = word       */
 /* (k mod 4) of the draw at counter (i_lo, i_hi, k / 4, 1): uniform on       */
 /* [-0.5/dim, 0.5/dim).  C = 0.                                              */
@@ -314,9 +424,13 @@ int orc_train(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t
               const uint32_t* thr_e, const uint32_t* alias_e, const uint32_t* thr_n, const uint32_t* alias_n,
               int order, int dim, int K, double lr0, int schedule, double lr_floor_frac, uint64_t lr_total,
               uint64_t n_samples, uint64_t seed, int64_t batch, double lambda, double alpha_neg,
-              uint64_t sample_offset, double* U, double* C) {
+              uint64_t sample_offset, double* U, double* C, const double* walk_cw, int walk_len, int window) {
     if (batch <= 0 || dim <= 0 || K < 0 || (order != 1 && order != 2)) return -1;
+    if (walk_cw && (walk_len < 1 || window < 1 || window > walk_len)) return -1;
     orc_tables T = {n_nodes, n_arcs, src, dst, thr_e, alias_e, thr_n, alias_n};
+    orc_walker Wk = {T, walk_cw};
+    int32_t* wnodes = walk_cw ? (int32_t*)malloc(sizeof(int32_t) * (size_t)(walk_len + 1)) : NULL;
+    int64_t wcached = -1;
     double* Ctx = order == 2 ? C : U;
     double* dU = (double*)calloc((size_t)n_nodes * (size_t)dim, sizeof(double));
     double* dC = order == 2 ? (double*)calloc((size_t)n_nodes * (size_t)dim, sizeof(double)) : dU;
@@ -334,7 +448,8 @@ int orc_train(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t
         int32_t* rows_u = rows;
         int32_t* rows_c = rows + batch * (K + 2);
         for (uint64_t t = t0; t < t1; ++t) {
-            sample_one(&T, seed, 0, t, K, rec);
+            if (walk_cw) sample_walk_one(&Wk, seed, t, K, walk_len, window, wnodes, &wcached, rec);
+            else sample_one(&T, seed, 0, t, K, rec);
             int32_t x = rec[0];
             for (int j = 0; j <= K; ++j) {
                 int32_t y = rec[1 + j];
@@ -370,6 +485,7 @@ int orc_train(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t
     }
     free(rec);
     free(rows);
+    free(wnodes);
     if (order == 2) { free(dC); free(touchC); }
     free(dU);
     free(touchU);
