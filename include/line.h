@@ -107,6 +107,10 @@ typedef struct {
     int timing;              /* 1: time the training kernels with CUDA events (line_get_stats) */
     int graph;               /* 1: batched mode replays each full chunk's launches from a
                                 captured CUDA graph (same results); 0: direct launches */
+    int walk_length;         /* L > 0: positive pairs from random walks of L steps
+                                (Algorithms 2-3, see line_sample_walk_debug); 0: arcs
+                                drawn by weight (Eq. 1).  At most 1024. */
+    int window;              /* W: pair window of the walk sampler, 1 <= W <= L */
 } line_train_opts;
 
 /* Per-kernel timing collected when opts.timing == 1 (reset by line_reset_stats). */
@@ -159,6 +163,25 @@ LINE_API line_status line_get_alias(line_ctx* ctx, int table, uint32_t* thr, uin
  * out[count][K+2] = (u, v, n_1 .. n_K) (a buffer). */
 LINE_API line_status line_sample_debug(line_ctx* ctx, int K, uint64_t seed, uint32_t domain, uint64_t t0,
                               int64_t count, int32_t* out);
+
+/* Walk sampler (Algorithms 2-3, the local walk of one partition): write the
+ * records of samples t0 .. t0+count-1 as out[count][K+2] = (u, v, n_1 .. n_K)
+ * (a host or device buffer).  Sample t takes pair t mod P of walk t / P,
+ * P = L W - W (W - 1) / 2.  Walk wk starts at the arc drawn from the edge
+ * alias table with draw (wk, call 0) of domain 8: nodes[0] = src,
+ * nodes[1] = dst.  Step i = 1 .. L-1 leaves x = nodes[i] by the first of its
+ * arcs e whose running FP64 weight sum cw[e] (arc order) exceeds
+ * u * cw[last arc of x], u = ((w1:w0) >> 11) 2^-53 from words w0, w1 of draw
+ * (wk, call i) of domain 8 (the last arc if none does); a node without
+ * out-arcs steps back to nodes[i-1].  The pairs of a walk are
+ * (nodes[i], nodes[i+k]), i = 0 .. L-1, k = 1 .. W, i + k <= L, in (i, k)
+ * order.  Negatives are the edge sampler's (domain 0, calls 1..K at counter
+ * t).  The first call builds the per-node arc offsets and weight sums
+ * (12 bytes per arc with the kept weights, 8 per node), freed with the graph.
+ * Errors: LINE_ERR_ARG (K, count, or not 1 <= W <= L <= 1024),
+ * LINE_ERR_STATE (no graph). */
+LINE_API line_status line_sample_walk_debug(line_ctx* ctx, int K, uint64_t seed, int walk_length, int window,
+                                            uint64_t t0, int64_t count, int32_t* out);
 
 /* (Re)create the tables of one order: order 1 has U only (the context of a
  * pair is U, first-order proximity), order 2 has U and C (second order).

@@ -56,6 +56,23 @@ line_status check_status(line_ctx* c, const char* what, bool timeout_sticky) {
     return LINE_OK;
 }
 
+line_status ensure_walk_tables(line_ctx* c) {
+    if (c->cw) return LINE_OK;
+    int64_t* rp = nullptr;
+    double* cw = nullptr;
+    cudaError_t e = cudaMalloc(&rp, sizeof(int64_t) * (size_t)(c->n_nodes + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&cw, sizeof(double) * (size_t)c->n_arcs);
+    if (e == cudaSuccess) e = walk_tables(c->n_nodes, c->n_arcs, c->src, c->w, rp, cw, c->stream);
+    if (e != cudaSuccess) {
+        if (rp) cudaFree(rp);
+        if (cw) cudaFree(cw);
+        return cuda_fail(c, e, "walk sampler tables");
+    }
+    c->row_ptr = rp;
+    c->cw = cw;
+    return LINE_OK;
+}
+
 
 }  // namespace line
 
@@ -68,10 +85,14 @@ void free_tables(Tables& t) {
 }
 
 void free_graph(line_ctx* c, bool keep_tables = false) {
-    for (void* p : {(void*)c->src, (void*)c->dst, (void*)c->deg, (void*)c->edge_tab, (void*)c->neg_tab})
+    for (void* p : {(void*)c->src, (void*)c->dst, (void*)c->deg, (void*)c->edge_tab, (void*)c->neg_tab, (void*)c->w,
+                    (void*)c->row_ptr, (void*)c->cw})
         if (p) cudaFree(p);
     c->src = c->dst = nullptr;
     c->deg = nullptr;
+    c->w = nullptr;
+    c->row_ptr = nullptr;
+    c->cw = nullptr;
     c->edge_tab = c->neg_tab = nullptr;
     c->has_graph = false;
     if (keep_tables) return;
@@ -98,6 +119,8 @@ void line_train_opts_default(line_train_opts* o) {
     o->warps_per_block = 0;
     o->timing = 0;
     o->graph = 1;
+    o->walk_length = 0;
+    o->window = 0;
 }
 
 const char* line_status_string(line_status s) {
@@ -203,7 +226,7 @@ line_status line_build_alias(line_ctx* c, const line_graph_desc* g) {
         if ((e = alias_build(x, n, c->neg_tab, tmp, c->status, s)) != cudaSuccess) { result = cuda_fail(c, e, "negative alias"); break; }
         if ((result = check_status(c, "line_build_alias (negatives)"))) break;
     } while (false);
-    if (w) cudaFree(w);
+    c->w = w;  // kept for the walk sampler's tables (freed with the graph)
     if (x) cudaFree(x);
     if (tmp) cudaFree(tmp);
     if (result != LINE_OK) {
@@ -267,6 +290,53 @@ line_status line_sample_debug(line_ctx* c, int K, uint64_t seed, uint32_t domain
     return LINE_OK;
 }
 
+line_status line_sample_walk_debug(line_ctx* c, int K, uint64_t seed, int walk_length, int window, uint64_t t0,
+                                   int64_t count, int32_t* out) {
+    line_status st = enter(c);
+    if (st) return st;
+    if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_sample_walk_debug: no graph");
+    if (K < 0 || K > kMaxK || count < 0 || (!out && count > 0))
+        return fail(c, LINE_ERR_ARG, "line_sample_walk_debug: bad arguments");
+    if (walk_length < 1 || walk_length > kMaxWalkLen || window < 1 || window > walk_length)
+        return fail(c, LINE_ERR_ARG, "line_sample_walk_debug: need 1 <= window <= walk_length <= %d", kMaxWalkLen);
+    if (count == 0) return LINE_OK;
+    if ((st = ensure_walk_tables(c))) return st;
+    int32_t* buf = nullptr;
+    const size_t bytes = sizeof(int32_t) * (size_t)count * (K + 2);
+    cudaPointerAttributes attr;
+    bool dev_out = cudaPointerGetAttributes(&attr, out) == cudaSuccess && attr.type == cudaMemoryTypeDevice;
+    cudaGetLastError();
+    if (!dev_out) CK(cudaMalloc(&buf, bytes), "sample scratch");
+    int32_t* rec = dev_out ? out : buf;
+    // negatives: the edge sampler's draws (domain 0, calls 1..K); its slots 0
+    // and 1 are then overwritten by the walk pairs
+    cudaError_t e = sample_records(c->src, c->dst, c->edge_tab, c->n_arcs, c->neg_tab, c->n_nodes, seed, 0u, t0,
+                                   count, K, rec, c->stream);
+    if (e == cudaSuccess) {
+        WalkParams wp{};
+        wp.src = c->src;
+        wp.dst = c->dst;
+        wp.edge_tab = c->edge_tab;
+        wp.n_arcs = c->n_arcs;
+        wp.row_ptr = c->row_ptr;
+        wp.cw = c->cw;
+        wp.seed = seed;
+        wp.t0 = t0;
+        wp.count = count;
+        wp.L = walk_length;
+        wp.W = window;
+        wp.P = (uint64_t)walk_length * window - (uint64_t)window * (window - 1) / 2;
+        wp.R = (uint64_t)(K + 2);
+        wp.rec = rec;
+        e = walk_pairs(wp, c->stream);
+    }
+    if (e == cudaSuccess && !dev_out) e = cudaMemcpyAsync(out, buf, bytes, cudaMemcpyDefault, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (buf) cudaFree(buf);
+    if (e != cudaSuccess) return cuda_fail(c, e, "line_sample_walk_debug");
+    return LINE_OK;
+}
+
 line_status line_init_embeddings(line_ctx* c, int order, int dim, int dtype, uint64_t seed) {
     line_status st = enter(c);
     if (st) return st;
@@ -311,6 +381,13 @@ line_status make_train_args(line_ctx* c, const char* what, int order, int dim, i
     if (o.mode != LINE_MODE_BATCHED && o.mode != LINE_MODE_PERSISTENT) return fail(c, LINE_ERR_ARG, "%s: bad mode", what);
     if (o.warps_per_block < 0 || o.warps_per_block > 32) return fail(c, LINE_ERR_ARG, "%s: bad warps_per_block", what);
     if (o.sample_offset + n_samples < o.sample_offset) return fail(c, LINE_ERR_ARG, "%s: sample range overflows", what);
+    if (o.walk_length < 0 || o.walk_length > kMaxWalkLen ||
+        (o.walk_length > 0 && (o.window < 1 || o.window > o.walk_length)))
+        return fail(c, LINE_ERR_ARG, "%s: need 1 <= window <= walk_length <= %d", what, kMaxWalkLen);
+    if (o.walk_length > 0) {
+        line_status ws = ensure_walk_tables(c);
+        if (ws) return ws;
+    }
     TrainArgs a{};
     a.order = order;
     a.dim = dim;
@@ -339,6 +416,10 @@ line_status make_train_args(line_ctx* c, const char* what, int order, int dim, i
     a.chunk_batches = o.chunk_batches;
     a.warps_per_block = o.warps_per_block;
     a.timing = o.timing;
+    a.walk_len = o.walk_length;
+    a.window = o.walk_length > 0 ? o.window : 0;
+    a.row_ptr = c->row_ptr;
+    a.cw = c->cw;
     a.graph = o.graph;
     *out = a;
     return LINE_OK;

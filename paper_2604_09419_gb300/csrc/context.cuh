@@ -34,6 +34,11 @@ struct line_ctx {
     int32_t* src = nullptr;
     int32_t* dst = nullptr;
     float* deg = nullptr;  // weighted out-degree of each node (FP64 sum, stored FP32)
+    float* w = nullptr;    // arc weights (null: all 1)
+    // walk sampler tables, built on first use: first arc of each node and the
+    // running FP64 weight sums per node
+    int64_t* row_ptr = nullptr;
+    double* cw = nullptr;
     uint2* edge_tab = nullptr;
     uint2* neg_tab = nullptr;
     // tables by order (index 1 and 2)
@@ -65,6 +70,8 @@ line_status cuda_fail(line_ctx* c, cudaError_t e, const char* what);
 line_status enter(line_ctx* c);
 // Reads and clears the device status word (synchronises the stream).
 line_status check_status(line_ctx* c, const char* what, bool timeout_sticky = true);
+// Builds the walk sampler tables (row_ptr, cw) if they are missing.
+line_status ensure_walk_tables(line_ctx* c);
 
 }  // namespace line
 

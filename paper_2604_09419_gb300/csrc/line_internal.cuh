@@ -140,6 +140,33 @@ cudaError_t convert_rows(const void* src, int src_dtype, void* dst, int dst_dtyp
                          int64_t n_rows, int dim, int64_t n_nodes, uint32_t* status, cudaStream_t s);
 cudaError_t debug_wait(uint32_t* flag, int64_t limit, uint32_t* status, cudaStream_t s);
 
+// walk.cu: the walk sampler (Algorithms 2-3).  Limits: 1 <= W <= L <= kMaxWalkLen.
+constexpr int kMaxWalkLen = 1024;
+struct WalkParams {
+    const int32_t* src;
+    const int32_t* dst;
+    const uint2* edge_tab;
+    int64_t n_arcs;
+    const int64_t* row_ptr;  // [n_nodes + 1]
+    const double* cw;        // [n_arcs] running weight sums per node
+    uint64_t seed;
+    uint64_t t0;             // global index of the first sample
+    int64_t count;
+    int L, W;
+    uint64_t P;              // pairs per walk: L W - W (W - 1) / 2
+    uint64_t R;              // record stride (K + 2)
+    int32_t* rec;            // rec[s R], rec[s R + 1] = the pair of sample t0 + s
+    uint64_t* items;         // nullable: grouping items of slots 0 and 1
+    uint32_t ctx_off;        // row offset of the context table in the items
+    uint32_t slot_bits;      // item value = (s << slot_bits) | slot
+};
+size_t walk_smem_bytes(int L);
+// row_ptr[n+1] (first arc of each node) and cw[m] from the sorted src and the
+// arc weights (nullable: weight 1).
+cudaError_t walk_tables(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const float* w, int64_t* row_ptr,
+                        double* cw, cudaStream_t s);
+cudaError_t walk_pairs(const WalkParams& p, cudaStream_t s);
+
 // eval.cu
 cudaError_t eval_loss_terms(const void* U, const void* Ctx, int dtype, int dim, int K, const int32_t* src,
                             const int32_t* dst, const uint2* edge_tab, int64_t n_arcs, const uint2* neg_tab,
@@ -189,6 +216,10 @@ struct TrainArgs {
     int warps_per_block;
     int timing;
     int graph;
+    // walk sampler (walk_len > 0): positive pairs from random walks
+    const int64_t* row_ptr;
+    const double* cw;
+    int walk_len, window;
 };
 
 struct TrainTimes {

@@ -755,6 +755,7 @@ struct PrepassParams {
     int64_t chunk_samples;
     int64_t batch;
     int K, order;
+    int walk;  // 1: slots 0 and 1 come from the walk sampler (no arc draw here)
     int32_t* rec;
     uint64_t* items;
     uint64_t* t_out;  // receives t_chunk (read by graph replays of the data phase)
@@ -775,6 +776,7 @@ __global__ void k_chunk_draws(PrepassParams p) {
         const uint32_t ctx_off = p.order == 2 ? (uint32_t)p.n_nodes : 0u;
         const uint32_t base = s * R;
         if (c == 0) {
+            if (p.walk) continue;
             const uint32_t e = alias_pick(p.edge_tab, (uint64_t)p.n_arcs, w);
             const int32_t u = __ldg(p.src + e), v = __ldg(p.dst + e);
             p.rec[base] = u;
@@ -1776,7 +1778,26 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     pp.batch = a.batch;
     pp.K = a.K;
     pp.order = a.order;
+    pp.walk = a.walk_len > 0;
     pp.items = (uint64_t*)ws->items0.p;
+
+    WalkParams wp{};
+    if (a.walk_len > 0) {
+        wp.src = a.src;
+        wp.dst = a.dst;
+        wp.edge_tab = a.edge_tab;
+        wp.n_arcs = a.n_arcs;
+        wp.row_ptr = a.row_ptr;
+        wp.cw = a.cw;
+        wp.seed = a.seed;
+        wp.L = a.walk_len;
+        wp.W = a.window;
+        wp.P = (uint64_t)a.walk_len * a.window - (uint64_t)a.window * (a.window - 1) / 2;
+        wp.R = (uint64_t)R;
+        wp.items = (uint64_t*)ws->items0.p;
+        wp.ctx_off = a.order == 2 ? (uint32_t)a.n_nodes : 0u;
+        wp.slot_bits = kSlotBits;
+    }
 
     GroupParams gq{};
     gq.batch = a.batch;
@@ -1847,6 +1868,13 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
             const int64_t work = cs * (a.K + 1);
             const unsigned g = (unsigned)std::min<int64_t>((work + 255) / 256, 152 * 64);
             k_chunk_draws<<<g, 256, 0, ps>>>(pp);
+            if (a.walk_len > 0) {
+                wp.t0 = t;
+                wp.count = cs;
+                wp.rec = (int32_t*)cset.rec.p;
+                if ((e = walk_pairs(wp, ps)) != cudaSuccess) return e;
+                ++launches;
+            }
             k_batch_eta<<<(unsigned)((cb + 127) / 128), 128, 0, ps>>>(cb, t, a.batch, (float)a.lr0, a.lr_schedule,
                                                                       (float)a.lr_floor, a.lr_total,
                                                                       (float*)cset.eta.p);

@@ -40,7 +40,7 @@ class TrainOpts(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int64), ("lambda_", ctypes.c_double), ("alpha_neg", ctypes.c_double),
                 ("sample_offset", ctypes.c_uint64), ("mode", ctypes.c_int), ("spin_limit", ctypes.c_int64),
                 ("chunk_batches", ctypes.c_int), ("warps_per_block", ctypes.c_int), ("timing", ctypes.c_int),
-                ("graph", ctypes.c_int)]
+                ("graph", ctypes.c_int), ("walk_length", ctypes.c_int), ("window", ctypes.c_int)]
 
 
 class TuneOpts(ctypes.Structure):
@@ -70,6 +70,7 @@ def _load():
         "line_get_graph_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "line_get_alias": (i32, [vp, i32, vp, vp]),
         "line_sample_debug": (i32, [vp, i32, u64, u32, u64, i64, vp]),
+        "line_sample_walk_debug": (i32, [vp, i32, u64, i32, i32, u64, i64, vp]),
         "line_init_embeddings": (i32, [vp, i32, i32, i32, u64]),
         "line_train_steps": (i32, [vp, i32, i32, i32, ctypes.POINTER(LR), u64, u64, ctypes.POINTER(TrainOpts)]),
         "line_train_orders": (i32, [vp, i32, i32, ctypes.POINTER(LR), u64, u64, ctypes.POINTER(TrainOpts)]),
@@ -103,7 +104,7 @@ def _load():
 
 lib = _load()
 EXPORTED = ("line_train_opts_default", "line_status_string", "line_create", "line_destroy", "line_last_error",
-            "line_build_alias", "line_get_graph_info", "line_get_alias", "line_sample_debug",
+            "line_build_alias", "line_get_graph_info", "line_get_alias", "line_sample_debug", "line_sample_walk_debug",
             "line_init_embeddings", "line_train_steps", "line_train_orders", "line_get_embeddings", "line_set_embeddings",
             "line_eval_loss", "line_eval_loss_noalloc", "line_eval_auc", "line_mlp_create", "line_mlp_features", "line_mlp_features_rows",
             "line_mlp_get_features", "line_mlp_get_params", "line_mlp_set_params", "line_mlp_grad", "line_mlp_train",
@@ -178,6 +179,9 @@ class Context:
 
     def sample_debug(self, K, seed, domain, t0, count, out):
         return self._ck(lib.line_sample_debug(self.h, K, seed, domain, t0, count, ptr(out)))
+
+    def sample_walk_debug(self, K, seed, walk_length, window, t0, count, out):
+        return self._ck(lib.line_sample_walk_debug(self.h, K, seed, walk_length, window, t0, count, ptr(out)))
 
     def init_embeddings(self, order, dim, dtype=DTYPE_F32, seed=0):
         return self._ck(lib.line_init_embeddings(self.h, order, dim, dtype, seed))
