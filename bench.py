@@ -11,6 +11,11 @@ streams; the same tables as one order after the other).
 
 Other workloads (``--workload``; not the default line):
 
+* ``rmat20walk`` - the default workload with the positive pairs drawn by the
+  walk sampler instead of by arc weight: walks of length 100 from roots drawn
+  by arc weight, weighted steps, pairs within a window of 2 (Algorithms 2-3,
+  the local walk); the negatives, update and schedule are unchanged.
+
 * ``dchung22`` - weighted directed Chung-Lu graph, 4,194,304 nodes, 2^26 arc
   draws (out-weights power law 2.2, lognormal(0,1) weights); order 2, d=128,
   K=5: the FP32 path at B=4096 against BF16 tables with stochastic rounding
@@ -75,7 +80,9 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-samples", type=int, default=1 << 20)
-    p.add_argument("--workload", default="rmat20", choices=["rmat20", "dchung22", "warm22", "rmat24"])
+    p.add_argument("--workload", default="rmat20", choices=["rmat20", "rmat20walk", "dchung22", "warm22", "rmat24"])
+    p.add_argument("--walk-length", type=int, default=100, help="rmat20walk: steps per walk")
+    p.add_argument("--window", type=int, default=2, help="rmat20walk: pair window")
     p.add_argument("--epochs", type=int, default=10, help="rmat24: samples per order = epochs x |E|")
     p.add_argument("--checkpoints", type=int, default=10, help="warm22: refinement epochs (checkpoints)")
     return p.parse_args()
@@ -190,7 +197,16 @@ def measured_traffic():
     return None
 
 
-def cpu_baseline(g, n_samples: int):
+def metric_of(args):
+    return "walk-pair updates/s (d=128,K=5)" if walk_of(args)[0] else METRIC
+
+
+def walk_of(args):
+    """(walk_length, window) of the workload; (0, 0) for arcs drawn by weight."""
+    return (args.walk_length, args.window) if args.workload == "rmat20walk" else (0, 0)
+
+
+def cpu_baseline(g, n_samples: int, walk=(0, 0)):
     """The FP64 oracle, single-threaded, on a prefix of the same workload (order 2)."""
     import numpy as np
 
@@ -198,8 +214,9 @@ def cpu_baseline(g, n_samples: int):
     T = O.Tables(g)
     U = O.init_uniform(g.n_nodes, DIM, 1)
     C = np.zeros_like(U)
+    wk = (O.walk_cumw(g), walk[0], walk[1]) if walk[0] > 0 else None
     t0 = time.perf_counter()
-    O.train(T, U, C, order=2, K=K, n_samples=n_samples, seed=11, batch=B, lr_total=20 * 16 * g.n_nodes)
+    O.train(T, U, C, order=2, K=K, n_samples=n_samples, seed=11, batch=B, lr_total=20 * 16 * g.n_nodes, walk=wk)
     dt = time.perf_counter() - t0
     return {"value": n_samples / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
             "sample": f"order-2 FP64 oracle on the first {n_samples} samples of the workload "
@@ -215,12 +232,12 @@ def run_reference(args):
     n = min(args.cpu_samples, 1 << 19)
     times = []
     for _ in range(args.warmup if args.warmup < 1 else 1):
-        cpu_baseline(g, 4096)
+        cpu_baseline(g, 4096, walk_of(args))
     for _ in range(args.steps):
-        r = cpu_baseline(g, n)
+        r = cpu_baseline(g, n, walk_of(args))
         times.append(n / r["value"])
     value = n / statistics.median(times)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+    line = {"impl": "reference", "metric": metric_of(args), "value": value, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(args, g),
@@ -231,12 +248,18 @@ def run_reference(args):
 
 
 def workload_config(args, g):
-    return {"workload": f"rmat{args.scale}_line_order1+2_d{DIM}_K{K}_B{B}_fp32",
-            "graph": f"R-MAT scale {args.scale}, edge factor 16, (.57,.19,.19,.05), symmetrised",
-            "n_nodes": g.n_nodes, "n_arcs": g.n_arcs, "dim": DIM, "K": K, "batch": B,
-            "samples_per_step": 2 * samples_per_step(args),
-            "lr": "0.025 linear decay over 20*|E| samples per order",
-            "l2": "inputs larger than L2 (FP32 U1, U2, C2 tables: 1.5 GiB; alias tables 258 MB)"}
+    wl, ww = walk_of(args)
+    sampler = f"_walk{wl}w{ww}" if wl else ""
+    c = {"workload": f"rmat{args.scale}_line_order1+2_d{DIM}_K{K}_B{B}_fp32{sampler}",
+         "graph": f"R-MAT scale {args.scale}, edge factor 16, (.57,.19,.19,.05), symmetrised",
+         "n_nodes": g.n_nodes, "n_arcs": g.n_arcs, "dim": DIM, "K": K, "batch": B,
+         "samples_per_step": 2 * samples_per_step(args),
+         "lr": "0.025 linear decay over 20*|E| samples per order",
+         "l2": "inputs larger than L2 (FP32 U1, U2, C2 tables: 1.5 GiB; alias tables 258 MB)"}
+    if wl:
+        c["positive_pairs"] = (f"walk sampler: walks of {wl} steps from arcs drawn by weight, weighted steps, "
+                               f"pairs within a window of {ww}")
+    return c
 
 
 def samples_per_step(args):
@@ -526,6 +549,8 @@ def main():
     if args.impl == "reference":
         run_reference(args)
         return
+    if args.workload == "rmat20walk":
+        args.scale = 20
     if args.workload == "dchung22":
         run_dchung22(args)
         return
@@ -558,12 +583,16 @@ def main():
     mode = {"auto": L.MODE_BATCHED, "batched": L.MODE_BATCHED, "persistent": L.MODE_PERSISTENT}[args.mode]
     seed = replica_seed(rank)
 
+    walk_len, window = walk_of(args)
+
     def opts(offset):
         o = L.train_opts_default()
         o.batch = B
         o.mode = mode
         o.timing = 1
         o.sample_offset = offset
+        o.walk_length = walk_len
+        o.window = window
         return o
 
     ctx.init_embeddings(1, DIM, L.DTYPE_F32, seed=1)
@@ -617,7 +646,7 @@ def main():
         upd_ms = st.update_ms
         achieved = st.update_samples * ALG_BYTES_UPDATE / (upd_ms / 1e3) / 1e9 if upd_ms > 0 else None
         kernel = "update phase (k_gather + k_apply)" if mode == L.MODE_BATCHED else "k_persistent"
-    traffic = measured_traffic() if mode == L.MODE_BATCHED and args.scale == 20 else None
+    traffic = measured_traffic() if mode == L.MODE_BATCHED and args.scale == 20 and not walk_len else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
                 "traffic_unit": "DRAM bytes per 4,096-sample batch (k_gather + k_apply, warm L2, ncu)",
@@ -628,9 +657,10 @@ def main():
                 "path_frac": value / world * ALG_BYTES_PATH / 1e9 / peak}
     if concurrent:
         # counted from the schedule: per order and step, two launches per
-        # batch and three pre-pass launches per chunk of 64 batches
+        # batch and three pre-pass launches per chunk of 64 batches (four
+        # with the walk sampler)
         batches = -(-S // B)
-        launches = int(2 * args.steps * (2 * batches + 3 * -(-batches // 64)))
+        launches = int(2 * args.steps * (2 * batches + (3 + (walk_len > 0)) * -(-batches // 64)))
     else:
         launches = int(st.update_launches + st.prepass_launches)
 
@@ -666,10 +696,10 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(g, args.cpu_samples)
+        cpu = cpu_baseline(g, args.cpu_samples, walk_of(args))
 
     if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        line = {"metric": metric_of(args), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(args, g), "roofline": roofline, "cpu_baseline": cpu,
