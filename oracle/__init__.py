@@ -94,6 +94,8 @@ def lib():
             L.orc_train.argtypes = TABLE_ARGS + [_int, _int, _int, _dbl, _int, _dbl, _u64, _u64, _u64,
                                                  _i64, _dbl, _dbl, _u64, _f64p, ctypes.c_void_p, ctypes.c_void_p,
                                                  _int, _int]
+            L.orc_train_pairwise.argtypes = L.orc_train.argtypes
+            L.orc_train_pairwise.restype = _int
             L.orc_walk_cumw.argtypes = [_i64, _i32p, ctypes.c_void_p, _f64p]
             L.orc_walk_cumw.restype = None
             L.orc_walk_pairs_per_walk.argtypes = [_int, _int]
@@ -247,6 +249,26 @@ def train(T: Tables, U: np.ndarray, C, *, order: int, K: int, lr0: float = 0.025
                          None if cw is None else cw.ctypes.data, L, W)
     if rc:
         raise ValueError(f"orc_train failed ({rc})")
+
+
+def train_pairwise(T: Tables, U: np.ndarray, C, *, order: int, K: int, lr0: float = 0.025, schedule: int = 1,
+                   lr_floor_frac: float = 1e-4, lr_total: int = 0, n_samples: int, seed: int, batch: int,
+                   lam: float = 0.0, alpha_neg: float = 1.0, sample_offset: int = 0, walk=None):
+    """Per-pair immediate LINE updates (Algorithm 1's local path with
+    LineUpdate) in place on FP64 tables; `batch` only sets the steps of the
+    learning-rate schedule."""
+    assert U.dtype == np.float64 and U.flags.c_contiguous
+    dim = U.shape[1]
+    cptr = None
+    if order == 2:
+        assert C is not None and C.dtype == np.float64 and C.flags.c_contiguous and C.shape == U.shape
+        cptr = C.ctypes.data
+    cw, L, W = walk if walk is not None else (None, 0, 0)
+    rc = lib().orc_train_pairwise(*T.args(), order, dim, K, lr0, schedule, lr_floor_frac, lr_total, n_samples,
+                                  seed, batch, lam, alpha_neg, sample_offset, U, cptr,
+                                  None if cw is None else cw.ctypes.data, L, W)
+    if rc:
+        raise ValueError(f"orc_train_pairwise failed ({rc})")
 
 
 def eval_loss(T: Tables, U: np.ndarray, C, *, order: int, K: int, seed: int, m: int) -> float:

@@ -493,6 +493,61 @@ int orc_train(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t
 }
 
 /* ------------------------------------------------------------------------ */
+/* Per-pair immediate updates: the local path of Algorithm 1 with            */
+/* LineUpdate, one pair after the other.  Samples t run in order, and the    */
+/* pairs of a sample in the order (u, v), (u, n_1) .. (u, n_K).  One call:   */
+/*   x = U[u], c = Ctx[y] (both read before either is written),              */
+/*   s = x . c,  g = eta (1 - sigma(s)) (positive) or                        */
+/*               g = -eta alpha_neg sigma(s) (negative),                     */
+/*   U[u]  <- x + (g c - eta lambda x),                                      */
+/*   Ctx[y] <- c + (g x - eta lambda c), written after U[u] (with order 1    */
+/*   and y = u this value stays).                                            */
+/* eta is the schedule's value at the first sample of t's block of `batch`   */
+/* samples counted from sample_offset; pairs come from the arc sampler or,   */
+/* with walk_cw, the walk sampler, as in orc_train.                          */
+/* ------------------------------------------------------------------------ */
+int orc_train_pairwise(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t* dst,
+                       const uint32_t* thr_e, const uint32_t* alias_e, const uint32_t* thr_n,
+                       const uint32_t* alias_n, int order, int dim, int K, double lr0, int schedule,
+                       double lr_floor_frac, uint64_t lr_total, uint64_t n_samples, uint64_t seed, int64_t batch,
+                       double lambda, double alpha_neg, uint64_t sample_offset, double* U, double* C,
+                       const double* walk_cw, int walk_len, int window) {
+    if (batch <= 0 || dim <= 0 || K < 0 || (order != 1 && order != 2)) return -1;
+    if (walk_cw && (walk_len < 1 || window < 1 || window > walk_len)) return -1;
+    orc_tables T = {n_nodes, n_arcs, src, dst, thr_e, alias_e, thr_n, alias_n};
+    orc_walker Wk = {T, walk_cw};
+    int32_t* wnodes = walk_cw ? (int32_t*)malloc(sizeof(int32_t) * (size_t)(walk_len + 1)) : NULL;
+    int64_t wcached = -1;
+    double* Ctx = order == 2 ? C : U;
+    int32_t* rec = (int32_t*)malloc(sizeof(int32_t) * (size_t)(K + 2));
+    double* x = (double*)malloc(sizeof(double) * (size_t)dim);
+    double* c = (double*)malloc(sizeof(double) * (size_t)dim);
+    if (!rec || !x || !c || (walk_cw && !wnodes)) return -2;
+    uint64_t Ttot = lr_total ? lr_total : sample_offset + n_samples;
+    uint64_t end = sample_offset + n_samples;
+    for (uint64_t t = sample_offset; t < end; ++t) {
+        uint64_t t0 = sample_offset + (t - sample_offset) / (uint64_t)batch * (uint64_t)batch;
+        double eta = orc_batch_lr(lr0, schedule, lr_floor_frac, Ttot, t0);
+        if (walk_cw) sample_walk_one(&Wk, seed, t, K, walk_len, window, wnodes, &wcached, rec);
+        else sample_one(&T, seed, 0, t, K, rec);
+        double* urow = U + (int64_t)rec[0] * dim;
+        for (int j = 0; j <= K; ++j) {
+            double* crow = Ctx + (int64_t)rec[1 + j] * dim;
+            for (int k = 0; k < dim; ++k) { x[k] = urow[k]; c[k] = crow[k]; }
+            double s = dot(x, c, dim);
+            double g = j == 0 ? eta * (1.0 - sigmoid(s)) : -eta * alpha_neg * sigmoid(s);
+            for (int k = 0; k < dim; ++k) urow[k] = x[k] + (g * c[k] - eta * lambda * x[k]);
+            for (int k = 0; k < dim; ++k) crow[k] = c[k] + (g * x[k] - eta * lambda * c[k]);
+        }
+    }
+    free(c);
+    free(x);
+    free(rec);
+    free(wnodes);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Negative-sampling LINE loss over m fixed samples (draw domain 3):         */
 /*   L = - sum_t [ log sigma(s+) + sum_j log sigma(-s-_j) ]                  */
 /* with s = U[u] . Ctx[y] (Ctx = C for order 2, U for order 1).              */
