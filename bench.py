@@ -72,7 +72,8 @@ def parse():
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--mode", default="auto", choices=["auto", "batched", "persistent"])
+    p.add_argument("--mode", default="auto", choices=["auto", "batched", "persistent", "hogwild"],
+                   help="hogwild: per-pair immediate updates by lock-free concurrent workers (not deterministic)")
     p.add_argument("--orders", default="concurrent", choices=["concurrent", "sequential"],
                    help="train the two orders' tables concurrently (line_train_orders) or one after the other")
     p.add_argument("--scale", type=int, default=20)
@@ -580,7 +581,8 @@ def main():
     dst = torch.from_numpy(g.dst).cuda()
     w = torch.from_numpy(g.w).cuda()
     ctx.build_alias(g.n_nodes, src, dst, w)
-    mode = {"auto": L.MODE_BATCHED, "batched": L.MODE_BATCHED, "persistent": L.MODE_PERSISTENT}[args.mode]
+    mode = {"auto": L.MODE_BATCHED, "batched": L.MODE_BATCHED, "persistent": L.MODE_PERSISTENT,
+            "hogwild": L.MODE_HOGWILD}[args.mode]
     seed = replica_seed(rank)
 
     walk_len, window = walk_of(args)
@@ -640,12 +642,14 @@ def main():
         # durations overlap too: their algorithmic bytes over the timed
         # region (CUDA events on the caller's stream) instead
         achieved = 2 * S * args.steps * ALG_BYTES_UPDATE / (ms / 1e3) / 1e9
-        kernel = "update phase of both orders (k_gather + k_apply), concurrent streams, over the timed region"
+        kernel = ("update phase of both orders (" + ("k_hogwild" if mode == L.MODE_HOGWILD else "k_gather + k_apply")
+                  + "), concurrent streams, over the timed region")
     else:
         # the update kernels' own CUDA events
         upd_ms = st.update_ms
         achieved = st.update_samples * ALG_BYTES_UPDATE / (upd_ms / 1e3) / 1e9 if upd_ms > 0 else None
-        kernel = "update phase (k_gather + k_apply)" if mode == L.MODE_BATCHED else "k_persistent"
+        kernel = {L.MODE_BATCHED: "update phase (k_gather + k_apply)", L.MODE_PERSISTENT: "k_persistent",
+                  L.MODE_HOGWILD: "k_hogwild"}[mode]
     traffic = measured_traffic() if mode == L.MODE_BATCHED and args.scale == 20 and not walk_len else None
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
@@ -660,7 +664,11 @@ def main():
         # batch and three pre-pass launches per chunk of 64 batches (four
         # with the walk sampler)
         batches = -(-S // B)
-        launches = int(2 * args.steps * (2 * batches + (3 + (walk_len > 0)) * -(-batches // 64)))
+        chunks = -(-batches // 64)
+        if mode == L.MODE_HOGWILD:  # per chunk: the draws (+ walks) and one update launch
+            launches = int(2 * args.steps * chunks * (2 + (walk_len > 0)))
+        else:
+            launches = int(2 * args.steps * (2 * batches + (3 + (walk_len > 0)) * chunks))
     else:
         launches = int(st.update_launches + st.prepass_launches)
 
@@ -704,7 +712,8 @@ def main():
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(args, g), "roofline": roofline, "cpu_baseline": cpu,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
-                "mode": "batched" if mode == L.MODE_BATCHED else "persistent", "orders": args.orders}
+                "mode": {L.MODE_BATCHED: "batched", L.MODE_PERSISTENT: "persistent", L.MODE_HOGWILD: "hogwild"}[mode],
+                "orders": args.orders}
         print(json.dumps(line), flush=True)
     ctx.close()
     if world > 1:

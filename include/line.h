@@ -67,7 +67,7 @@ typedef enum {
 enum { LINE_DTYPE_F32 = 0, LINE_DTYPE_BF16 = 1 };
 enum { LINE_TABLE_EDGE = 0, LINE_TABLE_NEG = 1 };
 enum { LINE_WHICH_U = 0, LINE_WHICH_C = 1 };
-enum { LINE_MODE_BATCHED = 0, LINE_MODE_PERSISTENT = 1 };
+enum { LINE_MODE_BATCHED = 0, LINE_MODE_PERSISTENT = 1, LINE_MODE_HOGWILD = 2 };
 enum { LINE_SCORE_DOT = 0, LINE_SCORE_COSINE = 1 };
 
 /* Graph as directed arcs (an undirected edge is two arcs), Section II / V-A.
@@ -100,7 +100,8 @@ typedef struct {
     double lambda;           /* weight decay lambda of Eq. 2-3 (>= 0) */
     double alpha_neg;        /* negative weight alpha_neg of Algorithm 1 */
     uint64_t sample_offset;  /* global index of the first sample; batches start here */
-    int mode;                /* LINE_MODE_BATCHED or LINE_MODE_PERSISTENT */
+    int mode;                /* LINE_MODE_BATCHED or LINE_MODE_PERSISTENT (minibatch-synchronous,
+                                Eq. 4, deterministic), or LINE_MODE_HOGWILD (see below) */
     int64_t spin_limit;      /* bound on every device wait loop (iterations); <= 0: default */
     int chunk_batches;       /* batches per pre-pass chunk; 0: automatic */
     int warps_per_block;     /* 0: automatic */
@@ -111,7 +112,23 @@ typedef struct {
                                 (Algorithms 2-3, see line_sample_walk_debug); 0: arcs
                                 drawn by weight (Eq. 1).  At most 1024. */
     int window;              /* W: pair window of the walk sampler, 1 <= W <= L */
+    int hogwild_workers;     /* LINE_MODE_HOGWILD: samples in flight at once (>= 0; 0: one
+                                resident wave of the GPU, one worker per lane group) */
 } line_train_opts;
+
+/* LINE_MODE_HOGWILD: the local path of Algorithm 1 - LineUpdate applied pair
+ * after pair, at once, with no minibatch.  For each sample in order and each
+ * of its pairs (u, v), (u, n_1) .. (u, n_K) in order: x = U[u], c = Ctx[y]
+ * (both before the call), s = x . c, g = eta (1 - sigma(s)) or
+ * -eta alpha_neg sigma(s), U[u] <- x + (g c - eta lambda x), then
+ * Ctx[y] <- c + (g x - eta lambda c).  eta is the schedule's value at the
+ * first sample of the sample's block of opts.batch samples.  Workers run
+ * samples concurrently on the shared tables without locks (Hogwild): a
+ * worker sees other workers' rows as they are when it loads them, and
+ * concurrent writes of a row keep one of them.  The result is therefore not
+ * deterministic, except with hogwild_workers = 1, which is the sequential
+ * per-pair SGD.  Samples (arcs or walk pairs, negatives) are the same as in
+ * the other modes. */
 
 /* Per-kernel timing collected when opts.timing == 1 (reset by line_reset_stats). */
 typedef struct {

@@ -121,6 +121,7 @@ void line_train_opts_default(line_train_opts* o) {
     o->graph = 1;
     o->walk_length = 0;
     o->window = 0;
+    o->hogwild_workers = 0;
 }
 
 const char* line_status_string(line_status s) {
@@ -378,7 +379,9 @@ line_status make_train_args(line_ctx* c, const char* what, int order, int dim, i
     if (opts) o = *opts;
     if (o.batch < 1 || o.batch > (1 << 20)) return fail(c, LINE_ERR_ARG, "%s: batch out of range", what);
     if (!(o.lambda >= 0.0) || !(o.alpha_neg >= 0.0)) return fail(c, LINE_ERR_ARG, "%s: bad lambda/alpha_neg", what);
-    if (o.mode != LINE_MODE_BATCHED && o.mode != LINE_MODE_PERSISTENT) return fail(c, LINE_ERR_ARG, "%s: bad mode", what);
+    if (o.mode != LINE_MODE_BATCHED && o.mode != LINE_MODE_PERSISTENT && o.mode != LINE_MODE_HOGWILD)
+        return fail(c, LINE_ERR_ARG, "%s: bad mode", what);
+    if (o.hogwild_workers < 0) return fail(c, LINE_ERR_ARG, "%s: hogwild_workers must be >= 0", what);
     if (o.warps_per_block < 0 || o.warps_per_block > 32) return fail(c, LINE_ERR_ARG, "%s: bad warps_per_block", what);
     if (o.sample_offset + n_samples < o.sample_offset) return fail(c, LINE_ERR_ARG, "%s: sample range overflows", what);
     if (o.walk_length < 0 || o.walk_length > kMaxWalkLen ||
@@ -416,6 +419,7 @@ line_status make_train_args(line_ctx* c, const char* what, int order, int dim, i
     a.chunk_batches = o.chunk_batches;
     a.warps_per_block = o.warps_per_block;
     a.timing = o.timing;
+    a.hogwild_workers = o.hogwild_workers;
     a.walk_len = o.walk_length;
     a.window = o.walk_length > 0 ? o.window : 0;
     a.row_ptr = c->row_ptr;

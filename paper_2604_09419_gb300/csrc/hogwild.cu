@@ -1,0 +1,287 @@
+// Hogwild schedule (LINE_MODE_HOGWILD): the local path of Algorithm 1, with
+// LineUpdate applied pair after pair and at once.  Many workers run it
+// concurrently on the shared tables without locks, in the manner of Hogwild
+// (Recht et al., NeurIPS 2011).  There is no grouping pass, no delta slab
+// and no apply kernel.
+//
+// A worker is a lane group (the row geometry of the minibatch kernels: L
+// lanes per row, E values per lane).  Worker w takes samples w, w + n_w,
+// w + 2 n_w, ... of the chunk's records (written by the pre-pass) and, per
+// sample:
+//   - loads each distinct row of the sample once (the U row of u and the
+//     context rows of v, n_1 .. n_K; in order 1 the context table is U, so
+//     u may also be a context row) into its shared-memory stage;
+//   - runs the K+1 calls in order on the staged rows: x = U[u], c = Ctx[y],
+//     s = x . c, g = eta (1 - sigma(s)) or -eta alpha_neg sigma(s),
+//     U[u] <- x + (g c - eta lambda x), Ctx[y] <- c + (g x - eta lambda c)
+//     (both from the values before the call; Ctx[y] written last);
+//   - adds each distinct row's net change (final - loaded) to the table
+//     with atomic read-modify-writes: FP32 rows by vector float atomic
+//     adds, BF16 rows by a 64-bit compare-and-swap of 4 values that rounds
+//     the sum stochastically.
+// Inside a sample this is exactly the sequential order of the calls.  Across
+// workers, reads are not synchronised, so a sample may compute on rows that
+// other workers are changing, but no worker's change is overwritten by
+// another's, as in CPU Hogwild where every element update is an in-place
+// add.  Overwriting whole rows instead loses almost every update of the hub
+// rows once thousands of workers run.  With one worker the run is the
+// sequential per-pair SGD.  eta is the schedule's value at the first sample
+// of the sample's batch.
+#include <algorithm>
+
+#include "line_internal.cuh"
+#include "rows.cuh"
+
+namespace line {
+namespace {
+
+constexpr int kHogWarps = 4;   // warps per block, at most (fewer when a block's stages exceed the shared memory)
+constexpr int kCasTries = 256;  // BF16: compare-and-swap attempts before a plain store
+
+// Shared memory per lane group: the staged rows, the rows as loaded, then the
+// record and the first-occurrence slot of each slot, rounded up to 16 bytes.
+__host__ __device__ inline size_t group_bytes(int dim, int K) {
+    return (sizeof(float) * 2 * (size_t)(K + 2) * dim + sizeof(int32_t) * 2 * (K + 2) + 15) & ~(size_t)15;
+}
+
+// table[row] += d for this lane's values.  BF16: each 4-value word is
+// replaced by its sum with d rounded stochastically (the bits of store_row's
+// key for sample t), retried while other workers change the word; after
+// kCasTries attempts the last sum is stored plainly.
+template <int D, int DT>
+__device__ __forceinline__ void add_row(void* table, int64_t row, int lig, const float (&d)[Geom<D, DT>::E],
+                                        uint64_t seed, uint64_t t, uint32_t table_id) {
+    using G = Geom<D, DT>;
+    if constexpr (DT == LINE_DTYPE_F32) {
+        float4* p = reinterpret_cast<float4*>(reinterpret_cast<float*>(table) + row * D + lig * G::E);
+#pragma unroll
+        for (int q = 0; q < G::NV; ++q) atomicAdd(p + q, make_float4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]));
+    } else {
+        unsigned long long* p =
+            reinterpret_cast<unsigned long long*>(reinterpret_cast<__nv_bfloat16*>(table) + row * D + lig * G::E);
+#pragma unroll
+        for (int q = 0; q < G::NV; ++q) {
+            const uint32_t k4 = (uint32_t)((lig * G::E + 4 * q) >> 2);
+            const uint64_t r = sr_bits(seed, table_id, (uint64_t)row, t, k4);
+            const uint32_t r0 = (uint32_t)r, r1 = (uint32_t)(r >> 32);
+            unsigned long long old = __ldcg(p + q), next = old;
+            for (int it = 0; it < kCasTries; ++it) {
+                const uint32_t lo = (uint32_t)old, hi = (uint32_t)(old >> 32);
+                const float v0 = __uint_as_float(lo << 16) + d[4 * q];
+                const float v1 = __uint_as_float(lo & 0xFFFF0000u) + d[4 * q + 1];
+                const float v2 = __uint_as_float(hi << 16) + d[4 * q + 2];
+                const float v3 = __uint_as_float(hi & 0xFFFF0000u) + d[4 * q + 3];
+                const uint32_t x = (uint32_t)bf16_sr(v0, r0) | ((uint32_t)bf16_sr(v1, r0 >> 16) << 16);
+                const uint32_t y = (uint32_t)bf16_sr(v2, r1) | ((uint32_t)bf16_sr(v3, r1 >> 16) << 16);
+                next = ((unsigned long long)y << 32) | x;
+                const unsigned long long prev = atomicCAS(p + q, old, next);
+                if (prev == old) break;
+                old = prev;
+                if (it == kCasTries - 1) __stcg(p + q, next);
+            }
+        }
+    }
+}
+
+template <int D, int DT>
+__global__ void __launch_bounds__(kHogWarps * 32) k_hogwild(HogwildParams p) {
+    using G = Geom<D, DT>;
+    extern __shared__ __align__(16) unsigned char s_raw[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane / G::L, lig = lane % G::L;
+    const int R = p.K + 2;
+    const uint32_t gm = group_mask<G::L>(grp);
+    const int gid = warp * G::GPW + grp;
+    unsigned char* base = s_raw + (size_t)gid * group_bytes(D, p.K);
+    float* stage = reinterpret_cast<float*>(base);
+    float* first = stage + (size_t)R * D;  // the rows as loaded
+    int32_t* srow = reinterpret_cast<int32_t*>(first + (size_t)R * D);
+    int32_t* sid = srow + R;
+    const int64_t worker = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * G::GPW + grp;
+    const int64_t nw = p.workers;
+    const int64_t n = p.chunk_samples;
+    // every lane of the warp runs the same number of rounds (the dot
+    // products reduce over full-warp shuffles)
+    const int64_t rounds = (n + nw - 1) / nw;
+    const uint32_t ctx_tab = p.order == 2 ? 1u : 0u;
+    void* ctx = p.order == 2 ? p.C : p.U;
+    for (int64_t r = 0; r < rounds; ++r) {
+        const int64_t s = r * nw + worker;
+        const bool active = worker < nw && s < n;
+        for (int k = lig; k < R; k += G::L) {
+            int32_t row = active ? __ldg(p.rec + s * R + k) : 0;
+            if (active && (row < 0 || row >= p.n_nodes)) {
+                atomicOr(p.status, DEV_ERR_INDEX);
+                row = 0;
+            }
+            srow[k] = row;
+        }
+        __syncwarp(gm);
+        // first slot holding the same row of the same table
+        for (int k = lig; k < R; k += G::L) {
+            const uint32_t tk = k == 0 ? 0u : ctx_tab;
+            int id = k;
+            for (int q = 0; q < k; ++q) {
+                const uint32_t tq = q == 0 ? 0u : ctx_tab;
+                if (tq == tk && srow[q] == srow[k]) {
+                    id = q;
+                    break;
+                }
+            }
+            sid[k] = id;
+        }
+        __syncwarp(gm);
+        // stage the distinct rows, up to CH loads in flight per lane
+        constexpr int CH = G::E <= 4 ? 8 : 4;
+        if (active) {
+            for (int k0 = 0; k0 < R; k0 += CH) {
+                float v[CH][G::E];
+#pragma unroll
+                for (int kk = 0; kk < CH; ++kk) {
+                    const int k = k0 + kk;
+                    if (k < R && sid[k] == k) load_row<D, DT>(k == 0 ? p.U : ctx, srow[k], lig, v[kk]);
+                }
+#pragma unroll
+                for (int kk = 0; kk < CH; ++kk) {
+                    const int k = k0 + kk;
+                    if (k < R && sid[k] == k) {
+                        float4* st = reinterpret_cast<float4*>(stage + (size_t)k * D + lig * G::E);
+                        float4* st0 = reinterpret_cast<float4*>(first + (size_t)k * D + lig * G::E);
+#pragma unroll
+                        for (int q = 0; q < G::NV; ++q) {
+                            const float4 a = make_float4(v[kk][4 * q], v[kk][4 * q + 1], v[kk][4 * q + 2], v[kk][4 * q + 3]);
+                            st[q] = a;
+                            st0[q] = a;
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp(gm);
+        const uint64_t t = p.t_chunk + (uint64_t)(active ? s : 0);
+        float eta = p.lr0;
+        if (p.lr_schedule == 1) {
+            const uint64_t t0 = p.t_chunk + (uint64_t)((active ? s : 0) / p.batch) * (uint64_t)p.batch;
+            float f = t0 >= p.lr_total ? 0.0f : (float)(p.lr_total - t0) / (float)p.lr_total;
+            if (f < p.lr_floor) f = p.lr_floor;
+            eta = p.lr0 * f;
+        }
+        const float etalam = eta * p.lambda;
+        float x[G::E];
+        {
+            const float4* ld = reinterpret_cast<const float4*>(stage + lig * G::E);
+#pragma unroll
+            for (int q = 0; q < G::NV; ++q) {
+                const float4 a = ld[q];
+                x[4 * q] = a.x;
+                x[4 * q + 1] = a.y;
+                x[4 * q + 2] = a.z;
+                x[4 * q + 3] = a.w;
+            }
+        }
+        for (int j = 0; j <= p.K; ++j) {
+            const int cj = sid[1 + j];
+            float c[G::E];
+            if (cj == 0) {
+#pragma unroll
+                for (int e = 0; e < G::E; ++e) c[e] = x[e];
+            } else {
+                const float4* ld = reinterpret_cast<const float4*>(stage + (size_t)cj * D + lig * G::E);
+#pragma unroll
+                for (int q = 0; q < G::NV; ++q) {
+                    const float4 a = ld[q];
+                    c[4 * q] = a.x;
+                    c[4 * q + 1] = a.y;
+                    c[4 * q + 2] = a.z;
+                    c[4 * q + 3] = a.w;
+                }
+            }
+            float sdot = 0.0f;
+#pragma unroll
+            for (int e = 0; e < G::E; ++e) sdot = fmaf(x[e], c[e], sdot);
+            sdot = group_sum<G::L>(sdot);
+            const float sig = 1.0f / (1.0f + expf(-sdot));
+            const float g = j == 0 ? eta * (1.0f - sig) : -eta * p.alpha_neg * sig;
+            float cn[G::E];
+#pragma unroll
+            for (int e = 0; e < G::E; ++e) {
+                cn[e] = c[e] + (g * x[e] - etalam * c[e]);
+                x[e] = x[e] + (g * c[e] - etalam * x[e]);
+            }
+            if (cj == 0) {
+                // order 1 with y = u: the context write comes last and stays
+#pragma unroll
+                for (int e = 0; e < G::E; ++e) x[e] = cn[e];
+            } else {
+                float4* st = reinterpret_cast<float4*>(stage + (size_t)cj * D + lig * G::E);
+#pragma unroll
+                for (int q = 0; q < G::NV; ++q) st[q] = make_float4(cn[4 * q], cn[4 * q + 1], cn[4 * q + 2], cn[4 * q + 3]);
+            }
+        }
+        if (active) {
+            for (int k = 0; k < R; ++k) {
+                if (sid[k] != k) continue;
+                float d[G::E];
+                const float4* ld = reinterpret_cast<const float4*>(stage + (size_t)k * D + lig * G::E);
+                const float4* ld0 = reinterpret_cast<const float4*>(first + (size_t)k * D + lig * G::E);
+#pragma unroll
+                for (int q = 0; q < G::NV; ++q) {
+                    const float4 a = ld[q], b = ld0[q];
+                    d[4 * q] = a.x - b.x;
+                    d[4 * q + 1] = a.y - b.y;
+                    d[4 * q + 2] = a.z - b.z;
+                    d[4 * q + 3] = a.w - b.w;
+                }
+                if (k == 0) {
+#pragma unroll
+                    for (int e = 0; e < G::E; ++e) d[e] = x[e] - first[lig * G::E + e];
+                }
+                add_row<D, DT>(k == 0 ? p.U : ctx, srow[k], lig, d, p.seed, t, k == 0 ? 0u : ctx_tab);
+            }
+        }
+        __syncwarp(gm);  // the stage is rewritten by the next round
+    }
+}
+
+template <int D, int DT>
+cudaError_t launch(const HogwildParams& p, int64_t max_workers, cudaStream_t s) {
+    using G = Geom<D, DT>;
+    constexpr size_t kMaxSmem = 227 * 1024;
+    const size_t per_warp = (size_t)G::GPW * group_bytes(D, p.K);
+    const int wpb = (int)std::min<size_t>(kHogWarps, kMaxSmem / per_warp);
+    if (wpb < 1) return cudaErrorInvalidValue;  // K and D beyond one warp's shared memory (not reachable for K <= 32)
+    const size_t smem = (size_t)wpb * per_warp;
+    cudaError_t e = cudaFuncSetAttribute(k_hogwild<D, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0, dev = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hogwild<D, DT>, wpb * 32, smem)) != cudaSuccess)
+        return e;
+    const int64_t per_block = (int64_t)wpb * G::GPW;
+    const int64_t full = (int64_t)std::max(per_sm, 1) * sms * per_block;  // one resident wave
+    HogwildParams q = p;
+    q.workers = max_workers > 0 ? std::min<int64_t>(max_workers, full) : full;
+    q.workers = std::min<int64_t>(q.workers, std::max<int64_t>(p.chunk_samples, 1));
+    const unsigned grid = (unsigned)((q.workers + per_block - 1) / per_block);
+    k_hogwild<D, DT><<<grid, wpb * 32, smem, s>>>(q);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t hogwild_chunk(const HogwildParams& p, int dim, int dtype, int64_t max_workers, cudaStream_t s) {
+    const bool bf = dtype == LINE_DTYPE_BF16;
+    switch (dim) {
+        case 16: return bf ? launch<16, LINE_DTYPE_BF16>(p, max_workers, s) : launch<16, LINE_DTYPE_F32>(p, max_workers, s);
+        case 32: return bf ? launch<32, LINE_DTYPE_BF16>(p, max_workers, s) : launch<32, LINE_DTYPE_F32>(p, max_workers, s);
+        case 64: return bf ? launch<64, LINE_DTYPE_BF16>(p, max_workers, s) : launch<64, LINE_DTYPE_F32>(p, max_workers, s);
+        case 128:
+            return bf ? launch<128, LINE_DTYPE_BF16>(p, max_workers, s) : launch<128, LINE_DTYPE_F32>(p, max_workers, s);
+        case 256:
+            return bf ? launch<256, LINE_DTYPE_BF16>(p, max_workers, s) : launch<256, LINE_DTYPE_F32>(p, max_workers, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+}  // namespace line

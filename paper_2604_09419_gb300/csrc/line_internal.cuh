@@ -193,6 +193,28 @@ cudaError_t eval_loss_noalloc(int device, const void* U, const void* Ctx, int dt
                               const uint2* neg_tab, int64_t n_nodes, uint64_t seed, int64_t m, double* out_dev,
                               cudaStream_t s);
 
+// hogwild.cu: one chunk of the Hogwild schedule (per-pair immediate updates
+// by concurrent lane-group workers) over the chunk's records.
+struct HogwildParams {
+    void* U;
+    void* C;
+    int order, K;
+    int64_t n_nodes;
+    const int32_t* rec;  // [chunk_samples][K+2]
+    int64_t chunk_samples;
+    uint64_t t_chunk;    // global index of the chunk's first sample (a batch start)
+    int64_t batch;       // learning-rate steps
+    float lr0, lr_floor;
+    int lr_schedule;
+    uint64_t lr_total;
+    float lambda, alpha_neg;
+    uint64_t seed;
+    int64_t workers;     // set by the launcher
+    uint32_t* status;
+};
+// max_workers <= 0: one resident wave of workers.
+cudaError_t hogwild_chunk(const HogwildParams& p, int dim, int dtype, int64_t max_workers, cudaStream_t s);
+
 // train.cu
 struct TrainArgs {
     int order, dim, K, dtype;
@@ -220,6 +242,7 @@ struct TrainArgs {
     const int64_t* row_ptr;
     const double* cw;
     int walk_len, window;
+    int64_t hogwild_workers;  // LINE_MODE_HOGWILD: concurrent workers (0: one resident wave)
 };
 
 struct TrainTimes {

@@ -52,105 +52,12 @@
 #include <cooperative_groups.h>
 
 #include "line_internal.cuh"
+#include "rows.cuh"
 #include "scan.cuh"
 
 namespace line {
 
 namespace cg = cooperative_groups;
-
-// ---------------------------------------------------------------------------
-// Row geometry: a row of D values is handled by L lanes, E values per lane,
-// moved as vectors of 4 values (16 bytes of FP32, 8 bytes of BF16).
-// ---------------------------------------------------------------------------
-// (host and device share these two: the work-item map of the persistent
-// schedule is laid out on the host)
-constexpr int geom_vec(int /*dtype*/) { return 4; }
-constexpr int geom_lanes(int dim, int dtype) { return dim / geom_vec(dtype) < 32 ? dim / geom_vec(dtype) : 32; }
-
-template <int D, int DT>
-struct Geom {
-    static constexpr int VEC = geom_vec(DT);
-    static constexpr int L = geom_lanes(D, DT);
-    static constexpr int E = D / L;
-    static constexpr int NV = E / VEC;
-    static constexpr int GPW = 32 / L;  // lane groups per warp
-    static_assert(D % (VEC * L) == 0 && NV >= 1, "unsupported dim");
-};
-
-template <int D, int DT>
-__device__ __forceinline__ void load_row(const void* table, int64_t row, int lig, float (&v)[Geom<D, DT>::E]) {
-    using G = Geom<D, DT>;
-    if constexpr (DT == LINE_DTYPE_F32) {
-        const float4* p = reinterpret_cast<const float4*>(reinterpret_cast<const float*>(table) + row * D + lig * G::E);
-#pragma unroll
-        for (int q = 0; q < G::NV; ++q) {
-            const float4 a = ld_cg(p + q);
-            v[4 * q] = a.x;
-            v[4 * q + 1] = a.y;
-            v[4 * q + 2] = a.z;
-            v[4 * q + 3] = a.w;
-        }
-    } else {
-        const uint2* p = reinterpret_cast<const uint2*>(reinterpret_cast<const __nv_bfloat16*>(table) + row * D + lig * G::E);
-#pragma unroll
-        for (int q = 0; q < G::NV; ++q) {
-            const uint2 a = __ldcg(p + q);
-            v[4 * q] = __uint_as_float(a.x << 16);
-            v[4 * q + 1] = __uint_as_float(a.x & 0xFFFF0000u);
-            v[4 * q + 2] = __uint_as_float(a.y << 16);
-            v[4 * q + 3] = __uint_as_float(a.y & 0xFFFF0000u);
-        }
-    }
-}
-
-// 64 random bits for the stochastic rounding of the 4 values at columns
-// 4 k4 .. 4 k4 + 3 of `row` of table `table_id`, written by the batch that
-// starts at sample t0: the SplitMix64 output function (Steele, Lea, Flood,
-// OOPSLA 2014) of a key built from the seed, the batch, the row and k4.
-__device__ __forceinline__ uint64_t sr_bits(uint64_t seed, uint32_t table_id, uint64_t row, uint64_t t0, uint32_t k4) {
-    uint64_t z = seed ^ (t0 * 0x9E3779B97F4A7C15ull) ^
-                 (((row << 16) | ((uint64_t)table_id << 15) | (uint64_t)k4) * 0xD1B54A32D192ED03ull);
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-// Store a row part; BF16 rounds stochastically: value i of a 4-value vector
-// adds bits [16 i, 16 i + 16) of sr_bits(...) below the BF16 mantissa, then
-// truncates.
-template <int D, int DT>
-__device__ __forceinline__ void store_row(void* table, int64_t row, int lig, const float (&v)[Geom<D, DT>::E],
-                                          uint64_t seed, uint64_t t0, uint32_t table_id) {
-    using G = Geom<D, DT>;
-    if constexpr (DT == LINE_DTYPE_F32) {
-        float4* p = reinterpret_cast<float4*>(reinterpret_cast<float*>(table) + row * D + lig * G::E);
-#pragma unroll
-        for (int q = 0; q < G::NV; ++q) st_cg(p + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
-    } else {
-        uint2* p = reinterpret_cast<uint2*>(reinterpret_cast<__nv_bfloat16*>(table) + row * D + lig * G::E);
-#pragma unroll
-        for (int q = 0; q < G::NV; ++q) {
-            const uint32_t k4 = (uint32_t)((lig * G::E + 4 * q) >> 2);
-            const uint64_t r = sr_bits(seed, table_id, (uint64_t)row, t0, k4);
-            const uint32_t r0 = (uint32_t)r, r1 = (uint32_t)(r >> 32);
-            const uint32_t x = (uint32_t)bf16_sr(v[4 * q], r0) | ((uint32_t)bf16_sr(v[4 * q + 1], r0 >> 16) << 16);
-            const uint32_t y = (uint32_t)bf16_sr(v[4 * q + 2], r1) | ((uint32_t)bf16_sr(v[4 * q + 3], r1 >> 16) << 16);
-            __stcg(p + q, make_uint2(x, y));
-        }
-    }
-}
-
-template <int L>
-__device__ __forceinline__ float group_sum(float v) {
-#pragma unroll
-    for (int o = L / 2; o >= 1; o >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, o);
-    return v;
-}
-
-template <int L>
-__device__ __forceinline__ uint32_t group_mask(int grp) {
-    return L == 32 ? 0xFFFFFFFFu : (((1u << L) - 1u) << (grp * L));
-}
 
 // Programmatic dependent launch: let the next kernel of the stream start its
 // prologue, and wait until the previous kernel's writes are visible.
@@ -757,7 +664,7 @@ struct PrepassParams {
     int K, order;
     int walk;  // 1: slots 0 and 1 come from the walk sampler (no arc draw here)
     int32_t* rec;
-    uint64_t* items;
+    uint64_t* items;  // null: records only (Hogwild schedule)
     uint64_t* t_out;  // receives t_chunk (read by graph replays of the data phase)
 };
 
@@ -781,12 +688,14 @@ __global__ void k_chunk_draws(PrepassParams p) {
             const int32_t u = __ldg(p.src + e), v = __ldg(p.dst + e);
             p.rec[base] = u;
             p.rec[base + 1] = v;
-            p.items[base] = make_item((uint32_t)u, s, 0u);
-            p.items[base + 1] = make_item((uint32_t)v + ctx_off, s, 1u);
+            if (p.items) {
+                p.items[base] = make_item((uint32_t)u, s, 0u);
+                p.items[base + 1] = make_item((uint32_t)v + ctx_off, s, 1u);
+            }
         } else {
             const uint32_t y = alias_pick(p.neg_tab, (uint64_t)p.n_nodes, w);
             p.rec[base + 1 + c] = (int32_t)y;
-            p.items[base + 1 + c] = make_item(y + ctx_off, s, 1u + c);
+            if (p.items) p.items[base + 1 + c] = make_item(y + ctx_off, s, 1u + c);
         }
     }
 }
@@ -1687,6 +1596,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     while (a.batch * R > ((int64_t)3584 << log_parts)) ++log_parts;
     const bool direct = log_parts <= kGroupMaxLog;
     const bool persistent = a.mode == LINE_MODE_PERSISTENT;
+    const bool hogwild = a.mode == LINE_MODE_HOGWILD;  // records only: no grouping, slab or apply
     // shared segments (two or more entries) and long ones (more than kChunk)
     // per batch, at most
     const uint32_t mcap = (uint32_t)(a.batch * R / 2 + 1);
@@ -1705,6 +1615,11 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     if ((e = ws->init(device)) != cudaSuccess) return e;
     // every scratch buffer and its size for this call
     auto each = [&](auto&& f) -> bool {
+        if (hogwild) {
+            for (auto& cs : ws->set)
+                if (!f(cs.rec, sizeof(int32_t) * max_items) || !f(cs.tchunk, 256)) return false;
+            return true;
+        }
         if (!f(ws->items0, sizeof(uint64_t) * max_items) || !f(ws->items1, sizeof(uint64_t) * max_items) ||
             !f(ws->gcnt, sizeof(uint32_t) * (size_t)nb * parts * kBuckets) ||
             !f(ws->boff, sizeof(uint32_t) * (size_t)nb * (kBuckets + 1)) || !f(ws->counters, 256) ||
@@ -1779,7 +1694,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     pp.K = a.K;
     pp.order = a.order;
     pp.walk = a.walk_len > 0;
-    pp.items = (uint64_t*)ws->items0.p;
+    pp.items = hogwild ? nullptr : (uint64_t*)ws->items0.p;
 
     WalkParams wp{};
     if (a.walk_len > 0) {
@@ -1794,7 +1709,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         wp.W = a.window;
         wp.P = (uint64_t)a.walk_len * a.window - (uint64_t)a.window * (a.window - 1) / 2;
         wp.R = (uint64_t)R;
-        wp.items = (uint64_t*)ws->items0.p;
+        wp.items = hogwild ? nullptr : (uint64_t*)ws->items0.p;
         wp.ctx_off = a.order == 2 ? (uint32_t)a.n_nodes : 0u;
         wp.slot_bits = kSlotBits;
     }
@@ -1875,50 +1790,55 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
                 if ((e = walk_pairs(wp, ps)) != cudaSuccess) return e;
                 ++launches;
             }
-            k_batch_eta<<<(unsigned)((cb + 127) / 128), 128, 0, ps>>>(cb, t, a.batch, (float)a.lr0, a.lr_schedule,
-                                                                      (float)a.lr_floor, a.lr_total,
-                                                                      (float*)cset.eta.p);
+            if (!hogwild)
+                k_batch_eta<<<(unsigned)((cb + 127) / 128), 128, 0, ps>>>(cb, t, a.batch, (float)a.lr0, a.lr_schedule,
+                                                                          (float)a.lr_floor, a.lr_total,
+                                                                          (float*)cset.eta.p);
         }
-        gq.n_batches = cb;
-        gq.chunk_samples = cs;
-        gq.slot_info = (uint2*)cset.slot_info.p;
-        gq.mdesc = (uint4*)cset.mdesc.p;
-        gq.mcount = (uint32_t*)cset.mcount.p;
-        gq.ldesc = (uint4*)cset.ldesc.p;
-        gq.lcount = (uint32_t*)cset.lcount.p;
-        gq.nseg = persistent ? (uint32_t*)cset.nseg.p : nullptr;
-        if ((e = cudaMemsetAsync(cset.mcount.p, 0, sizeof(uint32_t) * (cb + 1), ps)) != cudaSuccess) return e;
-        if ((e = cudaMemsetAsync(cset.lcount.p, 0, sizeof(uint32_t) * (cb + 1), ps)) != cudaSuccess) return e;
-        if (persistent && (e = cudaMemsetAsync(cset.nseg.p, 0, sizeof(uint32_t) * (cb + 1), ps)) != cudaSuccess) return e;
-        if (direct) {
-            cudaLaunchConfig_t cfg = {};
-            cfg.gridDim = dim3(1u << log_parts, cb);
-            cfg.blockDim = dim3(kGroupThreads);
-            cfg.dynamicSmemBytes = group_smem;
-            cfg.stream = ps;
-            cudaLaunchAttribute attr[1];
-            attr[0].id = cudaLaunchAttributeClusterDimension;
-            attr[0].val.clusterDim.x = 1u << log_parts;
-            attr[0].val.clusterDim.y = 1;
-            attr[0].val.clusterDim.z = 1;
-            cfg.attrs = attr;
-            cfg.numAttrs = 1;
-            if ((e = cudaLaunchKernelEx(&cfg, k_group_cluster, gq, log_parts)) != cudaSuccess) return e;
-            launches += 3;
+        if (!hogwild) {
+            gq.n_batches = cb;
+            gq.chunk_samples = cs;
+            gq.slot_info = (uint2*)cset.slot_info.p;
+            gq.mdesc = (uint4*)cset.mdesc.p;
+            gq.mcount = (uint32_t*)cset.mcount.p;
+            gq.ldesc = (uint4*)cset.ldesc.p;
+            gq.lcount = (uint32_t*)cset.lcount.p;
+            gq.nseg = persistent ? (uint32_t*)cset.nseg.p : nullptr;
+            if ((e = cudaMemsetAsync(cset.mcount.p, 0, sizeof(uint32_t) * (cb + 1), ps)) != cudaSuccess) return e;
+            if ((e = cudaMemsetAsync(cset.lcount.p, 0, sizeof(uint32_t) * (cb + 1), ps)) != cudaSuccess) return e;
+            if (persistent && (e = cudaMemsetAsync(cset.nseg.p, 0, sizeof(uint32_t) * (cb + 1), ps)) != cudaSuccess) return e;
+            if (direct) {
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(1u << log_parts, cb);
+                cfg.blockDim = dim3(kGroupThreads);
+                cfg.dynamicSmemBytes = group_smem;
+                cfg.stream = ps;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = 1u << log_parts;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                if ((e = cudaLaunchKernelEx(&cfg, k_group_cluster, gq, log_parts)) != cudaSuccess) return e;
+                launches += 3;
+            } else {
+                k_bucket_count<<<dim3(parts, cb), kBucketThreads, 0, ps>>>(gq);
+                k_bucket_scatter<<<dim3(parts, cb), kBucketThreads, 0, ps>>>(gq);
+                k_bucket_sort<<<dim3(kBuckets / kSortBucketsPerCta, cb), kSortThreads, sort_smem, ps>>>(gq);
+                launches += 5;
+            }
+            if (persistent) {
+                const unsigned g = (unsigned)std::min<int64_t>((n_items + 255) / 256, 152 * 16);
+                k_prev_lookup<<<g, 256, 0, ps>>>(gq, (const int32_t*)cset.rec.p, a.order == 2 ? (uint32_t)a.n_nodes : 0u,
+                                                 (int32_t*)cset.slot_prev.p);
+                k_item_base<<<1, 32, 0, ps>>>((const uint32_t*)cset.mcount.p, cb, a.batch, cs,
+                                              groups_per_warp(a.dim, a.dtype), (uint64_t*)cset.item_base.p);
+                if ((e = cudaMemsetAsync(cset.arrive.p, 0, sizeof(uint32_t) * n_items, ps)) != cudaSuccess) return e;
+                launches += 2;
+            }
         } else {
-            k_bucket_count<<<dim3(parts, cb), kBucketThreads, 0, ps>>>(gq);
-            k_bucket_scatter<<<dim3(parts, cb), kBucketThreads, 0, ps>>>(gq);
-            k_bucket_sort<<<dim3(kBuckets / kSortBucketsPerCta, cb), kSortThreads, sort_smem, ps>>>(gq);
-            launches += 5;
-        }
-        if (persistent) {
-            const unsigned g = (unsigned)std::min<int64_t>((n_items + 255) / 256, 152 * 16);
-            k_prev_lookup<<<g, 256, 0, ps>>>(gq, (const int32_t*)cset.rec.p, a.order == 2 ? (uint32_t)a.n_nodes : 0u,
-                                             (int32_t*)cset.slot_prev.p);
-            k_item_base<<<1, 32, 0, ps>>>((const uint32_t*)cset.mcount.p, cb, a.batch, cs,
-                                          groups_per_warp(a.dim, a.dtype), (uint64_t*)cset.item_base.p);
-            if ((e = cudaMemsetAsync(cset.arrive.p, 0, sizeof(uint32_t) * n_items, ps)) != cudaSuccess) return e;
-            launches += 2;
+            launches += 1;  // the draws alone
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         if (a.timing) {
@@ -1932,62 +1852,84 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
             if ((e = ws->event(n_ev + 2, &ev)) != cudaSuccess) return e;
             cudaEventRecord(ev, s);
         }
-        dp.rec = (const int32_t*)cset.rec.p;
-        dp.slot_info = (const uint2*)cset.slot_info.p;
-        dp.mdesc = (const uint4*)cset.mdesc.p;
-        dp.mcount = (const uint32_t*)cset.mcount.p;
-        dp.ldesc = (const uint4*)cset.ldesc.p;
-        dp.lcount = (const uint32_t*)cset.lcount.p;
-        dp.eta = (const float*)cset.eta.p;
-        dp.slot_prev = (const int32_t*)cset.slot_prev.p;
-        dp.nseg = (const uint32_t*)cset.nseg.p;
-        dp.arrive = (uint32_t*)cset.arrive.p;
-        dp.item_base = (const uint64_t*)cset.item_base.p;
-        dp.t_chunk = t;
-        dp.chunk_samples = cs;
-        dp.n_batches = cb;
-        if (persistent) {
-            if ((e = cudaMemsetAsync(abort_word, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-            if ((e = cudaMemsetAsync(ws->batch_applied.p, 0, sizeof(uint32_t) * (cb + 1), s)) != cudaSuccess) return e;
-            dp.gen = ++ws->gen;
-        }
-        if (!persistent && a.graph && !ws->graph_failed && cs == max_chunk && c > 0) {
-            // a full chunk: replay this set's captured data phase (the chunk's
-            // first sample index comes from the set's device copy)
-            dp.t_chunk_dev = (const uint64_t*)cset.tchunk.p;
-            DataParams key = dp;
-            key.t_chunk = 0;
-            if (!cset.graph || cset.graph_wpb != a.warps_per_block ||
-                memcmp(&key, &cset.graph_key, sizeof key) != 0) {
-                if (cset.graph) cudaGraphExecDestroy(cset.graph);
-                cset.graph = nullptr;
-                cudaGraph_t g = nullptr;
-                cudaError_t ce = cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal);
-                if (ce == cudaSuccess) {
-                    const cudaError_t le = data(dp, a.warps_per_block, ws->cap);
-                    ce = cudaStreamEndCapture(ws->cap, &g);
-                    if (ce == cudaSuccess) ce = le;
-                }
-                if (ce == cudaSuccess) ce = cudaGraphInstantiate(&cset.graph, g, 0);
-                if (g) cudaGraphDestroy(g);
-                if (ce != cudaSuccess) {
-                    cudaGetLastError();
-                    cset.graph = nullptr;
-                    ws->graph_failed = true;
-                } else {
-                    cset.graph_key = key;
-                    cset.graph_wpb = a.warps_per_block;
-                }
+        if (hogwild) {
+            HogwildParams hp{};
+            hp.U = a.U;
+            hp.C = a.C;
+            hp.order = a.order;
+            hp.K = a.K;
+            hp.n_nodes = a.n_nodes;
+            hp.rec = (const int32_t*)cset.rec.p;
+            hp.chunk_samples = cs;
+            hp.t_chunk = t;
+            hp.batch = a.batch;
+            hp.lr0 = (float)a.lr0;
+            hp.lr_floor = (float)a.lr_floor;
+            hp.lr_schedule = a.lr_schedule;
+            hp.lr_total = a.lr_total;
+            hp.lambda = (float)a.lambda;
+            hp.alpha_neg = (float)a.alpha_neg;
+            hp.seed = a.seed;
+            hp.status = status;
+            if ((e = hogwild_chunk(hp, a.dim, a.dtype, a.hogwild_workers, s)) != cudaSuccess) return e;
+        } else {
+            dp.rec = (const int32_t*)cset.rec.p;
+            dp.slot_info = (const uint2*)cset.slot_info.p;
+            dp.mdesc = (const uint4*)cset.mdesc.p;
+            dp.mcount = (const uint32_t*)cset.mcount.p;
+            dp.ldesc = (const uint4*)cset.ldesc.p;
+            dp.lcount = (const uint32_t*)cset.lcount.p;
+            dp.eta = (const float*)cset.eta.p;
+            dp.slot_prev = (const int32_t*)cset.slot_prev.p;
+            dp.nseg = (const uint32_t*)cset.nseg.p;
+            dp.arrive = (uint32_t*)cset.arrive.p;
+            dp.item_base = (const uint64_t*)cset.item_base.p;
+            dp.t_chunk = t;
+            dp.chunk_samples = cs;
+            dp.n_batches = cb;
+            if (persistent) {
+                if ((e = cudaMemsetAsync(abort_word, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
+                if ((e = cudaMemsetAsync(ws->batch_applied.p, 0, sizeof(uint32_t) * (cb + 1), s)) != cudaSuccess) return e;
+                dp.gen = ++ws->gen;
             }
-            if (cset.graph) {
-                if ((e = cudaGraphLaunch(cset.graph, s)) != cudaSuccess) return e;
+            if (!persistent && a.graph && !ws->graph_failed && cs == max_chunk && c > 0) {
+                // a full chunk: replay this set's captured data phase (the chunk's
+                // first sample index comes from the set's device copy)
+                dp.t_chunk_dev = (const uint64_t*)cset.tchunk.p;
+                DataParams key = dp;
+                key.t_chunk = 0;
+                if (!cset.graph || cset.graph_wpb != a.warps_per_block ||
+                    memcmp(&key, &cset.graph_key, sizeof key) != 0) {
+                    if (cset.graph) cudaGraphExecDestroy(cset.graph);
+                    cset.graph = nullptr;
+                    cudaGraph_t g = nullptr;
+                    cudaError_t ce = cudaStreamBeginCapture(ws->cap, cudaStreamCaptureModeThreadLocal);
+                    if (ce == cudaSuccess) {
+                        const cudaError_t le = data(dp, a.warps_per_block, ws->cap);
+                        ce = cudaStreamEndCapture(ws->cap, &g);
+                        if (ce == cudaSuccess) ce = le;
+                    }
+                    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&cset.graph, g, 0);
+                    if (g) cudaGraphDestroy(g);
+                    if (ce != cudaSuccess) {
+                        cudaGetLastError();
+                        cset.graph = nullptr;
+                        ws->graph_failed = true;
+                    } else {
+                        cset.graph_key = key;
+                        cset.graph_wpb = a.warps_per_block;
+                    }
+                }
+                if (cset.graph) {
+                    if ((e = cudaGraphLaunch(cset.graph, s)) != cudaSuccess) return e;
+                } else {
+                    dp.t_chunk_dev = nullptr;
+                    if ((e = data(dp, a.warps_per_block, s)) != cudaSuccess) return e;
+                }
             } else {
                 dp.t_chunk_dev = nullptr;
                 if ((e = data(dp, a.warps_per_block, s)) != cudaSuccess) return e;
             }
-        } else {
-            dp.t_chunk_dev = nullptr;
-            if ((e = data(dp, a.warps_per_block, s)) != cudaSuccess) return e;
         }
         if (a.timing) {
             if ((e = ws->event(n_ev + 3, &ev)) != cudaSuccess) return e;
@@ -2009,7 +1951,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
             times->prepass_ms += ms1;
             times->update_ms += ms2;
             times->prepass_launches += r.prepass_launches;
-            times->update_launches += persistent ? 1 : 2 * (int64_t)r.batches;
+            times->update_launches += (persistent || hogwild) ? 1 : 2 * (int64_t)r.batches;
             times->update_samples += (uint64_t)r.samples;
         }
     }

@@ -22,7 +22,7 @@ LINE_OK, LINE_ERR_ARG, LINE_ERR_OOM, LINE_ERR_CUDA, LINE_ERR_TIMEOUT, LINE_ERR_S
 DTYPE_F32, DTYPE_BF16 = 0, 1
 TABLE_EDGE, TABLE_NEG = 0, 1
 WHICH_U, WHICH_C = 0, 1
-MODE_BATCHED, MODE_PERSISTENT = 0, 1
+MODE_BATCHED, MODE_PERSISTENT, MODE_HOGWILD = 0, 1, 2
 SCORE_DOT, SCORE_COSINE = 0, 1
 
 
@@ -40,7 +40,8 @@ class TrainOpts(ctypes.Structure):
     _fields_ = [("batch", ctypes.c_int64), ("lambda_", ctypes.c_double), ("alpha_neg", ctypes.c_double),
                 ("sample_offset", ctypes.c_uint64), ("mode", ctypes.c_int), ("spin_limit", ctypes.c_int64),
                 ("chunk_batches", ctypes.c_int), ("warps_per_block", ctypes.c_int), ("timing", ctypes.c_int),
-                ("graph", ctypes.c_int), ("walk_length", ctypes.c_int), ("window", ctypes.c_int)]
+                ("graph", ctypes.c_int), ("walk_length", ctypes.c_int), ("window", ctypes.c_int),
+                ("hogwild_workers", ctypes.c_int)]
 
 
 class TuneOpts(ctypes.Structure):
