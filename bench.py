@@ -207,8 +207,9 @@ def walk_of(args):
     return (args.walk_length, args.window) if args.workload == "rmat20walk" else (0, 0)
 
 
-def cpu_baseline(g, n_samples: int, walk=(0, 0)):
-    """The FP64 oracle, single-threaded, on a prefix of the same workload (order 2)."""
+def cpu_baseline(g, n_samples: int, walk=(0, 0), pairwise=False):
+    """The FP64 oracle, single-threaded, on a prefix of the same workload
+    (order 2): the minibatch oracle, or the per-pair one for the Hogwild mode."""
     import numpy as np
 
     import oracle as O
@@ -216,11 +217,13 @@ def cpu_baseline(g, n_samples: int, walk=(0, 0)):
     U = O.init_uniform(g.n_nodes, DIM, 1)
     C = np.zeros_like(U)
     wk = (O.walk_cumw(g), walk[0], walk[1]) if walk[0] > 0 else None
+    fn = O.train_pairwise if pairwise else O.train
     t0 = time.perf_counter()
-    O.train(T, U, C, order=2, K=K, n_samples=n_samples, seed=11, batch=B, lr_total=20 * 16 * g.n_nodes, walk=wk)
+    fn(T, U, C, order=2, K=K, n_samples=n_samples, seed=11, batch=B, lr_total=20 * 16 * g.n_nodes, walk=wk)
     dt = time.perf_counter() - t0
+    kind = "per-pair" if pairwise else "minibatch"
     return {"value": n_samples / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"order-2 FP64 oracle on the first {n_samples} samples of the workload "
+            "sample": f"order-2 FP64 {kind} oracle on the first {n_samples} samples of the workload "
                       f"(single thread, host has {os.cpu_count()} cores); {dt:.1f} s"}
 
 
@@ -704,7 +707,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(g, args.cpu_samples, walk_of(args))
+        cpu = cpu_baseline(g, args.cpu_samples, walk_of(args), pairwise=mode == L.MODE_HOGWILD)
 
     if rank == 0:
         line = {"metric": metric_of(args), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
