@@ -15,10 +15,11 @@
 //     s = x . c, g = eta (1 - sigma(s)) or -eta alpha_neg sigma(s),
 //     U[u] <- x + (g c - eta lambda x), Ctx[y] <- c + (g x - eta lambda c)
 //     (both from the values before the call; Ctx[y] written last);
-//   - adds each distinct row's net change (final - loaded) to the table
-//     with atomic read-modify-writes: FP32 rows by vector float atomic
-//     adds, BF16 rows by a 64-bit compare-and-swap of 4 values that rounds
-//     the sum stochastically.
+//   - adds each call's change of the context row to the table at once, and
+//     the U row's net change (final - loaded) after the last call, with
+//     atomic read-modify-writes: FP32 rows by vector float atomic adds, BF16
+//     rows by a 64-bit compare-and-swap of 4 values that rounds the sum
+//     stochastically.
 // Inside a sample this is exactly the sequential order of the calls.  Across
 // workers, reads are not synchronised, so a sample may compute on rows that
 // other workers are changing, but no worker's change is overwritten by
@@ -38,19 +39,20 @@ namespace {
 constexpr int kHogWarps = 4;   // warps per block, at most (fewer when a block's stages exceed the shared memory)
 constexpr int kCasTries = 256;  // BF16: compare-and-swap attempts before a plain store
 
-// Shared memory per lane group: the staged rows, the rows as loaded, then the
-// record and the first-occurrence slot of each slot, rounded up to 16 bytes.
+// Shared memory per lane group: the staged rows, then the record and the
+// first-occurrence slot of each slot, rounded up to 16 bytes.
 __host__ __device__ inline size_t group_bytes(int dim, int K) {
-    return (sizeof(float) * 2 * (size_t)(K + 2) * dim + sizeof(int32_t) * 2 * (K + 2) + 15) & ~(size_t)15;
+    return (sizeof(float) * (size_t)(K + 2) * dim + sizeof(int32_t) * 2 * (K + 2) + 15) & ~(size_t)15;
 }
 
 // table[row] += d for this lane's values.  BF16: each 4-value word is
-// replaced by its sum with d rounded stochastically (the bits of store_row's
-// key for sample t), retried while other workers change the word; after
-// kCasTries attempts the last sum is stored plainly.
+// replaced by its sum with d rounded stochastically (the SplitMix64 bits of
+// the row write's key, with `key` in place of the batch start), retried
+// while other workers change the word; after kCasTries attempts the last
+// sum is stored plainly.
 template <int D, int DT>
 __device__ __forceinline__ void add_row(void* table, int64_t row, int lig, const float (&d)[Geom<D, DT>::E],
-                                        uint64_t seed, uint64_t t, uint32_t table_id) {
+                                        uint64_t seed, uint64_t key, uint32_t table_id) {
     using G = Geom<D, DT>;
     if constexpr (DT == LINE_DTYPE_F32) {
         float4* p = reinterpret_cast<float4*>(reinterpret_cast<float*>(table) + row * D + lig * G::E);
@@ -62,7 +64,7 @@ __device__ __forceinline__ void add_row(void* table, int64_t row, int lig, const
 #pragma unroll
         for (int q = 0; q < G::NV; ++q) {
             const uint32_t k4 = (uint32_t)((lig * G::E + 4 * q) >> 2);
-            const uint64_t r = sr_bits(seed, table_id, (uint64_t)row, t, k4);
+            const uint64_t r = sr_bits(seed, table_id, (uint64_t)row, key, k4);
             const uint32_t r0 = (uint32_t)r, r1 = (uint32_t)(r >> 32);
             unsigned long long old = __ldcg(p + q), next = old;
             for (int it = 0; it < kCasTries; ++it) {
@@ -94,8 +96,7 @@ __global__ void __launch_bounds__(kHogWarps * 32) k_hogwild(HogwildParams p) {
     const int gid = warp * G::GPW + grp;
     unsigned char* base = s_raw + (size_t)gid * group_bytes(D, p.K);
     float* stage = reinterpret_cast<float*>(base);
-    float* first = stage + (size_t)R * D;  // the rows as loaded
-    int32_t* srow = reinterpret_cast<int32_t*>(first + (size_t)R * D);
+    int32_t* srow = reinterpret_cast<int32_t*>(stage + (size_t)R * D);
     int32_t* sid = srow + R;
     const int64_t worker = ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * G::GPW + grp;
     const int64_t nw = p.workers;
@@ -108,31 +109,54 @@ __global__ void __launch_bounds__(kHogWarps * 32) k_hogwild(HogwildParams p) {
     for (int64_t r = 0; r < rounds; ++r) {
         const int64_t s = r * nw + worker;
         const bool active = worker < nw && s < n;
-        for (int k = lig; k < R; k += G::L) {
-            int32_t row = active ? __ldg(p.rec + s * R + k) : 0;
-            if (active && (row < 0 || row >= p.n_nodes)) {
-                atomicOr(p.status, DEV_ERR_INDEX);
-                row = 0;
-            }
-            srow[k] = row;
-        }
-        __syncwarp(gm);
-        // first slot holding the same row of the same table
-        for (int k = lig; k < R; k += G::L) {
-            const uint32_t tk = k == 0 ? 0u : ctx_tab;
-            int id = k;
-            for (int q = 0; q < k; ++q) {
-                const uint32_t tq = q == 0 ? 0u : ctx_tab;
-                if (tq == tk && srow[q] == srow[k]) {
-                    id = q;
-                    break;
+        if (R <= G::L) {
+            // one slot per lane: the first slot of the worker holding the
+            // same row of the same table, by matching keys across the warp
+            int32_t row = 0;
+            if (active && lig < R) {
+                row = __ldg(p.rec + s * R + lig);
+                if (row < 0 || row >= p.n_nodes) {
+                    atomicOr(p.status, DEV_ERR_INDEX);
+                    row = 0;
                 }
             }
-            sid[k] = id;
+            const uint32_t tk = lig == 0 ? 0u : ctx_tab;
+            const unsigned long long key = lig < R ? ((unsigned long long)gid << 40) | ((unsigned long long)tk << 32) |
+                                                         (unsigned long long)(uint32_t)row
+                                                   : (1ull << 63) | (unsigned long long)lane;
+            const unsigned m = __match_any_sync(0xFFFFFFFFu, key);
+            if (lig < R) {
+                srow[lig] = row;
+                sid[lig] = __ffs(m) - 1 - grp * G::L;
+            }
+        } else {
+            for (int k = lig; k < R; k += G::L) {
+                int32_t row = active ? __ldg(p.rec + s * R + k) : 0;
+                if (active && (row < 0 || row >= p.n_nodes)) {
+                    atomicOr(p.status, DEV_ERR_INDEX);
+                    row = 0;
+                }
+                srow[k] = row;
+            }
+            __syncwarp(gm);
+            for (int k = lig; k < R; k += G::L) {
+                const uint32_t tk = k == 0 ? 0u : ctx_tab;
+                int id = k;
+                for (int q = 0; q < k; ++q) {
+                    const uint32_t tq = q == 0 ? 0u : ctx_tab;
+                    if (tq == tk && srow[q] == srow[k]) {
+                        id = q;
+                        break;
+                    }
+                }
+                sid[k] = id;
+            }
         }
         __syncwarp(gm);
-        // stage the distinct rows, up to CH loads in flight per lane
-        constexpr int CH = G::E <= 4 ? 8 : 4;
+        // the U row into registers, the distinct context rows into the
+        // stage, up to CH loads in flight per lane
+        constexpr int CH = 4;
+        float x[G::E], x0[G::E];
         if (active) {
             for (int k0 = 0; k0 < R; k0 += CH) {
                 float v[CH][G::E];
@@ -141,44 +165,38 @@ __global__ void __launch_bounds__(kHogWarps * 32) k_hogwild(HogwildParams p) {
                     const int k = k0 + kk;
                     if (k < R && sid[k] == k) load_row<D, DT>(k == 0 ? p.U : ctx, srow[k], lig, v[kk]);
                 }
+                if (k0 == 0) {
+#pragma unroll
+                    for (int e = 0; e < G::E; ++e) x0[e] = v[0][e];
+                }
 #pragma unroll
                 for (int kk = 0; kk < CH; ++kk) {
                     const int k = k0 + kk;
-                    if (k < R && sid[k] == k) {
+                    if (k > 0 && k < R && sid[k] == k) {
                         float4* st = reinterpret_cast<float4*>(stage + (size_t)k * D + lig * G::E);
-                        float4* st0 = reinterpret_cast<float4*>(first + (size_t)k * D + lig * G::E);
 #pragma unroll
-                        for (int q = 0; q < G::NV; ++q) {
-                            const float4 a = make_float4(v[kk][4 * q], v[kk][4 * q + 1], v[kk][4 * q + 2], v[kk][4 * q + 3]);
-                            st[q] = a;
-                            st0[q] = a;
-                        }
+                        for (int q = 0; q < G::NV; ++q)
+                            st[q] = make_float4(v[kk][4 * q], v[kk][4 * q + 1], v[kk][4 * q + 2], v[kk][4 * q + 3]);
                     }
                 }
             }
+        } else {
+#pragma unroll
+            for (int e = 0; e < G::E; ++e) x0[e] = 0.0f;
         }
+#pragma unroll
+        for (int e = 0; e < G::E; ++e) x[e] = x0[e];
         __syncwarp(gm);
-        const uint64_t t = p.t_chunk + (uint64_t)(active ? s : 0);
+        const uint32_t sl = active ? (uint32_t)s : 0u;  // s < 2^26 within a chunk
+        const uint64_t t = p.t_chunk + sl;
         float eta = p.lr0;
         if (p.lr_schedule == 1) {
-            const uint64_t t0 = p.t_chunk + (uint64_t)((active ? s : 0) / p.batch) * (uint64_t)p.batch;
+            const uint64_t t0 = p.t_chunk + (uint64_t)(sl / (uint32_t)p.batch) * (uint64_t)p.batch;
             float f = t0 >= p.lr_total ? 0.0f : (float)(p.lr_total - t0) / (float)p.lr_total;
             if (f < p.lr_floor) f = p.lr_floor;
             eta = p.lr0 * f;
         }
         const float etalam = eta * p.lambda;
-        float x[G::E];
-        {
-            const float4* ld = reinterpret_cast<const float4*>(stage + lig * G::E);
-#pragma unroll
-            for (int q = 0; q < G::NV; ++q) {
-                const float4 a = ld[q];
-                x[4 * q] = a.x;
-                x[4 * q + 1] = a.y;
-                x[4 * q + 2] = a.z;
-                x[4 * q + 3] = a.w;
-            }
-        }
         for (int j = 0; j <= p.K; ++j) {
             const int cj = sid[1 + j];
             float c[G::E];
@@ -202,42 +220,30 @@ __global__ void __launch_bounds__(kHogWarps * 32) k_hogwild(HogwildParams p) {
             sdot = group_sum<G::L>(sdot);
             const float sig = 1.0f / (1.0f + expf(-sdot));
             const float g = j == 0 ? eta * (1.0f - sig) : -eta * p.alpha_neg * sig;
-            float cn[G::E];
+            float dc[G::E];
 #pragma unroll
             for (int e = 0; e < G::E; ++e) {
-                cn[e] = c[e] + (g * x[e] - etalam * c[e]);
+                dc[e] = g * x[e] - etalam * c[e];
                 x[e] = x[e] + (g * c[e] - etalam * x[e]);
             }
             if (cj == 0) {
                 // order 1 with y = u: the context write comes last and stays
 #pragma unroll
-                for (int e = 0; e < G::E; ++e) x[e] = cn[e];
+                for (int e = 0; e < G::E; ++e) x[e] = c[e] + dc[e];
             } else {
                 float4* st = reinterpret_cast<float4*>(stage + (size_t)cj * D + lig * G::E);
 #pragma unroll
-                for (int q = 0; q < G::NV; ++q) st[q] = make_float4(cn[4 * q], cn[4 * q + 1], cn[4 * q + 2], cn[4 * q + 3]);
+                for (int q = 0; q < G::NV; ++q)
+                    st[q] = make_float4(c[4 * q] + dc[4 * q], c[4 * q + 1] + dc[4 * q + 1], c[4 * q + 2] + dc[4 * q + 2],
+                                        c[4 * q + 3] + dc[4 * q + 3]);
+                if (active) add_row<D, DT>(ctx, srow[cj], lig, dc, p.seed, t * 64u + 1u + (uint64_t)j, ctx_tab);
             }
         }
         if (active) {
-            for (int k = 0; k < R; ++k) {
-                if (sid[k] != k) continue;
-                float d[G::E];
-                const float4* ld = reinterpret_cast<const float4*>(stage + (size_t)k * D + lig * G::E);
-                const float4* ld0 = reinterpret_cast<const float4*>(first + (size_t)k * D + lig * G::E);
+            float d[G::E];
 #pragma unroll
-                for (int q = 0; q < G::NV; ++q) {
-                    const float4 a = ld[q], b = ld0[q];
-                    d[4 * q] = a.x - b.x;
-                    d[4 * q + 1] = a.y - b.y;
-                    d[4 * q + 2] = a.z - b.z;
-                    d[4 * q + 3] = a.w - b.w;
-                }
-                if (k == 0) {
-#pragma unroll
-                    for (int e = 0; e < G::E; ++e) d[e] = x[e] - first[lig * G::E + e];
-                }
-                add_row<D, DT>(k == 0 ? p.U : ctx, srow[k], lig, d, p.seed, t, k == 0 ? 0u : ctx_tab);
-            }
+            for (int e = 0; e < G::E; ++e) d[e] = x[e] - x0[e];
+            add_row<D, DT>(p.U, srow[0], lig, d, p.seed, t * 64u, 0u);
         }
         __syncwarp(gm);  // the stage is rewritten by the next round
     }
