@@ -665,10 +665,11 @@ def main():
     if concurrent:
         # counted from the schedule: per order and step, two launches per
         # batch and three pre-pass launches per chunk of 64 batches (four
-        # with the walk sampler)
+        # with the walk sampler); Hogwild: the draws (+ walks) and one update
+        # launch per chunk of 64 batches (256 with walks)
         batches = -(-S // B)
-        chunks = -(-batches // 64)
-        if mode == L.MODE_HOGWILD:  # per chunk: the draws (+ walks) and one update launch
+        chunks = -(-batches // (256 if mode == L.MODE_HOGWILD and walk_len else 64))
+        if mode == L.MODE_HOGWILD:
             launches = int(2 * args.steps * chunks * (2 + (walk_len > 0)))
         else:
             launches = int(2 * args.steps * (2 * batches + (3 + (walk_len > 0)) * chunks))

@@ -17,9 +17,9 @@
 //     (both from the values before the call; Ctx[y] written last);
 //   - adds each call's change of the context row to the table at once, and
 //     the U row's net change (final - loaded) after the last call, with
-//     atomic read-modify-writes: FP32 rows by vector float atomic adds, BF16
-//     rows by a 64-bit compare-and-swap of 4 values that rounds the sum
-//     stochastically.
+//     atomic adds: FP32 rows by vector float adds, BF16 rows by BF16 adds
+//     of the change plus one unit in the last place of uniform noise, which
+//     makes the rounding stochastic in expectation.
 // Inside a sample this is exactly the sequential order of the calls.  Across
 // workers, reads are not synchronised, so a sample may compute on rows that
 // other workers are changing, but no worker's change is overwritten by
@@ -37,7 +37,6 @@ namespace line {
 namespace {
 
 constexpr int kHogWarps = 4;   // warps per block, at most (fewer when a block's stages exceed the shared memory)
-constexpr int kCasTries = 256;  // BF16: compare-and-swap attempts before a plain store
 
 // Shared memory per lane group: the staged rows, then the record and the
 // first-occurrence slot of each slot, rounded up to 16 bytes.
@@ -45,42 +44,46 @@ __host__ __device__ inline size_t group_bytes(int dim, int K) {
     return (sizeof(float) * (size_t)(K + 2) * dim + sizeof(int32_t) * 2 * (K + 2) + 15) & ~(size_t)15;
 }
 
-// table[row] += d for this lane's values.  BF16: each 4-value word is
-// replaced by its sum with d rounded stochastically (the SplitMix64 bits of
-// the row write's key, with `key` in place of the batch start), retried
-// while other workers change the word; after kCasTries attempts the last
-// sum is stored plainly.
+// Spacing of BF16 values (8 significant bits) around v; below the normal
+// range, that of the smallest normal binade.
+__device__ __forceinline__ float bf16_ulp(float v) {
+    const uint32_t e = (__float_as_uint(v) >> 23) & 0xFFu;
+    return __uint_as_float((e > 8u ? e - 7u : 1u) << 23);
+}
+
+// table[row] += d for this lane's values, as fire-and-forget atomics.
+// FP32: vector float adds.  BF16: the hardware BF16 add rounds to nearest,
+// which would drop every change below half a unit in the last place; so
+// each change first gets uniform noise of one unit in the last place of
+// `ref` (the value the worker saw; noise from the SplitMix64 bits of the
+// row write's key, with `key` in place of the batch start).  The rounded
+// sum is then correct in expectation, as with stochastic rounding.
 template <int D, int DT>
 __device__ __forceinline__ void add_row(void* table, int64_t row, int lig, const float (&d)[Geom<D, DT>::E],
-                                        uint64_t seed, uint64_t key, uint32_t table_id) {
+                                        const float (&ref)[Geom<D, DT>::E], uint64_t seed, uint64_t key,
+                                        uint32_t table_id) {
     using G = Geom<D, DT>;
     if constexpr (DT == LINE_DTYPE_F32) {
         float4* p = reinterpret_cast<float4*>(reinterpret_cast<float*>(table) + row * D + lig * G::E);
 #pragma unroll
         for (int q = 0; q < G::NV; ++q) atomicAdd(p + q, make_float4(d[4 * q], d[4 * q + 1], d[4 * q + 2], d[4 * q + 3]));
     } else {
-        unsigned long long* p =
-            reinterpret_cast<unsigned long long*>(reinterpret_cast<__nv_bfloat16*>(table) + row * D + lig * G::E);
+        __nv_bfloat162* p = reinterpret_cast<__nv_bfloat162*>(reinterpret_cast<__nv_bfloat16*>(table) + row * D + lig * G::E);
 #pragma unroll
         for (int q = 0; q < G::NV; ++q) {
             const uint32_t k4 = (uint32_t)((lig * G::E + 4 * q) >> 2);
             const uint64_t r = sr_bits(seed, table_id, (uint64_t)row, key, k4);
-            const uint32_t r0 = (uint32_t)r, r1 = (uint32_t)(r >> 32);
-            unsigned long long old = __ldcg(p + q), next = old;
-            for (int it = 0; it < kCasTries; ++it) {
-                const uint32_t lo = (uint32_t)old, hi = (uint32_t)(old >> 32);
-                const float v0 = __uint_as_float(lo << 16) + d[4 * q];
-                const float v1 = __uint_as_float(lo & 0xFFFF0000u) + d[4 * q + 1];
-                const float v2 = __uint_as_float(hi << 16) + d[4 * q + 2];
-                const float v3 = __uint_as_float(hi & 0xFFFF0000u) + d[4 * q + 3];
-                const uint32_t x = (uint32_t)bf16_sr(v0, r0) | ((uint32_t)bf16_sr(v1, r0 >> 16) << 16);
-                const uint32_t y = (uint32_t)bf16_sr(v2, r1) | ((uint32_t)bf16_sr(v3, r1 >> 16) << 16);
-                next = ((unsigned long long)y << 32) | x;
-                const unsigned long long prev = atomicCAS(p + q, old, next);
-                if (prev == old) break;
-                old = prev;
-                if (it == kCasTries - 1) __stcg(p + q, next);
+            float dd[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float u = (float)((uint32_t)(r >> (16 * i)) & 0xFFFFu) * (1.0f / 65536.0f) - 0.5f;
+                dd[i] = fmaf(u, bf16_ulp(ref[4 * q + i]), d[4 * q + i]);
             }
+            const __nv_bfloat162 lo = __floats2bfloat162_rn(dd[0], dd[1]), hi = __floats2bfloat162_rn(dd[2], dd[3]);
+            // one 8-byte vector reduction (two BF16 pairs)
+            asm volatile("red.global.add.noftz.v2.bf16x2 [%0], {%1, %2};" ::"l"(p + 2 * q),
+                         "r"(*reinterpret_cast<const uint32_t*>(&lo)), "r"(*reinterpret_cast<const uint32_t*>(&hi))
+                         : "memory");
         }
     }
 }
@@ -236,14 +239,14 @@ __global__ void __launch_bounds__(kHogWarps * 32) k_hogwild(HogwildParams p) {
                 for (int q = 0; q < G::NV; ++q)
                     st[q] = make_float4(c[4 * q] + dc[4 * q], c[4 * q + 1] + dc[4 * q + 1], c[4 * q + 2] + dc[4 * q + 2],
                                         c[4 * q + 3] + dc[4 * q + 3]);
-                if (active) add_row<D, DT>(ctx, srow[cj], lig, dc, p.seed, t * 64u + 1u + (uint64_t)j, ctx_tab);
+                if (active) add_row<D, DT>(ctx, srow[cj], lig, dc, c, p.seed, t * 64u + 1u + (uint64_t)j, ctx_tab);
             }
         }
         if (active) {
             float d[G::E];
 #pragma unroll
             for (int e = 0; e < G::E; ++e) d[e] = x[e] - x0[e];
-            add_row<D, DT>(p.U, srow[0], lig, d, p.seed, t * 64u, 0u);
+            add_row<D, DT>(p.U, srow[0], lig, d, x0, p.seed, t * 64u, 0u);
         }
         __syncwarp(gm);  // the stage is rewritten by the next round
     }

@@ -1578,9 +1578,14 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         *err = "too many nodes for 32-bit row ids";
         return cudaErrorInvalidValue;
     }
-    // batches per chunk: about 2^18 samples, limited by 31-bit positions and
-    // by the chunk-sample field of item values
-    int64_t nb = a.chunk_batches > 0 ? a.chunk_batches : std::max<int64_t>(1, (int64_t(1) << 18) / a.batch);
+    // batches per chunk: about 2^18 samples (2^20 for walk pairs in the
+    // Hogwild schedule, whose faster update launch would otherwise wait for
+    // the next chunk's walks: a walk's steps are sequential, so a chunk's
+    // walks take about the same time whatever their number), limited by
+    // 31-bit positions and by the chunk-sample field of item values
+    const bool long_chunks = a.mode == LINE_MODE_HOGWILD && a.walk_len > 0;
+    int64_t nb = a.chunk_batches > 0 ? a.chunk_batches
+                                     : std::max<int64_t>(1, (int64_t(1) << (long_chunks ? 20 : 18)) / a.batch);
     while (nb > 1 && ((uint64_t)nb * (uint64_t)a.batch * (uint64_t)R >= (1ull << 31) ||
                       (uint64_t)nb * (uint64_t)a.batch > (1ull << (32 - kSlotBits))))
         nb >>= 1;

@@ -11,8 +11,10 @@
 // i = 0 .. L-1, k = 1 .. W, i + k <= L, in (i, k) order.
 //
 // One warp per walk: the L steps are sequential, each a row_ptr lookup and a
-// lane-parallel search of cw (32 probes per round, ballot); the nodes stay in
-// shared memory while the warp writes the pairs of the samples in range.
+// lane-parallel search of cw.  A node of at most 32 arcs takes one round of
+// loads (every arc's running sum and head, then a ballot); larger ones a
+// search of 32 probes per round.  The nodes stay in shared memory while the
+// warp writes the pairs of the samples in range.
 #include <algorithm>
 
 #include "line_internal.cuh"
@@ -118,9 +120,20 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk_pairs(WalkParams p) {
                 const uint4 w = draw_words(p.seed, kWalkDomain, wk, (uint32_t)i);
                 const uint64_t r = (((uint64_t)w.y << 32) | (uint64_t)w.x) >> 11;
                 const double u = (double)r * 0x1p-53;
-                const double target = u * __ldg(p.cw + hi - 1);
-                const int64_t f = first_above(p.cw, lo, hi, target, lane);
-                next = __ldg(p.dst + (f < hi ? f : hi - 1));
+                const int64_t deg = hi - lo;
+                if (deg <= 32) {
+                    // one round of loads: every arc's running sum and head
+                    const bool in = lane < deg;
+                    const double cwl = in ? __ldg(p.cw + lo + lane) : 0.0;
+                    const int32_t dl = in ? __ldg(p.dst + lo + lane) : 0;
+                    const double target = u * __shfl_sync(0xFFFFFFFFu, cwl, (int)deg - 1);
+                    const unsigned m = __ballot_sync(0xFFFFFFFFu, in && cwl > target);
+                    next = __shfl_sync(0xFFFFFFFFu, dl, m ? __ffs(m) - 1 : (int)deg - 1);
+                } else {
+                    const double target = u * __ldg(p.cw + hi - 1);
+                    const int64_t f = first_above(p.cw, lo, hi, target, lane);
+                    next = __ldg(p.dst + (f < hi ? f : hi - 1));
+                }
             }
             prev = x;
             x = next;
