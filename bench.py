@@ -16,6 +16,12 @@ Other workloads (``--workload``; not the default line):
   by arc weight, weighted steps, pairs within a window of 2 (Algorithms 2-3,
   the local walk); the negatives, update and schedule are unchanged.
 
+* ``reuse20`` - the walk-reuse ablation (a single-device form of the paper's
+  Reuse-Spill variant): R-MAT 20 with 10% of the edges held out, orders 1
+  and 2 trained concurrently on walk pairs (L=100, W=2) for ``--epochs``
+  epochs, each walk's pairs serving r = 1, 4 and 16 passes, in the
+  minibatch and the Hogwild schedule: updates/s, second-order loss and
+  link-prediction AUC of each.
 * ``dchung22`` - weighted directed Chung-Lu graph, 4,194,304 nodes, 2^26 arc
   draws (out-weights power law 2.2, lognormal(0,1) weights); order 2, d=128,
   K=5: the FP32 path at B=4096 against BF16 tables with stochastic rounding
@@ -81,10 +87,11 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-samples", type=int, default=1 << 20)
-    p.add_argument("--workload", default="rmat20", choices=["rmat20", "rmat20walk", "dchung22", "warm22", "rmat24"])
+    p.add_argument("--workload", default="rmat20",
+                   choices=["rmat20", "rmat20walk", "reuse20", "dchung22", "warm22", "rmat24"])
     p.add_argument("--walk-length", type=int, default=100, help="rmat20walk: steps per walk")
     p.add_argument("--window", type=int, default=2, help="rmat20walk: pair window")
-    p.add_argument("--epochs", type=int, default=10, help="rmat24: samples per order = epochs x |E|")
+    p.add_argument("--epochs", type=int, default=10, help="rmat24, reuse20: samples per order = epochs x |E|")
     p.add_argument("--checkpoints", type=int, default=10, help="warm22: refinement epochs (checkpoints)")
     return p.parse_args()
 
@@ -548,6 +555,59 @@ def run_rmat24(args):
     ctx.close()
 
 
+def run_reuse20(args):
+    """Walk reuse r in {1, 4, 16} x {minibatch, Hogwild}: throughput vs quality."""
+    import torch
+
+    from paper_2604_09419_gb300 import inputs as I
+    from paper_2604_09419_gb300 import line as L
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    g = I.rmat20()
+    tr, hs, hd = I.split_edges(g, 0.1, seed=4)
+    ns, nd = I.non_edges(g, len(hs), seed=7)
+    ctx = L.Context(local, stream.cuda_stream)
+    ctx.build_alias(tr.n_nodes, torch.from_numpy(tr.src).cuda(), torch.from_numpy(tr.dst).cuda(),
+                    torch.from_numpy(tr.w).cuda())
+    n = args.epochs * tr.n_arcs // B * B
+    peak, peak_kind = peaks()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    for mode, mname in ((L.MODE_BATCHED, "batched"), (L.MODE_HOGWILD, "hogwild")):
+        for r in (1, 4, 16):
+            ctx.init_embeddings(1, DIM, L.DTYPE_F32, seed=1)
+            ctx.init_embeddings(2, DIM, L.DTYPE_F32, seed=2)
+            o = L.train_opts_default()
+            o.batch = B
+            o.mode = mode
+            o.walk_length, o.window, o.walk_reuse = args.walk_length, args.window, r
+            torch.cuda.synchronize()
+            with ClockSampler(local) as clk:
+                ev0.record(stream)
+                ctx.train_orders(DIM, K, n, 5, total=n, opts=o)
+                ev1.record(stream)
+                torch.cuda.synchronize()
+            sec = ev0.elapsed_time(ev1) / 1e3
+            rate = 2 * n / sec
+            rows.append({"mode": mname, "reuse": r, "value": rate, "seconds": sec,
+                         "roofline_frac": rate * ALG_BYTES_UPDATE / 1e9 / peak,
+                         "auc_orders_1_2": ctx.eval_auc(3, hs, hd, ns, nd)[0],
+                         "auc_order_2": ctx.eval_auc(2, hs, hd, ns, nd)[0],
+                         "loss_order_2": ctx.eval_loss(2, K, 99, 1 << 20), "clocks": clk.summary()})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+    line = {"metric": "walk-pair updates/s (d=128,K=5) and AUC by walk reuse", "unit": UNIT,
+            "value": max(x["value"] for x in rows), "n_gpus": 1, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": f"rmat20_walk{args.walk_length}w{args.window}_reuse_ablation",
+                       "graph": "R-MAT scale 20, edge factor 16, (.57,.19,.19,.05), symmetrised; 10% of edges held out",
+                       "n_nodes": tr.n_nodes, "n_arcs_train": tr.n_arcs, "epochs": args.epochs,
+                       "samples_per_order": n, "auc_pairs": len(hs), "peak_gbs": peak, "peak_kind": peak_kind},
+            "runs": rows}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -563,6 +623,9 @@ def main():
         return
     if args.workload == "rmat24":
         run_rmat24(args)
+        return
+    if args.workload == "reuse20":
+        run_reuse20(args)
         return
     import numpy as np
     import torch

@@ -114,6 +114,9 @@ typedef struct {
     int window;              /* W: pair window of the walk sampler, 1 <= W <= L */
     int hogwild_workers;     /* LINE_MODE_HOGWILD: samples in flight at once (>= 0; 0: one
                                 resident wave of the GPU, one worker per lane group) */
+    int walk_reuse;          /* r: passes over each walk's pairs, 1..1024 (0 means 1): sample t
+                                takes pair t mod P of walk t / (r P) - a single-device form of
+                                the Reuse-Spill variant (§IV-C) */
 } line_train_opts;
 
 /* LINE_MODE_HOGWILD: the local path of Algorithm 1 - LineUpdate applied pair
@@ -193,12 +196,15 @@ LINE_API line_status line_sample_debug(line_ctx* ctx, int K, uint64_t seed, uint
  * out-arcs steps back to nodes[i-1].  The pairs of a walk are
  * (nodes[i], nodes[i+k]), i = 0 .. L-1, k = 1 .. W, i + k <= L, in (i, k)
  * order.  Negatives are the edge sampler's (domain 0, calls 1..K at counter
- * t).  The first call builds the per-node arc offsets and weight sums
+ * t).  With reuse r > 1 each walk's pairs serve r passes in a row: sample
+ * t takes pair t mod P of walk t / (r P).  The first call builds the
+ * per-node arc offsets and weight sums
  * (12 bytes per arc with the kept weights, 8 per node), freed with the graph.
- * Errors: LINE_ERR_ARG (K, count, or not 1 <= W <= L <= 1024),
+ * Errors: LINE_ERR_ARG (K, count, not 1 <= W <= L <= 1024, or reuse
+ * outside 1..1024),
  * LINE_ERR_STATE (no graph). */
 LINE_API line_status line_sample_walk_debug(line_ctx* ctx, int K, uint64_t seed, int walk_length, int window,
-                                            uint64_t t0, int64_t count, int32_t* out);
+                                            int reuse, uint64_t t0, int64_t count, int32_t* out);
 
 /* (Re)create the tables of one order: order 1 has U only (the context of a
  * pair is U, first-order proximity), order 2 has U and C (second order).

@@ -93,14 +93,14 @@ def lib():
             L.orc_batch_lr.restype = _dbl
             L.orc_train.argtypes = TABLE_ARGS + [_int, _int, _int, _dbl, _int, _dbl, _u64, _u64, _u64,
                                                  _i64, _dbl, _dbl, _u64, _f64p, ctypes.c_void_p, ctypes.c_void_p,
-                                                 _int, _int]
+                                                 _int, _int, _int]
             L.orc_train_pairwise.argtypes = L.orc_train.argtypes
             L.orc_train_pairwise.restype = _int
             L.orc_walk_cumw.argtypes = [_i64, _i32p, ctypes.c_void_p, _f64p]
             L.orc_walk_cumw.restype = None
             L.orc_walk_pairs_per_walk.argtypes = [_int, _int]
             L.orc_walk_pairs_per_walk.restype = _i64
-            L.orc_sample_walk.argtypes = TABLE_ARGS + [_f64p, _u64, _u64, _i64, _int, _int, _int, _i32p]
+            L.orc_sample_walk.argtypes = TABLE_ARGS + [_f64p, _u64, _u64, _i64, _int, _int, _int, _int, _i32p]
             L.orc_sample_walk.restype = _int
             L.orc_train.restype = _int
             L.orc_eval_loss.argtypes = TABLE_ARGS + [_int, _int, _int, _u64, _i64, _f64p, ctypes.c_void_p]
@@ -223,30 +223,39 @@ def walk_pairs_per_walk(L: int, W: int) -> int:
     return lib().orc_walk_pairs_per_walk(L, W)
 
 
-def sample_walk(T: Tables, cw: np.ndarray, seed: int, t0: int, count: int, K: int, L: int, W: int) -> np.ndarray:
-    """[count][K+2] records of the walk sampler (Algorithms 2-3, local walk)."""
+def sample_walk(T: Tables, cw: np.ndarray, seed: int, t0: int, count: int, K: int, L: int, W: int,
+                reuse: int = 1) -> np.ndarray:
+    """[count][K+2] records of the walk sampler (Algorithms 2-3, local walk);
+    with reuse r each walk's pairs serve r passes in a row."""
     out = np.zeros((count, K + 2), np.int32)
-    rc = lib().orc_sample_walk(*T.args(), cw, seed, t0, count, K, L, W, out.reshape(-1))
+    rc = lib().orc_sample_walk(*T.args(), cw, seed, t0, count, K, L, W, reuse, out.reshape(-1))
     if rc:
         raise ValueError(f"orc_sample_walk failed ({rc})")
     return out
+
+
+def _walk_args(walk):
+    if walk is None:
+        return None, 0, 0, 1
+    return (walk[0], walk[1], walk[2], walk[3] if len(walk) > 3 else 1)
 
 
 def train(T: Tables, U: np.ndarray, C, *, order: int, K: int, lr0: float = 0.025, schedule: int = 1,
           lr_floor_frac: float = 1e-4, lr_total: int = 0, n_samples: int, seed: int, batch: int,
           lam: float = 0.0, alpha_neg: float = 1.0, sample_offset: int = 0, walk=None):
     """Minibatch-synchronous LINE in place on FP64 tables U (and C for order 2).
-    walk: None (arcs drawn by weight) or (cw, L, W) for the walk sampler."""
+    walk: None (arcs drawn by weight) or (cw, L, W) or (cw, L, W, reuse) for
+    the walk sampler."""
     assert U.dtype == np.float64 and U.flags.c_contiguous
     dim = U.shape[1]
     cptr = None
     if order == 2:
         assert C is not None and C.dtype == np.float64 and C.flags.c_contiguous and C.shape == U.shape
         cptr = C.ctypes.data
-    cw, L, W = walk if walk is not None else (None, 0, 0)
+    cw, L, W, R = _walk_args(walk)
     rc = lib().orc_train(*T.args(), order, dim, K, lr0, schedule, lr_floor_frac, lr_total, n_samples,
                          seed, batch, lam, alpha_neg, sample_offset, U, cptr,
-                         None if cw is None else cw.ctypes.data, L, W)
+                         None if cw is None else cw.ctypes.data, L, W, R)
     if rc:
         raise ValueError(f"orc_train failed ({rc})")
 
@@ -263,10 +272,10 @@ def train_pairwise(T: Tables, U: np.ndarray, C, *, order: int, K: int, lr0: floa
     if order == 2:
         assert C is not None and C.dtype == np.float64 and C.flags.c_contiguous and C.shape == U.shape
         cptr = C.ctypes.data
-    cw, L, W = walk if walk is not None else (None, 0, 0)
+    cw, L, W, R = _walk_args(walk)
     rc = lib().orc_train_pairwise(*T.args(), order, dim, K, lr0, schedule, lr_floor_frac, lr_total, n_samples,
                                   seed, batch, lam, alpha_neg, sample_offset, U, cptr,
-                                  None if cw is None else cw.ctypes.data, L, W)
+                                  None if cw is None else cw.ctypes.data, L, W, R)
     if rc:
         raise ValueError(f"orc_train_pairwise failed ({rc})")
 

@@ -277,7 +277,9 @@ int orc_sample(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_
 /* (nodes[i], nodes[i+k]) for i = 0 .. L-1, k = 1 .. W, i + k <= L, in       */
 /* (i, k) order: P = L W - W (W - 1) / 2 of them.  Sample t takes pair       */
 /* t mod P of walk t / P; its negatives are the edge sampler's (domain 0,    */
-/* calls 1..K at counter t).                                                 */
+/* calls 1..K at counter t).  With reuse r (a single-device form of the      */
+/* Reuse-Spill variant, §IV-C), each walk's pairs serve r passes in a row:   */
+/* sample t takes pair t mod P of walk t / (r P).                            */
 /* ------------------------------------------------------------------------ */
 #define WALK_DOMAIN 8u
 
@@ -295,6 +297,7 @@ void orc_walk_cumw(int64_t n_arcs, const int32_t* src, const float* w, double* c
 typedef struct {
     orc_tables T;
     const double* cw;
+    int reuse;  /* passes over each walk's pairs (>= 1) */
 } orc_walker;
 
 static int64_t first_arc_of(const orc_tables* T, int32_t v) {
@@ -347,7 +350,7 @@ static void walk_pair(int L, int Wn, int64_t p, int* i_out, int* k_out) {
 static void sample_walk_one(const orc_walker* W, uint64_t seed, uint64_t t, int K, int L, int Wn, int32_t* nodes,
                             int64_t* cached, int32_t* rec) {
     int64_t P = orc_walk_pairs_per_walk(L, Wn);
-    uint64_t wk = t / (uint64_t)P;
+    uint64_t wk = t / ((uint64_t)P * (uint64_t)W->reuse);
     if (*cached != (int64_t)wk) { walk_nodes(W, seed, wk, L, nodes); *cached = (int64_t)wk; }
     int i, k;
     walk_pair(L, Wn, (int64_t)(t % (uint64_t)P), &i, &k);
@@ -363,9 +366,9 @@ static void sample_walk_one(const orc_walker* W, uint64_t seed, uint64_t t, int 
 int orc_sample_walk(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t* dst,
                     const uint32_t* thr_e, const uint32_t* alias_e, const uint32_t* thr_n, const uint32_t* alias_n,
                     const double* cw, uint64_t seed, uint64_t t0, int64_t count, int K, int L, int Wn,
-                    int32_t* out) {
-    if (L < 1 || Wn < 1 || Wn > L) return -1;
-    orc_walker W = {{n_nodes, n_arcs, src, dst, thr_e, alias_e, thr_n, alias_n}, cw};
+                    int reuse, int32_t* out) {
+    if (L < 1 || Wn < 1 || Wn > L || reuse < 1) return -1;
+    orc_walker W = {{n_nodes, n_arcs, src, dst, thr_e, alias_e, thr_n, alias_n}, cw, reuse};
     int32_t* nodes = (int32_t*)malloc(sizeof(int32_t) * (size_t)(L + 1));
     if (!nodes) return -2;
     int64_t cached = -1;
@@ -424,11 +427,12 @@ int orc_train(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t
               const uint32_t* thr_e, const uint32_t* alias_e, const uint32_t* thr_n, const uint32_t* alias_n,
               int order, int dim, int K, double lr0, int schedule, double lr_floor_frac, uint64_t lr_total,
               uint64_t n_samples, uint64_t seed, int64_t batch, double lambda, double alpha_neg,
-              uint64_t sample_offset, double* U, double* C, const double* walk_cw, int walk_len, int window) {
+              uint64_t sample_offset, double* U, double* C, const double* walk_cw, int walk_len, int window,
+              int walk_reuse) {
     if (batch <= 0 || dim <= 0 || K < 0 || (order != 1 && order != 2)) return -1;
-    if (walk_cw && (walk_len < 1 || window < 1 || window > walk_len)) return -1;
+    if (walk_cw && (walk_len < 1 || window < 1 || window > walk_len || walk_reuse < 1)) return -1;
     orc_tables T = {n_nodes, n_arcs, src, dst, thr_e, alias_e, thr_n, alias_n};
-    orc_walker Wk = {T, walk_cw};
+    orc_walker Wk = {T, walk_cw, walk_reuse};
     int32_t* wnodes = walk_cw ? (int32_t*)malloc(sizeof(int32_t) * (size_t)(walk_len + 1)) : NULL;
     int64_t wcached = -1;
     double* Ctx = order == 2 ? C : U;
@@ -511,11 +515,11 @@ int orc_train_pairwise(int64_t n_nodes, int64_t n_arcs, const int32_t* src, cons
                        const uint32_t* alias_n, int order, int dim, int K, double lr0, int schedule,
                        double lr_floor_frac, uint64_t lr_total, uint64_t n_samples, uint64_t seed, int64_t batch,
                        double lambda, double alpha_neg, uint64_t sample_offset, double* U, double* C,
-                       const double* walk_cw, int walk_len, int window) {
+                       const double* walk_cw, int walk_len, int window, int walk_reuse) {
     if (batch <= 0 || dim <= 0 || K < 0 || (order != 1 && order != 2)) return -1;
-    if (walk_cw && (walk_len < 1 || window < 1 || window > walk_len)) return -1;
+    if (walk_cw && (walk_len < 1 || window < 1 || window > walk_len || walk_reuse < 1)) return -1;
     orc_tables T = {n_nodes, n_arcs, src, dst, thr_e, alias_e, thr_n, alias_n};
-    orc_walker Wk = {T, walk_cw};
+    orc_walker Wk = {T, walk_cw, walk_reuse};
     int32_t* wnodes = walk_cw ? (int32_t*)malloc(sizeof(int32_t) * (size_t)(walk_len + 1)) : NULL;
     int64_t wcached = -1;
     double* Ctx = order == 2 ? C : U;

@@ -121,6 +121,7 @@ void line_train_opts_default(line_train_opts* o) {
     o->graph = 1;
     o->walk_length = 0;
     o->window = 0;
+    o->walk_reuse = 1;
     o->hogwild_workers = 0;
 }
 
@@ -291,8 +292,8 @@ line_status line_sample_debug(line_ctx* c, int K, uint64_t seed, uint32_t domain
     return LINE_OK;
 }
 
-line_status line_sample_walk_debug(line_ctx* c, int K, uint64_t seed, int walk_length, int window, uint64_t t0,
-                                   int64_t count, int32_t* out) {
+line_status line_sample_walk_debug(line_ctx* c, int K, uint64_t seed, int walk_length, int window, int reuse,
+                                   uint64_t t0, int64_t count, int32_t* out) {
     line_status st = enter(c);
     if (st) return st;
     if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_sample_walk_debug: no graph");
@@ -300,6 +301,8 @@ line_status line_sample_walk_debug(line_ctx* c, int K, uint64_t seed, int walk_l
         return fail(c, LINE_ERR_ARG, "line_sample_walk_debug: bad arguments");
     if (walk_length < 1 || walk_length > kMaxWalkLen || window < 1 || window > walk_length)
         return fail(c, LINE_ERR_ARG, "line_sample_walk_debug: need 1 <= window <= walk_length <= %d", kMaxWalkLen);
+    if (reuse < 1 || reuse > kMaxWalkReuse)
+        return fail(c, LINE_ERR_ARG, "line_sample_walk_debug: need 1 <= reuse <= %d", kMaxWalkReuse);
     if (count == 0) return LINE_OK;
     if ((st = ensure_walk_tables(c))) return st;
     int32_t* buf = nullptr;
@@ -327,6 +330,7 @@ line_status line_sample_walk_debug(line_ctx* c, int K, uint64_t seed, int walk_l
         wp.L = walk_length;
         wp.W = window;
         wp.P = (uint64_t)walk_length * window - (uint64_t)window * (window - 1) / 2;
+        wp.reuse = (uint32_t)reuse;
         wp.R = (uint64_t)(K + 2);
         wp.rec = rec;
         e = walk_pairs(wp, c->stream);
@@ -387,6 +391,8 @@ line_status make_train_args(line_ctx* c, const char* what, int order, int dim, i
     if (o.walk_length < 0 || o.walk_length > kMaxWalkLen ||
         (o.walk_length > 0 && (o.window < 1 || o.window > o.walk_length)))
         return fail(c, LINE_ERR_ARG, "%s: need 1 <= window <= walk_length <= %d", what, kMaxWalkLen);
+    if (o.walk_reuse < 0 || o.walk_reuse > kMaxWalkReuse)
+        return fail(c, LINE_ERR_ARG, "%s: need 0 <= walk_reuse <= %d", what, kMaxWalkReuse);
     if (o.walk_length > 0) {
         line_status ws = ensure_walk_tables(c);
         if (ws) return ws;
@@ -422,6 +428,7 @@ line_status make_train_args(line_ctx* c, const char* what, int order, int dim, i
     a.hogwild_workers = o.hogwild_workers;
     a.walk_len = o.walk_length;
     a.window = o.walk_length > 0 ? o.window : 0;
+    a.walk_reuse = o.walk_reuse > 0 ? o.walk_reuse : 1;
     a.row_ptr = c->row_ptr;
     a.cw = c->cw;
     a.graph = o.graph;

@@ -140,8 +140,10 @@ cudaError_t convert_rows(const void* src, int src_dtype, void* dst, int dst_dtyp
                          int64_t n_rows, int dim, int64_t n_nodes, uint32_t* status, cudaStream_t s);
 cudaError_t debug_wait(uint32_t* flag, int64_t limit, uint32_t* status, cudaStream_t s);
 
-// walk.cu: the walk sampler (Algorithms 2-3).  Limits: 1 <= W <= L <= kMaxWalkLen.
+// walk.cu: the walk sampler (Algorithms 2-3).  Limits: 1 <= W <= L <= kMaxWalkLen,
+// 1 <= reuse <= kMaxWalkReuse.
 constexpr int kMaxWalkLen = 1024;
+constexpr int kMaxWalkReuse = 1024;
 struct WalkParams {
     const int32_t* src;
     const int32_t* dst;
@@ -154,6 +156,7 @@ struct WalkParams {
     int64_t count;
     int L, W;
     uint64_t P;              // pairs per walk: L W - W (W - 1) / 2
+    uint32_t reuse;          // passes over each walk's pairs (>= 1)
     uint64_t R;              // record stride (K + 2)
     int32_t* rec;            // rec[s R], rec[s R + 1] = the pair of sample t0 + s
     uint64_t* items;         // nullable: grouping items of slots 0 and 1
@@ -241,7 +244,7 @@ struct TrainArgs {
     // walk sampler (walk_len > 0): positive pairs from random walks
     const int64_t* row_ptr;
     const double* cw;
-    int walk_len, window;
+    int walk_len, window, walk_reuse;
     int64_t hogwild_workers;  // LINE_MODE_HOGWILD: concurrent workers (0: one resident wave)
 };
 

@@ -1713,6 +1713,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         wp.L = a.walk_len;
         wp.W = a.window;
         wp.P = (uint64_t)a.walk_len * a.window - (uint64_t)a.window * (a.window - 1) / 2;
+        wp.reuse = (uint32_t)a.walk_reuse;
         wp.R = (uint64_t)R;
         wp.items = hogwild ? nullptr : (uint64_t*)ws->items0.p;
         wp.ctx_off = a.order == 2 ? (uint32_t)a.n_nodes : 0u;

@@ -8,7 +8,9 @@
 // the first arc e of x with cw[e] > target (the last arc if none), cw the
 // running FP64 sum of x's arc weights in arc order.  A node without out-arcs
 // steps back to nodes[i-1].  Pairs of a walk: (nodes[i], nodes[i+k]),
-// i = 0 .. L-1, k = 1 .. W, i + k <= L, in (i, k) order.
+// i = 0 .. L-1, k = 1 .. W, i + k <= L, in (i, k) order.  With reuse r (a
+// single-device form of the Reuse-Spill variant of §IV-C) each walk's pairs
+// serve r passes in a row: sample t takes pair t mod P of walk t / (r P).
 //
 // One warp per walk: the L steps are sequential, each a row_ptr lookup and a
 // lane-parallel search of cw.  A node of at most 32 arcs takes one round of
@@ -98,8 +100,8 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk_pairs(WalkParams p) {
     extern __shared__ int32_t s_nodes[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int32_t* nodes = s_nodes + warp * (p.L + 1);
-    const uint64_t P = p.P;
-    const uint64_t w_first = p.t0 / P, w_last = (p.t0 + (uint64_t)p.count - 1) / P;
+    const uint64_t P = p.P, RP = p.P * (uint64_t)p.reuse;
+    const uint64_t w_first = p.t0 / RP, w_last = (p.t0 + (uint64_t)p.count - 1) / RP;
     for (uint64_t wk = w_first + (uint64_t)blockIdx.x * kWalkWarps + warp; wk <= w_last;
          wk += (uint64_t)gridDim.x * kWalkWarps) {
         int32_t prev, x;
@@ -140,10 +142,10 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk_pairs(WalkParams p) {
             if (lane == 0) nodes[i + 1] = x;
         }
         __syncwarp();
-        const uint64_t s_begin = max(wk * P, p.t0), s_end = min((wk + 1) * P, p.t0 + (uint64_t)p.count);
+        const uint64_t s_begin = max(wk * RP, p.t0), s_end = min((wk + 1) * RP, p.t0 + (uint64_t)p.count);
         for (uint64_t t = s_begin + lane; t < s_end; t += 32) {
             int i, k;
-            pair_of((uint32_t)(t - wk * P), p.L, p.W, &i, &k);
+            pair_of((uint32_t)((t - wk * RP) % P), p.L, p.W, &i, &k);
             const int32_t u = nodes[i], v = nodes[i + k];
             const uint64_t s = t - p.t0;
             p.rec[s * p.R] = u;
@@ -173,7 +175,8 @@ cudaError_t walk_tables(int64_t n_nodes, int64_t n_arcs, const int32_t* src, con
 
 cudaError_t walk_pairs(const WalkParams& p, cudaStream_t s) {
     if (p.count <= 0) return cudaSuccess;
-    const uint64_t n_walks = (p.t0 + (uint64_t)p.count - 1) / p.P - p.t0 / p.P + 1;
+    const uint64_t RP = p.P * (uint64_t)p.reuse;
+    const uint64_t n_walks = (p.t0 + (uint64_t)p.count - 1) / RP - p.t0 / RP + 1;
     const unsigned g = (unsigned)std::min<uint64_t>((n_walks + kWalkWarps - 1) / kWalkWarps, 152 * 16);
     k_walk_pairs<<<g, kWalkWarps * 32, walk_smem_bytes(p.L), s>>>(p);
     return cudaGetLastError();

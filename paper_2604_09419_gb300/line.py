@@ -41,7 +41,7 @@ class TrainOpts(ctypes.Structure):
                 ("sample_offset", ctypes.c_uint64), ("mode", ctypes.c_int), ("spin_limit", ctypes.c_int64),
                 ("chunk_batches", ctypes.c_int), ("warps_per_block", ctypes.c_int), ("timing", ctypes.c_int),
                 ("graph", ctypes.c_int), ("walk_length", ctypes.c_int), ("window", ctypes.c_int),
-                ("hogwild_workers", ctypes.c_int)]
+                ("hogwild_workers", ctypes.c_int), ("walk_reuse", ctypes.c_int)]
 
 
 class TuneOpts(ctypes.Structure):
@@ -71,7 +71,7 @@ def _load():
         "line_get_graph_info": (i32, [vp, ctypes.POINTER(i64), ctypes.POINTER(i64)]),
         "line_get_alias": (i32, [vp, i32, vp, vp]),
         "line_sample_debug": (i32, [vp, i32, u64, u32, u64, i64, vp]),
-        "line_sample_walk_debug": (i32, [vp, i32, u64, i32, i32, u64, i64, vp]),
+        "line_sample_walk_debug": (i32, [vp, i32, u64, i32, i32, i32, u64, i64, vp]),
         "line_init_embeddings": (i32, [vp, i32, i32, i32, u64]),
         "line_train_steps": (i32, [vp, i32, i32, i32, ctypes.POINTER(LR), u64, u64, ctypes.POINTER(TrainOpts)]),
         "line_train_orders": (i32, [vp, i32, i32, ctypes.POINTER(LR), u64, u64, ctypes.POINTER(TrainOpts)]),
@@ -181,8 +181,8 @@ class Context:
     def sample_debug(self, K, seed, domain, t0, count, out):
         return self._ck(lib.line_sample_debug(self.h, K, seed, domain, t0, count, ptr(out)))
 
-    def sample_walk_debug(self, K, seed, walk_length, window, t0, count, out):
-        return self._ck(lib.line_sample_walk_debug(self.h, K, seed, walk_length, window, t0, count, ptr(out)))
+    def sample_walk_debug(self, K, seed, walk_length, window, t0, count, out, reuse=1):
+        return self._ck(lib.line_sample_walk_debug(self.h, K, seed, walk_length, window, reuse, t0, count, ptr(out)))
 
     def init_embeddings(self, order, dim, dtype=DTYPE_F32, seed=0):
         return self._ck(lib.line_init_embeddings(self.h, order, dim, dtype, seed))

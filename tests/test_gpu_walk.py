@@ -9,6 +9,8 @@ oracle, through the C ABI:
 * FP32 training with walk pairs within 1e-5 of the FP64 oracle, in both
   orders, both modes, with walks split across pre-pass chunks, and for the
   concurrent two-order call;
+* walk reuse (each walk's pairs serving r passes): samples bit-exact and
+  training within 1e-5 in the minibatch and the one-worker Hogwild schedule;
 * argument errors.
 """
 import numpy as np
@@ -71,6 +73,34 @@ def test_walk_samples_bit_exact(ctx, name, L, W):
         got = _gpu_walk(ctx, K, seed, L, W, t0, count)
         want = O.sample_walk(T, cw, seed, t0, count, K, L, W)
         assert np.array_equal(got, want), (name, L, W, t0)
+
+
+@pytest.mark.parametrize("name", ["tiny", "dchung"])
+def test_walk_samples_with_reuse_bit_exact(ctx, name):
+    g, T, cw = _setup(ctx, name)
+    L, W, r = 30, 2, 3
+    P = O.walk_pairs_per_walk(L, W)
+    for t0, count, K in [(0, 20_000, 5), (r * P + P // 2, 5000, 1)]:
+        out = np.empty((count, K + 2), np.int32)
+        ctx.sample_walk_debug(K, 77, L, W, t0, count, out, reuse=r)
+        assert np.array_equal(out, O.sample_walk(T, cw, 77, t0, count, K, L, W, reuse=r)), (name, t0)
+
+
+def test_walk_training_with_reuse(ctx):
+    from paper_2604_09419_gb300 import line as L_
+    g, T, cw = _setup(ctx, "tiny")
+    n, B = 40_000, 512
+    for mode in (L_.MODE_BATCHED, L_.MODE_HOGWILD):
+        ctx.init_embeddings(2, 32, L_.DTYPE_F32, seed=1)
+        kw = {"hogwild_workers": 1} if mode == L_.MODE_HOGWILD else {}
+        ctx.train_steps(2, 32, 5, n, 3, batch=B, walk_length=20, window=2, walk_reuse=4, mode=mode, **kw)
+        U, C = G.tables(ctx, g, 2, 32)
+        Uo = O.init_uniform(g.n_nodes, 32, 1)
+        Co = np.zeros_like(Uo)
+        fn = O.train_pairwise if mode == L_.MODE_HOGWILD else O.train
+        fn(T, Uo, Co, order=2, K=5, n_samples=n, seed=3, batch=B, walk=(cw, 20, 2, 4))
+        err = max(np.abs(U - Uo).max(), np.abs(C - Co).max())
+        assert err <= TOL, (mode, err)
 
 
 def test_walk_tables_follow_a_new_graph(ctx):
@@ -154,6 +184,12 @@ def test_walk_argument_errors(ctx):
     from paper_2604_09419_gb300 import line as L_
     _setup(ctx, "tiny")
     ctx.init_embeddings(2, 32, L_.DTYPE_F32, seed=1)
+    with pytest.raises(L_.LineError) as ei:
+        ctx.train_steps(2, 32, 5, 1000, 5, walk_length=10, window=2, walk_reuse=1025)
+    assert ei.value.status == L_.LINE_ERR_ARG
+    with pytest.raises(L_.LineError) as ei:
+        ctx.sample_walk_debug(2, 1, 10, 2, 0, 10, np.empty((10, 4), np.int32), reuse=0)
+    assert ei.value.status == L_.LINE_ERR_ARG
     for Lw, W in [(10, 0), (10, 11), (1025, 4), (-1, 1)]:
         with pytest.raises(L_.LineError) as ei:
             ctx.train_steps(2, 32, 5, 1000, 5, walk_length=Lw, window=W)

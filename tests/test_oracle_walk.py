@@ -124,3 +124,26 @@ def test_walk_training_differs_from_edge_training_and_is_deterministic():
     C = np.zeros_like(U)
     O.train(T, U, C, order=2, K=3, n_samples=5000, seed=4, batch=128)
     assert not np.array_equal(U, runs[0][0])
+
+
+def test_reuse_replays_each_walk_and_keeps_the_negatives():
+    """With reuse r, the r passes over a walk repeat the positive pairs of
+    that walk (as drawn without reuse at the walk's own index), and the
+    negatives stay the edge sampler's at each sample's counter."""
+    g = I.tiny_chung_lu()
+    T, cw = O.Tables(g), O.walk_cumw(g)
+    L, W, r, K = 12, 3, 3, 4
+    P = O.walk_pairs_per_walk(L, W)
+    n_walks = 5
+    one = O.sample_walk(T, cw, 21, 0, n_walks * P, K, L, W)
+    rec = O.sample_walk(T, cw, 21, 0, n_walks * r * P, K, L, W, reuse=r)
+    for wk in range(n_walks):
+        for q in range(r):
+            blk = rec[(wk * r + q) * P:(wk * r + q + 1) * P]
+            np.testing.assert_array_equal(blk[:, :2], one[wk * P:(wk + 1) * P, :2])
+    negs = O.sample(T, 21, 0, n_walks * r * P, K)
+    np.testing.assert_array_equal(rec[:, 2:], negs[:, 2:])
+    # reuse 1 is the plain walk sampler; a window starting mid-pass agrees
+    np.testing.assert_array_equal(O.sample_walk(T, cw, 21, 0, 50, K, L, W, reuse=1), one[:50])
+    np.testing.assert_array_equal(O.sample_walk(T, cw, 21, 2 * P + 5, 40, K, L, W, reuse=r),
+                                  rec[2 * P + 5:2 * P + 45])
