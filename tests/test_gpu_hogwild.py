@@ -43,6 +43,9 @@ def _oracle_pairwise(name, order, dim, K, n, seed, B, walk=None, **kw):
     ("tiny", 1, 128, 5, 20_000, 1, {}),
     ("tiny", 2, 64, 3, 10_000, 100, {"lam": 1e-3, "alpha_neg": 0.5}),
     ("dchung", 2, 32, 5, 10_000, 4096, {}),
+    ("tiny", 2, 256, 32, 3_000, 64, {}),     # R = 34 > 32 lanes: the slot search by shared memory
+    ("tiny", 1, 16, 0, 20_000, 128, {}),     # K = 0: one call per sample
+    ("two", 1, 32, 6, 2_000, 16, {}),        # 2 nodes, order 1: negatives are u or v nearly always
 ])
 def test_one_worker_is_the_sequential_per_pair_sgd(ctx, name, order, dim, K, n, B, kw):
     from paper_2604_09419_gb300 import line as L
@@ -61,6 +64,23 @@ def test_one_worker_is_the_sequential_per_pair_sgd(ctx, name, order, dim, K, n, 
     ctx.train_steps(order, dim, K, n, 5, batch=B, mode=L.MODE_HOGWILD, hogwild_workers=1, **kw)
     U2, C2 = G.tables(ctx, g, order, dim)
     assert np.array_equal(U, U2) and (order == 1 or np.array_equal(C, C2))
+
+
+def test_one_worker_on_walk_pairs_order_1_bf16_runs(ctx):
+    """Order 1 on walk pairs with one worker (FP32 parity), and the BF16
+    tables of the same run keep every value finite."""
+    from paper_2604_09419_gb300 import line as L
+    g = G.graph("tiny")
+    G.upload(ctx, g)
+    ctx.init_embeddings(1, 64, L.DTYPE_F32, seed=1)
+    ctx.train_steps(1, 64, 4, 8_000, 2, batch=64, mode=L.MODE_HOGWILD, hogwild_workers=1, walk_length=10, window=4)
+    U, _ = G.tables(ctx, g, 1, 64)
+    Uo, _ = _oracle_pairwise("tiny", 1, 64, 4, 8_000, 2, 64, walk=(O.walk_cumw(g), 10, 4))
+    assert np.abs(U - Uo).max() <= TOL
+    ctx.init_embeddings(1, 64, L.DTYPE_BF16, seed=1)
+    ctx.train_steps(1, 64, 4, 200_000, 2, batch=64, mode=L.MODE_HOGWILD, walk_length=10, window=4)
+    U, _ = G.tables(ctx, g, 1, 64)
+    assert np.isfinite(U).all()
 
 
 def test_one_worker_on_walk_pairs(ctx):
