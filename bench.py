@@ -447,8 +447,10 @@ def run_warm22(args):
     arms["bf16"] = refine({"name": "bf16, random rows for new nodes", "phase0_s": t0_bf16}, 0.0)
     # arm B: BF16, the new rows from the MLP at arrival
     start_tables(L.DTYPE_BF16, U16, C16)
-    arrival = {"features_new_rows_s": timed(lambda: ctx.mlp_features_rows(known, rows)),
-               "predict_s": timed(lambda: ctx.mlp_predict(rows))}
+    # the arrival's ids and known-mask come from pinned host buffers
+    rows_h, known_h = torch.from_numpy(rows).pin_memory(), torch.from_numpy(known).pin_memory()
+    arrival = {"features_new_rows_s": timed(lambda: ctx.mlp_features_rows(known_h, rows_h)),
+               "predict_s": timed(lambda: ctx.mlp_predict(rows_h))}
     arms["bf16_warm"] = refine({"name": "bf16 + MLP warm start of the new rows", "phase0_s": t0_bf16,
                                 "one_off_before_arrival": one_off, "at_arrival": arrival, "mlp_steps": mlp_steps,
                                 "mlp_batch": mlp_batch, "mlp_first_loss": float(box["losses"][0]),

@@ -56,19 +56,30 @@ line_status check_status(line_ctx* c, const char* what, bool timeout_sticky) {
     return LINE_OK;
 }
 
-line_status ensure_walk_tables(line_ctx* c) {
-    if (c->cw) return LINE_OK;
+line_status ensure_row_ptr(line_ctx* c) {
+    if (c->row_ptr) return LINE_OK;
     int64_t* rp = nullptr;
-    double* cw = nullptr;
     cudaError_t e = cudaMalloc(&rp, sizeof(int64_t) * (size_t)(c->n_nodes + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&cw, sizeof(double) * (size_t)c->n_arcs);
-    if (e == cudaSuccess) e = walk_tables(c->n_nodes, c->n_arcs, c->src, c->w, rp, cw, c->stream);
+    if (e == cudaSuccess) e = row_offsets(c->n_nodes, c->n_arcs, c->src, rp, c->stream);
     if (e != cudaSuccess) {
         if (rp) cudaFree(rp);
+        return cuda_fail(c, e, "row offsets");
+    }
+    c->row_ptr = rp;
+    return LINE_OK;
+}
+
+line_status ensure_walk_tables(line_ctx* c) {
+    if (c->cw) return LINE_OK;
+    line_status st = ensure_row_ptr(c);
+    if (st) return st;
+    double* cw = nullptr;
+    cudaError_t e = cudaMalloc(&cw, sizeof(double) * (size_t)c->n_arcs);
+    if (e == cudaSuccess) e = walk_cumw(c->n_nodes, c->row_ptr, c->w, cw, c->stream);
+    if (e != cudaSuccess) {
         if (cw) cudaFree(cw);
         return cuda_fail(c, e, "walk sampler tables");
     }
-    c->row_ptr = rp;
     c->cw = cw;
     return LINE_OK;
 }

@@ -35,8 +35,8 @@ struct line_ctx {
     int32_t* dst = nullptr;
     float* deg = nullptr;  // weighted out-degree of each node (FP64 sum, stored FP32)
     float* w = nullptr;    // arc weights (null: all 1)
-    // walk sampler tables, built on first use: first arc of each node and the
-    // running FP64 weight sums per node
+    // built on first use: the first arc of each node (walks, MLP inputs) and
+    // the running FP64 weight sums per node (walks)
     int64_t* row_ptr = nullptr;
     double* cw = nullptr;
     uint2* edge_tab = nullptr;
@@ -70,6 +70,8 @@ line_status cuda_fail(line_ctx* c, cudaError_t e, const char* what);
 line_status enter(line_ctx* c);
 // Reads and clears the device status word (synchronises the stream).
 line_status check_status(line_ctx* c, const char* what, bool timeout_sticky = true);
+// Builds row_ptr if it is missing.
+line_status ensure_row_ptr(line_ctx* c);
 // Builds the walk sampler tables (row_ptr, cw) if they are missing.
 line_status ensure_walk_tables(line_ctx* c);
 

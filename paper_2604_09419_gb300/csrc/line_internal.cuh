@@ -164,10 +164,10 @@ struct WalkParams {
     uint32_t slot_bits;      // item value = (s << slot_bits) | slot
 };
 size_t walk_smem_bytes(int L);
-// row_ptr[n+1] (first arc of each node) and cw[m] from the sorted src and the
-// arc weights (nullable: weight 1).
-cudaError_t walk_tables(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const float* w, int64_t* row_ptr,
-                        double* cw, cudaStream_t s);
+// row_ptr[n+1]: first arc of each node, from the sorted src.
+cudaError_t row_offsets(int64_t n_nodes, int64_t n_arcs, const int32_t* src, int64_t* row_ptr, cudaStream_t s);
+// cw[m]: running FP64 sums of each node's arc weights (w nullable: weight 1).
+cudaError_t walk_cumw(int64_t n_nodes, const int64_t* row_ptr, const float* w, double* cw, cudaStream_t s);
 cudaError_t walk_pairs(const WalkParams& p, cudaStream_t s);
 
 // eval.cu

@@ -55,13 +55,22 @@ struct MlpState {
     int64_t loss_cap = 0;
     int32_t* nodes = nullptr;   // training node list (device copy)
     int64_t nodes_cap = 0;
+    // input computation scratch: the known mask, the hub list ([count] then
+    // ids), the requested rows and their range flag
+    uint8_t* kmask = nullptr;
+    uint32_t* hubs = nullptr;
+    int64_t hubs_cap = 0;
+    int32_t* frows = nullptr;
+    int64_t frows_cap = 0;
+    uint32_t* flag = nullptr;
 };
 
 void mlp_destroy(MlpState* s) {
     if (!s) return;
     for (void* p : {(void*)s->params, (void*)s->grads, (void*)s->m, (void*)s->v, s->X, (void*)s->rows, s->Xb,
                     (void*)s->Tb, (void*)s->A1, s->Hb, (void*)s->Yb, (void*)s->dH, (void*)s->part,
-                    (void*)s->rowloss, s->sum_tmp, (void*)s->losses, (void*)s->nodes})
+                    (void*)s->rowloss, s->sum_tmp, (void*)s->losses, (void*)s->nodes, (void*)s->kmask,
+                    (void*)s->hubs, (void*)s->frows, (void*)s->flag})
         if (p) cudaFree(p);
     delete s;
 }
@@ -93,15 +102,6 @@ __device__ __forceinline__ float load_row_elem(const void* U, int dtype, int64_t
                                    : __bfloat162float(reinterpret_cast<const __nv_bfloat16*>(U)[idx]);
 }
 
-__device__ __forceinline__ int64_t lower_bound_src(const int32_t* src, int64_t n, int32_t v) {
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (src[mid] < v) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
 
 // ---- initialisation --------------------------------------------------------
 __global__ void k_mlp_init(float* __restrict__ p, int H, int P, int D, uint64_t seed, float s1, float s2) {
@@ -121,33 +121,82 @@ __global__ void k_mlp_init(float* __restrict__ p, int H, int P, int D, uint64_t 
 }
 
 // ---- features: one warp per node -------------------------------------------
-constexpr int kMaxE = 8;            // D <= 256: values of a row per lane
 constexpr int64_t kHubArcs = 2048;   // nodes with more arcs are summed by a whole CTA
 constexpr int kHubWarps = 16;
 
+// Row geometry of the inputs: lane l holds values [l E, l E + E) of a row of
+// D values (E = D/32, or 1 with lanes >= D idle when D < 32), loaded as one
+// vector.
+template <int D>
+struct FGeom {
+    static constexpr int E = D >= 32 ? D / 32 : 1;
+    static constexpr int LANES = D / E;
+};
+
+template <int D, int UDT>
+__device__ __forceinline__ void load_vals(const void* U, int64_t row, int lane, float (&v)[FGeom<D>::E]) {
+    constexpr int E = FGeom<D>::E;
+    if constexpr (UDT == LINE_DTYPE_F32) {
+        const float* p = reinterpret_cast<const float*>(U) + row * D + lane * E;
+        if constexpr (E == 8) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(p)), b = __ldg(reinterpret_cast<const float4*>(p) + 1);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
+        } else if constexpr (E == 4) {
+            const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+        } else if constexpr (E == 2) {
+            const float2 a = __ldg(reinterpret_cast<const float2*>(p));
+            v[0] = a.x; v[1] = a.y;
+        } else {
+            v[0] = __ldg(p);
+        }
+    } else {
+        const __nv_bfloat16* p = reinterpret_cast<const __nv_bfloat16*>(U) + row * D + lane * E;
+        if constexpr (E == 8) {
+            const uint4 a = __ldg(reinterpret_cast<const uint4*>(p));
+            const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                v[2 * i] = __uint_as_float(w[i] << 16);
+                v[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+            }
+        } else if constexpr (E == 4) {
+            const uint2 a = __ldg(reinterpret_cast<const uint2*>(p));
+            v[0] = __uint_as_float(a.x << 16); v[1] = __uint_as_float(a.x & 0xFFFF0000u);
+            v[2] = __uint_as_float(a.y << 16); v[3] = __uint_as_float(a.y & 0xFFFF0000u);
+        } else if constexpr (E == 2) {
+            const uint32_t a = __ldg(reinterpret_cast<const unsigned int*>(p));
+            v[0] = __uint_as_float(a << 16); v[1] = __uint_as_float(a & 0xFFFF0000u);
+        } else {
+            v[0] = __bfloat162float(p[0]);
+        }
+    }
+}
+
 // Adds the rows U[dst[e]] of the known neighbours among arcs [lo, hi) to acc
-// (lane: values lane, lane + 32, ...), in arc order; returns their number.
+// in arc order (each value's sum runs over the neighbours in arc order);
+// returns their number.  Arcs are taken 32 at a time (one per lane), and up
+// to 8 known rows (4 at d = 256) are loaded at once before they are added.
+template <int D, int UDT>
 __device__ __forceinline__ int sum_known_rows(int64_t lo, int64_t hi, const int32_t* __restrict__ dst, const void* U,
-                                             int udt, int D, const uint8_t* __restrict__ known, float (&acc)[kMaxE]) {
+                                             const uint8_t* __restrict__ known, float (&acc)[FGeom<D>::E]) {
+    using F = FGeom<D>;
+    constexpr int kGroup = F::E <= 4 ? 8 : 4;
     const int lane = threadIdx.x & 31;
+    const bool holds = lane < F::LANES;
     int cnt = 0;
     for (int64_t e0 = lo; e0 < hi; e0 += 32) {
-        // 32 arcs at a time: lane l reads arc e0 + l; known neighbours
-        // are then added in arc order
         const int64_t e = e0 + lane;
-        const int32_t w = e < hi ? dst[e] : 0;
-        const bool ok = e < hi && known[w];
+        const int32_t w = e < hi ? __ldg(dst + e) : 0;
+        const bool ok = e < hi && __ldg(known + w);
         uint32_t mask = __ballot_sync(0xFFFFFFFFu, ok);
         cnt += __popc(mask);
         while (mask) {
-            // up to kGroup known neighbours: all their loads in flight,
-            // then added in arc order
-            constexpr int kGroup = 8;
-            int64_t rows[kGroup];
+            int32_t rows[kGroup];
             int m = 0;
 #pragma unroll
             for (int j = 0; j < kGroup; ++j) {
-                rows[j] = -1;
+                rows[j] = 0;
                 if (mask) {
                     const int l = __ffs(mask) - 1;
                     mask &= mask - 1;
@@ -155,103 +204,136 @@ __device__ __forceinline__ int sum_known_rows(int64_t lo, int64_t hi, const int3
                     m = j + 1;
                 }
             }
-            float val[kGroup][kMaxE];
+            float val[kGroup][F::E];
 #pragma unroll
             for (int j = 0; j < kGroup; ++j)
-#pragma unroll
-                for (int i = 0; i < kMaxE; ++i) {
-                    const int k = lane + 32 * i;
-                    val[j][i] = (j < m && k < D) ? load_row_elem(U, udt, rows[j] * D + k) : 0.0f;
-                }
+                if (j < m && holds) load_vals<D, UDT>(U, rows[j], lane, val[j]);
 #pragma unroll
             for (int j = 0; j < kGroup; ++j)
                 if (j < m)
 #pragma unroll
-                    for (int i = 0; i < kMaxE; ++i) acc[i] += val[j][i];
+                    for (int i = 0; i < F::E; ++i) acc[i] += val[j][i];
         }
     }
     return cnt;
 }
 
-template <typename TX>
-__device__ __forceinline__ void write_features(TX* x, float deg, const float (&acc)[kMaxE], int cnt, int D, int P) {
+template <int D, typename TX>
+__device__ __forceinline__ void write_features(TX* x, float deg, const float (&acc)[FGeom<D>::E], int cnt, int P) {
+    using F = FGeom<D>;
     const int lane = threadIdx.x & 31;
     if (lane == 0) x[0] = from_f<TX>(log1pf(deg));
+    if (lane < F::LANES) {
 #pragma unroll
-    for (int i = 0; i < kMaxE; ++i) {
-        const int k = lane + 32 * i;
-        if (k < D) x[1 + k] = from_f<TX>(cnt ? acc[i] / (float)cnt : 0.0f);
+        for (int i = 0; i < F::E; ++i) x[1 + lane * F::E + i] = from_f<TX>(cnt ? acc[i] / (float)cnt : 0.0f);
     }
     for (int k = D + 1 + lane; k < P; k += 32) x[k] = from_f<TX>(0.0f);
 }
 
+// flag |= 1 if a requested row id is out of range.
+__global__ void k_check_rows(const int32_t* __restrict__ rows, int64_t n_rows, int64_t n_nodes, uint32_t* flag) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n_rows; i += (int64_t)gridDim.x * blockDim.x)
+        if (rows[i] < 0 || rows[i] >= n_nodes) atomicOr(flag, 1u);
+}
+
+struct FeatParams {
+    int64_t n_nodes;
+    const int64_t* row_ptr;
+    const int32_t* dst;
+    const float* deg;
+    const void* U;
+    const uint8_t* known;
+    int P;
+    void* X;
+    uint32_t* hubs;    // listed hub nodes
+    uint32_t* n_hubs;  // their number
+    const int32_t* rows;
+    int64_t n_rows;
+    const uint32_t* flag;
+};
+
 // One warp per node; nodes with more than kHubArcs arcs are listed in hubs
-// (order irrelevant) and left to k_mlp_features_hub.
-template <typename TX>
-__global__ void k_mlp_features(int64_t n_nodes, int64_t n_arcs, const int32_t* __restrict__ src,
-                               const int32_t* __restrict__ dst, const float* __restrict__ deg, const void* U, int udt,
-                               int D, const uint8_t* __restrict__ known, int P, TX* __restrict__ X,
-                               uint32_t* __restrict__ hubs, uint32_t* __restrict__ n_hubs,
-                               const int32_t* __restrict__ rows, int64_t n_rows) {
+// (order irrelevant) and left to k_mlp_features_hub.  Nothing is written
+// when *flag is set (a requested row id was out of range).
+template <int D, int UDT, typename TX>
+__global__ void __launch_bounds__(256, 3) k_mlp_features(FeatParams p) {
+    if (*(volatile const uint32_t*)p.flag) return;
+    using F = FGeom<D>;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    const int64_t count = rows ? n_rows : n_nodes;
+    const int64_t count = p.rows ? p.n_rows : p.n_nodes;
     for (int64_t r = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); r < count; r += warps) {
-        const int64_t v = rows ? (int64_t)rows[r] : r;
-        if (v < 0 || v >= n_nodes) continue;  // rows are checked on the host
-        const int64_t lo = lower_bound_src(src, n_arcs, (int32_t)v);
-        const int64_t hi = lower_bound_src(src, n_arcs, (int32_t)(v + 1));
+        const int64_t v = p.rows ? (int64_t)p.rows[r] : r;
+        const int64_t lo = __ldg(p.row_ptr + v), hi = __ldg(p.row_ptr + v + 1);
         if (hi - lo > kHubArcs) {
-            if (lane == 0) hubs[atomicAdd(n_hubs, 1u)] = (uint32_t)v;
+            if (lane == 0) p.hubs[atomicAdd(p.n_hubs, 1u)] = (uint32_t)v;
             continue;
         }
-        float acc[kMaxE];
+        float acc[F::E];
 #pragma unroll
-        for (int i = 0; i < kMaxE; ++i) acc[i] = 0.0f;
-        const int cnt = sum_known_rows(lo, hi, dst, U, udt, D, known, acc);
-        write_features<TX>(X + v * (int64_t)P, deg[v], acc, cnt, D, P);
+        for (int i = 0; i < F::E; ++i) acc[i] = 0.0f;
+        const int cnt = sum_known_rows<D, UDT>(lo, hi, p.dst, p.U, p.known, acc);
+        write_features<D, TX>(reinterpret_cast<TX*>(p.X) + v * (int64_t)p.P, __ldg(p.deg + v), acc, cnt, p.P);
     }
 }
 
 // One CTA per listed hub: warp w sums the w-th of kHubWarps contiguous arc
 // slices, the partial sums are added in warp order.
-template <typename TX>
-__global__ void __launch_bounds__(kHubWarps * 32) k_mlp_features_hub(
-    int64_t n_arcs, const int32_t* __restrict__ src, const int32_t* __restrict__ dst, const float* __restrict__ deg,
-    const void* U, int udt, int D, const uint8_t* __restrict__ known, int P, TX* __restrict__ X,
-    const uint32_t* __restrict__ hubs, const uint32_t* __restrict__ n_hubs) {
-    __shared__ float part[kHubWarps][256];
+template <int D, int UDT, typename TX>
+__global__ void __launch_bounds__(kHubWarps * 32) k_mlp_features_hub(FeatParams p) {
+    using F = FGeom<D>;
+    __shared__ float part[kHubWarps][D];
     __shared__ int pcnt[kHubWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t nh = *n_hubs;
+    const uint32_t nh = *p.n_hubs;
     for (uint32_t h = blockIdx.x; h < nh; h += gridDim.x) {
-        const int64_t v = hubs[h];
-        const int64_t lo = lower_bound_src(src, n_arcs, (int32_t)v);
-        const int64_t hi = lower_bound_src(src, n_arcs, (int32_t)(v + 1));
+        const int64_t v = p.hubs[h];
+        const int64_t lo = p.row_ptr[v], hi = p.row_ptr[v + 1];
         const int64_t per = (hi - lo + kHubWarps - 1) / kHubWarps;
         const int64_t a = min(hi, lo + warp * per), b = min(hi, a + per);
-        float acc[kMaxE];
+        float acc[F::E];
 #pragma unroll
-        for (int i = 0; i < kMaxE; ++i) acc[i] = 0.0f;
-        const int c = sum_known_rows(a, b, dst, U, udt, D, known, acc);
+        for (int i = 0; i < F::E; ++i) acc[i] = 0.0f;
+        const int c = sum_known_rows<D, UDT>(a, b, p.dst, p.U, p.known, acc);
+        if (lane < F::LANES)
 #pragma unroll
-        for (int i = 0; i < kMaxE; ++i)
-            if (lane + 32 * i < D) part[warp][lane + 32 * i] = acc[i];
+            for (int i = 0; i < F::E; ++i) part[warp][lane * F::E + i] = acc[i];
         if (lane == 0) pcnt[warp] = c;
         __syncthreads();
         if (warp == 0) {
             int cnt = 0;
 #pragma unroll
-            for (int i = 0; i < kMaxE; ++i) acc[i] = 0.0f;
+            for (int i = 0; i < F::E; ++i) acc[i] = 0.0f;
             for (int w = 0; w < kHubWarps; ++w) {
                 cnt += pcnt[w];
+                if (lane < F::LANES)
 #pragma unroll
-                for (int i = 0; i < kMaxE; ++i)
-                    if (lane + 32 * i < D) acc[i] += part[w][lane + 32 * i];
+                    for (int i = 0; i < F::E; ++i) acc[i] += part[w][lane * F::E + i];
             }
-            write_features<TX>(X + v * (int64_t)P, deg[v], acc, cnt, D, P);
+            write_features<D, TX>(reinterpret_cast<TX*>(p.X) + v * (int64_t)p.P, p.deg[v], acc, cnt, p.P);
         }
         __syncthreads();
+    }
+}
+
+template <int D, int UDT, typename TX>
+cudaError_t launch_features(const FeatParams& p, int64_t count, int64_t max_hubs, cudaStream_t s) {
+    const unsigned g = (unsigned)std::min<int64_t>((count + 7) / 8, 152 * 16);
+    const unsigned gh = (unsigned)std::min<int64_t>(max_hubs, 152 * 4);
+    k_mlp_features<D, UDT, TX><<<g, 256, 0, s>>>(p);
+    k_mlp_features_hub<D, UDT, TX><<<gh, kHubWarps * 32, 0, s>>>(p);
+    return cudaGetLastError();
+}
+
+template <int UDT, typename TX>
+cudaError_t features_for(int D, const FeatParams& p, int64_t count, int64_t max_hubs, cudaStream_t s) {
+    switch (D) {
+        case 16: return launch_features<16, UDT, TX>(p, count, max_hubs, s);
+        case 32: return launch_features<32, UDT, TX>(p, count, max_hubs, s);
+        case 64: return launch_features<64, UDT, TX>(p, count, max_hubs, s);
+        case 128: return launch_features<128, UDT, TX>(p, count, max_hubs, s);
+        case 256: return launch_features<256, UDT, TX>(p, count, max_hubs, s);
+        default: return cudaErrorInvalidValue;
     }
 }
 
@@ -790,55 +872,50 @@ static line_status mlp_features_impl(line_ctx* c, const char* what, const uint8_
     if (rows && !s.has_features) return fail(c, LINE_ERR_STATE, "%s: compute every node's inputs first", what);
     if (rows && n_rows == 0) return LINE_OK;
     const Tables& t = c->tab[s.order];
-    uint8_t* kd = nullptr;
-    uint32_t* hubs = nullptr;  // [count] then the listed hub nodes
-    int32_t* rd = nullptr;
+    if ((st = ensure_row_ptr(c))) return st;
+    // scratch kept in the MLP state (grown, never shrunk)
     const int64_t max_hubs = c->n_arcs / kHubArcs + 1;
-    cudaError_t e = cudaMalloc(&kd, c->n_nodes);
-    if (e == cudaSuccess) e = cudaMalloc(&hubs, sizeof(uint32_t) * (max_hubs + 1));
-    if (e == cudaSuccess && rows) e = cudaMalloc(&rd, sizeof(int32_t) * n_rows);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(kd, known, c->n_nodes, cudaMemcpyDefault, c->stream);
-    if (e == cudaSuccess && rows) e = cudaMemcpyAsync(rd, rows, sizeof(int32_t) * n_rows, cudaMemcpyDefault, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(hubs, 0, sizeof(uint32_t), c->stream);
-    if (e == cudaSuccess && rows) {
-        // ids out of range are refused before any work
-        std::vector<int32_t> h(n_rows);
-        e = cudaMemcpyAsync(h.data(), rd, sizeof(int32_t) * n_rows, cudaMemcpyDeviceToHost, c->stream);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-        for (int64_t i = 0; e == cudaSuccess && i < n_rows; ++i)
-            if (h[i] < 0 || h[i] >= c->n_nodes) {
-                cudaFree(kd);
-                cudaFree(hubs);
-                cudaFree(rd);
-                return fail(c, LINE_ERR_ARG, "%s: row id %d out of range", what, h[i]);
-            }
+    cudaError_t e = cudaSuccess;
+    if (!s.kmask) e = cudaMalloc(&s.kmask, (size_t)c->n_nodes);
+    if (e == cudaSuccess && !s.flag) e = cudaMalloc(&s.flag, sizeof(uint32_t));
+    if (e == cudaSuccess && s.hubs_cap < max_hubs + 1) {
+        if (s.hubs) cudaFree(s.hubs);
+        s.hubs = nullptr;
+        s.hubs_cap = 0;
+        if ((e = cudaMalloc(&s.hubs, sizeof(uint32_t) * (size_t)(max_hubs + 1))) == cudaSuccess) s.hubs_cap = max_hubs + 1;
     }
-    if (e == cudaSuccess) {
-        const int64_t count = rows ? n_rows : c->n_nodes;
-        const unsigned g = grid_of(count * 32, 256, 152 * 64);
-        const unsigned gh = (unsigned)std::min<int64_t>(max_hubs, 152 * 4);
-        if (s.act == LINE_DTYPE_F32) {
-            float* X = reinterpret_cast<float*>(s.X);
-            k_mlp_features<float><<<g, 256, 0, c->stream>>>(c->n_nodes, c->n_arcs, c->src, c->dst, c->deg, t.U,
-                                                            t.dtype, s.dim, kd, s.P, X, hubs + 1, hubs, rd, n_rows);
-            k_mlp_features_hub<float><<<gh, kHubWarps * 32, 0, c->stream>>>(c->n_arcs, c->src, c->dst, c->deg, t.U,
-                                                                             t.dtype, s.dim, kd, s.P, X, hubs + 1,
-                                                                             hubs);
-        } else {
-            __nv_bfloat16* X = reinterpret_cast<__nv_bfloat16*>(s.X);
-            k_mlp_features<__nv_bfloat16><<<g, 256, 0, c->stream>>>(c->n_nodes, c->n_arcs, c->src, c->dst, c->deg,
-                                                                    t.U, t.dtype, s.dim, kd, s.P, X, hubs + 1, hubs,
-                                                                    rd, n_rows);
-            k_mlp_features_hub<__nv_bfloat16><<<gh, kHubWarps * 32, 0, c->stream>>>(
-                c->n_arcs, c->src, c->dst, c->deg, t.U, t.dtype, s.dim, kd, s.P, X, hubs + 1, hubs);
-        }
-        e = cudaGetLastError();
+    if (e == cudaSuccess && rows && s.frows_cap < n_rows) {
+        if (s.frows) cudaFree(s.frows);
+        s.frows = nullptr;
+        s.frows_cap = 0;
+        if ((e = cudaMalloc(&s.frows, sizeof(int32_t) * (size_t)n_rows)) == cudaSuccess) s.frows_cap = n_rows;
     }
-    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-    if (kd) cudaFree(kd);
-    if (hubs) cudaFree(hubs);
-    if (rd) cudaFree(rd);
     if (e != cudaSuccess) return cuda_fail(c, e, what);
+    cudaStream_t str = c->stream;
+    uint32_t* hubs = s.hubs;  // [count] then the listed hub nodes
+    int32_t* rd = rows ? s.frows : nullptr;
+    e = cudaMemcpyAsync(s.kmask, known, c->n_nodes, cudaMemcpyDefault, str);
+    if (e == cudaSuccess && rows) e = cudaMemcpyAsync(rd, rows, sizeof(int32_t) * n_rows, cudaMemcpyDefault, str);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hubs, 0, sizeof(uint32_t), str);
+    if (e == cudaSuccess) e = cudaMemsetAsync(s.flag, 0, sizeof(uint32_t), str);
+    if (e == cudaSuccess) {
+        // ids out of range are refused before any work: the flag stops the
+        // input kernels
+        if (rows) k_check_rows<<<grid_of(n_rows, 256, 152 * 16), 256, 0, str>>>(rd, n_rows, c->n_nodes, s.flag);
+        const int64_t count = rows ? n_rows : c->n_nodes;
+        FeatParams fp{c->n_nodes, c->row_ptr, c->dst, c->deg, t.U, s.kmask, s.P, s.X, hubs + 1, hubs, rd, n_rows, s.flag};
+        if (s.act == LINE_DTYPE_F32)
+            e = t.dtype == LINE_DTYPE_F32 ? features_for<LINE_DTYPE_F32, float>(s.dim, fp, count, max_hubs, str)
+                                          : features_for<LINE_DTYPE_BF16, float>(s.dim, fp, count, max_hubs, str);
+        else
+            e = t.dtype == LINE_DTYPE_F32 ? features_for<LINE_DTYPE_F32, __nv_bfloat16>(s.dim, fp, count, max_hubs, str)
+                                          : features_for<LINE_DTYPE_BF16, __nv_bfloat16>(s.dim, fp, count, max_hubs, str);
+    }
+    uint32_t bad = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, s.flag, sizeof(uint32_t), cudaMemcpyDeviceToHost, str);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(str);
+    if (e != cudaSuccess) return cuda_fail(c, e, what);
+    if (bad) return fail(c, LINE_ERR_ARG, "%s: a row id is out of range", what);
     s.has_features = true;
     return LINE_OK;
 }
@@ -992,9 +1069,17 @@ line_status line_mlp_predict(line_ctx* c, const int32_t* rows, int64_t n_rows, f
     if (y_out) CK(cudaMalloc(&ybuf, sizeof(float) * n_rows * s.dim), "line_mlp_predict");
     const Layout L(s);
     cudaError_t e = cudaSuccess;
+    // all requested ids in one copy; each chunk then takes its slice on the device
+    if (s.frows_cap < n_rows) {
+        if (s.frows) cudaFree(s.frows);
+        s.frows = nullptr;
+        s.frows_cap = 0;
+        if ((e = cudaMalloc(&s.frows, sizeof(int32_t) * (size_t)n_rows)) == cudaSuccess) s.frows_cap = n_rows;
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(s.frows, rows, sizeof(int32_t) * n_rows, cudaMemcpyDefault, str);
     for (int64_t r0 = 0; r0 < n_rows && e == cudaSuccess; r0 += chunk) {
         const int64_t B = std::min(chunk, n_rows - r0);
-        e = cudaMemcpyAsync(s.rows, rows + r0, sizeof(int32_t) * B, cudaMemcpyDefault, str);
+        e = cudaMemcpyAsync(s.rows, s.frows + r0, sizeof(int32_t) * B, cudaMemcpyDeviceToDevice, str);
         if (e == cudaSuccess)
             e = s.act == LINE_DTYPE_F32 ? forward<float>(s, B, t, false, c->status, c->n_nodes, str)
                                         : forward<__nv_bfloat16>(s, B, t, false, c->status, c->n_nodes, str);

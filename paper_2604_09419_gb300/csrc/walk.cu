@@ -164,12 +164,15 @@ __global__ void __launch_bounds__(kWalkWarps * 32) k_walk_pairs(WalkParams p) {
 
 size_t walk_smem_bytes(int L) { return sizeof(int32_t) * (size_t)kWalkWarps * (size_t)(L + 1); }
 
-cudaError_t walk_tables(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const float* w, int64_t* row_ptr,
-                        double* cw, cudaStream_t s) {
-    const unsigned g1 = (unsigned)std::min<int64_t>((n_arcs + 1 + 255) / 256, 152 * 32);
-    k_row_ptr<<<g1, 256, 0, s>>>(src, n_arcs, n_nodes, row_ptr);
-    const unsigned g2 = (unsigned)std::min<int64_t>((n_nodes + 127) / 128, 152 * 32);
-    k_cumw<<<g2, 128, 0, s>>>(row_ptr, w, n_nodes, cw);
+cudaError_t row_offsets(int64_t n_nodes, int64_t n_arcs, const int32_t* src, int64_t* row_ptr, cudaStream_t s) {
+    const unsigned g = (unsigned)std::min<int64_t>((n_arcs + 1 + 255) / 256, 152 * 32);
+    k_row_ptr<<<g, 256, 0, s>>>(src, n_arcs, n_nodes, row_ptr);
+    return cudaGetLastError();
+}
+
+cudaError_t walk_cumw(int64_t n_nodes, const int64_t* row_ptr, const float* w, double* cw, cudaStream_t s) {
+    const unsigned g = (unsigned)std::min<int64_t>((n_nodes + 127) / 128, 152 * 32);
+    k_cumw<<<g, 128, 0, s>>>(row_ptr, w, n_nodes, cw);
     return cudaGetLastError();
 }
 
