@@ -18,6 +18,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <vector>
 
 #include "context.cuh"
@@ -63,6 +64,11 @@ struct MlpState {
     int32_t* frows = nullptr;
     int64_t frows_cap = 0;
     uint32_t* flag = nullptr;
+    // the weights as tensor-core tiles (TF32, core-matrix layout), rebuilt by
+    // every forward pass: W1 and W2 as the B operands of the forward
+    // products, W2 as that of dL/dh
+    float* wt = nullptr;
+    size_t wt_elems = 0;
 };
 
 void mlp_destroy(MlpState* s) {
@@ -70,7 +76,7 @@ void mlp_destroy(MlpState* s) {
     for (void* p : {(void*)s->params, (void*)s->grads, (void*)s->m, (void*)s->v, s->X, (void*)s->rows, s->Xb,
                     (void*)s->Tb, (void*)s->A1, s->Hb, (void*)s->Yb, (void*)s->dH, (void*)s->part,
                     (void*)s->rowloss, s->sum_tmp, (void*)s->losses, (void*)s->nodes, (void*)s->kmask,
-                    (void*)s->hubs, (void*)s->frows, (void*)s->flag})
+                    (void*)s->hubs, (void*)s->frows, (void*)s->flag, (void*)s->wt})
         if (p) cudaFree(p);
     delete s;
 }
@@ -427,18 +433,23 @@ __global__ void __launch_bounds__(256) k_gemm(int M, int N, int K, int kslice, c
 }
 
 // ---- the same contraction on the 5th-generation tensor cores (tcgen05) ----
-// One CTA (4 warps) per 128 x 64 tile of C and slice of K.  Per K step of 32
-// the threads stage A (128 x 32) and B (64 x 32) into shared memory as TF32
-// (rounded to nearest) in the no-swizzle K-major layout of 8-row x 16-byte
-// core matrices (byte (r, k) = (r/8) 1024 + (k/4) 128 + (r%8) 16 + (k%4) 4);
-// one thread issues four tcgen05.mma kind::tf32 (K = 8 each) accumulating
-// into a 128 x 64 FP32 tile in tensor memory and commits them to an
-// mbarrier; after the K loop each warp reads its 32 rows back with
-// tcgen05.ld.  Every wait is bounded: on a timeout the tile is not written
-// and the status word records it.
-constexpr int kTcM = 128, kTcN = 64, kTcK = 32;
+// One CTA (8 warps) per 128 x NT tile of C (NT = 64, 128 or 256) and slice
+// of K.  Per K step of 32 the threads stage A (128 x 32) and B (NT x 32) into
+// shared memory as TF32 (rounded to nearest) in the no-swizzle K-major layout
+// of 8-row x 16-byte core matrices (byte (r, k) = (r/8) 1024 + (k/4) 128 +
+// (r%8) 16 + (k%4) 4).  Two stages: while the tensor core multiplies step i
+// (one thread issues four tcgen05.mma kind::tf32 of K = 8 into a 128 x NT FP32
+// tile in tensor memory and commits them to the stage's mbarrier), the
+// threads stage step i+1 into the other buffers; a stage is refilled only
+// after its previous MMAs completed.  Runs of 16 values contiguous in memory
+// are loaded as vectors.  After the K loop warps w and w+4 read rows
+// 32 (w%4) .. 32 (w%4) + 31 (their tensor-memory lanes), each half of the
+// columns, with tcgen05.ld.  Every wait is bounded: on a timeout the tile is
+// not written and the status word records it.
+constexpr int kTcM = 128, kTcK = 32, kTcThreads = 256;
 constexpr uint32_t kTcLbo = 128;                // next core matrix along K
 constexpr uint32_t kTcSbo = (kTcK / 4) * 128;  // next group of 8 rows
+constexpr int kTcWaitLimit = 1 << 22;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -451,8 +462,9 @@ __device__ __forceinline__ uint64_t tc_smem_desc(uint32_t addr) {
 
 // Instruction descriptor of kind::tf32: D = F32, A = B = TF32, both K-major,
 // N >> 3 at bits 17-22, M >> 4 at bits 24-28.
-constexpr uint32_t kTcIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kTcN >> 3) << 17) |
-                              ((uint32_t)(kTcM >> 4) << 24);
+__host__ __device__ constexpr uint32_t tc_idesc(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kTcM >> 4) << 24);
+}
 
 __device__ __forceinline__ float to_tf32(float x) {
     uint32_t r;
@@ -460,86 +472,195 @@ __device__ __forceinline__ float to_tf32(float x) {
     return __uint_as_float(r);
 }
 
-template <typename TA, typename TB, bool AK, bool BK>
-__global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int kslice, const TA* __restrict__ A, int lda,
-                                                 const TB* __restrict__ B, int ldb, float* __restrict__ C,
-                                                 uint32_t* status) {
-    __shared__ __align__(1024) float sA[kTcM * kTcK];
-    __shared__ __align__(1024) float sB[kTcN * kTcK];
-    __shared__ __align__(8) uint64_t mbar;
+// 16 consecutive values of a row (T = float or BF16) at p; a vector load when
+// aligned and complete, else element by element up to n.
+template <typename T>
+__device__ __forceinline__ void load16(const T* p, int n, float (&v)[16]) {
+    if (n >= 16 && (reinterpret_cast<uintptr_t>(p) & 15) == 0) {
+        if constexpr (sizeof(T) == 4) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 a = __ldg(reinterpret_cast<const float4*>(p) + q);
+                v[4 * q] = a.x; v[4 * q + 1] = a.y; v[4 * q + 2] = a.z; v[4 * q + 3] = a.w;
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const uint4 a = __ldg(reinterpret_cast<const uint4*>(p) + q);
+                const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    v[8 * q + 2 * i] = __uint_as_float(w[i] << 16);
+                    v[8 * q + 2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+                }
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v[i] = i < n ? to_f(p[i]) : 0.0f;
+    }
+}
+
+// Stage rows [r0, r0 + R) x K step [k0, k0 + 32) of X (X(r, k) = XK ?
+// X[r ld + k] : X[k ld + r]; values outside [0, rmax) x [k0, ke) are zero) as
+// TF32 into the core-matrix layout at s.
+template <typename T, bool XK, int R>
+__device__ __forceinline__ void stage_tile(float* __restrict__ s, const T* __restrict__ X, int ld, int r0, int rmax,
+                                           int k0, int ke) {
+    if constexpr (XK) {
+        // work item: (row, 16 consecutive k)
+        for (int it = threadIdx.x; it < R * 2; it += kTcThreads) {
+            const int r = it >> 1, kg = (it & 1) * 16;
+            const int gr = r0 + r, gk = k0 + kg;
+            float v[16];
+            if (gr < rmax && gk < ke) load16(X + (size_t)gr * ld + gk, ke - gk, v);
+            else
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = 0.0f;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float4* dst = reinterpret_cast<float4*>(s + (r >> 3) * (kTcSbo / 4) + ((kg >> 2) + q) * (kTcLbo / 4) + (r & 7) * 4);
+                *dst = make_float4(to_tf32(v[4 * q]), to_tf32(v[4 * q + 1]), to_tf32(v[4 * q + 2]), to_tf32(v[4 * q + 3]));
+            }
+        }
+    } else {
+        // work item: (k, 16 consecutive rows)
+        for (int it = threadIdx.x; it < (R / 16) * kTcK; it += kTcThreads) {
+            const int k = it / (R / 16), rg = (it % (R / 16)) * 16;
+            const int gk = k0 + k, gr = r0 + rg;
+            float v[16];
+            if (gk < ke && gr < rmax) load16(X + (size_t)gk * ld + gr, rmax - gr, v);
+            else
+#pragma unroll
+                for (int i = 0; i < 16; ++i) v[i] = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const int r = rg + i;
+                s[(r >> 3) * (kTcSbo / 4) + (k >> 2) * (kTcLbo / 4) + (r & 7) * 4 + (k & 3)] = to_tf32(v[i]);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+    uint32_t done = 0;
+    for (int it = 0; it < kTcWaitLimit && !done; ++it) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(bar), "r"(parity));
+    }
+    return done != 0;
+}
+
+template <int NT>
+constexpr size_t tc_smem_bytes() {
+    return 1024 + 2 * sizeof(float) * (size_t)(kTcM + NT) * kTcK;  // 1024: room to align the stages
+}
+
+template <typename TA, typename TB, bool AK, bool BK, int NT>
+__global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, int kslice, const TA* __restrict__ A,
+                                                        int lda, const TB* __restrict__ B, int ldb,
+                                                        const float* __restrict__ Bt, float* __restrict__ C,
+                                                        uint32_t* status) {
+    extern __shared__ unsigned char tc_raw[];
+    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t full[2];  // B tile of the stage arrived (bulk copy path)
     __shared__ uint32_t tmem_base;
+    // stage st: A at base + st (128 x 32), B at base + 2 (128 x 32) + st (NT x 32)
+    float* base = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(tc_raw) + 1023) & ~(uintptr_t)1023);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * kTcN;
+    const int m0 = blockIdx.y * kTcM, n0 = blockIdx.x * NT;
     const int kb = blockIdx.z * kslice, ke = min(K, kb + kslice);
+    const int nk = ke > kb ? (ke - kb + kTcK - 1) / kTcK : 0;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
-                     "r"(kTcN));
+                     "r"(NT));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar)));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&mbar[1])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[0])));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(&full[1])));
         asm volatile("fence.mbarrier_init.release.cluster;");
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_base;
-    uint32_t phase = 0;
     bool ok = true;
-    bool first = true;
-    for (int k0 = kb; k0 < ke; k0 += kTcK) {
-        for (int i = tid; i < kTcM * kTcK; i += 128) {
-            const int r = AK ? i / kTcK : i % kTcM, k = AK ? i % kTcK : i / kTcM;
-            const int gm = m0 + r, gk = k0 + k;
-            float a = 0.0f;
-            if (gm < M && gk < ke) a = to_f(AK ? A[(size_t)gm * lda + gk] : A[(size_t)gk * lda + gm]);
-            sA[(r >> 3) * (kTcSbo / 4) + (k >> 2) * (kTcLbo / 4) + (r & 7) * 4 + (k & 3)] = to_tf32(a);
+    for (int i = 0; i < nk; ++i) {
+        const int st = i & 1;
+        if (i >= 2) {
+            // the MMAs of step i-2 read this stage
+            ok = mbar_wait(smem_addr(&mbar[st]), (uint32_t)(((i - 2) >> 1) & 1));
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            if (!__syncthreads_and(ok)) break;
         }
-        for (int i = tid; i < kTcN * kTcK; i += 128) {
-            const int r = BK ? i / kTcK : i % kTcN, k = BK ? i % kTcK : i / kTcN;
-            const int gn = n0 + r, gk = k0 + k;
-            float b = 0.0f;
-            if (gn < N && gk < ke) b = to_f(BK ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn]);
-            sB[(r >> 3) * (kTcSbo / 4) + (k >> 2) * (kTcLbo / 4) + (r & 7) * 4 + (k & 3)] = to_tf32(b);
+        const int k0 = kb + i * kTcK;
+        float* sa = base + st * (kTcM * kTcK);
+        float* sb = base + 2 * (kTcM * kTcK) + st * (NT * kTcK);
+        if (Bt) {
+            // the B tile is already TF32 in the core-matrix layout: one bulk
+            // copy, completing on the stage's `full` barrier
+            if (tid == 0) {
+                constexpr uint32_t bytes = NT * kTcK * sizeof(float);
+                const float* src = Bt + ((size_t)blockIdx.x * ((K + kTcK - 1) / kTcK) + k0 / kTcK) * (NT * kTcK);
+                asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(&full[st])),
+                             "r"(bytes)
+                             : "memory");
+                asm volatile(
+                    "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                        smem_addr(sb)),
+                    "l"(src), "r"(bytes), "r"(smem_addr(&full[st]))
+                    : "memory");
+            }
+        } else {
+            stage_tile<TB, BK, NT>(sb, B, ldb, n0, N, k0, ke);
         }
+        stage_tile<TA, AK, kTcM>(sa, A, lda, m0, M, k0, ke);
         asm volatile("fence.proxy.async.shared::cta;");  // the tensor core reads through the async proxy
         __syncthreads();
+        bool issued = true;
         if (tid == 0) {
+            if (Bt && !mbar_wait(smem_addr(&full[st]), (uint32_t)((i >> 1) & 1))) issued = false;
             asm volatile("tcgen05.fence::after_thread_sync;");
+        }
+        if (!__syncthreads_and(issued)) {
+            ok = false;
+            break;
+        }
+        if (tid == 0) {
 #pragma unroll
             for (int kk = 0; kk < kTcK / 8; ++kk) {
-                const uint64_t da = tc_smem_desc(smem_addr(sA) + kk * 2 * kTcLbo);
-                const uint64_t db = tc_smem_desc(smem_addr(sB) + kk * 2 * kTcLbo);
-                const uint32_t acc = (!first || kk > 0) ? 1u : 0u;
+                const uint64_t da = tc_smem_desc(smem_addr(sa) + kk * 2 * kTcLbo);
+                const uint64_t db = tc_smem_desc(smem_addr(sb) + kk * 2 * kTcLbo);
+                const uint32_t acc = (i > 0 || kk > 0) ? 1u : 0u;
                 asm volatile(
                     "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
                     "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                    "l"(da), "l"(db), "r"(kTcIdesc), "r"(acc));
+                    "l"(da), "l"(db), "r"(tc_idesc(NT)), "r"(acc));
             }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                smem_addr(&mbar)));
+                smem_addr(&mbar[st])));
         }
-        first = false;
-        // the tiles are restaged only after the MMAs that read them are done
-        uint32_t done = 0;
-        for (int it = 0; it < (1 << 22) && !done; ++it) {
-            asm volatile(
-                "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-                : "=r"(done)
-                : "r"(smem_addr(&mbar)), "r"(phase));
-        }
-        phase ^= 1;
-        ok = ok && done;
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (!__syncthreads_and(ok)) break;
     }
-    if (ok && !first) {
-        float* Cz = C + (size_t)blockIdx.z * M * N;
-        const int row = m0 + warp * 32 + lane;
+    if (ok && nk > 0) {
+        // the last commit tracks every earlier MMA of this thread
+        const int last = nk - 1;
+        ok = mbar_wait(smem_addr(&mbar[last & 1]), (uint32_t)((last >> 1) & 1));
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        ok = __syncthreads_and(ok);
+    }
+    float* Cz = C + (size_t)blockIdx.z * M * N;
+    if (ok && nk > 0) {
+        const int quarter = warp & 3, half = warp >> 2;
+        const int row = m0 + quarter * 32 + lane;
 #pragma unroll
-        for (int c0 = 0; c0 < kTcN; c0 += 16) {
+        for (int c0 = half * (NT / 2); c0 < (half + 1) * (NT / 2); c0 += 16) {
             uint32_t r[16];
-            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
+            const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)c0;
             asm volatile(
                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
                 "[%16];"
@@ -554,31 +675,75 @@ __global__ void __launch_bounds__(128) k_gemm_tc(int M, int N, int K, int kslice
                     if (n0 + c0 + j < N) Cz[(size_t)row * N + n0 + c0 + j] = __uint_as_float(r[j]);
             }
         }
-    } else if (!first) {
+    } else if (nk > 0) {
         if (tid == 0) atomicOr(status, DEV_ERR_TIMEOUT);
     } else {
         // an empty K slice: the partial sum is zero
-        float* Cz = C + (size_t)blockIdx.z * M * N;
-        for (int i = tid; i < kTcM * kTcN; i += 128) {
-            const int r = m0 + i / kTcN, cc = n0 + i % kTcN;
+        for (int i = tid; i < kTcM * NT; i += kTcThreads) {
+            const int r = m0 + i / NT, cc = n0 + i % NT;
             if (r < M && cc < N) Cz[(size_t)r * N + cc] = 0.0f;
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcN));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NT));
 }
 
-// C_z = A B over K slice z: on the tensor cores (TF32 operands) when tc is
-// set - the BF16-activation mode - else in FP32 on the CUDA cores.
+template <typename TA, typename TB, bool AK, bool BK, int NT>
+cudaError_t launch_tc(int M, int N, int K, int slices, const TA* A, int lda, const TB* B, int ldb, const float* Bt,
+                      float* C, uint32_t* status, cudaStream_t s) {
+    constexpr size_t smem = tc_smem_bytes<NT>();
+    static std::atomic<uint64_t> attr_set{0};  // devices whose kernel attribute is set
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if (!(attr_set.load(std::memory_order_acquire) & bit)) {
+        e = cudaFuncSetAttribute(k_gemm_tc<TA, TB, AK, BK, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr_set.fetch_or(bit, std::memory_order_acq_rel);
+    }
+    const int kslice = ((K + slices - 1) / slices + kTcK - 1) / kTcK * kTcK;
+    const dim3 grid((N + NT - 1) / NT, (M + kTcM - 1) / kTcM, slices);
+    k_gemm_tc<TA, TB, AK, BK, NT><<<grid, kTcThreads, smem, s>>>(M, N, K, kslice, A, lda, B, ldb, Bt, C, status);
+    return cudaGetLastError();
+}
+
+// The N tile of the tensor-core product: the widest that does not exceed N
+// by more than half a tile.
+inline int tc_tile_n(int N) { return N > 128 ? 256 : N > 64 ? 128 : 64; }
+
+// Bt[(n_tile ceil(K/32) + k_step) NT 32 ...]: B(k, n) (BK ? B[n ldb + k] :
+// B[k ldb + n]) as TF32 tiles of NT x 32 in the core-matrix layout of
+// k_gemm_tc's stages, zero outside N x K.
+template <bool BK>
+__global__ void k_tile_b(const float* __restrict__ B, int ldb, int N, int K, int NT, float* __restrict__ Bt) {
+    const int ks = (K + kTcK - 1) / kTcK, nt = (N + NT - 1) / NT;
+    const int64_t total = (int64_t)nt * ks * NT * kTcK;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t tile = i / (NT * kTcK);
+        const int r = (int)((i % (NT * kTcK)) / kTcK), k = (int)(i % kTcK);
+        const int gn = (int)(tile / ks) * NT + r, gk = (int)(tile % ks) * kTcK + k;
+        const float v = (gn < N && gk < K) ? (BK ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn]) : 0.0f;
+        Bt[tile * (NT * kTcK) + (r >> 3) * (kTcSbo / 4) + (k >> 2) * (kTcLbo / 4) + (r & 7) * 4 + (k & 3)] = to_tf32(v);
+    }
+}
+
+inline size_t tile_b_elems(int N, int K) {
+    const int NT = tc_tile_n(N);
+    return (size_t)((N + NT - 1) / NT) * ((K + kTcK - 1) / kTcK) * NT * kTcK;
+}
+
+// C_z = A B over K slice z, on the tensor cores when tc is set; Bt (tc only,
+// nullable): B already as tiles (k_tile_b), copied in bulk.
 template <typename TA, typename TB, bool AK, bool BK>
 cudaError_t gemm(bool tc, int M, int N, int K, int slices, const TA* A, int lda, const TB* B, int ldb, float* C,
-                 uint32_t* status, cudaStream_t s) {
+                 uint32_t* status, cudaStream_t s, const float* Bt = nullptr) {
     if (tc) {
-        const int kslice = ((K + slices - 1) / slices + kTcK - 1) / kTcK * kTcK;
-        const dim3 grid((N + kTcN - 1) / kTcN, (M + kTcM - 1) / kTcM, slices);
-        k_gemm_tc<TA, TB, AK, BK><<<grid, 128, 0, s>>>(M, N, K, kslice, A, lda, B, ldb, C, status);
-        return cudaGetLastError();
+        const int NT = tc_tile_n(N);
+        if (NT == 256) return launch_tc<TA, TB, AK, BK, 256>(M, N, K, slices, A, lda, B, ldb, Bt, C, status, s);
+        if (NT == 128) return launch_tc<TA, TB, AK, BK, 128>(M, N, K, slices, A, lda, B, ldb, Bt, C, status, s);
+        return launch_tc<TA, TB, AK, BK, 64>(M, N, K, slices, A, lda, B, ldb, Bt, C, status, s);
     }
     const int kslice = ((K + slices - 1) / slices + kBK - 1) / kBK * kBK;
     const dim3 grid((N + kBN - 1) / kBN, (M + kBM - 1) / kBM, slices);
@@ -689,6 +854,17 @@ struct Layout {
 
 int slices_for(int64_t B) { return (int)std::max<int64_t>(1, std::min<int64_t>(32, (B + 127) / 128)); }
 
+cudaError_t ensure_weight_tiles(MlpState& s) {
+    const size_t need = tile_b_elems(s.hidden, s.P) + tile_b_elems(s.dim, s.hidden) + tile_b_elems(s.hidden, s.dim);
+    if (s.wt && s.wt_elems >= need) return cudaSuccess;
+    if (s.wt) cudaFree(s.wt);
+    s.wt = nullptr;
+    s.wt_elems = 0;
+    cudaError_t e = cudaMalloc(&s.wt, sizeof(float) * need);
+    if (e == cudaSuccess) s.wt_elems = need;
+    return e;
+}
+
 cudaError_t ensure_cap(MlpState& s, int64_t rows) {
     if (rows <= s.cap) return cudaSuccess;
     const int64_t cap = std::max<int64_t>(rows, 1024);
@@ -730,11 +906,24 @@ cudaError_t forward(MlpState& s, int64_t B, const Tables& t, bool targets, uint3
                                                             Xb, t.U, t.dtype, s.dim, targets ? s.Tb : nullptr, status);
     cudaError_t e;
     const bool tc = s.act == LINE_DTYPE_BF16;
-    if ((e = gemm<TX, float, true, true>(tc, (int)B, s.hidden, s.P, 1, Xb, s.P, W1, s.P, s.A1, status, st)) !=
+    const float* W1t = nullptr;
+    const float* W2t = nullptr;
+    if (tc) {
+        // the weights as tensor-core tiles, copied in bulk by the products
+        if ((e = ensure_weight_tiles(s)) != cudaSuccess) return e;
+        const size_t e1 = tile_b_elems(s.hidden, s.P);
+        k_tile_b<true><<<grid_of((int64_t)e1, 256), 256, 0, st>>>(W1, s.P, s.hidden, s.P, tc_tile_n(s.hidden), s.wt);
+        k_tile_b<true><<<grid_of((int64_t)tile_b_elems(s.dim, s.hidden), 256), 256, 0, st>>>(
+            W2, s.hidden, s.dim, s.hidden, tc_tile_n(s.dim), s.wt + e1);
+        W1t = s.wt;
+        W2t = s.wt + e1;
+    }
+    if ((e = gemm<TX, float, true, true>(tc, (int)B, s.hidden, s.P, 1, Xb, s.P, W1, s.P, s.A1, status, st, W1t)) !=
         cudaSuccess)
         return e;
     k_ep_hidden<TX><<<grid_of(B * s.hidden, 256), 256, 0, st>>>(s.A1, b1, B, s.hidden, Hb);
-    return gemm<TX, float, true, true>(tc, (int)B, s.dim, s.hidden, 1, Hb, s.hidden, W2, s.hidden, s.Yb, status, st);
+    return gemm<TX, float, true, true>(tc, (int)B, s.dim, s.hidden, 1, Hb, s.hidden, W2, s.hidden, s.Yb, status, st,
+                                       W2t);
 }
 
 // Loss and gradients of the batch s.rows[0..B) into s.grads; the batch loss
@@ -751,8 +940,15 @@ cudaError_t loss_grad(MlpState& s, int64_t B, const Tables& t, uint32_t* status,
     k_ep_loss<<<grid_of(B * 32, 256), 256, 0, st>>>(s.Yb, b2, s.Tb, B, s.dim, scale, s.rowloss);
     // dH = dY W2, then dA = dH GELU'(a)
     const bool tc = s.act == LINE_DTYPE_BF16;
+    const float* W2tT = nullptr;
+    if (tc) {
+        float* dst = s.wt + tile_b_elems(s.hidden, s.P) + tile_b_elems(s.dim, s.hidden);
+        k_tile_b<false><<<grid_of((int64_t)tile_b_elems(s.hidden, s.dim), 256), 256, 0, st>>>(
+            W2, s.hidden, s.hidden, s.dim, tc_tile_n(s.hidden), dst);
+        W2tT = dst;
+    }
     if ((e = gemm<float, float, true, false>(tc, (int)B, s.hidden, s.dim, 1, s.Yb, s.dim, W2, s.hidden, s.dH, status,
-                                             st)) != cudaSuccess)
+                                             st, W2tT)) != cudaSuccess)
         return e;
     k_ep_dact<<<grid_of(B * s.hidden, 256), 256, 0, st>>>(s.dH, s.A1, B * s.hidden);
     const TX* Xb = reinterpret_cast<const TX*>(s.Xb);
