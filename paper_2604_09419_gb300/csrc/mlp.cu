@@ -558,11 +558,14 @@ constexpr size_t tc_smem_bytes() {
     return 1024 + 2 * sizeof(float) * (size_t)(kTcM + NT) * kTcK;  // 1024: room to align the stages
 }
 
-template <typename TA, typename TB, bool AK, bool BK, int NT>
+// Epilogue of the hidden layer (HID): C = A1 = acc + bias[n] and
+// H[m][n] = GELU(A1) in TH, written straight from tensor memory.
+template <typename TA, typename TB, bool AK, bool BK, int NT, bool HID = false, typename TH = float>
 __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, int kslice, const TA* __restrict__ A,
                                                         int lda, const TB* __restrict__ B, int ldb,
                                                         const float* __restrict__ Bt, float* __restrict__ C,
-                                                        uint32_t* status) {
+                                                        uint32_t* status, const float* __restrict__ bias = nullptr,
+                                                        TH* __restrict__ H = nullptr) {
     extern __shared__ unsigned char tc_raw[];
     __shared__ __align__(8) uint64_t mbar[2];
     __shared__ __align__(8) uint64_t full[2];  // B tile of the stage arrived (bulk copy path)
@@ -669,10 +672,52 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, int
                   "=r"(r[15])
                 : "r"(taddr));
             asm volatile("tcgen05.wait::ld.sync.aligned;");
-            if (row < M) {
+            if constexpr (HID) {
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    if (n0 + c0 + j < N) Cz[(size_t)row * N + n0 + c0 + j] = __uint_as_float(r[j]);
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + c0 + j;
+                    r[j] = __float_as_uint(__uint_as_float(r[j]) + (n < N ? __ldg(bias + n) : 0.0f));
+                }
+                if (row < M) {
+                    TH* hout = H + (size_t)row * N + n0 + c0;
+                    if (n0 + c0 + 16 <= N && (reinterpret_cast<uintptr_t>(hout) & 15) == 0) {
+                        if constexpr (sizeof(TH) == 2) {
+                            uint32_t w[8];
+#pragma unroll
+                            for (int q = 0; q < 8; ++q) {
+                                const __nv_bfloat162 v = __floats2bfloat162_rn(gelu(__uint_as_float(r[2 * q])),
+                                                                               gelu(__uint_as_float(r[2 * q + 1])));
+                                w[q] = *reinterpret_cast<const uint32_t*>(&v);
+                            }
+                            reinterpret_cast<uint4*>(hout)[0] = make_uint4(w[0], w[1], w[2], w[3]);
+                            reinterpret_cast<uint4*>(hout)[1] = make_uint4(w[4], w[5], w[6], w[7]);
+                        } else {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                reinterpret_cast<float4*>(hout)[q] = make_float4(
+                                    gelu(__uint_as_float(r[4 * q])), gelu(__uint_as_float(r[4 * q + 1])),
+                                    gelu(__uint_as_float(r[4 * q + 2])), gelu(__uint_as_float(r[4 * q + 3])));
+                        }
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 16; ++j)
+                            if (n0 + c0 + j < N) hout[j] = from_f<TH>(gelu(__uint_as_float(r[j])));
+                    }
+                }
+            }
+            if (row < M) {
+                float* out = Cz + (size_t)row * N + n0 + c0;
+                if (n0 + c0 + 16 <= N && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        reinterpret_cast<float4*>(out)[q] =
+                            make_float4(__uint_as_float(r[4 * q]), __uint_as_float(r[4 * q + 1]),
+                                        __uint_as_float(r[4 * q + 2]), __uint_as_float(r[4 * q + 3]));
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        if (n0 + c0 + j < N) out[j] = __uint_as_float(r[j]);
+                }
             }
         }
     } else if (nk > 0) {
@@ -689,9 +734,9 @@ __global__ void __launch_bounds__(kTcThreads) k_gemm_tc(int M, int N, int K, int
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NT));
 }
 
-template <typename TA, typename TB, bool AK, bool BK, int NT>
+template <typename TA, typename TB, bool AK, bool BK, int NT, bool HID = false, typename TH = float>
 cudaError_t launch_tc(int M, int N, int K, int slices, const TA* A, int lda, const TB* B, int ldb, const float* Bt,
-                      float* C, uint32_t* status, cudaStream_t s) {
+                      float* C, uint32_t* status, cudaStream_t s, const float* bias = nullptr, TH* H = nullptr) {
     constexpr size_t smem = tc_smem_bytes<NT>();
     static std::atomic<uint64_t> attr_set{0};  // devices whose kernel attribute is set
     int dev = 0;
@@ -699,13 +744,15 @@ cudaError_t launch_tc(int M, int N, int K, int slices, const TA* A, int lda, con
     if (e != cudaSuccess) return e;
     const uint64_t bit = 1ull << (dev & 63);
     if (!(attr_set.load(std::memory_order_acquire) & bit)) {
-        e = cudaFuncSetAttribute(k_gemm_tc<TA, TB, AK, BK, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = cudaFuncSetAttribute(k_gemm_tc<TA, TB, AK, BK, NT, HID, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem);
         if (e != cudaSuccess) return e;
         attr_set.fetch_or(bit, std::memory_order_acq_rel);
     }
     const int kslice = ((K + slices - 1) / slices + kTcK - 1) / kTcK * kTcK;
     const dim3 grid((N + NT - 1) / NT, (M + kTcM - 1) / kTcM, slices);
-    k_gemm_tc<TA, TB, AK, BK, NT><<<grid, kTcThreads, smem, s>>>(M, N, K, kslice, A, lda, B, ldb, Bt, C, status);
+    k_gemm_tc<TA, TB, AK, BK, NT, HID, TH><<<grid, kTcThreads, smem, s>>>(M, N, K, kslice, A, lda, B, ldb, Bt, C,
+                                                                           status, bias, H);
     return cudaGetLastError();
 }
 
@@ -918,10 +965,22 @@ cudaError_t forward(MlpState& s, int64_t B, const Tables& t, bool targets, uint3
         W1t = s.wt;
         W2t = s.wt + e1;
     }
-    if ((e = gemm<TX, float, true, true>(tc, (int)B, s.hidden, s.P, 1, Xb, s.P, W1, s.P, s.A1, status, st, W1t)) !=
-        cudaSuccess)
-        return e;
-    k_ep_hidden<TX><<<grid_of(B * s.hidden, 256), 256, 0, st>>>(s.A1, b1, B, s.hidden, Hb);
+    if (tc) {
+        // A1 = X W1^T + b1 and H = GELU(A1) from the product's epilogue
+        const int NT = tc_tile_n(s.hidden);
+        e = NT == 256 ? launch_tc<TX, float, true, true, 256, true, TX>((int)B, s.hidden, s.P, 1, Xb, s.P, W1, s.P, W1t,
+                                                                       s.A1, status, st, b1, Hb)
+            : NT == 128 ? launch_tc<TX, float, true, true, 128, true, TX>((int)B, s.hidden, s.P, 1, Xb, s.P, W1, s.P,
+                                                                         W1t, s.A1, status, st, b1, Hb)
+                        : launch_tc<TX, float, true, true, 64, true, TX>((int)B, s.hidden, s.P, 1, Xb, s.P, W1, s.P, W1t,
+                                                                        s.A1, status, st, b1, Hb);
+        if (e != cudaSuccess) return e;
+    } else {
+        if ((e = gemm<TX, float, true, true>(tc, (int)B, s.hidden, s.P, 1, Xb, s.P, W1, s.P, s.A1, status, st)) !=
+            cudaSuccess)
+            return e;
+        k_ep_hidden<TX><<<grid_of(B * s.hidden, 256), 256, 0, st>>>(s.A1, b1, B, s.hidden, Hb);
+    }
     return gemm<TX, float, true, true>(tc, (int)B, s.dim, s.hidden, 1, Hb, s.hidden, W2, s.hidden, s.Yb, status, st,
                                        W2t);
 }
