@@ -22,6 +22,9 @@ Other workloads (``--workload``; not the default line):
   epochs, each walk's pairs serving r = 1, 4 and 16 passes, in the
   minibatch and the Hogwild schedule: updates/s, second-order loss and
   link-prediction AUC of each.
+* ``mlp20`` - the warm-start MLP's kernels alone on R-MAT 20 (BF16 tables,
+  d=128, hidden 256, BF16 activations): the inputs of every node, the inputs
+  of 10% held-out nodes and their predictions, device time of each call.
 * ``dchung22`` - weighted directed Chung-Lu graph, 4,194,304 nodes, 2^26 arc
   draws (out-weights power law 2.2, lognormal(0,1) weights); order 2, d=128,
   K=5: the FP32 path at B=4096 against BF16 tables with stochastic rounding
@@ -88,7 +91,7 @@ def parse():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-samples", type=int, default=1 << 20)
     p.add_argument("--workload", default="rmat20",
-                   choices=["rmat20", "rmat20walk", "reuse20", "dchung22", "warm22", "rmat24"])
+                   choices=["rmat20", "rmat20walk", "reuse20", "mlp20", "dchung22", "warm22", "rmat24"])
     p.add_argument("--walk-length", type=int, default=100, help="rmat20walk: steps per walk")
     p.add_argument("--window", type=int, default=2, help="rmat20walk: pair window")
     p.add_argument("--epochs", type=int, default=10, help="rmat24, reuse20: samples per order = epochs x |E|")
@@ -557,6 +560,49 @@ def run_rmat24(args):
     ctx.close()
 
 
+def run_mlp20(args):
+    """The MLP input and prediction kernels on R-MAT 20 (two repetitions)."""
+    import numpy as np
+    import torch
+
+    from paper_2604_09419_gb300 import inputs as I
+    from paper_2604_09419_gb300 import line as L
+    _, _, local = dist_env()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    g = I.rmat20()
+    ctx = L.Context(local, stream.cuda_stream)
+    ctx.build_alias(g.n_nodes, torch.from_numpy(g.src).cuda(), torch.from_numpy(g.dst).cuda(),
+                    torch.from_numpy(g.w).cuda())
+    ctx.init_embeddings(2, DIM, L.DTYPE_BF16, seed=2)
+    ctx.mlp_create(2, hidden=256, act_dtype=L.DTYPE_BF16, seed=9)
+    held = I.uniform01(1, I.STREAM_NODE_SPLIT, np.arange(g.n_nodes, dtype=np.uint64)) < 0.1
+    known = torch.from_numpy((~held).astype(np.uint8)).pin_memory()
+    rows = torch.from_numpy(np.flatnonzero(held).astype(np.int32)).pin_memory()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        fn()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    reps = []
+    for _ in range(2):
+        reps.append({"inputs_all_ms": timed(lambda: ctx.mlp_features(known)),
+                     "inputs_rows_ms": timed(lambda: ctx.mlp_features_rows(known, rows)),
+                     "predict_ms": timed(lambda: ctx.mlp_predict(rows))})
+    line = {"metric": "warm-start MLP kernels, device ms", "unit": "ms", "value": reps[-1]["predict_ms"],
+            "higher_is_better": False, "n_gpus": 1, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": "mlp20_inputs_and_predictions_d128_h256_bf16", "n_nodes": g.n_nodes,
+                       "n_arcs": g.n_arcs, "rows": int(rows.shape[0])},
+            "repetitions": reps}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+
+
 def run_reuse20(args):
     """Walk reuse r in {1, 4, 16} x {minibatch, Hogwild}: throughput vs quality."""
     import torch
@@ -628,6 +674,9 @@ def main():
         return
     if args.workload == "reuse20":
         run_reuse20(args)
+        return
+    if args.workload == "mlp20":
+        run_mlp20(args)
         return
     import numpy as np
     import torch
