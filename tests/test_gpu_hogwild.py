@@ -162,3 +162,42 @@ def test_hogwild_argument_errors(ctx):
     with pytest.raises(L.LineError) as ei:
         ctx.train_steps(2, 32, 5, 1000, 5, mode=3)
     assert ei.value.status == L.LINE_ERR_ARG
+
+
+def test_full_size_rmat20_hogwild(ctx):
+    """The benchmark workload in the Hogwild schedule (R-MAT 20, d=128, K=5):
+    one worker within 1e-5 of the per-pair oracle on a short prefix, and the
+    benchmark's launch configuration (a full wave, both orders concurrently)
+    on a longer prefix: rows no sample touched are unchanged and the
+    second-order loss is within 1% of the sequential FP64 run's."""
+    from paper_2604_09419_gb300 import line as L
+    g = G.graph("rmat20")
+    G.upload(ctx, g)
+    T = G.oracle_tables("rmat20")
+    total = 335_544_320
+    n1 = 20_000
+    ctx.init_embeddings(2, 128, L.DTYPE_F32, seed=2)
+    ctx.train_steps(2, 128, 5, n1, 1000, batch=4096, total=total, mode=L.MODE_HOGWILD, hogwild_workers=1)
+    U, C = G.tables(ctx, g, 2, 128)
+    Uo = O.init_uniform(g.n_nodes, 128, 2)
+    Co = np.zeros_like(Uo)
+    O.train_pairwise(T, Uo, Co, order=2, K=5, n_samples=n1, seed=1000, batch=4096, lr_total=total)
+    assert max(np.abs(U - Uo).max(), np.abs(C - Co).max()) <= TOL
+    n = 4096 * 256
+    for o in (1, 2):
+        ctx.init_embeddings(o, 128, L.DTYPE_F32, seed=o)
+    ctx.train_orders(128, 5, n, 1000, batch=4096, total=total, mode=L.MODE_HOGWILD)
+    U, C = G.tables(ctx, g, 2, 128)
+    Uo = O.init_uniform(g.n_nodes, 128, 2)
+    Co = np.zeros_like(Uo)
+    O.train_pairwise(T, Uo, Co, order=2, K=5, n_samples=n, seed=1000, batch=4096, lr_total=total)
+    rec = O.sample(T, 1000, 0, n, 5)
+    touched = np.zeros(g.n_nodes, bool)
+    touched[rec[:, 0]] = True
+    assert np.array_equal(U[~touched], Uo[~touched].astype(np.float32))
+    ctouched = np.zeros(g.n_nodes, bool)
+    ctouched[rec[:, 1:].ravel()] = True
+    assert np.array_equal(C[~ctouched], Co[~ctouched].astype(np.float32))
+    lg = O.eval_loss(T, U.astype(np.float64), C.astype(np.float64), order=2, K=5, seed=99, m=20_000)
+    lo = O.eval_loss(T, Uo, Co, order=2, K=5, seed=99, m=20_000)
+    assert abs(lg - lo) <= 0.01 * lo, (lg, lo)

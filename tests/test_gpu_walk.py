@@ -198,3 +198,33 @@ def test_walk_argument_errors(ctx):
             with pytest.raises(L_.LineError) as ei:
                 ctx.sample_walk_debug(2, 1, Lw, W, 0, 10, np.empty((10, 4), np.int32))
             assert ei.value.status == L_.LINE_ERR_ARG
+
+
+def test_full_size_rmat20_walks(ctx):
+    """The rmat20walk benchmark workload (R-MAT 20, L=100, W=2, d=128, K=5,
+    B=4096) in the benchmark's launch configuration (both orders
+    concurrently): sampled windows bit-exact, and a training prefix the
+    oracle finishes in seconds within 1e-5."""
+    from paper_2604_09419_gb300 import line as L_
+    g = G.graph("rmat20")
+    G.upload(ctx, g)
+    T = G.oracle_tables("rmat20")
+    cw = O.walk_cumw(g)
+    total = 335_544_320
+    for t0 in (0, total - 200_000):
+        out = np.empty((200_000, 7), np.int32)
+        ctx.sample_walk_debug(5, 1000, 100, 2, t0, 200_000, out)
+        assert np.array_equal(out, O.sample_walk(T, cw, 1000, t0, 200_000, 5, 100, 2)), t0
+    n = 4096 * 48
+    for o in (1, 2):
+        ctx.init_embeddings(o, 128, L_.DTYPE_F32, seed=o)
+    ctx.train_orders(128, 5, n, 1000, batch=4096, total=total, walk_length=100, window=2)
+    for o in (1, 2):
+        U, C = G.tables(ctx, g, o, 128)
+        Uo = O.init_uniform(g.n_nodes, 128, o)
+        Co = np.zeros_like(Uo) if o == 2 else None
+        O.train(T, Uo, Co, order=o, K=5, n_samples=n, seed=1000, batch=4096, lr_total=total, walk=(cw, 100, 2))
+        err = np.abs(U - Uo).max()
+        if o == 2:
+            err = max(err, np.abs(C - Co).max())
+        assert err <= TOL, (o, err)
