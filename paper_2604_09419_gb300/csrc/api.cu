@@ -491,6 +491,7 @@ line_status line_train_orders(line_ctx* c, int dim, int K, const line_lr* lr, ui
     // serialise the two streams: the call is timed as a whole instead
     const bool timing = a1.timing != 0;
     a1.timing = a2.timing = 0;
+    a1.concurrent = a2.concurrent = true;
     if (!c->ws2) c->ws2 = workspace_create();
     if (!c->side) CK(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking), "line_train_orders: stream");
     if (!c->ev_fork) CK(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming), "line_train_orders: event");

@@ -246,6 +246,7 @@ struct TrainArgs {
     const double* cw;
     int walk_len, window, walk_reuse;
     int64_t hogwild_workers;  // LINE_MODE_HOGWILD: concurrent workers (0: one resident wave)
+    bool concurrent;          // another order trains at the same time (line_train_orders)
 };
 
 struct TrainTimes {

@@ -83,6 +83,7 @@ struct DataParams {
     void* U;
     void* C;       // order 2 context table; == U for order 1
     int order, K;  // records have K+2 entries
+    int apply_warps;  // warps of an apply block (batched schedule)
     int64_t n_nodes;
     uint32_t row_bits;
     const int32_t* rec;      // [chunk samples][K+2]
@@ -430,11 +431,17 @@ __device__ __forceinline__ bool segment_item(const DataParams& p, uint4 d, int l
     return true;
 }
 
-// A long shared segment summed by the 8 warps of a CTA: warp w sums chunks
-// w, w+8, ... (entry order within a chunk); warp 0 adds the chunk partials in
-// chunk order - the same order as segment_item.  Uses lane group 0 of each
-// warp.  part: shared, 8 x D floats.
-template <int D, int DT>
+// Warps of an apply block: 16 when one order trains alone (a hub row's
+// chunks are summed in fewer rounds), 8 when two orders train concurrently
+// (smaller blocks interleave better with the other order's kernels).
+constexpr int kApplyWarpsAlone = 16, kApplyWarpsShared = 8;
+
+// A long shared segment summed by the NW warps of a CTA: warp w sums chunks
+// w, w+NW, ... (entry order within a chunk); warp 0 adds the chunk partials
+// in chunk order - the same order as segment_item, so the result does not
+// depend on the number of warps.  Uses lane group 0 of each warp.  part:
+// shared, NW x D floats.
+template <int D, int DT, int NW>
 __device__ __forceinline__ void long_segment_cta(const DataParams& p, uint4 d, float eta, uint64_t t0, float* part) {
     using G = Geom<D, DT>;
     constexpr int PF = G::E <= 4 ? 8 : 4;
@@ -453,7 +460,7 @@ __device__ __forceinline__ void long_segment_cta(const DataParams& p, uint4 d, f
 #pragma unroll
     for (int e = 0; e < G::E; ++e) acc[e] = 0.0f;
     const float* base = p.slab + (int64_t)d.x * D + (mine ? lig : 0) * G::E;
-    for (uint32_t r0 = 0; r0 < n_chunks; r0 += 8) {
+    for (uint32_t r0 = 0; r0 < n_chunks; r0 += NW) {
         const uint32_t c = r0 + (uint32_t)warp;
         if (mine && c < n_chunks) {
             float pt[G::E];
@@ -489,7 +496,7 @@ __device__ __forceinline__ void long_segment_cta(const DataParams& p, uint4 d, f
         }
         __syncthreads();
         if (warp == 0 && mine) {
-            const uint32_t nr = min(8u, n_chunks - r0);
+            const uint32_t nr = min((uint32_t)NW, n_chunks - r0);
             for (uint32_t w = 0; w < nr; ++w)
 #pragma unroll
                 for (int e = 0; e < G::E; ++e) acc[e] += part[w * D + lig * G::E + e];
@@ -532,13 +539,12 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 7) k_gather(DataParams p, i
 }
 
 // Blocks [0, g_long) take the batch's long shared segments, one per CTA; the
-// other blocks take the short ones, one per lane group.  8 warps per block.
-constexpr int kApplyThreads = 256;
+// other blocks take the short ones, one per lane group.
 
-template <int D, int DT>
-__global__ void __launch_bounds__(kApplyThreads) k_apply(DataParams p, int b, int g_long) {
+template <int D, int DT, int NW>
+__global__ void __launch_bounds__(NW * 32) k_apply(DataParams p, int b, int g_long) {
     using G = Geom<D, DT>;
-    __shared__ float part[8 * D];
+    __shared__ float part[NW * D];
     pdl_launch_dependents();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int grp = lane / G::L, lig = lane % G::L;
@@ -553,7 +559,7 @@ __global__ void __launch_bounds__(kApplyThreads) k_apply(DataParams p, int b, in
         pdl_wait();  // the slab and the rows: written by the gather
         for (uint32_t l = blockIdx.x; l < n_long; l += (uint32_t)g_long) {
             if (l != blockIdx.x) d = p.ldesc[(size_t)b * p.lcap + l];
-            long_segment_cta<D, DT>(p, d, eta, t0, part);
+            long_segment_cta<D, DT, NW>(p, d, eta, t0, part);
         }
         return;
     }
@@ -1502,7 +1508,8 @@ static cudaError_t launch_data_batched(const DataParams& p, int warps_per_block,
         cudaFuncSetAttribute(k_gather<D, DT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
     });
     const int64_t per_block = (int64_t)wpb * G::GPW;
-    const int64_t apply_per_block = (int64_t)(kApplyThreads / 32) * G::GPW;
+    const int aw = p.apply_warps == kApplyWarpsAlone ? kApplyWarpsAlone : kApplyWarpsShared;
+    const int64_t apply_per_block = (int64_t)aw * G::GPW;
     // long shared segments (more than kChunk entries, ~34 per batch on R-MAT 20)
     // each get a CTA of their own
     const int g_long = 64;
@@ -1520,7 +1527,12 @@ static cudaError_t launch_data_batched(const DataParams& p, int warps_per_block,
         // short shared segments run about 10% of the batch's entries (R-MAT
         // 20: ~2.9K of 28.7K); 2 blocks per SM leave room for the next kernel
         const unsigned g2 = (unsigned)std::min<int64_t>((max_m + apply_per_block - 1) / apply_per_block, 152 * 2);
-        e = launch_pdl(k_apply<D, DT>, (unsigned)g_long + g2, kApplyThreads, 0, s, true, p, b, g_long);
+        if (aw == kApplyWarpsAlone)
+            e = launch_pdl(k_apply<D, DT, kApplyWarpsAlone>, (unsigned)g_long + g2, kApplyWarpsAlone * 32, 0, s, true, p,
+                           b, g_long);
+        else
+            e = launch_pdl(k_apply<D, DT, kApplyWarpsShared>, (unsigned)g_long + g2, kApplyWarpsShared * 32, 0, s, true,
+                           p, b, g_long);
     }
     if (e != cudaSuccess) return e;
     return cudaGetLastError();
@@ -1757,6 +1769,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     dp.batch_applied = (uint32_t*)ws->batch_applied.p;
     dp.spin_limit = a.spin_limit;
     dp.abort_word = abort_word;
+    dp.apply_warps = a.concurrent ? kApplyWarpsShared : kApplyWarpsAlone;
 
     struct ChunkRec {
         int64_t samples;
