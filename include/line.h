@@ -167,7 +167,11 @@ LINE_API const char* line_last_error(const line_ctx* ctx);
  * 2^32 becomes a light bucket with thr = r topped up by the next heavy one.
  * Replaces any previous graph.  Embedding tables (and the warm-start MLP)
  * are kept when the new graph has the same n_nodes - so training can
- * continue on a changed edge set - and dropped otherwise.
+ * continue on a changed edge set - and dropped otherwise.  The library
+ * keeps its own device copy of src, dst and w (4 bytes per arc each; w only
+ * when given), the alias tables and the weighted degrees; per-node arc
+ * offsets (8 bytes per node) and the walk sampler's weight sums (8 bytes per
+ * arc) are added on first use.
  * Errors: LINE_ERR_ARG (sizes), LINE_ERR_VALIDATE (unsorted src, ids out of
  * range, non-positive or non-finite weights, a node set with no positive
  * weight), LINE_ERR_OOM. */

@@ -29,6 +29,8 @@
 // sequential per-pair SGD.  eta is the schedule's value at the first sample
 // of the sample's batch.
 #include <algorithm>
+#include <mutex>
+#include <vector>
 
 #include "line_internal.cuh"
 #include "rows.cuh"
@@ -260,13 +262,44 @@ cudaError_t launch(const HogwildParams& p, int64_t max_workers, cudaStream_t s) 
     const int wpb = (int)std::min<size_t>(kHogWarps, kMaxSmem / per_warp);
     if (wpb < 1) return cudaErrorInvalidValue;  // K and D beyond one warp's shared memory (not reachable for K <= 32)
     const size_t smem = (size_t)wpb * per_warp;
-    cudaError_t e = cudaFuncSetAttribute(k_hogwild<D, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    int per_sm = 0, sms = 0, dev = 0;
-    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hogwild<D, DT>, wpb * 32, smem)) != cudaSuccess)
-        return e;
+    // per device: the largest stage allowed so far (the attribute only
+    // grows, so every cached wave stays launchable) and the resident wave
+    // for each K (the stage size depends on K)
+    struct Wave {
+        int dev, K, sms, per_sm;
+    };
+    static std::mutex mu;
+    static std::vector<Wave> waves;
+    static std::vector<std::pair<int, size_t>> allowed;
+    std::lock_guard<std::mutex> lock(mu);
+    size_t* cap = nullptr;
+    for (auto& a : allowed)
+        if (a.first == dev) cap = &a.second;
+    if (!cap) {
+        allowed.push_back({dev, 0});
+        cap = &allowed.back().second;
+    }
+    if (*cap < smem) {
+        if ((e = cudaFuncSetAttribute(k_hogwild<D, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+            cudaSuccess)
+            return e;
+        *cap = smem;
+    }
+    int per_sm = -1, sms = 0;
+    for (const Wave& w : waves)
+        if (w.dev == dev && w.K == p.K) {
+            per_sm = w.per_sm;
+            sms = w.sms;
+        }
+    if (per_sm < 0) {
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_hogwild<D, DT>, wpb * 32, smem)) != cudaSuccess)
+            return e;
+        waves.push_back({dev, p.K, sms, per_sm});
+    }
     const int64_t per_block = (int64_t)wpb * G::GPW;
     const int64_t full = (int64_t)std::max(per_sm, 1) * sms * per_block;  // one resident wave
     HogwildParams q = p;
