@@ -169,3 +169,21 @@ def test_training_lowers_loss():
     O.train(T, U, C, order=2, K=5, n_samples=100_000, seed=0, batch=256)
     after = O.eval_loss(T, U, C, order=2, K=5, seed=0, m=20000)
     assert after < 0.9 * before
+
+
+def test_init_is_uniform_on_the_stated_interval():
+    """Initial U rows are uniform on [-0.5/d, 0.5/d) (the workload's
+    initialisation): every value in range and exact in FP32, the
+    distribution passes a Kolmogorov-Smirnov test, row i does not depend on
+    the table size, and seeds give different tables."""
+    from scipy.stats import kstest
+    for dim in (16, 128):
+        U = O.init_uniform(4000, dim, seed=5)
+        lo, hi = -0.5 / dim, 0.5 / dim
+        assert U.min() >= lo and U.max() < hi
+        assert np.array_equal(U.astype(np.float32).astype(np.float64), U)
+        assert kstest(U.ravel(), "uniform", args=(lo, hi - lo)).pvalue > 1e-3
+        np.testing.assert_array_equal(O.init_uniform(100, dim, seed=5), U[:100])
+        assert not np.array_equal(O.init_uniform(100, dim, seed=6), U[:100])
+        # neighbouring values are not correlated
+        assert abs(np.corrcoef(U[:, 0], U[:, 1])[0, 1]) < 0.1
