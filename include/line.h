@@ -287,8 +287,9 @@ LINE_API line_status line_set_embeddings(line_ctx* ctx, int order, int which, co
  * Result in *out_host (host pointer). */
 LINE_API line_status line_eval_loss(line_ctx* ctx, int order, int K, uint64_t seed, int64_t m, double* out_host);
 
-/* Link-prediction AUC (Section VI judges embeddings by link prediction on
- * held-out edges).  orders: bit mask of the tables to use - 1 the order-1 U
+/* Link-prediction AUC: held-out edges against non-edges (the paper's own
+ * quality measure, node classification in §V-C, needs node labels).
+ * orders: bit mask of the tables to use - 1 the order-1 U
  * table, 2 the order-2 U table, 3 both.  With z(x) the concatenation over
  * those orders of U_o[x], a pair (u, v) scores, in FP32,
  *   LINE_SCORE_DOT:    z(u).z(v);

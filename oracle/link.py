@@ -3,9 +3,10 @@
 TEST INFRASTRUCTURE: only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this module.
 
-The paper judges embeddings by how well they separate linked from unlinked
-vertex pairs (Section VI, link prediction on held-out edges).  The score and
-the statistic are the plain textbook definitions, written out:
+Embeddings are judged here by how well they separate held-out edges from
+vertex pairs that are not edges (link prediction; the paper's own measure,
+node classification by Micro/Macro-F1 in §V-C, needs node labels).  The
+score and the statistic are the plain textbook definitions, written out:
 
 * ``pair_scores`` - the inner product of the endpoints' concatenated U
   rows of the requested orders (``score="dot"``), or their cosine similarity

@@ -1,6 +1,8 @@
 // Link-prediction evaluation (reporting): scores of node pairs and the exact
-// Mann-Whitney AUC of positive against negative pairs (the paper's
-// link-prediction judgement of embeddings, Section VI).  Over the requested
+// Mann-Whitney AUC of positive against negative pairs: held-out edges
+// against non-edges, the measure of embedding quality this library reports
+// (the paper's own, node classification by Micro/Macro-F1 in §V-C, needs
+// node labels).  Over the requested
 // orders o, with z(x) = [U_o[x]]_o the concatenated rows:
 //
 //   dot:     score(u, v) = z(u).z(v) = sum_o U_o[u].U_o[v]
