@@ -237,6 +237,25 @@ def cpu_baseline(g, n_samples: int, walk=(0, 0), pairwise=False):
                       f"(single thread, host has {os.cpu_count()} cores); {dt:.1f} s"}
 
 
+def cpu_hogwild_context(g, n_samples: int):
+    """Context, not a reference: multi-threaded FP32 CPU Hogwild LINE (order 2)
+    on all host cores, on a prefix of the workload - the kind of CPU LINE the
+    paper's multi-threaded baselines are."""
+    import numpy as np
+
+    import oracle as O
+    T = O.Tables(g)
+    U = O.init_uniform(g.n_nodes, DIM, 1).astype(np.float32)
+    C = np.zeros_like(U)
+    threads = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    O.train_hogwild_cpu(T, U, C, order=2, K=K, n_samples=n_samples, seed=11, batch=B, lr_total=20 * 16 * g.n_nodes,
+                        threads=threads)
+    dt = time.perf_counter() - t0
+    return {"value": n_samples / dt, "unit": UNIT, "cores": threads, "kind": "multi-threaded FP32 CPU Hogwild (context)",
+            "sample": f"order-2 per-pair updates, {n_samples} samples, {threads} threads; {dt:.1f} s"}
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if world > 1 and rank != 0:
@@ -821,14 +840,18 @@ def main():
                "includes": "graph upload + alias build + table init + both orders + U2 read-back"}
 
     cpu = None
+    cpu_mt = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(g, args.cpu_samples, walk_of(args), pairwise=mode == L.MODE_HOGWILD)
+        if not walk_len:
+            cpu_mt = cpu_hogwild_context(g, 4 * args.cpu_samples)
 
     if rank == 0:
         line = {"metric": metric_of(args), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                 "config": workload_config(args, g), "roofline": roofline, "cpu_baseline": cpu,
+                "cpu_hogwild_context": cpu_mt,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),
                 "mode": {L.MODE_BATCHED: "batched", L.MODE_PERSISTENT: "persistent", L.MODE_HOGWILD: "hogwild"}[mode],
                 "orders": args.orders}

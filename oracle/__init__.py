@@ -58,7 +58,7 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
         tmp = _LIB_PATH + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-Wall", "-shared",
-                               "-fPIC", "-o", tmp, _SRC, "-lm"])
+                               "-fPIC", "-pthread", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -96,6 +96,10 @@ def lib():
                                                  _int, _int, _int]
             L.orc_train_pairwise.argtypes = L.orc_train.argtypes
             L.orc_train_pairwise.restype = _int
+            _f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
+            L.orc_train_hogwild_mt.argtypes = TABLE_ARGS + [_int, _int, _int, _dbl, _int, _dbl, _u64, _u64, _u64,
+                                                            _i64, _dbl, _dbl, _u64, _f32p, ctypes.c_void_p, _int]
+            L.orc_train_hogwild_mt.restype = _int
             L.orc_walk_cumw.argtypes = [_i64, _i32p, ctypes.c_void_p, _f64p]
             L.orc_walk_cumw.restype = None
             L.orc_walk_pairs_per_walk.argtypes = [_int, _int]
@@ -278,6 +282,22 @@ def train_pairwise(T: Tables, U: np.ndarray, C, *, order: int, K: int, lr0: floa
                                   None if cw is None else cw.ctypes.data, L, W, R)
     if rc:
         raise ValueError(f"orc_train_pairwise failed ({rc})")
+
+
+def train_hogwild_cpu(T: Tables, U: np.ndarray, C, *, order: int, K: int, lr0: float = 0.025, schedule: int = 1,
+                      lr_floor_frac: float = 1e-4, lr_total: int = 0, n_samples: int, seed: int, batch: int,
+                      lam: float = 0.0, alpha_neg: float = 1.0, sample_offset: int = 0, threads: int = 1):
+    """Multi-threaded CPU Hogwild in FP32 (context for the benchmark, not a
+    reference): the per-pair updates on FP32 tables U (and C), in place."""
+    assert U.dtype == np.float32 and U.flags.c_contiguous
+    cptr = None
+    if order == 2:
+        assert C is not None and C.dtype == np.float32 and C.flags.c_contiguous and C.shape == U.shape
+        cptr = C.ctypes.data
+    rc = lib().orc_train_hogwild_mt(*T.args(), order, U.shape[1], K, lr0, schedule, lr_floor_frac, lr_total,
+                                    n_samples, seed, batch, lam, alpha_neg, sample_offset, U, cptr, threads)
+    if rc:
+        raise ValueError(f"orc_train_hogwild_mt failed ({rc})")
 
 
 def eval_loss(T: Tables, U: np.ndarray, C, *, order: int, K: int, seed: int, m: int) -> float:

@@ -20,6 +20,7 @@
  * fusion.  Build: gcc -O2 -ffp-contract=off -shared -fPIC.
  */
 #include <math.h>
+#include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -549,6 +550,92 @@ int orc_train_pairwise(int64_t n_nodes, int64_t n_arcs, const int32_t* src, cons
     free(rec);
     free(wnodes);
     return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Multi-threaded CPU Hogwild in FP32 - context for the benchmark, not a     */
+/* reference: the per-pair updates of orc_train_pairwise on FP32 tables,     */
+/* with `threads` POSIX threads; thread i takes samples i, i + threads, ...  */
+/* and reads and writes the shared rows without locks, as multi-threaded     */
+/* CPU LINE does.  With one thread it is the sequential per-pair run in      */
+/* FP32.                                                                     */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    orc_tables T;
+    int order, dim, K, schedule;
+    double lr0, floor_frac;
+    uint64_t Ttot, n_samples, seed, offset;
+    int64_t batch;
+    float lambda, alpha_neg;
+    float *U, *C;
+    int tid, threads, status;
+} orc_hog_job;
+
+static void* orc_hog_worker(void* arg) {
+    orc_hog_job* j = (orc_hog_job*)arg;
+    const int dim = j->dim;
+    int32_t* rec = (int32_t*)malloc(sizeof(int32_t) * (size_t)(j->K + 2));
+    float* x = (float*)malloc(sizeof(float) * (size_t)dim);
+    float* c = (float*)malloc(sizeof(float) * (size_t)dim);
+    if (!rec || !x || !c) {
+        j->status = -2;
+        free(rec); free(x); free(c);
+        return NULL;
+    }
+    float* Ctx = j->order == 2 ? j->C : j->U;
+    for (uint64_t i = (uint64_t)j->tid; i < j->n_samples; i += (uint64_t)j->threads) {
+        const uint64_t t = j->offset + i;
+        const uint64_t t0 = j->offset + i / (uint64_t)j->batch * (uint64_t)j->batch;
+        const float eta = (float)orc_batch_lr(j->lr0, j->schedule, j->floor_frac, j->Ttot, t0);
+        sample_one(&j->T, j->seed, 0, t, j->K, rec);
+        float* urow = j->U + (int64_t)rec[0] * dim;
+        for (int k = 0; k <= j->K; ++k) {
+            float* crow = Ctx + (int64_t)rec[1 + k] * dim;
+            float sdot = 0.0f;
+            for (int e = 0; e < dim; ++e) {
+                x[e] = urow[e];
+                c[e] = crow[e];
+                sdot += x[e] * c[e];
+            }
+            const float sig = 1.0f / (1.0f + expf(-sdot));
+            const float g = k == 0 ? eta * (1.0f - sig) : -eta * j->alpha_neg * sig;
+            for (int e = 0; e < dim; ++e) urow[e] = x[e] + (g * c[e] - eta * j->lambda * x[e]);
+            for (int e = 0; e < dim; ++e) crow[e] = c[e] + (g * x[e] - eta * j->lambda * c[e]);
+        }
+    }
+    free(rec); free(x); free(c);
+    return NULL;
+}
+
+int orc_train_hogwild_mt(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t* dst,
+                         const uint32_t* thr_e, const uint32_t* alias_e, const uint32_t* thr_n,
+                         const uint32_t* alias_n, int order, int dim, int K, double lr0, int schedule,
+                         double lr_floor_frac, uint64_t lr_total, uint64_t n_samples, uint64_t seed, int64_t batch,
+                         double lambda, double alpha_neg, uint64_t sample_offset, float* U, float* C, int threads) {
+    if (batch <= 0 || dim <= 0 || K < 0 || (order != 1 && order != 2) || threads < 1 || threads > 1024) return -1;
+    orc_hog_job* jobs = (orc_hog_job*)calloc((size_t)threads, sizeof(orc_hog_job));
+    pthread_t* th = (pthread_t*)calloc((size_t)threads, sizeof(pthread_t));
+    if (!jobs || !th) { free(jobs); free(th); return -2; }
+    int rc = 0, started = 0;
+    for (int i = 0; i < threads; ++i) {
+        orc_hog_job* j = &jobs[i];
+        j->T = (orc_tables){n_nodes, n_arcs, src, dst, thr_e, alias_e, thr_n, alias_n};
+        j->order = order; j->dim = dim; j->K = K; j->schedule = schedule;
+        j->lr0 = lr0; j->floor_frac = lr_floor_frac;
+        j->Ttot = lr_total ? lr_total : sample_offset + n_samples;
+        j->n_samples = n_samples; j->seed = seed; j->offset = sample_offset; j->batch = batch;
+        j->lambda = (float)lambda; j->alpha_neg = (float)alpha_neg;
+        j->U = U; j->C = C; j->tid = i; j->threads = threads;
+        if (pthread_create(&th[i], NULL, orc_hog_worker, j) != 0) { rc = -3; break; }
+        ++started;
+    }
+    for (int i = 0; i < started; ++i) {
+        pthread_join(th[i], NULL);
+        if (jobs[i].status) rc = jobs[i].status;
+    }
+    free(jobs);
+    free(th);
+    return rc;
 }
 
 /* ------------------------------------------------------------------------ */

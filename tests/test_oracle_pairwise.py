@@ -107,3 +107,23 @@ def test_zero_lr_leaves_tables_unchanged():
     U0, C0 = U.copy(), C.copy()
     O.train_pairwise(T, U, C, order=2, K=5, n_samples=2000, seed=1, batch=64, lr0=0.0)
     assert np.array_equal(U, U0) and np.array_equal(C, C0)
+
+
+def test_cpu_hogwild_context_baseline():
+    """The multi-threaded CPU Hogwild (FP32, context for the benchmark): one
+    thread is the per-pair run in FP32 (within 1e-5 of FP64); four threads
+    racing on the rows land near the same loss."""
+    g = I.tiny_chung_lu()
+    T = O.Tables(g)
+    kw = dict(order=2, K=5, n_samples=50_000, seed=3, batch=256)
+    U, C = _tables(g, 2, 32)
+    U0, C0 = U.astype(np.float32), C.astype(np.float32)
+    O.train_pairwise(T, U, C, **kw)
+    U1, C1 = U0.copy(), C0.copy()
+    O.train_hogwild_cpu(T, U1, C1, threads=1, **kw)
+    assert max(np.abs(U1 - U).max(), np.abs(C1 - C).max()) <= 1e-5
+    U4, C4 = U0.copy(), C0.copy()
+    O.train_hogwild_cpu(T, U4, C4, threads=4, **kw)
+    l_seq = O.eval_loss(T, U, C, order=2, K=5, seed=9, m=5000)
+    l_mt = O.eval_loss(T, U4.astype(np.float64), C4.astype(np.float64), order=2, K=5, seed=9, m=5000)
+    assert abs(l_mt - l_seq) <= 0.05 * l_seq
