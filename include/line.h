@@ -14,12 +14,20 @@
  *     batch are computed from the batch-start tables and summed before being
  *     applied once, as the owner applies the summed remote deltas of Eq. 4.
  *     The sum runs over a sorted segmented reduction in a fixed order, so
- *     results are bitwise reproducible.
+ *     results are bitwise reproducible;
+ *   - alternatively, the local path of Algorithm 1 (LineUpdate applied pair
+ *     after pair) run by lock-free concurrent workers (LINE_MODE_HOGWILD);
+ *   - positive pairs from weighted random walks (Algorithms 2-3, the Local
+ *     variant of Section IV-C; opts.walk_length, opts.window, opts.walk_reuse);
+ *   - link-prediction AUC and the LINE loss for reporting, and an MLP that
+ *     predicts the rows of new nodes from their degree and neighbours (the
+ *     line_mlp_* calls).
  *
  * Every draw is a Philox4x32-10 output (Salmon et al., SC'11) at counter
  * (t_lo, t_hi, call, domain) under key (seed_lo, seed_hi); t is the global
  * sample index, call 0 draws the arc and calls 1..K the negatives, domain 0
- * is training and 3 the loss evaluation.  A draw maps its words (w0, w1, w2)
+ * is training, 1 table initialisation, 3 the loss evaluation, 7 the MLP and
+ * 8 the walks.  A draw maps its words (w0, w1, w2)
  * through an alias table: i = mulhi64(w1:w0, n), k = w2 < thr[i] ? i : alias[i].
  *
  * Conventions
