@@ -362,11 +362,13 @@ line_status line_init_embeddings(line_ctx* c, int order, int dim, int dtype, uin
     Tables& t = c->tab[order];
     free_tables(t);
     const size_t bytes = (size_t)c->n_nodes * dim * elem_size(dtype);
-    CK(cudaMalloc(&t.U, bytes), "table allocation");
-    CK(init_table(t.U, dtype, c->n_nodes, dim, seed, c->stream), "table init");
-    if (order == 2) {
-        CK(cudaMalloc(&t.C, bytes), "table allocation");
-        CK(cudaMemsetAsync(t.C, 0, bytes, c->stream), "table init");
+    cudaError_t e = cudaMalloc(&t.U, bytes);
+    if (e == cudaSuccess) e = init_table(t.U, dtype, c->n_nodes, dim, seed, c->stream);
+    if (e == cudaSuccess && order == 2) e = cudaMalloc(&t.C, bytes);
+    if (e == cudaSuccess && order == 2) e = cudaMemsetAsync(t.C, 0, bytes, c->stream);
+    if (e != cudaSuccess) {
+        free_tables(t);  // nothing of a failed call is kept
+        return cuda_fail(c, e, "line_init_embeddings: table allocation");
     }
     t.dim = dim;
     t.dtype = dtype;

@@ -88,3 +88,22 @@ def test_set_get_roundtrip():
     with pytest.raises(L.LineError):
         ctx.set_embeddings(2, L.WHICH_U, vals, L.DTYPE_F32, np.array([1, 2, 3, 5000], np.int32))
     ctx.close()
+
+
+def test_allocation_failure_is_reported_and_not_sticky():
+    """A real device allocation failure (tables of 2^29 nodes x 256 FP32
+    values, 549 GB, far above the GPU's memory; the first allocation already
+    fails, so nothing large is ever held): LINE_ERR_OOM, nothing is kept,
+    and the context goes on working."""
+    from paper_2604_09419_gb300 import line as L
+    ctx = G.context()
+    n = 1 << 29
+    ctx.build_alias(n, np.array([0, 1], np.int32), np.array([1, 0], np.int32), None)
+    with pytest.raises(L.LineError) as e:
+        ctx.init_embeddings(2, 256, L.DTYPE_F32, 0)
+    assert e.value.status == L.LINE_ERR_OOM
+    g = G.graph("tiny")
+    G.upload(ctx, g)
+    ctx.init_embeddings(2, 16, L.DTYPE_F32, 0)
+    ctx.train_steps(2, 16, 5, 1000, 1, batch=64)
+    ctx.close()
