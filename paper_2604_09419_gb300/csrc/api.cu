@@ -195,6 +195,7 @@ void line_destroy(line_ctx* c) {
 const char* line_last_error(const line_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
 line_status line_build_alias(line_ctx* c, const line_graph_desc* g) {
+    NvtxRange nvtx("line_build_alias");
     line_status st = enter(c);
     if (st) return st;
     if (!g || !g->src || !g->dst) return fail(c, LINE_ERR_ARG, "line_build_alias: null graph arrays");
@@ -283,6 +284,7 @@ line_status line_get_alias(line_ctx* c, int table, uint32_t* thr, uint32_t* alia
 
 line_status line_sample_debug(line_ctx* c, int K, uint64_t seed, uint32_t domain, uint64_t t0, int64_t count,
                               int32_t* out) {
+    NvtxRange nvtx("line_sample_debug");
     line_status st = enter(c);
     if (st) return st;
     if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_sample_debug: no graph");
@@ -305,6 +307,7 @@ line_status line_sample_debug(line_ctx* c, int K, uint64_t seed, uint32_t domain
 
 line_status line_sample_walk_debug(line_ctx* c, int K, uint64_t seed, int walk_length, int window, int reuse,
                                    uint64_t t0, int64_t count, int32_t* out) {
+    NvtxRange nvtx("line_sample_walk_debug");
     line_status st = enter(c);
     if (st) return st;
     if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_sample_walk_debug: no graph");
@@ -354,6 +357,7 @@ line_status line_sample_walk_debug(line_ctx* c, int K, uint64_t seed, int walk_l
 }
 
 line_status line_init_embeddings(line_ctx* c, int order, int dim, int dtype, uint64_t seed) {
+    NvtxRange nvtx("line_init_embeddings");
     line_status st = enter(c);
     if (st) return st;
     if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_init_embeddings: no graph");
@@ -460,6 +464,7 @@ extern "C" {
 
 line_status line_train_steps(line_ctx* c, int order, int dim, int K, const line_lr* lr, uint64_t n_samples,
                              uint64_t seed, const line_train_opts* opts) {
+    NvtxRange nvtx("line_train_steps");
     line_status st = enter(c);
     if (st) return st;
     TrainArgs a{};
@@ -483,6 +488,7 @@ line_status line_train_steps(line_ctx* c, int order, int dim, int K, const line_
 
 line_status line_train_orders(line_ctx* c, int dim, int K, const line_lr* lr, uint64_t n_samples, uint64_t seed,
                               const line_train_opts* opts) {
+    NvtxRange nvtx("line_train_orders");
     line_status st = enter(c);
     if (st) return st;
     TrainArgs a1{}, a2{};
@@ -530,6 +536,7 @@ line_status line_train_orders(line_ctx* c, int dim, int K, const line_lr* lr, ui
 }
 
 line_status line_get_embeddings(line_ctx* c, int order, int which, void* dst, int dst_dtype) {
+    NvtxRange nvtx("line_get_embeddings");
     line_status st = enter(c);
     if (st) return st;
     if (order != 1 && order != 2) return fail(c, LINE_ERR_ARG, "line_get_embeddings: bad order");
@@ -559,6 +566,7 @@ line_status line_get_embeddings(line_ctx* c, int order, int which, void* dst, in
 
 line_status line_set_embeddings(line_ctx* c, int order, int which, const void* src, int src_dtype,
                                 const int32_t* rows, int64_t n_rows) {
+    NvtxRange nvtx("line_set_embeddings");
     line_status st = enter(c);
     if (st) return st;
     if (order != 1 && order != 2) return fail(c, LINE_ERR_ARG, "line_set_embeddings: bad order");
@@ -587,6 +595,7 @@ line_status line_set_embeddings(line_ctx* c, int order, int which, const void* s
 }
 
 line_status line_eval_loss(line_ctx* c, int order, int K, uint64_t seed, int64_t m, double* out_host) {
+    NvtxRange nvtx("line_eval_loss");
     line_status st = enter(c);
     if (st) return st;
     if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_eval_loss: no graph");
@@ -617,6 +626,7 @@ line_status line_eval_loss(line_ctx* c, int order, int K, uint64_t seed, int64_t
 line_status line_eval_auc(line_ctx* c, int orders, int score, const int32_t* pos_src, const int32_t* pos_dst, int64_t n_pos,
                           const int32_t* neg_src, const int32_t* neg_dst, int64_t n_neg, float* scores_out,
                           uint64_t* counts_out, double* auc_out) {
+    NvtxRange nvtx("line_eval_auc");
     line_status st = enter(c);
     if (st) return st;
     if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_eval_auc: no graph");

@@ -2,6 +2,8 @@
 // C entry points (api.cu, mlp.cu).  Internal: not part of include/line.h.
 #pragma once
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <string>
 
 #include "line_internal.cuh"
@@ -74,6 +76,15 @@ line_status check_status(line_ctx* c, const char* what, bool timeout_sticky = tr
 line_status ensure_row_ptr(line_ctx* c);
 // Builds the walk sampler tables (row_ptr, cw) if they are missing.
 line_status ensure_walk_tables(line_ctx* c);
+
+// An NVTX range over an entry point's host scope (no cost unless a profiler
+// is attached; ncu and nsys can filter launches by it).
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 }  // namespace line
 

@@ -1072,6 +1072,7 @@ cudaError_t upload_nodes(MlpState& s, const int32_t* nodes, int64_t n, cudaStrea
 extern "C" {
 
 line_status line_mlp_create(line_ctx* c, int order, int hidden, int act_dtype, uint64_t seed) {
+    NvtxRange nvtx("line_mlp_create");
     line_status st = enter(c);
     if (st) return st;
     if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_mlp_create: no graph");
@@ -1176,10 +1177,12 @@ static line_status mlp_features_impl(line_ctx* c, const char* what, const uint8_
 }
 
 line_status line_mlp_features(line_ctx* c, const uint8_t* known) {
+    NvtxRange nvtx("line_mlp_features");
     return mlp_features_impl(c, "line_mlp_features", known, nullptr, 0);
 }
 
 line_status line_mlp_features_rows(line_ctx* c, const uint8_t* known, const int32_t* rows, int64_t n_rows) {
+    NvtxRange nvtx("line_mlp_features_rows");
     if (!rows) return c ? fail(c, LINE_ERR_ARG, "line_mlp_features_rows: null rows") : LINE_ERR_ARG;
     return mlp_features_impl(c, "line_mlp_features_rows", known, rows, n_rows);
 }
@@ -1237,6 +1240,7 @@ line_status line_mlp_set_params(line_ctx* c, const float* in) {
 }
 
 line_status line_mlp_grad(line_ctx* c, const int32_t* rows, int64_t n_rows, float* grads_out, double* loss_out) {
+    NvtxRange nvtx("line_mlp_grad");
     line_status st = enter(c);
     if (st) return st;
     if ((st = mlp_ready(c, "line_mlp_grad", true))) return st;
@@ -1266,6 +1270,7 @@ line_status line_mlp_grad(line_ctx* c, const int32_t* rows, int64_t n_rows, floa
 
 line_status line_mlp_train(line_ctx* c, const int32_t* nodes, int64_t n_nodes, int64_t steps, int64_t batch,
                            double lr, uint64_t seed, uint64_t step_offset, double* losses_out) {
+    NvtxRange nvtx("line_mlp_train");
     line_status st = enter(c);
     if (st) return st;
     if ((st = mlp_ready(c, "line_mlp_train", true))) return st;
@@ -1310,6 +1315,7 @@ line_status line_mlp_train(line_ctx* c, const int32_t* nodes, int64_t n_nodes, i
 }
 
 line_status line_mlp_predict(line_ctx* c, const int32_t* rows, int64_t n_rows, float* y_out) {
+    NvtxRange nvtx("line_mlp_predict");
     line_status st = enter(c);
     if (st) return st;
     if ((st = mlp_ready(c, "line_mlp_predict", true))) return st;

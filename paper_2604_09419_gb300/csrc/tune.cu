@@ -13,6 +13,7 @@ extern "C" {
 
 line_status line_autotune(line_ctx* c, int order, int dim, int K, const line_lr* lr, const line_tune_opts* topts,
                           line_train_opts* io, double* best_rate) {
+    NvtxRange nvtx("line_autotune");
     line_status st = enter(c);
     if (st) return st;
     if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_autotune: no graph");
