@@ -64,7 +64,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-METRIC = "edge-sample updates/s (d=128,K=5)"
+# the headline metric as the workload states it; `value` is its first part
+# (updates/s), `roofline.frac` the second, and the warm22 workload the third
+METRIC = "edge-sample updates/s (d=128,K=5), HBM roofline %, BF16+warm vs FP32 at equal AUC"
 UNIT = "updates/s"
 DIM, K, B = 128, 5, 4096
 ROW_BYTES_F32 = DIM * 4
