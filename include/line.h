@@ -135,9 +135,13 @@ typedef struct {
  * Ctx[y] <- c + (g x - eta lambda c).  eta is the schedule's value at the
  * first sample of the sample's block of opts.batch samples.  Workers run
  * samples concurrently on the shared tables without locks (Hogwild): a
- * worker sees other workers' rows as they are when it loads them, and
- * concurrent writes of a row keep one of them.  The result is therefore not
- * deterministic, except with hogwild_workers = 1, which is the sequential
+ * worker sees other workers' rows as they are when it loads them, and adds
+ * its changes to the rows with atomic read-modify-writes, so no worker's
+ * change is overwritten by another's (the context row's change after each
+ * call, U[u]'s net change after the sample's last call; BF16 tables add the
+ * change plus uniform noise of one unit in the last place, rounded to
+ * nearest).  With more than one worker the order of the additions, hence the
+ * result, is not deterministic; hogwild_workers = 1 is the sequential
  * per-pair SGD.  Samples (arcs or walk pairs, negatives) are the same as in
  * the other modes. */
 
@@ -157,7 +161,10 @@ LINE_API const char* line_status_string(line_status s);
 
 /* Create a context on CUDA device `device`; all work goes to `cuda_stream`
  * (a cudaStream_t, NULL for the legacy default stream).  *out receives the
- * context or NULL on failure. */
+ * context or NULL on failure.  No paper counterpart: the context holds what
+ * one NOMAD process keeps in memory (its graph partition, distributions and
+ * embedding rows, Algorithm 1's inputs), here for the whole graph on one GPU.
+ * Errors: LINE_ERR_ARG (no such device, out NULL), LINE_ERR_CUDA. */
 LINE_API line_status line_create(line_ctx** out, int device, void* cuda_stream);
 LINE_API void line_destroy(line_ctx* ctx);
 LINE_API const char* line_last_error(const line_ctx* ctx);
@@ -185,10 +192,17 @@ LINE_API const char* line_last_error(const line_ctx* ctx);
  * weight), LINE_ERR_OOM. */
 LINE_API line_status line_build_alias(line_ctx* ctx, const line_graph_desc* g);
 
+/* Node and arc counts of the current graph (host pointers, either may be
+ * NULL).  No paper counterpart (bookkeeping).  Errors: LINE_ERR_STATE (no
+ * graph). */
 LINE_API line_status line_get_graph_info(line_ctx* ctx, int64_t* n_nodes, int64_t* n_arcs);
 
 /* Export an alias table (LINE_TABLE_EDGE: n_arcs entries; LINE_TABLE_NEG:
- * n_nodes entries) into two uint32 buffers thr[] and alias[]. */
+ * n_nodes entries) into two uint32 buffers thr[] and alias[].  These are the
+ * samplers of the edge distribution of Algorithm 3 and of q(v) of Eq. 1
+ * (Section IV-A); the paper names only the distributions, the alias form is
+ * this library's (see line_build_alias).  Errors: LINE_ERR_ARG (bad table,
+ * NULL buffer), LINE_ERR_STATE (no graph). */
 LINE_API line_status line_get_alias(line_ctx* ctx, int table, uint32_t* thr, uint32_t* alias);
 
 /* Write the draws of samples t0 .. t0+count-1 in `domain` as int32 records
@@ -279,13 +293,19 @@ LINE_API line_status line_autotune(line_ctx* ctx, int order, int dim, int K, con
                                    const line_tune_opts* topts, line_train_opts* io, double* best_rate);
 
 /* Copy a whole table (n_nodes x dim, row-major) into `dst` (a buffer) as
- * dst_dtype (F32, or BF16 when the table is BF16). */
+ * dst_dtype (F32, or BF16 when the table is BF16).  These are the outputs U
+ * and C of Algorithm 1 (the trained embeddings); the call itself has no
+ * paper counterpart.  Errors: LINE_ERR_ARG, LINE_ERR_STATE (no such table). */
 LINE_API line_status line_get_embeddings(line_ctx* ctx, int order, int which, void* dst, int dst_dtype);
 
 /* Overwrite rows of a table from `src` (a buffer of n_rows x dim values of
  * src_dtype).  rows: n_rows int32 row ids (a buffer), or NULL for rows
  * 0..n_rows-1.  F32 into a BF16 table rounds to nearest even.  Used for
- * warm starts and checkpoint restore. */
+ * warm starts and checkpoint restore.  No paper counterpart: the paper's
+ * rows start only from the random initialisation of Algorithm 1.
+ * Errors: LINE_ERR_ARG (bad arguments, or a row id out of range: that row is
+ * skipped, the others are written), LINE_ERR_STATE (no such table),
+ * LINE_ERR_OOM. */
 LINE_API line_status line_set_embeddings(line_ctx* ctx, int order, int which, const void* src, int src_dtype,
                                 const int32_t* rows, int64_t n_rows);
 
@@ -407,9 +427,12 @@ LINE_API line_status line_mlp_predict(line_ctx* ctx, const int32_t* rows, int64_
  * array of LINE_NOALLOC_MAX_SAMPLES + 1024 doubles (8 MiB + 8 KiB) that every
  * GPU loading this library holds until the process exits; the result is the
  * same as line_eval_loss.  m must be 1..LINE_NOALLOC_MAX_SAMPLES, otherwise
- * LINE_ERR_ARG and nothing runs.  The first call on a device looks up the
- * array's device address (once per device, that device current); make that
- * first call before any stream capture.  All calls, from every context, share
+ * LINE_ERR_ARG and nothing runs.  line_create looks up the array's device
+ * address on its device (under lazy module loading that first look-up loads
+ * the array and may allocate it), so this call itself allocates nothing.  The
+ * call ends by copying the result to the host and synchronising the
+ * context's stream: it must not be made while that stream is being captured
+ * into a CUDA graph.  All calls, from every context, share
  * the one array: calls whose GPU work overlaps (different streams or
  * contexts on the same device) race and give wrong results; calls ordered on
  * one stream are safe, and no state carries over from one call to the next.

@@ -94,6 +94,16 @@ def lib():
             L.orc_train.argtypes = TABLE_ARGS + [_int, _int, _int, _dbl, _int, _dbl, _u64, _u64, _u64,
                                                  _i64, _dbl, _dbl, _u64, _f64p, ctypes.c_void_p, ctypes.c_void_p,
                                                  _int, _int, _int]
+            L.orc_train_bf16.argtypes = L.orc_train.argtypes
+            L.orc_train_bf16.restype = _int
+            L.orc_splitmix64_mix.argtypes = [_u64]
+            L.orc_splitmix64_mix.restype = _u64
+            L.orc_sr_bits.argtypes = [_u64, _u32, _u64, _u64, _u32]
+            L.orc_sr_bits.restype = _u64
+            L.orc_bf16_sr_bits.argtypes = [ctypes.c_float, _u32]
+            L.orc_bf16_sr_bits.restype = ctypes.c_uint16
+            L.orc_bf16_rn_bits.argtypes = [ctypes.c_float]
+            L.orc_bf16_rn_bits.restype = ctypes.c_uint16
             L.orc_train_pairwise.argtypes = L.orc_train.argtypes
             L.orc_train_pairwise.restype = _int
             _f32p = np.ctypeslib.ndpointer(np.float32, flags="C_CONTIGUOUS")
@@ -246,10 +256,12 @@ def _walk_args(walk):
 
 def train(T: Tables, U: np.ndarray, C, *, order: int, K: int, lr0: float = 0.025, schedule: int = 1,
           lr_floor_frac: float = 1e-4, lr_total: int = 0, n_samples: int, seed: int, batch: int,
-          lam: float = 0.0, alpha_neg: float = 1.0, sample_offset: int = 0, walk=None):
+          lam: float = 0.0, alpha_neg: float = 1.0, sample_offset: int = 0, walk=None, bf16: bool = False):
     """Minibatch-synchronous LINE in place on FP64 tables U (and C for order 2).
     walk: None (arcs drawn by weight) or (cw, L, W) or (cw, L, W, reuse) for
-    the walk sampler."""
+    the walk sampler.  bf16: the tables hold BF16 values and every row
+    written after a batch is rounded to FP32, then stochastically to BF16
+    (``bf16_sr`` with the bits of ``sr_bits``)."""
     assert U.dtype == np.float64 and U.flags.c_contiguous
     dim = U.shape[1]
     cptr = None
@@ -257,11 +269,48 @@ def train(T: Tables, U: np.ndarray, C, *, order: int, K: int, lr0: float = 0.025
         assert C is not None and C.dtype == np.float64 and C.flags.c_contiguous and C.shape == U.shape
         cptr = C.ctypes.data
     cw, L, W, R = _walk_args(walk)
-    rc = lib().orc_train(*T.args(), order, dim, K, lr0, schedule, lr_floor_frac, lr_total, n_samples,
-                         seed, batch, lam, alpha_neg, sample_offset, U, cptr,
-                         None if cw is None else cw.ctypes.data, L, W, R)
+    fn = lib().orc_train_bf16 if bf16 else lib().orc_train
+    rc = fn(*T.args(), order, dim, K, lr0, schedule, lr_floor_frac, lr_total, n_samples,
+            seed, batch, lam, alpha_neg, sample_offset, U, cptr,
+            None if cw is None else cw.ctypes.data, L, W, R)
     if rc:
         raise ValueError(f"orc_train failed ({rc})")
+
+
+def splitmix64_mix(z: int) -> int:
+    """The SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014)."""
+    return int(lib().orc_splitmix64_mix(z & 0xFFFFFFFFFFFFFFFF))
+
+
+def sr_bits(seed: int, table: int, row: int, t0: int, k4: int) -> int:
+    """The 64 stochastic-rounding bits of values 4 k4 .. 4 k4 + 3 of `row`
+    of table `table` (0 U, 1 C) written by the batch starting at sample t0."""
+    return int(lib().orc_sr_bits(seed & 0xFFFFFFFFFFFFFFFF, table, row, t0, k4))
+
+
+def bf16_sr_bits(x: float, r16: int) -> int:
+    """BF16 bit pattern of the FP32 value x rounded stochastically with 16 bits r16."""
+    return int(lib().orc_bf16_sr_bits(float(np.float32(x)), r16))
+
+
+def bf16_rn_bits(x: float) -> int:
+    """BF16 bit pattern of the FP32 value x rounded to nearest, ties to even."""
+    return int(lib().orc_bf16_rn_bits(float(np.float32(x))))
+
+
+def bf16_value(h: int) -> float:
+    """The value of a BF16 bit pattern."""
+    return float(np.array([h << 16], np.uint32).view(np.float32)[0])
+
+
+def round_bf16_rn(x: np.ndarray) -> np.ndarray:
+    """Values of an FP32-exact array rounded to BF16 (nearest even), as FP64."""
+    f = np.ascontiguousarray(x, np.float32).ravel()
+    out = np.empty(f.size, np.float64)
+    fn = lib().orc_bf16_rn_bits
+    for i, v in enumerate(f.tolist()):
+        out[i] = bf16_value(int(fn(v)))
+    return out.reshape(np.shape(x))
 
 
 def train_pairwise(T: Tables, U: np.ndarray, C, *, order: int, K: int, lr0: float = 0.025, schedule: int = 1,

@@ -424,12 +424,77 @@ double orc_batch_lr(double lr0, int schedule, double floor_frac, uint64_t T, uin
  * where _b is the state at the start of the batch; after the batch X += dX.
  * order 2: Ctx = C (a separate table); order 1: Ctx = U (C is unused).
  * lr_total is T of the schedule (0 means sample_offset + n_samples). */
-int orc_train(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t* dst,
-              const uint32_t* thr_e, const uint32_t* alias_e, const uint32_t* thr_n, const uint32_t* alias_n,
-              int order, int dim, int K, double lr0, int schedule, double lr_floor_frac, uint64_t lr_total,
-              uint64_t n_samples, uint64_t seed, int64_t batch, double lambda, double alpha_neg,
-              uint64_t sample_offset, double* U, double* C, const double* walk_cw, int walk_len, int window,
-              int walk_reuse) {
+/* ------------------------------------------------------------------------ */
+/* BF16 tables with stochastic rounding (a storage mode of the target; the   */
+/* paper's tables are FP32).  A value written back is first the exact sum    */
+/* X_b + dX rounded to FP32 (nearest), then rounded to BF16 stochastically:  */
+/* 16 random bits r are added to the FP32 bit pattern below the BF16         */
+/* mantissa and the low 16 bits are dropped; Inf and NaN pass unchanged.     */
+/* Over the 2^16 equally likely r the expected BF16 value is the FP32 value  */
+/* exactly.  The bits for the values 4k4 .. 4k4+3 of `row` of table `table`  */
+/* (0: U, 1: C) written by the batch whose first sample is t0 are the        */
+/* SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014) of the key   */
+/*   seed ^ (t0 * 0x9E3779B97F4A7C15) ^                                      */
+/*   (((row << 16) | (table << 15) | k4) * 0xD1B54A32D192ED03)               */
+/* (mod 2^64); value i of the four takes bits [16 i, 16 i + 16).             */
+/* ------------------------------------------------------------------------ */
+uint64_t orc_splitmix64_mix(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+uint64_t orc_sr_bits(uint64_t seed, uint32_t table, uint64_t row, uint64_t t0, uint32_t k4) {
+    uint64_t key = ((row << 16) | ((uint64_t)table << 15) | (uint64_t)k4) * 0xD1B54A32D192ED03ull;
+    return orc_splitmix64_mix(seed ^ (t0 * 0x9E3779B97F4A7C15ull) ^ key);
+}
+
+static uint32_t f32_bits(float x) {
+    uint32_t b;
+    memcpy(&b, &x, 4);
+    return b;
+}
+
+static double bf16_bits_value(uint16_t h) {
+    uint32_t b = (uint32_t)h << 16;
+    float f;
+    memcpy(&f, &b, 4);
+    return (double)f;
+}
+
+/* BF16 bit pattern of FP32 x rounded stochastically with the 16 bits r16. */
+uint16_t orc_bf16_sr_bits(float x, uint32_t r16) {
+    uint32_t b = f32_bits(x);
+    if ((b & 0x7F800000u) != 0x7F800000u) b += r16 & 0xFFFFu;
+    return (uint16_t)(b >> 16);
+}
+
+/* BF16 bit pattern of FP32 x rounded to nearest, ties to even (NaN kept). */
+uint16_t orc_bf16_rn_bits(float x) {
+    uint32_t b = f32_bits(x);
+    if ((b & 0x7F800000u) == 0x7F800000u) return (uint16_t)(b >> 16) | ((b & 0xFFFFu) ? 0x40u : 0u);
+    uint32_t lsb = (b >> 16) & 1u;
+    b += 0x7FFFu + lsb;
+    return (uint16_t)(b >> 16);
+}
+
+/* Row v of a BF16 table after the batch starting at t0: X_b + dX, rounded. */
+static void bf16_write_row(double* X, const double* dX, int64_t v, int dim, uint64_t seed, uint32_t table,
+                           uint64_t t0) {
+    for (int k = 0; k < dim; ++k) {
+        float f = (float)(X[v * dim + k] + dX[v * dim + k]);
+        uint64_t r = orc_sr_bits(seed, table, (uint64_t)v, t0, (uint32_t)(k / 4));
+        uint32_t r16 = (uint32_t)(r >> (16 * (k % 4))) & 0xFFFFu;
+        X[v * dim + k] = bf16_bits_value(orc_bf16_sr_bits(f, r16));
+    }
+}
+
+static int train_minibatch(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t* dst,
+                           const uint32_t* thr_e, const uint32_t* alias_e, const uint32_t* thr_n,
+                           const uint32_t* alias_n, int order, int dim, int K, double lr0, int schedule,
+                           double lr_floor_frac, uint64_t lr_total, uint64_t n_samples, uint64_t seed, int64_t batch,
+                           double lambda, double alpha_neg, uint64_t sample_offset, double* U, double* C,
+                           const double* walk_cw, int walk_len, int window, int walk_reuse, int bf16) {
     if (batch <= 0 || dim <= 0 || K < 0 || (order != 1 && order != 2)) return -1;
     if (walk_cw && (walk_len < 1 || window < 1 || window > walk_len || walk_reuse < 1)) return -1;
     orc_tables T = {n_nodes, n_arcs, src, dst, thr_e, alias_e, thr_n, alias_n};
@@ -479,12 +544,16 @@ int orc_train(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t
         }
         for (int64_t r = 0; r < nrows_u; ++r) {
             int64_t v = rows_u[r];
-            for (int k = 0; k < dim; ++k) { U[v * dim + k] += dU[v * dim + k]; dU[v * dim + k] = 0.0; }
+            if (bf16) bf16_write_row(U, dU, v, dim, seed, 0u, t0);
+            else for (int k = 0; k < dim; ++k) U[v * dim + k] += dU[v * dim + k];
+            for (int k = 0; k < dim; ++k) dU[v * dim + k] = 0.0;
             touchU[v] = 0;
         }
         for (int64_t r = 0; r < nrows_c; ++r) {
             int64_t v = rows_c[r];
-            for (int k = 0; k < dim; ++k) { C[v * dim + k] += dC[v * dim + k]; dC[v * dim + k] = 0.0; }
+            if (bf16) bf16_write_row(C, dC, v, dim, seed, 1u, t0);
+            else for (int k = 0; k < dim; ++k) C[v * dim + k] += dC[v * dim + k];
+            for (int k = 0; k < dim; ++k) dC[v * dim + k] = 0.0;
             touchC[v] = 0;
         }
     }
@@ -495,6 +564,30 @@ int orc_train(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t
     free(dU);
     free(touchU);
     return 0;
+}
+
+int orc_train(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t* dst,
+              const uint32_t* thr_e, const uint32_t* alias_e, const uint32_t* thr_n, const uint32_t* alias_n,
+              int order, int dim, int K, double lr0, int schedule, double lr_floor_frac, uint64_t lr_total,
+              uint64_t n_samples, uint64_t seed, int64_t batch, double lambda, double alpha_neg,
+              uint64_t sample_offset, double* U, double* C, const double* walk_cw, int walk_len, int window,
+              int walk_reuse) {
+    return train_minibatch(n_nodes, n_arcs, src, dst, thr_e, alias_e, thr_n, alias_n, order, dim, K, lr0, schedule,
+                           lr_floor_frac, lr_total, n_samples, seed, batch, lambda, alpha_neg, sample_offset, U, C,
+                           walk_cw, walk_len, window, walk_reuse, 0);
+}
+
+/* The same batches on BF16 tables: U (and C) hold BF16 values (as doubles)
+ * and every row written after a batch is rounded as described above. */
+int orc_train_bf16(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t* dst,
+                   const uint32_t* thr_e, const uint32_t* alias_e, const uint32_t* thr_n, const uint32_t* alias_n,
+                   int order, int dim, int K, double lr0, int schedule, double lr_floor_frac, uint64_t lr_total,
+                   uint64_t n_samples, uint64_t seed, int64_t batch, double lambda, double alpha_neg,
+                   uint64_t sample_offset, double* U, double* C, const double* walk_cw, int walk_len, int window,
+                   int walk_reuse) {
+    return train_minibatch(n_nodes, n_arcs, src, dst, thr_e, alias_e, thr_n, alias_n, order, dim, K, lr0, schedule,
+                           lr_floor_frac, lr_total, n_samples, seed, batch, lambda, alpha_neg, sample_offset, U, C,
+                           walk_cw, walk_len, window, walk_reuse, 1);
 }
 
 /* ------------------------------------------------------------------------ */

@@ -27,8 +27,6 @@ namespace line {
 
 namespace {
 
-constexpr int kSumBlock = 1024;
-
 // Fixed-order FP64 sum of one block of 1024 values: halving strides.
 __global__ void __launch_bounds__(kSumBlock / 2) k_tree_sum(const double* __restrict__ x, int64_t n,
                                                              double* __restrict__ out) {

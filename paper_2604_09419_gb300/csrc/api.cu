@@ -168,6 +168,14 @@ line_status line_create(line_ctx** out, int device, void* cuda_stream) {
         return LINE_ERR_CUDA;
     }
     c->flag = c->status + 32;  // never set: target of line_debug_wait_timeout
+    // load the fixed array of line_eval_loss_noalloc on this device now, so
+    // that its callers never trigger a module load or allocation later
+    double* noalloc_scratch = nullptr;
+    if (noalloc_scratch_address(device, &noalloc_scratch) != cudaSuccess) {
+        cudaGetLastError();
+        line_destroy(c);
+        return LINE_ERR_CUDA;
+    }
     c->ws = workspace_create();
     *out = c;
     return LINE_OK;
@@ -676,6 +684,7 @@ line_status line_eval_auc(line_ctx* c, int orders, int score, const int32_t* pos
 }
 
 line_status line_eval_loss_noalloc(line_ctx* c, int order, int K, uint64_t seed, int64_t m, double* out_host) {
+    NvtxRange nvtx("line_eval_loss_noalloc");
     line_status st = enter(c);
     if (st) return st;
     if (!c->has_graph) return fail(c, LINE_ERR_STATE, "line_eval_loss_noalloc: no graph");

@@ -117,6 +117,9 @@ struct DeviceScratch {
 };
 
 // alias.cu
+// Block of the fixed-order FP64 sum: blocks of kSumBlock values are each
+// reduced by halving strides, then the block sums likewise, recursively.
+constexpr int kSumBlock = 1024;
 cudaError_t fixed_sum_f64(const double* x, int64_t n, double* tmp, double* out, cudaStream_t s);
 size_t fixed_sum_tmp_bytes(int64_t n);
 cudaError_t validate_graph(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t* dst,

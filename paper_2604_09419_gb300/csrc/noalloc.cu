@@ -5,8 +5,11 @@
 // library holds it until the process exits.  In host code its name is only a
 // stand-in, not a device address, so the address is looked up once per device
 // with cudaGetSymbolAddress (with that device current) and passed to the
-// kernels.  Every call reuses the same array; nothing in it has to start at
-// zero because each call writes every cell it later reads.
+// kernels.  line_create does that look-up for its device, so the array is
+// loaded and its address known before any entry point runs (under lazy
+// module loading the array is created by the first look-up, which may
+// allocate).  Every call reuses the same array; nothing in it has to start
+// at zero because each call writes every cell it later reads.
 #include <mutex>
 
 #include "line_internal.cuh"
@@ -15,10 +18,12 @@ namespace line {
 
 namespace {
 
-// m per-sample loss terms, then the <= 1024 block sums of the fixed-order
-// reduction of m <= LINE_NOALLOC_MAX_SAMPLES terms.
+// m per-sample loss terms, then the block sums of the fixed-order reduction
+// of m <= LINE_NOALLOC_MAX_SAMPLES terms.  With at most kSumBlock block sums
+// the reduction has one intermediate level, which fits in kSumSlots.
 constexpr int64_t kMaxM = LINE_NOALLOC_MAX_SAMPLES;
-constexpr int64_t kSumSlots = (kMaxM + 1023) / 1024;
+constexpr int64_t kSumSlots = (kMaxM + kSumBlock - 1) / kSumBlock;
+static_assert(kMaxM <= (int64_t)kSumBlock * kSumBlock, "the fixed-order sum would need a second intermediate level");
 static __device__ __align__(256) double g_loss_scratch[kMaxM + kSumSlots];
 
 constexpr int kMaxDevices = 64;
@@ -45,6 +50,9 @@ cudaError_t eval_loss_noalloc(int device, const void* U, const void* Ctx, int dt
                               const uint2* neg_tab, int64_t n_nodes, uint64_t seed, int64_t m, double* out_dev,
                               cudaStream_t s) {
     if (m < 1 || m > kMaxM) return cudaErrorInvalidValue;
+    // the block sums of the one intermediate level must fit in kSumSlots
+    const int64_t n_block_sums = (m + kSumBlock - 1) / kSumBlock;
+    if (n_block_sums > kSumSlots || n_block_sums > kSumBlock) return cudaErrorInvalidValue;
     double* scratch = nullptr;
     cudaError_t e = noalloc_scratch_address(device, &scratch);
     if (e != cudaSuccess) return e;

@@ -3,19 +3,20 @@ allocate device memory while they run (a service that reserved all device
 memory up front, a latency-bound loop where cudaMalloc/cudaFree would
 synchronise the device).  Its scratch is one fixed device array that every
 call reuses, so two calls in a row must each agree with the allocating
-line_eval_loss; sizes beyond the array are refused.
+line_eval_loss; sizes beyond the array are refused; and the calls leave the
+device's free memory unchanged.
 
-This file is named to be collected last.
+Both calls run the same loss kernel and the same fixed-order FP64 sum, so
+they agree bit for bit.  This file is named to be collected last.
 """
 import ctypes
 
 import pytest
+import torch
 
 from tests import gpu_util as G
 
 pytestmark = pytest.mark.gpu
-
-REL_TOL = 1e-9  # the loss tolerance of the other loss tests
 
 
 def test_noalloc_loss_matches_allocating_call_twice_in_a_row():
@@ -31,12 +32,20 @@ def test_noalloc_loss_matches_allocating_call_twice_in_a_row():
         for m, seed in ((L.NOALLOC_MAX_SAMPLES, 9), (1000, 4)):
             want = ctx.eval_loss(2, 5, seed, m)
             got = ctx.eval_loss_noalloc(2, 5, seed, m)
-            assert abs(got - want) <= REL_TOL * abs(want), (m, got, want)
+            assert got == want, (m, got, want)
+        # no device memory is taken by further calls
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        for m, seed in ((L.NOALLOC_MAX_SAMPLES, 11), (77, 12), (L.NOALLOC_MAX_SAMPLES, 13)):
+            ctx.eval_loss_noalloc(2, 5, seed, m)
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0, (free0, free1)
         # first order, BF16 tables
         ctx.init_embeddings(1, 32, L.DTYPE_BF16, seed=2)
         ctx.train_steps(1, 32, 5, 10_000, 5, batch=128)
         want = ctx.eval_loss(1, 5, 7, 4096)
-        assert abs(ctx.eval_loss_noalloc(1, 5, 7, 4096) - want) <= REL_TOL * abs(want)
+        assert ctx.eval_loss_noalloc(1, 5, 7, 4096) == want
         # sizes outside the fixed array are refused before any work
         out = ctypes.c_double()
         for m in (0, L.NOALLOC_MAX_SAMPLES + 1):
@@ -45,6 +54,6 @@ def test_noalloc_loss_matches_allocating_call_twice_in_a_row():
             assert "fixed scratch" in ctx.last_error()
         # the context is still usable
         want = ctx.eval_loss(2, 5, 3, 2048)
-        assert abs(ctx.eval_loss_noalloc(2, 5, 3, 2048) - want) <= REL_TOL * abs(want)
+        assert ctx.eval_loss_noalloc(2, 5, 3, 2048) == want
     finally:
         ctx.close()
