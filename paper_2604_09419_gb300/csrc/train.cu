@@ -39,10 +39,10 @@
 // would give it.  Two schedules run the same per-sample and per-segment code:
 //   LINE_MODE_BATCHED     two launches per batch, chained with programmatic
 //                         dependent launch;
-//   LINE_MODE_PERSISTENT  one cooperative launch per chunk: every warp walks
-//                         a fixed list of work items (batch b's samples, then
-//                         b's shared segments, then b+1's ...) and waits,
-//                         with bounded spins, only on the items it depends on.
+//   LINE_MODE_PERSISTENT  one cooperative launch per chunk: resident CTAs
+//                         loop over the chunk's batches, rows staged in
+//                         shared memory by bulk copies, a grid-wide barrier
+//                         after each batch's gather and after its apply.
 #include <algorithm>
 #include <atomic>
 #include <cstdio>
@@ -51,6 +51,7 @@
 
 #include <cooperative_groups.h>
 
+#include "bulk.cuh"
 #include "line_internal.cuh"
 #include "rows.cuh"
 #include "scan.cuh"
@@ -76,6 +77,24 @@ constexpr uint32_t kSlotMask = (1u << kSlotBits) - 1u;
 // slot_info.x: sorted position, bit 31 set for a singleton segment.
 constexpr uint32_t kSingleBit = 1u << 31;
 
+// Fibonacci hashing: spreads the hot (low) row ids of skewed graphs.  The
+// multiplier is odd, so hrow is a bijection of 32-bit words (inverse
+// 0x0E8B2F51); within a batch items are ordered by (hrow(row), index), which
+// puts them bucket by bucket (bucket = top 8 bits) and each row's entries
+// together in index order.
+__device__ __forceinline__ uint32_t hrow(uint32_t row) { return row * 0x9E3779B1u; }
+__device__ __forceinline__ uint32_t unhrow(uint32_t h) { return h * 0x0E8B2F51u; }
+__device__ __forceinline__ uint32_t bucket_of(uint32_t row) { return hrow(row) >> 24; }
+
+// Rows a batch touches, as a bitmap of 2^kDepLog bits indexed by the top bits
+// of hrow(row id) (row ids: U rows 0..n-1, C rows n..2n-1 in second order).
+// A row whose bit is clear in batch b's map is not written by batch b, so it
+// may be read for batch b+1 while batch b is still running (a false positive
+// only delays a read).
+constexpr int kDepLog = 18;
+constexpr uint32_t kDepWords = 1u << (kDepLog - 5);
+__device__ __forceinline__ uint32_t dep_bit(uint32_t rowid) { return hrow(rowid) >> (32 - kDepLog); }
+
 // ---------------------------------------------------------------------------
 // Kernel parameters shared by the data-phase kernels.
 // ---------------------------------------------------------------------------
@@ -95,6 +114,7 @@ struct DataParams {
     const uint32_t* lcount;  // [n_batches]
     uint32_t lcap;
     float* slab;             // [chunk samples * (K+2)][D], by position
+    const uint32_t* depmap;  // [n_batches][kDepWords] rows each batch touches (bit dep_bit(row id))
     uint64_t t_chunk;        // global index of the chunk's first sample
     const uint64_t* t_chunk_dev;  // when set, the same read from device memory (graph replays)
     int64_t chunk_samples;
@@ -105,13 +125,8 @@ struct DataParams {
     float lambda, alpha_neg;
     uint32_t* status;
     // persistent schedule
-    const int32_t* slot_prev;   // [chunk samples][K+2]: segment of the same row in the previous batch, or -1
-    const uint32_t* nseg;       // [n_batches] segments of each batch
-    uint32_t* batch_applied;    // [n_batches] segments of each batch whose row is written
-    uint32_t* seg_done;         // [positions] generation flags: the segment's row is written
-    uint32_t* arrive;           // [positions] contributions of a shared segment in the slab
-    const uint64_t* item_base;  // [n_batches + 1] first work item of each batch
-    uint32_t gen;
+    uint32_t* gbar;           // grid barrier: {arrivals, completed rounds}, zero at launch
+    int slots;                // shared-memory row slots per warp (1 or 2)
     int64_t spin_limit;
     uint32_t* abort_word;
 };
@@ -131,7 +146,7 @@ __device__ __forceinline__ T rec_entry(uint32_t gm, T held, const T* row, int id
 }
 
 // ---------------------------------------------------------------------------
-// Per-sample work.  Returns false when a bounded wait ran out (persistent).
+// Per-sample work.
 // ctx_stage: this warp's shared staging area, (K+1) x 32 lanes x E floats.
 // ---------------------------------------------------------------------------
 // Register-resident gather body for K + 1 <= 8: the K+1 context rows stay in
@@ -212,37 +227,15 @@ __device__ __forceinline__ void sample_body_reg(const DataParams& p, int lig, bo
     }
 }
 
-template <int D, int DT, bool PERSIST, bool PDL = false>
-__device__ __forceinline__ bool sample_item(const DataParams& p, int b, int64_t s_local, int lig, int lane,
-                                            bool active, float eta, uint64_t t0, float* ctx_stage) {
+// Staged gather body (any K): the K+1 context rows are staged in shared
+// memory (ctx_stage: (K+1) x 32 lanes x E floats), the dots reduced JB at a
+// time.  Same arithmetic, in the same order, as the register body.
+template <int D, int DT>
+__device__ __forceinline__ void sample_body_staged(const DataParams& p, int lig, int lane, bool active, float eta,
+                                                   uint64_t t0, uint32_t gm, int32_t r0, uint2 i0, const int32_t* rec,
+                                                   const uint2* info, float* ctx_stage) {
     using G = Geom<D, DT>;
     constexpr int CH = G::E <= 4 ? 8 : 4;  // context rows in flight per lane
-    const int R = p.K + 2;
-    const int64_t sbase = (active ? s_local : 0) * R;
-    const int32_t* rec = p.rec + sbase;
-    const uint2* info = p.slot_info + sbase;
-    const uint32_t gm = group_mask<G::L>(lane / G::L);
-    const int32_t r0 = (active && lig < R) ? rec[lig] : 0;
-    const uint2 i0 = (active && lig < R) ? info[lig] : make_uint2(0u, 0u);
-    if constexpr (PDL) pdl_wait();  // the tables' rows: written by the previous kernel
-    bool ok = true;
-    if constexpr (PERSIST) {
-        // rows written by an earlier segment of this chunk: wait for it
-        if (active) {
-            for (int k = lig; k < R; k += G::L) {
-                const int32_t pv = p.slot_prev[sbase + k];
-                if (pv >= 0 && ok) ok = wait_geq(p.seg_done + pv, p.gen, p.spin_limit, p.abort_word);
-            }
-        }
-        __syncwarp(gm);
-        if (!__all_sync(gm, ok)) return false;
-    }
-    if constexpr (!PERSIST && G::E <= 4) {
-        if (p.K < 8) {
-            sample_body_reg<D, DT>(p, lig, active, eta, t0, gm, r0, i0, rec, info);
-            return true;
-        }
-    }
     const int32_t u = __shfl_sync(gm, r0, 0, G::L);
     float xu[G::E];
     load_row<D, DT>(p.U, u, lig, xu);
@@ -342,47 +335,41 @@ __device__ __forceinline__ bool sample_item(const DataParams& p, int b, int64_t 
             for (int q = 0; q < G::E / 4; ++q) st_cg(dst + q, make_float4(du[4 * q], du[4 * q + 1], du[4 * q + 2], du[4 * q + 3]));
         }
     }
-    if constexpr (PERSIST) {
-        // publish: the group's stores are ordered before the release
-        // operations by the warp barrier; lane k signals slot k, and the
-        // batch's applied-segment count grows by the singletons written
-        __syncwarp(gm);
-        uint32_t singles = 0;
-        if (active) {
-            for (int k = lig; k < R; k += G::L) {
-                const uint2 inf = info[k];
-                if (inf.x & kSingleBit) {
-                    st_release(p.seg_done + inf.y, p.gen);
-                    ++singles;
-                } else {
-                    red_release_add(p.arrive + inf.y, 1u);
-                }
-            }
+}
+
+template <int D, int DT, bool PDL = false>
+__device__ __forceinline__ void sample_item(const DataParams& p, int64_t s_local, int lig, int lane, bool active,
+                                            float eta, uint64_t t0, float* ctx_stage) {
+    using G = Geom<D, DT>;
+    const int R = p.K + 2;
+    const int64_t sbase = (active ? s_local : 0) * R;
+    const int32_t* rec = p.rec + sbase;
+    const uint2* info = p.slot_info + sbase;
+    const uint32_t gm = group_mask<G::L>(lane / G::L);
+    const int32_t r0 = (active && lig < R) ? rec[lig] : 0;
+    const uint2 i0 = (active && lig < R) ? info[lig] : make_uint2(0u, 0u);
+    if constexpr (PDL) pdl_wait();  // the tables' rows: written by the previous kernel
+    if constexpr (G::E <= 4) {
+        if (p.K < 8) {
+            sample_body_reg<D, DT>(p, lig, active, eta, t0, gm, r0, i0, rec, info);
+            return;
         }
-#pragma unroll
-        for (int o = G::L / 2; o >= 1; o >>= 1) singles += __shfl_xor_sync(gm, singles, o, G::L);
-        if (active && lig == 0 && singles) red_release_add(p.batch_applied + b, singles);
     }
-    return ok;
+    sample_body_staged<D, DT>(p, lig, lane, active, eta, t0, gm, r0, i0, rec, info, ctx_stage);
 }
 
 // ---------------------------------------------------------------------------
 // Per shared segment: fixed-order sum of its contiguous slab entries and the
-// write-back.  Returns false when a bounded wait ran out (persistent).
+// write-back.
 // ---------------------------------------------------------------------------
-template <int D, int DT, bool PERSIST>
-__device__ __forceinline__ bool segment_item(const DataParams& p, uint4 d, int lig, bool active, float eta,
+template <int D, int DT>
+__device__ __forceinline__ void segment_item(const DataParams& p, uint4 d, int lig, bool active, float eta,
                                              uint64_t t0) {
     using G = Geom<D, DT>;
     constexpr int PF = G::E <= 4 ? 8 : 4;  // slab entries in flight per lane
-    if (!active) return true;
+    if (!active) return;
     // d = {first position, length | long bit, row, pair count}
     const uint32_t len = d.y & ~kLongBit;
-    if constexpr (PERSIST) {
-        // all contributions written (and, through them, every read of the
-        // row's batch-start value and the row's previous write done)
-        if (!wait_geq(p.arrive + d.x, len, p.spin_limit, p.abort_word)) return false;
-    }
     const uint32_t rowid = d.z & ((1u << p.row_bits) - 1u);
     const bool is_c = p.order == 2 && rowid >= (uint32_t)p.n_nodes;
     void* table = is_c ? p.C : p.U;
@@ -428,7 +415,6 @@ __device__ __forceinline__ bool segment_item(const DataParams& p, uint4 d, int l
 #pragma unroll
     for (int e = 0; e < G::E; ++e) x[e] = fmaf(-decay, x[e], x[e]) + acc[e];
     store_row<D, DT>(table, row, lig, x, p.seed, t0, is_c ? 1u : 0u);
-    return true;
 }
 
 // Warps of an apply block: 16 when one order trains alone (a hub row's
@@ -534,8 +520,7 @@ __global__ void __launch_bounds__(kGatherWarps * 32, 7) k_gather(DataParams p, i
     const int64_t s_local = s_begin + ((int64_t)blockIdx.x * (blockDim.x >> 5) + warp) * G::GPW + grp;
     float* stage = smem + (size_t)warp * (p.K + 1) * 32 * G::E;
     const uint64_t tc = p.t_chunk_dev ? *p.t_chunk_dev : p.t_chunk;
-    sample_item<D, DT, false, PDL>(p, b, s_local, lig, lane, s_local < s_end, p.eta[b], tc + (uint64_t)s_begin,
-                                   stage);
+    sample_item<D, DT, PDL>(p, s_local, lig, lane, s_local < s_end, p.eta[b], tc + (uint64_t)s_begin, stage);
 }
 
 // Blocks [0, g_long) take the batch's long shared segments, one per CTA; the
@@ -570,86 +555,436 @@ __global__ void __launch_bounds__(NW * 32) k_apply(DataParams p, int b, int g_lo
     for (int64_t m = m0; m < n_m; m += groups) {
         if (m != m0) d = md[m];
         if (d.y & kLongBit) continue;
-        segment_item<D, DT, false>(p, d, lig, true, eta, t0);
+        segment_item<D, DT>(p, d, lig, true, eta, t0);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Persistent schedule: one cooperative launch per chunk.  Work items in a
-// fixed order - batch 0's sample items, batch 0's shared-segment items, batch
-// 1's sample items, ... - are dealt round robin to the warps; every warp walks
-// its items in increasing order.  An item waits only on items earlier in that
-// order, so the earliest unfinished item can always run (all warps are
-// resident): the schedule cannot deadlock, and every wait is bounded anyway.
-//   sample item of batch b: for a row also touched by batch b-1 it waits for
-//     that segment (written by a sample item when it was a singleton, by a
-//     segment item otherwise); batches b-2 and b-3 must be fully written.  It
-//     then writes its singleton rows and publishes them, and counts its
-//     shared contributions in.
-//   segment item: waits until all contributions of its segment are in, sums
-//     them, writes the row and publishes it.
+// Persistent schedule (LINE_MODE_PERSISTENT): one cooperative launch per
+// chunk; one CTA of W warps per SM stays resident for all the chunk's
+// batches.  For batch b:
+//   gather  warp u takes the samples of units u, u + NW, ... (NW warps in
+//           all; a unit is one sample per lane group).  A sample's K+2 rows
+//           (U[u], then the context rows) are brought into the warp's
+//           shared-memory slot by bulk copies (cp.async.bulk) that complete
+//           on the slot's mbarrier; with two slots the next unit's copies run
+//           while one unit is computed.  The arithmetic is the batched
+//           gather's, reading the rows from shared memory; singleton rows
+//           are written back, shared rows' contributions go to the slab.
+//   barrier (grid-wide)
+//   apply   each warp first starts the copies of its first unit of batch b+1
+//           for the rows that batch b does not touch (b's row map: those rows
+//           are not written in batch b); then every CTA applies some of
+//           batch b's long shared segments (all its warps on one segment)
+//           and every lane group some of its short ones.
+//   barrier
+// The rows of batch b+1 that batch b touches are copied after the second
+// barrier.  Every wait is bounded: a barrier or a copy that does not finish
+// within spin_limit polls records DEV_ERR_TIMEOUT, raises the abort word,
+// waits (bounded) for the warp's own copies in flight, and returns.
 // ---------------------------------------------------------------------------
-constexpr int kPersistThreads = 256;  // 8 warps per block
-constexpr int kPersistMinBlocks = 3;
+constexpr int kPersistMaxWarps = 16;
+constexpr int kPersistDefaultWarps = 16;
 
 __device__ __forceinline__ void fail_abort(const DataParams& p) {
     atomicOr(p.status, DEV_ERR_TIMEOUT);
     atomicExch(p.abort_word, 1u);
 }
 
-__device__ __forceinline__ bool batch_applied_ok(const DataParams& p, int bb) {
-    if (bb < 0) return true;
-    return wait_geq(p.batch_applied + bb, p.nseg[bb], p.spin_limit, p.abort_word);
+// Grid-wide barrier: round r completes when all CTAs have arrived r+1 times
+// (gbar[0] counts arrivals; the last arriver publishes r+1 in gbar[1]).
+// Every thread's earlier global writes are visible to every CTA after it.
+// Returns false when the wait ran out or another CTA aborted.
+__device__ __forceinline__ bool grid_barrier(const DataParams& p, uint32_t r, uint32_t* s_flag) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        const uint32_t old = atom_add_acq_rel(p.gbar, 1u);
+        if (old == (r + 1u) * gridDim.x - 1u) {
+            st_release(p.gbar + 1, r + 1u);
+        } else {
+            int64_t it = 0;
+            while (ld_acquire(p.gbar + 1) < r + 1u) {
+                if (++it > p.spin_limit || *(volatile const uint32_t*)p.abort_word) {
+                    ok = false;
+                    break;
+                }
+                if (it > 64) __nanosleep(32);
+            }
+        }
+        if (!ok) fail_abort(p);
+        *s_flag = ok ? 1u : 0u;
+    }
+    __syncthreads();
+    return *s_flag != 0u;
+}
+
+// One lane group's sample from its staged rows (slot: row 0 = U[u], rows
+// 1..K+1 = the context rows, D values each in the table's type).  The
+// arithmetic is sample_body_staged's, in the same order.
+template <int D, int DT>
+__device__ __forceinline__ void slot_row(const unsigned char* set, int j, int lig, float (&v)[Geom<D, DT>::E]) {
+    using G = Geom<D, DT>;
+    if constexpr (DT == LINE_DTYPE_F32) {
+        const float4* q = reinterpret_cast<const float4*>(set + (size_t)j * D * 4 + (size_t)lig * G::E * 4);
+#pragma unroll
+        for (int k = 0; k < G::NV; ++k) {
+            const float4 a = q[k];
+            v[4 * k] = a.x;
+            v[4 * k + 1] = a.y;
+            v[4 * k + 2] = a.z;
+            v[4 * k + 3] = a.w;
+        }
+    } else {
+        const uint2* q = reinterpret_cast<const uint2*>(set + (size_t)j * D * 2 + (size_t)lig * G::E * 2);
+#pragma unroll
+        for (int k = 0; k < G::NV; ++k) {
+            const uint2 a = q[k];
+            v[4 * k] = __uint_as_float(a.x << 16);
+            v[4 * k + 1] = __uint_as_float(a.x & 0xFFFF0000u);
+            v[4 * k + 2] = __uint_as_float(a.y << 16);
+            v[4 * k + 3] = __uint_as_float(a.y & 0xFFFF0000u);
+        }
+    }
 }
 
 template <int D, int DT>
-__global__ void __launch_bounds__(kPersistThreads, kPersistMinBlocks) k_persistent(DataParams p) {
+__device__ __forceinline__ void sample_body_slot(const DataParams& p, int lig, bool active, float eta, uint64_t t0,
+                                                 uint32_t gm, int32_t r0, uint2 i0, const int32_t* rec,
+                                                 const uint2* info, const unsigned char* set) {
     using G = Geom<D, DT>;
-    extern __shared__ float4 smem4[];
-    float* smem = reinterpret_cast<float*>(smem4);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int grp = lane / G::L, lig = lane % G::L;
-    const int wpb = blockDim.x >> 5;
-    float* stage = smem + (size_t)warp * (p.K + 1) * 32 * G::E;
-    const uint64_t W = (uint64_t)gridDim.x * wpb;
-    const uint64_t total = p.item_base[p.n_batches];
-    int b = 0, checked_b = -1;
-    for (uint64_t t = (uint64_t)blockIdx.x * wpb + warp; t < total; t += W) {
-        while (t >= p.item_base[b + 1]) ++b;
-        if (*(volatile uint32_t*)p.abort_word) return;
-        const uint64_t local = t - p.item_base[b];
-        const int64_t s_begin = (int64_t)b * p.batch;
-        const int64_t nb = min((int64_t)p.batch, p.chunk_samples - s_begin);
-        const uint64_t nA = (uint64_t)((nb + G::GPW - 1) / G::GPW);
-        const uint64_t t0 = p.t_chunk + (uint64_t)s_begin;
-        const float eta = p.eta[b];
-        bool ok = true;
-        if (local < nA) {
-            // rows last written in batch b-1 are awaited per row; batches
-            // b-2 and b-3 must be complete (by induction, so is every earlier
-            // batch of the chunk)
-            if (checked_b != b) {
-                ok = batch_applied_ok(p, b - 2) && batch_applied_ok(p, b - 3);
-                checked_b = b;
-            }
-            if (__all_sync(0xFFFFFFFFu, ok)) {
-                const int64_t s_local = s_begin + (int64_t)local * G::GPW + grp;
-                ok = sample_item<D, DT, true>(p, b, s_local, lig, lane, s_local < s_begin + nb, eta, t0, stage);
-            }
-        } else {
-            const uint32_t m = (uint32_t)((local - nA) * G::GPW) + grp;
-            const bool active = m < p.mcount[b];
-            const uint4 d = active ? p.mdesc[(size_t)b * p.mcap + m] : make_uint4(0u, 0u, 0u, 0u);
-            ok = segment_item<D, DT, true>(p, d, lig, active, eta, t0);
-            __syncwarp();
-            if (ok && active && lig == 0) {
-                st_release(p.seg_done + d.x, p.gen);
-                red_release_add(p.batch_applied + b, 1u);
+    constexpr int JB = 8;
+    const int32_t u = __shfl_sync(gm, r0, 0, G::L);
+    float xu[G::E];
+    slot_row<D, DT>(set, 0, lig, xu);
+    const uint32_t ctx_table = p.order == 2 ? 1u : 0u;
+    const float etalam = eta * p.lambda;
+    float du[G::E];
+#pragma unroll
+    for (int e = 0; e < G::E; ++e) du[e] = 0.0f;
+    for (int j0 = 0; j0 <= p.K; j0 += JB) {
+        float sj[JB];
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj) {
+            sj[jj] = 0.0f;
+            if (j0 + jj <= p.K) {
+                float c[G::E];
+                slot_row<D, DT>(set, 1 + j0 + jj, lig, c);
+#pragma unroll
+                for (int e = 0; e < G::E; ++e) sj[jj] = fmaf(xu[e], c[e], sj[jj]);
             }
         }
-        if (!__all_sync(0xFFFFFFFFu, ok)) {
+#pragma unroll
+        for (int o = G::L / 2; o >= 1; o >>= 1)
+#pragma unroll
+            for (int jj = 0; jj < JB; ++jj) sj[jj] += __shfl_xor_sync(0xFFFFFFFFu, sj[jj], o);
+#pragma unroll
+        for (int jj = 0; jj < JB; ++jj) {
+            const int j = j0 + jj;
+            if (j > p.K) break;
+            float c[G::E];
+            slot_row<D, DT>(set, 1 + j, lig, c);
+            const float sig = 1.0f / (1.0f + expf(-sj[jj]));
+            const float g = j == 0 ? eta * (1.0f - sig) : -eta * p.alpha_neg * sig;
+#pragma unroll
+            for (int e = 0; e < G::E; ++e) du[e] = fmaf(g, c[e], du[e]);
+            const uint2 inf = rec_entry<G::L>(gm, i0, info, 1 + j, active);
+            const int32_t y = rec_entry<G::L>(gm, r0, rec, 1 + j, active);
+            if (active) {
+                if (inf.x & kSingleBit) {
+                    const float decay = 1.0f * etalam;
+                    float x[G::E];
+#pragma unroll
+                    for (int e = 0; e < G::E; ++e) x[e] = fmaf(-decay, c[e], c[e]) + g * xu[e];
+                    store_row<D, DT>(p.C, y, lig, x, p.seed, t0, ctx_table);
+                } else {
+                    float4* dst = reinterpret_cast<float4*>(p.slab + (int64_t)inf.x * D + lig * G::E);
+#pragma unroll
+                    for (int q = 0; q < G::E / 4; ++q)
+                        st_cg(dst + q, make_float4(g * xu[4 * q], g * xu[4 * q + 1], g * xu[4 * q + 2], g * xu[4 * q + 3]));
+                }
+            }
+        }
+    }
+    const uint2 inf0 = shfl_w(gm, i0, 0, G::L);
+    if (active) {
+        if (inf0.x & kSingleBit) {
+            const float decay = (float)(p.K + 1) * etalam;
+#pragma unroll
+            for (int e = 0; e < G::E; ++e) xu[e] = fmaf(-decay, xu[e], xu[e]) + du[e];
+            store_row<D, DT>(p.U, u, lig, xu, p.seed, t0, 0u);
+        } else {
+            float4* dst = reinterpret_cast<float4*>(p.slab + (int64_t)inf0.x * D + lig * G::E);
+#pragma unroll
+            for (int q = 0; q < G::E / 4; ++q) st_cg(dst + q, make_float4(du[4 * q], du[4 * q + 1], du[4 * q + 2], du[4 * q + 3]));
+        }
+    }
+}
+
+// Starts the bulk copies of rows j (bit j of `want`, j < K+2) of a lane
+// group's sample into its row set, completing on `bar`.  arrive: this is the
+// group's last issue for the slot's current phase (an arrival, with the
+// bytes); otherwise only the bytes are announced.  Row j of the sample is
+// U[rec[0]] for j = 0, Ctx[rec[j]] otherwise.
+template <int D, int DT>
+__device__ __forceinline__ void issue_rows(const DataParams& p, const int32_t* rec, int lig, uint32_t gm, int R,
+                                           uint64_t want, bool arrive, unsigned char* set, uint64_t* bar) {
+    using G = Geom<D, DT>;
+    constexpr uint32_t kRowBytes = D * (DT == LINE_DTYPE_F32 ? 4 : 2);
+    const uint32_t bytes = (uint32_t)__popcll(want) * kRowBytes;
+    if (lig == 0) {
+        if (arrive) mbar_arrive_expect_tx(bar, bytes);
+        else if (bytes) mbar_expect_tx(bar, bytes);
+    }
+    __syncwarp(gm);
+    for (int j = lig; j < R; j += G::L) {
+        if ((want >> j) & 1ull) {
+            const int32_t row = rec[j];
+            const void* table = j == 0 ? p.U : p.C;
+            const unsigned char* src = reinterpret_cast<const unsigned char*>(table) + (size_t)row * kRowBytes;
+            bulk_load(set + (size_t)j * kRowBytes, src, kRowBytes, bar);
+        }
+    }
+}
+
+// A long shared segment summed by all W warps of the CTA (runtime W): warp w
+// sums chunks w, w+W, ... (entry order within a chunk); warp 0 adds the
+// chunk partials in chunk order, as segment_item does.  part: W x D floats.
+template <int D, int DT>
+__device__ __forceinline__ void long_segment_rt(const DataParams& p, uint4 d, float eta, uint64_t t0, float* part, int W) {
+    using G = Geom<D, DT>;
+    constexpr int PF = G::E <= 4 ? 8 : 4;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool mine = lane < G::L;
+    const int lig = lane;
+    const uint32_t len = d.y & ~kLongBit;
+    const uint32_t n_chunks = (len + kChunk - 1) / kChunk;
+    const uint32_t rowid = d.z & ((1u << p.row_bits) - 1u);
+    const bool is_c = p.order == 2 && rowid >= (uint32_t)p.n_nodes;
+    void* table = is_c ? p.C : p.U;
+    const int64_t row = is_c ? (int64_t)rowid - p.n_nodes : (int64_t)rowid;
+    float x[G::E];
+    if (warp == 0 && mine) load_row<D, DT>(table, row, lig, x);
+    float acc[G::E];
+#pragma unroll
+    for (int e = 0; e < G::E; ++e) acc[e] = 0.0f;
+    const float* base = p.slab + (int64_t)d.x * D + (mine ? lig : 0) * G::E;
+    for (uint32_t r0 = 0; r0 < n_chunks; r0 += (uint32_t)W) {
+        const uint32_t c = r0 + (uint32_t)warp;
+        if (mine && c < n_chunks) {
+            float pt[G::E];
+#pragma unroll
+            for (int e = 0; e < G::E; ++e) pt[e] = 0.0f;
+            const uint32_t c0 = c * kChunk;
+#pragma unroll
+            for (uint32_t k0 = 0; k0 < kChunk; k0 += PF) {
+                float4 buf[PF][G::E / 4];
+#pragma unroll
+                for (int kk = 0; kk < PF; ++kk)
+                    if (c0 + k0 + kk < len)
+#pragma unroll
+                        for (int q = 0; q < G::E / 4; ++q)
+                            buf[kk][q] = ld_cg(reinterpret_cast<const float4*>(base + (int64_t)(c0 + k0 + kk) * D) + q);
+#pragma unroll
+                for (int kk = 0; kk < PF; ++kk)
+                    if (c0 + k0 + kk < len)
+#pragma unroll
+                        for (int q = 0; q < G::E / 4; ++q) {
+                            pt[4 * q] += buf[kk][q].x;
+                            pt[4 * q + 1] += buf[kk][q].y;
+                            pt[4 * q + 2] += buf[kk][q].z;
+                            pt[4 * q + 3] += buf[kk][q].w;
+                        }
+            }
+#pragma unroll
+            for (int e = 0; e < G::E; ++e) part[warp * D + lig * G::E + e] = pt[e];
+        }
+        __syncthreads();
+        if (warp == 0 && mine) {
+            const uint32_t nr = min((uint32_t)W, n_chunks - r0);
+            for (uint32_t w = 0; w < nr; ++w)
+#pragma unroll
+                for (int e = 0; e < G::E; ++e) acc[e] += part[w * D + lig * G::E + e];
+        }
+        __syncthreads();
+    }
+    if (warp == 0 && mine) {
+        const float decay = (float)d.w * (eta * p.lambda);
+#pragma unroll
+        for (int e = 0; e < G::E; ++e) x[e] = fmaf(-decay, x[e], x[e]) + acc[e];
+        store_row<D, DT>(table, row, lig, x, p.seed, t0, is_c ? 1u : 0u);
+    }
+}
+
+// Row bytes of one lane group's sample set, rounded up to 128.
+__host__ __device__ inline size_t persist_set_bytes(int dim, int dtype, int K) {
+    return (((size_t)(K + 2) * dim * (dtype == LINE_DTYPE_F32 ? 4 : 2)) + 127) & ~(size_t)127;
+}
+
+// Dynamic shared memory of a W-warp CTA: the warps' row slots, the long
+// segments' partials (W x D floats) and two mbarriers per warp.
+__host__ __device__ inline size_t persist_smem_bytes(int dim, int dtype, int K, int W, int slots, int gpw) {
+    return (size_t)W * slots * gpw * persist_set_bytes(dim, dtype, K) + (size_t)W * dim * sizeof(float) +
+           (size_t)W * 2 * sizeof(uint64_t);
+}
+
+template <int D, int DT>
+__global__ void __launch_bounds__(kPersistMaxWarps * 32, 1) k_persistent(DataParams p) {
+    using G = Geom<D, DT>;
+    extern __shared__ __align__(128) unsigned char psm[];
+    __shared__ uint32_t s_flag;
+    const int W = (int)(blockDim.x >> 5);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int grp = lane / G::L, lig = lane % G::L;
+    const uint32_t gm = group_mask<G::L>(grp);
+    const int R = p.K + 2;
+    const size_t set_bytes = persist_set_bytes(D, DT, p.K);
+    const int slots = p.slots;
+    unsigned char* wslots = psm + (size_t)warp * slots * G::GPW * set_bytes;
+    float* part = reinterpret_cast<float*>(psm + (size_t)W * slots * G::GPW * set_bytes);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(part + (size_t)W * D) + 2 * warp;
+    if (lane == 0) {
+        mbar_init(bars, G::GPW);  // one arrival per lane group and phase
+        mbar_init(bars + 1, G::GPW);
+        mbar_init_fence();
+    }
+    __syncwarp();
+    const int64_t NW = (int64_t)gridDim.x * W;                 // warps in all
+    const int64_t uwarp = (int64_t)blockIdx.x * W + warp;      // this warp
+    uint32_t par0 = 0, par1 = 0;                               // phase parity of each slot
+    bool pending0 = false, pending1 = false;                   // copies issued, not yet waited for
+    uint64_t pre_want = 0;                                     // rows of unit 0 already requested (prefetch)
+    bool prefetched = false;
+    uint32_t round = 0;
+    bool ok = true;
+    const uint64_t all_rows = R >= 64 ? ~0ull : ((1ull << R) - 1ull);
+    for (int b = 0; b < p.n_batches && ok; ++b) {
+        const int64_t s_begin = (int64_t)b * p.batch;
+        const int64_t nb = min((int64_t)p.batch, p.chunk_samples - s_begin);
+        const int64_t units = (nb + G::GPW - 1) / G::GPW;
+        const uint64_t t0 = p.t_chunk + (uint64_t)s_begin;
+        const float eta = p.eta[b];
+        const int64_t n_mine = uwarp < units ? (units - 1 - uwarp) / NW + 1 : 0;
+        // ---- gather of batch b
+        // copies of the first two units (unit 0's prefetched rows are in flight)
+        for (int k = 0; k < 2 && k < n_mine; ++k) {
+            const int64_t s_local = s_begin + (uwarp + k * NW) * G::GPW + grp;
+            const bool active = s_local < s_begin + nb;
+            const int32_t* rec = p.rec + (active ? s_local : 0) * R;
+            uint64_t want = active ? all_rows : 0ull;
+            if (k == 0 && prefetched) want &= ~pre_want;
+            fence_proxy_async_global();
+            issue_rows<D, DT>(p, rec, lig, gm, R, want, true, wslots + (size_t)k * G::GPW * set_bytes + grp * set_bytes,
+                              bars + k);
+            if (k == 0) pending0 = true;
+            else pending1 = true;
+        }
+        prefetched = false;
+        for (int64_t k = 0; k < n_mine && ok; ++k) {
+            const int sl = (int)(k & 1);
+            const int64_t s_local = s_begin + (uwarp + k * NW) * G::GPW + grp;
+            const bool active = s_local < s_begin + nb;
+            // wait for the unit's rows
+            uint64_t* bar = bars + sl;
+            const uint32_t par = sl ? par1 : par0;
+            int64_t it = 0;
+            while (!mbar_try_wait(bar, par)) {
+                if (++it > p.spin_limit || *(volatile const uint32_t*)p.abort_word) {
+                    ok = false;
+                    break;
+                }
+            }
+            ok = __all_sync(0xFFFFFFFFu, ok);
+            if (!ok) break;
+            if (sl) {
+                par1 ^= 1u;
+                pending1 = false;
+            } else {
+                par0 ^= 1u;
+                pending0 = false;
+            }
+            const unsigned char* set = wslots + (size_t)sl * G::GPW * set_bytes + grp * set_bytes;
+            const int64_t sbase = (active ? s_local : 0) * R;
+            const int32_t* rec = p.rec + sbase;
+            const uint2* info = p.slot_info + sbase;
+            const int32_t r0 = (active && lig < R) ? rec[lig] : 0;
+            const uint2 i0 = (active && lig < R) ? info[lig] : make_uint2(0u, 0u);
+            sample_body_slot<D, DT>(p, lig, active, eta, t0, gm, r0, i0, rec, info, set);
+            // the slot's rows are read: it may be refilled by bulk copies
+            fence_proxy_async_smem();
+            __syncwarp();
+            if (k + 2 < n_mine) {
+                const int64_t s2 = s_begin + (uwarp + (k + 2) * NW) * G::GPW + grp;
+                const bool act2 = s2 < s_begin + nb;
+                issue_rows<D, DT>(p, p.rec + (act2 ? s2 : 0) * R, lig, gm, R, act2 ? all_rows : 0ull, true,
+                                  wslots + (size_t)sl * G::GPW * set_bytes + grp * set_bytes, bar);
+                if (sl) pending1 = true;
+                else pending0 = true;
+            }
+        }
+        if (!__all_sync(0xFFFFFFFFu, ok)) ok = false;
+        if (!ok) {
             if (lane == 0) fail_abort(p);
-            return;
+            break;
+        }
+        if (!grid_barrier(p, round++, &s_flag)) {
+            ok = false;
+            break;
+        }
+        // ---- apply of batch b; first the prefetch of batch b+1's rows that
+        // batch b does not touch
+        if (b + 1 < p.n_batches) {
+            const int64_t s1_begin = (int64_t)(b + 1) * p.batch;
+            const int64_t nb1 = min((int64_t)p.batch, p.chunk_samples - s1_begin);
+            const int64_t units1 = (nb1 + G::GPW - 1) / G::GPW;
+            if (uwarp < units1) {
+                const int64_t s_local = s1_begin + uwarp * G::GPW + grp;
+                const bool active = s_local < s1_begin + nb1;
+                const int32_t* rec = p.rec + (active ? s_local : 0) * R;
+                // rows of the group's sample that batch b does not touch
+                bool free_row = false;
+                if (active && lig < R) {
+                    const uint32_t rowid = (uint32_t)rec[lig] + (lig > 0 && p.order == 2 ? (uint32_t)p.n_nodes : 0u);
+                    const uint32_t db = dep_bit(rowid);
+                    free_row = !((__ldcg(p.depmap + (size_t)b * kDepWords + (db >> 5)) >> (db & 31u)) & 1u);
+                }
+                uint32_t fm = __ballot_sync(0xFFFFFFFFu, free_row);
+                fm = G::L == 32 ? fm : (fm >> (grp * G::L)) & ((1u << G::L) - 1u);
+                pre_want = (uint64_t)fm;  // rows >= L: copied after the barrier
+                fence_proxy_async_global();
+                issue_rows<D, DT>(p, rec, lig, gm, R, pre_want, false, wslots + grp * set_bytes, bars);
+                prefetched = true;
+                pending0 = true;
+            }
+        }
+        {
+            // long shared segments: one CTA each
+            const uint32_t n_long = p.lcount[b];
+            for (uint32_t l = blockIdx.x; l < n_long; l += gridDim.x)
+                long_segment_rt<D, DT>(p, p.ldesc[(size_t)b * p.lcap + l], eta, t0, part, W);
+            // short ones: one lane group each
+            const uint32_t n_m = p.mcount[b];
+            const uint4* md = p.mdesc + (size_t)b * p.mcap;
+            for (int64_t m = uwarp * G::GPW + grp; m < n_m; m += NW * G::GPW) {
+                const uint4 d = md[m];
+                if (d.y & kLongBit) continue;
+                segment_item<D, DT>(p, d, lig, true, eta, t0);
+            }
+        }
+        if (!grid_barrier(p, round++, &s_flag)) {
+            ok = false;
+            break;
+        }
+    }
+    if (!ok) {
+        // wait (bounded) for this warp's copies still in flight, then return
+        for (int sl = 0; sl < 2; ++sl) {
+            if (!(sl ? pending1 : pending0)) continue;
+            uint64_t* bar = bars + sl;
+            const uint32_t par = sl ? par1 : par0;
+            for (int64_t it = 0; it <= p.spin_limit && !mbar_try_wait(bar, par); ++it) {
+            }
         }
     }
 }
@@ -712,14 +1047,6 @@ __global__ void k_chunk_draws(PrepassParams p) {
 // ---------------------------------------------------------------------------
 constexpr int kBuckets = 256;            // bucket = 8-bit multiplicative hash of the row id
 
-// Fibonacci hashing: spreads the hot (low) row ids of skewed graphs.  The
-// multiplier is odd, so hrow is a bijection of 32-bit words (inverse
-// 0x0E8B2F51); within a batch items are ordered by (hrow(row), index), which
-// puts them bucket by bucket (bucket = top 8 bits) and each row's entries
-// together in index order.
-__device__ __forceinline__ uint32_t hrow(uint32_t row) { return row * 0x9E3779B1u; }
-__device__ __forceinline__ uint32_t unhrow(uint32_t h) { return h * 0x0E8B2F51u; }
-__device__ __forceinline__ uint32_t bucket_of(uint32_t row) { return hrow(row) >> 24; }
 constexpr int kBucketThreads = 1024;
 constexpr int kBucketWarps = kBucketThreads / 32;
 constexpr uint32_t kPartItems = 16384;   // items of a batch per bucketing CTA
@@ -744,9 +1071,7 @@ struct GroupParams {
     uint4* ldesc;
     uint32_t* lcount;
     uint32_t lcap;
-    uint32_t* nseg;       // persistent only (nullptr otherwise)
-    uint32_t* sorted_row; // persistent only: hrow(row id) by position
-    uint32_t* seghead;    // persistent only: first position of the position's segment
+    uint32_t* depmap;     // [n_batches][kDepWords] rows each batch touches (zeroed before), or null
 };
 
 __device__ __forceinline__ void batch_range(const GroupParams& q, int b, uint64_t* base, uint32_t* n) {
@@ -764,8 +1089,14 @@ __global__ void __launch_bounds__(kBucketThreads) k_bucket_count(GroupParams q) 
     uint32_t n;
     batch_range(q, b, &base, &n);
     const uint32_t lo = min(n, (uint32_t)part * kPartItems), hi = min(n, lo + kPartItems);
-    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x)
-        atomicAdd(&cnt[bucket_of((uint32_t)(q.items[base + i] >> 32))], 1u);
+    for (uint32_t i = lo + threadIdx.x; i < hi; i += blockDim.x) {
+        const uint32_t rowid = (uint32_t)(q.items[base + i] >> 32);
+        atomicAdd(&cnt[bucket_of(rowid)], 1u);
+        if (q.depmap) {
+            const uint32_t db = dep_bit(rowid);
+            atomicOr(q.depmap + (size_t)b * kDepWords + (db >> 5), 1u << (db & 31u));
+        }
+    }
     __syncthreads();
     if (threadIdx.x < kBuckets) q.gcnt[((size_t)b * q.parts + part) * kBuckets + threadIdx.x] = cnt[threadIdx.x];
 }
@@ -971,12 +1302,7 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort(GroupParams q) {
             cnt += slot == 0 ? q.K + 1 : 1u;
             const uint32_t pos = (uint32_t)(gpos + k);
             q.slot_info[(v >> kSlotBits) * q.R + slot] = make_uint2(pos | (len == 1 ? kSingleBit : 0u), head);
-            if (q.sorted_row) {
-                q.sorted_row[pos] = hrow(key);
-                q.seghead[pos] = head;
-            }
         }
-        if (q.nseg) atomicAdd(q.nseg + b, 1u);
         if (len > 1) {
             uint32_t flagged = len;
             if (len > kChunk) {
@@ -1137,13 +1463,8 @@ __device__ __forceinline__ void group_tail(const GroupParams& q, uint64_t* a, ui
                     const uint32_t slot = v & kSlotMask;
                     const uint32_t pos = (uint32_t)(gpos + i);
                     q.slot_info[(v >> kSlotBits) * q.R + slot] = make_uint2(pos | (len == 1 ? kSingleBit : 0u), hpos);
-                    if (q.sorted_row) {
-                        q.sorted_row[pos] = hk;
-                        q.seghead[pos] = hpos;
-                    }
                 }
                 if (is_head) {
-                    if (q.nseg) atomicAdd(q.nseg + b, 1u);
                     if (len > 1) {
                         // pair count of the segment: K + 1 for a source entry, 1 otherwise
                         uint32_t cnt = 0;
@@ -1224,6 +1545,10 @@ __global__ void __launch_bounds__(kGroupThreads) k_group_cluster(GroupParams q, 
                 const uint32_t hv = hrow((uint32_t)(it[k] >> 32));
                 const uint32_t pt = log_parts ? hv >> (32 - log_parts) : 0u;
                 atomicAdd(&s_cnt[pt][(hv >> sub_shift) & (kSub - 1)], 1u);
+                if (q.depmap) {
+                    const uint32_t db = hv >> (32 - kDepLog);
+                    atomicOr(q.depmap + (size_t)b * kDepWords + (db >> 5), 1u << (db & 31u));
+                }
             }
         }
     }
@@ -1306,32 +1631,6 @@ __global__ void __launch_bounds__(kGroupThreads) k_group_cluster(GroupParams q, 
     else group_tail(q, q.bucketed + base + qbase, nq, base, n, qbase, b, me, P, log_parts, sh);
 }
 
-// slot_prev[(s, slot)] = segment of the same row in the previous batch of the
-// chunk, or -1: binary search in that batch's bucket (sorted by row).
-__global__ void k_prev_lookup(GroupParams q, const int32_t* __restrict__ rec, uint32_t ctx_off,
-                              int32_t* __restrict__ slot_prev) {
-    const uint64_t total = (uint64_t)q.chunk_samples * q.R;
-    for (uint64_t it = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; it < total; it += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t s = (uint32_t)(it / q.R), slot = (uint32_t)(it - (uint64_t)s * q.R);
-        const int b = (int)(s / (uint32_t)q.batch);
-        int32_t pv = -1;
-        if (b > 0) {
-            const uint32_t row = slot == 0 ? (uint32_t)rec[(uint64_t)s * q.R] : (uint32_t)rec[it] + ctx_off;
-            const uint32_t d = bucket_of(row), hr = hrow(row);
-            const uint64_t pbase = (uint64_t)(b - 1) * (uint64_t)q.batch * q.R;
-            uint32_t lo = q.boff[(size_t)(b - 1) * (kBuckets + 1) + d], hi = q.boff[(size_t)(b - 1) * (kBuckets + 1) + d + 1];
-            const uint32_t end = hi;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (q.sorted_row[pbase + mid] < hr) lo = mid + 1;
-                else hi = mid;
-            }
-            if (lo < end && q.sorted_row[pbase + lo] == hr) pv = (int32_t)q.seghead[pbase + lo];
-        }
-        slot_prev[it] = pv;
-    }
-}
-
 // eta[b] = lr0 (schedule 0) or lr0 * max(1 - t0/T, floor) (schedule 1) for
 // the batch starting at global sample t0 = t_chunk + b * batch, in FP32:
 // 1 - t0/T as (T - t0) / T from the exact integer difference.
@@ -1346,20 +1645,6 @@ __global__ void k_batch_eta(int n_batches, uint64_t t_chunk, int64_t batch, floa
         if (f < floor_frac) f = floor_frac;
     }
     eta[b] = lr0 * f;
-}
-
-// item_base[b] = first work item of batch b (sample items, then shared-segment items).
-__global__ void k_item_base(const uint32_t* __restrict__ mcount, int n_batches, int64_t batch, int64_t chunk_samples,
-                            int gpw, uint64_t* __restrict__ item_base) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    uint64_t acc = 0;
-    for (int b = 0; b < n_batches; ++b) {
-        item_base[b] = acc;
-        const int64_t nb = min(batch, chunk_samples - (int64_t)b * batch);
-        acc += (uint64_t)((nb + gpw - 1) / gpw);
-        acc += (uint64_t)((mcount[b] + gpw - 1) / gpw);
-    }
-    item_base[n_batches] = acc;
 }
 
 // ---------------------------------------------------------------------------
@@ -1386,7 +1671,7 @@ struct Buf {
 // pre-pass of chunk c+1 (on its own low-priority stream) fills one while the
 // data phase of chunk c reads the other.
 struct ChunkSet {
-    Buf rec, slot_info, mdesc, mcount, ldesc, lcount, eta, slot_prev, arrive, item_base, nseg, tchunk;
+    Buf rec, slot_info, depmap, mdesc, mcount, ldesc, lcount, eta, tchunk;
     // captured data phase of a full chunk of this set, and what it was captured for
     cudaGraphExec_t graph = nullptr;
     DataParams graph_key{};
@@ -1397,7 +1682,7 @@ struct ChunkSet {
 };
 
 struct TrainWorkspace {
-    Buf items0, items1, gcnt, boff, counters, slab, sorted_row, seghead, seg_done, batch_applied;
+    Buf items0, items1, gcnt, boff, counters, slab, gbar;
     ChunkSet set[2];
     cudaStream_t prep = nullptr;    // pre-pass stream
     cudaStream_t cap = nullptr;     // stream the data-phase graphs are captured on
@@ -1405,7 +1690,6 @@ struct TrainWorkspace {
     cudaEvent_t start = nullptr;    // caller-stream work before the call
     cudaEvent_t prep_end = nullptr; // last pre-pass of the call
     std::vector<cudaEvent_t> events;  // timing events
-    uint32_t gen = 0;
     cudaError_t event(size_t i, cudaEvent_t* out) {
         while (events.size() <= i) {
             cudaEvent_t e;
@@ -1540,21 +1824,37 @@ static cudaError_t launch_data_batched(const DataParams& p, int warps_per_block,
 
 template <int D, int DT>
 static cudaError_t launch_data_persistent(const DataParams& p, int warps_per_block, cudaStream_t s) {
-    size_t smem = 0;
-    const int wpb = gather_warps<D, DT>(p, warps_per_block, kPersistThreads / 32, &smem);
-    static std::atomic<uint64_t> attr_set{0};
-    once_per_device(attr_set,
-                    [] { cudaFuncSetAttribute(k_persistent<D, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem); });
-    int dev = 0, sms = 0, per_sm = 0;
+    using G = Geom<D, DT>;
+    int dev = 0, sms = 0, optin = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<D, DT>, wpb * 32, smem);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     if (e != cudaSuccess) return e;
+    int W = warps_per_block > 0 ? std::min(warps_per_block, kPersistMaxWarps) : kPersistDefaultWarps;
+    // two row slots per warp when a warp has two or more units of a batch
+    auto slots_for = [&](int w) {
+        const int64_t units = (p.batch + G::GPW - 1) / G::GPW;
+        return units > (int64_t)sms * w ? 2 : 1;
+    };
+    size_t smem = persist_smem_bytes(D, DT, p.K, W, slots_for(W), G::GPW);
+    while (W > 1 && smem > (size_t)optin) {
+        --W;
+        smem = persist_smem_bytes(D, DT, p.K, W, slots_for(W), G::GPW);
+    }
+    if (smem > (size_t)optin) return cudaErrorInvalidConfiguration;
+    if ((e = cudaFuncSetAttribute(k_persistent<D, DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return e;
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_persistent<D, DT>, W * 32, smem)) != cudaSuccess)
+        return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     DataParams pc = p;
+    pc.slots = slots_for(W);
+    if ((e = cudaMemsetAsync(p.gbar, 0, 2 * sizeof(uint32_t), s)) != cudaSuccess) return e;
     void* args[] = {&pc};
-    return cudaLaunchCooperativeKernel((const void*)k_persistent<D, DT>, dim3((unsigned)(per_sm * sms)),
-                                       dim3((unsigned)(wpb * 32)), args, smem, s);
+    return cudaLaunchCooperativeKernel((const void*)k_persistent<D, DT>, dim3((unsigned)sms), dim3((unsigned)(W * 32)),
+                                       args, smem, s);
 }
 
 using LaunchFn = cudaError_t (*)(const DataParams&, int, cudaStream_t);
@@ -1576,8 +1876,6 @@ static LaunchFn pick_launcher(int dim, int dtype, bool persistent) {
 #undef LINE_PICK
     return nullptr;
 }
-
-static int groups_per_warp(int dim, int dtype) { return 32 / geom_lanes(dim, dtype); }
 
 cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, TrainTimes* times, cudaStream_t s,
                       std::string* err) {
@@ -1612,7 +1910,10 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     int log_parts = 0;
     while (a.batch * R > ((int64_t)3584 << log_parts)) ++log_parts;
     const bool direct = log_parts <= kGroupMaxLog;
-    const bool persistent = a.mode == LINE_MODE_PERSISTENT;
+    // the persistent schedule needs all its CTAs resident at once, which a
+    // second cooperative launch on the other order's stream could prevent:
+    // concurrent orders run the batched schedule
+    const bool persistent = a.mode == LINE_MODE_PERSISTENT && !a.concurrent;
     const bool hogwild = a.mode == LINE_MODE_HOGWILD;  // records only: no grouping, slab or apply
     // shared segments (two or more entries) and long ones (more than kChunk)
     // per batch, at most
@@ -1648,10 +1949,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
                 !f(cs.mcount, sizeof(uint32_t) * (nb + 1)) || !f(cs.ldesc, sizeof(uint4) * (size_t)nb * lcap) ||
                 !f(cs.lcount, sizeof(uint32_t) * (nb + 1)) || !f(cs.tchunk, 256))
                 return false;
-            if (persistent && (!f(cs.slot_prev, sizeof(int32_t) * max_items) ||
-                               !f(cs.arrive, sizeof(uint32_t) * max_items) ||
-                               !f(cs.item_base, sizeof(uint64_t) * (nb + 1)) || !f(cs.nseg, sizeof(uint32_t) * (nb + 1))))
-                return false;
+            if (persistent && !f(cs.depmap, sizeof(uint32_t) * (size_t)nb * kDepWords)) return false;
         }
         return true;
     };
@@ -1669,19 +1967,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         for (auto& cs : ws->set) cs.data_pending = false;
         if (!each(ensure)) return e;
     }
-    if (persistent) {
-        if (!ensure(ws->sorted_row, sizeof(uint32_t) * max_items) || !ensure(ws->seghead, sizeof(uint32_t) * max_items) ||
-            !ensure(ws->batch_applied, sizeof(uint32_t) * (nb + 1)))
-            return e;
-        // generation flags start at zero and are never reset: a chunk's
-        // flags are "done" when they equal its generation number
-        const size_t need = sizeof(uint32_t) * max_items;
-        if (ws->seg_done.cap < need) {
-            if (!ensure(ws->seg_done, need)) return e;
-            if ((e = cudaMemsetAsync(ws->seg_done.p, 0, need, s)) != cudaSuccess) return e;
-            ws->gen = 0;
-        }
-    }
+    if (persistent && !ensure(ws->gbar, 256)) return e;
     LaunchFn data = pick_launcher(a.dim, a.dtype, persistent);
     if (!data) {
         *err = "unsupported dim";
@@ -1745,8 +2031,6 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     gq.boff = (uint32_t*)ws->boff.p;
     gq.mcap = mcap;
     gq.lcap = lcap;
-    gq.sorted_row = persistent ? (uint32_t*)ws->sorted_row.p : nullptr;
-    gq.seghead = persistent ? (uint32_t*)ws->seghead.p : nullptr;
 
     uint32_t* abort_word = (uint32_t*)ws->counters.p + 16;
 
@@ -1765,8 +2049,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     dp.lambda = (float)a.lambda;
     dp.alpha_neg = (float)a.alpha_neg;
     dp.status = status;
-    dp.seg_done = (uint32_t*)ws->seg_done.p;
-    dp.batch_applied = (uint32_t*)ws->batch_applied.p;
+    dp.gbar = (uint32_t*)ws->gbar.p;
     dp.spin_limit = a.spin_limit;
     dp.abort_word = abort_word;
     dp.apply_warps = a.concurrent ? kApplyWarpsShared : kApplyWarpsAlone;
@@ -1822,10 +2105,12 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
             gq.mcount = (uint32_t*)cset.mcount.p;
             gq.ldesc = (uint4*)cset.ldesc.p;
             gq.lcount = (uint32_t*)cset.lcount.p;
-            gq.nseg = persistent ? (uint32_t*)cset.nseg.p : nullptr;
+            gq.depmap = persistent ? (uint32_t*)cset.depmap.p : nullptr;
             if ((e = cudaMemsetAsync(cset.mcount.p, 0, sizeof(uint32_t) * (cb + 1), ps)) != cudaSuccess) return e;
             if ((e = cudaMemsetAsync(cset.lcount.p, 0, sizeof(uint32_t) * (cb + 1), ps)) != cudaSuccess) return e;
-            if (persistent && (e = cudaMemsetAsync(cset.nseg.p, 0, sizeof(uint32_t) * (cb + 1), ps)) != cudaSuccess) return e;
+            if (persistent &&
+                (e = cudaMemsetAsync(cset.depmap.p, 0, sizeof(uint32_t) * (size_t)cb * kDepWords, ps)) != cudaSuccess)
+                return e;
             if (direct) {
                 cudaLaunchConfig_t cfg = {};
                 cfg.gridDim = dim3(1u << log_parts, cb);
@@ -1846,15 +2131,6 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
                 k_bucket_scatter<<<dim3(parts, cb), kBucketThreads, 0, ps>>>(gq);
                 k_bucket_sort<<<dim3(kBuckets / kSortBucketsPerCta, cb), kSortThreads, sort_smem, ps>>>(gq);
                 launches += 5;
-            }
-            if (persistent) {
-                const unsigned g = (unsigned)std::min<int64_t>((n_items + 255) / 256, 152 * 16);
-                k_prev_lookup<<<g, 256, 0, ps>>>(gq, (const int32_t*)cset.rec.p, a.order == 2 ? (uint32_t)a.n_nodes : 0u,
-                                                 (int32_t*)cset.slot_prev.p);
-                k_item_base<<<1, 32, 0, ps>>>((const uint32_t*)cset.mcount.p, cb, a.batch, cs,
-                                              groups_per_warp(a.dim, a.dtype), (uint64_t*)cset.item_base.p);
-                if ((e = cudaMemsetAsync(cset.arrive.p, 0, sizeof(uint32_t) * n_items, ps)) != cudaSuccess) return e;
-                launches += 2;
             }
         } else {
             launches += 1;  // the draws alone
@@ -1899,18 +2175,11 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
             dp.ldesc = (const uint4*)cset.ldesc.p;
             dp.lcount = (const uint32_t*)cset.lcount.p;
             dp.eta = (const float*)cset.eta.p;
-            dp.slot_prev = (const int32_t*)cset.slot_prev.p;
-            dp.nseg = (const uint32_t*)cset.nseg.p;
-            dp.arrive = (uint32_t*)cset.arrive.p;
-            dp.item_base = (const uint64_t*)cset.item_base.p;
+            dp.depmap = (const uint32_t*)cset.depmap.p;
             dp.t_chunk = t;
             dp.chunk_samples = cs;
             dp.n_batches = cb;
-            if (persistent) {
-                if ((e = cudaMemsetAsync(abort_word, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
-                if ((e = cudaMemsetAsync(ws->batch_applied.p, 0, sizeof(uint32_t) * (cb + 1), s)) != cudaSuccess) return e;
-                dp.gen = ++ws->gen;
-            }
+            if (persistent && (e = cudaMemsetAsync(abort_word, 0, sizeof(uint32_t), s)) != cudaSuccess) return e;
             if (!persistent && a.graph && !ws->graph_failed && cs == max_chunk && c > 0) {
                 // a full chunk: replay this set's captured data phase (the chunk's
                 // first sample index comes from the set's device copy)
