@@ -75,6 +75,11 @@ ROW_BYTES_F32 = DIM * 4
 ALG_BYTES_PATH = 14 * ROW_BYTES_F32 + 8 + 8 + 8 * K
 # the update kernels alone move the 14 rows
 ALG_BYTES_UPDATE = 14 * ROW_BYTES_F32
+META_BYTES = 8 + 8 + 8 * K
+
+
+def row_bytes(dtype_name: str) -> int:
+    return DIM * (2 if dtype_name == "bf16" else 4)
 
 
 def parse():
@@ -88,6 +93,8 @@ def parse():
     p.add_argument("--orders", default="concurrent", choices=["concurrent", "sequential"],
                    help="train the two orders' tables concurrently (line_train_orders) or one after the other")
     p.add_argument("--scale", type=int, default=20)
+    p.add_argument("--dtype", default="fp32", choices=["fp32", "bf16"],
+                   help="table storage of the default and rmat20walk workloads (bf16: stochastic rounding)")
     p.add_argument("--samples-per-step", type=int, default=0, help="0: |E| = 16 * 2^scale")
     p.add_argument("--e2e-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -285,12 +292,14 @@ def run_reference(args):
 def workload_config(args, g):
     wl, ww = walk_of(args)
     sampler = f"_walk{wl}w{ww}" if wl else ""
-    c = {"workload": f"rmat{args.scale}_line_order1+2_d{DIM}_K{K}_B{B}_fp32{sampler}",
+    tables_gib = 3 * g.n_nodes * row_bytes(args.dtype) / 2 ** 30
+    c = {"workload": f"rmat{args.scale}_line_order1+2_d{DIM}_K{K}_B{B}_{args.dtype}{sampler}",
          "graph": f"R-MAT scale {args.scale}, edge factor 16, (.57,.19,.19,.05), symmetrised",
          "n_nodes": g.n_nodes, "n_arcs": g.n_arcs, "dim": DIM, "K": K, "batch": B,
          "samples_per_step": 2 * samples_per_step(args),
          "lr": "0.025 linear decay over 20*|E| samples per order",
-         "l2": "inputs larger than L2 (FP32 U1, U2, C2 tables: 1.5 GiB; alias tables 258 MB)"}
+         "l2": f"inputs larger than L2 ({args.dtype.upper()} U1, U2, C2 tables: {tables_gib:.2f} GiB; "
+               f"alias tables 258 MB)"}
     if wl:
         c["positive_pairs"] = (f"walk sampler: walks of {wl} steps from arcs drawn by weight, weighted steps, "
                                f"pairs within a window of {ww}")
@@ -724,6 +733,10 @@ def main():
     seed = replica_seed(rank)
 
     walk_len, window = walk_of(args)
+    tdtype = L.DTYPE_BF16 if args.dtype == "bf16" else L.DTYPE_F32
+    rb = row_bytes(args.dtype)
+    alg_update = 14 * rb
+    alg_path = alg_update + META_BYTES
 
     def opts(offset):
         o = L.train_opts_default()
@@ -735,8 +748,8 @@ def main():
         o.window = window
         return o
 
-    ctx.init_embeddings(1, DIM, L.DTYPE_F32, seed=1)
-    ctx.init_embeddings(2, DIM, L.DTYPE_F32, seed=2)
+    ctx.init_embeddings(1, DIM, tdtype, seed=1)
+    ctx.init_embeddings(2, DIM, tdtype, seed=2)
     state = {"offset": 0}
 
     concurrent = args.orders == "concurrent"
@@ -775,41 +788,35 @@ def main():
     value = updates / (ms / 1e3)
 
     peak, peak_kind = peaks()
+    update_kernels = {L.MODE_BATCHED: "k_gather + k_apply", L.MODE_PERSISTENT: "k_persistent",
+                      L.MODE_HOGWILD: "k_hogwild"}[mode]
     if concurrent:
         # the two orders' update kernels overlap on two streams, so per-launch
         # durations overlap too: their algorithmic bytes over the timed
         # region (CUDA events on the caller's stream) instead
-        achieved = 2 * S * args.steps * ALG_BYTES_UPDATE / (ms / 1e3) / 1e9
-        kernel = ("update phase of both orders (" + ("k_hogwild" if mode == L.MODE_HOGWILD else "k_gather + k_apply")
-                  + "), concurrent streams, over the timed region")
+        achieved = 2 * S * args.steps * alg_update / (ms / 1e3) / 1e9
+        kernel = f"update phase of both orders ({update_kernels}), concurrent streams, over the timed region"
     else:
         # the update kernels' own CUDA events
         upd_ms = st.update_ms
-        achieved = st.update_samples * ALG_BYTES_UPDATE / (upd_ms / 1e3) / 1e9 if upd_ms > 0 else None
-        kernel = {L.MODE_BATCHED: "update phase (k_gather + k_apply)", L.MODE_PERSISTENT: "k_persistent",
-                  L.MODE_HOGWILD: "k_hogwild"}[mode]
-    traffic = measured_traffic() if mode == L.MODE_BATCHED and args.scale == 20 and not walk_len else None
+        achieved = st.update_samples * alg_update / (upd_ms / 1e3) / 1e9 if upd_ms > 0 else None
+        kernel = f"update phase ({update_kernels}), its own CUDA events"
+    traffic = (measured_traffic() if mode == L.MODE_BATCHED and args.scale == 20 and not walk_len
+               and args.dtype == "fp32" else None)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak if achieved else None, "traffic": traffic,
-                "traffic_unit": "DRAM bytes per 4,096-sample batch (k_gather + k_apply, warm L2, ncu)",
-                "alg_bytes_per_batch": B * ALG_BYTES_UPDATE,
+                "traffic_unit": "DRAM bytes per 4,096-sample batch (k_gather + k_apply, warm L2)",
+                "traffic_source": ("not measured in this run: the ncu summary "
+                                   "profiles/k_gather_k_apply_rmat20_d128_K5_B4096.md, taken on the same train.cu "
+                                   "(sha256 prefix checked)") if traffic else None,
+                "alg_bytes_per_batch": B * alg_update,
                 "kernel": kernel,
-                "alg_bytes_per_sample": ALG_BYTES_UPDATE, "peak_kind": peak_kind,
-                "path_achieved_gbs": value / world * ALG_BYTES_PATH / 1e9,
-                "path_frac": value / world * ALG_BYTES_PATH / 1e9 / peak}
-    if concurrent:
-        # counted from the schedule: per order and step, two launches per
-        # batch and three pre-pass launches per chunk of 64 batches (four
-        # with the walk sampler); Hogwild: the draws (+ walks) and one update
-        # launch per chunk of 64 batches (256 with walks)
-        batches = -(-S // B)
-        chunks = -(-batches // (256 if mode == L.MODE_HOGWILD and walk_len else 64))
-        if mode == L.MODE_HOGWILD:
-            launches = int(2 * args.steps * chunks * (2 + (walk_len > 0)))
-        else:
-            launches = int(2 * args.steps * (2 * batches + (3 + (walk_len > 0)) * chunks))
-    else:
-        launches = int(st.update_launches + st.prepass_launches)
+                "alg_bytes_per_sample": alg_update, "peak_kind": peak_kind,
+                "path_achieved_gbs": value / world * alg_path / 1e9,
+                "path_frac": value / world * alg_path / 1e9 / peak}
+    # kernel launches of the library in the timed region, counted by the
+    # library (line_get_stats; a replayed CUDA graph counts its kernels)
+    launches = int(st.update_launches + st.prepass_launches)
 
     # end to end through the C ABI from pinned host buffers
     e2e = None
@@ -817,29 +824,32 @@ def main():
         hs = torch.from_numpy(g.src).pin_memory()
         hd = torch.from_numpy(g.dst).pin_memory()
         hw = torch.from_numpy(g.w).pin_memory()
-        out = torch.empty((g.n_nodes, DIM), dtype=torch.float32).pin_memory()
+        tt = torch.bfloat16 if tdtype == L.DTYPE_BF16 else torch.float32
+        outs = [torch.empty((g.n_nodes, DIM), dtype=tt).pin_memory() for _ in range(3)]
         ctx2 = L.Context(local, stream.cuda_stream)
         ctx2.build_alias(g.n_nodes, hs, hd, hw)
-        ctx2.init_embeddings(1, DIM, L.DTYPE_F32, seed=1)
-        ctx2.init_embeddings(2, DIM, L.DTYPE_F32, seed=2)
+        ctx2.init_embeddings(1, DIM, tdtype, seed=1)
+        ctx2.init_embeddings(2, DIM, tdtype, seed=2)
         barrier()
         t0 = time.perf_counter()
         for i in range(args.e2e_steps):
             ctx2.build_alias(g.n_nodes, hs, hd, hw)
-            ctx2.init_embeddings(1, DIM, L.DTYPE_F32, seed=1)
-            ctx2.init_embeddings(2, DIM, L.DTYPE_F32, seed=2)
+            ctx2.init_embeddings(1, DIM, tdtype, seed=1)
+            ctx2.init_embeddings(2, DIM, tdtype, seed=2)
             if concurrent:
                 ctx2.train_orders(DIM, K, S, seed, total=total_per_order, opts=opts(0))
             else:
                 for order in (1, 2):
                     ctx2.train_steps(order, DIM, K, S, seed, total=total_per_order, opts=opts(0))
-            ctx2.get_embeddings(2, L.WHICH_U, out)
+            ctx2.get_embeddings(1, L.WHICH_U, outs[0], tdtype)
+            ctx2.get_embeddings(2, L.WHICH_U, outs[1], tdtype)
+            ctx2.get_embeddings(2, L.WHICH_C, outs[2], tdtype)
         barrier()
         dt = time.perf_counter() - t0
         ctx2.close()
         e2e = {"value": 2 * S * args.e2e_steps * world / dt, "unit": UNIT,
-               "h2d_bytes_per_step": int(g.n_arcs * 12), "d2h_bytes_per_step": int(g.n_nodes * DIM * 4),
-               "includes": "graph upload + alias build + table init + both orders + U2 read-back"}
+               "h2d_bytes_per_step": int(g.n_arcs * 12), "d2h_bytes_per_step": int(3 * g.n_nodes * rb),
+               "includes": "graph upload + alias build + table init + both orders + read-back of U1, U2 and C2"}
 
     cpu = None
     cpu_mt = None
@@ -851,7 +861,8 @@ def main():
     if rank == 0:
         line = {"metric": metric_of(args), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.dtype == "bf16" else "f32",
+                "data": "synthetic",
                 "config": workload_config(args, g), "roofline": roofline, "cpu_baseline": cpu,
                 "cpu_hogwild_context": cpu_mt,
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(),

@@ -145,15 +145,18 @@ typedef struct {
  * per-pair SGD.  Samples (arcs or walk pairs, negatives) are the same as in
  * the other modes. */
 
-/* Per-kernel timing collected when opts.timing == 1 (reset by line_reset_stats). */
+/* Counters of the training calls since the last line_reset_stats.  Launch
+ * and sample counts are kept on every call (a replayed CUDA graph counts the
+ * kernels it holds; line_train_orders counts both orders); the times only
+ * with opts.timing == 1. */
 typedef struct {
-    int64_t update_launches;   /* launches of the row-update kernel(s) */
-    double update_ms;          /* their summed CUDA-event time */
+    int64_t update_launches;   /* launches of the row-update kernels (gather, apply, persistent, Hogwild) */
+    double update_ms;          /* their summed CUDA-event time (opts.timing; not for line_train_orders) */
     uint64_t update_samples;   /* samples those launches processed */
     int64_t prepass_launches;  /* sampling + sort + segment launches */
-    double prepass_ms;
-    double total_ms;           /* event time of whole line_train_steps calls */
-    uint64_t total_samples;
+    double prepass_ms;         /* (opts.timing; not for line_train_orders) */
+    double total_ms;           /* event time of whole training calls (opts.timing) */
+    uint64_t total_samples;    /* samples of those calls (opts.timing) */
 } line_stats;
 
 LINE_API void line_train_opts_default(line_train_opts* opts);

@@ -108,6 +108,17 @@ __device__ __forceinline__ uint16_t bf16_sr(float x, uint32_t r16) {
     return (uint16_t)(b >> 16);
 }
 
+// The same rounding of two values in one instruction: cvt.rs (stochastic
+// rounding with explicit random bits) puts `hi` in the upper half of the
+// result, rounded with bits [16, 32) of r, and `lo` in the lower half with
+// bits [0, 16) - that is, bf16_sr(lo, r) | bf16_sr(hi, r >> 16) << 16, bit for
+// bit on every input except the payload of a NaN (a NaN stays a NaN).
+__device__ __forceinline__ uint32_t bf16x2_sr(float lo, float hi, uint32_t r) {
+    uint32_t d;
+    asm("cvt.rs.bf16x2.f32 %0, %1, %2, %3;" : "=r"(d) : "f"(hi), "f"(lo), "r"(r));
+    return d;
+}
+
 // ---------------------------------------------------------------------------
 // Launchers (defined in the .cu files).  All enqueue on `s`.
 // ---------------------------------------------------------------------------

@@ -66,7 +66,7 @@ __device__ __forceinline__ uint64_t sr_bits(uint64_t seed, uint32_t table_id, ui
 
 // Store a row part; BF16 rounds stochastically: value i of a 4-value vector
 // adds bits [16 i, 16 i + 16) of sr_bits(...) below the BF16 mantissa, then
-// truncates.
+// truncates (two values per cvt.rs instruction).
 template <int D, int DT>
 __device__ __forceinline__ void store_row(void* table, int64_t row, int lig, const float (&v)[Geom<D, DT>::E],
                                           uint64_t seed, uint64_t t0, uint32_t table_id) {
@@ -82,9 +82,7 @@ __device__ __forceinline__ void store_row(void* table, int64_t row, int lig, con
             const uint32_t k4 = (uint32_t)((lig * G::E + 4 * q) >> 2);
             const uint64_t r = sr_bits(seed, table_id, (uint64_t)row, t0, k4);
             const uint32_t r0 = (uint32_t)r, r1 = (uint32_t)(r >> 32);
-            const uint32_t x = (uint32_t)bf16_sr(v[4 * q], r0) | ((uint32_t)bf16_sr(v[4 * q + 1], r0 >> 16) << 16);
-            const uint32_t y = (uint32_t)bf16_sr(v[4 * q + 2], r1) | ((uint32_t)bf16_sr(v[4 * q + 3], r1 >> 16) << 16);
-            __stcg(p + q, make_uint2(x, y));
+            __stcg(p + q, make_uint2(bf16x2_sr(v[4 * q], v[4 * q + 1], r0), bf16x2_sr(v[4 * q + 2], v[4 * q + 3], r1)));
         }
     }
 }

@@ -2055,9 +2055,6 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
     dp.apply_warps = a.concurrent ? kApplyWarpsShared : kApplyWarpsAlone;
 
     struct ChunkRec {
-        int64_t samples;
-        int batches;
-        int prepass_launches;
         size_t ev;  // events ev, ev+1 (pre-pass stream), ev+2, ev+3 (data stream)
     };
     std::vector<ChunkRec> chunk_log;
@@ -2222,11 +2219,16 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         if (a.timing) {
             if ((e = ws->event(n_ev + 3, &ev)) != cudaSuccess) return e;
             cudaEventRecord(ev, s);
-            chunk_log.push_back({cs, cb, launches, n_ev});
+            chunk_log.push_back({n_ev});
             n_ev += 4;
         }
         if ((e = cudaEventRecord(cset.data_done, s)) != cudaSuccess) return e;
         cset.data_pending = true;
+        // launches counted whether or not they are timed (a graph replay
+        // counts the kernels it holds)
+        times->prepass_launches += launches;
+        times->update_launches += (persistent || hogwild) ? 1 : 2 * (int64_t)cb;
+        times->update_samples += (uint64_t)cs;
     }
     // the pre-pass stream's work is all ordered before the last data phase
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -2238,9 +2240,6 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
             cudaEventElapsedTime(&ms2, ws->events[r.ev + 2], ws->events[r.ev + 3]);
             times->prepass_ms += ms1;
             times->update_ms += ms2;
-            times->prepass_launches += r.prepass_launches;
-            times->update_launches += (persistent || hogwild) ? 1 : 2 * (int64_t)r.batches;
-            times->update_samples += (uint64_t)r.samples;
         }
     }
     return cudaSuccess;
