@@ -377,11 +377,11 @@ LINE_API line_status line_mlp_create(line_ctx* ctx, int order, int hidden, int a
  * embedding (neighbours that are not known are left out of the mean). */
 LINE_API line_status line_mlp_features(line_ctx* ctx, const uint8_t* known);
 
-/* Recompute the inputs of the nodes rows[0 .. n_rows) only (a buffer of
- * node ids), from the current graph and U table - for nodes that joined
- * after line_mlp_features; the other nodes' inputs are unchanged.  Needs a
- * line_mlp_features call first.  Errors: LINE_ERR_ARG (an id out of range;
- * nothing is computed), LINE_ERR_STATE. */
+/* Compute the inputs of the nodes rows[0 .. n_rows) only (a buffer of node
+ * ids), from the current graph and U table - for a sample of nodes to fit
+ * on, or for nodes that joined later; the other nodes' inputs are unchanged
+ * (zero until computed: line_mlp_create clears them).  Errors: LINE_ERR_ARG
+ * (an id out of range; nothing is computed), LINE_ERR_STATE. */
 LINE_API line_status line_mlp_features_rows(line_ctx* ctx, const uint8_t* known, const int32_t* rows,
                                             int64_t n_rows);
 
@@ -399,7 +399,8 @@ LINE_API line_status line_mlp_set_params(line_ctx* ctx, const float* in);
 /* Loss and gradient of the minibatch rows[0 .. n_rows) (a buffer of node
  * ids, 1 <= n_rows <= 65536) at the current parameters, targets the current
  * U rows; no update.  grads_out: NULL or a buffer of n_params floats;
- * loss_out: NULL or a host pointer.  Needs line_mlp_features. */
+ * loss_out: NULL or a host pointer.  Needs the rows' inputs (line_mlp_features or
+ * line_mlp_features_rows). */
 LINE_API line_status line_mlp_grad(line_ctx* ctx, const int32_t* rows, int64_t n_rows, float* grads_out,
                                    double* loss_out);
 
@@ -407,7 +408,8 @@ LINE_API line_status line_mlp_grad(line_ctx* ctx, const int32_t* rows, int64_t n
  * (1..65536) drawn from nodes[0 .. n) (a buffer), global steps
  * step_offset .. step_offset + steps - 1; targets the current U rows.
  * losses_out: NULL or a host array of `steps` doubles, each step's loss
- * before its update.  Needs line_mlp_features.  Node ids out of range:
+ * before its update.  Needs the nodes' inputs (line_mlp_features or
+ * line_mlp_features_rows).  Node ids out of range:
  * LINE_ERR_ARG (the step uses row 0 instead). */
 LINE_API line_status line_mlp_train(line_ctx* ctx, const int32_t* nodes, int64_t n, int64_t steps, int64_t batch,
                                     double lr, uint64_t seed, uint64_t step_offset, double* losses_out);
@@ -415,7 +417,8 @@ LINE_API line_status line_mlp_train(line_ctx* ctx, const int32_t* nodes, int64_t
 /* Predictions y for the nodes rows[0 .. n_rows) (a buffer).  y_out NULL:
  * written into those rows of the U table (BF16 tables round to nearest
  * even) - the warm start; otherwise a buffer of n_rows x d floats and the
- * table is untouched.  Needs line_mlp_features. */
+ * table is untouched.  Needs the rows' inputs (line_mlp_features or
+ * line_mlp_features_rows). */
 LINE_API line_status line_mlp_predict(line_ctx* ctx, const int32_t* rows, int64_t n_rows, float* y_out);
 
 /* Largest m accepted by line_eval_loss_noalloc. */

@@ -1050,7 +1050,8 @@ line_status mlp_ready(line_ctx* c, const char* what, bool need_features) {
     if (!c->tab[c->mlp->order].ready || c->tab[c->mlp->order].dim != c->mlp->dim)
         return fail(c, LINE_ERR_STATE, "%s: the tables of order %d (dim %d) are gone", what, c->mlp->order,
                     c->mlp->dim);
-    if (need_features && !c->mlp->has_features) return fail(c, LINE_ERR_STATE, "%s: no features (call line_mlp_features)", what);
+    if (need_features && !c->mlp->has_features)
+        return fail(c, LINE_ERR_STATE, "%s: no inputs (call line_mlp_features or line_mlp_features_rows)", what);
     return LINE_OK;
 }
 
@@ -1098,6 +1099,8 @@ line_status line_mlp_create(line_ctx* c, int order, int hidden, int act_dtype, u
     if (e == cudaSuccess) e = cudaMalloc(&s->m, pb);
     if (e == cudaSuccess) e = cudaMalloc(&s->v, pb);
     if (e == cudaSuccess) e = cudaMalloc(&s->X, (size_t)c->n_nodes * s->P * elem_size(act_dtype));
+    // inputs not yet computed are zero (line_mlp_features_rows may compute a subset)
+    if (e == cudaSuccess) e = cudaMemsetAsync(s->X, 0, (size_t)c->n_nodes * s->P * elem_size(act_dtype), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->m, 0, pb, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->v, 0, pb, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->grads, 0, pb, c->stream);
@@ -1125,7 +1128,6 @@ static line_status mlp_features_impl(line_ctx* c, const char* what, const uint8_
     if (!known) return fail(c, LINE_ERR_ARG, "%s: null mask", what);
     if (rows && n_rows < 0) return fail(c, LINE_ERR_ARG, "%s: bad row count", what);
     MlpState& s = *c->mlp;
-    if (rows && !s.has_features) return fail(c, LINE_ERR_STATE, "%s: compute every node's inputs first", what);
     if (rows && n_rows == 0) return LINE_OK;
     const Tables& t = c->tab[s.order];
     if ((st = ensure_row_ptr(c))) return st;

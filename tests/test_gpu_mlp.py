@@ -119,6 +119,30 @@ def test_features_of_a_row_subset(ctx):
     assert ei.value.status == L.LINE_ERR_ARG
 
 
+def test_features_of_a_sample_alone(ctx):
+    """Inputs of a node sample computed without a pass over every node equal
+    those of the full pass for those rows, and the other rows stay zero: the
+    warm start can fit on a sample of the kept nodes."""
+    from paper_2604_09419_gb300 import line as L
+    g = G.graph("rmat14")
+    G.upload(ctx, g)
+    U, C = trained_tables("rmat14", 64, 40_000, 6)
+    G.upload_tables(ctx, 2, U, C)
+    held, _ = I.hold_out_nodes(g, 0.1, seed=3)
+    known = (~held).astype(np.uint8)
+    rows = np.flatnonzero(~held)[::7].astype(np.int32)
+    ctx.mlp_create(2, hidden=32, act_dtype=L.DTYPE_BF16, seed=1)
+    ctx.mlp_features_rows(known, rows)
+    part = np.empty((g.n_nodes, 80), np.float32)
+    ctx.mlp_get_features(part)
+    ctx.mlp_features(known)
+    full = np.empty_like(part)
+    ctx.mlp_get_features(full)
+    assert np.array_equal(part[rows], full[rows]) and part[rows].any()
+    others = np.setdiff1d(np.arange(g.n_nodes), rows)
+    assert not part[others].any()
+
+
 def elementwise_excess(got, want, tol):
     """Largest excess of |got - want| over tol max|want| + tol |want|, taken
     element by element (<= 0 when every element is within the bound)."""
