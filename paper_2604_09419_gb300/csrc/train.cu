@@ -149,15 +149,16 @@ __device__ __forceinline__ T rec_entry(uint32_t gm, T held, const T* row, int id
 // Per-sample work.
 // ctx_stage: this warp's shared staging area, (K+1) x 32 lanes x E floats.
 // ---------------------------------------------------------------------------
-// Register-resident gather body for K + 1 <= 8: the K+1 context rows stay in
-// registers; the dots, their reductions and the K+1 sigmoids are independent
-// chains.  Same arithmetic, in the same order, as the staged body below.
-template <int D, int DT>
+// Register-resident gather body for K + 1 <= JB (6 or 8): the K+1 context
+// rows stay in registers; the dots, their reductions and the K+1 sigmoids are
+// independent chains.  Same arithmetic, in the same order, as the staged
+// body.  JB = 6 covers K <= 5 in fewer registers, so that a batch's gather
+// leaves room on every SM for the next chunk's pre-pass.
+template <int D, int DT, int JB = 8>
 __device__ __forceinline__ void sample_body_reg(const DataParams& p, int lig, bool active, float eta, uint64_t t0,
                                                 uint32_t gm, int32_t r0, uint2 i0, const int32_t* rec,
                                                 const uint2* info) {
     using G = Geom<D, DT>;
-    constexpr int JB = 8;
     const int32_t u = __shfl_sync(gm, r0, 0, G::L);
     float xu[G::E];
     float c[JB][G::E];
@@ -350,8 +351,12 @@ __device__ __forceinline__ void sample_item(const DataParams& p, int64_t s_local
     const uint2 i0 = (active && lig < R) ? info[lig] : make_uint2(0u, 0u);
     if constexpr (PDL) pdl_wait();  // the tables' rows: written by the previous kernel
     if constexpr (G::E <= 4) {
+        if (p.K < 6) {
+            sample_body_reg<D, DT, 6>(p, lig, active, eta, t0, gm, r0, i0, rec, info);
+            return;
+        }
         if (p.K < 8) {
-            sample_body_reg<D, DT>(p, lig, active, eta, t0, gm, r0, i0, rec, info);
+            sample_body_reg<D, DT, 8>(p, lig, active, eta, t0, gm, r0, i0, rec, info);
             return;
         }
     }
@@ -502,13 +507,15 @@ __device__ __forceinline__ void long_segment_cta(const DataParams& p, uint4 d, f
 // ---------------------------------------------------------------------------
 constexpr size_t kMaxSmem = 200 * 1024;
 
-// Gathers run in blocks of at most 4 warps at 7 blocks per SM (at most 73
+// Gathers run in blocks of at most 4 warps at 8 blocks per SM (at most 64
 // registers), so that a 4,096-sample batch (4,096 warps at d = 128) is
-// resident in one wave.
+// resident in one wave and still leaves registers on every SM for the
+// pre-pass kernels of the next chunk (one batch at 72 registers filled 95%
+// of the register file, and any pre-pass block displaced gather warps).
 constexpr int kGatherWarps = 4;
 
 template <int D, int DT, bool PDL>
-__global__ void __launch_bounds__(kGatherWarps * 32, 7) k_gather(DataParams p, int b) {
+__global__ void __launch_bounds__(kGatherWarps * 32, 8) k_gather(DataParams p, int b) {
     using G = Geom<D, DT>;
     extern __shared__ float4 smem4[];
     float* smem = reinterpret_cast<float*>(smem4);
