@@ -180,33 +180,43 @@ def test_autotune_keeps_tables_and_returns_a_valid_configuration(ctx):
     assert np.array_equal(V1, X1) and np.array_equal(V2, X2) and np.array_equal(W2, Y2)
 
 
-@pytest.mark.parametrize("dtype,cb", [(0, 0), (0, 3), (1, 2)])
-def test_train_orders_equals_two_sequential_calls(ctx, dtype, cb):
-    """Both orders trained concurrently give the tables of two separate calls."""
+@pytest.mark.parametrize("dtype,cb,dim,K,extra", [(0, 0, 64, 5, {}), (0, 3, 64, 5, {}), (1, 2, 64, 5, {}),
+                                                   (0, 0, 128, 5, {}), (0, 3, 128, 5, {}), (1, 2, 128, 5, {}),
+                                                   (1, 0, 128, 5, {}), (0, 2, 128, 3, {"lam": 1e-3, "alpha_neg": 0.5}),
+                                                   (0, 2, 128, 8, {})])
+def test_train_orders_equals_two_sequential_calls(ctx, dtype, cb, dim, K, extra):
+    """Both orders trained together on two streams give the tables of two
+    separate calls: at the bench's d = 128 and at d = 64, for the register
+    gather (K <= 7) and the staged one (K = 8), FP32 and BF16, with graph
+    replays of full chunks (cb > 0) and with weight decay and a negative
+    weight."""
     from paper_2604_09419_gb300 import line as L
     g = G.graph("rmat14")
     G.upload(ctx, g)
     n, B = 80_000, 1024
-    ctx.init_embeddings(1, 64, dtype, seed=1)
-    ctx.init_embeddings(2, 64, dtype, seed=2)
+    ctx.init_embeddings(1, dim, dtype, seed=1)
+    ctx.init_embeddings(2, dim, dtype, seed=2)
     for order in (1, 2):
-        ctx.train_steps(order, 64, 5, n, 9, batch=B, chunk_batches=cb, total=2 * n)
-    ctx.train_steps(1, 64, 5, n, 9, batch=B, chunk_batches=cb, total=2 * n, sample_offset=n)
-    ctx.train_steps(2, 64, 5, n, 9, batch=B, chunk_batches=cb, total=2 * n, sample_offset=n)
-    want1, _ = G.tables(ctx, g, 1, 64)
-    want2 = G.tables(ctx, g, 2, 64)
-    ctx.init_embeddings(1, 64, dtype, seed=1)
-    ctx.init_embeddings(2, 64, dtype, seed=2)
-    ctx.train_orders(64, 5, n, 9, batch=B, chunk_batches=cb, total=2 * n)
-    ctx.train_orders(64, 5, n, 9, batch=B, chunk_batches=cb, total=2 * n, sample_offset=n)
-    got1, _ = G.tables(ctx, g, 1, 64)
-    got2 = G.tables(ctx, g, 2, 64)
+        ctx.train_steps(order, dim, K, n, 9, batch=B, chunk_batches=cb, total=2 * n, **extra)
+    ctx.train_steps(1, dim, K, n, 9, batch=B, chunk_batches=cb, total=2 * n, sample_offset=n, **extra)
+    ctx.train_steps(2, dim, K, n, 9, batch=B, chunk_batches=cb, total=2 * n, sample_offset=n, **extra)
+    want1, _ = G.tables(ctx, g, 1, dim)
+    want2 = G.tables(ctx, g, 2, dim)
+    ctx.init_embeddings(1, dim, dtype, seed=1)
+    ctx.init_embeddings(2, dim, dtype, seed=2)
+    ctx.reset_stats()
+    ctx.train_orders(dim, K, n, 9, batch=B, chunk_batches=cb, total=2 * n, **extra)
+    ctx.train_orders(dim, K, n, 9, batch=B, chunk_batches=cb, total=2 * n, sample_offset=n, **extra)
+    st = ctx.stats()
+    assert st.update_samples == 4 * n
+    got1, _ = G.tables(ctx, g, 1, dim)
+    got2 = G.tables(ctx, g, 2, dim)
     assert np.array_equal(want1, got1)
     assert np.array_equal(want2[0], got2[0]) and np.array_equal(want2[1], got2[1])
     # both orders must exist with the given dim
     ctx.init_embeddings(1, 32, dtype, seed=1)
     with pytest.raises(L.LineError) as ei:
-        ctx.train_orders(64, 5, n, 9)
+        ctx.train_orders(dim, K, n, 9)
     assert ei.value.status == L.LINE_ERR_STATE
 
 
