@@ -27,7 +27,9 @@
 //             slot 1+j: g_j U_b[u] for Ctx[y_j].  A singleton row is written
 //             back at once (Eq. 2-3); a shared row's contribution goes to the
 //             delta slab at its position, so a segment's entries are
-//             contiguous.
+//             contiguous.  Positions count from the batch's first item: every
+//             batch reuses one slab region, whose lines stay in L2 instead of
+//             being written back to DRAM.
 //     apply   per shared segment: the entries summed in a fixed chunked
 //             order, X <- X_b - cnt eta_b lambda X_b + sum, cnt the number of
 //             pair occurrences of the row (the batch-summed update of Eq. 4).
@@ -74,7 +76,7 @@ constexpr uint32_t kLongBit = 1u << 31;  // in mdesc.y: summed by a CTA
 // Sort item value: (sample within the chunk) << kSlotBits | slot.
 constexpr uint32_t kSlotBits = 6;
 constexpr uint32_t kSlotMask = (1u << kSlotBits) - 1u;
-// slot_info.x: sorted position, bit 31 set for a singleton segment.
+// slot_info.x: sorted position within the batch, bit 31 set for a singleton segment.
 constexpr uint32_t kSingleBit = 1u << 31;
 
 // Fibonacci hashing: spreads the hot (low) row ids of skewed graphs.  The
@@ -113,7 +115,7 @@ struct DataParams {
     const uint4* ldesc;      // [n_batches][lcap] long shared segments (also in mdesc, flagged)
     const uint32_t* lcount;  // [n_batches]
     uint32_t lcap;
-    float* slab;             // [chunk samples * (K+2)][D], by position
+    float* slab;             // [batch * (K+2)][D], by position within the batch
     const uint32_t* depmap;  // [n_batches][kDepWords] rows each batch touches (bit dep_bit(row id))
     uint64_t t_chunk;        // global index of the chunk's first sample
     const uint64_t* t_chunk_dev;  // when set, the same read from device memory (graph replays)
@@ -1294,7 +1296,7 @@ __global__ void __launch_bounds__(kSortThreads) k_bucket_sort(GroupParams q) {
         __syncwarp();
         a = x;
     }
-    const uint64_t gpos = base + lo;  // position of the bucket's first item in the chunk
+    const uint32_t gpos = lo;  // position of the bucket's first item in the batch
     for (uint32_t i = lane; i < c; i += 32) {
         const uint32_t key = (uint32_t)(a[i] >> 32);
         if (i > 0 && (uint32_t)(a[i - 1] >> 32) == key) continue;
@@ -1393,13 +1395,13 @@ struct GroupShared {
     uint32_t* lbase;
 };
 
-__device__ __forceinline__ void group_tail(const GroupParams& q, uint64_t* a, uint32_t nq, uint64_t base, uint32_t n,
+__device__ __forceinline__ void group_tail(const GroupParams& q, uint64_t* a, uint32_t nq, uint32_t n,
                                            uint32_t qbase, int b, uint32_t me, uint32_t P, int log_parts,
                                            const GroupShared& sh) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int kWarps = kGroupThreads / 32;
     const uint32_t* s_start = sh.start;
-    const uint64_t gpos = base + qbase;  // position of the part's first key in the chunk
+    const uint32_t gpos = qbase;  // position of the part's first key in the batch
     // sort each sub-bucket by (hrow(row), index): up to 32 keys by ranks
     // within a warp, larger ones (a hot row) by a warp bitonic sort
     for (int sb = warp; sb < kSub; sb += kWarps) {
@@ -1634,8 +1636,8 @@ __global__ void __launch_bounds__(kGroupThreads) k_group_cluster(GroupParams q, 
     }
     cl.sync();
     const GroupShared sh{s_start, s_big, &s_nbig, &s_mcnt, &s_lcnt, &s_mbase, &s_lbase};
-    if (fits[me]) group_tail(q, gkeys, nq, base, n, qbase, b, me, P, log_parts, sh);
-    else group_tail(q, q.bucketed + base + qbase, nq, base, n, qbase, b, me, P, log_parts, sh);
+    if (fits[me]) group_tail(q, gkeys, nq, n, qbase, b, me, P, log_parts, sh);
+    else group_tail(q, q.bucketed + base + qbase, nq, n, qbase, b, me, P, log_parts, sh);
 }
 
 // eta[b] = lr0 (schedule 0) or lr0 * max(1 - t0/T, floor) (schedule 1) for
@@ -1948,7 +1950,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
         if (!f(ws->items0, sizeof(uint64_t) * max_items) || !f(ws->items1, sizeof(uint64_t) * max_items) ||
             !f(ws->gcnt, sizeof(uint32_t) * (size_t)nb * parts * kBuckets) ||
             !f(ws->boff, sizeof(uint32_t) * (size_t)nb * (kBuckets + 1)) || !f(ws->counters, 256) ||
-            !f(ws->slab, sizeof(float) * (size_t)max_items * a.dim))
+            !f(ws->slab, sizeof(float) * (size_t)std::min<int64_t>(max_items, a.batch * R) * a.dim))
             return false;
         for (auto& cs : ws->set) {
             if (!f(cs.rec, sizeof(int32_t) * max_items) || !f(cs.eta, sizeof(float) * (nb + 1)) ||
