@@ -9,19 +9,25 @@
 //   L = sum (y - U[v])^2 / (B d) over a minibatch,  Adam (beta 0.9/0.999, eps 1e-8)
 //
 // Weights, gradients and optimiser state are FP32; the activations x and h
-// are stored as FP32 or BF16 (round to nearest even).  Every contraction is
-// one tiled kernel with FP32 FMA accumulation in index order (split over the
-// batch into slices summed in slice order for the weight gradients), so
-// training is bitwise reproducible.  Random numbers: Philox domain 7, call 0
+// are stored as FP32 or BF16 (round to nearest even).  With FP32 activations
+// every contraction is one tiled kernel with FP32 FMA accumulation in index
+// order (split over the batch into slices summed in slice order for the
+// weight gradients).  With BF16 activations the contractions run on the
+// tensor cores: the forward products in mlp_fwd.cu (BF16 x BF16 hi/lo
+// weights), the backward ones in k_gemm_tc (TF32).  Either way every sum has
+// a fixed order, so training is bitwise reproducible.  Random numbers: Philox domain 7, call 0
 // for minibatch picks (counter s*B + j), call 1 for the initial weights
 // (counter = the parameter's flat index).
 #include <math.h>
 
 #include <algorithm>
 #include <atomic>
+#include <type_traits>
 #include <vector>
 
 #include "context.cuh"
+#include "mlp_fwd.cuh"
+#include "mlp_math.cuh"
 
 namespace line {
 
@@ -69,6 +75,9 @@ struct MlpState {
     // products, W2 as that of dL/dh
     float* wt = nullptr;
     size_t wt_elems = 0;
+    // BF16 hi/lo tiles of W1 and W2 for the forward products of mlp_fwd.cu
+    __nv_bfloat16* w16 = nullptr;
+    size_t w16_elems = 0;
 };
 
 void mlp_destroy(MlpState* s) {
@@ -76,7 +85,7 @@ void mlp_destroy(MlpState* s) {
     for (void* p : {(void*)s->params, (void*)s->grads, (void*)s->m, (void*)s->v, s->X, (void*)s->rows, s->Xb,
                     (void*)s->Tb, (void*)s->A1, s->Hb, (void*)s->Yb, (void*)s->dH, (void*)s->part,
                     (void*)s->rowloss, s->sum_tmp, (void*)s->losses, (void*)s->nodes, (void*)s->kmask,
-                    (void*)s->hubs, (void*)s->frows, (void*)s->flag, (void*)s->wt})
+                    (void*)s->hubs, (void*)s->frows, (void*)s->flag, (void*)s->wt, (void*)s->w16})
         if (p) cudaFree(p);
     delete s;
 }
@@ -98,10 +107,6 @@ __device__ __forceinline__ float from_f<float>(float x) { return x; }
 template <>
 __device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
 
-__device__ __forceinline__ float gelu(float a) { return 0.5f * a * (1.0f + erff(a * 0.70710678118654752f)); }
-__device__ __forceinline__ float gelu_grad(float a) {
-    return 0.5f * (1.0f + erff(a * 0.70710678118654752f)) + a * expf(-0.5f * a * a) * 0.39894228040143268f;
-}
 
 __device__ __forceinline__ float load_row_elem(const void* U, int dtype, int64_t idx) {
     return dtype == LINE_DTYPE_F32 ? reinterpret_cast<const float*>(U)[idx]
@@ -912,6 +917,23 @@ cudaError_t ensure_weight_tiles(MlpState& s) {
     return e;
 }
 
+// Both forward products on mlp_fwd.cu's kernel (BF16 activations, layer
+// shapes it takes).
+bool fwd_fast(const MlpState& s) {
+    return s.act == LINE_DTYPE_BF16 && fwd_tc_supported(s.hidden, s.P) && fwd_tc_supported(s.dim, s.hidden);
+}
+
+cudaError_t ensure_w16(MlpState& s) {
+    const size_t need = fwd_w16_elems(s.hidden, s.P) + fwd_w16_elems(s.dim, s.hidden);
+    if (s.w16 && s.w16_elems >= need) return cudaSuccess;
+    if (s.w16) cudaFree(s.w16);
+    s.w16 = nullptr;
+    s.w16_elems = 0;
+    cudaError_t e = cudaMalloc(&s.w16, sizeof(__nv_bfloat16) * need);
+    if (e == cudaSuccess) s.w16_elems = need;
+    return e;
+}
+
 cudaError_t ensure_cap(MlpState& s, int64_t rows) {
     if (rows <= s.cap) return cudaSuccess;
     const int64_t cap = std::max<int64_t>(rows, 1024);
@@ -952,6 +974,21 @@ cudaError_t forward(MlpState& s, int64_t B, const Tables& t, bool targets, uint3
     k_mlp_gather<TX><<<grid_of(B * 32, 256), 256, 0, st>>>(s.rows, B, n_nodes, reinterpret_cast<const TX*>(s.X), s.P,
                                                             Xb, t.U, t.dtype, s.dim, targets ? s.Tb : nullptr, status);
     cudaError_t e;
+    if constexpr (std::is_same<TX, __nv_bfloat16>::value) {
+        if (fwd_fast(s)) {
+            // H = GELU(X W1^T + b1) (and A1 = X W1^T + b1 when training),
+            // then Y = H W2^T, both on the tensor cores with the weights as
+            // BF16 hi/lo pairs
+            if ((e = ensure_w16(s)) != cudaSuccess) return e;
+            const size_t e1 = fwd_w16_elems(s.hidden, s.P);
+            if ((e = fwd_tile_weights(W1, s.hidden, s.P, s.w16, st)) != cudaSuccess) return e;
+            if ((e = fwd_tile_weights(W2, s.dim, s.hidden, s.w16 + e1, st)) != cudaSuccess) return e;
+            if ((e = fwd_tc((int)B, s.hidden, s.P, Xb, s.w16, b1, targets ? s.A1 : nullptr, Hb, nullptr, status,
+                            st)) != cudaSuccess)
+                return e;
+            return fwd_tc((int)B, s.dim, s.hidden, Hb, s.w16 + e1, nullptr, nullptr, nullptr, s.Yb, status, st);
+        }
+    }
     const bool tc = s.act == LINE_DTYPE_BF16;
     const float* W1t = nullptr;
     const float* W2t = nullptr;
@@ -1001,6 +1038,7 @@ cudaError_t loss_grad(MlpState& s, int64_t B, const Tables& t, uint32_t* status,
     const bool tc = s.act == LINE_DTYPE_BF16;
     const float* W2tT = nullptr;
     if (tc) {
+        if ((e = ensure_weight_tiles(s)) != cudaSuccess) return e;
         float* dst = s.wt + tile_b_elems(s.hidden, s.P) + tile_b_elems(s.dim, s.hidden);
         k_tile_b<false><<<grid_of((int64_t)tile_b_elems(s.hidden, s.dim), 256), 256, 0, st>>>(
             W2, s.hidden, s.hidden, s.dim, tc_tile_n(s.hidden), dst);

@@ -1,0 +1,481 @@
+// Forward products of the warm-start MLP with BF16 activations (see
+// mlp_fwd.cuh for the operation): one persistent CTA per SM loops over
+// 128-row tiles of A.
+//
+//   warp 0     (one lane) copies the weights' hi and lo tiles into shared
+//              memory once (one bulk copy), then streams A through a ring
+//              of stages: per tile, ceil(K/64) TMA loads of 128 rows x 64
+//              BF16 (128-byte rows, 128-byte swizzle); rows beyond M and
+//              columns beyond K arrive as zeros;
+//   warp 1     allocates 2N tensor-memory columns (two accumulators) and
+//              issues, per stage, two tcgen05.mma kind::f16 (A x W_hi^T,
+//              A x W_lo^T) for every 16 columns of K inside [0, K), into
+//              the tile's accumulator; a commit frees the stage when its
+//              products are done, another marks the accumulator full;
+//   warps 2-17 the epilogue: warp w reads rows 32 (w % 4) .. + 31 of the
+//              accumulator (its tensor-memory lanes), one quarter of the
+//              columns, 16 at a time (tcgen05.ld), adds the bias, applies
+//              GELU, writes the 32 x 16 block into its staging buffer in the
+//              swizzled layout of the output's tensor map, and one lane
+//              stores the block with a TMA tensor store (rows beyond M
+//              clipped); then it releases the accumulator, so that the
+//              products of tile i+1 run while tile i is written out.  Four
+//              epilogue warps per scheduler keep the GELU's instruction
+//              stream issuing.
+//
+// Every wait is bounded: a wait that runs out records DEV_ERR_TIMEOUT and
+// raises the CTA's abort flag, on which the other roles stop; before the
+// CTA exits, the copy lane waits (bounded) for its own copies in flight and
+// the product lane for its own products, and warp 1 frees the tensor memory.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "bulk.cuh"
+#include "line_internal.cuh"
+#include "mlp_fwd.cuh"
+#include "mlp_math.cuh"
+
+namespace line {
+
+namespace {
+
+constexpr int kFM = 128;                                 // rows of a tile (the products' M)
+constexpr int kFKS = 64;                                 // K per stage: one 128-byte row of BF16
+constexpr uint32_t kFStageBytes = kFM * kFKS * 2;        // 16 KB
+constexpr int kFMaxStages = 4;
+constexpr int kFEpiWarps = 16;
+constexpr int kFChunk = 16;  // accumulator columns per tcgen05.ld and per stored block
+constexpr int kFThreads = 32 * (2 + kFEpiWarps);         // copy warp, product warp, epilogue warps
+constexpr size_t kFSmemLimit = 226 * 1024;  // dynamic shared memory of one CTA (227 KB less the static part)
+constexpr int64_t kFWaitLimit = int64_t(1) << 24;        // polls of one mbarrier wait
+
+struct FwdArgs {
+    int M, N, K, n_tiles, stages;
+    int hidden;               // 1: bias + GELU into H (BF16), 0: the sums into Y (FP32)
+    const __nv_bfloat16* Wt;  // W_hi then W_lo, core-matrix layout
+    const float* bias;        // hidden layer: [N], 16-byte aligned
+    float* A1;                // hidden layer, nullable: [M][N] sums + bias
+    uint32_t* status;
+};
+
+// Staging buffer of one epilogue warp: a 32 x 16 block of the output (BF16
+// rows of 32 bytes for H, FP32 rows of 64 bytes for Y).
+constexpr uint32_t out_block_bytes(bool hidden) { return hidden ? 32 * 32 : 32 * 64; }
+
+size_t w_bytes(int N, int K) { return fwd_w16_elems(N, K) * sizeof(__nv_bfloat16); }
+
+int stages_for(int N, int K, bool hidden) {
+    // 1024: room to align the stages
+    const size_t fixed = 1024 + w_bytes(N, K) + (size_t)kFEpiWarps * out_block_bytes(hidden);
+    if (fixed >= kFSmemLimit) return 0;
+    return (int)std::min<size_t>(kFMaxStages, (kFSmemLimit - fixed) / kFStageBytes);
+}
+
+size_t smem_bytes(int N, int K, int stages, bool hidden) {
+    return 1024 + (size_t)stages * kFStageBytes + w_bytes(N, K) + (size_t)kFEpiWarps * out_block_bytes(hidden);
+}
+
+// Shared-memory descriptor of an A stage: start >> 4; leading offset unused
+// for a swizzled K-major operand (1); 1024 bytes between groups of 8 rows;
+// version 1 at bits 46-47; 128-byte swizzle (2) at bits 61-63.  A step of 16
+// values along K inside the 128-byte row adds 32 bytes to the start.
+__device__ __forceinline__ uint64_t desc_a(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// Descriptor of a weight tile without swizzle: core matrices (8 rows x 16
+// bytes) 128 bytes apart along K, groups of 8 rows `sbo` bytes apart.
+__device__ __forceinline__ uint64_t desc_w(uint32_t addr, uint32_t sbo) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(128 >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: D = F32 (bits 4-5), A = B = BF16
+// (bits 7-9, 10-12), both K-major, N >> 3 at bits 17-22, M >> 4 at 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kFM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_addr(bar))
+        : "memory");
+}
+
+// TMA tensor store of the block at src (laid out as the map's box, swizzled
+// as the map says) to columns x.., rows y.. of the map's tensor.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(smem_addr(src))
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// This thread's bulk stores have read their shared-memory sources.
+__device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// This thread's bulk stores are complete.
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+__device__ __forceinline__ void st_shared_v4(uint32_t addr, uint32_t x, uint32_t y, uint32_t z, uint32_t w) {
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Arrives on `bar` once every earlier tcgen05.mma of this thread is done.
+__device__ __forceinline__ void tc_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\ntcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// 16 consecutive FP32 columns of this warp's 32 tensor-memory lanes (one row per lane).
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Wait for the phase of `bar` of the given parity.  False when another role
+// aborted, or when the wait ran out (then this role aborts the CTA).
+__device__ __forceinline__ bool fwd_wait(uint64_t* bar, uint32_t parity, volatile uint32_t* abort_flag,
+                                         uint32_t* status) {
+    for (int64_t it = 0;; ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (*abort_flag) return false;
+        if (it > kFWaitLimit) {
+            *abort_flag = 1u;
+            atomicOr(status, DEV_ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// The same wait regardless of the abort flag, for a role's own copies or
+// products before the CTA exits (bounded as well).
+__device__ __forceinline__ void fwd_drain(uint64_t* bar, uint32_t parity) {
+    for (int64_t it = 0; it <= kFWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return;
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+__global__ void __launch_bounds__(kFThreads, 1) k_mlp_fwd_tc(const __grid_constant__ CUtensorMap tmA,
+                                                             const __grid_constant__ CUtensorMap tmO, FwdArgs a) {
+    extern __shared__ unsigned char fwd_raw[];
+    __shared__ __align__(8) uint64_t full[kFMaxStages], empty[kFMaxStages], tfull[2], tempty[2], wbar, fin;
+    __shared__ uint32_t tmem_base;
+    __shared__ uint32_t abort_word;
+    volatile uint32_t* abort_flag = &abort_word;
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(fwd_raw) + 1023) & ~(uintptr_t)1023);
+    const int S = a.stages, N = a.N, K = a.K;
+    unsigned char* sA = base;                                                            // S stages of 16 KB
+    __nv_bfloat16* sW = reinterpret_cast<__nv_bfloat16*>(base + (size_t)S * kFStageBytes);  // W_hi, W_lo
+    // the epilogue warps' staging blocks (1024-byte aligned: N K 4 is a multiple of 4096)
+    const uint32_t wbytes = (uint32_t)(2 * (size_t)N * K * sizeof(__nv_bfloat16));
+    unsigned char* sOut = base + (size_t)S * kFStageBytes + (size_t)wbytes;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nks = (K + kFKS - 1) / kFKS;
+    uint32_t cols = 32;
+    while (cols < 2u * (uint32_t)N) cols <<= 1;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < S; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&tfull[i], 1);
+            mbar_init(&tempty[i], kFEpiWarps);
+        }
+        mbar_init(&wbar, 1);
+        mbar_init(&fin, 1);
+        abort_word = 0u;
+        mbar_init_fence();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmA)) : "memory");
+            mbar_arrive_expect_tx(&wbar, wbytes);
+            bulk_load(sW, a.Wt, wbytes, &wbar);
+            uint32_t g = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; ok && t < a.n_tiles; t += gridDim.x) {
+                for (int ks = 0; ks < nks; ++ks) {
+                    const uint32_t st = g % (uint32_t)S, j = g / (uint32_t)S;
+                    if (!fwd_wait(&empty[st], (j & 1u) ^ 1u, abort_flag, a.status)) {
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[st], kFStageBytes);
+                    tma_load_2d(sA + (size_t)st * kFStageBytes, &tmA, ks * kFKS, t * kFM, &full[st]);
+                    ++g;
+                }
+            }
+            // this lane's copies in flight: the weights, and after an abort
+            // the last S stage loads (earlier ones were consumed)
+            fwd_drain(&wbar, 0u);
+            if (!ok) {
+                for (uint32_t i = 0; i < (uint32_t)S && i < g; ++i) {
+                    const uint32_t gg = g - 1 - i;
+                    fwd_drain(&full[gg % (uint32_t)S], (gg / (uint32_t)S) & 1u);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            bool ok = fwd_wait(&wbar, 0u, abort_flag, a.status);
+            tc_fence_after();
+            const uint32_t w_hi = smem_addr(sW), w_lo = w_hi + (uint32_t)((size_t)N * K * sizeof(__nv_bfloat16));
+            const uint32_t sbo = (uint32_t)K * 16u;  // 8 rows of K BF16
+            const uint32_t idesc = idesc_bf16(N);
+            uint32_t g = 0, i = 0;
+            for (int t = blockIdx.x; ok && t < a.n_tiles; t += gridDim.x, ++i) {
+                const uint32_t acc = i & 1u, u = i >> 1;
+                if (!fwd_wait(&tempty[acc], (u & 1u) ^ 1u, abort_flag, a.status)) break;
+                tc_fence_after();
+                const uint32_t d = tmem + acc * (uint32_t)N;
+                for (int ks = 0; ks < nks; ++ks, ++g) {
+                    const uint32_t st = g % (uint32_t)S, j = g / (uint32_t)S;
+                    if (!fwd_wait(&full[st], j & 1u, abort_flag, a.status)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t sa = smem_addr(sA + (size_t)st * kFStageBytes);
+#pragma unroll
+                    for (int kk = 0; kk < kFKS / 16; ++kk) {
+                        const int k = ks * kFKS + kk * 16;
+                        if (k >= K) break;
+                        const uint64_t da = desc_a(sa + (uint32_t)kk * 32u);
+                        const uint32_t wo = (uint32_t)(k >> 3) * 128u;
+                        tc_mma(d, da, desc_w(w_hi + wo, sbo), idesc, (ks | kk) ? 1u : 0u);
+                        tc_mma(d, da, desc_w(w_lo + wo, sbo), idesc, 1u);
+                    }
+                    tc_commit(&empty[st]);  // the stage is free once these products are done
+                }
+                if (!ok) break;
+                tc_commit(&tfull[acc]);
+            }
+            // every product of this lane done before the CTA exits
+            tc_commit(&fin);
+            fwd_drain(&fin, 0u);
+        }
+        __syncwarp();
+    } else {
+        const int e = warp - 2, q = warp & 3, h = e >> 2;
+        const int quarter = N / 4;
+        const bool hid = a.hidden != 0;
+        unsigned char* blk = sOut + (size_t)e * out_block_bytes(hid);
+        const uint32_t so = smem_addr(blk);
+        uint32_t i = 0;
+        for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++i) {
+            const uint32_t acc = i & 1u, u = i >> 1;
+            const bool ok = fwd_wait(&tfull[acc], u & 1u, abort_flag, a.status);
+            if (!__all_sync(0xFFFFFFFFu, ok)) break;
+            tc_fence_after();
+            const int row0 = t * kFM + q * 32, row = row0 + lane;
+            for (int c0 = h * quarter; c0 < (h + 1) * quarter; c0 += kFChunk) {
+                uint32_t r[16];
+                tc_ld16(tmem + ((uint32_t)(q * 32) << 16) + acc * (uint32_t)N + (uint32_t)c0, r);
+                // the block's previous store has read the staging buffer
+                if (lane == 0) bulk_wait_read();
+                __syncwarp();
+                if (hid) {
+                    float v[16];
+                    const float4* bp = reinterpret_cast<const float4*>(a.bias + c0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float4 b = __ldg(bp + j);
+                        v[4 * j] = __uint_as_float(r[4 * j]) + b.x;
+                        v[4 * j + 1] = __uint_as_float(r[4 * j + 1]) + b.y;
+                        v[4 * j + 2] = __uint_as_float(r[4 * j + 2]) + b.z;
+                        v[4 * j + 3] = __uint_as_float(r[4 * j + 3]) + b.w;
+                    }
+                    if (a.A1 && row < a.M) {
+                        float4* p = reinterpret_cast<float4*>(a.A1 + (size_t)row * N + c0);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) p[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                    }
+                    // row `lane` of the block: 2 pieces of 16 bytes, piece j at
+                    // j ^ ((lane >> 2) & 1) (the map's 32-byte swizzle)
+#pragma unroll
+                    for (int j = 0; j < 2; ++j)
+                        st_shared_v4(so + (uint32_t)lane * 32u + ((uint32_t)(j ^ ((lane >> 2) & 1)) << 4),
+                                     pack_bf16x2(gelu_bf16out(v[8 * j]), gelu_bf16out(v[8 * j + 1])),
+                                     pack_bf16x2(gelu_bf16out(v[8 * j + 2]), gelu_bf16out(v[8 * j + 3])),
+                                     pack_bf16x2(gelu_bf16out(v[8 * j + 4]), gelu_bf16out(v[8 * j + 5])),
+                                     pack_bf16x2(gelu_bf16out(v[8 * j + 6]), gelu_bf16out(v[8 * j + 7])));
+                } else {
+                    // 4 pieces of 16 bytes, piece j at j ^ ((lane >> 1) & 3) (64-byte swizzle)
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        st_shared_v4(so + (uint32_t)lane * 64u + ((uint32_t)(j ^ ((lane >> 1) & 3)) << 4), r[4 * j],
+                                     r[4 * j + 1], r[4 * j + 2], r[4 * j + 3]);
+                }
+                fence_proxy_async_smem();  // the tensor store reads the block through the async proxy
+                __syncwarp();
+                if (lane == 0) {
+                    tma_store_2d(&tmO, c0, row0, blk);
+                    bulk_commit();
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&tempty[acc]);
+        }
+        if (lane == 0) bulk_wait_all();  // the stores are done before the CTA's shared memory goes
+        __syncwarp();
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+    }
+}
+
+// W -> hi/lo BF16 tiles (see fwd_tile_weights).
+__global__ void k_tile_w16(const float* __restrict__ W, int N, int K, __nv_bfloat16* __restrict__ Wt) {
+    const int64_t total = (int64_t)N * K;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int n = (int)(i / K), k = (int)(i % K);
+        const float w = W[i];
+        const __nv_bfloat16 hi = __float2bfloat16_rn(w);
+        const __nv_bfloat16 lo = __float2bfloat16_rn(w - __bfloat162float(hi));  // w - hi is exact in FP32
+        const int64_t o = (int64_t)(n >> 3) * (K * 8) + (k >> 3) * 64 + (n & 7) * 8 + (k & 7);
+        Wt[o] = hi;
+        Wt[total + o] = lo;
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+}  // namespace
+
+bool fwd_tc_supported(int N, int K) {
+    // (the output layer's staging is the larger: both layers fit when it does)
+    return N >= 64 && N <= 256 && N % (4 * kFChunk) == 0 && K >= 16 && K % 16 == 0 && stages_for(N, K, false) >= 2;
+}
+
+cudaError_t fwd_tile_weights(const float* W, int N, int K, __nv_bfloat16* Wt, cudaStream_t s) {
+    const int64_t total = (int64_t)N * K;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 1024);
+    k_tile_w16<<<blocks, 256, 0, s>>>(W, N, K, Wt);
+    return cudaGetLastError();
+}
+
+cudaError_t fwd_tc(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Wt, const float* bias, float* A1,
+                   __nv_bfloat16* H, float* Y, uint32_t* status, cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    const bool hidden = H != nullptr;
+    if (!fwd_tc_supported(N, K) || (hidden ? bias == nullptr || (reinterpret_cast<uintptr_t>(bias) & 15) : Y == nullptr))
+        return cudaErrorInvalidValue;
+    PFN_cuTensorMapEncodeTiled_v12000 encode = encode_tiled();
+    if (!encode) return cudaErrorNotSupported;
+    const cuuint32_t elem_strides[2] = {1, 1};
+    // A: K columns (inner) x M rows, row pitch 2K bytes; boxes of 64 x 128
+    CUtensorMap map;
+    {
+        const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)M};
+        const cuuint64_t strides[1] = {(cuuint64_t)K * sizeof(__nv_bfloat16)};
+        const cuuint32_t box[2] = {(cuuint32_t)kFKS, (cuuint32_t)kFM};
+        if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(A), dims, strides, box,
+                   elem_strides, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    // the output (H: BF16, Y: FP32): N columns x M rows, boxes of 16 x 32,
+    // swizzled over the box's row (32 or 64 bytes)
+    CUtensorMap omap;
+    {
+        const size_t esz = hidden ? sizeof(__nv_bfloat16) : sizeof(float);
+        const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)M};
+        const cuuint64_t strides[1] = {(cuuint64_t)N * esz};
+        const cuuint32_t box[2] = {(cuuint32_t)kFChunk, 32};
+        if (encode(&omap, hidden ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                   hidden ? (void*)H : (void*)Y, dims, strides, box, elem_strides, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   hidden ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+    }
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int stages = stages_for(N, K, hidden);
+    const size_t smem = smem_bytes(N, K, stages, hidden);
+    {
+        // the kernel's dynamic shared-memory limit, raised per device to the
+        // largest launch so far
+        static std::mutex mu;
+        static size_t granted[64] = {};
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (granted[dev] < smem) {
+            e = cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            granted[dev] = smem;
+        }
+    }
+    FwdArgs a;
+    a.M = M;
+    a.N = N;
+    a.K = K;
+    a.n_tiles = (M + kFM - 1) / kFM;
+    a.stages = stages;
+    a.hidden = hidden ? 1 : 0;
+    a.Wt = Wt;
+    a.bias = bias;
+    a.A1 = hidden ? A1 : nullptr;
+    a.status = status;
+    const int grid = std::min(a.n_tiles, sms);
+    k_mlp_fwd_tc<<<grid, kFThreads, smem, s>>>(map, omap, a);
+    return cudaGetLastError();
+}
+
+}  // namespace line

@@ -222,6 +222,39 @@ def test_training_bf16_tracks_oracle_and_is_deterministic(ctx):
     assert np.array_equal(again, losses) and np.array_equal(ctx.mlp_get_params(), p1)
 
 
+def test_predict_bf16_activations_on_the_tensor_cores(ctx):
+    """BF16 activations at d = 128, hidden 256: both forward products run on
+    the tensor cores (activations by TMA, weights as BF16 hi/lo pairs).
+    Predictions of 1, 77, 128 and 40,000 rows (a partial tile, one tile, and
+    313 tiles, so that every CTA takes several tiles and both accumulators
+    alternate) against the oracle's FP64 forward pass with x and h rounded to
+    BF16, element by element, within 1e-3.  That bound allows for the
+    roundings of h to BF16 that fall the other way (a sum off by a few parts
+    in 10^6 changes about one h value in 10^3, and a row has 256).  The
+    product itself is pinned by the median error: the hi/lo weights carry
+    about 17 significant bits, so the typical output is within 1e-5 of the
+    largest (TF32 weights, 11 bits, would give about 1e-4)."""
+    from paper_2604_09419_gb300 import line as L
+    dim, hidden = 128, 256
+    g, U, known, X = setup(ctx, "rmat14", dim, L.DTYPE_BF16, hidden=hidden)
+    rng = np.random.default_rng(9)
+    p = OM.init_params(dim, hidden, 11)
+    p["b1"] = rng.normal(size=hidden) * 0.1
+    p["b2"] = rng.normal(size=dim) * 0.01
+    pv = flat(p).astype(np.float32)
+    ctx.mlp_set_params(pv)
+    p = unflat(pv, dim, hidden)
+    for n_rows in (1, 77, 128, 40_000):
+        rows = rng.integers(0, g.n_nodes, n_rows).astype(np.int32)
+        y = np.empty((n_rows, dim), np.float32)
+        ctx.mlp_predict(rows, y)
+        want = OM.predict(p, X[rows], act_bf16=True)
+        ex = elementwise_excess(y, want, 1e-3)
+        assert ex <= 0, (n_rows, ex)
+        med = float(np.median(np.abs(y - want))) / float(np.abs(want).max())
+        assert med <= 1e-5, (n_rows, med)
+
+
 @pytest.mark.parametrize("table_dtype", [0, 1])
 def test_predict_into_rows(ctx, table_dtype):
     from paper_2604_09419_gb300 import line as L
