@@ -264,8 +264,9 @@ LINE_API line_status line_train_steps(line_ctx* ctx, int order, int dim, int K, 
  * line_train_steps(order 1) followed by line_train_steps(order 2) with the
  * same arguments, while the GPU overlaps one run's latency-bound phases with
  * the other's.  The order-1 run uses a second stream and workspace owned by
- * the context; work after the call on the context's stream follows both
- * runs.  opts.timing times the call as a whole (total_ms, total_samples =
+ * the context; the two runs are issued in alternate slices of about 2^24
+ * samples, so that a long call keeps work of both orders queued.  Work after
+ * the call on the context's stream follows both runs.  opts.timing times the call as a whole (total_ms, total_samples =
  * 2 n_samples) and not per kernel.  Errors: as line_train_steps. */
 LINE_API line_status line_train_orders(line_ctx* ctx, int dim, int K, const line_lr* lr, uint64_t n_samples,
                                        uint64_t seed, const line_train_opts* opts);
@@ -283,8 +284,10 @@ typedef struct {
  * has no such knobs): for every candidate - gather warps per block (1, 2,
  * 4), batches per pre-pass chunk (about 2^18 samples, and half that), the
  * batched schedule with graph replay (and the persistent one if asked), each
- * listed batch size - it runs an untimed and a timed training run of
- * trial_samples on scratch copies of the order's tables, and writes the
+ * listed batch size - it runs an untimed training run of trial_samples from
+ * io->sample_offset and a timed one of the next trial_samples (fresh rows,
+ * as training meets them) on scratch copies of the order's tables, and
+ * writes the
  * fastest into *io (batch, warps_per_block, chunk_batches, mode, graph; the
  * other fields of *io are used as given).  With topts->both_orders the trials
  * train both orders concurrently (line_train_orders) and the rate counts both.  The tables, the statistics and

@@ -517,12 +517,28 @@ line_status line_train_orders(line_ctx* c, int dim, int K, const line_lr* lr, ui
     CK(cudaEventRecord(c->ev_fork, c->stream), "line_train_orders: fork");
     CK(cudaStreamWaitEvent(c->side, c->ev_fork, 0), "line_train_orders: fork");
     std::string err;
-    cudaError_t e = train_run(a1, c->ws2, c->status, &c->times, c->side, &err);
-    if (e != cudaSuccess) {
-        cudaStreamSynchronize(c->side);
-        return train_fail(c, e, err, "line_train_orders");
+    // Both orders in alternate slices of about 2^24 samples (whole pre-pass
+    // chunks): order 1's slice on the side stream, then order 2's.  The
+    // launch queues then always hold work of both orders.  Enqueuing one
+    // order's whole run first would, once a long run fills the queues, hold
+    // the host inside order 1 and train the orders one after the other.
+    // Splitting at whole batches leaves the tables bitwise unchanged.
+    const uint64_t chunk =
+        (uint64_t)(a1.chunk_batches > 0 ? a1.chunk_batches : std::max<int64_t>(1, ((int64_t)1 << 18) / a1.batch)) *
+        (uint64_t)a1.batch;
+    const uint64_t slice = std::max<uint64_t>(chunk, ((uint64_t)1 << 24) / chunk * chunk);
+    cudaError_t e = cudaSuccess;
+    for (uint64_t t0 = a1.t_begin; t0 < a1.t_end && e == cudaSuccess; t0 += slice) {
+        TrainArgs s1 = a1, s2 = a2;
+        s1.t_begin = s2.t_begin = t0;
+        s1.t_end = s2.t_end = std::min<uint64_t>(a1.t_end, t0 + slice);
+        e = train_run(s1, c->ws2, c->status, &c->times, c->side, &err);
+        if (e != cudaSuccess) {
+            cudaStreamSynchronize(c->side);
+            return train_fail(c, e, err, "line_train_orders");
+        }
+        e = train_run(s2, c->ws, c->status, &c->times, c->stream, &err);
     }
-    e = train_run(a2, c->ws, c->status, &c->times, c->stream, &err);
     // the caller's stream continues after both
     cudaError_t ej = cudaEventRecord(c->ev_join, c->side);
     if (ej == cudaSuccess) ej = cudaStreamWaitEvent(c->stream, c->ev_join, 0);

@@ -1,7 +1,9 @@
 // Autotuner of the training launch configuration: times short training runs
 // of each candidate (gather warps per block, batches per pre-pass chunk,
 // schedule, and optionally the batch size) on scratch copies of the tables,
-// and returns the fastest.  The caller's tables are not modified.
+// and returns the fastest.  Each candidate trains an untimed window of
+// samples, then is timed on the following window (fresh rows, as in
+// training).  The caller's tables are not modified.
 #include <cstring>
 #include <vector>
 
@@ -105,15 +107,19 @@ line_status line_autotune(line_ctx* c, int order, int dim, int K, const line_lr*
         // at least four chunks, or the requested count, rounded to whole batches
         uint64_t n = to.trial_samples ? to.trial_samples : (uint64_t)4 * cd.cb * cd.batch;
         n = (n + cd.batch - 1) / cd.batch * cd.batch;
-        // one untimed run (allocations, graph capture), then the timed one
-        auto trial = [&] {
+        // one untimed run (allocations, graph capture), then the timed one on
+        // the next n samples: a repeat of the same samples would find their
+        // rows in L2 and rate every candidate above what training sees
+        const uint64_t off0 = io->sample_offset;
+        auto trial = [&](uint64_t offset) {
+            o.sample_offset = offset;
             return to.both_orders ? line_train_orders(c, dim, K, lr, n, 0x5EED, &o)
                                   : line_train_steps(c, order, dim, K, lr, n, 0x5EED, &o);
         };
-        st = trial();
+        st = trial(off0);
         if (st) break;
         if ((e = cudaEventRecord(e0, c->stream)) != cudaSuccess) break;
-        st = trial();
+        st = trial(off0 + n);
         if (st) break;
         if ((e = cudaEventRecord(e1, c->stream)) != cudaSuccess) break;
         if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;

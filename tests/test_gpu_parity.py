@@ -180,6 +180,30 @@ def test_autotune_keeps_tables_and_returns_a_valid_configuration(ctx):
     assert np.array_equal(V1, X1) and np.array_equal(V2, X2) and np.array_equal(W2, Y2)
 
 
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_train_orders_long_call_equals_two_sequential_calls(ctx, dtype):
+    """A call longer than one slice (the orders are issued in alternate
+    slices of about 2^24 samples) with a ragged last batch: bitwise the
+    tables of one train_steps call per order."""
+    g = G.graph("rmat14")
+    G.upload(ctx, g)
+    n = (1 << 24) + 3 * 4096 + 1000 + 17
+    B = 4096
+    ctx.init_embeddings(1, 16, dtype, seed=1)
+    ctx.init_embeddings(2, 16, dtype, seed=2)
+    ctx.train_steps(1, 16, 5, n, 9, batch=B, total=n)
+    ctx.train_steps(2, 16, 5, n, 9, batch=B, total=n)
+    want1, _ = G.tables(ctx, g, 1, 16)
+    want2 = G.tables(ctx, g, 2, 16)
+    ctx.init_embeddings(1, 16, dtype, seed=1)
+    ctx.init_embeddings(2, 16, dtype, seed=2)
+    ctx.train_orders(16, 5, n, 9, batch=B, total=n)
+    got1, _ = G.tables(ctx, g, 1, 16)
+    got2 = G.tables(ctx, g, 2, 16)
+    assert np.array_equal(want1, got1)
+    assert np.array_equal(want2[0], got2[0]) and np.array_equal(want2[1], got2[1])
+
+
 @pytest.mark.parametrize("dtype,cb,dim,K,extra", [(0, 0, 64, 5, {}), (0, 3, 64, 5, {}), (1, 2, 64, 5, {}),
                                                    (0, 0, 128, 5, {}), (0, 3, 128, 5, {}), (1, 2, 128, 5, {}),
                                                    (1, 0, 128, 5, {}), (0, 2, 128, 3, {"lam": 1e-3, "alpha_neg": 0.5}),
