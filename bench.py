@@ -528,7 +528,7 @@ def warm_compare(scale: int, *, phase0_epochs: int = 10, marks=(0.05, 0.1, 0.2, 
 
     out = {"graph": f"R-MAT scale {scale}", "n_nodes": g.n_nodes, "n_arcs_train": E, "new_nodes": int(len(rows)),
            "phase0_epochs": phase0_epochs, "target_auc": target, "fp32_final_auc": fp32_final,
-           "target_loss": loss_ref, "fit_s": t_fit, "arrival_s": t_arr,
+           "target_loss": loss_ref, "fit_s": t_fit, "arrival_s": t_arr, "fit_parts_s": fit, "arrival_parts_s": arrival,
            "bf16_warm_wins_from_arrival_fit_included": won("from_arrival_s"),
            "bf16_warm_wins_from_phase0_start": won("from_phase0_start_s"),
            "arms": summary, "generation_s": t_gen,

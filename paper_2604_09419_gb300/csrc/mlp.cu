@@ -54,6 +54,10 @@ struct MlpState {
     void* Hb = nullptr;      // [cap][hidden] activations
     float* Yb = nullptr;     // [cap][dim] outputs, then dL/dy
     float* dH = nullptr;     // [cap][hidden] dL/dh, then dL/da
+    // BF16 hi/lo pairs of dL/dy ([2][cap][dim]) and dL/da ([2][cap][hidden]),
+    // the first operands of the tensor-core weight gradients
+    __nv_bfloat16* gY = nullptr;
+    __nv_bfloat16* gA = nullptr;
     float* part = nullptr;   // split partials
     size_t part_elems = 0;
     double* rowloss = nullptr;  // [cap]
@@ -85,7 +89,8 @@ void mlp_destroy(MlpState* s) {
     for (void* p : {(void*)s->params, (void*)s->grads, (void*)s->m, (void*)s->v, s->X, (void*)s->rows, s->Xb,
                     (void*)s->Tb, (void*)s->A1, s->Hb, (void*)s->Yb, (void*)s->dH, (void*)s->part,
                     (void*)s->rowloss, s->sum_tmp, (void*)s->losses, (void*)s->nodes, (void*)s->kmask,
-                    (void*)s->hubs, (void*)s->frows, (void*)s->flag, (void*)s->wt, (void*)s->w16})
+                    (void*)s->hubs, (void*)s->frows, (void*)s->flag, (void*)s->wt, (void*)s->w16, (void*)s->gY,
+                    (void*)s->gA})
         if (p) cudaFree(p);
     delete s;
 }
@@ -815,10 +820,19 @@ __global__ void k_ep_hidden(float* __restrict__ A1, const float* __restrict__ b1
     }
 }
 
+// BF16 hi/lo pair of v at hl[i] and hl[half + i] (v = hi + lo to about 16
+// significant bits).
+__device__ __forceinline__ void store_hilo(__nv_bfloat16* hl, int64_t half, int64_t i, float v) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    hl[i] = hi;
+    hl[half + i] = __float2bfloat16_rn(v - __bfloat162float(hi));
+}
+
 // Training: y = Y + b2, r = y - t, dY = 2 r / (B D), rowloss[m] = sum r^2
-// (FP64 over the row's lanes in butterfly order).  One warp per row.
+// (FP64 over the row's lanes in butterfly order).  One warp per row.  hl
+// (nullable): dY's BF16 hi/lo pair as well.
 __global__ void k_ep_loss(float* __restrict__ Y, const float* __restrict__ b2, const float* __restrict__ Tb, int64_t M,
-                          int D, float scale, double* __restrict__ rowloss) {
+                          int D, float scale, double* __restrict__ rowloss, __nv_bfloat16* __restrict__ hl) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t m = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); m < M; m += warps) {
@@ -827,6 +841,7 @@ __global__ void k_ep_loss(float* __restrict__ Y, const float* __restrict__ b2, c
             const float r = (Y[m * D + n] + b2[n]) - Tb[m * D + n];
             acc += (double)r * (double)r;
             Y[m * D + n] = scale * r;
+            if (hl) store_hilo(hl, M * D, m * D + n, scale * r);
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
@@ -849,10 +864,14 @@ __global__ void k_ep_predict(const float* __restrict__ Y, const float* __restric
     }
 }
 
-// dA = dH * GELU'(A1), in place.
-__global__ void k_ep_dact(float* __restrict__ dH, const float* __restrict__ A1, int64_t n) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        dH[i] *= gelu_grad(A1[i]);
+// dA = dH * GELU'(A1), in place; hl (nullable): dA's BF16 hi/lo pair as well.
+__global__ void k_ep_dact(float* __restrict__ dH, const float* __restrict__ A1, int64_t n,
+                          __nv_bfloat16* __restrict__ hl) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = dH[i] * gelu_grad(A1[i]);
+        dH[i] = v;
+        if (hl) store_hilo(hl, n, i, v);
+    }
 }
 
 // out[i] = sum_z part[z][i], z ascending.
@@ -864,15 +883,28 @@ __global__ void k_sum_slices(const float* __restrict__ part, int S, int64_t coun
     }
 }
 
-// part[z][n] = sum of X[m][n] over the rows m of slice z, m ascending.
-__global__ void k_colsum_slices(const float* __restrict__ X, int64_t M, int N, int64_t rows_per,
-                                float* __restrict__ part) {
-    const int n = blockIdx.x * blockDim.x + threadIdx.x;
-    if (n >= N) return;
+// part[z][n] = sum of X[m][n] over the rows m of slice z: the slice's rows
+// split into kColGroups consecutive groups, each summed in row order by one
+// thread of a 32-column block, then the groups added in group order.
+constexpr int kColGroups = 8;
+__global__ void __launch_bounds__(32 * kColGroups) k_colsum_slices(const float* __restrict__ X, int64_t M, int N,
+                                                                   int64_t rows_per, float* __restrict__ part) {
+    __shared__ float acc[kColGroups][32];
+    const int n = blockIdx.x * 32 + threadIdx.x;
     const int64_t m0 = (int64_t)blockIdx.y * rows_per, m1 = min(M, m0 + rows_per);
+    const int64_t per = (rows_per + kColGroups - 1) / kColGroups;
+    const int64_t a = m0 + threadIdx.y * per, b = min(m1, a + per);
     float s = 0.0f;
-    for (int64_t m = m0; m < m1; ++m) s += X[m * N + n];
-    part[(size_t)blockIdx.y * N + n] = s;
+    if (n < N)
+        for (int64_t m = a; m < b; ++m) s += X[m * N + n];
+    acc[threadIdx.y][threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.y == 0 && n < N) {
+        float t = 0.0f;
+#pragma unroll
+        for (int y = 0; y < kColGroups; ++y) t += acc[y][threadIdx.x];
+        part[(size_t)blockIdx.y * N + n] = t;
+    }
 }
 
 __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -938,13 +970,13 @@ cudaError_t ensure_cap(MlpState& s, int64_t rows) {
     if (rows <= s.cap) return cudaSuccess;
     const int64_t cap = std::max<int64_t>(rows, 1024);
     for (void** p : {(void**)&s.rows, &s.Xb, (void**)&s.Tb, (void**)&s.A1, &s.Hb, (void**)&s.Yb, (void**)&s.dH,
-                     (void**)&s.part, (void**)&s.rowloss, &s.sum_tmp}) {
+                     (void**)&s.part, (void**)&s.rowloss, &s.sum_tmp, (void**)&s.gY, (void**)&s.gA}) {
         if (*p) cudaFree(*p);
         *p = nullptr;
     }
     s.cap = 0;
     const size_t act = s.act == LINE_DTYPE_F32 ? 4 : 2;
-    const int S = 32;
+    const int S = std::max(32, kWgradMaxSlices);
     s.part_elems = (size_t)S * std::max<int64_t>((int64_t)s.hidden * s.P, (int64_t)s.dim * s.hidden);
     cudaError_t e;
     if ((e = cudaMalloc(&s.rows, sizeof(int32_t) * cap)) != cudaSuccess) return e;
@@ -957,6 +989,10 @@ cudaError_t ensure_cap(MlpState& s, int64_t rows) {
     if ((e = cudaMalloc(&s.part, sizeof(float) * s.part_elems)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&s.rowloss, sizeof(double) * cap)) != cudaSuccess) return e;
     if ((e = cudaMalloc(&s.sum_tmp, fixed_sum_tmp_bytes(cap))) != cudaSuccess) return e;
+    if (s.act == LINE_DTYPE_BF16) {
+        if ((e = cudaMalloc(&s.gY, sizeof(__nv_bfloat16) * 2 * cap * s.dim)) != cudaSuccess) return e;
+        if ((e = cudaMalloc(&s.gA, sizeof(__nv_bfloat16) * 2 * cap * s.hidden)) != cudaSuccess) return e;
+    }
     s.cap = cap;
     return cudaSuccess;
 }
@@ -1033,9 +1069,13 @@ cudaError_t loss_grad(MlpState& s, int64_t B, const Tables& t, uint32_t* status,
     const float* W2 = s.params + L.W2;
     const float* b2 = s.params + L.b2;
     const float scale = (float)(2.0 / ((double)B * s.dim));
-    k_ep_loss<<<grid_of(B * 32, 256), 256, 0, st>>>(s.Yb, b2, s.Tb, B, s.dim, scale, s.rowloss);
-    // dH = dY W2, then dA = dH GELU'(a)
+    // the weight gradients on the tensor cores (BF16 activations, shapes the
+    // kernel takes): dY and dA also as BF16 hi/lo pairs
     const bool tc = s.act == LINE_DTYPE_BF16;
+    const bool wtc = tc && s.gY && s.gA && wgrad_tc_supported(s.dim, s.hidden) && wgrad_tc_supported(s.hidden, s.P) &&
+                     B <= INT32_MAX;
+    k_ep_loss<<<grid_of(B * 32, 256), 256, 0, st>>>(s.Yb, b2, s.Tb, B, s.dim, scale, s.rowloss, wtc ? s.gY : nullptr);
+    // dH = dY W2, then dA = dH GELU'(a)
     const float* W2tT = nullptr;
     if (tc) {
         if ((e = ensure_weight_tiles(s)) != cudaSuccess) return e;
@@ -1047,27 +1087,44 @@ cudaError_t loss_grad(MlpState& s, int64_t B, const Tables& t, uint32_t* status,
     if ((e = gemm<float, float, true, false>(tc, (int)B, s.hidden, s.dim, 1, s.Yb, s.dim, W2, s.hidden, s.dH, status,
                                              st, W2tT)) != cudaSuccess)
         return e;
-    k_ep_dact<<<grid_of(B * s.hidden, 256), 256, 0, st>>>(s.dH, s.A1, B * s.hidden);
+    k_ep_dact<<<grid_of(B * s.hidden, 256), 256, 0, st>>>(s.dH, s.A1, B * s.hidden, wtc ? s.gA : nullptr);
     const TX* Xb = reinterpret_cast<const TX*>(s.Xb);
     const TX* Hb = reinterpret_cast<const TX*>(s.Hb);
     const int S = slices_for(B);
-    // gW2 = dY^T H
-    if ((e = gemm<float, TX, false, false>(tc, s.dim, s.hidden, (int)B, S, s.Yb, s.dim, Hb, s.hidden, s.part, status,
-                                           st)) != cudaSuccess)
-        return e;
-    k_sum_slices<<<grid_of((int64_t)s.dim * s.hidden, 256), 256, 0, st>>>(s.part, S, (int64_t)s.dim * s.hidden,
-                                                                          s.grads + L.W2);
-    // gW1 = dA^T X
-    if ((e = gemm<float, TX, false, false>(tc, s.hidden, s.P, (int)B, S, s.dH, s.hidden, Xb, s.P, s.part, status,
-                                           st)) != cudaSuccess)
-        return e;
-    k_sum_slices<<<grid_of((int64_t)s.hidden * s.P, 256), 256, 0, st>>>(s.part, S, (int64_t)s.hidden * s.P,
-                                                                       s.grads + L.W1);
+    if constexpr (std::is_same<TX, __nv_bfloat16>::value) {
+        if (wtc) {
+            // gW2 = dY^T H and gW1 = dA^T X, split over the batch, the slices
+            // summed in order
+            const int SW = wgrad_slices((int)B);
+            const int64_t nW2 = (int64_t)s.dim * s.hidden, nW1 = (int64_t)s.hidden * s.P;
+            if ((e = wgrad_tc(s.dim, s.hidden, (int)B, s.gY, s.gY + B * s.dim, Hb, s.part, status, st)) != cudaSuccess)
+                return e;
+            k_sum_slices<<<grid_of(nW2, 256), 256, 0, st>>>(s.part, SW, nW2, s.grads + L.W2);
+            if ((e = wgrad_tc(s.hidden, s.P, (int)B, s.gA, s.gA + B * s.hidden, Xb, s.part, status, st)) !=
+                cudaSuccess)
+                return e;
+            k_sum_slices<<<grid_of(nW1, 256), 256, 0, st>>>(s.part, SW, nW1, s.grads + L.W1);
+        }
+    }
+    if (!wtc) {
+        // gW2 = dY^T H
+        if ((e = gemm<float, TX, false, false>(tc, s.dim, s.hidden, (int)B, S, s.Yb, s.dim, Hb, s.hidden, s.part,
+                                               status, st)) != cudaSuccess)
+            return e;
+        k_sum_slices<<<grid_of((int64_t)s.dim * s.hidden, 256), 256, 0, st>>>(s.part, S, (int64_t)s.dim * s.hidden,
+                                                                              s.grads + L.W2);
+        // gW1 = dA^T X
+        if ((e = gemm<float, TX, false, false>(tc, s.hidden, s.P, (int)B, S, s.dH, s.hidden, Xb, s.P, s.part,
+                                               status, st)) != cudaSuccess)
+            return e;
+        k_sum_slices<<<grid_of((int64_t)s.hidden * s.P, 256), 256, 0, st>>>(s.part, S, (int64_t)s.hidden * s.P,
+                                                                           s.grads + L.W1);
+    }
     // bias gradients: column sums in slices of rows, slices summed in order
     const int64_t rows_per = (B + S - 1) / S;
-    k_colsum_slices<<<dim3((s.hidden + 255) / 256, S), 256, 0, st>>>(s.dH, B, s.hidden, rows_per, s.part);
+    k_colsum_slices<<<dim3((s.hidden + 31) / 32, S), dim3(32, kColGroups), 0, st>>>(s.dH, B, s.hidden, rows_per, s.part);
     k_sum_slices<<<grid_of(s.hidden, 256), 256, 0, st>>>(s.part, S, s.hidden, s.grads + L.b1);
-    k_colsum_slices<<<dim3((s.dim + 255) / 256, S), 256, 0, st>>>(s.Yb, B, s.dim, rows_per, s.part);
+    k_colsum_slices<<<dim3((s.dim + 31) / 32, S), dim3(32, kColGroups), 0, st>>>(s.Yb, B, s.dim, rows_per, s.part);
     k_sum_slices<<<grid_of(s.dim, 256), 256, 0, st>>>(s.part, S, s.dim, s.grads + L.b2);
     if ((e = fixed_sum_f64(s.rowloss, B, reinterpret_cast<double*>(s.sum_tmp), loss_dev, st)) != cudaSuccess) return e;
     return cudaGetLastError();

@@ -367,6 +367,171 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fwd_tc(const __grid_consta
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// Weight gradients with BF16 activations: G[m][n] = sum_k A[k][m] B[k][n]
+// over the batch k, for A = dL/dy or dL/da (FP32, given as its BF16 hi/lo
+// pair) and B = h or x (BF16).  A and B are row-major over the batch, so
+// both enter the products M/N-major: TMA boxes of 64 columns x 64 batch rows
+// (128-byte rows, 128-byte swizzle), consecutive 64-column boxes 8 KB apart.
+// Split over K: CTA (z, y) takes batch rows [z Ks, (z+1) Ks) and the 128
+// rows y*128 .. of G, and writes its partial sums to part[z] (summed in z
+// order by the caller).  Warp 0 copies, warp 1 issues the products
+// (A_hi B, then A_lo B, per 16 batch rows), warps 2-5 write the partial.
+// ---------------------------------------------------------------------------
+constexpr int kWK = 64;                     // batch rows per stage
+constexpr uint32_t kWBox = 64 * kWK * 2;    // one 64-column box of a stage: 8 KB
+constexpr int kWStages = 3;
+constexpr int kWThreads = 32 * 6;
+
+struct WgradArgs {
+    int M, N, K, Ks, nkb;  // nkb: 64-column boxes of B
+    float* part;           // [S][M][N]
+    uint32_t* status;
+};
+
+__host__ __device__ constexpr uint32_t w_stage_bytes(int nkb) { return 4 * kWBox + (uint32_t)nkb * kWBox; }
+
+// Descriptor of an M/N-major operand in a stage: start >> 4; 8 KB between
+// 64-column boxes (leading); 1024 bytes between groups of 8 batch rows
+// (stride); version 1; 128-byte swizzle.  16 batch rows further on is 2 KB.
+__device__ __forceinline__ uint64_t desc_mn(uint32_t addr) {
+    return (uint64_t)((addr & 0x3FFFF) >> 4) | ((uint64_t)(kWBox >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+           ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+
+// kind::f16, D = F32, A = B = BF16, both M/N-major (bits 15, 16).
+__host__ __device__ constexpr uint32_t idesc_bf16_mn(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(kFM >> 4) << 24);
+}
+
+__global__ void __launch_bounds__(kWThreads, 1)
+    k_mlp_wgrad_tc(const __grid_constant__ CUtensorMap tmAh, const __grid_constant__ CUtensorMap tmAl,
+                   const __grid_constant__ CUtensorMap tmB, WgradArgs a) {
+    extern __shared__ unsigned char w_raw[];
+    __shared__ __align__(8) uint64_t full[kWStages], empty[kWStages], tfull, fin;
+    __shared__ uint32_t tmem_base;
+    __shared__ uint32_t abort_word;
+    volatile uint32_t* abort_flag = &abort_word;
+    unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(w_raw) + 1023) & ~(uintptr_t)1023);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int N = a.N;
+    const uint32_t sbytes = w_stage_bytes(a.nkb);
+    const int z = blockIdx.x, m0 = blockIdx.y * kFM;
+    const int k0 = z * a.Ks, k1 = min(a.K, k0 + a.Ks);
+    const int nst = (k1 - k0 + kWK - 1) / kWK;
+    uint32_t cols = 32;
+    while (cols < (uint32_t)N) cols <<= 1;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kWStages; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        mbar_init(&tfull, 1);
+        mbar_init(&fin, 1);
+        abort_word = 0u;
+        mbar_init_fence();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_base)),
+                     "r"(cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            uint32_t g = 0;
+            bool ok = true;
+            for (int i = 0; i < nst; ++i, ++g) {
+                const uint32_t st = g % kWStages, j = g / kWStages;
+                if (!fwd_wait(&empty[st], (j & 1u) ^ 1u, abort_flag, a.status)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* sp = base + (size_t)st * sbytes;
+                const int kr = k0 + i * kWK;
+                mbar_arrive_expect_tx(&full[st], sbytes);
+                // stage: A_hi (2 boxes), A_lo (2 boxes), B (nkb boxes)
+                tma_load_2d(sp, &tmAh, m0, kr, &full[st]);
+                tma_load_2d(sp + kWBox, &tmAh, m0 + 64, kr, &full[st]);
+                tma_load_2d(sp + 2 * kWBox, &tmAl, m0, kr, &full[st]);
+                tma_load_2d(sp + 3 * kWBox, &tmAl, m0 + 64, kr, &full[st]);
+                for (int b = 0; b < a.nkb; ++b) tma_load_2d(sp + (4 + b) * kWBox, &tmB, 64 * b, kr, &full[st]);
+            }
+            if (!ok) {
+                for (uint32_t i = 0; i < (uint32_t)kWStages && i < g; ++i) {
+                    const uint32_t gg = g - 1 - i;
+                    fwd_drain(&full[gg % kWStages], (gg / kWStages) & 1u);
+                }
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            const uint32_t idesc = idesc_bf16_mn(N);
+            bool ok = true;
+            for (int i = 0; i < nst; ++i) {
+                const uint32_t st = (uint32_t)i % kWStages, j = (uint32_t)i / kWStages;
+                if (!fwd_wait(&full[st], j & 1u, abort_flag, a.status)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t sp = smem_addr(base + (size_t)st * sbytes);
+#pragma unroll
+                for (int kk = 0; kk < kWK / 16; ++kk) {
+                    const uint32_t off = (uint32_t)kk * 2048u;
+                    const uint64_t db = desc_mn(sp + 4 * kWBox + off);
+                    tc_mma(tmem, desc_mn(sp + off), db, idesc, (i | kk) ? 1u : 0u);
+                    tc_mma(tmem, desc_mn(sp + 2 * kWBox + off), db, idesc, 1u);
+                }
+                tc_commit(&empty[st]);
+            }
+            if (ok && nst > 0) tc_commit(&tfull);
+            tc_commit(&fin);
+            fwd_drain(&fin, 0u);
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3;
+        bool ok = nst > 0 && fwd_wait(&tfull, 0u, abort_flag, a.status);
+        ok = __all_sync(0xFFFFFFFFu, ok);
+        if (ok) {
+            tc_fence_after();
+            const int row = m0 + q * 32 + lane;
+            float* out = a.part + ((size_t)z * a.M + row) * N;
+            for (int c0 = 0; c0 < N; c0 += kFChunk) {
+                uint32_t r[16];
+                tc_ld16(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, r);
+                if (row < a.M) {
+                    float4* p = reinterpret_cast<float4*>(out + c0);
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        p[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                           __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+                }
+            }
+        } else if (nst == 0 && lane == 0) {
+            // an empty slice: zero partial sums
+            for (int rr = 0; rr < 32; ++rr) {
+                const int row = m0 + q * 32 + rr;
+                if (row < a.M)
+                    for (int c = 0; c < N; ++c) a.part[((size_t)z * a.M + row) * N + c] = 0.0f;
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
+    }
+}
+
 // W -> hi/lo BF16 tiles (see fwd_tile_weights).
 __global__ void k_tile_w16(const float* __restrict__ W, int N, int K, __nv_bfloat16* __restrict__ Wt) {
     const int64_t total = (int64_t)N * K;
@@ -475,6 +640,68 @@ cudaError_t fwd_tc(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloa
     a.status = status;
     const int grid = std::min(a.n_tiles, sms);
     k_mlp_fwd_tc<<<grid, kFThreads, smem, s>>>(map, omap, a);
+    return cudaGetLastError();
+}
+
+
+bool wgrad_tc_supported(int M, int N) {
+    return M >= kFM && M % kFM == 0 && N >= 16 && N <= 256 && N % 16 == 0 &&
+           1024 + (size_t)kWStages * w_stage_bytes((N + 63) / 64) <= kFSmemLimit;
+}
+
+namespace {
+// batch rows per slice: a multiple of 64, at most kWgradMaxSlices slices
+int wgrad_rows_per(int K) {
+    const int per = (K + kWgradMaxSlices - 1) / kWgradMaxSlices;
+    return std::max(kWK, (per + kWK - 1) / kWK * kWK);
+}
+}  // namespace
+
+int wgrad_slices(int K) { return K <= 0 ? 0 : (K + wgrad_rows_per(K) - 1) / wgrad_rows_per(K); }
+
+cudaError_t wgrad_tc(int M, int N, int K, const __nv_bfloat16* A_hi, const __nv_bfloat16* A_lo,
+                     const __nv_bfloat16* B, float* part, uint32_t* status, cudaStream_t s) {
+    if (K <= 0) return cudaErrorInvalidValue;
+    if (!wgrad_tc_supported(M, N)) return cudaErrorInvalidValue;
+    PFN_cuTensorMapEncodeTiled_v12000 encode = encode_tiled();
+    if (!encode) return cudaErrorNotSupported;
+    const cuuint32_t elem_strides[2] = {1, 1};
+    const cuuint32_t box[2] = {64, (cuuint32_t)kWK};
+    // row-major over the batch: `cols` columns (inner) x K rows
+    auto make = [&](CUtensorMap* map, const __nv_bfloat16* p, int cols) {
+        const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)K};
+        const cuuint64_t strides[1] = {(cuuint64_t)cols * sizeof(__nv_bfloat16)};
+        return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(p), dims, strides, box,
+                      elem_strides, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    CUtensorMap mah, mal, mb;
+    if (!make(&mah, A_hi, M) || !make(&mal, A_lo, M) || !make(&mb, B, N)) return cudaErrorInvalidValue;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const int nkb = (N + 63) / 64;
+    const size_t smem = 1024 + (size_t)kWStages * w_stage_bytes(nkb);
+    {
+        static std::mutex mu;
+        static size_t granted[64] = {};
+        std::lock_guard<std::mutex> lock(mu);
+        if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+        if (granted[dev] < smem) {
+            e = cudaFuncSetAttribute(k_mlp_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+            granted[dev] = smem;
+        }
+    }
+    WgradArgs w;
+    w.M = M;
+    w.N = N;
+    w.K = K;
+    w.Ks = wgrad_rows_per(K);
+    w.nkb = nkb;
+    w.part = part;
+    w.status = status;
+    k_mlp_wgrad_tc<<<dim3((unsigned)wgrad_slices(K), (unsigned)(M / kFM)), kWThreads, smem, s>>>(mah, mal, mb, w);
     return cudaGetLastError();
 }
 

@@ -1,5 +1,5 @@
-// Forward products of the warm-start MLP with BF16 activations on the
-// tensor cores (mlp_fwd.cu): C = A W^T for an M x K activation matrix A
+// Products of the warm-start MLP with BF16 activations on the tensor cores
+// (mlp_fwd.cu).  Forward: C = A W^T for an M x K activation matrix A
 // (BF16, row-major) and an N x K FP32 weight matrix W, with
 //   hidden layer: A1 = C + b (FP32, optional) and H = GELU(C + b) (BF16);
 //   output layer: Y = C (FP32).
@@ -36,5 +36,17 @@ cudaError_t fwd_tile_weights(const float* W, int N, int K, __nv_bfloat16* Wt, cu
 // leaves the outputs incomplete.
 cudaError_t fwd_tc(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Wt, const float* bias, float* A1,
                    __nv_bfloat16* H, float* Y, uint32_t* status, cudaStream_t s);
+
+// Weight gradients with BF16 activations: part[z][m][n] = sum over the
+// batch rows k of slice z of A[k][m] B[k][n], for A given as its BF16 hi/lo
+// pair (A_hi = bf16(A), A_lo = bf16(A - A_hi), each K x M row-major) and B
+// BF16 (K x N row-major); the caller sums part[0..wgrad_slices(K)) in slice
+// order.  M a multiple of 128, N a multiple of 16 up to 256.  Slices are
+// whole multiples of 64 rows, at most kWgradMaxSlices of them.
+constexpr int kWgradMaxSlices = 64;
+bool wgrad_tc_supported(int M, int N);
+int wgrad_slices(int K);
+cudaError_t wgrad_tc(int M, int N, int K, const __nv_bfloat16* A_hi, const __nv_bfloat16* A_lo,
+                     const __nv_bfloat16* B, float* part, uint32_t* status, cudaStream_t s);
 
 }  // namespace line
