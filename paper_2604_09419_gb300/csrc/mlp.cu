@@ -829,23 +829,24 @@ __device__ __forceinline__ void store_hilo(__nv_bfloat16* hl, int64_t half, int6
 }
 
 // Training: y = Y + b2, r = y - t, dY = 2 r / (B D), rowloss[m] = sum r^2
-// (FP64 over the row's lanes in butterfly order).  One warp per row.  hl
-// (nullable): dY's BF16 hi/lo pair as well.
+// (FP32 per lane in column order, then over the lanes in butterfly order;
+// the rows' sum is FP64).  One warp per row.  hl (nullable): dY's BF16
+// hi/lo pair as well.
 __global__ void k_ep_loss(float* __restrict__ Y, const float* __restrict__ b2, const float* __restrict__ Tb, int64_t M,
                           int D, float scale, double* __restrict__ rowloss, __nv_bfloat16* __restrict__ hl) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t m = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); m < M; m += warps) {
-        double acc = 0.0;
+        float acc = 0.0f;
         for (int n = lane; n < D; n += 32) {
             const float r = (Y[m * D + n] + b2[n]) - Tb[m * D + n];
-            acc += (double)r * (double)r;
+            acc = fmaf(r, r, acc);
             Y[m * D + n] = scale * r;
             if (hl) store_hilo(hl, M * D, m * D + n, scale * r);
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-        if (lane == 0) rowloss[m] = acc;
+        if (lane == 0) rowloss[m] = (double)acc;
     }
 }
 
@@ -878,6 +879,7 @@ __global__ void k_ep_dact(float* __restrict__ dH, const float* __restrict__ A1, 
 __global__ void k_sum_slices(const float* __restrict__ part, int S, int64_t count, float* __restrict__ out) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
         float s = 0.0f;
+#pragma unroll 8
         for (int z = 0; z < S; ++z) s += part[(size_t)z * count + i];
         out[i] = s;
     }
@@ -895,8 +897,10 @@ __global__ void __launch_bounds__(32 * kColGroups) k_colsum_slices(const float* 
     const int64_t per = (rows_per + kColGroups - 1) / kColGroups;
     const int64_t a = m0 + threadIdx.y * per, b = min(m1, a + per);
     float s = 0.0f;
-    if (n < N)
+    if (n < N) {
+#pragma unroll 8
         for (int64_t m = a; m < b; ++m) s += X[m * N + n];
+    }
     acc[threadIdx.y][threadIdx.x] = s;
     __syncthreads();
     if (threadIdx.y == 0 && n < N) {
