@@ -108,6 +108,7 @@ def parse():
     p.add_argument("--fit-nodes", type=int, default=1 << 16, help="warm start: kept nodes the MLP is fit on")
     p.add_argument("--fit-steps", type=int, default=16, help="warm start: Adam steps of the fit")
     p.add_argument("--no-warm", action="store_true", help="default workload: skip the warm-start leg")
+    p.add_argument("--no-c3", action="store_true", help="default workload: skip the directed Chung-Lu leg")
     return p.parse_args()
 
 
@@ -313,8 +314,11 @@ def samples_per_step(args):
     return args.samples_per_step or 16 * (1 << args.scale)
 
 
-def run_dchung22(args):
-    """Directed Chung-Lu, order 2: FP32 at B=4096 vs autotuned BF16."""
+def c3_compare(steps: int, warmup: int, samples_per_step: int = 0) -> dict:
+    """Directed Chung-Lu (4M nodes, 2^26 arc draws), order 2: the FP32 path
+    at B = 4096 against BF16 tables with an autotuned batch (4K-64K), gather
+    warps, chunk size and schedule; `steps` timed steps of |E| samples (or
+    `samples_per_step`) after `warmup` untimed ones, each arm."""
     import torch
 
     from paper_2604_09419_gb300 import inputs as I
@@ -328,7 +332,7 @@ def run_dchung22(args):
                     torch.from_numpy(g.w).cuda())
     E = g.n_arcs
     total = 10 * E
-    S = args.samples_per_step or E
+    S = samples_per_step or E
     peak, peak_kind = peaks()
     res = {}
     for name, dtype in (("fp32", L.DTYPE_F32), ("bf16", L.DTYPE_BF16)):
@@ -340,7 +344,7 @@ def run_dchung22(args):
             o, rate_tuned = ctx.autotune(2, DIM, K, batches=[4096, 8192, 16384, 32768, 65536], try_persistent=True,
                                          total=total, opts=o)
         o.timing = 1
-        for i in range(args.warmup):
+        for i in range(warmup):
             o.sample_offset = i * S
             ctx.train_steps(2, DIM, K, S, 7, total=total, opts=o)
         ctx.reset_stats()
@@ -348,17 +352,17 @@ def run_dchung22(args):
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         with ClockSampler(local) as clk:
             ev0.record(stream)
-            for i in range(args.steps):
-                o.sample_offset = (args.warmup + i) * S
+            for i in range(steps):
+                o.sample_offset = (warmup + i) * S
                 ctx.train_steps(2, DIM, K, S, 7, total=total, opts=o)
             ev1.record(stream)
             torch.cuda.synchronize()
         ms = ev0.elapsed_time(ev1)
         st = ctx.stats()
         row = DIM * (4 if dtype == L.DTYPE_F32 else 2)
-        rate = S * args.steps / (ms / 1e3)
+        rate = S * steps / (ms / 1e3)
         upd = st.update_samples * 14 * row / (st.update_ms / 1e3) / 1e9 if st.update_ms > 0 else None
-        res[name] = {"value": rate, "ms_per_step": ms / args.steps, "batch": int(o.batch),
+        res[name] = {"value": rate, "ms_per_step": ms / steps, "batch": int(o.batch),
                      "mode": "batched" if o.mode == L.MODE_BATCHED else "persistent",
                      "warps_per_block": int(o.warps_per_block), "chunk_batches": int(o.chunk_batches),
                      "autotuned_rate": rate_tuned,
@@ -367,17 +371,27 @@ def run_dchung22(args):
                                   "peak_kind": peak_kind,
                                   "path_frac": rate * (14 * row + 8 + 8 + 8 * K) / 1e9 / peak},
                      "loss_after": ctx.eval_loss(2, K, 99, 1 << 20),
-                     "samples_trained": S * (args.warmup + args.steps), "clocks": clk.summary()}
-    line = {"metric": METRIC, "value": res["bf16"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-            "warmup": args.warmup, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": "dchung22_line_order2_d128_K5_bf16_vs_fp32",
-                       "graph": "directed Chung-Lu, 4,194,304 nodes, 2^26 arc draws, out-weight power law 2.2, "
-                                "lognormal(0,1) arc weights", "n_nodes": g.n_nodes, "n_arcs": E,
-                       "samples_per_step": S, "lr": "0.025 linear decay over 10*|E|"},
-            "fp32": res["fp32"], "bf16": res["bf16"],
-            "loss_rel_diff": (res["bf16"]["loss_after"] - res["fp32"]["loss_after"]) / res["fp32"]["loss_after"]}
-    print(json.dumps(line), flush=True)
+                     "samples_trained": S * (warmup + steps), "clocks": clk.summary()}
+    out = {"workload": "dchung22_line_order2_d128_K5_bf16_vs_fp32",
+           "graph": "directed Chung-Lu, 4,194,304 nodes, 2^26 arc draws, out-weight power law 2.2, "
+                    "lognormal(0,1) arc weights", "n_nodes": g.n_nodes, "n_arcs": E,
+           "samples_per_step": S, "steps": steps, "warmup": warmup, "lr": "0.025 linear decay over 10*|E|",
+           "fp32": res["fp32"], "bf16": res["bf16"],
+           "bf16_over_fp32": res["bf16"]["value"] / res["fp32"]["value"],
+           "loss_rel_diff": (res["bf16"]["loss_after"] - res["fp32"]["loss_after"]) / res["fp32"]["loss_after"]}
     ctx.close()
+    return out
+
+
+def run_dchung22(args):
+    """Directed Chung-Lu, order 2: FP32 at B=4096 vs autotuned BF16."""
+    r = c3_compare(args.steps, args.warmup, args.samples_per_step)
+    line = {"metric": METRIC, "value": r["bf16"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+            "config": {k: r[k] for k in ("workload", "graph", "n_nodes", "n_arcs", "samples_per_step", "lr")},
+            "fp32": r["fp32"], "bf16": r["bf16"], "bf16_over_fp32": r["bf16_over_fp32"],
+            "loss_rel_diff": r["loss_rel_diff"]}
+    print(json.dumps(line), flush=True)
 
 
 def warm_compare(scale: int, *, phase0_epochs: int = 10, marks=(0.05, 0.1, 0.2, 0.35, 0.5, 0.75, 1, 1.5, 2),
@@ -912,6 +926,12 @@ def main():
         w = warm_compare(20, fit_nodes=args.fit_nodes, fit_steps=args.fit_steps, curves=False)
         warm = {"workload": "warm20_rmat20_order2_d128_K5_B4096", **w}
 
+    # configuration C3 (directed Chung-Lu, order 2, BF16 autotuned against
+    # FP32), two timed steps of |E| samples per arm
+    c3 = None
+    if rank == 0 and world == 1 and not walk_len and not args.no_c3:
+        c3 = c3_compare(2, 1)
+
     if rank == 0:
         line = {"metric": metric_of(args), "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -919,7 +939,7 @@ def main():
                 "data": "synthetic",
                 "config": workload_config(args, g), "roofline": roofline, "cpu_baseline": cpu,
                 "cpu_hogwild_context": cpu_mt,
-                "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "warm": warm,
+                "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "warm": warm, "c3": c3,
                 "mode": {L.MODE_BATCHED: "batched", L.MODE_PERSISTENT: "persistent", L.MODE_HOGWILD: "hogwild"}[mode],
                 "orders": args.orders}
         print(json.dumps(line), flush=True)
