@@ -109,6 +109,8 @@ def parse():
     p.add_argument("--fit-steps", type=int, default=16, help="warm start: Adam steps of the fit")
     p.add_argument("--no-warm", action="store_true", help="default workload: skip the warm-start leg")
     p.add_argument("--no-c3", action="store_true", help="default workload: skip the directed Chung-Lu leg")
+    p.add_argument("--no-variants", action="store_true",
+                   help="default workload: skip the BF16 and one-order variants")
     return p.parse_args()
 
 
@@ -879,6 +881,41 @@ def main():
     # library (line_get_stats; a replayed CUDA graph counts its kernels)
     launches = int(st.update_launches + st.prepass_launches)
 
+    # the same workload with BF16 tables, and one order alone (FP32, BF16):
+    # a few timed steps each, after the main measurement, on fresh tables
+    variants = None
+    if (rank == 0 and world == 1 and mode == L.MODE_BATCHED and not walk_len and args.dtype == "fp32"
+            and concurrent and not args.no_variants):
+        variants = {}
+        for name, vdt, both in (("bf16_both_orders", L.DTYPE_BF16, True), ("fp32_one_order", L.DTYPE_F32, False),
+                                ("bf16_one_order", L.DTYPE_BF16, False)):
+            ctx.init_embeddings(1, DIM, vdt, seed=1)
+            ctx.init_embeddings(2, DIM, vdt, seed=2)
+            vst = {"offset": 0}
+
+            def vstep():
+                off = vst["offset"] % total_per_order
+                if both:
+                    ctx.train_orders(DIM, K, S, seed, total=total_per_order, opts=opts(off))
+                else:
+                    ctx.train_steps(2, DIM, K, S, seed, total=total_per_order, opts=opts(off))
+                vst["offset"] += S
+
+            vsteps = 5
+            for _ in range(2):
+                vstep()
+            torch.cuda.synchronize()
+            v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            v0.record(stream)
+            for _ in range(vsteps):
+                vstep()
+            v1.record(stream)
+            torch.cuda.synchronize()
+            vrate = (2 if both else 1) * S * vsteps / (v0.elapsed_time(v1) / 1e3)
+            vpath = 14 * row_bytes("bf16" if vdt == L.DTYPE_BF16 else "fp32") + META_BYTES
+            variants[name] = {"value": vrate, "unit": UNIT, "steps": vsteps, "warmup": 2,
+                              "path_bytes_per_update": vpath, "path_frac": vrate * vpath / 1e9 / peak}
+
     # end to end through the C ABI from pinned host buffers
     e2e = None
     if args.e2e_steps > 0:
@@ -939,7 +976,8 @@ def main():
                 "data": "synthetic",
                 "config": workload_config(args, g), "roofline": roofline, "cpu_baseline": cpu,
                 "cpu_hogwild_context": cpu_mt,
-                "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "warm": warm, "c3": c3,
+                "e2e": e2e, "gpu_launches": launches, "clocks": clk.summary(), "variants": variants, "warm": warm,
+                "c3": c3,
                 "mode": {L.MODE_BATCHED: "batched", L.MODE_PERSISTENT: "persistent", L.MODE_HOGWILD: "hogwild"}[mode],
                 "orders": args.orders}
         print(json.dumps(line), flush=True)
