@@ -181,6 +181,35 @@ def test_loss_and_gradients_match_oracle(ctx, act, tol):
     assert not got["W1"][:, pad].any() and not gw["W1"][:, pad].any()
 
 
+def test_gradients_of_small_and_ragged_batches_bf16(ctx):
+    """BF16 activations at d = 128, hidden 256 (the tensor-core forward and
+    weight-gradient kernels): batches of 1, 17, 64, 65 and 200 rows, so the
+    batch is below, at and just past one 64-row slice of the weight gradient
+    and always a partial 128-row tile of the forward products; every element
+    of every gradient against the oracle."""
+    from paper_2604_09419_gb300 import line as L
+    dim, hidden = 128, 256
+    g, U, known, X = setup(ctx, "rmat14", dim, L.DTYPE_BF16, hidden=hidden)
+    rng = np.random.default_rng(21)
+    p = OM.init_params(dim, hidden, 11)
+    p["b1"] = rng.normal(size=hidden) * 0.1
+    p["b2"] = rng.normal(size=dim) * 0.01
+    pv = flat(p).astype(np.float32)
+    ctx.mlp_set_params(pv)
+    p = unflat(pv, dim, hidden)
+    kept = np.flatnonzero(known)
+    for B in (1, 17, 64, 65, 200):
+        rows = rng.choice(kept, size=B, replace=False).astype(np.int32)
+        grads = np.empty(pv.shape, np.float32)
+        loss = ctx.mlp_grad(rows, grads)
+        Lo, gw = OM.loss_and_grads(p, X[rows], U[rows], act_bf16=True)
+        assert abs(loss - Lo) <= 1e-3 * Lo, (B, loss, Lo)
+        got = unflat(grads, dim, hidden)
+        for k in ("W1", "b1", "W2", "b2"):
+            ex = elementwise_excess(got[k], gw[k], 1e-3)
+            assert ex <= 0, (B, k, ex)
+
+
 def test_training_steps_match_oracle(ctx):
     dim, hidden = 16, 32
     g, U, known, X = setup(ctx, "tiny", dim, 0, hidden=hidden)
