@@ -37,7 +37,8 @@ constexpr int64_t kMlpMaxBatch = 1 << 16;
 struct MlpState {
     int order = 0, dim = 0, hidden = 0, P = 0, act = 0;
     int64_t n_params = 0;
-    float* params = nullptr;  // [W1 (hidden x P) | b1 (hidden) | W2 (dim x hidden) | b2 (dim)]
+    float* params = nullptr;  // [W1 (hidden x P) | b1 (hidden) | W2 (dim x hidden) | b2 (dim)];
+                              // grads, m and v follow in the same allocation
     float* grads = nullptr;
     float* m = nullptr;
     float* v = nullptr;
@@ -58,6 +59,7 @@ struct MlpState {
     // the first operands of the tensor-core weight gradients
     __nv_bfloat16* gY = nullptr;
     __nv_bfloat16* gA = nullptr;
+    void* arena = nullptr;  // the allocation holding every batch buffer above
     float* part = nullptr;   // split partials
     size_t part_elems = 0;
     double* rowloss = nullptr;  // [cap]
@@ -86,11 +88,10 @@ struct MlpState {
 
 void mlp_destroy(MlpState* s) {
     if (!s) return;
-    for (void* p : {(void*)s->params, (void*)s->grads, (void*)s->m, (void*)s->v, s->X, (void*)s->rows, s->Xb,
-                    (void*)s->Tb, (void*)s->A1, s->Hb, (void*)s->Yb, (void*)s->dH, (void*)s->part,
-                    (void*)s->rowloss, s->sum_tmp, (void*)s->losses, (void*)s->nodes, (void*)s->kmask,
-                    (void*)s->hubs, (void*)s->frows, (void*)s->flag, (void*)s->wt, (void*)s->w16, (void*)s->gY,
-                    (void*)s->gA})
+    // params, grads, m and v share one allocation (params first); the
+    // batch buffers share s->arena
+    for (void* p : {(void*)s->params, s->X, s->arena, (void*)s->losses, (void*)s->nodes, (void*)s->kmask,
+                    (void*)s->hubs, (void*)s->frows, (void*)s->flag, (void*)s->wt, (void*)s->w16})
         if (p) cudaFree(p);
     delete s;
 }
@@ -973,30 +974,54 @@ cudaError_t ensure_w16(MlpState& s) {
 cudaError_t ensure_cap(MlpState& s, int64_t rows) {
     if (rows <= s.cap) return cudaSuccess;
     const int64_t cap = std::max<int64_t>(rows, 1024);
-    for (void** p : {(void**)&s.rows, &s.Xb, (void**)&s.Tb, (void**)&s.A1, &s.Hb, (void**)&s.Yb, (void**)&s.dH,
-                     (void**)&s.part, (void**)&s.rowloss, &s.sum_tmp, (void**)&s.gY, (void**)&s.gA}) {
-        if (*p) cudaFree(*p);
-        *p = nullptr;
-    }
+    if (s.arena) cudaFree(s.arena);
+    s.arena = nullptr;
+    s.rows = nullptr;
+    s.Xb = s.Hb = s.sum_tmp = nullptr;
+    s.Tb = s.A1 = s.Yb = s.dH = s.part = nullptr;
+    s.rowloss = nullptr;
+    s.gY = s.gA = nullptr;
     s.cap = 0;
     const size_t act = s.act == LINE_DTYPE_F32 ? 4 : 2;
     const int S = std::max(32, kWgradMaxSlices);
     s.part_elems = (size_t)S * std::max<int64_t>((int64_t)s.hidden * s.P, (int64_t)s.dim * s.hidden);
-    cudaError_t e;
-    if ((e = cudaMalloc(&s.rows, sizeof(int32_t) * cap)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&s.Xb, act * cap * s.P)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&s.Tb, sizeof(float) * cap * s.dim)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&s.A1, sizeof(float) * cap * s.hidden)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&s.Hb, act * cap * s.hidden)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&s.Yb, sizeof(float) * cap * s.dim)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&s.dH, sizeof(float) * cap * s.hidden)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&s.part, sizeof(float) * s.part_elems)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&s.rowloss, sizeof(double) * cap)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&s.sum_tmp, fixed_sum_tmp_bytes(cap))) != cudaSuccess) return e;
-    if (s.act == LINE_DTYPE_BF16) {
-        if ((e = cudaMalloc(&s.gY, sizeof(__nv_bfloat16) * 2 * cap * s.dim)) != cudaSuccess) return e;
-        if ((e = cudaMalloc(&s.gA, sizeof(__nv_bfloat16) * 2 * cap * s.hidden)) != cudaSuccess) return e;
+    // every batch buffer in one allocation, each at a 256-byte boundary
+    const bool hilo = s.act == LINE_DTYPE_BF16;
+    const size_t sizes[] = {sizeof(int32_t) * cap,
+                            act * cap * s.P,
+                            sizeof(float) * cap * s.dim,
+                            sizeof(float) * cap * s.hidden,
+                            act * cap * s.hidden,
+                            sizeof(float) * cap * s.dim,
+                            sizeof(float) * cap * s.hidden,
+                            sizeof(float) * s.part_elems,
+                            sizeof(double) * cap,
+                            fixed_sum_tmp_bytes(cap),
+                            hilo ? sizeof(__nv_bfloat16) * 2 * cap * s.dim : 0,
+                            hilo ? sizeof(__nv_bfloat16) * 2 * cap * s.hidden : 0};
+    constexpr int kBufs = sizeof(sizes) / sizeof(sizes[0]);
+    size_t off[kBufs], total = 0;
+    for (int i = 0; i < kBufs; ++i) {
+        off[i] = total;
+        total += (sizes[i] + 255) / 256 * 256;
     }
+    void* arena = nullptr;
+    cudaError_t e = cudaMalloc(&arena, total);
+    if (e != cudaSuccess) return e;
+    unsigned char* b = reinterpret_cast<unsigned char*>(arena);
+    s.arena = arena;
+    s.rows = reinterpret_cast<int32_t*>(b + off[0]);
+    s.Xb = b + off[1];
+    s.Tb = reinterpret_cast<float*>(b + off[2]);
+    s.A1 = reinterpret_cast<float*>(b + off[3]);
+    s.Hb = b + off[4];
+    s.Yb = reinterpret_cast<float*>(b + off[5]);
+    s.dH = reinterpret_cast<float*>(b + off[6]);
+    s.part = reinterpret_cast<float*>(b + off[7]);
+    s.rowloss = reinterpret_cast<double*>(b + off[8]);
+    s.sum_tmp = b + off[9];
+    s.gY = hilo ? reinterpret_cast<__nv_bfloat16*>(b + off[10]) : nullptr;
+    s.gA = hilo ? reinterpret_cast<__nv_bfloat16*>(b + off[11]) : nullptr;
     s.cap = cap;
     return cudaSuccess;
 }
@@ -1193,10 +1218,15 @@ line_status line_mlp_create(line_ctx* c, int order, int hidden, int act_dtype, u
     const Layout L(*s);
     s->n_params = L.n;
     const size_t pb = sizeof(float) * L.n;
-    cudaError_t e = cudaMalloc(&s->params, pb);
-    if (e == cudaSuccess) e = cudaMalloc(&s->grads, pb);
-    if (e == cudaSuccess) e = cudaMalloc(&s->m, pb);
-    if (e == cudaSuccess) e = cudaMalloc(&s->v, pb);
+    // params, grads, m and v in one allocation, each at a 256-byte boundary
+    const size_t pbs = (pb + 255) / 256 * 256;
+    cudaError_t e = cudaMalloc(&s->params, 4 * pbs);
+    if (e == cudaSuccess) {
+        unsigned char* b = reinterpret_cast<unsigned char*>(s->params);
+        s->grads = reinterpret_cast<float*>(b + pbs);
+        s->m = reinterpret_cast<float*>(b + 2 * pbs);
+        s->v = reinterpret_cast<float*>(b + 3 * pbs);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&s->X, (size_t)c->n_nodes * s->P * elem_size(act_dtype));
     // inputs not yet computed are zero (line_mlp_features_rows may compute a subset)
     if (e == cudaSuccess) e = cudaMemsetAsync(s->X, 0, (size_t)c->n_nodes * s->P * elem_size(act_dtype), c->stream);
