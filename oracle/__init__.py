@@ -98,6 +98,8 @@ def lib():
             L.orc_train_bf16.restype = _int
             L.orc_splitmix64_mix.argtypes = [_u64]
             L.orc_splitmix64_mix.restype = _u64
+            L.orc_fmix32.argtypes = [_u32]
+            L.orc_fmix32.restype = _u32
             L.orc_sr_bits.argtypes = [_u64, _u32, _u64, _u64, _u32]
             L.orc_sr_bits.restype = _u64
             L.orc_bf16_sr_bits.argtypes = [ctypes.c_float, _u32]
@@ -282,9 +284,16 @@ def splitmix64_mix(z: int) -> int:
     return int(lib().orc_splitmix64_mix(z & 0xFFFFFFFFFFFFFFFF))
 
 
+def fmix32(h: int) -> int:
+    """MurmurHash3's 32-bit finaliser (Appleby)."""
+    return int(lib().orc_fmix32(h & 0xFFFFFFFF))
+
+
 def sr_bits(seed: int, table: int, row: int, t0: int, k4: int) -> int:
     """The 64 stochastic-rounding bits of values 4 k4 .. 4 k4 + 3 of `row`
-    of table `table` (0 U, 1 C) written by the batch starting at sample t0."""
+    of table `table` (0 U, 1 C) written by the batch starting at sample t0:
+    fmix32 of (lo32(s) + (2 row + table) 0x9E3779B1 + 2 k4 + j) for j = 0, 1
+    (low, high word), with s the SplitMix64 output of seed ^ t0 0x9E3779B97F4A7C15."""
     return int(lib().orc_sr_bits(seed & 0xFFFFFFFFFFFFFFFF, table, row, t0, k4))
 
 

@@ -432,11 +432,13 @@ double orc_batch_lr(double lr0, int schedule, double floor_frac, uint64_t T, uin
 /* mantissa and the low 16 bits are dropped; Inf and NaN pass unchanged.     */
 /* Over the 2^16 equally likely r the expected BF16 value is the FP32 value  */
 /* exactly.  The bits for the values 4k4 .. 4k4+3 of `row` of table `table`  */
-/* (0: U, 1: C) written by the batch whose first sample is t0 are the        */
-/* SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014) of the key   */
-/*   seed ^ (t0 * 0x9E3779B97F4A7C15) ^                                      */
-/*   (((row << 16) | (table << 15) | k4) * 0xD1B54A32D192ED03)               */
-/* (mod 2^64); value i of the four takes bits [16 i, 16 i + 16).             */
+/* (0: U, 1: C) written by the batch whose first sample is t0: with the      */
+/* batch's salt s = SplitMix64 output function (Steele, Lea, Flood, OOPSLA   */
+/* 2014) of seed ^ (t0 * 0x9E3779B97F4A7C15) (mod 2^64), the words           */
+/*   w_j = fmix32(lo32(s) + (2 row + table) * 0x9E3779B1 + 2 k4 + j)         */
+/* (mod 2^32, j = 0, 1; fmix32 is the 32-bit finaliser of Appleby's          */
+/* MurmurHash3) form the 64 bits w_1 : w_0; value i of the four takes bits   */
+/* [16 i, 16 i + 16).                                                        */
 /* ------------------------------------------------------------------------ */
 uint64_t orc_splitmix64_mix(uint64_t z) {
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -444,9 +446,21 @@ uint64_t orc_splitmix64_mix(uint64_t z) {
     return z ^ (z >> 31);
 }
 
+/* MurmurHash3's 32-bit finaliser (fmix32). */
+uint32_t orc_fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
 uint64_t orc_sr_bits(uint64_t seed, uint32_t table, uint64_t row, uint64_t t0, uint32_t k4) {
-    uint64_t key = ((row << 16) | ((uint64_t)table << 15) | (uint64_t)k4) * 0xD1B54A32D192ED03ull;
-    return orc_splitmix64_mix(seed ^ (t0 * 0x9E3779B97F4A7C15ull) ^ key);
+    const uint64_t s = orc_splitmix64_mix(seed ^ (t0 * 0x9E3779B97F4A7C15ull));
+    const uint32_t base = (uint32_t)s + (uint32_t)(2 * row + table) * 0x9E3779B1u + 2u * k4;
+    const uint32_t w0 = orc_fmix32(base), w1 = orc_fmix32(base + 1u);
+    return ((uint64_t)w1 << 32) | w0;
 }
 
 static uint32_t f32_bits(float x) {

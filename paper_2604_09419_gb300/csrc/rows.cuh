@@ -52,16 +52,30 @@ __device__ __forceinline__ void load_row(const void* table, int64_t row, int lig
     }
 }
 
+// MurmurHash3's 32-bit finaliser (Appleby).
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85EBCA6Bu;
+    h ^= h >> 13;
+    h *= 0xC2B2AE35u;
+    h ^= h >> 16;
+    return h;
+}
+
 // 64 random bits for the stochastic rounding of the 4 values at columns
 // 4 k4 .. 4 k4 + 3 of `row` of table `table_id`, written by the batch that
-// starts at sample t0: the SplitMix64 output function (Steele, Lea, Flood,
-// OOPSLA 2014) of a key built from the seed, the batch, the row and k4.
+// starts at sample t0: with the batch's salt s, the SplitMix64 output
+// function (Steele, Lea, Flood, OOPSLA 2014) of seed ^ t0 0x9E3779B97F4A7C15
+// (the same for every row of the batch, so it is computed once per thread),
+// the words w_j = fmix32(lo32(s) + (2 row + table) 0x9E3779B1 + 2 k4 + j),
+// j = 0 (low) and 1 (high).
 __device__ __forceinline__ uint64_t sr_bits(uint64_t seed, uint32_t table_id, uint64_t row, uint64_t t0, uint32_t k4) {
-    uint64_t z = seed ^ (t0 * 0x9E3779B97F4A7C15ull) ^
-                 (((row << 16) | ((uint64_t)table_id << 15) | (uint64_t)k4) * 0xD1B54A32D192ED03ull);
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
+    uint64_t s = seed ^ (t0 * 0x9E3779B97F4A7C15ull);
+    s = (s ^ (s >> 30)) * 0xBF58476D1CE4E5B9ull;
+    s = (s ^ (s >> 27)) * 0x94D049BB133111EBull;
+    s ^= s >> 31;
+    const uint32_t base = (uint32_t)s + (uint32_t)(2 * row + table_id) * 0x9E3779B1u + 2u * k4;
+    return ((uint64_t)fmix32(base + 1u) << 32) | fmix32(base);
 }
 
 // Store a row part; BF16 rounds stochastically: value i of a 4-value vector

@@ -1,7 +1,9 @@
 """Pins of the oracle's BF16 storage mode (a target addition; the paper's
-tables are FP32): the SplitMix64 output function, the stochastic-rounding
-rule, round-to-nearest for initial tables, and the wiring of both into the
-minibatch oracle (Algorithm 1 with the batch-summed deltas of Eq. 4).
+tables are FP32): the SplitMix64 output function and MurmurHash3's fmix32
+(the two parts of the rounding bits) against published vectors, the
+statistics of the bits, the stochastic-rounding rule, round-to-nearest for
+initial tables, and the wiring of both into the minibatch oracle
+(Algorithm 1 with the batch-summed deltas of Eq. 4).
 
 Runs on the CPU (no GPU)."""
 import os
@@ -33,6 +35,60 @@ def test_splitmix64_published_vectors():
         x = (x + GAMMA) & M64
         got.append(O.splitmix64_mix(x))
     assert got == want
+
+
+MURMUR = os.path.join(os.path.dirname(__file__), "golden", "murmur3_x86_32.txt")
+
+
+def murmur3_x86_32(data: bytes, seed: int) -> int:
+    """MurmurHash3_x86_32 (Appleby): 4-byte blocks mixed into the state, the
+    tail, the length, then the finaliser - here the oracle's fmix32."""
+    M = 0xFFFFFFFF
+    c1, c2 = 0xCC9E2D51, 0x1B873593
+
+    def rotl(x, r):
+        return ((x << r) | (x >> (32 - r))) & M
+
+    h = seed
+    n = len(data)
+    for i in range(0, n - n % 4, 4):
+        k = int.from_bytes(data[i:i + 4], "little")
+        h ^= (rotl((k * c1) & M, 15) * c2) & M
+        h = (rotl(h, 13) * 5 + 0xE6546B64) & M
+    tail = data[n - n % 4:]
+    if tail:
+        k = int.from_bytes(tail, "little")
+        h ^= (rotl((k * c1) & M, 15) * c2) & M
+    return O.fmix32(h ^ n)
+
+
+def test_fmix32_published_vectors():
+    n = 0
+    for line in open(MURMUR):
+        if not line.strip() or line.startswith("#"):
+            continue
+        data_hex, seed_hex, want_hex = line.split()
+        data = b"" if data_hex == "-" else bytes.fromhex(data_hex)
+        seed, want = int(seed_hex, 16), int(want_hex, 16)
+        if not data:
+            assert O.fmix32(seed) == want, (seed_hex, want_hex)
+        assert murmur3_x86_32(data, seed) == want, (data_hex, seed_hex, want_hex)
+        n += 1
+    assert n == 7
+
+
+def test_sr_bits_uncorrelated_across_batches():
+    # the property stochastic rounding relies on over training: for a fixed
+    # row and column group, the bits of consecutive batches are uniform and
+    # independent (lag-1 correlation and chi-square over 64 bins)
+    for table, row, k4 in ((0, 0, 0), (1, 12345, 17), (0, 1 << 20, 31)):
+        w = np.array([O.sr_bits(9, table, row, 4096 * b, k4) for b in range(6000)], np.uint64)
+        for i in range(4):
+            r = ((w >> np.uint64(16 * i)) & np.uint64(0xFFFF)).astype(np.float64)
+            assert abs(np.corrcoef(r[:-1], r[1:])[0, 1]) < 0.06
+            hist = np.bincount((r.astype(np.int64) >> 10), minlength=64)
+            exp = r.size / 64
+            assert ((hist - exp) ** 2 / exp).sum() < 110  # 63 degrees of freedom, p ~ 0.0002
 
 
 def test_sr_bits_uniform_and_distinct():
