@@ -95,21 +95,46 @@ void free_tables(Tables& t) {
     t = Tables{};
 }
 
+// The graph is gone: its walk tables are dropped (they are built again for
+// the next graph on first use); the graph and alias buffers stay allocated
+// for the next build (release_graph frees them).
 void free_graph(line_ctx* c, bool keep_tables = false) {
-    for (void* p : {(void*)c->src, (void*)c->dst, (void*)c->deg, (void*)c->edge_tab, (void*)c->neg_tab, (void*)c->w,
-                    (void*)c->row_ptr, (void*)c->cw})
+    for (void* p : {(void*)c->row_ptr, (void*)c->cw})
         if (p) cudaFree(p);
-    c->src = c->dst = nullptr;
-    c->deg = nullptr;
-    c->w = nullptr;
     c->row_ptr = nullptr;
     c->cw = nullptr;
-    c->edge_tab = c->neg_tab = nullptr;
+    c->w = nullptr;
     c->has_graph = false;
     if (keep_tables) return;
     mlp_destroy(c->mlp);
     c->mlp = nullptr;
     for (auto& t : c->tab) free_tables(t);
+}
+
+void release_graph(line_ctx* c) {
+    free_graph(c);
+    for (void* p : {(void*)c->src, (void*)c->dst, (void*)c->deg, (void*)c->edge_tab, (void*)c->neg_tab, (void*)c->w_buf,
+                    (void*)c->alias_x, c->alias_tmp})
+        if (p) cudaFree(p);
+    c->src = c->dst = nullptr;
+    c->deg = nullptr;
+    c->edge_tab = c->neg_tab = nullptr;
+    c->w_buf = nullptr;
+    c->alias_x = nullptr;
+    c->alias_tmp = nullptr;
+    c->src_cap = c->dst_cap = c->edge_cap = c->neg_cap = c->deg_cap = c->w_cap = c->x_cap = c->tmp_cap = 0;
+}
+
+// *p holds at least `bytes` (a larger earlier allocation is kept).
+template <typename T>
+cudaError_t grow(T** p, size_t* cap, size_t bytes) {
+    if (*p && *cap >= bytes) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (e == cudaSuccess) *cap = bytes;
+    return e;
 }
 
 bool dim_ok(int dim) { return dim == 16 || dim == 32 || dim == 64 || dim == 128 || dim == 256; }
@@ -186,7 +211,7 @@ void line_destroy(line_ctx* c) {
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
     else cudaDeviceSynchronize();
-    free_graph(c);
+    release_graph(c);
     workspace_destroy(c->ws);
     workspace_destroy(c->ws2);
     if (c->side) cudaStreamDestroy(c->side);
@@ -214,21 +239,23 @@ line_status line_build_alias(line_ctx* c, const line_graph_desc* g) {
     free_graph(c, keep);
     const int64_t n = g->n_nodes, m = g->n_arcs;
     cudaStream_t s = c->stream;
-    CK(cudaMalloc(&c->src, sizeof(int32_t) * m), "graph allocation");
-    CK(cudaMalloc(&c->dst, sizeof(int32_t) * m), "graph allocation");
-    CK(cudaMalloc(&c->edge_tab, sizeof(uint2) * m), "alias allocation");
-    CK(cudaMalloc(&c->neg_tab, sizeof(uint2) * n), "alias allocation");
-    CK(cudaMalloc(&c->deg, sizeof(float) * n), "degree allocation");
+    // the buffers of an earlier graph are reused when large enough; the
+    // work queued on the stream before this call may still read them, and
+    // the stream orders it before the copies below
+    CK(grow(&c->src, &c->src_cap, sizeof(int32_t) * m), "graph allocation");
+    CK(grow(&c->dst, &c->dst_cap, sizeof(int32_t) * m), "graph allocation");
+    CK(grow(&c->edge_tab, &c->edge_cap, sizeof(uint2) * m), "alias allocation");
+    CK(grow(&c->neg_tab, &c->neg_cap, sizeof(uint2) * n), "alias allocation");
+    CK(grow(&c->deg, &c->deg_cap, sizeof(float) * n), "degree allocation");
     CK(cudaMemcpyAsync(c->src, g->src, sizeof(int32_t) * m, cudaMemcpyDefault, s), "graph copy");
     CK(cudaMemcpyAsync(c->dst, g->dst, sizeof(int32_t) * m, cudaMemcpyDefault, s), "graph copy");
     float* w = nullptr;
-    void* tmp = nullptr;
-    double* x = nullptr;
     line_status result = LINE_OK;
     do {
         cudaError_t e;
         if (g->w) {
-            if ((e = cudaMalloc(&w, sizeof(float) * m)) != cudaSuccess) { result = cuda_fail(c, e, "weights"); break; }
+            if ((e = grow(&c->w_buf, &c->w_cap, sizeof(float) * m)) != cudaSuccess) { result = cuda_fail(c, e, "weights"); break; }
+            w = c->w_buf;
             if ((e = cudaMemcpyAsync(w, g->w, sizeof(float) * m, cudaMemcpyDefault, s)) != cudaSuccess) {
                 result = cuda_fail(c, e, "weights copy");
                 break;
@@ -237,8 +264,10 @@ line_status line_build_alias(line_ctx* c, const line_graph_desc* g) {
         if ((e = validate_graph(n, m, c->src, c->dst, w, c->status, s)) != cudaSuccess) { result = cuda_fail(c, e, "validate"); break; }
         if ((result = check_status(c, "line_build_alias"))) break;
         const int64_t big = n > m ? n : m;
-        if ((e = cudaMalloc(&x, sizeof(double) * big)) != cudaSuccess) { result = cuda_fail(c, e, "alias scratch"); break; }
-        if ((e = cudaMalloc(&tmp, alias_build_tmp_bytes(big))) != cudaSuccess) { result = cuda_fail(c, e, "alias scratch"); break; }
+        if ((e = grow(&c->alias_x, &c->x_cap, sizeof(double) * big)) != cudaSuccess) { result = cuda_fail(c, e, "alias scratch"); break; }
+        if ((e = grow(&c->alias_tmp, &c->tmp_cap, alias_build_tmp_bytes(big))) != cudaSuccess) { result = cuda_fail(c, e, "alias scratch"); break; }
+        double* x = c->alias_x;
+        void* tmp = c->alias_tmp;
         // edge table: arc weights (Algorithm 3)
         if ((e = edge_weights(m, w, x, s)) != cudaSuccess) { result = cuda_fail(c, e, "edge weights"); break; }
         if ((e = alias_build(x, m, c->edge_tab, tmp, c->status, s)) != cudaSuccess) { result = cuda_fail(c, e, "edge alias"); break; }
@@ -248,9 +277,7 @@ line_status line_build_alias(line_ctx* c, const line_graph_desc* g) {
         if ((e = alias_build(x, n, c->neg_tab, tmp, c->status, s)) != cudaSuccess) { result = cuda_fail(c, e, "negative alias"); break; }
         if ((result = check_status(c, "line_build_alias (negatives)"))) break;
     } while (false);
-    c->w = w;  // kept for the walk sampler's tables (freed with the graph)
-    if (x) cudaFree(x);
-    if (tmp) cudaFree(tmp);
+    c->w = w;  // kept for the walk sampler's tables (null: unit weights)
     if (result != LINE_OK) {
         cudaStreamSynchronize(s);
         free_graph(c);

@@ -43,6 +43,12 @@ struct line_ctx {
     double* cw = nullptr;
     uint2* edge_tab = nullptr;
     uint2* neg_tab = nullptr;
+    // bytes allocated behind src, dst, edge_tab, neg_tab, deg and the weights,
+    // and the alias build's scratch: a later graph that fits reuses them
+    size_t src_cap = 0, dst_cap = 0, edge_cap = 0, neg_cap = 0, deg_cap = 0, w_cap = 0, x_cap = 0, tmp_cap = 0;
+    float* w_buf = nullptr;     // the weights' allocation (w points here for a weighted graph)
+    double* alias_x = nullptr;  // alias build scratch
+    void* alias_tmp = nullptr;
     // tables by order (index 1 and 2)
     line::Tables tab[3];
     // device status word and small scratch

@@ -37,6 +37,28 @@ def test_alias_tables_bit_exact(ctx, name):
     assert np.array_equal(thr, T.thr_n) and np.array_equal(alias, T.alias_n)
 
 
+def test_alias_rebuilds_in_one_context(ctx):
+    """One context, graphs of growing, shrinking and equal sizes, weighted
+    and unit-weight (the graph buffers of an earlier build are reused when
+    large enough): both alias tables bit-exact after every build."""
+    import dataclasses
+
+    import torch
+
+    from paper_2604_09419_gb300 import line as L
+    tiny = G.graph("tiny")
+    unit = dataclasses.replace(tiny, w=np.ones(tiny.n_arcs, np.float32))
+    seq = [("rmat14", G.graph("rmat14"), True), ("tiny", tiny, True), ("tiny unit", unit, False),
+           ("dchung", G.graph("dchung"), True), ("rmat14", G.graph("rmat14"), True)]
+    for name, g, weighted in seq:
+        T = O.Tables(g)
+        w = torch.from_numpy(g.w).cuda() if weighted else None
+        ctx.build_alias(g.n_nodes, torch.from_numpy(g.src).cuda(), torch.from_numpy(g.dst).cuda(), w)
+        for which, (thr_o, alias_o) in ((L.TABLE_EDGE, (T.thr_e, T.alias_e)), (L.TABLE_NEG, (T.thr_n, T.alias_n))):
+            thr, alias = G.gpu_alias(ctx, g, which)
+            assert np.array_equal(thr, thr_o) and np.array_equal(alias, alias_o), (name, which)
+
+
 def test_alias_host_buffers(ctx):
     from paper_2604_09419_gb300 import line as L
     g = G.graph("rmat14")
