@@ -189,7 +189,9 @@ LINE_API const char* line_last_error(const line_ctx* ctx);
  * keeps its own device copy of src, dst and w (4 bytes per arc each; w only
  * when given), the alias tables and the weighted degrees; per-node arc
  * offsets (8 bytes per node) and the walk sampler's weight sums (8 bytes per
- * arc) are added on first use.
+ * arc) are added on first use.  A later graph reuses these buffers (and the
+ * build's FP64 scratch, 8 bytes per arc or node) when they are large enough;
+ * they are freed by line_destroy.
  * Errors: LINE_ERR_ARG (sizes), LINE_ERR_VALIDATE (unsorted src, ids out of
  * range, non-positive or non-finite weights, a node set with no positive
  * weight), LINE_ERR_OOM. */
