@@ -961,7 +961,8 @@ bool fwd_fast(const MlpState& s) {
 }
 
 cudaError_t ensure_w16(MlpState& s) {
-    const size_t need = fwd_w16_elems(s.hidden, s.P) + fwd_w16_elems(s.dim, s.hidden);
+    // W1, W2 and W2^T as hi/lo tiles
+    const size_t need = fwd_w16_elems(s.hidden, s.P) + 2 * fwd_w16_elems(s.dim, s.hidden);
     if (s.w16 && s.w16_elems >= need) return cudaSuccess;
     if (s.w16) cudaFree(s.w16);
     s.w16 = nullptr;
@@ -1104,19 +1105,29 @@ cudaError_t loss_grad(MlpState& s, int64_t B, const Tables& t, uint32_t* status,
     const bool wtc = tc && s.gY && s.gA && wgrad_tc_supported(s.dim, s.hidden) && wgrad_tc_supported(s.hidden, s.P) &&
                      B <= INT32_MAX;
     k_ep_loss<<<grid_of(B * 32, 256), 256, 0, st>>>(s.Yb, b2, s.Tb, B, s.dim, scale, s.rowloss, wtc ? s.gY : nullptr);
-    // dH = dY W2, then dA = dH GELU'(a)
-    const float* W2tT = nullptr;
-    if (tc) {
-        if ((e = ensure_weight_tiles(s)) != cudaSuccess) return e;
-        float* dst = s.wt + tile_b_elems(s.hidden, s.P) + tile_b_elems(s.dim, s.hidden);
-        k_tile_b<false><<<grid_of((int64_t)tile_b_elems(s.hidden, s.dim), 256), 256, 0, st>>>(
-            W2, s.hidden, s.hidden, s.dim, tc_tile_n(s.hidden), dst);
-        W2tT = dst;
+    // dH = dY W2, then dA = dH GELU'(a): with the tensor-core weight
+    // gradients, one pass on the forward kernel (dY as its hi/lo pair, W2^T as
+    // hi/lo tiles) that writes dA and its hi/lo pair
+    if (wtc && fwd_fast(s) && s.w16 && dact_tc_supported(s.hidden, s.dim)) {
+        __nv_bfloat16* w2t = s.w16 + fwd_w16_elems(s.hidden, s.P) + fwd_w16_elems(s.dim, s.hidden);
+        if ((e = fwd_tile_weights_t(W2, s.hidden, s.dim, w2t, st)) != cudaSuccess) return e;
+        if ((e = dact_tc((int)B, s.hidden, s.dim, s.gY, s.gY + B * s.dim, w2t, s.A1, s.dH, s.gA, status, st)) !=
+            cudaSuccess)
+            return e;
+    } else {
+        const float* W2tT = nullptr;
+        if (tc) {
+            if ((e = ensure_weight_tiles(s)) != cudaSuccess) return e;
+            float* dst = s.wt + tile_b_elems(s.hidden, s.P) + tile_b_elems(s.dim, s.hidden);
+            k_tile_b<false><<<grid_of((int64_t)tile_b_elems(s.hidden, s.dim), 256), 256, 0, st>>>(
+                W2, s.hidden, s.hidden, s.dim, tc_tile_n(s.hidden), dst);
+            W2tT = dst;
+        }
+        if ((e = gemm<float, float, true, false>(tc, (int)B, s.hidden, s.dim, 1, s.Yb, s.dim, W2, s.hidden, s.dH,
+                                                 status, st, W2tT)) != cudaSuccess)
+            return e;
+        k_ep_dact<<<grid_of(B * s.hidden, 256), 256, 0, st>>>(s.dH, s.A1, B * s.hidden, wtc ? s.gA : nullptr);
     }
-    if ((e = gemm<float, float, true, false>(tc, (int)B, s.hidden, s.dim, 1, s.Yb, s.dim, W2, s.hidden, s.dH, status,
-                                             st, W2tT)) != cudaSuccess)
-        return e;
-    k_ep_dact<<<grid_of(B * s.hidden, 256), 256, 0, st>>>(s.dH, s.A1, B * s.hidden, wtc ? s.gA : nullptr);
     const TX* Xb = reinterpret_cast<const TX*>(s.Xb);
     const TX* Hb = reinterpret_cast<const TX*>(s.Hb);
     const int S = slices_for(B);

@@ -52,30 +52,41 @@ constexpr int kFThreads = 32 * (2 + kFEpiWarps);         // copy warp, product w
 constexpr size_t kFSmemLimit = 226 * 1024;  // dynamic shared memory of one CTA (227 KB less the static part)
 constexpr int64_t kFWaitLimit = int64_t(1) << 24;        // polls of one mbarrier wait
 
+// What the epilogue makes of the sums C:
+//   kModeOut     Y = C (FP32), by TMA stores;
+//   kModeHidden  A1 = C + b (FP32, optional) and H = GELU(C + b) (BF16, TMA);
+//   kModeDact    dA = C GELU'(A1) (FP32) and its BF16 hi/lo pair, stored
+//                directly; A enters as its hi/lo pair (two A streams).
+enum { kModeOut = 0, kModeHidden = 1, kModeDact = 2 };
+
 struct FwdArgs {
     int M, N, K, n_tiles, stages;
-    int hidden;               // 1: bias + GELU into H (BF16), 0: the sums into Y (FP32)
+    int mode;
+    int nA;                   // A matrices per stage: 1, or 2 (hi, lo) in kModeDact
     const __nv_bfloat16* Wt;  // W_hi then W_lo, core-matrix layout
-    const float* bias;        // hidden layer: [N], 16-byte aligned
-    float* A1;                // hidden layer, nullable: [M][N] sums + bias
+    const float* bias;        // kModeHidden: [N], 16-byte aligned
+    float* A1;                // kModeHidden, nullable: [M][N] sums + bias
+    const float* A1in;        // kModeDact: [M][N] the pre-activations
+    float* dA;                // kModeDact: [M][N]
+    __nv_bfloat16* dA_hl;     // kModeDact: [2][M][N] hi, lo
     uint32_t* status;
 };
 
 // Staging buffer of one epilogue warp: a 32 x 16 block of the output (BF16
-// rows of 32 bytes for H, FP32 rows of 64 bytes for Y).
-constexpr uint32_t out_block_bytes(bool hidden) { return hidden ? 32 * 32 : 32 * 64; }
+// rows of 32 bytes for H, FP32 rows of 64 bytes for Y; none for dA).
+constexpr uint32_t out_block_bytes(int mode) { return mode == kModeHidden ? 32 * 32 : mode == kModeOut ? 32 * 64 : 0; }
 
 size_t w_bytes(int N, int K) { return fwd_w16_elems(N, K) * sizeof(__nv_bfloat16); }
 
-int stages_for(int N, int K, bool hidden) {
+int stages_for(int N, int K, int mode, int nA) {
     // 1024: room to align the stages
-    const size_t fixed = 1024 + w_bytes(N, K) + (size_t)kFEpiWarps * out_block_bytes(hidden);
+    const size_t fixed = 1024 + w_bytes(N, K) + (size_t)kFEpiWarps * out_block_bytes(mode);
     if (fixed >= kFSmemLimit) return 0;
-    return (int)std::min<size_t>(kFMaxStages, (kFSmemLimit - fixed) / kFStageBytes);
+    return (int)std::min<size_t>(kFMaxStages, (kFSmemLimit - fixed) / ((size_t)nA * kFStageBytes));
 }
 
-size_t smem_bytes(int N, int K, int stages, bool hidden) {
-    return 1024 + (size_t)stages * kFStageBytes + w_bytes(N, K) + (size_t)kFEpiWarps * out_block_bytes(hidden);
+size_t smem_bytes(int N, int K, int stages, int mode, int nA) {
+    return 1024 + (size_t)stages * nA * kFStageBytes + w_bytes(N, K) + (size_t)kFEpiWarps * out_block_bytes(mode);
 }
 
 // Shared-memory descriptor of an A stage: start >> 4; leading offset unused
@@ -184,6 +195,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 }
 
 __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fwd_tc(const __grid_constant__ CUtensorMap tmA,
+                                                             const __grid_constant__ CUtensorMap tmA2,
                                                              const __grid_constant__ CUtensorMap tmO, FwdArgs a) {
     extern __shared__ unsigned char fwd_raw[];
     __shared__ __align__(8) uint64_t full[kFMaxStages], empty[kFMaxStages], tfull[2], tempty[2], wbar, fin;
@@ -192,11 +204,12 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fwd_tc(const __grid_consta
     volatile uint32_t* abort_flag = &abort_word;
     unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(fwd_raw) + 1023) & ~(uintptr_t)1023);
     const int S = a.stages, N = a.N, K = a.K;
-    unsigned char* sA = base;                                                            // S stages of 16 KB
-    __nv_bfloat16* sW = reinterpret_cast<__nv_bfloat16*>(base + (size_t)S * kFStageBytes);  // W_hi, W_lo
+    const uint32_t sbytes = (uint32_t)a.nA * kFStageBytes;  // a stage: A (or A_hi, A_lo), 16 KB each
+    unsigned char* sA = base;                                // S stages
+    __nv_bfloat16* sW = reinterpret_cast<__nv_bfloat16*>(base + (size_t)S * sbytes);  // W_hi, W_lo
     // the epilogue warps' staging blocks (1024-byte aligned: N K 4 is a multiple of 4096)
     const uint32_t wbytes = (uint32_t)(2 * (size_t)N * K * sizeof(__nv_bfloat16));
-    unsigned char* sOut = base + (size_t)S * kFStageBytes + (size_t)wbytes;
+    unsigned char* sOut = base + (size_t)S * sbytes + (size_t)wbytes;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nks = (K + kFKS - 1) / kFKS;
     uint32_t cols = 32;
@@ -239,8 +252,9 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fwd_tc(const __grid_consta
                         ok = false;
                         break;
                     }
-                    mbar_arrive_expect_tx(&full[st], kFStageBytes);
-                    tma_load_2d(sA + (size_t)st * kFStageBytes, &tmA, ks * kFKS, t * kFM, &full[st]);
+                    mbar_arrive_expect_tx(&full[st], sbytes);
+                    tma_load_2d(sA + (size_t)st * sbytes, &tmA, ks * kFKS, t * kFM, &full[st]);
+                    if (a.nA == 2) tma_load_2d(sA + (size_t)st * sbytes + kFStageBytes, &tmA2, ks * kFKS, t * kFM, &full[st]);
                     ++g;
                 }
             }
@@ -274,7 +288,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fwd_tc(const __grid_consta
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t sa = smem_addr(sA + (size_t)st * kFStageBytes);
+                    const uint32_t sa = smem_addr(sA + (size_t)st * sbytes);
 #pragma unroll
                     for (int kk = 0; kk < kFKS / 16; ++kk) {
                         const int k = ks * kFKS + kk * 16;
@@ -283,6 +297,9 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fwd_tc(const __grid_consta
                         const uint32_t wo = (uint32_t)(k >> 3) * 128u;
                         tc_mma(d, da, desc_w(w_hi + wo, sbo), idesc, (ks | kk) ? 1u : 0u);
                         tc_mma(d, da, desc_w(w_lo + wo, sbo), idesc, 1u);
+                        // A_lo W_hi; A_lo W_lo, about 2^-18 of the product, is left
+                        // out, as the weights' own truncation at about 2^-17 is
+                        if (a.nA == 2) tc_mma(d, desc_a(sa + kFStageBytes + (uint32_t)kk * 32u), desc_w(w_hi + wo, sbo), idesc, 1u);
                     }
                     tc_commit(&empty[st]);  // the stage is free once these products are done
                 }
@@ -297,8 +314,9 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fwd_tc(const __grid_consta
     } else {
         const int e = warp - 2, q = warp & 3, h = e >> 2;
         const int quarter = N / 4;
-        const bool hid = a.hidden != 0;
-        unsigned char* blk = sOut + (size_t)e * out_block_bytes(hid);
+        const int mode = a.mode;
+        const bool hid = mode == kModeHidden;
+        unsigned char* blk = sOut + (size_t)e * out_block_bytes(mode);
         const uint32_t so = smem_addr(blk);
         uint32_t i = 0;
         for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++i) {
@@ -310,6 +328,41 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fwd_tc(const __grid_consta
             for (int c0 = h * quarter; c0 < (h + 1) * quarter; c0 += kFChunk) {
                 uint32_t r[16];
                 tc_ld16(tmem + ((uint32_t)(q * 32) << 16) + acc * (uint32_t)N + (uint32_t)c0, r);
+                if (mode == kModeDact) {
+                    // dA = C GELU'(A1), FP32 and its BF16 hi/lo pair, this row's 16 columns
+                    if (row < a.M) {
+                        const size_t o = (size_t)row * N + c0;
+                        const float4* ap = reinterpret_cast<const float4*>(a.A1in + o);
+                        float v[16];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float4 a1 = __ldg(ap + j);
+                            v[4 * j] = __uint_as_float(r[4 * j]) * gelu_grad_fast(a1.x);
+                            v[4 * j + 1] = __uint_as_float(r[4 * j + 1]) * gelu_grad_fast(a1.y);
+                            v[4 * j + 2] = __uint_as_float(r[4 * j + 2]) * gelu_grad_fast(a1.z);
+                            v[4 * j + 3] = __uint_as_float(r[4 * j + 3]) * gelu_grad_fast(a1.w);
+                        }
+                        float4* dp = reinterpret_cast<float4*>(a.dA + o);
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) dp[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                        float hi[16], lo[16];
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            hi[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
+                            lo[j] = v[j] - hi[j];
+                        }
+                        uint4* hp = reinterpret_cast<uint4*>(a.dA_hl + o);
+                        uint4* lp = reinterpret_cast<uint4*>(a.dA_hl + (size_t)a.M * N + o);
+#pragma unroll
+                        for (int j = 0; j < 2; ++j) {
+                            hp[j] = make_uint4(pack_bf16x2(hi[8 * j], hi[8 * j + 1]), pack_bf16x2(hi[8 * j + 2], hi[8 * j + 3]),
+                                               pack_bf16x2(hi[8 * j + 4], hi[8 * j + 5]), pack_bf16x2(hi[8 * j + 6], hi[8 * j + 7]));
+                            lp[j] = make_uint4(pack_bf16x2(lo[8 * j], lo[8 * j + 1]), pack_bf16x2(lo[8 * j + 2], lo[8 * j + 3]),
+                                               pack_bf16x2(lo[8 * j + 4], lo[8 * j + 5]), pack_bf16x2(lo[8 * j + 6], lo[8 * j + 7]));
+                        }
+                    }
+                    continue;
+                }
                 // the block's previous store has read the staging buffer
                 if (lane == 0) bulk_wait_read();
                 __syncwarp();
@@ -532,12 +585,14 @@ __global__ void __launch_bounds__(kWThreads, 1)
     }
 }
 
-// W -> hi/lo BF16 tiles (see fwd_tile_weights).
+// W -> hi/lo BF16 tiles (see fwd_tile_weights); TRANS: W is stored K x N
+// (row-major), its transpose is tiled.
+template <bool TRANS>
 __global__ void k_tile_w16(const float* __restrict__ W, int N, int K, __nv_bfloat16* __restrict__ Wt) {
     const int64_t total = (int64_t)N * K;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
         const int n = (int)(i / K), k = (int)(i % K);
-        const float w = W[i];
+        const float w = TRANS ? W[(int64_t)k * N + n] : W[i];
         const __nv_bfloat16 hi = __float2bfloat16_rn(w);
         const __nv_bfloat16 lo = __float2bfloat16_rn(w - __bfloat162float(hi));  // w - hi is exact in FP32
         const int64_t o = (int64_t)(n >> 3) * (K * 8) + (k >> 3) * 64 + (n & 7) * 8 + (k & 7);
@@ -564,40 +619,44 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
 
 bool fwd_tc_supported(int N, int K) {
     // (the output layer's staging is the larger: both layers fit when it does)
-    return N >= 64 && N <= 256 && N % (4 * kFChunk) == 0 && K >= 16 && K % 16 == 0 && stages_for(N, K, false) >= 2;
+    return N >= 64 && N <= 256 && N % (4 * kFChunk) == 0 && K >= 16 && K % 16 == 0 &&
+           stages_for(N, K, kModeOut, 1) >= 2;
 }
 
 cudaError_t fwd_tile_weights(const float* W, int N, int K, __nv_bfloat16* Wt, cudaStream_t s) {
     const int64_t total = (int64_t)N * K;
     const int blocks = (int)std::min<int64_t>((total + 255) / 256, 1024);
-    k_tile_w16<<<blocks, 256, 0, s>>>(W, N, K, Wt);
+    k_tile_w16<false><<<blocks, 256, 0, s>>>(W, N, K, Wt);
     return cudaGetLastError();
 }
 
-cudaError_t fwd_tc(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Wt, const float* bias, float* A1,
-                   __nv_bfloat16* H, float* Y, uint32_t* status, cudaStream_t s) {
-    if (M <= 0) return cudaSuccess;
-    const bool hidden = H != nullptr;
-    if (!fwd_tc_supported(N, K) || (hidden ? bias == nullptr || (reinterpret_cast<uintptr_t>(bias) & 15) : Y == nullptr))
-        return cudaErrorInvalidValue;
+namespace {
+
+// One launch of k_mlp_fwd_tc in `mode` (see kModeOut ...).
+cudaError_t launch_fwd(int mode, int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* A_lo,
+                       const __nv_bfloat16* Wt, const float* bias, float* A1, const float* A1in, __nv_bfloat16* H,
+                       float* Y, float* dA, __nv_bfloat16* dA_hl, uint32_t* status, cudaStream_t s) {
     PFN_cuTensorMapEncodeTiled_v12000 encode = encode_tiled();
     if (!encode) return cudaErrorNotSupported;
+    const int nA = A_lo ? 2 : 1;
     const cuuint32_t elem_strides[2] = {1, 1};
-    // A: K columns (inner) x M rows, row pitch 2K bytes; boxes of 64 x 128
-    CUtensorMap map;
-    {
+    // A (and A_lo): K columns (inner) x M rows, row pitch 2K bytes; boxes of 64 x 128
+    auto a_map = [&](CUtensorMap* map, const __nv_bfloat16* p) {
         const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)M};
         const cuuint64_t strides[1] = {(cuuint64_t)K * sizeof(__nv_bfloat16)};
         const cuuint32_t box[2] = {(cuuint32_t)kFKS, (cuuint32_t)kFM};
-        if (encode(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(A), dims, strides, box,
-                   elem_strides, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-            return cudaErrorInvalidValue;
-    }
-    // the output (H: BF16, Y: FP32): N columns x M rows, boxes of 16 x 32,
-    // swizzled over the box's row (32 or 64 bytes)
-    CUtensorMap omap;
-    {
+        return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(p), dims, strides, box,
+                      elem_strides, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    };
+    CUtensorMap map, map2;
+    if (!a_map(&map, A) || !a_map(&map2, A_lo ? A_lo : A)) return cudaErrorInvalidValue;
+    // the output of kModeHidden (H: BF16) or kModeOut (Y: FP32): N columns x
+    // M rows, boxes of 16 x 32, swizzled over the box's row (32 or 64 bytes);
+    // kModeDact stores directly and takes the A map as a placeholder
+    CUtensorMap omap = map;
+    if (mode != kModeDact) {
+        const bool hidden = mode == kModeHidden;
         const size_t esz = hidden ? sizeof(__nv_bfloat16) : sizeof(float);
         const cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)M};
         const cuuint64_t strides[1] = {(cuuint64_t)N * esz};
@@ -612,8 +671,9 @@ cudaError_t fwd_tc(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloa
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const int stages = stages_for(N, K, hidden);
-    const size_t smem = smem_bytes(N, K, stages, hidden);
+    const int stages = stages_for(N, K, mode, nA);
+    if (stages < 2) return cudaErrorInvalidValue;
+    const size_t smem = smem_bytes(N, K, stages, mode, nA);
     {
         // the kernel's dynamic shared-memory limit, raised per device to the
         // largest launch so far
@@ -633,16 +693,52 @@ cudaError_t fwd_tc(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloa
     a.K = K;
     a.n_tiles = (M + kFM - 1) / kFM;
     a.stages = stages;
-    a.hidden = hidden ? 1 : 0;
+    a.mode = mode;
+    a.nA = nA;
     a.Wt = Wt;
     a.bias = bias;
-    a.A1 = hidden ? A1 : nullptr;
+    a.A1 = mode == kModeHidden ? A1 : nullptr;
+    a.A1in = A1in;
+    a.dA = dA;
+    a.dA_hl = dA_hl;
     a.status = status;
     const int grid = std::min(a.n_tiles, sms);
-    k_mlp_fwd_tc<<<grid, kFThreads, smem, s>>>(map, omap, a);
+    k_mlp_fwd_tc<<<grid, kFThreads, smem, s>>>(map, map2, omap, a);
     return cudaGetLastError();
 }
 
+}  // namespace
+
+cudaError_t fwd_tc(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Wt, const float* bias, float* A1,
+                   __nv_bfloat16* H, float* Y, uint32_t* status, cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    const bool hidden = H != nullptr;
+    if (!fwd_tc_supported(N, K) || (hidden ? bias == nullptr || (reinterpret_cast<uintptr_t>(bias) & 15) : Y == nullptr))
+        return cudaErrorInvalidValue;
+    return launch_fwd(hidden ? kModeHidden : kModeOut, M, N, K, A, nullptr, Wt, bias, A1, nullptr, H, Y, nullptr,
+                      nullptr, status, s);
+}
+
+bool dact_tc_supported(int N, int K) {
+    return N >= 64 && N <= 256 && N % (4 * kFChunk) == 0 && K >= 16 && K % 16 == 0 &&
+           stages_for(N, K, kModeDact, 2) >= 2;
+}
+
+cudaError_t dact_tc(int M, int N, int K, const __nv_bfloat16* A_hi, const __nv_bfloat16* A_lo,
+                    const __nv_bfloat16* Wt, const float* A1, float* dA, __nv_bfloat16* dA_hl, uint32_t* status,
+                    cudaStream_t s) {
+    if (M <= 0) return cudaSuccess;
+    if (!dact_tc_supported(N, K) || !A_lo || !A1 || !dA || !dA_hl) return cudaErrorInvalidValue;
+    return launch_fwd(kModeDact, M, N, K, A_hi, A_lo, Wt, nullptr, nullptr, A1, nullptr, nullptr, dA, dA_hl, status,
+                      s);
+}
+
+cudaError_t fwd_tile_weights_t(const float* W, int N, int K, __nv_bfloat16* Wt, cudaStream_t s) {
+    const int64_t total = (int64_t)N * K;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, 1024);
+    k_tile_w16<true><<<blocks, 256, 0, s>>>(W, N, K, Wt);
+    return cudaGetLastError();
+}
 
 bool wgrad_tc_supported(int M, int N) {
     return M >= kFM && M % kFM == 0 && N >= 16 && N <= 256 && N % 16 == 0 &&

@@ -37,6 +37,19 @@ cudaError_t fwd_tile_weights(const float* W, int N, int K, __nv_bfloat16* Wt, cu
 cudaError_t fwd_tc(int M, int N, int K, const __nv_bfloat16* A, const __nv_bfloat16* Wt, const float* bias, float* A1,
                    __nv_bfloat16* H, float* Y, uint32_t* status, cudaStream_t s);
 
+// dL/da of the hidden layer on the same kernel: dA = (dY W2) * GELU'(A1),
+// dY given as its BF16 hi/lo pair (A_hi, A_lo: M x K row-major, K = dim)
+// and W2^T tiled by fwd_tile_weights_t (N = hidden); three products per 16
+// columns of K (A_hi W_hi, A_hi W_lo, A_lo W_hi).  Writes dA (FP32, M x N)
+// and its hi/lo pair (dA_hl: hi, then lo at dA_hl + M N).
+bool dact_tc_supported(int N, int K);
+cudaError_t dact_tc(int M, int N, int K, const __nv_bfloat16* A_hi, const __nv_bfloat16* A_lo,
+                    const __nv_bfloat16* Wt, const float* A1, float* dA, __nv_bfloat16* dA_hl, uint32_t* status,
+                    cudaStream_t s);
+// The tiles of W^T for W stored K x N row-major (as fwd_tile_weights of the
+// transpose).
+cudaError_t fwd_tile_weights_t(const float* W, int N, int K, __nv_bfloat16* Wt, cudaStream_t s);
+
 // Weight gradients with BF16 activations: part[z][m][n] = sum over the
 // batch rows k of slice z of A[k][m] B[k][n], for A given as its BF16 hi/lo
 // pair (A_hi = bf16(A), A_lo = bf16(A - A_hi), each K x M row-major) and B
