@@ -228,9 +228,10 @@ LINE_API line_status line_sample_debug(line_ctx* ctx, int K, uint64_t seed, uint
  * (nodes[i], nodes[i+k]), i = 0 .. L-1, k = 1 .. W, i + k <= L, in (i, k)
  * order.  Negatives are the edge sampler's (domain 0, calls 1..K at counter
  * t).  With reuse r > 1 each walk's pairs serve r passes in a row: sample
- * t takes pair t mod P of walk t / (r P).  The first call builds the
- * per-node arc offsets and weight sums
- * (12 bytes per arc with the kept weights, 8 per node), freed with the graph.
+ * t takes pair t mod P of walk t / (r P).  The first call on a graph builds
+ * the per-node arc offsets and weight sums (12 bytes per arc with the kept
+ * weights, 8 per node); their memory is reused by later graphs that fit and
+ * freed by line_destroy.
  * Errors: LINE_ERR_ARG (K, count, not 1 <= W <= L <= 1024, or reuse
  * outside 1..1024),
  * LINE_ERR_STATE (no graph). */
@@ -244,9 +245,11 @@ LINE_API line_status line_sample_walk_debug(line_ctx* ctx, int K, uint64_t seed,
  * C = 0.  dim in {16, 32, 64, 128, 256}; dtype LINE_DTYPE_F32 or
  * LINE_DTYPE_BF16 (storage; arithmetic is FP32, BF16 write-back uses
  * stochastic rounding: 16 random bits added below the BF16 mantissa, then
- * truncation; the bits of values 4k..4k+3 of a row written by the batch
- * starting at sample t0 are the SplitMix64 output function of a key of
- * (seed, table, row, t0, k)). */
+ * truncation; the 64 bits of values 4k..4k+3 of a row written by the batch
+ * starting at sample t0 are two MurmurHash3 fmix32 words, of b and b + 1,
+ * b = lo32(SplitMix64 output of seed ^ t0 0x9E3779B97F4A7C15) +
+ * (2 row + table) 0x9E3779B1 + 2k, table 0 for U and 1 for C).  Re-creating
+ * tables reuses their device memory when it is large enough. */
 LINE_API line_status line_init_embeddings(line_ctx* ctx, int order, int dim, int dtype, uint64_t seed);
 
 /* Train n_samples samples (global indices sample_offset .. +n_samples-1) of
@@ -374,7 +377,10 @@ LINE_API line_status line_eval_auc(line_ctx* ctx, int orders, int score, const i
 
 /* Create (or replace) the MLP for the U table of `order` (which must exist),
  * hidden width 1..4096, activations act_dtype, initial weights from `seed`.
- * Errors: LINE_ERR_ARG, LINE_ERR_STATE (no graph or tables), LINE_ERR_OOM. */
+ * Replacing an MLP of the same order, width, activation type and node count
+ * keeps its device memory; weights, optimiser state and inputs start over
+ * either way.  Errors: LINE_ERR_ARG, LINE_ERR_STATE (no graph or tables),
+ * LINE_ERR_OOM. */
 LINE_API line_status line_mlp_create(line_ctx* ctx, int order, int hidden, int act_dtype, uint64_t seed);
 
 /* Compute the inputs x of every node from the current U table.  known: a

@@ -56,31 +56,35 @@ line_status check_status(line_ctx* c, const char* what, bool timeout_sticky) {
     return LINE_OK;
 }
 
+// *p holds at least `bytes` (a larger earlier allocation is kept).
+template <typename T>
+cudaError_t grow(T** p, size_t* cap, size_t bytes) {
+    if (*p && *cap >= bytes) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    *cap = 0;
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
+    if (e == cudaSuccess) *cap = bytes;
+    return e;
+}
+
 line_status ensure_row_ptr(line_ctx* c) {
-    if (c->row_ptr) return LINE_OK;
-    int64_t* rp = nullptr;
-    cudaError_t e = cudaMalloc(&rp, sizeof(int64_t) * (size_t)(c->n_nodes + 1));
-    if (e == cudaSuccess) e = row_offsets(c->n_nodes, c->n_arcs, c->src, rp, c->stream);
-    if (e != cudaSuccess) {
-        if (rp) cudaFree(rp);
-        return cuda_fail(c, e, "row offsets");
-    }
-    c->row_ptr = rp;
+    if (c->row_ptr_ok) return LINE_OK;
+    cudaError_t e = grow(&c->row_ptr, &c->row_ptr_cap, sizeof(int64_t) * (size_t)(c->n_nodes + 1));
+    if (e == cudaSuccess) e = row_offsets(c->n_nodes, c->n_arcs, c->src, c->row_ptr, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "row offsets");
+    c->row_ptr_ok = true;
     return LINE_OK;
 }
 
 line_status ensure_walk_tables(line_ctx* c) {
-    if (c->cw) return LINE_OK;
+    if (c->cw_ok) return LINE_OK;
     line_status st = ensure_row_ptr(c);
     if (st) return st;
-    double* cw = nullptr;
-    cudaError_t e = cudaMalloc(&cw, sizeof(double) * (size_t)c->n_arcs);
-    if (e == cudaSuccess) e = walk_cumw(c->n_nodes, c->row_ptr, c->w, cw, c->stream);
-    if (e != cudaSuccess) {
-        if (cw) cudaFree(cw);
-        return cuda_fail(c, e, "walk sampler tables");
-    }
-    c->cw = cw;
+    cudaError_t e = grow(&c->cw, &c->cw_cap, sizeof(double) * (size_t)std::max<int64_t>(1, c->n_arcs));
+    if (e == cudaSuccess) e = walk_cumw(c->n_nodes, c->row_ptr, c->w, c->cw, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "walk sampler tables");
+    c->cw_ok = true;
     return LINE_OK;
 }
 
@@ -95,14 +99,11 @@ void free_tables(Tables& t) {
     t = Tables{};
 }
 
-// The graph is gone: its walk tables are dropped (they are built again for
-// the next graph on first use); the graph and alias buffers stay allocated
-// for the next build (release_graph frees them).
+// The graph is gone: its row offsets and walk tables are out of date (they
+// are built again for the next graph on first use); the graph, alias and
+// walk buffers stay allocated for the next build (release_graph frees them).
 void free_graph(line_ctx* c, bool keep_tables = false) {
-    for (void* p : {(void*)c->row_ptr, (void*)c->cw})
-        if (p) cudaFree(p);
-    c->row_ptr = nullptr;
-    c->cw = nullptr;
+    c->row_ptr_ok = c->cw_ok = false;
     c->w = nullptr;
     c->has_graph = false;
     if (keep_tables) return;
@@ -114,8 +115,11 @@ void free_graph(line_ctx* c, bool keep_tables = false) {
 void release_graph(line_ctx* c) {
     free_graph(c);
     for (void* p : {(void*)c->src, (void*)c->dst, (void*)c->deg, (void*)c->edge_tab, (void*)c->neg_tab, (void*)c->w_buf,
-                    (void*)c->alias_x, c->alias_tmp})
+                    (void*)c->alias_x, c->alias_tmp, (void*)c->row_ptr, (void*)c->cw})
         if (p) cudaFree(p);
+    c->row_ptr = nullptr;
+    c->cw = nullptr;
+    c->row_ptr_cap = c->cw_cap = 0;
     c->src = c->dst = nullptr;
     c->deg = nullptr;
     c->edge_tab = c->neg_tab = nullptr;
@@ -123,18 +127,6 @@ void release_graph(line_ctx* c) {
     c->alias_x = nullptr;
     c->alias_tmp = nullptr;
     c->src_cap = c->dst_cap = c->edge_cap = c->neg_cap = c->deg_cap = c->w_cap = c->x_cap = c->tmp_cap = 0;
-}
-
-// *p holds at least `bytes` (a larger earlier allocation is kept).
-template <typename T>
-cudaError_t grow(T** p, size_t* cap, size_t bytes) {
-    if (*p && *cap >= bytes) return cudaSuccess;
-    if (*p) cudaFree(*p);
-    *p = nullptr;
-    *cap = 0;
-    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(p), bytes);
-    if (e == cudaSuccess) *cap = bytes;
-    return e;
 }
 
 bool dim_ok(int dim) { return dim == 16 || dim == 32 || dim == 64 || dim == 128 || dim == 256; }
@@ -399,11 +391,12 @@ line_status line_init_embeddings(line_ctx* c, int order, int dim, int dtype, uin
     if ((order != 1 && order != 2) || !dim_ok(dim) || (dtype != LINE_DTYPE_F32 && dtype != LINE_DTYPE_BF16))
         return fail(c, LINE_ERR_ARG, "line_init_embeddings: bad order/dim/dtype");
     Tables& t = c->tab[order];
-    free_tables(t);
+    t.ready = false;
+    // the tables' earlier allocations are reused when they are large enough
     const size_t bytes = (size_t)c->n_nodes * dim * elem_size(dtype);
-    cudaError_t e = cudaMalloc(&t.U, bytes);
+    cudaError_t e = grow(&t.U, &t.u_cap, bytes);
     if (e == cudaSuccess) e = init_table(t.U, dtype, c->n_nodes, dim, seed, c->stream);
-    if (e == cudaSuccess && order == 2) e = cudaMalloc(&t.C, bytes);
+    if (e == cudaSuccess && order == 2) e = grow(&t.C, &t.c_cap, bytes);
     if (e == cudaSuccess && order == 2) e = cudaMemsetAsync(t.C, 0, bytes, c->stream);
     if (e != cudaSuccess) {
         free_tables(t);  // nothing of a failed call is kept
@@ -481,8 +474,8 @@ line_status make_train_args(line_ctx* c, const char* what, int order, int dim, i
     a.walk_len = o.walk_length;
     a.window = o.walk_length > 0 ? o.window : 0;
     a.walk_reuse = o.walk_reuse > 0 ? o.walk_reuse : 1;
-    a.row_ptr = c->row_ptr;
-    a.cw = c->cw;
+    a.row_ptr = o.walk_length > 0 ? c->row_ptr : nullptr;
+    a.cw = o.walk_length > 0 ? c->cw : nullptr;
     a.graph = o.graph;
     *out = a;
     return LINE_OK;

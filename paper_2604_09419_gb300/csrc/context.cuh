@@ -13,6 +13,7 @@ namespace line {
 struct Tables {
     void* U = nullptr;
     void* C = nullptr;
+    size_t u_cap = 0, c_cap = 0;  // bytes allocated (a later init that fits reuses them)
     int dim = 0;
     int dtype = 0;
     bool ready = false;
@@ -37,10 +38,13 @@ struct line_ctx {
     int32_t* dst = nullptr;
     float* deg = nullptr;  // weighted out-degree of each node (FP64 sum, stored FP32)
     float* w = nullptr;    // arc weights (null: all 1)
-    // built on first use: the first arc of each node (walks, MLP inputs) and
-    // the running FP64 weight sums per node (walks)
+    // built on first use for the current graph (the *_ok flags): the first
+    // arc of each node (walks, MLP inputs) and the running FP64 weight sums
+    // per node (walks); their allocations outlive the graph, like src..deg
     int64_t* row_ptr = nullptr;
     double* cw = nullptr;
+    bool row_ptr_ok = false, cw_ok = false;
+    size_t row_ptr_cap = 0, cw_cap = 0;
     uint2* edge_tab = nullptr;
     uint2* neg_tab = nullptr;
     // bytes allocated behind src, dst, edge_tab, neg_tab, deg and the weights,

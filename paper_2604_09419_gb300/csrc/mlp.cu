@@ -13,9 +13,11 @@
 // every contraction is one tiled kernel with FP32 FMA accumulation in index
 // order (split over the batch into slices summed in slice order for the
 // weight gradients).  With BF16 activations the contractions run on the
-// tensor cores: the forward products in mlp_fwd.cu (BF16 x BF16 hi/lo
-// weights), the backward ones in k_gemm_tc (TF32).  Either way every sum has
-// a fixed order, so training is bitwise reproducible.  Random numbers: Philox domain 7, call 0
+// tensor cores in mlp_fwd.cu: the forward products and dL/da against the
+// weights' BF16 hi/lo pairs, the weight gradients with dL/dy and dL/da as
+// BF16 hi/lo pairs (k_gemm_tc, TF32, takes shapes those kernels do not).
+// Either way every sum has a fixed order, so training is bitwise
+// reproducible.  Random numbers: Philox domain 7, call 0
 // for minibatch picks (counter s*B + j), call 1 for the initial weights
 // (counter = the parameter's flat index).
 #include <math.h>
@@ -1217,28 +1219,39 @@ line_status line_mlp_create(line_ctx* c, int order, int hidden, int act_dtype, u
         return fail(c, LINE_ERR_ARG, "line_mlp_create: bad order, hidden width or activation type");
     const Tables& t = c->tab[order];
     if (!t.ready) return fail(c, LINE_ERR_STATE, "line_mlp_create: no tables of order %d", order);
-    mlp_destroy(c->mlp);
+    MlpState* s = c->mlp;
     c->mlp = nullptr;
-    MlpState* s = new MlpState();
-    s->order = order;
-    s->dim = t.dim;
-    s->hidden = hidden;
-    s->P = (t.dim + 1 + 15) / 16 * 16;
-    s->act = act_dtype;
-    s->n_nodes = c->n_nodes;
-    const Layout L(*s);
-    s->n_params = L.n;
-    const size_t pb = sizeof(float) * L.n;
-    // params, grads, m and v in one allocation, each at a 256-byte boundary
-    const size_t pbs = (pb + 255) / 256 * 256;
-    cudaError_t e = cudaMalloc(&s->params, 4 * pbs);
-    if (e == cudaSuccess) {
-        unsigned char* b = reinterpret_cast<unsigned char*>(s->params);
-        s->grads = reinterpret_cast<float*>(b + pbs);
-        s->m = reinterpret_cast<float*>(b + 2 * pbs);
-        s->v = reinterpret_cast<float*>(b + 3 * pbs);
+    cudaError_t e = cudaSuccess;
+    if (s && s->order == order && s->dim == t.dim && s->hidden == hidden && s->act == act_dtype &&
+        s->n_nodes == c->n_nodes) {
+        // an MLP of the same shape: its allocations are kept, its contents
+        // start over below (weights, optimiser state, inputs)
+        s->t = 0;
+        s->has_features = false;
+    } else {
+        mlp_destroy(s);
+        s = new MlpState();
+        s->order = order;
+        s->dim = t.dim;
+        s->hidden = hidden;
+        s->P = (t.dim + 1 + 15) / 16 * 16;
+        s->act = act_dtype;
+        s->n_nodes = c->n_nodes;
+        const Layout L0(*s);
+        s->n_params = L0.n;
+        // params, grads, m and v in one allocation, each at a 256-byte boundary
+        const size_t pbs = (sizeof(float) * L0.n + 255) / 256 * 256;
+        e = cudaMalloc(&s->params, 4 * pbs);
+        if (e == cudaSuccess) {
+            unsigned char* b = reinterpret_cast<unsigned char*>(s->params);
+            s->grads = reinterpret_cast<float*>(b + pbs);
+            s->m = reinterpret_cast<float*>(b + 2 * pbs);
+            s->v = reinterpret_cast<float*>(b + 3 * pbs);
+        }
+        if (e == cudaSuccess) e = cudaMalloc(&s->X, (size_t)c->n_nodes * s->P * elem_size(act_dtype));
     }
-    if (e == cudaSuccess) e = cudaMalloc(&s->X, (size_t)c->n_nodes * s->P * elem_size(act_dtype));
+    const Layout L(*s);
+    const size_t pb = sizeof(float) * L.n;
     // inputs not yet computed are zero (line_mlp_features_rows may compute a subset)
     if (e == cudaSuccess) e = cudaMemsetAsync(s->X, 0, (size_t)c->n_nodes * s->P * elem_size(act_dtype), c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(s->m, 0, pb, c->stream);

@@ -321,35 +321,59 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fwd_tc(const __grid_consta
         uint32_t i = 0;
         for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x, ++i) {
             const uint32_t acc = i & 1u, u = i >> 1;
+            const int row0 = t * kFM + q * 32, row = row0 + lane;
+            const int c_end = (h + 1) * quarter;
+            // dL/da: the pre-activations of this warp's first 16 columns are
+            // loaded before the products are waited for, and those of the
+            // next 16 columns while the current ones are worked on
+            float4 a1_next[4];
+            if (mode == kModeDact && row < a.M) {
+                const float4* ap = reinterpret_cast<const float4*>(a.A1in + (size_t)row * N + h * quarter);
+#pragma unroll
+                for (int j = 0; j < 4; ++j) a1_next[j] = __ldg(ap + j);
+            }
             const bool ok = fwd_wait(&tfull[acc], u & 1u, abort_flag, a.status);
             if (!__all_sync(0xFFFFFFFFu, ok)) break;
             tc_fence_after();
-            const int row0 = t * kFM + q * 32, row = row0 + lane;
-            for (int c0 = h * quarter; c0 < (h + 1) * quarter; c0 += kFChunk) {
+            for (int c0 = h * quarter; c0 < c_end; c0 += kFChunk) {
                 uint32_t r[16];
                 tc_ld16(tmem + ((uint32_t)(q * 32) << 16) + acc * (uint32_t)N + (uint32_t)c0, r);
                 if (mode == kModeDact) {
                     // dA = C GELU'(A1), FP32 and its BF16 hi/lo pair, this row's 16 columns
                     if (row < a.M) {
                         const size_t o = (size_t)row * N + c0;
-                        const float4* ap = reinterpret_cast<const float4*>(a.A1in + o);
+                        float4 a1_cur[4];
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) a1_cur[j] = a1_next[j];
+                        if (c0 + kFChunk < c_end) {
+                            const float4* ap = reinterpret_cast<const float4*>(a.A1in + o + kFChunk);
+#pragma unroll
+                            for (int j = 0; j < 4; ++j) a1_next[j] = __ldg(ap + j);
+                        }
                         float v[16];
 #pragma unroll
                         for (int j = 0; j < 4; ++j) {
-                            const float4 a1 = __ldg(ap + j);
-                            v[4 * j] = __uint_as_float(r[4 * j]) * gelu_grad_fast(a1.x);
-                            v[4 * j + 1] = __uint_as_float(r[4 * j + 1]) * gelu_grad_fast(a1.y);
-                            v[4 * j + 2] = __uint_as_float(r[4 * j + 2]) * gelu_grad_fast(a1.z);
-                            v[4 * j + 3] = __uint_as_float(r[4 * j + 3]) * gelu_grad_fast(a1.w);
+                            const float4 a1 = a1_cur[j];
+                            const float2 g0 = __fmul2_rn(make_float2(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1])),
+                                                         gelu_grad_fast2(make_float2(a1.x, a1.y)));
+                            const float2 g1 = __fmul2_rn(make_float2(__uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3])),
+                                                         gelu_grad_fast2(make_float2(a1.z, a1.w)));
+                            v[4 * j] = g0.x;
+                            v[4 * j + 1] = g0.y;
+                            v[4 * j + 2] = g1.x;
+                            v[4 * j + 3] = g1.y;
                         }
                         float4* dp = reinterpret_cast<float4*>(a.dA + o);
 #pragma unroll
                         for (int j = 0; j < 4; ++j) dp[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                         float hi[16], lo[16];
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
+                        for (int j = 0; j < 16; j += 2) {
                             hi[j] = __bfloat162float(__float2bfloat16_rn(v[j]));
-                            lo[j] = v[j] - hi[j];
+                            hi[j + 1] = __bfloat162float(__float2bfloat16_rn(v[j + 1]));
+                            const float2 l = __fadd2_rn(make_float2(v[j], v[j + 1]), make_float2(-hi[j], -hi[j + 1]));
+                            lo[j] = l.x;
+                            lo[j + 1] = l.y;
                         }
                         uint4* hp = reinterpret_cast<uint4*>(a.dA_hl + o);
                         uint4* lp = reinterpret_cast<uint4*>(a.dA_hl + (size_t)a.M * N + o);
@@ -372,10 +396,14 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fwd_tc(const __grid_consta
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const float4 b = __ldg(bp + j);
-                        v[4 * j] = __uint_as_float(r[4 * j]) + b.x;
-                        v[4 * j + 1] = __uint_as_float(r[4 * j + 1]) + b.y;
-                        v[4 * j + 2] = __uint_as_float(r[4 * j + 2]) + b.z;
-                        v[4 * j + 3] = __uint_as_float(r[4 * j + 3]) + b.w;
+                        const float2 s0 = __fadd2_rn(make_float2(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1])),
+                                                     make_float2(b.x, b.y));
+                        const float2 s1 = __fadd2_rn(make_float2(__uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3])),
+                                                     make_float2(b.z, b.w));
+                        v[4 * j] = s0.x;
+                        v[4 * j + 1] = s0.y;
+                        v[4 * j + 2] = s1.x;
+                        v[4 * j + 3] = s1.y;
                     }
                     if (a.A1 && row < a.M) {
                         float4* p = reinterpret_cast<float4*>(a.A1 + (size_t)row * N + c0);
@@ -385,12 +413,16 @@ __global__ void __launch_bounds__(kFThreads, 1) k_mlp_fwd_tc(const __grid_consta
                     // row `lane` of the block: 2 pieces of 16 bytes, piece j at
                     // j ^ ((lane >> 2) & 1) (the map's 32-byte swizzle)
 #pragma unroll
-                    for (int j = 0; j < 2; ++j)
-                        st_shared_v4(so + (uint32_t)lane * 32u + ((uint32_t)(j ^ ((lane >> 2) & 1)) << 4),
-                                     pack_bf16x2(gelu_bf16out(v[8 * j]), gelu_bf16out(v[8 * j + 1])),
-                                     pack_bf16x2(gelu_bf16out(v[8 * j + 2]), gelu_bf16out(v[8 * j + 3])),
-                                     pack_bf16x2(gelu_bf16out(v[8 * j + 4]), gelu_bf16out(v[8 * j + 5])),
-                                     pack_bf16x2(gelu_bf16out(v[8 * j + 6]), gelu_bf16out(v[8 * j + 7])));
+                    for (int j = 0; j < 2; ++j) {
+                        uint32_t w[4];
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            const float2 gq = gelu_bf16out2(make_float2(v[8 * j + 2 * q], v[8 * j + 2 * q + 1]));
+                            w[q] = pack_bf16x2(gq.x, gq.y);
+                        }
+                        st_shared_v4(so + (uint32_t)lane * 32u + ((uint32_t)(j ^ ((lane >> 2) & 1)) << 4), w[0], w[1],
+                                     w[2], w[3]);
+                    }
                 } else {
                     // 4 pieces of 16 bytes, piece j at j ^ ((lane >> 1) & 3) (64-byte swizzle)
 #pragma unroll

@@ -1681,10 +1681,14 @@ struct Buf {
 // data phase of chunk c reads the other.
 struct ChunkSet {
     Buf rec, slot_info, depmap, mdesc, mcount, ldesc, lcount, eta, tchunk;
-    // captured data phase of a full chunk of this set, and what it was captured for
+    // captured data phase of a full chunk of this set, and what it was
+    // captured for: the parameters, the warps per block and the kernels (the
+    // launcher of one row width and table type: tables of another type can
+    // sit at the same addresses)
     cudaGraphExec_t graph = nullptr;
     DataParams graph_key{};
     int graph_wpb = -1;
+    cudaError_t (*graph_fn)(const DataParams&, int, cudaStream_t) = nullptr;
     cudaEvent_t prep_done = nullptr;  // pre-pass of the set's current chunk finished
     cudaEvent_t data_done = nullptr;  // data phase of the set's previous chunk finished
     bool data_pending = false;
@@ -2192,7 +2196,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
                 dp.t_chunk_dev = (const uint64_t*)cset.tchunk.p;
                 DataParams key = dp;
                 key.t_chunk = 0;
-                if (!cset.graph || cset.graph_wpb != a.warps_per_block ||
+                if (!cset.graph || cset.graph_wpb != a.warps_per_block || cset.graph_fn != data ||
                     memcmp(&key, &cset.graph_key, sizeof key) != 0) {
                     if (cset.graph) cudaGraphExecDestroy(cset.graph);
                     cset.graph = nullptr;
@@ -2212,6 +2216,7 @@ cudaError_t train_run(const TrainArgs& a, TrainWorkspace* ws, uint32_t* status, 
                     } else {
                         cset.graph_key = key;
                         cset.graph_wpb = a.warps_per_block;
+                        cset.graph_fn = data;
                     }
                 }
                 if (cset.graph) {

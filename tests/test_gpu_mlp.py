@@ -251,6 +251,35 @@ def test_training_bf16_tracks_oracle_and_is_deterministic(ctx):
     assert np.array_equal(again, losses) and np.array_equal(ctx.mlp_get_params(), p1)
 
 
+def test_recreate_same_shape_starts_over(ctx):
+    """line_mlp_create over an MLP of the same shape keeps its memory but
+    starts over: initial weights, cleared inputs, zero optimiser state."""
+    from paper_2604_09419_gb300 import line as L
+    dim, hidden = 128, 256
+    g, U, known, X = setup(ctx, "rmat14", dim, L.DTYPE_BF16, hidden=hidden)
+    nodes = np.flatnonzero(known).astype(np.int32)
+    p0 = ctx.mlp_get_params()
+    losses = ctx.mlp_train(nodes, steps=6, batch=512, lr=1e-3, seed=8)
+    p1 = ctx.mlp_get_params()
+    for _ in range(2):
+        ctx.mlp_create(2, hidden=hidden, act_dtype=L.DTYPE_BF16, seed=11)
+        assert np.array_equal(ctx.mlp_get_params(), p0)
+        few = nodes[:10]
+        ctx.mlp_features_rows(known, few)
+        feats = np.empty((g.n_nodes, OM.in_width(dim)), np.float32)
+        ctx.mlp_get_features(feats)
+        others = np.ones(g.n_nodes, bool)
+        others[few] = False
+        assert not feats[others].any() and feats[few].any()
+        ctx.mlp_features(known)
+        again = ctx.mlp_train(nodes, steps=6, batch=512, lr=1e-3, seed=8)
+        assert np.array_equal(again, losses) and np.array_equal(ctx.mlp_get_params(), p1)
+    # another width, then this one again
+    ctx.mlp_create(2, hidden=64, act_dtype=L.DTYPE_BF16, seed=11)
+    ctx.mlp_create(2, hidden=hidden, act_dtype=L.DTYPE_BF16, seed=11)
+    assert np.array_equal(ctx.mlp_get_params(), p0)
+
+
 def test_predict_bf16_activations_on_the_tensor_cores(ctx):
     """BF16 activations at d = 128, hidden 256: both forward products run on
     the tensor cores (activations by TMA, weights as BF16 hi/lo pairs).

@@ -202,6 +202,30 @@ def test_autotune_keeps_tables_and_returns_a_valid_configuration(ctx):
     assert np.array_equal(V1, X1) and np.array_equal(V2, X2) and np.array_equal(W2, Y2)
 
 
+def test_tables_recreated_in_place_with_another_type(ctx):
+    """init_embeddings reuses the tables' memory: a run after tables of the
+    other type (same addresses, replayed CUDA graphs of full chunks) equals
+    the run of a fresh context."""
+    g = G.graph("rmat14")
+    n = 5 * (1 << 18) + 777
+
+    def run(c, dtype):
+        c.init_embeddings(2, 16, dtype, seed=2)
+        c.train_steps(2, 16, 5, n, 9, batch=4096, total=n)
+        return G.tables(c, g, 2, 16)
+
+    fresh = {}
+    for dtype in (0, 1):
+        c = G.context()
+        G.upload(c, g)
+        fresh[dtype] = run(c, dtype)
+        c.close()
+    G.upload(ctx, g)
+    for dtype in (0, 1, 0, 1):
+        U, C = run(ctx, dtype)
+        assert np.array_equal(U, fresh[dtype][0]) and np.array_equal(C, fresh[dtype][1]), dtype
+
+
 @pytest.mark.parametrize("dtype", [0, 1])
 def test_train_orders_long_call_equals_two_sequential_calls(ctx, dtype):
     """A call longer than one slice (the orders are issued in alternate
