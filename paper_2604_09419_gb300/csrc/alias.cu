@@ -65,16 +65,6 @@ __global__ void k_edge_weights(int64_t n, const float* __restrict__ w, double* _
         x[e] = w ? (double)w[e] : 1.0;
 }
 
-__device__ __forceinline__ int64_t lower_bound_i32(const int32_t* a, int64_t n, int32_t v) {
-    int64_t lo = 0, hi = n;
-    while (lo < hi) {
-        const int64_t mid = (lo + hi) >> 1;
-        if (a[mid] < v) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
 __device__ __forceinline__ void store_neg_weight(double d, int64_t v, double* __restrict__ x, float* __restrict__ deg) {
     double r = 0.0;
     if (d > 0.0) {
@@ -96,18 +86,18 @@ __global__ void k_weights_integral(int64_t n, const float* __restrict__ w, uint3
 }
 
 // x_v = d(v)^0.75 = sqrt(d) * sqrt(sqrt(d)), d = weights of v's arcs summed in
-// arc order (src is sorted, so v's arcs are one contiguous range).  Integer
-// weights (flag == 0): a warp per node sums them in 64-bit integers - exact,
-// so equal to the FP64 sum in arc order (partial sums stay below 2^53).
-__global__ void k_neg_weights_int(int64_t n_nodes, int64_t n_arcs, const int32_t* __restrict__ src,
+// arc order (src is sorted, so v's arcs are the range row_ptr[v] ..
+// row_ptr[v+1]).  Integer weights (flag == 0): a warp per node sums them in
+// 64-bit integers - exact, so equal to the FP64 sum in arc order (partial
+// sums stay below 2^53).
+__global__ void k_neg_weights_int(int64_t n_nodes, const int64_t* __restrict__ row_ptr,
                                   const float* __restrict__ w, const uint32_t* flag, double* __restrict__ x,
                                   float* __restrict__ deg) {
     if (flag && *flag) return;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     for (int64_t v = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); v < n_nodes; v += warps) {
-        const int64_t lo = lower_bound_i32(src, n_arcs, (int32_t)v);
-        const int64_t hi = lower_bound_i32(src, n_arcs, (int32_t)(v + 1));
+        const int64_t lo = row_ptr[v], hi = row_ptr[v + 1];
         unsigned long long sum = 0;
         if (w) {
             for (int64_t e = lo + lane; e < hi; e += 32) sum += (unsigned long long)w[e];
@@ -122,14 +112,13 @@ __global__ void k_neg_weights_int(int64_t n_nodes, int64_t n_arcs, const int32_t
 
 // Any other weights (flag != 0): one thread per node adds them in FP64 in arc
 // order.
-__global__ void k_neg_weights(int64_t n_nodes, int64_t n_arcs, const int32_t* __restrict__ src,
+__global__ void k_neg_weights(int64_t n_nodes, const int64_t* __restrict__ row_ptr,
                               const float* __restrict__ w, const uint32_t* flag, double* __restrict__ x,
                               float* __restrict__ deg) {
     if (!*flag) return;
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n_nodes;
          v += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t lo = lower_bound_i32(src, n_arcs, (int32_t)v);
-        const int64_t hi = lower_bound_i32(src, n_arcs, (int32_t)(v + 1));
+        const int64_t lo = row_ptr[v], hi = row_ptr[v + 1];
         double d = 0.0;
         for (int64_t e = lo; e < hi; ++e) d = __dadd_rn(d, (double)w[e]);
         store_neg_weight(d, v, x, deg);
@@ -333,18 +322,17 @@ cudaError_t edge_weights(int64_t n_arcs, const float* w, double* x, cudaStream_t
     return cudaGetLastError();
 }
 
-cudaError_t neg_weights(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const float* w, double* x, float* deg,
+cudaError_t neg_weights(int64_t n_nodes, int64_t n_arcs, const int64_t* row_ptr, const float* w, double* x, float* deg,
                         uint32_t* flag, cudaStream_t s) {
     if (!w) {  // unit weights: the arc counts
-        k_neg_weights_int<<<grid_for(n_nodes * 32, 256, 152 * 64), 256, 0, s>>>(n_nodes, n_arcs, src, w, nullptr, x,
-                                                                              deg);
+        k_neg_weights_int<<<grid_for(n_nodes * 32, 256, 152 * 64), 256, 0, s>>>(n_nodes, row_ptr, w, nullptr, x, deg);
         return cudaGetLastError();
     }
     cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     k_weights_integral<<<grid_for(n_arcs, 256, 152 * 32), 256, 0, s>>>(n_arcs, w, flag);
-    k_neg_weights_int<<<grid_for(n_nodes * 32, 256, 152 * 64), 256, 0, s>>>(n_nodes, n_arcs, src, w, flag, x, deg);
-    k_neg_weights<<<grid_for(n_nodes, 128, 1 << 20), 128, 0, s>>>(n_nodes, n_arcs, src, w, flag, x, deg);
+    k_neg_weights_int<<<grid_for(n_nodes * 32, 256, 152 * 64), 256, 0, s>>>(n_nodes, row_ptr, w, flag, x, deg);
+    k_neg_weights<<<grid_for(n_nodes, 128, 1 << 20), 128, 0, s>>>(n_nodes, row_ptr, w, flag, x, deg);
     return cudaGetLastError();
 }
 

@@ -264,8 +264,11 @@ line_status line_build_alias(line_ctx* c, const line_graph_desc* g) {
         if ((e = edge_weights(m, w, x, s)) != cudaSuccess) { result = cuda_fail(c, e, "edge weights"); break; }
         if ((e = alias_build(x, m, c->edge_tab, tmp, c->status, s)) != cudaSuccess) { result = cuda_fail(c, e, "edge alias"); break; }
         if ((result = check_status(c, "line_build_alias (edges)"))) break;
-        // negative table: d(v)^0.75 (Eq. 1)
-        if ((e = neg_weights(n, m, c->src, w, x, c->deg, c->flag + 1, s)) != cudaSuccess) { result = cuda_fail(c, e, "degree weights"); break; }
+        // negative table: d(v)^0.75 (Eq. 1), each node's arcs found by the
+        // row offsets (kept for the walk sampler and the MLP inputs)
+        if ((e = grow(&c->row_ptr, &c->row_ptr_cap, sizeof(int64_t) * (size_t)(n + 1))) != cudaSuccess) { result = cuda_fail(c, e, "row offsets"); break; }
+        if ((e = row_offsets(n, m, c->src, c->row_ptr, s)) != cudaSuccess) { result = cuda_fail(c, e, "row offsets"); break; }
+        if ((e = neg_weights(n, m, c->row_ptr, w, x, c->deg, c->flag + 1, s)) != cudaSuccess) { result = cuda_fail(c, e, "degree weights"); break; }
         if ((e = alias_build(x, n, c->neg_tab, tmp, c->status, s)) != cudaSuccess) { result = cuda_fail(c, e, "negative alias"); break; }
         if ((result = check_status(c, "line_build_alias (negatives)"))) break;
     } while (false);
@@ -278,6 +281,7 @@ line_status line_build_alias(line_ctx* c, const line_graph_desc* g) {
     c->n_nodes = n;
     c->n_arcs = m;
     c->has_graph = true;
+    c->row_ptr_ok = true;
     return LINE_OK;
 }
 

@@ -136,9 +136,9 @@ size_t fixed_sum_tmp_bytes(int64_t n);
 cudaError_t validate_graph(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const int32_t* dst,
                            const float* w, uint32_t* status, cudaStream_t s);
 cudaError_t edge_weights(int64_t n_arcs, const float* w, double* x, cudaStream_t s);
-// x[v] = d(v)^0.75; deg (nullable): d(v) rounded to FP32.  flag: one word
-// of device scratch.
-cudaError_t neg_weights(int64_t n_nodes, int64_t n_arcs, const int32_t* src, const float* w, double* x, float* deg,
+// x[v] = d(v)^0.75; deg (nullable): d(v) rounded to FP32.  row_ptr: the
+// first arc of each node (row_offsets).  flag: one word of device scratch.
+cudaError_t neg_weights(int64_t n_nodes, int64_t n_arcs, const int64_t* row_ptr, const float* w, double* x, float* deg,
                         uint32_t* flag, cudaStream_t s);
 size_t alias_build_tmp_bytes(int64_t n);
 // Builds tab[n] = {thr, alias} from weights x[n] (FP64).  tmp: alias_build_tmp_bytes(n).
