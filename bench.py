@@ -945,10 +945,16 @@ def main():
         outs = [torch.empty((g.n_nodes, DIM), dtype=tt).pin_memory() for _ in range(3)]
         ctx2 = L.Context(local, stream.cuda_stream)
 
+        phases = []
+
         def e2e_step():
             # the step's inputs from pinned host memory, the whole path, and
-            # its result (both orders' tables) back to pinned host memory
+            # its result (both orders' tables) back to pinned host memory;
+            # every call but init_embeddings returns after its work is done,
+            # so host stamps between them split the step
+            t = [time.perf_counter()]
             ctx2.build_alias(g.n_nodes, hs, hd, hw)
+            t.append(time.perf_counter())
             ctx2.init_embeddings(1, DIM, tdtype, seed=1)
             ctx2.init_embeddings(2, DIM, tdtype, seed=2)
             if concurrent:
@@ -956,22 +962,30 @@ def main():
             else:
                 for order in (1, 2):
                     ctx2.train_steps(order, DIM, K, S, seed, total=total_per_order, opts=opts(0))
+            t.append(time.perf_counter())
             ctx2.get_embeddings(1, L.WHICH_U, outs[0], tdtype)
             ctx2.get_embeddings(2, L.WHICH_U, outs[1], tdtype)
             ctx2.get_embeddings(2, L.WHICH_C, outs[2], tdtype)
+            t.append(time.perf_counter())
+            phases.append([1e3 * (b - a) for a, b in zip(t, t[1:])])
 
         e2e_step()  # untimed warm-up: the context's first-use allocations
+        phases.clear()
         barrier()
-        t0 = time.perf_counter()
-        for i in range(args.e2e_steps):
-            e2e_step()
-        barrier()
-        dt = time.perf_counter() - t0
+        with ClockSampler(local) as eclk:
+            t0 = time.perf_counter()
+            for i in range(args.e2e_steps):
+                e2e_step()
+            barrier()
+            dt = time.perf_counter() - t0
         ctx2.close()
+        med = [sorted(p[k] for p in phases)[len(phases) // 2] for k in range(3)]
         e2e = {"value": 2 * S * args.e2e_steps * world / dt, "unit": UNIT,
                "h2d_bytes_per_step": int(g.n_arcs * 12), "d2h_bytes_per_step": int(3 * g.n_nodes * rb),
                "includes": "graph upload + alias build + table init + both orders + read-back of U1, U2 and C2",
-               "warmup": 1}
+               "warmup": 1, "steps": args.e2e_steps,
+               "phases_ms_median": {"upload_and_alias_build": med[0], "init_and_training": med[1], "read_back": med[2]},
+               "clocks": eclk.summary()}
 
     cpu = None
     cpu_mt = None

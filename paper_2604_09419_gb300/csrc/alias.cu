@@ -87,26 +87,38 @@ __global__ void k_weights_integral(int64_t n, const float* __restrict__ w, uint3
 
 // x_v = d(v)^0.75 = sqrt(d) * sqrt(sqrt(d)), d = weights of v's arcs summed in
 // arc order (src is sorted, so v's arcs are the range row_ptr[v] ..
-// row_ptr[v+1]).  Integer weights (flag == 0): a warp per node sums them in
-// 64-bit integers - exact, so equal to the FP64 sum in arc order (partial
-// sums stay below 2^53).
+// row_ptr[v+1]).  Integer weights (flag == 0): a warp takes 32 consecutive
+// nodes, sums each node's weights across its lanes in 64-bit integers -
+// exact, so equal to the FP64 sum in arc order (partial sums stay below
+// 2^53) - and lane k keeps node k's sum; then every lane takes the FP64
+// square roots of its own node (all 32 lanes busy on the slow FP64 pipe,
+// not one).
 __global__ void k_neg_weights_int(int64_t n_nodes, const int64_t* __restrict__ row_ptr,
                                   const float* __restrict__ w, const uint32_t* flag, double* __restrict__ x,
                                   float* __restrict__ deg) {
     if (flag && *flag) return;
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t v = blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5); v < n_nodes; v += warps) {
-        const int64_t lo = row_ptr[v], hi = row_ptr[v + 1];
-        unsigned long long sum = 0;
+    for (int64_t v0 = 32 * (blockIdx.x * (int64_t)(blockDim.x >> 5) + (threadIdx.x >> 5)); v0 < n_nodes;
+         v0 += 32 * warps) {
+        // lane k: the arc range of node v0 + k
+        const int64_t vl = v0 + lane;
+        const int64_t lo_l = vl < n_nodes ? row_ptr[vl] : 0, hi_l = vl < n_nodes ? row_ptr[vl + 1] : 0;
+        unsigned long long mine = 0;
         if (w) {
-            for (int64_t e = lo + lane; e < hi; e += 32) sum += (unsigned long long)w[e];
+            const int64_t nk = min((int64_t)32, n_nodes - v0);
+            for (int k = 0; k < nk; ++k) {
+                const int64_t lo = __shfl_sync(0xFFFFFFFFu, lo_l, k), hi = __shfl_sync(0xFFFFFFFFu, hi_l, k);
+                unsigned long long sum = 0;
+                for (int64_t e = lo + lane; e < hi; e += 32) sum += (unsigned long long)w[e];
 #pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+                for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
+                if (lane == k) mine = sum;
+            }
         } else {
-            sum = (unsigned long long)(hi - lo);
+            mine = (unsigned long long)(hi_l - lo_l);
         }
-        if (lane == 0) store_neg_weight((double)sum, v, x, deg);
+        if (vl < n_nodes) store_neg_weight((double)mine, vl, x, deg);
     }
 }
 
@@ -325,13 +337,13 @@ cudaError_t edge_weights(int64_t n_arcs, const float* w, double* x, cudaStream_t
 cudaError_t neg_weights(int64_t n_nodes, int64_t n_arcs, const int64_t* row_ptr, const float* w, double* x, float* deg,
                         uint32_t* flag, cudaStream_t s) {
     if (!w) {  // unit weights: the arc counts
-        k_neg_weights_int<<<grid_for(n_nodes * 32, 256, 152 * 64), 256, 0, s>>>(n_nodes, row_ptr, w, nullptr, x, deg);
+        k_neg_weights_int<<<grid_for(n_nodes, 256, 152 * 16), 256, 0, s>>>(n_nodes, row_ptr, w, nullptr, x, deg);
         return cudaGetLastError();
     }
     cudaError_t e = cudaMemsetAsync(flag, 0, sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
     k_weights_integral<<<grid_for(n_arcs, 256, 152 * 32), 256, 0, s>>>(n_arcs, w, flag);
-    k_neg_weights_int<<<grid_for(n_nodes * 32, 256, 152 * 64), 256, 0, s>>>(n_nodes, row_ptr, w, flag, x, deg);
+    k_neg_weights_int<<<grid_for(n_nodes, 256, 152 * 16), 256, 0, s>>>(n_nodes, row_ptr, w, flag, x, deg);
     k_neg_weights<<<grid_for(n_nodes, 128, 1 << 20), 128, 0, s>>>(n_nodes, row_ptr, w, flag, x, deg);
     return cudaGetLastError();
 }

@@ -140,8 +140,32 @@ __global__ void k_mlp_init(float* __restrict__ p, int H, int P, int D, uint64_t 
 }
 
 // ---- features: one warp per node -------------------------------------------
-constexpr int64_t kHubArcs = 2048;   // nodes with more arcs are summed by a whole CTA
+// Nodes with more than kHubArcs arcs ("hubs") are summed by CTAs of
+// kHubWarps warps, one CTA per chunk of kHubChunk arcs: a hub of hundreds of
+// thousands of arcs is spread over many SMs instead of holding one.
+constexpr int64_t kHubArcs = 256;
+constexpr int64_t kHubChunk = 2048;
 constexpr int kHubWarps = 16;
+constexpr int kPlanThreads = 1024;
+
+// Hub-path scratch for a graph of n_nodes nodes and n_arcs arcs: a bitmap
+// of the hubs already listed (a node requested twice is listed once), the
+// hub count and list, the chunk offsets of all hubs and of the hubs with
+// two or more chunks (whose chunk sums are combined afterwards), and those
+// chunk sums.  At most n_arcs / kHubArcs distinct nodes are hubs; a hub of
+// more than kHubChunk arcs has fewer than 2 deg / kHubChunk chunks, so the
+// multi-chunk hubs have fewer than 2 n_arcs / kHubChunk chunks in all.
+struct HubScratch {
+    int64_t max_hubs, max_multi, map_words;
+    HubScratch(int64_t n_nodes, int64_t n_arcs)
+        : max_hubs(n_arcs / kHubArcs + 1), max_multi(2 * n_arcs / kHubChunk + 1), map_words((n_nodes + 31) / 32) {}
+    size_t list_words() const { return (size_t)max_hubs + 1; }
+    size_t off_words() const { return (size_t)max_hubs + 1; }
+    size_t bytes(int D) const {
+        return sizeof(uint32_t) * ((size_t)map_words + list_words() + 2 * off_words() + (size_t)max_multi) +
+               sizeof(float) * (size_t)max_multi * D + 256;
+    }
+};
 
 // Row geometry of the inputs: lane l holds values [l E, l E + E) of a row of
 // D values (E = D/32, or 1 with lanes >= D idle when D < 32), loaded as one
@@ -264,8 +288,13 @@ struct FeatParams {
     const uint8_t* known;
     int P;
     void* X;
-    uint32_t* hubs;    // listed hub nodes
-    uint32_t* n_hubs;  // their number
+    uint32_t* hub_map;  // [n_nodes / 32] bit v: node v is listed (zero at the call's start)
+    uint32_t* hubs;     // listed hub nodes
+    uint32_t* n_hubs;   // their number
+    uint32_t* off;     // [n_hubs + 1] first chunk of each hub (all hubs)
+    uint32_t* poff;    // [n_hubs + 1] first chunk-sum slot of each multi-chunk hub
+    float* part;       // [slots][D] chunk sums of the multi-chunk hubs
+    uint32_t* pcnt;    // [slots] their known-neighbour counts
     const int32_t* rows;
     int64_t n_rows;
     const uint32_t* flag;
@@ -285,7 +314,10 @@ __global__ void __launch_bounds__(256, 3) k_mlp_features(FeatParams p) {
         const int64_t v = p.rows ? (int64_t)p.rows[r] : r;
         const int64_t lo = __ldg(p.row_ptr + v), hi = __ldg(p.row_ptr + v + 1);
         if (hi - lo > kHubArcs) {
-            if (lane == 0) p.hubs[atomicAdd(p.n_hubs, 1u)] = (uint32_t)v;
+            if (lane == 0) {
+                const uint32_t bit = 1u << (v & 31);
+                if (!(atomicOr(p.hub_map + (v >> 5), bit) & bit)) p.hubs[atomicAdd(p.n_hubs, 1u)] = (uint32_t)v;
+            }
             continue;
         }
         float acc[F::E];
@@ -296,8 +328,74 @@ __global__ void __launch_bounds__(256, 3) k_mlp_features(FeatParams p) {
     }
 }
 
-// One CTA per listed hub: warp w sums the w-th of kHubWarps contiguous arc
-// slices, the partial sums are added in warp order.
+__device__ __forceinline__ uint32_t hub_chunks(const FeatParams& p, uint32_t h) {
+    const int64_t v = p.hubs[h];
+    return (uint32_t)((p.row_ptr[v + 1] - p.row_ptr[v] + kHubChunk - 1) / kHubChunk);
+}
+
+// One CTA: the exclusive prefix sums, in listing order, of the hubs' chunk
+// counts (off) and of the chunk counts of the hubs with two or more chunks
+// (poff); off[n] and poff[n] are the totals.
+__global__ void __launch_bounds__(kPlanThreads) k_hub_plan(FeatParams p) {
+    __shared__ uint32_t wsum[2][kPlanThreads / 32];
+    __shared__ uint32_t carry[2];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t nh = *p.n_hubs;
+    if (threadIdx.x < 2) carry[threadIdx.x] = 0u;
+    __syncthreads();
+    for (uint32_t base = 0; base < nh; base += kPlanThreads) {
+        const uint32_t h = base + threadIdx.x;
+        const uint32_t c = h < nh ? hub_chunks(p, h) : 0u;
+        uint32_t x[2] = {c, c > 1 ? c : 0u};
+        // inclusive warp scans, then the warp totals scanned by warp 0
+#pragma unroll
+        for (int k = 0; k < 2; ++k)
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x[k], o);
+                if (lane >= o) x[k] += y;
+            }
+        if (lane == 31) {
+            wsum[0][warp] = x[0];
+            wsum[1][warp] = x[1];
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                uint32_t t = wsum[k][lane];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+                    if (lane >= o) t += y;
+                }
+                wsum[k][lane] = t;  // inclusive over warps
+            }
+        }
+        __syncthreads();
+        if (h < nh) {
+            const uint32_t before0 = warp ? wsum[0][warp - 1] : 0u, before1 = warp ? wsum[1][warp - 1] : 0u;
+            p.off[h] = carry[0] + before0 + x[0] - c;
+            p.poff[h] = carry[1] + before1 + x[1] - (c > 1 ? c : 0u);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            carry[0] += wsum[0][kPlanThreads / 32 - 1];
+            carry[1] += wsum[1][kPlanThreads / 32 - 1];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        p.off[nh] = carry[0];
+        p.poff[nh] = carry[1];
+    }
+}
+
+// Chunk i of the hubs' arcs (hub h = the last with off[h] <= i, chunk
+// c = i - off[h] of kHubChunk arcs): warp w sums the w-th of kHubWarps
+// contiguous slices of the chunk, the warps' sums are added in warp order;
+// a one-chunk hub's inputs are written at once, the other chunks' sums go
+// to their slots for k_hub_combine.
 template <int D, int UDT, typename TX>
 __global__ void __launch_bounds__(kHubWarps * 32) k_mlp_features_hub(FeatParams p) {
     using F = FGeom<D>;
@@ -305,42 +403,86 @@ __global__ void __launch_bounds__(kHubWarps * 32) k_mlp_features_hub(FeatParams 
     __shared__ int pcnt[kHubWarps];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t nh = *p.n_hubs;
-    for (uint32_t h = blockIdx.x; h < nh; h += gridDim.x) {
+    const uint32_t total = p.off[nh];
+    for (uint32_t i = blockIdx.x; i < total; i += gridDim.x) {
+        uint32_t lo_h = 0, hi_h = nh;  // off[lo_h] <= i < off[hi_h]
+        while (hi_h - lo_h > 1) {
+            const uint32_t mid = (lo_h + hi_h) >> 1;
+            if (p.off[mid] <= i) lo_h = mid;
+            else hi_h = mid;
+        }
+        const uint32_t h = lo_h, c = i - p.off[h];
         const int64_t v = p.hubs[h];
-        const int64_t lo = p.row_ptr[v], hi = p.row_ptr[v + 1];
-        const int64_t per = (hi - lo + kHubWarps - 1) / kHubWarps;
-        const int64_t a = min(hi, lo + warp * per), b = min(hi, a + per);
+        const int64_t vlo = p.row_ptr[v], vhi = p.row_ptr[v + 1];
+        const int64_t clo = vlo + (int64_t)c * kHubChunk, chi = min(vhi, clo + kHubChunk);
+        const int64_t per = (chi - clo + kHubWarps - 1) / kHubWarps;
+        const int64_t a = min(chi, clo + warp * per), b = min(chi, a + per);
         float acc[F::E];
 #pragma unroll
-        for (int i = 0; i < F::E; ++i) acc[i] = 0.0f;
-        const int c = sum_known_rows<D, UDT>(a, b, p.dst, p.U, p.known, acc);
+        for (int k = 0; k < F::E; ++k) acc[k] = 0.0f;
+        const int cw = sum_known_rows<D, UDT>(a, b, p.dst, p.U, p.known, acc);
         if (lane < F::LANES)
 #pragma unroll
-            for (int i = 0; i < F::E; ++i) part[warp][lane * F::E + i] = acc[i];
-        if (lane == 0) pcnt[warp] = c;
+            for (int k = 0; k < F::E; ++k) part[warp][lane * F::E + k] = acc[k];
+        if (lane == 0) pcnt[warp] = cw;
         __syncthreads();
         if (warp == 0) {
             int cnt = 0;
 #pragma unroll
-            for (int i = 0; i < F::E; ++i) acc[i] = 0.0f;
+            for (int k = 0; k < F::E; ++k) acc[k] = 0.0f;
             for (int w = 0; w < kHubWarps; ++w) {
                 cnt += pcnt[w];
                 if (lane < F::LANES)
 #pragma unroll
-                    for (int i = 0; i < F::E; ++i) acc[i] += part[w][lane * F::E + i];
+                    for (int k = 0; k < F::E; ++k) acc[k] += part[w][lane * F::E + k];
             }
-            write_features<D, TX>(reinterpret_cast<TX*>(p.X) + v * (int64_t)p.P, p.deg[v], acc, cnt, p.P);
+            if (vhi - vlo <= kHubChunk) {
+                write_features<D, TX>(reinterpret_cast<TX*>(p.X) + v * (int64_t)p.P, p.deg[v], acc, cnt, p.P);
+            } else {
+                const uint32_t slot = p.poff[h] + c;
+                if (lane < F::LANES)
+#pragma unroll
+                    for (int k = 0; k < F::E; ++k) p.part[(size_t)slot * D + lane * F::E + k] = acc[k];
+                if (lane == 0) p.pcnt[slot] = (uint32_t)cnt;
+            }
         }
         __syncthreads();
+    }
+}
+
+// One warp per hub with two or more chunks: its chunk sums added in chunk
+// order, then its inputs written.
+template <int D, typename TX>
+__global__ void k_hub_combine(FeatParams p) {
+    using F = FGeom<D>;
+    const int lane = threadIdx.x & 31;
+    const uint32_t nh = *p.n_hubs;
+    const uint32_t warps = gridDim.x * (blockDim.x >> 5);
+    for (uint32_t h = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); h < nh; h += warps) {
+        const uint32_t c0 = p.poff[h], c1 = p.poff[h + 1];
+        if (c1 == c0) continue;  // one chunk: written by k_mlp_features_hub
+        float acc[F::E];
+#pragma unroll
+        for (int k = 0; k < F::E; ++k) acc[k] = 0.0f;
+        int cnt = 0;
+        for (uint32_t c = c0; c < c1; ++c) {
+            cnt += (int)p.pcnt[c];
+            if (lane < F::LANES)
+#pragma unroll
+                for (int k = 0; k < F::E; ++k) acc[k] += p.part[(size_t)c * D + lane * F::E + k];
+        }
+        const int64_t v = p.hubs[h];
+        write_features<D, TX>(reinterpret_cast<TX*>(p.X) + v * (int64_t)p.P, p.deg[v], acc, cnt, p.P);
     }
 }
 
 template <int D, int UDT, typename TX>
 cudaError_t launch_features(const FeatParams& p, int64_t count, int64_t max_hubs, cudaStream_t s) {
     const unsigned g = (unsigned)std::min<int64_t>((count + 7) / 8, 152 * 16);
-    const unsigned gh = (unsigned)std::min<int64_t>(max_hubs, 152 * 4);
     k_mlp_features<D, UDT, TX><<<g, 256, 0, s>>>(p);
-    k_mlp_features_hub<D, UDT, TX><<<gh, kHubWarps * 32, 0, s>>>(p);
+    k_hub_plan<<<1, kPlanThreads, 0, s>>>(p);
+    k_mlp_features_hub<D, UDT, TX><<<152 * 4, kHubWarps * 32, 0, s>>>(p);
+    k_hub_combine<D, TX><<<(unsigned)std::min<int64_t>((max_hubs + 7) / 8, 152 * 4), 256, 0, s>>>(p);
     return cudaGetLastError();
 }
 
@@ -1285,15 +1427,17 @@ static line_status mlp_features_impl(line_ctx* c, const char* what, const uint8_
     const Tables& t = c->tab[s.order];
     if ((st = ensure_row_ptr(c))) return st;
     // scratch kept in the MLP state (grown, never shrunk)
-    const int64_t max_hubs = c->n_arcs / kHubArcs + 1;
+    const int64_t max_hubs = HubScratch(c->n_nodes, c->n_arcs).max_hubs;
     cudaError_t e = cudaSuccess;
     if (!s.kmask) e = cudaMalloc(&s.kmask, (size_t)c->n_nodes);
     if (e == cudaSuccess && !s.flag) e = cudaMalloc(&s.flag, sizeof(uint32_t));
-    if (e == cudaSuccess && s.hubs_cap < max_hubs + 1) {
+    const HubScratch hs(c->n_nodes, c->n_arcs);
+    const size_t hub_bytes = hs.bytes(s.dim);
+    if (e == cudaSuccess && s.hubs_cap < (int64_t)hub_bytes) {
         if (s.hubs) cudaFree(s.hubs);
         s.hubs = nullptr;
         s.hubs_cap = 0;
-        if ((e = cudaMalloc(&s.hubs, sizeof(uint32_t) * (size_t)(max_hubs + 1))) == cudaSuccess) s.hubs_cap = max_hubs + 1;
+        if ((e = cudaMalloc(&s.hubs, hub_bytes)) == cudaSuccess) s.hubs_cap = (int64_t)hub_bytes;
     }
     if (e == cudaSuccess && rows && s.frows_cap < n_rows) {
         if (s.frows) cudaFree(s.frows);
@@ -1303,18 +1447,28 @@ static line_status mlp_features_impl(line_ctx* c, const char* what, const uint8_
     }
     if (e != cudaSuccess) return cuda_fail(c, e, what);
     cudaStream_t str = c->stream;
-    uint32_t* hubs = s.hubs;  // [count] then the listed hub nodes
+    // hub scratch: the listed-hub bitmap, [count] then the listed hub
+    // nodes, the chunk offsets (off, poff), the chunk-sum counts and the
+    // chunk sums (256-byte aligned)
+    uint32_t* hub_map = s.hubs;
+    uint32_t* hubs = hub_map + hs.map_words;
+    uint32_t* hub_off = hubs + hs.list_words();
+    uint32_t* hub_poff = hub_off + hs.off_words();
+    uint32_t* hub_pcnt = hub_poff + hs.off_words();
+    float* hub_part = reinterpret_cast<float*>(
+        (reinterpret_cast<uintptr_t>(hub_pcnt + hs.max_multi) + 255) & ~(uintptr_t)255);
     int32_t* rd = rows ? s.frows : nullptr;
     e = cudaMemcpyAsync(s.kmask, known, c->n_nodes, cudaMemcpyDefault, str);
     if (e == cudaSuccess && rows) e = cudaMemcpyAsync(rd, rows, sizeof(int32_t) * n_rows, cudaMemcpyDefault, str);
-    if (e == cudaSuccess) e = cudaMemsetAsync(hubs, 0, sizeof(uint32_t), str);
+    if (e == cudaSuccess) e = cudaMemsetAsync(hub_map, 0, sizeof(uint32_t) * ((size_t)hs.map_words + 1), str);
     if (e == cudaSuccess) e = cudaMemsetAsync(s.flag, 0, sizeof(uint32_t), str);
     if (e == cudaSuccess) {
         // ids out of range are refused before any work: the flag stops the
         // input kernels
         if (rows) k_check_rows<<<grid_of(n_rows, 256, 152 * 16), 256, 0, str>>>(rd, n_rows, c->n_nodes, s.flag);
         const int64_t count = rows ? n_rows : c->n_nodes;
-        FeatParams fp{c->n_nodes, c->row_ptr, c->dst, c->deg, t.U, s.kmask, s.P, s.X, hubs + 1, hubs, rd, n_rows, s.flag};
+        FeatParams fp{c->n_nodes, c->row_ptr, c->dst,  c->deg,   t.U,      s.kmask, s.P,    s.X,   hub_map, hubs + 1,
+                      hubs,       hub_off,    hub_poff, hub_part, hub_pcnt, rd,      n_rows, s.flag};
         if (s.act == LINE_DTYPE_F32)
             e = t.dtype == LINE_DTYPE_F32 ? features_for<LINE_DTYPE_F32, float>(s.dim, fp, count, max_hubs, str)
                                           : features_for<LINE_DTYPE_BF16, float>(s.dim, fp, count, max_hubs, str);

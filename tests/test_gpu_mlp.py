@@ -2,7 +2,9 @@
 
 * initial weights bit-exact (Philox domain 7);
 * inputs (log degree, mean known-neighbour row) within FP32 summation
-  bounds, and within one BF16 rounding for BF16 activations;
+  bounds, and within one BF16 rounding for BF16 activations; the same bits
+  for a row subset (repeated rows and hubs of many arc chunks included) as
+  for the full pass;
 * loss and gradients against the oracle's backpropagation, element by
   element: |g - g_oracle| <= tol max|g_oracle| + tol |g_oracle| per tensor,
   tol 1e-5 (FP32 activations) or 1e-3 (BF16 activations, oracle rounding x
@@ -117,6 +119,32 @@ def test_features_of_a_row_subset(ctx):
     with pytest.raises(L.LineError) as ei:
         ctx.mlp_features_rows(known, np.array([0, g.n_nodes], np.int32))
     assert ei.value.status == L.LINE_ERR_ARG
+
+
+def test_features_of_repeated_rows_and_hubs(ctx):
+    """A row list that names hubs many times (more often than the graph has
+    hubs) and spans hubs of one and of many arc chunks gives the inputs of
+    the full pass for those rows, bit for bit."""
+    from paper_2604_09419_gb300 import line as L
+    g = G.graph("rmat14")
+    G.upload(ctx, g)
+    U, C = trained_tables("rmat14", 64, 40_000, 6)
+    G.upload_tables(ctx, 2, U, C)
+    held, _ = I.hold_out_nodes(g, 0.1, seed=3)
+    known = (~held).astype(np.uint8)
+    deg = np.bincount(g.src, minlength=g.n_nodes)
+    assert deg.max() > 2048 and ((deg > 256) & (deg <= 2048)).any()  # hubs of one and of two chunks
+    hubs = np.flatnonzero(deg > 256).astype(np.int32)
+    rows = np.concatenate([np.repeat(hubs, 40), np.arange(0, g.n_nodes, 5, dtype=np.int32), hubs[::-1]])
+    assert len(rows) > g.n_arcs // 256 + 1
+    ctx.mlp_create(2, hidden=32, act_dtype=L.DTYPE_F32, seed=1)
+    ctx.mlp_features_rows(known, rows)
+    part = np.empty((g.n_nodes, 80), np.float32)
+    ctx.mlp_get_features(part)
+    ctx.mlp_features(known)
+    full = np.empty_like(part)
+    ctx.mlp_get_features(full)
+    assert np.array_equal(part[rows], full[rows]) and part[hubs].any()
 
 
 def test_features_of_a_sample_alone(ctx):
