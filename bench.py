@@ -53,6 +53,7 @@ the host cores instead (a bounded prefix of the same workload).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import statistics
@@ -96,7 +97,7 @@ def parse():
     p.add_argument("--dtype", default="fp32", choices=["fp32", "bf16"],
                    help="table storage of the default and rmat20walk workloads (bf16: stochastic rounding)")
     p.add_argument("--samples-per-step", type=int, default=0, help="0: |E| = 16 * 2^scale")
-    p.add_argument("--e2e-steps", type=int, default=4)
+    p.add_argument("--e2e-steps", type=int, default=6)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-samples", type=int, default=1 << 20)
     p.add_argument("--workload", default="rmat20",
@@ -446,10 +447,13 @@ def warm_compare(scale: int, *, phase0_epochs: int = 10, marks=(0.05, 0.1, 0.2, 
 
     def timed(fn):
         torch.cuda.synchronize()
+        gc.disable()
         t = time.perf_counter()
         fn()
         torch.cuda.synchronize()
-        return time.perf_counter() - t
+        dt = time.perf_counter() - t
+        gc.enable()
+        return dt
 
     E = tr.n_arcs
     n0 = phase0_epochs * kept.n_arcs
@@ -857,12 +861,15 @@ def main():
 
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    gc.collect()
+    gc.disable()  # no collector pause inside a timed region (as timeit does)
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
             step()
         ev1.record(stream)
         barrier()
+    gc.enable()
     ms = ev0.elapsed_time(ev1)
     st = ctx.stats()
     ms = max_over_ranks(ms, world)
@@ -972,12 +979,15 @@ def main():
         e2e_step()  # untimed warm-up: the context's first-use allocations
         phases.clear()
         barrier()
+        gc.collect()
+        gc.disable()
         with ClockSampler(local) as eclk:
             t0 = time.perf_counter()
             for i in range(args.e2e_steps):
                 e2e_step()
             barrier()
             dt = time.perf_counter() - t0
+        gc.enable()
         ctx2.close()
         med = [sorted(p[k] for p in phases)[len(phases) // 2] for k in range(3)]
         e2e = {"value": 2 * S * args.e2e_steps * world / dt, "unit": UNIT,
@@ -985,6 +995,7 @@ def main():
                "includes": "graph upload + alias build + table init + both orders + read-back of U1, U2 and C2",
                "warmup": 1, "steps": args.e2e_steps,
                "phases_ms_median": {"upload_and_alias_build": med[0], "init_and_training": med[1], "read_back": med[2]},
+               "step_ms": [sum(p) for p in phases],
                "clocks": eclk.summary()}
 
     cpu = None

@@ -91,8 +91,9 @@ __global__ void k_weights_integral(int64_t n, const float* __restrict__ w, uint3
 // nodes, sums each node's weights across its lanes in 64-bit integers -
 // exact, so equal to the FP64 sum in arc order (partial sums stay below
 // 2^53) - and lane k keeps node k's sum; then every lane takes the FP64
-// square roots of its own node (all 32 lanes busy on the slow FP64 pipe,
-// not one).
+// square roots of its own node.  GB300's FP64 pipe is slow: the weights
+// (integers in [1, 2^24]) are converted through 32-bit integers, and the
+// FP64 work is one root pair per node on full warps.
 __global__ void k_neg_weights_int(int64_t n_nodes, const int64_t* __restrict__ row_ptr,
                                   const float* __restrict__ w, const uint32_t* flag, double* __restrict__ x,
                                   float* __restrict__ deg) {
@@ -110,7 +111,7 @@ __global__ void k_neg_weights_int(int64_t n_nodes, const int64_t* __restrict__ r
             for (int k = 0; k < nk; ++k) {
                 const int64_t lo = __shfl_sync(0xFFFFFFFFu, lo_l, k), hi = __shfl_sync(0xFFFFFFFFu, hi_l, k);
                 unsigned long long sum = 0;
-                for (int64_t e = lo + lane; e < hi; e += 32) sum += (unsigned long long)w[e];
+                for (int64_t e = lo + lane; e < hi; e += 32) sum += __float2uint_rz(w[e]);
 #pragma unroll
                 for (int o = 16; o >= 1; o >>= 1) sum += __shfl_xor_sync(0xFFFFFFFFu, sum, o);
                 if (lane == k) mine = sum;
