@@ -389,10 +389,12 @@ LINE_API line_status line_mlp_create(line_ctx* ctx, int order, int hidden, int a
 LINE_API line_status line_mlp_features(line_ctx* ctx, const uint8_t* known);
 
 /* Compute the inputs of the nodes rows[0 .. n_rows) only (a buffer of node
- * ids), from the current graph and U table - for a sample of nodes to fit
- * on, or for nodes that joined later; the other nodes' inputs are unchanged
- * (zero until computed: line_mlp_create clears them).  Errors: LINE_ERR_ARG
- * (an id out of range; nothing is computed), LINE_ERR_STATE. */
+ * ids, which may repeat), from the current graph and U table - for a sample
+ * of nodes to fit on, or for nodes that joined later; the other nodes'
+ * inputs are unchanged (zero until computed: line_mlp_create clears them).
+ * A node's inputs are the same bits whether computed here or by
+ * line_mlp_features.  Errors: LINE_ERR_ARG (an id out of range; nothing is
+ * computed), LINE_ERR_STATE. */
 LINE_API line_status line_mlp_features_rows(line_ctx* ctx, const uint8_t* known, const int32_t* rows,
                                             int64_t n_rows);
 
