@@ -861,15 +861,12 @@ def main():
 
     barrier()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    gc.collect()
-    gc.disable()  # no collector pause inside a timed region (as timeit does)
     with ClockSampler(local) as clk:
         ev0.record(stream)
         for _ in range(args.steps):
             step()
         ev1.record(stream)
         barrier()
-    gc.enable()
     ms = ev0.elapsed_time(ev1)
     st = ctx.stats()
     ms = max_over_ranks(ms, world)
@@ -980,7 +977,7 @@ def main():
         phases.clear()
         barrier()
         gc.collect()
-        gc.disable()
+        gc.disable()  # no collector pause inside the host-timed region (as timeit does)
         with ClockSampler(local) as eclk:
             t0 = time.perf_counter()
             for i in range(args.e2e_steps):
